@@ -1,0 +1,252 @@
+"""FP64 CPU oracle for the 4D-GS render path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path and
+never imports it; it accepts any scene/camera object with the attributes of the
+seeded input generator (duck typing), and returns numpy float64 arrays.
+
+The arithmetic lives in ``fs4d_oracle.cpp`` (plain loops in double precision,
+each function citing the passage of the paper it follows).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+F64P = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+I32P = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+U32P = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+U64P = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+
+
+class OrcScene(C.Structure):
+    _fields_ = [("n", C.c_int32), ("sh_degree", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p),
+                ("aabb_min", C.c_double * 3), ("aabb_max", C.c_double * 3),
+                ("n_levels", C.c_int32), ("res_spatial", C.c_int32 * 4), ("res_time", C.c_int32),
+                ("feat_dim", C.c_int32), ("planes", C.c_void_p), ("mlp_width", C.c_int32),
+                ("mlp", C.c_void_p)]
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("znear", C.c_double),
+                ("world_to_cam", C.c_double * 16)]
+
+
+class OrcProjected(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("xy", "conic", "cov2d", "opacity", "rgb", "depth", "radius", "rect",
+                                          "margin")]
+
+
+class OrcGrads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes",
+                                          "mlp")]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_set_threads.argtypes = [C.c_int32]
+        L.orc_plane_sample.argtypes = [C.POINTER(OrcScene), C.c_int32, C.c_int32, C.c_double, C.c_double, F64P]
+        L.orc_features.argtypes = [C.POINTER(OrcScene), F64P, C.c_int32, C.c_double, F64P]
+        L.orc_mlp.argtypes = [C.POINTER(OrcScene), F64P, C.c_int32, F64P]
+        L.orc_deform.argtypes = [C.POINTER(OrcScene), C.c_double, F64P, F64P, F64P]
+        L.orc_sh_basis.argtypes = [C.c_int32, F64P, F64P]
+        L.orc_project.argtypes = [C.POINTER(OrcScene), F64P, F64P, F64P, C.POINTER(OrcCamera), C.c_int32,
+                                  C.POINTER(OrcProjected)]
+        L.orc_bin_sort.argtypes = [C.c_int32, U32P, I32P, C.c_int32, C.c_int32, C.c_int64, U64P, U32P, U32P]
+        L.orc_bin_sort.restype = C.c_int64
+        L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, U32P, U32P, F64P, F64P, F64P, F64P, F64P,
+                                    F64P, F64P, I32P, F64P]
+        L.orc_composite_bruteforce.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, I32P, I32P, F64P,
+                                               F64P, F64P, F64P, F64P, F64P, F64P]
+        L.orc_render.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.c_double, C.c_int32, C.c_int32,
+                                 F64P, F64P, I32P, F64P]
+        L.orc_render.restype = C.c_int64
+        L.orc_render_backward.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.c_double, C.c_int32,
+                                          C.c_int32, F64P, C.POINTER(OrcGrads)]
+        L.orc_render_backward.restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class _SceneHandle:
+    """Keeps the float32 arrays alive while the C struct points at them."""
+
+    def __init__(self, scene):
+        self.arrays = {k: _f32(getattr(scene, k)) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                             "sh", "planes", "mlp")}
+        s = OrcScene()
+        s.n = int(self.arrays["means"].shape[0])
+        s.sh_degree = int(scene.sh_degree)
+        for k, v in self.arrays.items():
+            setattr(s, k, v.ctypes.data)
+        s.aabb_min = (C.c_double * 3)(*[float(v) for v in scene.aabb_min])
+        s.aabb_max = (C.c_double * 3)(*[float(v) for v in scene.aabb_max])
+        rs = list(scene.res_spatial)
+        s.n_levels = len(rs)
+        s.res_spatial = (C.c_int32 * 4)(*(rs + [0] * (4 - len(rs))))
+        s.res_time = int(scene.res_time)
+        s.feat_dim = int(scene.feat_dim)
+        s.mlp_width = int(scene.mlp_width)
+        self.struct = s
+        self.n = s.n
+        self.hin = s.feat_dim * s.n_levels
+        self.k = (s.sh_degree + 1) ** 2
+
+
+def _camera(cam) -> OrcCamera:
+    c = OrcCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy, c.znear = (float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                                       float(cam.znear))
+    c.world_to_cam = (C.c_double * 16)(*[float(v) for v in np.asarray(cam.world_to_cam, np.float64).ravel()])
+    return c
+
+
+def plane_sample(scene, level: int, plane: int, ua: float, ub: float) -> np.ndarray:
+    h = _SceneHandle(scene)
+    out = np.zeros(int(scene.feat_dim), np.float64)
+    lib().orc_plane_sample(C.byref(h.struct), level, plane, ua, ub, out)
+    return out
+
+
+def features(scene, xyz: np.ndarray, t: float) -> np.ndarray:
+    h = _SceneHandle(scene)
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    n = xyz.shape[0]
+    out = np.zeros((n, h.hin), np.float64)
+    lib().orc_features(C.byref(h.struct), xyz, n, float(t), out)
+    return out
+
+
+def mlp(scene, fh: np.ndarray) -> np.ndarray:
+    h = _SceneHandle(scene)
+    fh = np.ascontiguousarray(fh, np.float64)
+    out = np.zeros((fh.shape[0], 10), np.float64)
+    lib().orc_mlp(C.byref(h.struct), fh, fh.shape[0], out)
+    return out
+
+
+def deform(scene, t: float):
+    """Eq. 6 deformed (means, quats, log_scales), float64."""
+    h = _SceneHandle(scene)
+    X = np.zeros((h.n, 3)); Q = np.zeros((h.n, 4)); S = np.zeros((h.n, 3))
+    lib().orc_deform(C.byref(h.struct), float(t), X, Q, S)
+    return X, Q, S
+
+
+def sh_basis(degree: int, direction) -> np.ndarray:
+    out = np.zeros(16, np.float64)
+    lib().orc_sh_basis(int(degree), np.ascontiguousarray(direction, np.float64), out)
+    return out[:(degree + 1) ** 2]
+
+
+def project(scene, cam, means=None, quats=None, log_scales=None, tile: int = 16) -> Dict[str, np.ndarray]:
+    h = _SceneHandle(scene)
+    n = h.n
+    X = np.ascontiguousarray(scene.means if means is None else means, np.float64)
+    Q = np.ascontiguousarray(scene.quats if quats is None else quats, np.float64)
+    S = np.ascontiguousarray(scene.log_scales if log_scales is None else log_scales, np.float64)
+    out = dict(xy=np.zeros((n, 2)), conic=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), opacity=np.zeros(n),
+               rgb=np.zeros((n, 3)), depth=np.zeros(n), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), margin=np.zeros(n))
+    P = OrcProjected(**{k: v.ctypes.data for k, v in out.items()})
+    cc = _camera(cam)
+    lib().orc_project(C.byref(h.struct), X, Q, S, C.byref(cc), int(tile), C.byref(P))
+    return out
+
+
+def bin_sort(depth_bits: np.ndarray, rect: np.ndarray, tiles_x: int, tiles_y: int):
+    """(keys, values, ranges) of the tile binning and (tile, depth, index) sort."""
+    depth_bits = np.ascontiguousarray(depth_bits, np.uint32)
+    rect = np.ascontiguousarray(rect, np.int32)
+    n = depth_bits.shape[0]
+    w = np.maximum(rect[:, 2] - rect[:, 0], 0).astype(np.int64)
+    hgt = np.maximum(rect[:, 3] - rect[:, 1], 0).astype(np.int64)
+    K = int((w * hgt).sum())
+    keys = np.zeros(max(K, 1), np.uint64)
+    values = np.zeros(max(K, 1), np.uint32)
+    ranges = np.zeros(2 * tiles_x * tiles_y, np.uint32)
+    k2 = lib().orc_bin_sort(n, depth_bits, rect, tiles_x, tiles_y, K, keys, values, ranges)
+    assert k2 == K
+    return keys[:K], values[:K], ranges.reshape(tiles_y * tiles_x, 2)
+
+
+def depth_bits(depth: np.ndarray) -> np.ndarray:
+    """float32 bit pattern of each depth: the key decision is taken in float32."""
+    return np.ascontiguousarray(depth, np.float64).astype(np.float32).view(np.uint32)
+
+
+def composite(cam_w: int, cam_h: int, ranges, values, proj, tile: int = 16):
+    n_pix = cam_w * cam_h
+    img = np.zeros((cam_h, cam_w, 3)); T = np.zeros((cam_h, cam_w)); nc = np.zeros((cam_h, cam_w), np.int32)
+    mg = np.zeros((cam_h, cam_w))
+    vals = np.ascontiguousarray(values, np.uint32)
+    if vals.size == 0:
+        vals = np.zeros(1, np.uint32)
+    lib().orc_composite(cam_w, cam_h, tile, np.ascontiguousarray(ranges, np.uint32).ravel(), vals,
+                        proj["xy"], proj["conic"], proj["opacity"], proj["rgb"], proj["depth"], img, T, nc, mg)
+    del n_pix
+    return img, T, nc, mg
+
+
+def composite_bruteforce(cam_w: int, cam_h: int, proj, tile: int = 16):
+    n = proj["depth"].shape[0]
+    img = np.zeros((cam_h, cam_w, 3)); T = np.zeros((cam_h, cam_w))
+    lib().orc_composite_bruteforce(n, cam_w, cam_h, tile, proj["radius"], proj["rect"], proj["xy"],
+                                   proj["conic"], proj["opacity"], proj["rgb"], proj["depth"], img, T)
+    return img, T
+
+
+def render(scene, cam, t: float, deform: bool = True, tile: int = 16):
+    """Full frame: (image [H][W][3], T_final [H][W], n_contrib [H][W], margin [H][W], K)."""
+    h = _SceneHandle(scene)
+    cc = _camera(cam)
+    H, W = int(cam.height), int(cam.width)
+    img = np.zeros((H, W, 3)); T = np.zeros((H, W)); nc = np.zeros((H, W), np.int32); mg = np.zeros((H, W))
+    K = lib().orc_render(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile), img, T, nc, mg)
+    return img, T, nc, mg, int(K)
+
+
+def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16):
+    """Gradients of sum(dl_dimage * image) w.r.t. every scene parameter (float64 dict)."""
+    h = _SceneHandle(scene)
+    cc = _camera(cam)
+    g = dict(means=np.zeros((h.n, 3)), log_scales=np.zeros((h.n, 3)), quats=np.zeros((h.n, 4)),
+             opacity_logits=np.zeros(h.n), sh=np.zeros((h.n, h.k, 3)),
+             planes=np.zeros(h.arrays["planes"].shape[0]), mlp=np.zeros(h.arrays["mlp"].shape[0]))
+    G = OrcGrads(**{k: v.ctypes.data for k, v in g.items()})
+    rc = lib().orc_render_backward(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile),
+                                   np.ascontiguousarray(dl_dimage, np.float64), C.byref(G))
+    if rc != 0:
+        raise RuntimeError(f"orc_render_backward failed: {rc}")
+    return g
+
+
+def kind() -> str:
+    return "oracle"
+
+
+def default_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))

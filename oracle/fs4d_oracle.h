@@ -1,0 +1,117 @@
+/*
+ * FP64 CPU oracle for the 4D Gaussian Splatting render path (arXiv 2310.08528).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this code; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark load it.  It shares no header, helper or constant with the CUDA
+ * path.
+ *
+ * Every function computes in double precision from the float32 scene as stored.
+ * Where a floating-point value decides an integer (the depth key of a tile
+ * pair), the oracle takes that decision in float32, the kernels' precision.
+ *
+ * Which passage each function follows:
+ *   orc_plane_sample / orc_features  Sec. 4.2, Eq. 5 (bilinear interp, Hadamard
+ *                                    product over six planes, concat over levels)
+ *   orc_mlp / orc_deform             Sec. 4.2 (tiny MLP phi_d, heads phi_x phi_r
+ *                                    phi_s) and Eq. 6 (X'=X+dX, r'=r+dr, s'=s+ds)
+ *   orc_project                      Sec. 3.1, Eq. 2 (Sigma = R S S^T R^T) and
+ *                                    Eq. 3 (Sigma' = J W Sigma W^T J^T), SH colour
+ *   orc_bin_sort                     tile binning and (tile, depth) ordering of the
+ *                                    differentiable splatting the paper uses (Sec. 4.1)
+ *   orc_composite                    Eq. 1 (Gaussian weight) and Eq. 4
+ *                                    (front-to-back alpha blending)
+ *   orc_composite_bruteforce         the same blend as a per-pixel loop over all
+ *                                    Gaussians (no tiling), used as a pin
+ *   orc_*_backward                   chain rule of all of the above (training,
+ *                                    Sec. 4.3)
+ *
+ * Parity pins: see tests/test_oracle_*.py.  Agreement with the paper's trained
+ * results is parity unpinned (no trained weights or datasets exist here).
+ */
+#ifndef FS4D_ORACLE_H
+#define FS4D_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_scene {
+  int32_t n;
+  int32_t sh_degree;        /* 0..3 */
+  const float* means;       /* [n][3] */
+  const float* log_scales;  /* [n][3] */
+  const float* quats;       /* [n][4] w x y z */
+  const float* opacity_logits; /* [n] */
+  const float* sh;          /* [n][(deg+1)^2][3] */
+  double aabb_min[3];
+  double aabb_max[3];
+  int32_t n_levels;
+  int32_t res_spatial[4];
+  int32_t res_time;
+  int32_t feat_dim;
+  const float* planes;      /* per level, per plane xy xz yz xt yt zt: [R_b][R_a][h] */
+  int32_t mlp_width;
+  const float* mlp;         /* d1 d2 x1 x2 r1 r2 s1 s2: W[out][in] then b[out] */
+} orc_scene;
+
+typedef struct orc_camera {
+  int32_t width, height;
+  double fx, fy, cx, cy, znear;
+  double world_to_cam[16]; /* row-major, x right, y down, z forward */
+} orc_camera;
+
+/* Projected Gaussian set, all caller-owned arrays of length n (x k). */
+typedef struct orc_projected {
+  double* xy;       /* [n][2] pixel coordinates of the projected mean */
+  double* conic;    /* [n][3] inverse of the dilated 2-D covariance (a, b, c) */
+  double* cov2d;    /* [n][3] dilated 2-D covariance (a, b, c) */
+  double* opacity;  /* [n] sigmoid(logit) */
+  double* rgb;      /* [n][3] */
+  double* depth;    /* [n] camera-space z */
+  int32_t* radius;  /* [n] 0 = culled */
+  int32_t* rect;    /* [n][4] tile x0, y0, x1, y1 (x1, y1 exclusive) */
+  double* margin;   /* [n] pixels between a rect/radius decision and its boundary */
+} orc_projected;
+
+void orc_set_threads(int32_t n);
+
+void orc_plane_sample(const orc_scene* s, int32_t level, int32_t plane, double ua, double ub, double* out);
+void orc_features(const orc_scene* s, const double* xyz, int32_t n, double t, double* fh);
+void orc_mlp(const orc_scene* s, const double* fh, int32_t n, double* delta);
+void orc_deform(const orc_scene* s, double t, double* means, double* quats, double* log_scales);
+void orc_sh_basis(int32_t degree, const double* dir, double* basis);
+void orc_project(const orc_scene* s, const double* means, const double* quats, const double* log_scales,
+                 const orc_camera* cam, int32_t tile, orc_projected* out);
+int64_t orc_bin_sort(int32_t n, const uint32_t* depth_bits, const int32_t* rect, int32_t tiles_x,
+                     int32_t tiles_y, int64_t capacity, uint64_t* keys, uint32_t* values, uint32_t* ranges);
+void orc_composite(int32_t width, int32_t height, int32_t tile, const uint32_t* ranges, const uint32_t* values,
+                   const double* xy, const double* conic, const double* opacity, const double* rgb,
+                   const double* depth, double* image, double* t_final, int32_t* n_contrib, double* margin);
+void orc_composite_bruteforce(int32_t n, int32_t width, int32_t height, int32_t tile, const int32_t* radius,
+                              const int32_t* rect, const double* xy, const double* conic,
+                              const double* opacity, const double* rgb, const double* depth,
+                              double* image, double* t_final);
+int64_t orc_render(const orc_scene* s, const orc_camera* cam, double t, int32_t deform, int32_t tile,
+                   double* image, double* t_final, int32_t* n_contrib, double* margin);
+
+/* Backward (Sec. 4.3 training): gradients of sum(dl_dimage * image) with respect to
+ * every scene parameter.  grads arrays have the shapes of the scene arrays. */
+typedef struct orc_grads {
+  double* means;          /* [n][3] */
+  double* log_scales;     /* [n][3] */
+  double* quats;          /* [n][4] */
+  double* opacity_logits; /* [n] */
+  double* sh;             /* [n][k][3] */
+  double* planes;         /* flat, like the scene's planes */
+  double* mlp;            /* flat, like the scene's mlp */
+} orc_grads;
+
+int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,
+                            int32_t tile, const double* dl_dimage, orc_grads* grads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

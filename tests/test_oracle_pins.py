@@ -1,0 +1,417 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed form,
+an independent library routine (scipy), a special case that reduces to a
+simpler model, or a brute-force restatement.  None needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_08528_gb300 import scenegen as sg
+
+
+def one_gaussian_scene(mean=(0.0, 0.0, 0.0), log_scale=(-3.0, -3.0, -3.0), quat=(1.0, 0.0, 0.0, 0.0),
+                       logit=0.3, dc=(0.0, 0.0, 0.0), extra=()):
+    base = sg.make_tiny(0, n=1 + len(extra))
+    rows = [(mean, log_scale, quat, logit, dc)] + list(extra)
+    base.means = np.array([r[0] for r in rows], np.float32)
+    base.log_scales = np.array([r[1] for r in rows], np.float32)
+    base.quats = np.array([r[2] for r in rows], np.float32)
+    base.opacity_logits = np.array([r[3] for r in rows], np.float32)
+    base.sh = np.array([[r[4]] for r in rows], np.float32)
+    return base
+
+
+def centred_camera(w=128, h=128):
+    cam = sg.tiny_camera(w, h)
+    cam.cx, cam.cy = w / 2 + 0.5, h / 2 + 0.5  # the origin projects onto pixel centre (w/2, h/2)
+    return cam
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+# --------------------------------------------------------------------- Eq. 1 / Eq. 4 closed forms
+
+def test_single_gaussian_at_pixel_centre_closed_form():
+    """Eq. 1 at the mean is 1 and Eq. 4 has one term: pixel = colour * min(0.99, sigmoid(o))."""
+    for logit in (-1.0, 0.3, 6.0):  # the last one hits the 0.99 clamp
+        s = one_gaussian_scene(logit=logit)
+        img, T, nc, _, K = oracle.render(s, centred_camera(), 0.5, deform=False)
+        o = sigmoid(float(np.float32(logit)))
+        a = min(0.99, o)
+        assert img[64, 64] == pytest.approx([0.5 * a] * 3, abs=1e-15)
+        assert T[64, 64] == pytest.approx(1.0 - a, abs=1e-15)
+        assert nc[64, 64] == 1
+
+
+def test_single_gaussian_neighbour_closed_form():
+    """Neighbouring pixel: alpha = o * exp(-d^2 / (2 var)), var = (f s / z)^2 + 0.3 (Eq. 3 on the axis)."""
+    ls = -3.0
+    s = one_gaussian_scene(log_scale=(ls, ls, ls), logit=0.0)
+    cam = centred_camera()
+    img, *_ = oracle.render(s, cam, 0.5, deform=False)
+    var = (cam.fx * math.exp(float(np.float32(ls))) / 4.0) ** 2 + 0.3
+    for d in (1, 2, 3):
+        a = 0.5 * math.exp(-0.5 * d * d / var)
+        want = 0.5 * a if a >= 1 / 255 else 0.0
+        assert img[64, 64 + d, 0] == pytest.approx(want, rel=1e-12, abs=1e-15)
+        assert img[64 + d, 64, 0] == pytest.approx(want, rel=1e-12, abs=1e-15)
+
+
+def test_front_to_back_order_and_stop_rule():
+    """Eq. 4 read as prod_{j<i}(1 - a_j): two opaque Gaussians give 0.99 c1 + 0.01*0.99 c2;
+    a third would take T to 1e-6 < 1e-4 and is not blended."""
+    c1, c2, c3 = 0.3, -0.2, 0.4  # DC coefficients; colours 0.5 + Y0 * dc
+    y0 = 0.5 / math.sqrt(math.pi)
+    extra = [((0.0, 0.5, 0.0), (-3.0,) * 3, (1.0, 0, 0, 0), 9.0, (c2,) * 3),
+             ((0.0, 1.0, 0.0), (-3.0,) * 3, (1.0, 0, 0, 0), 9.0, (c3,) * 3)]
+    s = one_gaussian_scene(logit=9.0, dc=(c1,) * 3, extra=extra)
+    img, T, nc, _, _ = oracle.render(s, centred_camera(), 0.5, deform=False)
+    col1 = 0.5 + y0 * float(np.float32(c1))
+    col2 = 0.5 + y0 * float(np.float32(c2))
+    assert img[64, 64, 0] == pytest.approx(0.99 * col1 + 0.01 * 0.99 * col2, rel=1e-12)
+    assert T[64, 64] == pytest.approx(0.01 * 0.01, rel=1e-12)
+    assert nc[64, 64] == 2
+
+
+# --------------------------------------------------------------------- Eq. 2 / Eq. 3 closed forms
+
+def test_ewa_covariance_axis_aligned():
+    """On the optical axis J = diag(f/z): Sigma' = diag(f^2 s_x^2 / z^2, f^2 s_z^2 / z^2) + 0.3 I
+    (camera x = world x, camera y = -world z for the tiny camera)."""
+    ls = (-3.0, -2.5, -2.0)
+    s = one_gaussian_scene(log_scale=ls)
+    cam = centred_camera()
+    p = oracle.project(s, cam)
+    sx, sy, sz = [math.exp(float(np.float32(v))) for v in ls]
+    z = 4.0
+    assert p["cov2d"][0] == pytest.approx([cam.fx ** 2 * sx ** 2 / z ** 2 + 0.3, 0.0,
+                                           cam.fy ** 2 * sz ** 2 / z ** 2 + 0.3], rel=1e-12, abs=1e-12)
+    assert p["depth"][0] == pytest.approx(z)
+    assert p["xy"][0] == pytest.approx([64.5, 64.5])
+
+
+def test_ewa_covariance_rotated_against_scipy_rotation():
+    """Rotation about the world y axis (the viewing axis) mixes image x and y; the
+    expected covariance uses scipy's quaternion-to-matrix, not the oracle's."""
+    from scipy.spatial.transform import Rotation
+    ang = 0.7
+    q = (math.cos(ang / 2), 0.0, math.sin(ang / 2), 0.0)  # w x y z
+    ls = (-3.0, -2.6, -2.2)
+    s = one_gaussian_scene(log_scale=ls, quat=q)
+    cam = centred_camera()
+    p = oracle.project(s, cam)
+    qf = np.array(q, np.float32).astype(np.float64)
+    R = Rotation.from_quat([qf[1], qf[2], qf[3], qf[0]]).as_matrix()
+    S = np.diag(np.exp(np.array(ls, np.float32).astype(np.float64)))
+    sig = R @ S @ S @ R.T
+    W = np.asarray(cam.world_to_cam, np.float64)[:3, :3]
+    J = np.array([[cam.fx / 4.0, 0, 0], [0, cam.fy / 4.0, 0]])  # on-axis Jacobian
+    want = J @ W @ sig @ W.T @ J.T + 0.3 * np.eye(2)
+    assert p["cov2d"][0] == pytest.approx([want[0, 0], want[0, 1], want[1, 1]], rel=1e-10, abs=1e-12)
+    assert abs(want[0, 1]) > 1.0  # the off-diagonal term is really exercised
+    det = want[0, 0] * want[1, 1] - want[0, 1] ** 2
+    assert p["conic"][0] == pytest.approx([want[1, 1] / det, -want[0, 1] / det, want[0, 0] / det], rel=1e-10)
+    lam = np.linalg.eigvalsh(want).max()
+    assert p["radius"][0] == math.ceil(3 * math.sqrt(lam))
+
+
+def test_projection_of_offaxis_mean_and_rect():
+    s = one_gaussian_scene(mean=(0.4, 0.0, -0.2), log_scale=(-3.0,) * 3)
+    cam = sg.tiny_camera()
+    p = oracle.project(s, cam)
+    X = np.array([0.4, 0.0, -0.2], np.float32).astype(np.float64)
+    u = cam.fx * X[0] / 4.0 + cam.cx
+    v = cam.fy * (-X[2]) / 4.0 + cam.cy
+    assert p["xy"][0] == pytest.approx([u, v], rel=1e-12)
+    r = p["radius"][0]
+    assert p["rect"][0].tolist() == [math.floor((u - r) / 16), math.floor((v - r) / 16),
+                                     math.floor((u + r) / 16) + 1, math.floor((v + r) / 16) + 1]
+
+
+def test_cull_behind_near_plane():
+    s = one_gaussian_scene(mean=(0.0, -3.9, 0.0))  # 0.1 in front of the camera, znear = 0.2
+    p = oracle.project(s, sg.tiny_camera())
+    assert p["radius"][0] == 0 and p["rect"][0].tolist() == [0, 0, 0, 0]
+
+
+# --------------------------------------------------------------------- SH colour
+
+def test_sh_basis_against_scipy():
+    """Real SH basis (no Condon-Shortley phase) built from scipy's complex harmonics."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        want = []
+        for l in range(4):
+            for m in range(-l, l + 1):
+                Y = sph_harm_y(l, abs(m), theta, phi)
+                if m > 0:
+                    want.append(float(math.sqrt(2) * (-1) ** m * Y.real))
+                elif m < 0:
+                    want.append(float(math.sqrt(2) * (-1) ** m * Y.imag))
+                else:
+                    want.append(float(Y.real))
+        assert oracle.sh_basis(3, d) == pytest.approx(want, abs=1e-12)
+
+
+def test_sh_colour_is_view_dependent_and_clamped():
+    s = sg.make_object(0, n=64, res_spatial=(8,), res_time=4, h=8)
+    cam = sg.hemisphere_cameras(1, width=64, height=64)[0]
+    p = oracle.project(s, cam)
+    vis = p["radius"] > 0
+    assert vis.sum() > 10
+    assert (p["rgb"][vis] >= 0).all()
+    # colour = max(0, 0.5 + sum_k Y_k(dir) c_k), dir from the camera centre to the mean
+    W = np.asarray(cam.world_to_cam, np.float64)
+    campos = -W[:3, :3].T @ W[:3, 3]
+    g = int(np.flatnonzero(vis)[0])
+    d = s.means[g].astype(np.float64) - campos
+    d /= np.linalg.norm(d)
+    Y = oracle.sh_basis(3, d)
+    want = np.maximum(0.0, 0.5 + Y @ s.sh[g].astype(np.float64))
+    assert p["rgb"][g] == pytest.approx(want, rel=1e-12)
+
+
+# --------------------------------------------------------------------- Eq. 5 HexPlane
+
+def test_bilinear_matches_scipy_regular_grid():
+    """interp of Eq. 5 is corner-aligned bilinear; compare with scipy's RegularGridInterpolator."""
+    from scipy.interpolate import RegularGridInterpolator
+    s = sg.make_tiny(3)
+    shapes = sg.plane_shapes(s.res_spatial, s.res_time, s.feat_dim)
+    offs = np.cumsum([0] + [int(np.prod(sh)) for sh in shapes])
+    rng = np.random.default_rng(0)
+    for p in range(6):
+        rb, ra, h = shapes[p]
+        grid = s.planes[offs[p]:offs[p + 1]].reshape(rb, ra, h).astype(np.float64)
+        f = RegularGridInterpolator((np.linspace(-1, 1, rb), np.linspace(-1, 1, ra)), grid)
+        for _ in range(10):
+            ua, ub = rng.uniform(-1, 1, 2)
+            assert oracle.plane_sample(s, 0, p, ua, ub) == pytest.approx(f([ub, ua])[0], rel=1e-12, abs=1e-14)
+        # vertices return the stored value; outside the box clamps to the border
+        assert oracle.plane_sample(s, 0, p, -1.0, 1.0) == pytest.approx(grid[rb - 1, 0], abs=0)
+        assert oracle.plane_sample(s, 0, p, -3.0, 7.0) == pytest.approx(grid[rb - 1, 0], abs=0)
+        assert oracle.plane_sample(s, 0, p, 1.0, -1.0) == pytest.approx(grid[0, ra - 1], abs=0)
+
+
+def test_hadamard_of_constant_planes_is_v_to_the_sixth():
+    s = sg.make_object(0, n=50, res_spatial=(8, 16), res_time=5, h=8)
+    shapes = sg.plane_shapes(s.res_spatial, s.res_time, s.feat_dim)
+    rng = np.random.default_rng(2)
+    v = rng.uniform(0.5, 1.5, (2, 8)).astype(np.float32)  # per level, per channel
+    parts = []
+    for i, sh in enumerate(shapes):
+        parts.append(np.broadcast_to(v[i // 6], sh).ravel())
+    s.planes = np.concatenate(parts).astype(np.float32)
+    fh = oracle.features(s, s.means.astype(np.float64), 0.3)
+    want = np.concatenate([v[0].astype(np.float64) ** 6, v[1].astype(np.float64) ** 6])
+    assert np.allclose(fh, want[None, :], rtol=1e-13, atol=0)
+
+
+def test_features_concat_levels_and_time_axis():
+    """Each level's block of f_h depends on its own planes only, and only the
+    xt/yt/zt planes see the time coordinate."""
+    s = sg.make_object(0, n=30, res_spatial=(8, 16), res_time=5, h=4)
+    X = s.means.astype(np.float64)
+    a = oracle.features(s, X, 0.2)
+    shapes = sg.plane_shapes(s.res_spatial, s.res_time, s.feat_dim)
+    sizes = [int(np.prod(x)) for x in shapes]
+    s2 = s.copy()
+    lvl1 = sum(sizes[:6])
+    s2.planes[lvl1:] *= 2.0  # scale every plane of level 1 by 2 -> level-1 features x 2^6
+    b = oracle.features(s2, X, 0.2)
+    assert np.allclose(b[:, :4], a[:, :4], rtol=0, atol=0)
+    assert np.allclose(b[:, 4:], 64.0 * a[:, 4:], rtol=1e-13)
+    # make the time planes constant in t: features no longer depend on t
+    s3 = s.copy()
+    off = 0
+    for i, (rb, ra, h) in enumerate(shapes):
+        if i % 6 >= 3:
+            blk = s3.planes[off:off + rb * ra * h].reshape(rb, ra, h)
+            blk[:] = blk[:1]
+        off += rb * ra * h
+    assert np.allclose(oracle.features(s3, X, 0.1), oracle.features(s3, X, 0.9), rtol=1e-13)
+    assert not np.allclose(oracle.features(s, X, 0.1), oracle.features(s, X, 0.9))
+
+
+# --------------------------------------------------------------------- MLP heads (Sec. 4.2)
+
+def _layers(s):
+    hin = s.feat_dim * s.n_levels
+    out, off = [], 0
+    for o, i in sg.mlp_layer_shapes(hin, s.mlp_width):
+        out.append((off, o, i))
+        off += o * i + o
+    return out
+
+
+def test_mlp_hand_built_network():
+    """A network wired by hand: dX_1 = 6 * relu(f_h[5]), dr_0 = 2 relu(f_h[5]) + 0.25,
+    ds_2 = -relu(f_h[5]); every other output is its bias."""
+    s = sg.make_tiny(0)
+    L = _layers(s)
+    m = np.zeros_like(s.mlp)
+
+    def W(k, o, i, v):
+        off, O, I = L[k]
+        m[off + o * I + i] = v
+
+    def B(k, o, v):
+        off, O, I = L[k]
+        m[off + O * I + o] = v
+
+    W(0, 0, 5, 1.0); W(1, 0, 0, 1.0)
+    W(2, 0, 0, 2.0); W(3, 1, 0, 3.0)                    # x head
+    W(4, 3, 0, 1.0); W(5, 0, 3, 2.0); B(5, 0, 0.25)     # r head
+    W(6, 7, 0, 1.0); W(7, 2, 7, -1.0); B(7, 0, 0.5)     # s head
+    s.mlp = m
+    fh = np.random.default_rng(0).normal(size=(40, 16))
+    d = oracle.mlp(s, fh)
+    r = np.maximum(fh[:, 5], 0)
+    want = np.zeros((40, 10))
+    want[:, 1] = 6 * r
+    want[:, 3] = 2 * r + 0.25
+    want[:, 7] = 0.5
+    want[:, 9] = -r
+    assert np.array_equal(d, want)
+
+
+def test_mlp_against_torch_linear_layers():
+    torch = pytest.importorskip("torch")
+    s = sg.make_tiny(1, mlp_std=0.3, bias_std=0.1)
+    L = _layers(s)
+    lins = []
+    for off, o, i in L:
+        lin = torch.nn.Linear(i, o).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(s.mlp[off:off + o * i].reshape(o, i).astype(np.float64)))
+            lin.bias.copy_(torch.from_numpy(s.mlp[off + o * i:off + o * i + o].astype(np.float64)))
+        lins.append(lin)
+    fh = np.random.default_rng(1).normal(size=(25, 16))
+    x = torch.from_numpy(fh)
+    relu = torch.relu
+    fd = relu(lins[1](relu(lins[0](x))))
+    outs = [lins[3 + 2 * h](relu(lins[2 + 2 * h](fd))) for h in range(3)]
+    want = torch.cat(outs, 1).detach().numpy()
+    assert oracle.mlp(s, fh) == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+def test_deform_is_eq6_addition():
+    s = sg.make_tiny(2, mlp_std=0.3)
+    X, Q, S = oracle.deform(s, 0.7)
+    d = oracle.mlp(s, oracle.features(s, s.means.astype(np.float64), 0.7))
+    assert np.allclose(X - s.means, d[:, :3], rtol=0, atol=1e-15)
+    assert np.allclose(Q - s.quats, d[:, 3:7], rtol=0, atol=1e-15)
+    assert np.allclose(S - s.log_scales, d[:, 7:], rtol=0, atol=1e-15)
+    assert np.abs(d).max() > 1e-3
+
+
+# --------------------------------------------------------------------- special case (b)
+
+def test_zero_heads_reduce_to_static_3dgs():
+    """Zeroing the head output layers gives dG = 0, so the 4D render equals the
+    static render of the canonical Gaussians (the warm-up mode of Sec. 4.3)."""
+    s = sg.make_tiny(4, mlp_std=0.3)
+    L = _layers(s)
+    for k in (3, 5, 7):
+        off, o, i = L[k]
+        s.mlp[off:off + o * i + o] = 0.0
+    X, Q, S = oracle.deform(s, 0.3)
+    assert np.array_equal(X, s.means.astype(np.float64))
+    assert np.array_equal(Q, s.quats.astype(np.float64))
+    cam = sg.tiny_camera()
+    a = oracle.render(s, cam, 0.3, deform=True)
+    b = oracle.render(s, cam, 0.3, deform=False)
+    assert np.array_equal(a[0], b[0]) and a[4] == b[4]
+
+
+def test_zero_planes_reduce_to_static_3dgs():
+    s = sg.make_tiny(5, mlp_std=0.3)
+    s.planes[:] = 0.0
+    cam = sg.tiny_camera()
+    a = oracle.render(s, cam, 0.8, deform=True)
+    b = oracle.render(s, cam, 0.8, deform=False)
+    assert np.array_equal(a[0], b[0])
+
+
+# --------------------------------------------------------------------- tiling, sort, ranges (c)
+
+def test_tiled_equals_bruteforce_per_pixel():
+    for seed in range(3):
+        s = sg.make_tiny(seed)
+        cam = sg.tiny_camera()
+        X, Q, S = oracle.deform(s, 0.5)
+        p = oracle.project(s, cam, X, Q, S)
+        keys, vals, ranges = oracle.bin_sort(oracle.depth_bits(p["depth"]), p["rect"], 8, 8)
+        img, T, nc, _ = oracle.composite(128, 128, ranges, vals, p)
+        img_bf, T_bf = oracle.composite_bruteforce(128, 128, p)
+        assert np.array_equal(img, img_bf) and np.array_equal(T, T_bf)
+        img_r, *_ = oracle.render(s, cam, 0.5)
+        assert np.array_equal(img, img_r)
+
+
+def test_bin_sort_against_numpy_lexsort():
+    rng = np.random.default_rng(7)
+    n, tx, ty = 3000, 13, 9
+    depth = rng.uniform(0.5, 9.0, n).astype(np.float32)
+    depth[::17] = depth[5]  # ties: broken by Gaussian index
+    x0 = rng.integers(0, tx, n); y0 = rng.integers(0, ty, n)
+    rect = np.stack([x0, y0, np.minimum(tx, x0 + rng.integers(0, 4, n)),
+                     np.minimum(ty, y0 + rng.integers(0, 4, n))], 1).astype(np.int32)
+    bits = depth.view(np.uint32)
+    keys, vals, ranges = oracle.bin_sort(bits, rect, tx, ty)
+    tiles, gids = [], []
+    for g in range(n):
+        for yy in range(rect[g, 1], rect[g, 3]):
+            for xx in range(rect[g, 0], rect[g, 2]):
+                tiles.append(yy * tx + xx); gids.append(g)
+    tiles, gids = np.array(tiles, np.int64), np.array(gids, np.int64)
+    order = np.lexsort((gids, depth[gids], tiles))
+    assert np.array_equal(vals, gids[order].astype(np.uint32))
+    assert np.array_equal(keys, ((tiles[order].astype(np.uint64) << np.uint64(32)) | bits[gids[order]]))
+    counts = np.bincount(tiles, minlength=tx * ty)
+    assert (ranges[:, 1] - ranges[:, 0]).sum() == len(tiles)
+    nz = counts > 0
+    assert np.array_equal((ranges[:, 1] - ranges[:, 0])[nz], counts[nz])
+    assert np.array_equal(ranges[nz, 0], np.cumsum(counts)[nz] - counts[nz])
+
+
+# --------------------------------------------------------------------- transmittance (d)
+
+def test_transmittance_invariants():
+    s = sg.make_tiny(6)
+    cam = sg.tiny_camera()
+    X, Q, S = oracle.deform(s, 0.5)
+    p = oracle.project(s, cam, X, Q, S)
+    _, vals, ranges = oracle.bin_sort(oracle.depth_bits(p["depth"]), p["rect"], 8, 8)
+    img, T, nc, _ = oracle.composite(128, 128, ranges, vals, p)
+    assert (T >= 1e-4).all() and (T <= 1.0).all()
+    lens = (ranges[:, 1] - ranges[:, 0]).reshape(8, 8)
+    assert (nc <= np.kron(lens, np.ones((16, 16), np.int64))).all()
+    assert (img >= 0).all() and (img <= p["rgb"].max() + 1e-12).all()
+    # T over prefixes of each tile's list is non-increasing
+    prev = np.ones((128, 128))
+    for k in range(0, int(lens.max()) + 1, 7):
+        r2 = ranges.copy()
+        r2[:, 1] = np.minimum(r2[:, 1], r2[:, 0] + k)
+        _, Tk, _, _ = oracle.composite(128, 128, r2, vals, p)
+        assert (Tk <= prev + 1e-15).all()
+        prev = Tk
+    assert np.array_equal(prev, T) or k < lens.max()
+
+
+def test_image_is_convex_combination_bound():
+    """sum_i a_i prod_{j<i}(1-a_j) = 1 - T_final, so each channel <= (1 - T) * max colour."""
+    s = sg.make_tiny(8)
+    img, T, *_ = oracle.render(s, sg.tiny_camera(), 0.5)
+    p = oracle.project(s, sg.tiny_camera(), *oracle.deform(s, 0.5))
+    assert (img <= (1.0 - T)[..., None] * p["rgb"].max(0)[None, None, :] + 1e-12).all()
