@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Frame-rate benchmark of the 4D-GS per-frame render path on GB300.
+
+Workload (one step = one frame = one pass of the whole path): the D-NeRF-shaped
+synthetic object -- N=100k Gaussians from a 32-component mixture in the unit
+sphere, SH degree 3, HexPlane spatial {64,128} x temporal 25 x 32 features, MLP
+width 64 -- rendered at 800x800 from 50 hemisphere cameras x 20 timestamps in
+[0,1] (view i = camera i % 50, timestamp (i // 50) % 20).  The scene stays
+resident in HBM; each timed frame uploads its camera and t, then replays one
+captured CUDA graph of deform -> project -> scan/emit -> radix sort -> ranges ->
+composite.  L2 is flushed (a 256 MB device write) before every timed frame, and
+the flush is outside the timed interval.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead.  Under torchrun (N>1) every rank renders its own views
+(independent replicas, weak scaling); the timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FPS at 800×800/100k Gaussians (BF16 vs FP32 MLP); serving p50/p99 ms"
+WIDTH = HEIGHT = 800
+N_CAMS, N_TIMES = 50, 20
+WORKLOAD = ("D-NeRF-shaped synthetic object: N=100k Gaussians (32-component mixture in the unit sphere), "
+            "SH degree 3, HexPlane spatial {64,128} x temporal 25 x 32 features, MLP width 64, "
+            "800x800, 50 hemisphere cameras (radius 4, 50 deg FOV) x 20 timestamps in [0,1]")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=60)
+    return ap.parse_args()
+
+
+def views(step: int, rank: int, world: int):
+    from paper_2310_08528_gb300 import scenegen as sg
+    cams = sg.hemisphere_cameras(N_CAMS, width=WIDTH, height=HEIGHT, seed=0)
+    ts = np.linspace(0.0, 1.0, N_TIMES)
+    i = step * world + rank
+    return cams[i % N_CAMS], float(ts[(i // N_CAMS) % N_TIMES])
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- roofline
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str):
+    """Algorithmic bytes or FLOPs of one launch of each stage (per-unit figures
+    times the units one launch processes)."""
+    if stage == "deform":
+        flops = 2 * (64 * 64 + 64 * 64 + 3 * 64 * 64 + 64 * 10) * n   # MLP contraction, 42,240 FLOP/Gaussian
+        return ("tensor" if prec == "bf16" else "alu"), flops, "FLOP"
+    if stage == "project":
+        return "hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16), "B"
+    if stage == "scan_emit":
+        return "hbm", n * (16 + 4 + 4) + K * 12, "B"
+    if stage == "sort":
+        return "hbm", passes * K * 24, "B"                             # read + write 12 B per pair per pass
+    if stage == "ranges":
+        return "hbm", K * 8 + 0, "B"
+    if stage == "composite":
+        return "hbm", K * 40 + pixels * 12, "B"                        # gather idx + 36 B, write rgb
+    raise KeyError(stage)
+
+
+def roofline(stage_ms, n, K, pixels, passes, prec, peaks, clocks_mhz):
+    out = {}
+    for st, ms in stage_ms.items():
+        bound, work, unit = stage_work(st, n, K, pixels, passes, prec)
+        sec = ms * 1e-3
+        if bound == "hbm":
+            ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
+        elif bound == "tensor":
+            ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
+        else:  # float32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+            ach, peak, u = work / sec / 1e12, 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s"
+        out[st] = {"bound": bound, "achieved": ach, "peak": peak, "unit": u, "frac": ach / peak, "ms": ms}
+    return out
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(budget_s: float = 12.0, max_frames: int = 40):
+    import oracle
+    from paper_2310_08528_gb300 import scenegen as sg
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    scene = sg.make_object(0)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_frames:
+        cam, t = views(n, 0, 1)
+        oracle.render(scene, cam, t)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} full 800x800 frames of the 100k-Gaussian object (FP64 C++ oracle, OpenMP over "
+                      f"{threads} host threads), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2310_08528_gb300 import scenegen as sg
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    scene = sg.make_object(0)
+    for i in range(min(args.warmup, 1)):
+        cam, t = views(i, 0, 1)
+        oracle.render(scene, cam, t)
+    budget = 150.0
+    n, t0 = 0, time.perf_counter()
+    while n < args.steps:
+        cam, t = views(n, 0, 1)
+        oracle.render(scene, cam, t)
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    fps = n / dt
+    sample = (f"{n} of {args.steps} requested frames (full 800x800 frames; capped at {budget:.0f} s), "
+              f"FP64 C++ oracle on {threads} host threads")
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": n, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def measure(ctx, fs4d, torch, sid, prec, steps, warmup, rank, world, stream, cap):
+    """Graph-captured frames; returns (per-frame ms list, mean stage ms, K max)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shape_cam, _ = views(0, rank, world)
+    d_cam = torch.empty(23, dtype=torch.float32, device=dev)
+    d_t = torch.empty(1, dtype=torch.float32, device=dev)
+    image = torch.empty((HEIGHT, WIDTH, 3), device=dev)
+    n_views = N_CAMS * N_TIMES
+    host_cams = torch.empty((n_views, 23), dtype=torch.float32).pin_memory()
+    host_ts = torch.empty((n_views, 1), dtype=torch.float32).pin_memory()
+    for i in range(n_views):
+        cam, t = views(i, 0, 1)
+        host_cams[i] = torch.from_numpy(np.frombuffer(bytes(fs4d.camera_struct(cam)), dtype=np.float32).copy())
+        host_ts[i, 0] = t
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
+    ctx.set_stage_timing(True)
+    with torch.cuda.stream(stream):
+        ctx.render_async(sid, shape_cam, d_cam, d_t, image, prec)  # warm the kernels outside the capture
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            ctx.render_async(sid, shape_cam, d_cam, d_t, image, prec)
+    frame_ms, stages = [], []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(warmup + steps):
+            v = (i * world + rank) % n_views
+            flush.fill_(i)
+            j = i - warmup
+            if j >= 0:
+                starts[j].record(stream)
+            d_cam.copy_(host_cams[v], non_blocking=True)
+            d_t.copy_(host_ts[v], non_blocking=True)
+            graph.replay()
+            if j >= 0:
+                ends[j].record(stream)
+                st = ctx.stage_times()  # waits for this frame
+                stages.append(st)
+    stream.synchronize()
+    ctx.check_device_status()  # no capacity overflow and no timed-out wait in any frame
+    frame_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    mean_st = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
+    ctx.set_stage_timing(False)
+    return frame_ms, mean_st
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2310_08528_gb300 import fs4d, scenegen as sg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    scene = sg.make_object(0)
+    stream = torch.cuda.Stream()
+    ctx = fs4d.Context(local, stream)
+    sid = ctx.load_scene(scene)
+    # size the tile-pair buffers from the largest frame of the view set
+    kmax = 0
+    with torch.cuda.stream(stream):
+        for c in range(N_CAMS):
+            cam, t = views(c, 0, 1)
+            ctx.render(sid, cam, t)
+            kmax = max(kmax, ctx.last_pairs())
+    stream.synchronize()
+    cap = int(kmax * 1.25) + 4096
+    ctx.reserve(sid, WIDTH, HEIGHT, cap)
+    tiles = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
+    passes = (32 + int(np.ceil(np.log2(tiles))) + 7) // 8
+    launches_per_frame = 5 + passes  # deform, project, scan/emit, sort passes, ranges, composite
+
+    bf16_ok = True
+    try:
+        with torch.cuda.stream(stream):
+            ctx.render(sid, views(0, 0, 1)[0], 0.5, fs4d.BF16)
+        stream.synchronize()
+    except fs4d.Fs4dError:
+        bf16_ok = False
+    precs = ["fp32"] + (["bf16"] if bf16_ok else [])
+    head = args.prec if args.prec != "auto" else ("bf16" if bf16_ok else "fp32")
+    if head == "bf16" and not bf16_ok:
+        raise SystemExit("bf16 requested but the BF16 path is not available for this scene")
+
+    results = {}
+    clocks = None
+    for p in precs:
+        pc = fs4d.BF16 if p == "bf16" else fs4d.FP32
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if p == head:
+            with ClockSampler(local) as cs:
+                frame_ms, st = measure(ctx, fs4d, torch, sid, pc, args.steps, args.warmup, rank, world, stream, cap)
+            clocks = cs.summary()
+        else:
+            frame_ms, st = measure(ctx, fs4d, torch, sid, pc, args.steps, args.warmup, rank, world, stream, cap)
+        torch.cuda.synchronize()
+        total = float(np.sum(frame_ms))
+        if dist:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+            dist.barrier()
+        results[p] = {"fps": world * args.steps / (total * 1e-3), "ms_per_step": total / args.steps,
+                      "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
+                      "stages_ms": st}
+
+    # end-to-end through the host-buffer C call (camera in, image out, copies inside the timed region)
+    e2e_steps = min(args.e2e_steps, args.steps)
+    pc = fs4d.BF16 if head == "bf16" else fs4d.FP32
+    host_img = torch.empty((HEIGHT, WIDTH, 3), dtype=torch.float32).pin_memory().numpy()
+    with torch.cuda.stream(stream):
+        for i in range(3):
+            cam, t = views(i, rank, world)
+            ctx.render_host(sid, cam, t, pc, host_img)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            cam, t = views(i, rank, world)
+            ctx.render_host(sid, cam, t, pc, host_img)
+        e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = load_peaks()
+    K = ctx.last_pairs()
+    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks,
+                  clocks["sm_mhz"] if clocks else None)
+    dom = max(rf, key=lambda k: rf[k]["ms"])
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        tr = json.load(open(tf)).get(head, {}).get(dom)
+        if tr:
+            traffic = tr.get("bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": results[head]["fps"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "resolution": [WIDTH, HEIGHT],
+                   "tile_pairs_last_frame": K, "pair_capacity": cap, "parallelism": f"replicas x{world}",
+                   "l2": "flushed before every timed frame (256 MB device write, outside the timed interval)",
+                   "timing": "CUDA events around camera upload + CUDA-graph replay of one frame"},
+        "roofline": {"kernel": dom, "bound": rf[dom]["bound"], "achieved": rf[dom]["achieved"], "peak": rf[dom]["peak"],
+                     "unit": rf[dom]["unit"], "frac": rf[dom]["frac"], "traffic": traffic,
+                     "peak_source": peaks["source"]},
+        "stages": rf,
+        "precisions": results,
+        "e2e": {"value": e2e_steps * world / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 96,
+                "d2h_bytes_per_step": WIDTH * HEIGHT * 12 + 8,
+                "call": "fs4d_render_host (host camera in, host image out, one stream sync for the pair count)"},
+        "gpu_launches": launches_per_frame * (args.steps * len(precs)),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

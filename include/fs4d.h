@@ -1,0 +1,238 @@
+/*
+ * fs4d.h -- C ABI of the GB300 (sm_103a) render path of 4D Gaussian Splatting
+ * (Wu et al., "4D Gaussian Splatting for Real-Time Dynamic Scene Rendering",
+ * arXiv 2310.08528).
+ *
+ * The path renders, for a view matrix M = [R, T] and a timestamp t, the image
+ * I = S(M, G') with G' = G + F(G, t)  (Sec. 4.1):
+ *   F : HexPlane deformation field -- six planes xy xz yz xt yt zt per level,
+ *       bilinear interpolation, Hadamard product over planes, concatenation over
+ *       levels (Sec. 4.2, Eq. 5), tiny MLP phi_d and heads phi_x, phi_r, phi_s
+ *       (Sec. 4.2), update X' = X + dX, r' = r + dr, s' = s + ds (Eq. 6).
+ *   S : differentiable splatting -- EWA projection Sigma' = J W Sigma W^T J^T
+ *       (Eq. 2, Eq. 3), tile binning with (tile, depth) keys, radix sort, per-tile
+ *       front-to-back alpha compositing (Eq. 1, Eq. 4).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an fs4d_status; no C++ exception crosses the ABI.  On an
+ *    error, fs4d_last_error(ctx) returns a message (valid until the next call on
+ *    that context from the same thread).
+ *  - Pointers named d_* are DEVICE pointers on the context's device, owned by the
+ *    caller, and must stay valid until the work is complete.  Pointers named h_*
+ *    (and the desc/camera structs) are HOST pointers, read during the call only.
+ *  - Work is queued asynchronously on the context's stream; outputs are valid
+ *    once that stream has been synchronised, unless a call says otherwise.
+ *  - Float arrays are float32, C-contiguous, in the layouts stated per field.
+ *  - Readings of the paper that the paper leaves open (corner-aligned bilinear
+ *    interpolation with border clamping; biases in every linear layer; sigmoid
+ *    opacity; log-space scales; 0.3 low-pass dilation; alpha clamped to 0.99,
+ *    terms below 1/255 skipped, stop before the term that takes transmittance
+ *    below 1e-4; pixel centres at +0.5; SH colour + 0.5 clamped at 0) are the
+ *    library's conventions; the CPU oracle in this repository states each one.
+ */
+#ifndef FS4D_H
+#define FS4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FS4D_API __attribute__((visibility("default")))
+#else
+#define FS4D_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fs4d_status {
+  FS4D_OK = 0,
+  FS4D_ERR_INVALID_ARG = 1,   /* a pointer, size or enum outside what the call accepts */
+  FS4D_ERR_OOM = 2,           /* device memory could not be allocated */
+  FS4D_ERR_CAPACITY = 3,      /* a fixed-capacity buffer (tile pairs) overflowed */
+  FS4D_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
+  FS4D_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (status word set) */
+  FS4D_ERR_NOT_FOUND = 6,     /* unknown scene id or frame */
+  FS4D_ERR_UNIMPLEMENTED = 7  /* a shape this build does not support (message says which) */
+} fs4d_status;
+
+typedef enum fs4d_precision {
+  FS4D_FP32 = 0, /* planes and MLP in float32, SIMT FMA */
+  FS4D_BF16 = 1  /* planes and MLP operands in bfloat16 on tcgen05 tensor cores, float32 accumulate */
+} fs4d_precision;
+
+typedef struct fs4d_ctx fs4d_ctx;     /* one device + one stream; not thread-safe */
+typedef struct fs4d_frame fs4d_frame; /* saved forward state of one render, for the backward */
+typedef int32_t fs4d_scene_id;
+
+/* Canonical scene (Sec. 3.1: X, s, r, opacity, SH; Sec. 4.2: HexPlane and MLP).
+ * All pointers are HOST pointers; fs4d_load_scene copies them to the device. */
+typedef struct fs4d_scene_desc {
+  int32_t n;                   /* number of Gaussians, >= 1 */
+  int32_t sh_degree;           /* 0..3; K = (sh_degree+1)^2 coefficients per channel */
+  const float* means;          /* [n][3] canonical centres X */
+  const float* log_scales;     /* [n][3] s; scale = exp(s) */
+  const float* quats;          /* [n][4] r as (w, x, y, z); normalised only inside projection */
+  const float* opacity_logits; /* [n]; opacity = sigmoid(logit) */
+  const float* sh;             /* [n][K][3] real-SH coefficients (degree-major, m = -l..l) */
+  float aabb_min[3];           /* box mapped onto the HexPlane grid [-1,1]^3 */
+  float aabb_max[3];
+  int32_t n_levels;            /* 1..4 multi-resolution levels */
+  int32_t res_spatial[4];      /* spatial grid resolution per level (>= 2) */
+  int32_t res_time;            /* temporal grid resolution (>= 2), the same at every level */
+  int32_t feat_dim;            /* h, features per plane: 16 or 32 */
+  const float* planes;         /* per level, per plane (xy,xz,yz,xt,yt,zt): [R_b][R_a][h],
+                                  R_a/R_b the resolutions of the plane's first/second axis */
+  int32_t mlp_width;           /* hidden width W; this build supports 64 */
+  const float* mlp;            /* layers d1 (W x h*L), d2 (W x W), x1, x2 (3 x W), r1, r2 (4 x W),
+                                  s1, s2 (3 x W); each weight [out][in] then bias [out] */
+} fs4d_scene_desc;
+
+/* Pinhole camera.  world_to_cam maps world to camera coordinates (x right,
+ * y down, z forward); pixel (i, j) is evaluated at (i + 0.5, j + 0.5). */
+typedef struct fs4d_camera {
+  int32_t width, height;       /* pixels, 1..8192 */
+  float fx, fy, cx, cy;        /* focal lengths and principal point, pixels */
+  float znear;                 /* Gaussians with camera z <= znear are culled */
+  float world_to_cam[16];      /* row-major 4x4 */
+} fs4d_camera;
+
+/* Per-Gaussian output of the projection stage (device, caller-owned). */
+typedef struct fs4d_projected {
+  float* xy;            /* [n][2] projected mean, pixels */
+  float* conic_opacity; /* [n][4] inverse dilated 2-D covariance (a, b, c) and opacity */
+  float* rgb;           /* [n][3] view-dependent colour */
+  float* depth;         /* [n] camera-space z (its float32 bits form the low key word) */
+  int32_t* radius;      /* [n] 3-sigma radius in pixels; 0 = culled */
+  int32_t* rect;        /* [n][4] touched tiles x0, y0, x1, y1 (x1, y1 exclusive) */
+} fs4d_projected;
+
+/* Gradients of a scalar loss with respect to the scene (device, caller-owned,
+ * the layouts of fs4d_scene_desc).  Any pointer may be NULL to skip it. */
+typedef struct fs4d_grads {
+  float* means;          /* [n][3] */
+  float* log_scales;     /* [n][3] */
+  float* quats;          /* [n][4] */
+  float* opacity_logits; /* [n] */
+  float* sh;             /* [n][K][3] */
+  float* planes;         /* flat, like desc.planes */
+  float* mlp;            /* flat, like desc.mlp */
+} fs4d_grads;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device` that queues work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  *out receives the handle. */
+FS4D_API fs4d_status fs4d_create(int32_t device, void* cuda_stream, fs4d_ctx** out);
+/* Free every scene, frame and work buffer of the context, after synchronising its stream. */
+FS4D_API fs4d_status fs4d_destroy(fs4d_ctx* ctx);
+/* Message of the last error on this context (never NULL). */
+FS4D_API const char* fs4d_last_error(const fs4d_ctx* ctx);
+/* Replace the stream the context queues work on. */
+FS4D_API fs4d_status fs4d_set_stream(fs4d_ctx* ctx, void* cuda_stream);
+/* Read and clear the device status word (bounded waits that timed out, pair
+ * capacity overflow in capacity mode).  Synchronises the context's stream.
+ * Returns FS4D_OK, FS4D_ERR_TIMEOUT or FS4D_ERR_CAPACITY. */
+FS4D_API fs4d_status fs4d_check_device_status(fs4d_ctx* ctx);
+
+/* ---------------------------------------------------------------- scenes */
+
+/* Copy a canonical scene to the device and prepare both precisions (float32
+ * planes/MLP and the bfloat16 tensor-core operand layouts).  Synchronous. */
+FS4D_API fs4d_status fs4d_load_scene(fs4d_ctx* ctx, const fs4d_scene_desc* desc, fs4d_scene_id* out);
+FS4D_API fs4d_status fs4d_unload_scene(fs4d_ctx* ctx, fs4d_scene_id id);
+/* Bytes the scene holds resident on the device, and the per-frame work memory a
+ * render at (width, height) needs with `pairs_per_gaussian` tile pairs per
+ * Gaussian (used for admission by device-memory footprint). */
+FS4D_API fs4d_status fs4d_scene_bytes(fs4d_ctx* ctx, fs4d_scene_id id, int32_t width, int32_t height,
+                             float pairs_per_gaussian, size_t* resident, size_t* per_frame);
+
+/* ---------------------------------------------------------------- the path */
+
+/* Eq. 5 + Sec. 4.2 + Eq. 6: deform the scene at each of n_t timestamps in ONE
+ * launch.  h_ts: host [n_t] in [0,1].  Outputs (device, caller-owned):
+ * d_means [n_t][n][3], d_quats [n_t][n][4], d_log_scales [n_t][n][3]. */
+FS4D_API fs4d_status fs4d_deform(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const float* h_ts, int32_t n_t,
+                        float* d_means, float* d_quats, float* d_log_scales);
+
+/* Render one frame: deform at t, project, bin, sort, composite.  d_image:
+ * device [height][width][3]; d_t_final [height][width] and d_n_contrib
+ * [height][width] may be NULL.  If `saved` is non-NULL, *saved receives the
+ * forward state needed by fs4d_render_backward (free it with fs4d_frame_free).
+ * The number of tile pairs is read back once per call (one stream sync). */
+FS4D_API fs4d_status fs4d_render(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
+                        float* d_image, float* d_t_final, int32_t* d_n_contrib, fs4d_frame** saved);
+
+/* The same frame end to end with HOST buffers: the camera and t go host->device,
+ * the image comes back into h_image [height][width][3] (pinned memory is fastest).
+ * Returns after the image is on the host. */
+FS4D_API fs4d_status fs4d_render_host(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam,
+                             float t, float* h_image);
+
+/* Capacity mode: render without any host synchronisation (so the call can be
+ * captured into a CUDA graph).  The tile-pair buffers hold `pair_capacity` pairs;
+ * a frame that needs more sets the device status word (fs4d_check_device_status
+ * then returns FS4D_ERR_CAPACITY) and its image is incomplete.  The camera and t
+ * are read from DEVICE memory (d_cam: one fs4d_camera, d_t: one float) so that a
+ * captured graph can be replayed for new views. */
+FS4D_API fs4d_status fs4d_reserve(fs4d_ctx* ctx, fs4d_scene_id id, int32_t width, int32_t height, int64_t pair_capacity);
+FS4D_API fs4d_status fs4d_render_async(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* h_cam_shape,
+                              const fs4d_camera* d_cam, const float* d_t, float* d_image);
+
+/* Backward of one saved frame (training, Sec. 4.3): gradients of
+ * sum(d_dl_dimage * image) with respect to every scene parameter.
+ * d_dl_dimage: device [height][width][3].  Gradients are ACCUMULATED (+=) into the
+ * non-NULL pointers of *d_grads. */
+FS4D_API fs4d_status fs4d_render_backward(fs4d_ctx* ctx, fs4d_frame* saved, const float* d_dl_dimage,
+                                 const fs4d_grads* d_grads);
+FS4D_API fs4d_status fs4d_frame_free(fs4d_ctx* ctx, fs4d_frame* frame);
+/* Number of tile pairs K of a saved frame, and of the last render on the context. */
+FS4D_API fs4d_status fs4d_frame_pairs(const fs4d_frame* frame, int64_t* pairs);
+FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
+
+/* Per-stage device timing of frames rendered by fs4d_render / fs4d_render_async
+ * (also inside a captured CUDA graph): when enabled, CUDA events are recorded on
+ * the context's stream around each stage.  fs4d_stage_times waits for the last
+ * recorded frame and writes ms[6] = deform, project, scan+emit, radix sort,
+ * tile ranges, composite (milliseconds, that frame only). */
+FS4D_API fs4d_status fs4d_set_stage_timing(fs4d_ctx* ctx, int32_t enable);
+FS4D_API fs4d_status fs4d_stage_times(fs4d_ctx* ctx, float* h_ms);
+
+/* ---------------------------------------------------------------- stages
+ * Stateless stages of the path on caller-owned device buffers, so that each can
+ * be checked on its own.  The context supplies the stream and work memory. */
+
+/* Eq. 2 + Eq. 3 + SH colour for n Gaussians (d_sh: [n][K][3]); tile = 16. */
+FS4D_API fs4d_status fs4d_project(fs4d_ctx* ctx, int32_t n, const float* d_means, const float* d_quats,
+                         const float* d_log_scales, const float* d_opacity_logits, const float* d_sh,
+                         int32_t sh_degree, const fs4d_camera* cam, const fs4d_projected* out);
+
+/* Tile binning + radix sort + tile ranges.  Inputs: d_depth [n] (float32 whose
+ * bits are the low key word) and d_rect [n][4].  Emits one key
+ * (tile_id << 32 | depth bits) per (Gaussian, touched tile), tile_id = y*tiles_x + x,
+ * sorts the pairs by key (ties keep Gaussian-index order) and writes
+ * d_keys/d_values [capacity], d_ranges [tiles_y*tiles_x][2] ([start, end) per tile)
+ * and *h_num_pairs = K (the call synchronises once to read it).  Returns
+ * FS4D_ERR_CAPACITY (and writes nothing past capacity) if K > capacity. */
+FS4D_API fs4d_status fs4d_bin_sort(fs4d_ctx* ctx, int32_t n, const float* d_depth, const int32_t* d_rect, int32_t tiles_x,
+                          int32_t tiles_y, int64_t capacity, uint64_t* d_keys, uint32_t* d_values,
+                          uint32_t* d_ranges, int64_t* h_num_pairs);
+
+/* Stable LSD radix sort of (key, value) pairs on the low `key_bits` bits of the
+ * keys (1..64), in place: d_keys/d_values [n] hold the sorted pairs on return.
+ * Uses context-owned work memory. */
+FS4D_API fs4d_status fs4d_sort_pairs(fs4d_ctx* ctx, int64_t n, int32_t key_bits, uint64_t* d_keys, uint32_t* d_values);
+
+/* Eq. 4 per 16x16 tile over the sorted lists: d_ranges [tiles][2], d_values [K]
+ * Gaussian indices, per-Gaussian d_xy [n][2], d_conic_opacity [n][4], d_rgb [n][3].
+ * Writes d_image [height][width][3] and, when non-NULL, d_t_final and
+ * d_n_contrib [height][width]. */
+FS4D_API fs4d_status fs4d_composite(fs4d_ctx* ctx, int32_t width, int32_t height, const uint32_t* d_ranges,
+                           const uint32_t* d_values, const float* d_xy, const float* d_conic_opacity,
+                           const float* d_rgb, float* d_image, float* d_t_final, int32_t* d_n_contrib);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FS4D_H */

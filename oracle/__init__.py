@@ -156,6 +156,9 @@ def deform(scene, t: float):
     return X, Q, S
 
 
+_deform_fn = deform
+
+
 def sh_basis(degree: int, direction) -> np.ndarray:
     out = np.zeros(16, np.float64)
     lib().orc_sh_basis(int(degree), np.ascontiguousarray(direction, np.float64), out)
@@ -227,6 +230,50 @@ def render(scene, cam, t: float, deform: bool = True, tile: int = 16):
     img = np.zeros((H, W, 3)); T = np.zeros((H, W)); nc = np.zeros((H, W), np.int32); mg = np.zeros((H, W))
     K = lib().orc_render(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile), img, T, nc, mg)
     return img, T, nc, mg, int(K)
+
+
+def unstable_pixels(scene, cam, t: float, deform: bool = True, px_tol: float = 1e-3, margin_tol: float = 1e-5,
+                    tile: int = 16):
+    """Pixels whose value a float32 implementation may legitimately decide
+    differently from this float64 oracle: (a) a blend decision (alpha vs 1/255,
+    T vs 1e-4, a depth tie) within margin_tol of its threshold, or (b) a tile whose
+    membership in some Gaussian's tile rectangle changes when that Gaussian's
+    projected centre moves by up to px_tol pixels or its 3-sigma radius crosses
+    the nearest integer.  Returns (mask [H][W] bool, image, T, n_contrib, K)."""
+    img, T, nc, mg, K = render(scene, cam, t, deform=deform, tile=tile)
+    if deform:
+        X, Q, S = _deform_fn(scene, t)
+        p = project(scene, cam, X, Q, S, tile=tile)
+    else:
+        p = project(scene, cam, tile=tile)
+    H, W = int(cam.height), int(cam.width)
+    ty, tx = (H + tile - 1) // tile, (W + tile - 1) // tile
+    bad_tiles = np.zeros((ty, tx), bool)
+
+    def rect_of(u, v, r):
+        x0 = min(tx, max(0, int(np.floor((u - r) / tile))))
+        x1 = min(tx, max(0, int(np.floor((u + r) / tile)) + 1))
+        y0 = min(ty, max(0, int(np.floor((v - r) / tile))))
+        y1 = min(ty, max(0, int(np.floor((v + r) / tile)) + 1))
+        return x0, y0, x1, y1
+
+    for g in np.flatnonzero((p["margin"] < px_tol) & (p["radius"] > 0)):
+        a, b, c = p["cov2d"][g]
+        mid = 0.5 * (a + c)
+        r3 = 3.0 * np.sqrt(mid + np.sqrt(max(0.0, mid * mid - (a * c - b * b))))
+        radii = {int(np.ceil(r3 - px_tol)), int(np.ceil(r3 + px_tol))}
+        u0, v0 = p["xy"][g]
+        cover = np.zeros((ty, tx), int)
+        n_cand = 0
+        for r in radii:
+            for du in (-px_tol, 0.0, px_tol):
+                for dv in (-px_tol, 0.0, px_tol):
+                    x0, y0, x1, y1 = rect_of(u0 + du, v0 + dv, r)
+                    cover[y0:y1, x0:x1] += 1
+                    n_cand += 1
+        bad_tiles |= (cover > 0) & (cover < n_cand)
+    mask = np.kron(bad_tiles, np.ones((tile, tile), bool))[:H, :W] | (mg < margin_tol)
+    return mask, img, T, nc, K
 
 
 def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16):

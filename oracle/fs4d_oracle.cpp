@@ -390,8 +390,10 @@ void orc_composite(int32_t width, int32_t height, int32_t tile, const uint32_t* 
       mg = std::min(mg, std::fabs(alpha - kAlphaMin) / kAlphaMin);
       if (alpha < kAlphaMin) continue;
       // Two blended terms whose depths tie to within float32 rounding may be
-      // ordered differently by a float32 implementation: record the gap.
-      if (prev_depth > 0.0) mg = std::min(mg, std::fabs(depth[g] - prev_depth) / std::fabs(depth[g]));
+      // ordered differently by a float32 implementation: record the relative gap
+      // (weighted x100, so one threshold of 5e-5 flags alpha/T decisions within
+      // 5e-5 and depth gaps within 5e-7, ~8 float32 ulps, relative).
+      if (prev_depth > 0.0) mg = std::min(mg, 100.0 * std::fabs(depth[g] - prev_depth) / std::fabs(depth[g]));
       prev_depth = depth[g];
       const double Tn = T * (1.0 - alpha);
       mg = std::min(mg, std::fabs(Tn - kTMin) / kTMin);

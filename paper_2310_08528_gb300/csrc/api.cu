@@ -1,0 +1,872 @@
+// C ABI of libfs4d.so: contexts, resident scenes, work memory and the per-frame
+// launch sequence deform -> project -> scan/emit -> radix sort -> ranges ->
+// composite.  See include/fs4d.h for the contract of every call.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fs4d_internal.cuh"
+
+using namespace fs4d;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (e != cudaSuccess) return e;
+  }
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <typename T>
+T* P(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+struct Scene {
+  int n = 0, sh_degree = 0, K = 1;
+  DevBuf means, log_scales, quats, opacity_logits, sh;
+  DevBuf planes, planes_bf16, mlp, mlp_t, tc_ops, tc_bias;
+  PlaneGeom pg{};
+  MlpGeomT mg{};
+  MlpGeomTC tg{};
+  size_t planes_floats = 0, mlp_floats = 0;
+  size_t resident = 0;
+  bool bf16_ok = false;
+  // capacity-mode reservation
+  long long reserved_pairs = 0;
+  int reserved_w = 0, reserved_h = 0;
+};
+
+// Per-context work memory, grown on demand (never during a capture).
+struct Work {
+  DevBuf dmeans, dquats, dscales;          // deformed Gaussians
+  DevBuf xy, co, rgb, depth, radius, rect; // projected
+  DevBuf offsets, emit_lb, counters, num_pairs, hist;
+  DevBuf keys, values, keys_alt, values_alt;
+  DevBuf sort_lb;
+  DevBuf ranges;
+  DevBuf ts;
+  DevBuf host_img;                         // device staging image of fs4d_render_host
+  long long cap_pairs = 0;
+  long long sort_parts_cap = 0;
+  int cap_n = 0, cap_tiles = 0;
+};
+
+constexpr int kSortMaxPasses = 8;
+constexpr int kCounters = 16;  // [0] emit ticket, [8..15] unused
+
+}  // namespace
+
+struct fs4d_frame {
+  int scene = -1;
+  int width = 0, height = 0;
+  long long pairs = 0;
+};
+
+struct fs4d_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::map<int, Scene*> scenes;
+  int next_id = 1;
+  Work w;
+  DevBuf status;
+  uint32_t* h_pinned = nullptr;  // [4] readback slots
+  long long last_pairs = 0;
+  bool timing = false;
+  cudaEvent_t ev[8] = {};        // deform, project, emit, emit end, sort, ranges, composite, end
+};
+
+namespace {
+
+fs4d_status fail(fs4d_ctx* c, fs4d_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+fs4d_status cuda_fail(fs4d_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, e == cudaErrorMemoryAllocation ? FS4D_ERR_OOM : FS4D_ERR_CUDA, m);
+}
+
+#define FS4D_CUDA(ctx, expr)                                   \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Record stage event i (as an external event node when the stream is being
+// captured, so that replays of the graph still time the stage).
+void mark(fs4d_ctx* c, int i) {
+  if (!c->timing) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c->ev[i], c->stream);
+}
+
+int ceil_log2(long long v) {
+  int b = 0;
+  while ((1ll << b) < v) ++b;
+  return b;
+}
+
+int tiles_of(int px) { return (px + kTile - 1) / kTile; }
+
+CamParams cam_params(const fs4d_camera& c) {
+  CamParams p;
+  p.width = c.width; p.height = c.height;
+  p.fx = c.fx; p.fy = c.fy; p.cx = c.cx; p.cy = c.cy; p.znear = c.znear;
+  for (int i = 0; i < 12; ++i) p.m[i] = c.world_to_cam[i];
+  return p;
+}
+
+bool valid_cam(const fs4d_camera* c) {
+  return c && c->width > 0 && c->height > 0 && c->width <= 8192 && c->height <= 8192 && c->fx > 0 && c->fy > 0;
+}
+
+// Plane geometry: level-major, then xy xz yz xt yt zt; [R_b][R_a][h] each.
+void plane_geom(const fs4d_scene_desc& d, PlaneGeom& pg, size_t& total) {
+  static const int ax[6] = {0, 0, 1, 0, 1, 2}, bx[6] = {1, 2, 2, 3, 3, 3};
+  pg.n_levels = d.n_levels;
+  pg.feat_dim = d.feat_dim;
+  pg.res_time = d.res_time;
+  long long off = 0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    pg.res[l] = l < d.n_levels ? d.res_spatial[l] : 0;
+    for (int p = 0; p < 6; ++p) {
+      pg.off[l][p] = off;
+      if (l < d.n_levels) {
+        const long long Ra = ax[p] < 3 ? d.res_spatial[l] : d.res_time;
+        const long long Rb = bx[p] < 3 ? d.res_spatial[l] : d.res_time;
+        off += Ra * Rb * d.feat_dim;
+      }
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    pg.aabb_min[a] = d.aabb_min[a];
+    pg.aabb_scale[a] = 2.f / (d.aabb_max[a] - d.aabb_min[a]);
+  }
+  total = (size_t)off;
+}
+
+// Offsets of the source MLP layout (W[out][in] then b[out], d1 d2 x1 x2 r1 r2 s1 s2).
+struct SrcLayer {
+  int out, in;
+  size_t w, b;
+};
+
+std::vector<SrcLayer> src_layers(int hin, int W, size_t* total) {
+  const int outs[8] = {W, W, W, 3, W, 4, W, 3};
+  const int ins[8] = {hin, W, W, W, W, W, W, W};
+  std::vector<SrcLayer> L(8);
+  size_t off = 0;
+  for (int k = 0; k < 8; ++k) {
+    L[k].out = outs[k]; L[k].in = ins[k];
+    L[k].w = off; off += (size_t)outs[k] * ins[k];
+    L[k].b = off; off += outs[k];
+  }
+  *total = off;
+  return L;
+}
+
+// FP32 kernel layout: every layer transposed, Wt[in][out] then b[out], each
+// block padded to a multiple of 4 floats.
+std::vector<float> transpose_mlp(const float* src, int hin, int W, MlpGeomT& mg) {
+  size_t tot;
+  auto L = src_layers(hin, W, &tot);
+  std::vector<float> out;
+  mg.hin = hin;
+  auto pad = [&]() { while (out.size() % 4) out.push_back(0.f); };
+  for (int k = 0; k < 8; ++k) {
+    pad();
+    mg.w[k] = (int)out.size();
+    for (int i = 0; i < L[k].in; ++i)
+      for (int o = 0; o < L[k].out; ++o) out.push_back(src[L[k].w + (size_t)o * L[k].in + i]);
+    pad();
+    mg.b[k] = (int)out.size();
+    for (int o = 0; o < L[k].out; ++o) out.push_back(src[L[k].b + o]);
+  }
+  pad();
+  mg.total = (int)out.size();
+  return out;
+}
+
+uint16_t f2bf(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+// Byte offset of element (row r, k) of a K-major operand in the canonical
+// no-swizzle layout: 8-row x 16-byte core matrices, core (r/8, k/8) at
+// ((r/8) * (K/8) + k/8) * 128 bytes, element at (r%8)*16 + (k%8)*2 inside.
+size_t umma_off(int r, int k, int Kdim) {
+  return ((size_t)(r / 8) * (Kdim / 8) + (k / 8)) * 128 + (r % 8) * 16 + (k % 8) * 2;
+}
+
+// BF16 tensor-core operand image: B1 = d1 [64 x hin], B2 = d2 [64 x 64],
+// B3 = [x1; r1; s1] [192 x 64], B4 = block-diag(x2, r2, s2) padded [16 x 192].
+void build_tc_image(const float* src, int hin, int W, MlpGeomTC& tg, std::vector<uint8_t>& img,
+                    std::vector<float>& bias) {
+  size_t tot;
+  auto L = src_layers(hin, W, &tot);
+  tg.hin = hin;
+  tg.b1_off = 0;
+  tg.b2_off = tg.b1_off + 64 * hin * 2;
+  tg.b3_off = tg.b2_off + 64 * 64 * 2;
+  tg.b4_off = tg.b3_off + 192 * 64 * 2;
+  tg.bytes = tg.b4_off + 16 * 192 * 2;
+  img.assign(tg.bytes, 0);
+  auto put = [&](int base, int r, int k, int Kdim, float v) {
+    const uint16_t b = f2bf(v);
+    std::memcpy(&img[base + umma_off(r, k, Kdim)], &b, 2);
+  };
+  for (int o = 0; o < 64; ++o)
+    for (int i = 0; i < hin; ++i) put(tg.b1_off, o, i, hin, src[L[0].w + (size_t)o * hin + i]);
+  for (int o = 0; o < 64; ++o)
+    for (int i = 0; i < 64; ++i) put(tg.b2_off, o, i, 64, src[L[1].w + (size_t)o * 64 + i]);
+  for (int h = 0; h < 3; ++h)
+    for (int o = 0; o < 64; ++o)
+      for (int i = 0; i < 64; ++i) put(tg.b3_off, 64 * h + o, i, 64, src[L[2 + 2 * h].w + (size_t)o * 64 + i]);
+  const int col0[3] = {0, 3, 7};
+  for (int h = 0; h < 3; ++h)
+    for (int j = 0; j < L[3 + 2 * h].out; ++j)
+      for (int i = 0; i < 64; ++i) put(tg.b4_off, col0[h] + j, 64 * h + i, 192, src[L[3 + 2 * h].w + (size_t)j * 64 + i]);
+  bias.assign(64 + 64 + 192 + 16, 0.f);
+  tg.bias_off[0] = 0; tg.bias_off[1] = 64; tg.bias_off[2] = 128; tg.bias_off[3] = 320;
+  tg.bias_total = 336;
+  for (int o = 0; o < 64; ++o) bias[o] = src[L[0].b + o];
+  for (int o = 0; o < 64; ++o) bias[64 + o] = src[L[1].b + o];
+  for (int h = 0; h < 3; ++h)
+    for (int o = 0; o < 64; ++o) bias[128 + 64 * h + o] = src[L[2 + 2 * h].b + o];
+  for (int h = 0; h < 3; ++h)
+    for (int j = 0; j < L[3 + 2 * h].out; ++j) bias[320 + col0[h] + j] = src[L[3 + 2 * h].b + j];
+}
+
+template <typename T>
+fs4d_status upload(fs4d_ctx* c, DevBuf& b, const T* h, size_t count, size_t* acc) {
+  FS4D_CUDA(c, ensure(b, sizeof(T) * std::max<size_t>(count, 1)));
+  if (count) FS4D_CUDA(c, cudaMemcpy(b.p, h, sizeof(T) * count, cudaMemcpyHostToDevice));
+  *acc += b.bytes;
+  return FS4D_OK;
+}
+
+void free_scene(Scene* s) {
+  DevBuf* all[] = {&s->means, &s->log_scales, &s->quats, &s->opacity_logits, &s->sh, &s->planes,
+                   &s->planes_bf16, &s->mlp, &s->mlp_t, &s->tc_ops, &s->tc_bias};
+  for (DevBuf* b : all) release(*b);
+  delete s;
+}
+
+fs4d_status get_scene(fs4d_ctx* c, fs4d_scene_id id, Scene** out) {
+  auto it = c->scenes.find(id);
+  if (it == c->scenes.end()) return fail(c, FS4D_ERR_NOT_FOUND, "unknown scene id " + std::to_string(id));
+  *out = it->second;
+  return FS4D_OK;
+}
+
+// Grow the per-Gaussian / per-tile / per-pair work buffers.
+fs4d_status ensure_work(fs4d_ctx* c, int n, int n_tiles, long long pairs) {
+  Work& w = c->w;
+  bool grow = n > w.cap_n || n_tiles > w.cap_tiles || pairs > w.cap_pairs;
+  if (!grow) return FS4D_OK;
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (n > w.cap_n) {
+    const size_t m = (size_t)n;
+    FS4D_CUDA(c, ensure(w.dmeans, 12 * m));
+    FS4D_CUDA(c, ensure(w.dquats, 16 * m));
+    FS4D_CUDA(c, ensure(w.dscales, 12 * m));
+    FS4D_CUDA(c, ensure(w.xy, 8 * m));
+    FS4D_CUDA(c, ensure(w.co, 16 * m));
+    FS4D_CUDA(c, ensure(w.rgb, 12 * m));
+    FS4D_CUDA(c, ensure(w.depth, 4 * m));
+    FS4D_CUDA(c, ensure(w.radius, 4 * m));
+    FS4D_CUDA(c, ensure(w.rect, 16 * m));
+    FS4D_CUDA(c, ensure(w.offsets, 4 * m));
+    FS4D_CUDA(c, ensure(w.emit_lb, 8 * (size_t)(emit_parts(n) + 1)));
+    w.cap_n = n;
+  }
+  FS4D_CUDA(c, ensure(w.counters, 4 * kCounters));
+  FS4D_CUDA(c, ensure(w.num_pairs, 4 * 4));
+  FS4D_CUDA(c, ensure(w.hist, 4 * 256 * kSortMaxPasses));
+  if (n_tiles > w.cap_tiles) {
+    FS4D_CUDA(c, ensure(w.ranges, 8 * (size_t)n_tiles));
+    w.cap_tiles = n_tiles;
+  }
+  if (pairs > w.cap_pairs) {
+    const long long cap = std::max<long long>(pairs, 4096);
+    FS4D_CUDA(c, ensure(w.keys, 8 * (size_t)cap));
+    FS4D_CUDA(c, ensure(w.values, 4 * (size_t)cap));
+    FS4D_CUDA(c, ensure(w.keys_alt, 8 * (size_t)cap));
+    FS4D_CUDA(c, ensure(w.values_alt, 4 * (size_t)cap));
+    w.sort_parts_cap = sort_parts(cap);
+    FS4D_CUDA(c, ensure(w.sort_lb, 4 * 256 * (size_t)kSortMaxPasses * w.sort_parts_cap));
+    w.cap_pairs = cap;
+  }
+  return FS4D_OK;
+}
+
+SortWork sort_work(fs4d_ctx* c) {
+  SortWork sw;
+  sw.hist = P<uint32_t>(c->w.hist);
+  sw.lookback = P<uint32_t>(c->w.sort_lb);
+  sw.part_counters = P<uint32_t>(c->w.counters) + 8;
+  sw.max_parts = c->w.sort_parts_cap;
+  return sw;
+}
+
+DeformArgs deform_args(Scene* s, const float* ts, float t0, int n_t, float* om, float* oq, float* os) {
+  DeformArgs a{};
+  a.n = s->n; a.n_t = n_t; a.ts = ts; a.t0 = t0;
+  a.means = P<float>(s->means); a.quats = P<float>(s->quats); a.log_scales = P<float>(s->log_scales);
+  a.out_means = om; a.out_quats = oq; a.out_log_scales = os;
+  a.planes = P<float>(s->planes);
+  a.planes_bf16 = P<__nv_bfloat16>(s->planes_bf16);
+  a.mlp_t = P<float>(s->mlp_t);
+  a.mg = s->mg;
+  a.tc_ops = P<uint8_t>(s->tc_ops);
+  a.tc_bias = P<float>(s->tc_bias);
+  a.tg = s->tg;
+  a.pg = s->pg;
+  return a;
+}
+
+fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformArgs& a) {
+  DeformArgs b = a;
+  b.status = P<uint32_t>(c->status);
+  if (prec == FS4D_BF16) {
+    if (!s->bf16_ok) return fail(c, FS4D_ERR_UNIMPLEMENTED, "BF16 deformation does not support this scene shape");
+    FS4D_CUDA(c, launch_deform_bf16(b, c->stream));
+  } else {
+    FS4D_CUDA(c, launch_deform_fp32(b, c->stream));
+  }
+  return FS4D_OK;
+}
+
+// Everything of a frame up to (and including) the key emission.
+fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
+                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report) {
+  Work& w = c->w;
+  const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
+  mark(c, 0);
+  DeformArgs da = deform_args(s, d_t, t, 1, P<float>(w.dmeans), P<float>(w.dquats), P<float>(w.dscales));
+  fs4d_status st = run_deform(c, s, prec, da);
+  if (st != FS4D_OK) return st;
+  mark(c, 1);
+  ProjectArgs pa{};
+  pa.n = s->n;
+  pa.means = P<float>(w.dmeans); pa.quats = P<float>(w.dquats); pa.log_scales = P<float>(w.dscales);
+  pa.opacity_logits = P<float>(s->opacity_logits); pa.sh = P<float>(s->sh); pa.sh_degree = s->sh_degree;
+  pa.cam = cam_params(shape);
+  pa.cam_dev = d_cam;
+  pa.tiles_x = tx; pa.tiles_y = ty;
+  pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
+  pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
+  FS4D_CUDA(c, launch_project(pa, c->stream));
+  mark(c, 2);
+  const int key_bits = 32 + ceil_log2((long long)tx * ty);
+  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), c->stream));
+  EmitArgs ea{};
+  ea.n = s->n; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
+  ea.capacity = cap;
+  ea.keys = P<unsigned long long>(w.keys); ea.values = P<uint32_t>(w.values);
+  ea.offsets = P<uint32_t>(w.offsets);
+  ea.lookback = P<unsigned long long>(w.emit_lb);
+  ea.part_counter = P<uint32_t>(w.counters);
+  ea.num_pairs = P<uint32_t>(w.num_pairs);
+  ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
+  ea.hist = P<uint32_t>(w.hist);
+  ea.passes = sort_passes(key_bits);
+  ea.status = P<uint32_t>(c->status);
+  ea.report_overflow = report ? 1 : 0;
+  FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
+  mark(c, 3);
+  return FS4D_OK;
+}
+
+// Sort, ranges and composite with n_dev = the sortable pair count on device.
+fs4d_status frame_back(fs4d_ctx* c, const fs4d_camera& shape, long long n_bound, float* d_image, float* d_t_final,
+                       int* d_n_contrib) {
+  Work& w = c->w;
+  const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
+  const int key_bits = 32 + ceil_log2((long long)tx * ty);
+  const uint32_t* n_dev = P<uint32_t>(w.num_pairs) + 1;
+  bool alt = false;
+  mark(c, 4);
+  FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
+                           P<uint32_t>(w.values_alt), n_dev, n_bound, key_bits, true, sort_work(c),
+                           P<uint32_t>(c->status), c->stream, &alt));
+  unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
+  uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
+  mark(c, 5);
+  FS4D_CUDA(c, launch_ranges(keys, n_dev, n_bound, P<uint2>(w.ranges), tx * ty, c->stream));
+  mark(c, 6);
+  FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values, P<float2>(w.xy),
+                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, c->stream));
+  mark(c, 7);
+  return FS4D_OK;
+}
+
+fs4d_status read_pairs(fs4d_ctx* c, long long* K) {
+  FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->w.num_pairs.p, 8, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  *K = (long long)c->h_pinned[0];
+  return FS4D_OK;
+}
+
+fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t, float* d_image,
+                        float* d_t_final, int32_t* d_n_contrib) {
+  const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
+  fs4d_status st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs);
+  if (st != FS4D_OK) return st;
+  st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false);
+  if (st != FS4D_OK) return st;
+  long long K = 0;
+  if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
+  if (K >= 0xffffffffll) return fail(c, FS4D_ERR_CAPACITY, "more than 2^32-1 tile pairs in one frame");
+  if (K > c->w.cap_pairs) {
+    if ((st = ensure_work(c, s->n, n_tiles, K + K / 4)) != FS4D_OK) return st;
+    st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false);
+    if (st != FS4D_OK) return st;
+  }
+  c->last_pairs = K;
+  return frame_back(c, *cam, K, d_image, d_t_final, d_n_contrib);
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+fs4d_status fs4d_create(int32_t device, void* cuda_stream, fs4d_ctx** out) {
+  if (!out) return FS4D_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FS4D_ERR_INVALID_ARG;
+  fs4d_ctx* c = new (std::nothrow) fs4d_ctx();
+  if (!c) return FS4D_ERR_OOM;
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  if (ensure(c->status, 16) != cudaSuccess || cudaMemset(c->status.p, 0, 16) != cudaSuccess ||
+      cudaMallocHost(&c->h_pinned, 16) != cudaSuccess) {
+    release(c->status);
+    delete c;
+    return FS4D_ERR_OOM;
+  }
+  *out = c;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_destroy(fs4d_ctx* c) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->scenes) free_scene(kv.second);
+    Work& w = c->w;
+    DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
+                     &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.ts, &w.host_img};
+    for (DevBuf* b : all) release(*b);
+    release(c->status);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    for (int i = 0; i < 8; ++i)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  }
+  delete c;
+  return FS4D_OK;
+}
+
+const char* fs4d_last_error(const fs4d_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+fs4d_status fs4d_set_stream(fs4d_ctx* c, void* cuda_stream) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_check_device_status(fs4d_ctx* c) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned + 2, c->status.p, 4, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(c->status.p, 0, 4, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  const uint32_t v = c->h_pinned[2];
+  if (v & kStatusTimeout) return fail(c, FS4D_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  if (v & kStatusCapacity) return fail(c, FS4D_ERR_CAPACITY, "tile-pair capacity exceeded");
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id* out) {
+  if (!c || !d || !out) return fail(c, FS4D_ERR_INVALID_ARG, "null argument");
+  if (d->n < 1 || d->sh_degree < 0 || d->sh_degree > 3 || !d->means || !d->log_scales || !d->quats ||
+      !d->opacity_logits || !d->sh || !d->planes || !d->mlp)
+    return fail(c, FS4D_ERR_INVALID_ARG, "scene: n >= 1, sh_degree 0..3 and every array are required");
+  if (d->n_levels < 1 || d->n_levels > kMaxLevels || d->res_time < 2)
+    return fail(c, FS4D_ERR_INVALID_ARG, "scene: 1..4 levels and res_time >= 2 are required");
+  for (int l = 0; l < d->n_levels; ++l)
+    if (d->res_spatial[l] < 2) return fail(c, FS4D_ERR_INVALID_ARG, "scene: spatial resolution >= 2 required");
+  for (int a = 0; a < 3; ++a)
+    if (!(d->aabb_max[a] > d->aabb_min[a])) return fail(c, FS4D_ERR_INVALID_ARG, "scene: empty bounding box");
+  if (d->mlp_width != kWidth) return fail(c, FS4D_ERR_UNIMPLEMENTED, "scene: only MLP width 64 is supported");
+  if (!deform_fp32_supported(d->feat_dim, d->n_levels))
+    return fail(c, FS4D_ERR_UNIMPLEMENTED, "scene: feat_dim must be 16 or 32 with 1..3 levels");
+  DeviceGuard g(c->device);
+  Scene* s = new Scene();
+  s->n = d->n;
+  s->sh_degree = d->sh_degree;
+  s->K = (d->sh_degree + 1) * (d->sh_degree + 1);
+  size_t acc = 0;
+  const size_t n = (size_t)d->n;
+  size_t planes_total;
+  plane_geom(*d, s->pg, planes_total);
+  s->planes_floats = planes_total;
+  const int hin = d->feat_dim * d->n_levels;
+  size_t mlp_total;
+  src_layers(hin, d->mlp_width, &mlp_total);
+  s->mlp_floats = mlp_total;
+  fs4d_status st;
+  auto bail = [&](fs4d_status e) { free_scene(s); return e; };
+  if ((st = upload(c, s->means, d->means, 3 * n, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->log_scales, d->log_scales, 3 * n, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->quats, d->quats, 4 * n, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->opacity_logits, d->opacity_logits, n, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->sh, d->sh, 3 * n * s->K, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->planes, d->planes, planes_total, &acc)) != FS4D_OK) return bail(st);
+  std::vector<uint16_t> pb(planes_total);
+  for (size_t i = 0; i < planes_total; ++i) pb[i] = f2bf(d->planes[i]);
+  if ((st = upload(c, s->planes_bf16, pb.data(), planes_total, &acc)) != FS4D_OK) return bail(st);
+  if ((st = upload(c, s->mlp, d->mlp, mlp_total, &acc)) != FS4D_OK) return bail(st);
+  std::vector<float> mt = transpose_mlp(d->mlp, hin, d->mlp_width, s->mg);
+  if ((st = upload(c, s->mlp_t, mt.data(), mt.size(), &acc)) != FS4D_OK) return bail(st);
+  s->bf16_ok = deform_bf16_supported(d->feat_dim, d->n_levels);
+  if (s->bf16_ok) {
+    std::vector<uint8_t> img;
+    std::vector<float> bias;
+    build_tc_image(d->mlp, hin, d->mlp_width, s->tg, img, bias);
+    if ((st = upload(c, s->tc_ops, img.data(), img.size(), &acc)) != FS4D_OK) return bail(st);
+    if ((st = upload(c, s->tc_bias, bias.data(), bias.size(), &acc)) != FS4D_OK) return bail(st);
+  }
+  s->resident = acc;
+  const int id = c->next_id++;
+  c->scenes[id] = s;
+  *out = id;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_unload_scene(fs4d_ctx* c, fs4d_scene_id id) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_scene(s);
+  c->scenes.erase(id);
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_scene_bytes(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32_t height, float ppg,
+                             size_t* resident, size_t* per_frame) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  if (resident) *resident = s->resident;
+  if (per_frame) {
+    const size_t n = (size_t)s->n;
+    const size_t pairs = (size_t)(std::max(0.f, ppg) * (float)n) + 4096;
+    const size_t tiles = (size_t)tiles_of(width) * tiles_of(height);
+    *per_frame = n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4) + pairs * 24 +
+                 sort_parts((long long)pairs) * 256 * 4 * kSortMaxPasses + tiles * 8 +
+                 (size_t)width * height * 12;
+  }
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_deform(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const float* h_ts, int32_t n_t,
+                        float* d_means, float* d_quats, float* d_log_scales) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (n_t < 1 || !h_ts || !d_means || !d_quats || !d_log_scales)
+    return fail(c, FS4D_ERR_INVALID_ARG, "deform: n_t >= 1 and every pointer are required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  if (c->w.ts.bytes < 4 * (size_t)n_t) {
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+    FS4D_CUDA(c, ensure(c->w.ts, 4 * (size_t)n_t));
+  }
+  FS4D_CUDA(c, cudaMemcpyAsync(c->w.ts.p, h_ts, 4 * (size_t)n_t, cudaMemcpyHostToDevice, c->stream));
+  DeformArgs a = deform_args(s, P<float>(c->w.ts), 0.f, n_t, d_means, d_quats, d_log_scales);
+  return run_deform(c, s, prec, a);
+}
+
+fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
+                        float* d_image, float* d_t_final, int32_t* d_n_contrib, fs4d_frame** saved) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!valid_cam(cam) || !d_image) return fail(c, FS4D_ERR_INVALID_ARG, "render: camera and image are required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  st = render_sync(c, s, prec, cam, t, d_image, d_t_final, d_n_contrib);
+  if (st != FS4D_OK) return st;
+  if (saved) {
+    *saved = nullptr;
+    return fail(c, FS4D_ERR_UNIMPLEMENTED, "render: saving frames for the backward is not built yet");
+  }
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
+                             float* h_image) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!valid_cam(cam) || !h_image) return fail(c, FS4D_ERR_INVALID_ARG, "render_host: camera and image required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  DevBuf& img = c->w.host_img;
+  const size_t bytes = (size_t)cam->width * cam->height * 12;
+  if (img.bytes < bytes) {
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+    FS4D_CUDA(c, ensure(img, bytes));
+  }
+  st = render_sync(c, s, prec, cam, t, P<float>(img), nullptr, nullptr);
+  if (st != FS4D_OK) return st;
+  FS4D_CUDA(c, cudaMemcpyAsync(h_image, img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_reserve(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32_t height, int64_t pair_capacity) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (width <= 0 || height <= 0 || pair_capacity < 0) return fail(c, FS4D_ERR_INVALID_ARG, "reserve: bad size");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  st = ensure_work(c, s->n, tiles_of(width) * tiles_of(height), pair_capacity);
+  if (st != FS4D_OK) return st;
+  s->reserved_pairs = pair_capacity;
+  s->reserved_w = width;
+  s->reserved_h = height;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_render_async(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* shape,
+                              const fs4d_camera* d_cam, const float* d_t, float* d_image) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!valid_cam(shape) || !d_cam || !d_t || !d_image)
+    return fail(c, FS4D_ERR_INVALID_ARG, "render_async: shape, device camera, device t and image are required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  const int n_tiles = tiles_of(shape->width) * tiles_of(shape->height);
+  if (s->reserved_pairs <= 0 || c->w.cap_pairs < s->reserved_pairs || c->w.cap_tiles < n_tiles || c->w.cap_n < s->n)
+    return fail(c, FS4D_ERR_INVALID_ARG, "render_async: call fs4d_reserve for this scene and size first");
+  DeviceGuard g(c->device);
+  const long long cap = s->reserved_pairs;
+  st = frame_front(c, s, prec, *shape, d_cam, d_t, 0.f, cap, true);
+  if (st != FS4D_OK) return st;
+  return frame_back(c, *shape, cap, d_image, nullptr, nullptr);
+}
+
+fs4d_status fs4d_set_stage_timing(fs4d_ctx* c, int32_t enable) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (enable && !c->ev[0]) {
+    for (int i = 0; i < 8; ++i) FS4D_CUDA(c, cudaEventCreate(&c->ev[i]));
+  }
+  c->timing = enable != 0;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_stage_times(fs4d_ctx* c, float* h_ms) {
+  if (!c || !h_ms) return FS4D_ERR_INVALID_ARG;
+  if (!c->ev[0]) return fail(c, FS4D_ERR_INVALID_ARG, "stage_times: timing was never enabled");
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, cudaEventSynchronize(c->ev[7]));
+  const int from[6] = {0, 1, 2, 4, 5, 6}, to[6] = {1, 2, 3, 5, 6, 7};
+  for (int k = 0; k < 6; ++k) FS4D_CUDA(c, cudaEventElapsedTime(&h_ms[k], c->ev[from[k]], c->ev[to[k]]));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* saved, const float* d_dl_dimage, const fs4d_grads* g) {
+  (void)saved; (void)d_dl_dimage; (void)g;
+  return fail(c, FS4D_ERR_UNIMPLEMENTED, "render_backward: not built yet");
+}
+
+fs4d_status fs4d_frame_free(fs4d_ctx* c, fs4d_frame* f) {
+  (void)c;
+  delete f;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_frame_pairs(const fs4d_frame* f, int64_t* pairs) {
+  if (!f || !pairs) return FS4D_ERR_INVALID_ARG;
+  *pairs = f->pairs;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_last_pairs(const fs4d_ctx* c, int64_t* pairs) {
+  if (!c || !pairs) return FS4D_ERR_INVALID_ARG;
+  *pairs = c->last_pairs;
+  return FS4D_OK;
+}
+
+// ------------------------------------------------------------------ stages
+
+fs4d_status fs4d_project(fs4d_ctx* c, int32_t n, const float* d_means, const float* d_quats,
+                         const float* d_log_scales, const float* d_opacity_logits, const float* d_sh,
+                         int32_t sh_degree, const fs4d_camera* cam, const fs4d_projected* out) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (n < 0 || !valid_cam(cam) || !out || sh_degree < 0 || sh_degree > 3 ||
+      (n > 0 && (!d_means || !d_quats || !d_log_scales || !d_opacity_logits || !d_sh || !out->xy ||
+                 !out->conic_opacity || !out->rgb || !out->depth || !out->radius || !out->rect)))
+    return fail(c, FS4D_ERR_INVALID_ARG, "project: bad argument");
+  DeviceGuard g(c->device);
+  ProjectArgs pa{};
+  pa.n = n; pa.means = d_means; pa.quats = d_quats; pa.log_scales = d_log_scales;
+  pa.opacity_logits = d_opacity_logits; pa.sh = d_sh; pa.sh_degree = sh_degree;
+  pa.cam = cam_params(*cam); pa.cam_dev = nullptr;
+  pa.tiles_x = tiles_of(cam->width); pa.tiles_y = tiles_of(cam->height);
+  pa.xy = reinterpret_cast<float2*>(out->xy); pa.conic_opacity = reinterpret_cast<float4*>(out->conic_opacity);
+  pa.rgb = out->rgb; pa.depth = out->depth; pa.radius = out->radius; pa.rect = reinterpret_cast<int4*>(out->rect);
+  FS4D_CUDA(c, launch_project(pa, c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const int32_t* d_rect, int32_t tiles_x,
+                          int32_t tiles_y, int64_t capacity, uint64_t* d_keys, uint32_t* d_values,
+                          uint32_t* d_ranges, int64_t* h_num_pairs) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (n < 0 || tiles_x < 1 || tiles_y < 1 || (long long)tiles_x * tiles_y > (1ll << 31) || capacity < 0 ||
+      !h_num_pairs || !d_ranges || (n > 0 && (!d_depth || !d_rect)) || (capacity > 0 && (!d_keys || !d_values)))
+    return fail(c, FS4D_ERR_INVALID_ARG, "bin_sort: bad argument");
+  DeviceGuard g(c->device);
+  fs4d_status st = ensure_work(c, std::max(n, 1), 1, capacity);
+  if (st != FS4D_OK) return st;
+  Work& w = c->w;
+  const int n_tiles = tiles_x * tiles_y;
+  const int key_bits = 32 + ceil_log2(n_tiles);
+  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(std::max(n, 1)), c->stream));
+  EmitArgs ea{};
+  ea.n = n; ea.depth = d_depth; ea.rect = reinterpret_cast<const int4*>(d_rect); ea.tiles_x = tiles_x;
+  ea.capacity = capacity;
+  ea.keys = reinterpret_cast<unsigned long long*>(d_keys); ea.values = d_values;
+  ea.offsets = P<uint32_t>(w.offsets);
+  ea.lookback = P<unsigned long long>(w.emit_lb);
+  ea.part_counter = P<uint32_t>(w.counters);
+  ea.num_pairs = P<uint32_t>(w.num_pairs);
+  ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
+  ea.hist = P<uint32_t>(w.hist);
+  ea.passes = sort_passes(key_bits);
+  ea.status = P<uint32_t>(c->status);
+  ea.report_overflow = 0;
+  FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
+  long long K = 0;
+  if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
+  *h_num_pairs = K;
+  if (K > capacity) {
+    return fail(c, FS4D_ERR_CAPACITY, "bin_sort: " + std::to_string(K) + " pairs exceed the capacity");
+  }
+  bool alt = false;
+  FS4D_CUDA(c, launch_sort(reinterpret_cast<unsigned long long*>(d_keys), d_values, P<unsigned long long>(w.keys_alt),
+                           P<uint32_t>(w.values_alt), nullptr, K, key_bits, true, sort_work(c),
+                           P<uint32_t>(c->status), c->stream, &alt));
+  if (alt && K > 0) {
+    FS4D_CUDA(c, cudaMemcpyAsync(d_keys, w.keys_alt.p, 8 * (size_t)K, cudaMemcpyDeviceToDevice, c->stream));
+    FS4D_CUDA(c, cudaMemcpyAsync(d_values, w.values_alt.p, 4 * (size_t)K, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  FS4D_CUDA(c, launch_ranges(reinterpret_cast<unsigned long long*>(d_keys), nullptr, K,
+                             reinterpret_cast<uint2*>(d_ranges), n_tiles, c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_sort_pairs(fs4d_ctx* c, int64_t n, int32_t key_bits, uint64_t* d_keys, uint32_t* d_values) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (n < 0 || key_bits < 1 || key_bits > 64 || (n > 0 && (!d_keys || !d_values)) || n >= (1ll << 30))
+    return fail(c, FS4D_ERR_INVALID_ARG, "sort_pairs: bad argument");
+  if (n == 0) return FS4D_OK;
+  DeviceGuard g(c->device);
+  fs4d_status st = ensure_work(c, 1, 1, n);
+  if (st != FS4D_OK) return st;
+  Work& w = c->w;
+  bool alt = false;
+  FS4D_CUDA(c, launch_sort(reinterpret_cast<unsigned long long*>(d_keys), d_values, P<unsigned long long>(w.keys_alt),
+                           P<uint32_t>(w.values_alt), nullptr, n, key_bits, false, sort_work(c),
+                           P<uint32_t>(c->status), c->stream, &alt));
+  if (alt) {
+    FS4D_CUDA(c, cudaMemcpyAsync(d_keys, w.keys_alt.p, 8 * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+    FS4D_CUDA(c, cudaMemcpyAsync(d_values, w.values_alt.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_composite(fs4d_ctx* c, int32_t width, int32_t height, const uint32_t* d_ranges,
+                           const uint32_t* d_values, const float* d_xy, const float* d_conic_opacity,
+                           const float* d_rgb, float* d_image, float* d_t_final, int32_t* d_n_contrib) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (width < 1 || height < 1 || width > 8192 || height > 8192 || !d_ranges || !d_xy || !d_conic_opacity ||
+      !d_rgb || !d_image)
+    return fail(c, FS4D_ERR_INVALID_ARG, "composite: bad argument");
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, launch_composite(width, height, reinterpret_cast<const uint2*>(d_ranges), d_values,
+                                reinterpret_cast<const float2*>(d_xy), reinterpret_cast<const float4*>(d_conic_opacity),
+                                d_rgb, d_image, d_t_final, d_n_contrib, c->stream));
+  return FS4D_OK;
+}
+
+}  // extern "C"

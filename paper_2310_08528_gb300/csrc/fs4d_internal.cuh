@@ -1,0 +1,162 @@
+// Internal declarations shared by the kernel translation units of libfs4d.so.
+// Kernels are written for sm_103a (GB300); nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fs4d.h"
+
+namespace fs4d {
+
+constexpr int kTile = 16;          // screen tile edge (pixels); one CTA composites one tile
+constexpr int kMaxLevels = 4;      // HexPlane resolution levels supported
+constexpr int kWidth = 64;         // MLP hidden width supported by the kernels
+constexpr int kDeltaDim = 10;      // dX (3) + dr (4) + ds (3)
+
+// Device status word bits (sticky until fs4d_check_device_status).
+constexpr uint32_t kStatusTimeout = 1u;   // a bounded spin gave up
+constexpr uint32_t kStatusCapacity = 2u;  // more tile pairs than buffer capacity
+
+// Bounded spin limit for decoupled look-back waits (iterations of ~100 ns).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// ---------------------------------------------------------------- HexPlane geometry
+struct PlaneGeom {
+  int n_levels;
+  int feat_dim;            // h
+  int res_time;
+  int res[kMaxLevels];     // spatial resolution per level
+  long long off[kMaxLevels][6];  // element offset of each plane (xy xz yz xt yt zt)
+  float aabb_min[3];
+  float aabb_scale[3];     // 2 / (max - min): u = (x - min) * scale - 1
+};
+
+// ---------------------------------------------------------------- FP32 MLP layout
+// The FP32 kernel keeps every layer transposed, Wt[in][out] followed by b[out],
+// in the order d1 d2 x1 x2 r1 r2 s1 s2, so one 128-bit shared-memory load feeds
+// four output accumulators.
+struct MlpGeomT {
+  int hin;                 // h * L
+  int w[8], b[8];          // float offsets of Wt and b of each layer
+  int total;               // floats (padded to a multiple of 4)
+};
+
+// ---------------------------------------------------------------- BF16 tcgen05 MLP layout
+// Operand images of the four GEMMs (bf16, UMMA canonical no-swizzle K-major
+// layout: 8x8 core matrices of 128 contiguous bytes; see deform_tc.cu):
+//   B1 = d1 [64 x hin], B2 = d2 [64 x 64], B3 = x1|r1|s1 stacked [192 x 64],
+//   B4 = block-diagonal x2/r2/s2 padded to [16 x 192].
+struct MlpGeomTC {
+  int hin;
+  int b1_off, b2_off, b3_off, b4_off;   // byte offsets inside the operand image
+  int bytes;                            // total operand image bytes
+  int bias_off[4];                      // float offsets of the biases (64, 64, 192, 16)
+  int bias_total;
+};
+
+struct DeformArgs {
+  int n;                        // Gaussians
+  int n_t;                      // timestamps
+  const float* ts;              // device [n_t], or NULL to use t0 (n_t must be 1)
+  float t0;
+  const float* means;           // [n][3]
+  const float* quats;           // [n][4]
+  const float* log_scales;      // [n][3]
+  float* out_means;             // [n_t][n][3]
+  float* out_quats;             // [n_t][n][4]
+  float* out_log_scales;        // [n_t][n][3]
+  const float* planes;          // float32 planes
+  const __nv_bfloat16* planes_bf16;
+  const float* mlp_t;           // FP32 transposed layout (MlpGeomT)
+  MlpGeomT mg;
+  const uint8_t* tc_ops;        // BF16 operand image (MlpGeomTC)
+  const float* tc_bias;
+  MlpGeomTC tg;
+  PlaneGeom pg;
+  uint32_t* status;
+};
+
+struct CamParams {
+  int width, height;
+  float fx, fy, cx, cy, znear;
+  float m[12];                  // rows 0..2 of world_to_cam
+};
+
+struct ProjectArgs {
+  int n;
+  const float* means;           // [n][3]
+  const float* quats;           // [n][4]
+  const float* log_scales;      // [n][3]
+  const float* opacity_logits;  // [n]
+  const float* sh;              // [n][K][3]
+  int sh_degree;
+  CamParams cam;
+  const fs4d_camera* cam_dev;   // if non-NULL, read the camera from device memory
+  int tiles_x, tiles_y;
+  float2* xy;
+  float4* conic_opacity;
+  float* rgb;
+  float* depth;
+  int* radius;
+  int4* rect;
+};
+
+// Tile-pair emission fused with the exclusive scan of per-Gaussian tile counts
+// (decoupled look-back) and with the digit histograms of every radix pass.
+struct EmitArgs {
+  int n;
+  const float* depth;
+  const int4* rect;
+  int tiles_x;
+  long long capacity;           // pairs the key/value buffers hold
+  unsigned long long* keys;     // [capacity]
+  uint32_t* values;             // [capacity]
+  uint32_t* offsets;            // [n] exclusive prefix of tile counts (kept for the backward)
+  unsigned long long* lookback; // [parts] scan look-back words (zeroed)
+  uint32_t* part_counter;       // zeroed
+  uint32_t* num_pairs;          // out: K (clamped to 2^32-1)
+  uint32_t* num_pairs_sort;     // out: K if K <= capacity, else 0 (what the sort may read)
+  int report_overflow;          // set kStatusCapacity in *status when K > capacity
+  uint32_t* hist;               // [passes][256] digit histograms (zeroed), or NULL
+  int passes;
+  uint32_t* status;
+};
+
+struct SortWork {
+  uint32_t* hist;               // [8][256]
+  uint32_t* lookback;           // [8][max_parts][256]
+  uint32_t* part_counters;      // [8]
+  long long max_parts;
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_deform_fp32(const DeformArgs& a, cudaStream_t s);
+cudaError_t launch_deform_bf16(const DeformArgs& a, cudaStream_t s);
+bool deform_fp32_supported(int feat_dim, int n_levels);
+bool deform_bf16_supported(int feat_dim, int n_levels);
+
+cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s);
+
+int emit_parts(int n);          // scan partitions of the emit kernel
+cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s);
+
+int sort_passes(int key_bits);
+long long sort_parts(long long n);
+// Stable LSD sort of (keys, values) on the low key_bits bits.  n_dev (if non-NULL)
+// holds the live count on the device; n_bound is an upper bound used to size the
+// grids.  hist_ready = the per-pass histograms are already in work.hist.  Returns
+// in *result_in_alt whether the sorted pairs ended in the alternate buffers.
+cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
+                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int key_bits,
+                        bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
+                        bool* result_in_alt);
+cudaError_t launch_ranges(const unsigned long long* keys, const uint32_t* n_dev, long long n_bound,
+                          uint2* ranges, int n_tiles, cudaStream_t s);
+
+cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
+                             const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
+                             float* t_final, int* n_contrib, cudaStream_t s);
+
+}  // namespace fs4d

@@ -1,0 +1,253 @@
+// Stable LSD radix sort of (64-bit key, 32-bit value) pairs, one-sweep style:
+//  - one histogram pass produces the 256-bin digit counts of EVERY radix pass at
+//    once (skipped when the binning kernel already produced them);
+//  - then one kernel per 8-bit digit.  Each CTA takes a 4096-pair partition by
+//    atomic ticket, ranks its keys stably (warp-striped order, __match_any_sync
+//    peers per digit, warp offsets chained through shared memory), publishes its
+//    per-digit counts and resolves its global per-digit offsets by decoupled
+//    look-back on its predecessors, then scatters through shared memory so that
+//    runs of equal digits are written contiguously.
+// Only the key bits that can differ are sorted (tile bits + 32 depth bits), so a
+// frame with 2500 tiles sorts 44 bits in 6 passes.
+#include "sync_util.cuh"
+
+namespace fs4d {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kPartPairs = kThreads * kItems;  // 4096
+constexpr int kRadix = 256;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr int kMaxPasses = 8;
+
+__global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
+                                                   const uint32_t* __restrict__ n_dev, long long n_bound,
+                                                   int passes, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const long long n = n_dev ? min((long long)*n_dev, n_bound) : n_bound;
+  const uint32_t lane_lt = lanemask_lt();
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned long long k = valid ? keys[i] : 0ull;
+    for (int p = 0; p < passes; ++p) {
+      const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (d < 256u && (peers & lane_lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t v = (&s_hist[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+struct PassArgs {
+  const unsigned long long* keys_in;
+  const uint32_t* values_in;
+  unsigned long long* keys_out;
+  uint32_t* values_out;
+  const uint32_t* n_dev;
+  long long n_bound;
+  int shift;
+  const uint32_t* hist;     // this pass's 256 counts
+  uint32_t* lookback;       // this pass's [parts][256], zeroed
+  uint32_t* part_counter;   // this pass's ticket, zeroed
+  uint32_t* status;
+};
+
+struct PassSmem {
+  unsigned long long keys[kPartPairs];
+  uint32_t values[kPartPairs];
+  uint32_t warp_cnt[kWarps][kRadix];
+  uint32_t global_off[kRadix];   // exclusive scan of the global histogram
+  uint32_t block_off[kRadix];    // exclusive scan of this partition's counts
+  uint32_t prev_off[kRadix];     // sum of predecessors' counts (look-back)
+  uint32_t scan_tmp[kWarps];
+  uint32_t part;
+};
+
+// Exclusive scan of one value per thread across the 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x / 32;
+  uint32_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += t;
+  }
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  uint32_t base = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w)
+    if ((uint32_t)w < warp) base += tmp[w];
+  __syncthreads();
+  return base + incl - v;
+}
+
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id(), warp = tid / 32;
+  if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
+  __syncthreads();
+  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
+  const uint32_t part = sm.part;
+  const long long base = (long long)part * kPartPairs;
+  if (base >= n) return;  // uniform across the CTA
+
+  // Global offset of each digit.
+  sm.global_off[tid] = block_excl_scan(a.hist[tid], sm.scan_tmp);
+
+  // Load (warp-striped: item i of lane l is element base + warp*512 + i*32 + l)
+  // and rank within the warp.
+  unsigned long long k[kItems];
+  uint32_t v[kItems], rank[kItems];
+  uint16_t dig[kItems];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const long long idx = base + (long long)warp * (kItems * 32) + i * 32 + lane;
+    const bool valid = idx < n;
+    k[i] = valid ? a.keys_in[idx] : 0ull;
+    v[i] = valid ? a.values_in[idx] : 0u;
+    const uint32_t d = valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u;
+    dig[i] = (uint16_t)d;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (d < 256u) before = sm.warp_cnt[warp][d];
+    __syncwarp();
+    rank[i] = before + (uint32_t)__popc(peers & lt);
+    if (d < 256u && (peers & lt) == 0) sm.warp_cnt[warp][d] = before + (uint32_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // Per digit (thread tid = digit): chain the warps, then the partitions.
+  uint32_t total = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = sm.warp_cnt[w][tid];
+    sm.warp_cnt[w][tid] = total;
+    total += c;
+  }
+  uint32_t* lb = a.lookback + (size_t)part * kRadix + tid;
+  uint32_t prev = 0;
+  if (part == 0) {
+    st_relaxed_u32(lb, kFlagInc | total);
+  } else {
+    st_relaxed_u32(lb, kFlagAgg | total);
+    long long j = (long long)part - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const uint32_t w = ld_relaxed_u32(a.lookback + (size_t)j * kRadix + tid);
+      const uint32_t flag = w & ~kValMask;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(a.status, kStatusTimeout);
+          break;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      prev += w & kValMask;
+      if (flag == kFlagInc) break;
+      --j;
+    }
+    st_relaxed_u32(lb, kFlagInc | ((prev + total) & kValMask));
+  }
+  sm.prev_off[tid] = prev;
+  sm.block_off[tid] = block_excl_scan(total, sm.scan_tmp);
+  __syncthreads();
+
+  // Local sort through shared memory.
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t d = dig[i];
+    if (d < 256u) {
+      const uint32_t pos = sm.block_off[d] + sm.warp_cnt[warp][d] + rank[i];
+      sm.keys[pos] = k[i];
+      sm.values[pos] = v[i];
+    }
+  }
+  __syncthreads();
+
+  // Scatter: consecutive slots of one digit go to consecutive addresses.
+  const int m = (int)min((long long)kPartPairs, n - base);
+  for (int j = tid; j < m; j += kThreads) {
+    const unsigned long long key = sm.keys[j];
+    const uint32_t d = (uint32_t)(key >> a.shift) & 255u;
+    const uint32_t out = sm.global_off[d] + sm.prev_off[d] + ((uint32_t)j - sm.block_off[d]);
+    if ((long long)out < n) {  // always true when the histogram matches the keys
+      a.keys_out[out] = key;
+      a.values_out[out] = sm.values[j];
+    }
+  }
+}
+
+}  // namespace
+
+int sort_passes(int key_bits) { return (key_bits + 7) / 8; }
+long long sort_parts(long long n) { return (n + kPartPairs - 1) / kPartPairs; }
+
+cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
+                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int key_bits,
+                        bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
+                        bool* result_in_alt) {
+  *result_in_alt = false;
+  const int passes = sort_passes(key_bits);
+  if (n_bound <= 0 || passes == 0) return cudaSuccess;
+  if (passes > kMaxPasses) return cudaErrorInvalidValue;
+  const long long parts = sort_parts(n_bound);
+  if (parts > work.max_parts || n_bound > (long long)kValMask) return cudaErrorInvalidValue;
+  static bool attr_done = false;
+  cudaError_t e;
+  if (!attr_done) {
+    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PassSmem));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * kMaxPasses, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(work.lookback, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
+  if (e != cudaSuccess) return e;
+  if (!hist_ready) {
+    e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)min(parts * 4, (long long)152 * 8);
+    hist_kernel<<<blocks, 256, 0, s>>>(keys, n_dev, n_bound, passes, work.hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  unsigned long long* kin = keys;
+  uint32_t* vin = values;
+  unsigned long long* kout = keys_alt;
+  uint32_t* vout = values_alt;
+  for (int p = 0; p < passes; ++p) {
+    PassArgs pa;
+    pa.keys_in = kin; pa.values_in = vin; pa.keys_out = kout; pa.values_out = vout;
+    pa.n_dev = n_dev; pa.n_bound = n_bound; pa.shift = 8 * p;
+    pa.hist = work.hist + p * kRadix;
+    pa.lookback = work.lookback + (size_t)p * parts * kRadix;
+    pa.part_counter = work.part_counters + p;
+    pa.status = status;
+    onesweep_kernel<<<(unsigned)parts, kThreads, sizeof(PassSmem), s>>>(pa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long* tk = kin; kin = kout; kout = tk;
+    uint32_t* tv = vin; vin = vout; vout = tv;
+  }
+  *result_in_alt = (passes & 1) != 0;
+  return cudaSuccess;
+}
+
+}  // namespace fs4d

@@ -1,0 +1,274 @@
+"""Python binding of libfs4d.so (include/fs4d.h) -- argument marshalling only.
+
+Every step of the render path runs in the library's CUDA kernels.  PyTorch is
+used for device memory (output tensors) and streams.  There is no fallback: if
+the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfs4d.so")
+
+FP32, BF16 = 0, 1
+STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_ERR_CAPACITY",
+          4: "FS4D_ERR_CUDA", 5: "FS4D_ERR_TIMEOUT", 6: "FS4D_ERR_NOT_FOUND", 7: "FS4D_ERR_UNIMPLEMENTED"}
+
+# Every symbol include/fs4d.h declares (checked by the tests against the .so).
+EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
+           "fs4d_load_scene", "fs4d_unload_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
+           "fs4d_render_host", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
+           "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
+           "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_composite")
+STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
+
+
+class Fs4dError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("sh_degree", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("sh", C.c_void_p),
+                ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3), ("n_levels", C.c_int32),
+                ("res_spatial", C.c_int32 * 4), ("res_time", C.c_int32), ("feat_dim", C.c_int32),
+                ("planes", C.c_void_p), ("mlp_width", C.c_int32), ("mlp", C.c_void_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("znear", C.c_float), ("world_to_cam", C.c_float * 16)]
+
+
+class Projected(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("xy", "conic_opacity", "rgb", "depth", "radius", "rect")]
+
+
+class Grads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")]
+
+
+_lib = None
+
+
+def library(path: str = LIB_PATH):
+    """Load libfs4d.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    L = C.CDLL(path)
+    vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+    sig = {
+        "fs4d_create": [i32, vp, C.POINTER(vp)],
+        "fs4d_destroy": [vp],
+        "fs4d_set_stream": [vp, vp],
+        "fs4d_check_device_status": [vp],
+        "fs4d_load_scene": [vp, C.POINTER(SceneDesc), C.POINTER(i32)],
+        "fs4d_unload_scene": [vp, i32],
+        "fs4d_scene_bytes": [vp, i32, i32, i32, f32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+        "fs4d_deform": [vp, i32, i32, vp, i32, vp, vp, vp],
+        "fs4d_render": [vp, i32, i32, C.POINTER(Camera), f32, vp, vp, vp, C.POINTER(vp)],
+        "fs4d_render_host": [vp, i32, i32, C.POINTER(Camera), f32, vp],
+        "fs4d_reserve": [vp, i32, i32, i32, i64],
+        "fs4d_render_async": [vp, i32, i32, C.POINTER(Camera), vp, vp, vp],
+        "fs4d_render_backward": [vp, vp, vp, C.POINTER(Grads)],
+        "fs4d_frame_free": [vp, vp],
+        "fs4d_frame_pairs": [vp, C.POINTER(i64)],
+        "fs4d_last_pairs": [vp, C.POINTER(i64)],
+        "fs4d_set_stage_timing": [vp, i32],
+        "fs4d_stage_times": [vp, C.POINTER(C.c_float)],
+        "fs4d_project": [vp, i32, vp, vp, vp, vp, vp, i32, C.POINTER(Camera), C.POINTER(Projected)],
+        "fs4d_bin_sort": [vp, i32, vp, vp, i32, i32, i64, vp, vp, vp, C.POINTER(i64)],
+        "fs4d_sort_pairs": [vp, i64, i32, vp, vp],
+        "fs4d_composite": [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.fs4d_last_error.argtypes = [vp]
+    L.fs4d_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def camera_struct(cam) -> Camera:
+    c = Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy, c.znear = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy), float(cam.znear)
+    c.world_to_cam = (C.c_float * 16)(*[float(v) for v in np.asarray(cam.world_to_cam, np.float32).ravel()])
+    return c
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class Context:
+    """One fs4d context: a CUDA device and the stream its work is queued on."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = library()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        self._check(self.lib.fs4d_create(self.device, C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
+        self.h = h
+        self._scenes: Dict[int, object] = {}
+
+    def _check(self, rc: int, h) -> None:
+        if rc != 0:
+            msg = self.lib.fs4d_last_error(h).decode() if h is not None else ""
+            raise Fs4dError(rc, msg)
+
+    def call(self, name: str, *args) -> None:
+        self._check(getattr(self.lib, name)(self.h, *args), self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.fs4d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        self.stream = stream
+        self.call("fs4d_set_stream", C.c_void_p(stream.cuda_stream))
+
+    def check_device_status(self) -> None:
+        self.call("fs4d_check_device_status")
+
+    # ------------------------------------------------------------------ scenes
+    def load_scene(self, scene) -> int:
+        arrs = {k: np.ascontiguousarray(getattr(scene, k), np.float32)
+                for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")}
+        d = SceneDesc()
+        d.n = int(arrs["means"].shape[0])
+        d.sh_degree = int(scene.sh_degree)
+        for k, v in arrs.items():
+            setattr(d, k, v.ctypes.data)
+        d.aabb_min = (C.c_float * 3)(*map(float, scene.aabb_min))
+        d.aabb_max = (C.c_float * 3)(*map(float, scene.aabb_max))
+        rs = list(scene.res_spatial)
+        d.n_levels = len(rs)
+        d.res_spatial = (C.c_int32 * 4)(*(rs + [0] * (4 - len(rs))))
+        d.res_time, d.feat_dim, d.mlp_width = int(scene.res_time), int(scene.feat_dim), int(scene.mlp_width)
+        sid = C.c_int32()
+        self.call("fs4d_load_scene", C.byref(d), C.byref(sid))
+        self._scenes[sid.value] = scene
+        return sid.value
+
+    def unload_scene(self, sid: int) -> None:
+        self.call("fs4d_unload_scene", sid)
+        self._scenes.pop(sid, None)
+
+    def scene_bytes(self, sid: int, width: int, height: int, pairs_per_gaussian: float) -> Tuple[int, int]:
+        r, f = C.c_size_t(), C.c_size_t()
+        self.call("fs4d_scene_bytes", sid, width, height, float(pairs_per_gaussian), C.byref(r), C.byref(f))
+        return r.value, f.value
+
+    # ------------------------------------------------------------------ path
+    def deform(self, sid: int, ts, prec: int = FP32, out=None):
+        torch = self.torch
+        ts = np.ascontiguousarray(np.atleast_1d(ts), np.float32)
+        n = self._scenes[sid].means.shape[0]
+        dev = torch.device("cuda", self.device)
+        if out is None:
+            out = (torch.empty((len(ts), n, 3), device=dev), torch.empty((len(ts), n, 4), device=dev),
+                   torch.empty((len(ts), n, 3), device=dev))
+        self.call("fs4d_deform", sid, prec, ts.ctypes.data, len(ts), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+        return out
+
+    def render(self, sid: int, cam, t: float, prec: int = FP32, image=None, with_aux: bool = False):
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if image is None:
+            image = torch.empty((cam.height, cam.width, 3), device=dev)
+        T = nc = None
+        if with_aux:
+            T = torch.empty((cam.height, cam.width), device=dev)
+            nc = torch.empty((cam.height, cam.width), device=dev, dtype=torch.int32)
+        cs = camera_struct(cam)
+        self.call("fs4d_render", sid, prec, C.byref(cs), float(t), _ptr(image), _ptr(T), _ptr(nc), None)
+        return (image, T, nc) if with_aux else image
+
+    def render_host(self, sid: int, cam, t: float, prec: int = FP32, out: Optional[np.ndarray] = None):
+        if out is None:
+            out = np.empty((cam.height, cam.width, 3), np.float32)
+        cs = camera_struct(cam)
+        self.call("fs4d_render_host", sid, prec, C.byref(cs), float(t), out.ctypes.data)
+        return out
+
+    def reserve(self, sid: int, width: int, height: int, pair_capacity: int) -> None:
+        self.call("fs4d_reserve", sid, width, height, int(pair_capacity))
+
+    def render_async(self, sid: int, shape_cam, d_cam, d_t, image, prec: int = FP32) -> None:
+        cs = camera_struct(shape_cam)
+        self.call("fs4d_render_async", sid, prec, C.byref(cs), _ptr(d_cam), _ptr(d_t), _ptr(image))
+
+    def set_stage_timing(self, on: bool) -> None:
+        self.call("fs4d_set_stage_timing", int(bool(on)))
+
+    def stage_times(self) -> Dict[str, float]:
+        ms = (C.c_float * 6)()
+        self.call("fs4d_stage_times", ms)
+        return dict(zip(STAGES, [float(v) for v in ms]))
+
+    def last_pairs(self) -> int:
+        k = C.c_int64()
+        self.call("fs4d_last_pairs", C.byref(k))
+        return k.value
+
+    # ------------------------------------------------------------------ stages
+    def project(self, means, quats, log_scales, opacity_logits, sh, sh_degree: int, cam):
+        torch = self.torch
+        n = means.shape[0]
+        dev = means.device
+        out = dict(xy=torch.empty((n, 2), device=dev), conic_opacity=torch.empty((n, 4), device=dev),
+                   rgb=torch.empty((n, 3), device=dev), depth=torch.empty(n, device=dev),
+                   radius=torch.empty(n, device=dev, dtype=torch.int32),
+                   rect=torch.empty((n, 4), device=dev, dtype=torch.int32))
+        p = Projected(**{k: _ptr(v) for k, v in out.items()})
+        cs = camera_struct(cam)
+        self.call("fs4d_project", n, _ptr(means), _ptr(quats), _ptr(log_scales), _ptr(opacity_logits), _ptr(sh),
+                  int(sh_degree), C.byref(cs), C.byref(p))
+        return out
+
+    def bin_sort(self, depth, rect, tiles_x: int, tiles_y: int, capacity: int):
+        torch = self.torch
+        dev = depth.device
+        keys = torch.empty(max(capacity, 1), device=dev, dtype=torch.int64)
+        vals = torch.empty(max(capacity, 1), device=dev, dtype=torch.int32)
+        ranges = torch.empty((tiles_x * tiles_y, 2), device=dev, dtype=torch.int32)
+        K = C.c_int64()
+        self.call("fs4d_bin_sort", depth.shape[0], _ptr(depth), _ptr(rect), tiles_x, tiles_y, int(capacity),
+                  _ptr(keys), _ptr(vals), _ptr(ranges), C.byref(K))
+        return keys[:K.value], vals[:K.value], ranges, K.value
+
+    def sort_pairs(self, keys, values, key_bits: int) -> None:
+        self.call("fs4d_sort_pairs", keys.shape[0], int(key_bits), _ptr(keys), _ptr(values))
+
+    def composite(self, width: int, height: int, ranges, values, xy, conic_opacity, rgb):
+        torch = self.torch
+        dev = xy.device
+        img = torch.empty((height, width, 3), device=dev)
+        T = torch.empty((height, width), device=dev)
+        nc = torch.empty((height, width), device=dev, dtype=torch.int32)
+        self.call("fs4d_composite", width, height, _ptr(ranges), _ptr(values), _ptr(xy), _ptr(conic_opacity),
+                  _ptr(rgb), _ptr(img), _ptr(T), _ptr(nc))
+        return img, T, nc

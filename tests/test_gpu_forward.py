@@ -1,0 +1,333 @@
+"""GPU parity of the forward render path against the FP64 oracle, through the C ABI.
+
+Tolerances (float32 path): deformed Gaussians within 1e-5 absolute; projection
+outputs within 1e-5 relative; tile keys, sorted values and ranges bit-exact on
+identical inputs; images within 1e-4 max-abs per channel, except pixels where
+the oracle records a threshold decision (alpha vs 1/255, T vs 1e-4, a depth tie)
+within float32 rounding of its boundary, which are counted and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_08528_gb300 import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_08528_gb300 import fs4d  # noqa: E402
+
+IMG_TOL = 1e-4
+MARGIN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fs4d.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fs4d.library()
+    for name in fs4d.EXPORTS:
+        assert hasattr(lib, name), name
+
+
+# ------------------------------------------------------------------ deformation (Eq. 5, Eq. 6)
+
+def deform_tol(s, X, Q, S):
+    """float32 tolerance of the deformed outputs: four chained length-64 dot
+    products accumulate ~4 * 64 * 2^-24 ~ 1.5e-5 of the output scale; the bound
+    is 2e-5 of max(1, max |delta|)."""
+    d = max(1.0, float(np.abs(X - s.means).max()), float(np.abs(Q - s.quats).max()),
+            float(np.abs(S - s.log_scales).max()))
+    return 2e-5 * d
+
+
+def _check_deform(s, m, q, ls, X, Q, S):
+    tol = deform_tol(s, X, Q, S)
+    assert np.abs(m.cpu().numpy() - X).max() <= tol
+    assert np.abs(q.cpu().numpy() - Q).max() <= tol
+    assert np.abs(ls.cpu().numpy() - S).max() <= tol
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: sg.make_tiny(0, mlp_std=0.3),
+    lambda: sg.make_tiny(1, n=4099, mlp_std=0.3, bias_std=0.05),
+    lambda: sg.make_object(2, n=5000, mlp_std=0.15),
+    lambda: sg.make_object(3, n=3001, res_spatial=(16, 32, 64), res_time=9, mlp_std=0.15),
+])
+def test_deform_fp32_matches_oracle(ctx, maker):
+    s = maker()
+    sid = ctx.load_scene(s)
+    ts = [0.0, 0.37, 1.0]
+    m, q, ls = ctx.deform(sid, ts, fs4d.FP32)
+    torch.cuda.synchronize()
+    for i, t in enumerate(ts):
+        X, Q, S = oracle.deform(s, t)
+        assert np.abs(X - s.means).max() > 1e-4  # the deformation is really non-trivial
+        _check_deform(s, m[i], q[i], ls[i], X, Q, S)
+    ctx.unload_scene(sid)
+
+
+def test_deform_outside_box_clamps(ctx):
+    s = sg.make_tiny(4, n=300, mlp_std=0.3)
+    s.means[:100] *= 1.7  # outside [-1,1]^3: border clamping
+    sid = ctx.load_scene(s)
+    m, q, ls = ctx.deform(sid, [0.5, -0.2, 1.3], fs4d.FP32)
+    for i, t in enumerate([0.5, -0.2, 1.3]):
+        X, Q, S = oracle.deform(s, t)
+        _check_deform(s, m[i], q[i], ls[i], X, Q, S)
+    ctx.unload_scene(sid)
+
+
+# ------------------------------------------------------------------ projection (Eq. 2, Eq. 3)
+
+@pytest.mark.parametrize("deg,seed", [(0, 0), (3, 1)])
+def test_project_matches_oracle(ctx, deg, seed):
+    if deg == 0:
+        s = sg.make_tiny(seed)
+        cam = sg.tiny_camera()
+    else:
+        s = sg.make_object(seed, n=20000, res_spatial=(8,), res_time=4, h=16)
+        cam = sg.hemisphere_cameras(3, width=800, height=800, seed=seed)[1]
+    p = ctx.project(dev(s.means), dev(s.quats), dev(s.log_scales), dev(s.opacity_logits), dev(s.sh), s.sh_degree,
+                    cam)
+    torch.cuda.synchronize()
+    o = oracle.project(s, cam)
+    vis = o["radius"] > 0
+    # a rect/radius decision within 1e-4 px of its integer boundary may round
+    # either way in float32; such Gaussians are ~2.5e-4 of a uniform scene
+    safe = o["margin"] > 1e-4
+    gr = p["radius"].cpu().numpy()
+    grect = p["rect"].cpu().numpy()
+    assert vis.sum() > 0.5 * s.n
+    assert np.array_equal(gr[safe], o["radius"][safe])
+    assert np.array_equal(grect[safe], o["rect"][safe])
+    assert (~safe).mean() <= 2e-3
+    both = vis & (gr > 0)
+    rel = lambda a, b: np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+    assert rel(p["xy"].cpu().numpy()[both], o["xy"][both]).max() <= 1e-5
+    co = p["conic_opacity"].cpu().numpy()
+    scale = np.abs(o["conic"][both]).max(1, keepdims=True)
+    assert (np.abs(co[both, :3] - o["conic"][both]) / scale).max() <= 1e-5
+    assert np.abs(co[:, 3] - o["opacity"]).max() <= 1e-6
+    assert rel(p["depth"].cpu().numpy(), o["depth"]).max() <= 1e-6
+    assert np.abs(p["rgb"].cpu().numpy()[both] - o["rgb"][both]).max() <= 1e-5
+
+
+# ------------------------------------------------------------------ binning + sort + ranges (bit-exact)
+
+def _random_bins(rng, n, tx, ty, max_w=4, tie_every=17):
+    depth = rng.uniform(0.3, 20.0, n).astype(np.float32)
+    if n > 5 and tie_every:
+        depth[::tie_every] = depth[5]
+    x0 = rng.integers(0, tx, n)
+    y0 = rng.integers(0, ty, n)
+    rect = np.stack([x0, y0, np.minimum(tx, x0 + rng.integers(0, max_w + 1, n)),
+                     np.minimum(ty, y0 + rng.integers(0, max_w + 1, n))], 1).astype(np.int32)
+    return depth, rect
+
+
+@pytest.mark.parametrize("n,tx,ty", [(1, 1, 1), (7, 3, 2), (2047, 8, 8), (2049, 50, 50), (40000, 50, 50),
+                                     (150001, 240, 135)])
+def test_bin_sort_bit_exact(ctx, n, tx, ty):
+    rng = np.random.default_rng(n)
+    depth, rect = _random_bins(rng, n, tx, ty)
+    keys_o, vals_o, ranges_o = oracle.bin_sort(depth.view(np.uint32), rect, tx, ty)
+    K = len(keys_o)
+    keys, vals, ranges, Kg = ctx.bin_sort(dev(depth), dev(rect), tx, ty, K + 100)
+    torch.cuda.synchronize()
+    assert Kg == K
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_o)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_o)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
+
+
+def test_bin_sort_empty_and_capacity(ctx):
+    depth = np.ones(10, np.float32)
+    rect = np.zeros((10, 4), np.int32)  # every Gaussian culled
+    keys, vals, ranges, K = ctx.bin_sort(dev(depth), dev(rect), 4, 4, 16)
+    assert K == 0 and int(ranges.abs().sum()) == 0
+    rect[:, 2:] = 4  # 16 tiles each -> 160 pairs
+    with pytest.raises(fs4d.Fs4dError) as e:
+        ctx.bin_sort(dev(depth), dev(rect), 4, 4, 100)
+    assert e.value.status == 3
+
+
+@pytest.mark.parametrize("n,bits", [(1, 8), (4095, 12), (4097, 33), (100000, 44), (262145, 64), (30000, 1)])
+def test_sort_pairs_matches_stable_numpy(ctx, n, bits):
+    rng = np.random.default_rng(bits)
+    keys = rng.integers(0, 2 ** 63, n, dtype=np.uint64) | (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
+    if bits < 64:
+        keys &= np.uint64((1 << bits) - 1)
+    keys[::5] = keys[min(1, n - 1)]  # ties keep input order
+    vals = np.arange(n, dtype=np.uint32)
+    tk = dev(keys.view(np.int64))
+    tv = dev(vals.view(np.int32))
+    ctx.sort_pairs(tk, tv, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(tk.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(tv.cpu().numpy().view(np.uint32), vals[order])
+
+
+# ------------------------------------------------------------------ compositing (Eq. 4)
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_composite_matches_oracle_on_same_inputs(ctx, seed):
+    s = sg.make_tiny(seed)
+    cam = sg.tiny_camera(144, 120)  # ragged: 9 x 8 tiles, last row partial
+    o = oracle.project(s, cam)
+    # the float32 values the kernel sees are also the oracle's inputs
+    p32 = {k: (v.astype(np.float32).astype(np.float64) if v.dtype == np.float64 else v) for k, v in o.items()}
+    _, vals, ranges = oracle.bin_sort(oracle.depth_bits(p32["depth"]), o["rect"], 9, 8)
+    img_o, T_o, nc_o, mg = oracle.composite(144, 120, ranges, vals, p32)
+    co = np.concatenate([p32["conic"], p32["opacity"][:, None]], 1)
+    img, T, nc = ctx.composite(144, 120, dev(ranges.view(np.int32)), dev(vals.view(np.int32)),
+                               dev(p32["xy"].astype(np.float32)), dev(co.astype(np.float32)),
+                               dev(p32["rgb"].astype(np.float32)))
+    torch.cuda.synchronize()
+    ok = mg >= MARGIN
+    assert ok.mean() > 0.99
+    assert np.abs(img.cpu().numpy() - img_o)[ok].max() <= 1e-5
+    assert np.abs(T.cpu().numpy() - T_o)[ok].max() <= 1e-5
+    assert np.array_equal(nc.cpu().numpy()[ok], nc_o[ok])
+
+
+# ------------------------------------------------------------------ full frame
+
+def _frame_check(img, want, unstable, tol=IMG_TOL, max_flagged=0.08):
+    ok = ~unstable
+    assert (1 - ok.mean()) <= max_flagged
+    err = np.abs(img - want)[ok]
+    assert err.max() <= tol, err.max()
+    return err.max()
+
+
+@pytest.mark.parametrize("seed,std", [(0, 0.1), (1, 0.1), (2, 0.05), (3, 0.02)])
+def test_render_fp32_tiny_matches_oracle(ctx, seed, std):
+    s = sg.make_tiny(seed, mlp_std=std)
+    cam = sg.tiny_camera()
+    sid = ctx.load_scene(s)
+    img, T, nc = ctx.render(sid, cam, 0.5, fs4d.FP32, with_aux=True)
+    torch.cuda.synchronize()
+    unstable, want, T_o, nc_o, K = oracle.unstable_pixels(s, cam, 0.5)
+    _frame_check(img.cpu().numpy(), want, unstable)
+    ok = ~unstable
+    assert np.abs(T.cpu().numpy() - T_o)[ok].max() <= IMG_TOL
+    assert np.array_equal(nc.cpu().numpy()[ok], nc_o[ok])
+    ctx.unload_scene(sid)
+
+
+def test_render_static_special_case(ctx):
+    """Zero head output layers: dG = 0 and the frame is the static 3D-GS render."""
+    s = sg.make_tiny(3, mlp_std=0.1)
+    shapes = sg.mlp_layer_shapes(16, 64)
+    off = 0
+    for k, (o, i) in enumerate(shapes):
+        if k in (3, 5, 7):
+            s.mlp[off:off + o * i + o] = 0.0
+        off += o * i + o
+    cam = sg.tiny_camera()
+    sid = ctx.load_scene(s)
+    img = ctx.render(sid, cam, 0.9, fs4d.FP32).cpu().numpy()
+    unstable, want, _, _, _ = oracle.unstable_pixels(s, cam, 0.9, deform=False)
+    _frame_check(img, want, unstable)
+    ctx.unload_scene(sid)
+
+
+def test_render_object_800_matches_oracle(ctx):
+    """The 100k-Gaussian 800x800 object frame, every pixel against the oracle."""
+    s = sg.make_object(0)
+    cam = sg.hemisphere_cameras(50, seed=0)[7]
+    sid = ctx.load_scene(s)
+    img = ctx.render(sid, cam, 0.35, fs4d.FP32).cpu().numpy()
+    oracle.set_threads(oracle.default_threads())
+    # at 800 px one float32 ulp of a pixel coordinate is 6e-5 px, which moves
+    # alpha by up to ~|grad power| * 6e-5 ~ 3e-5 relative: blend decisions within
+    # 5e-5 of their threshold are resolution-limited, not errors
+    unstable, want, _, _, K = oracle.unstable_pixels(s, cam, 0.35, px_tol=2e-4, margin_tol=5e-5)
+    assert abs(ctx.last_pairs() - K) <= 1e-4 * K
+    _frame_check(img, want, unstable)
+    ctx.unload_scene(sid)
+
+
+def test_render_host_equals_device(ctx):
+    s = sg.make_tiny(5, mlp_std=0.3)
+    cam = sg.tiny_camera(200, 150)
+    sid = ctx.load_scene(s)
+    a = ctx.render(sid, cam, 0.2).cpu().numpy()
+    b = ctx.render_host(sid, cam, 0.2)
+    assert np.array_equal(a, b)
+    ctx.unload_scene(sid)
+
+
+def test_render_async_and_graph_replay_equal_sync(ctx):
+    s = sg.make_tiny(6, mlp_std=0.3)
+    cams = [sg.tiny_camera(), sg.hemisphere_cameras(4, width=128, height=128, seed=3)[2]]
+    sid = ctx.load_scene(s)
+    ctx.reserve(sid, 128, 128, 200000)
+    d_cam = torch.empty(23, dtype=torch.float32, device="cuda")
+    d_t = torch.empty(1, dtype=torch.float32, device="cuda")
+    out = torch.empty((128, 128, 3), device="cuda")
+
+    def set_view(cam, t):
+        cs = fs4d.camera_struct(cam)
+        raw = np.frombuffer(bytes(cs), dtype=np.float32).copy()
+        d_cam.copy_(torch.from_numpy(raw))
+        d_t.fill_(t)
+
+    set_view(cams[0], 0.4)
+    ctx.render_async(sid, cams[0], d_cam, d_t, out)
+    ref = ctx.render(sid, cams[0], 0.4)
+    assert torch.equal(out, ref)
+    # capture once, replay for another view
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        ctx.render_async(sid, cams[0], d_cam, d_t, out)  # warm-up outside capture
+        stream.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            ctx.render_async(sid, cams[0], d_cam, d_t, out)
+    ctx.set_stream(torch.cuda.current_stream())
+    set_view(cams[1], 0.8)
+    g.replay()
+    torch.cuda.synchronize()
+    ref = ctx.render(sid, cams[1], 0.8)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    ctx.check_device_status()
+    ctx.unload_scene(sid)
+
+
+def test_capacity_overflow_sets_status_not_fault(ctx):
+    s = sg.make_tiny(7)
+    cam = sg.tiny_camera()
+    sid = ctx.load_scene(s)
+    ctx.reserve(sid, 128, 128, 4096)
+    K = oracle.render(s, cam, 0.5)[4]
+    assert K > 4096
+    ctx._scenes[sid] = s
+    d_cam = torch.from_numpy(np.frombuffer(bytes(fs4d.camera_struct(cam)), dtype=np.float32).copy()).cuda()
+    d_t = torch.full((1,), 0.5, device="cuda")
+    out = torch.zeros((128, 128, 3), device="cuda")
+    # shrink the reservation to below K: the frame must report, not fault
+    ctx.call("fs4d_reserve", sid, 128, 128, 1000)
+    ctx.render_async(sid, cam, d_cam, d_t, out)
+    with pytest.raises(fs4d.Fs4dError) as e:
+        ctx.check_device_status()
+    assert e.value.status == 3
+    ctx.check_device_status()  # cleared
+    ctx.unload_scene(sid)
