@@ -224,6 +224,30 @@ FS4D_API fs4d_status fs4d_bin_sort(fs4d_ctx* ctx, int32_t n, const float* d_dept
  * Uses context-owned work memory. */
 FS4D_API fs4d_status fs4d_sort_pairs(fs4d_ctx* ctx, int64_t n, int32_t key_bits, uint64_t* d_keys, uint32_t* d_values);
 
+/* Allocation-free radix sort (no counterpart in the paper; an integration aid).
+ * Some callers must not have this library allocate device memory: a host
+ * application that owns the whole device-memory budget and hands out every
+ * buffer itself, or a latency-critical loop in which cudaMalloc/cudaFree (which
+ * can synchronise the whole device) are not allowed.  Such a caller can sort
+ * with this call: it needs no context and allocates nothing.  It sorts like
+ * fs4d_sort_pairs (stable, low key_bits bits, in place in d_keys/d_values [n])
+ * on the given stream (a cudaStream_t of the CURRENT device; NULL = legacy
+ * default stream), using a fixed work area of about 14.7 MB that the library
+ * keeps in device memory of every GPU that loads it, until the process exits.
+ *  - n may be at most FS4D_NOALLOC_MAX_PAIRS; a larger n returns
+ *    FS4D_ERR_CAPACITY and launches nothing.  Other bad arguments return
+ *    FS4D_ERR_INVALID_ARG, a failed CUDA call FS4D_ERR_CUDA.
+ *  - The first call on each device performs a one-time set-up (it looks up the
+ *    device address of the work area); make that first call before any stream
+ *    capture begins.
+ *  - All calls on a device share the one work area (it keeps the last call's
+ *    contents; every call clears what must start at zero).  Calls whose work
+ *    overlaps on the GPU race with each other: serialise them (one stream, or
+ *    events between streams). */
+#define FS4D_NOALLOC_MAX_PAIRS (1 << 20)
+FS4D_API fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int32_t key_bits, uint64_t* d_keys,
+                                             uint32_t* d_values);
+
 /* Eq. 4 per 16x16 tile over the sorted lists: d_ranges [tiles][2], d_values [K]
  * Gaussian indices, per-Gaussian d_xy [n][2], d_conic_opacity [n][4], d_rgb [n][3].
  * Writes d_image [height][width][3] and, when non-NULL, d_t_final and

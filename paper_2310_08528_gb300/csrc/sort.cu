@@ -251,3 +251,75 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
 }
 
 }  // namespace fs4d
+
+// ---------------------------------------------------------------- allocation-free variant
+// fs4d_sort_pairs_noalloc runs the same sort with every scratch buffer (the
+// alternate key/value buffers, the digit histograms, the partition tickets, the
+// look-back table and the status word) carved out of one file-scope device
+// array, so the call itself never allocates.
+#include <mutex>
+
+namespace fs4d {
+namespace {
+
+constexpr long long kNaMaxPairs = FS4D_NOALLOC_MAX_PAIRS;
+constexpr long long kNaParts = (kNaMaxPairs + kPartPairs - 1) / kPartPairs;
+constexpr size_t kNaKeys = 0;
+constexpr size_t kNaValues = kNaKeys + 8 * (size_t)kNaMaxPairs;
+constexpr size_t kNaHist = kNaValues + 4 * (size_t)kNaMaxPairs;
+constexpr size_t kNaCounters = kNaHist + 4 * (size_t)kMaxPasses * kRadix;
+constexpr size_t kNaStatus = kNaCounters + 4 * (size_t)kMaxPasses;
+constexpr size_t kNaLookback = (kNaStatus + 4 + 255) / 256 * 256;
+constexpr size_t kNaBytes = kNaLookback + 4 * (size_t)kMaxPasses * kNaParts * kRadix;
+constexpr int kNaMaxDevices = 64;
+
+// The work area itself.  In host code this name is only a stand-in: its device
+// address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_sort_scratch[kNaBytes];
+
+std::mutex g_na_mutex;
+unsigned char* g_na_base[kNaMaxDevices] = {};
+
+}  // namespace
+}  // namespace fs4d
+
+extern "C" fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int32_t key_bits, uint64_t* d_keys,
+                                               uint32_t* d_values) {
+  using namespace fs4d;
+  if (n < 0 || key_bits < 1 || key_bits > 64 || (n > 0 && (!d_keys || !d_values))) return FS4D_ERR_INVALID_ARG;
+  if (n > kNaMaxPairs) return FS4D_ERR_CAPACITY;
+  if (n == 0) return FS4D_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return FS4D_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return FS4D_ERR_CUDA;
+      g_na_base[dev] = static_cast<unsigned char*>(p);
+    }
+    base = g_na_base[dev];
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  uint32_t* status = reinterpret_cast<uint32_t*>(base + kNaStatus);
+  if (cudaMemsetAsync(status, 0, 4, s) != cudaSuccess) return FS4D_ERR_CUDA;
+  SortWork w;
+  w.hist = reinterpret_cast<uint32_t*>(base + kNaHist);
+  w.lookback = reinterpret_cast<uint32_t*>(base + kNaLookback);
+  w.part_counters = reinterpret_cast<uint32_t*>(base + kNaCounters);
+  w.max_parts = kNaParts;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(d_keys);
+  unsigned long long* keys_alt = reinterpret_cast<unsigned long long*>(base + kNaKeys);
+  uint32_t* values_alt = reinterpret_cast<uint32_t*>(base + kNaValues);
+  bool alt = false;
+  if (launch_sort(keys, d_values, keys_alt, values_alt, nullptr, n, key_bits, false, w, status, s, &alt) !=
+      cudaSuccess)
+    return FS4D_ERR_CUDA;
+  if (alt) {
+    if (cudaMemcpyAsync(d_keys, keys_alt, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_values, values_alt, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return FS4D_ERR_CUDA;
+  }
+  return FS4D_OK;
+}

@@ -24,7 +24,7 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_load_scene", "fs4d_unload_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
            "fs4d_render_host", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
-           "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_composite")
+           "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_composite")
 STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
 
 
@@ -95,6 +95,8 @@ def library(path: str = LIB_PATH):
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = C.c_int
+    L.fs4d_sort_pairs_noalloc.argtypes = [vp, i64, i32, vp, vp]
+    L.fs4d_sort_pairs_noalloc.restype = C.c_int
     L.fs4d_last_error.argtypes = [vp]
     L.fs4d_last_error.restype = C.c_char_p
     _lib = L
