@@ -1,19 +1,397 @@
-// Gaussian deformation field, BF16 tensor-core path (placeholder until the
-// tcgen05 kernel lands).
+// Gaussian deformation field, BF16 tensor-core path (Sec. 4.2, Eq. 5, Eq. 6).
+//
+// Persistent CTAs of 256 threads, each owning 256 TMEM columns, walk tiles of
+// 128 (timestamp, Gaussian) rows:
+//   1. sampling: 256 threads take (row, level) items; each interpolates the six
+//      BF16 planes of its level bilinearly in FP32, multiplies them (Eq. 5) and
+//      stores its h features as BF16 straight into the A operand tile in shared
+//      memory (UMMA canonical no-swizzle K-major layout);
+//   2. four GEMMs on tcgen05 (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128):
+//        D1 = A1 . W_d1^T  (N 64)            f_h  -> hidden
+//        D2 = A2 . W_d2^T  (N 64)            hidden -> f_d
+//        D3 = A3 . [W_x1; W_r1; W_s1]^T (N 192)  three head hidden layers at once
+//        D4 = A4 . blockdiag(W_x2, W_r2, W_s2)^T (N 16, 10 used)
+//      one elected thread issues each GEMM and commits it to an mbarrier;
+//   3. between GEMMs, 8 warps read the accumulator back with tcgen05.ld, add the
+//      bias, apply ReLU, round to BF16 and write the next A tile;
+//   4. the last epilogue adds dX, dr, ds to X, r, s (Eq. 6).
+// Every wait on the mbarrier is bounded; on a timeout the CTA records
+// kStatusTimeout, stops, frees its TMEM and returns.
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
+namespace {
 
-bool deform_bf16_supported(int feat_dim, int n_levels) {
-  (void)feat_dim;
-  (void)n_levels;
+constexpr int kThreads = 256;
+constexpr int kRows = 128;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kWaitLimit = 1u << 20;
+constexpr int kXBytes = 48 * 1024;  // activation tiles (A1+A2, then A3, then A4)
+constexpr int kBiasFloats = 336;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, LBO = byte
+// distance between core matrices along K, SBO = along M/N, version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
   return false;
 }
 
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 32 columns of FP32 (this warp's lane quarter), waited on in the same asm.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (r, k) in a K-major no-swizzle operand with K columns:
+// 8x8 core matrices of 128 contiguous bytes, (r/8, k/8) at ((r/8)*(K/8) + k/8)*128.
+__device__ __forceinline__ uint32_t a_off(int r, int k, int K) {
+  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// relu(v + bias) of 32 columns -> BF16 row segment k0..k0+31 of an operand with K columns.
+__device__ __forceinline__ void store_relu32(uint8_t* tile, int r, int k0, int K, const float (&v)[32],
+                                             const float* bias) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 q;
+    q.x = pack_bf16(fmaxf(v[8 * j + 0] + bias[8 * j + 0], 0.f), fmaxf(v[8 * j + 1] + bias[8 * j + 1], 0.f));
+    q.y = pack_bf16(fmaxf(v[8 * j + 2] + bias[8 * j + 2], 0.f), fmaxf(v[8 * j + 3] + bias[8 * j + 3], 0.f));
+    q.z = pack_bf16(fmaxf(v[8 * j + 4] + bias[8 * j + 4], 0.f), fmaxf(v[8 * j + 5] + bias[8 * j + 5], 0.f));
+    q.w = pack_bf16(fmaxf(v[8 * j + 6] + bias[8 * j + 6], 0.f), fmaxf(v[8 * j + 7] + bias[8 * j + 7], 0.f));
+    *reinterpret_cast<uint4*>(tile + a_off(r, k0 + 8 * j, K)) = q;
+  }
+}
+
+// One GEMM of K columns into TMEM column `col`: K/16 MMAs, then a commit.
+__device__ __forceinline__ void issue_gemm(uint32_t tmem, int col, uint32_t a_addr, uint32_t b_addr, int K, int N,
+                                           uint32_t mbar) {
+  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+  const uint32_t id = idesc_bf16(kRows, N);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t da = smem_desc(a_addr + 256u * kk, 128u, sbo);
+    const uint64_t db = smem_desc(b_addr + 256u * kk, 128u, sbo);
+    mma(tmem + (uint32_t)col, da, db, id, kk > 0 ? 1u : 0u);
+  }
+  mma_commit(mbar);
+}
+
+__device__ __forceinline__ void axis_setup(float u, int R, int& i0, float& f) {
+  const float uc = fminf(1.f, fmaxf(-1.f, u));
+  const float g = (uc + 1.f) * 0.5f * (float)(R - 1);
+  int i = (int)floorf(g);
+  i = max(0, min(i, R - 2));
+  i0 = i;
+  f = g - (float)i;
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <int H, int L>
+__global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
+  constexpr int HL = H * L;
+  constexpr int kA2 = ((kRows * HL * 2) + 1023) / 1024 * 1024;  // A2 follows A1 inside X
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const MlpGeomTC& tg = a.tg;
+  const int b_bytes = (tg.bytes + 1023) / 1024 * 1024;
+  uint8_t* sB = smem;
+  uint8_t* sX = smem + b_bytes;
+  float* sBias = reinterpret_cast<float*>(sX + kXBytes);
+  uint64_t* sMbar = reinterpret_cast<uint64_t*>(sBias + kBiasFloats);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(sMbar + 1);
+  uint32_t* sFail = sTmem + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < tg.bytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(a.tc_ops)[i];
+  for (int i = tid; i < kBiasFloats; i += kThreads) sBias[i] = a.tc_bias[i];
+  const uint32_t mbar = smem_u32(sMbar);
+  if (tid == 0) {
+    mbar_init(mbar);
+    *sFail = 0;
+  }
+  if (warp == 0) tmem_alloc(smem_u32(sTmem), kTmemCols);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t b_addr = smem_u32(sB), x_addr = smem_u32(sX);
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const int row = (warp & 3) * 32 + lane;   // accumulator row this thread reads back
+  const int half = warp >> 2;               // which column half it handles
+  uint32_t phase = 0;
+  const PlaneGeom& pg = a.pg;
+  const long long total = (long long)a.n * a.n_t;
+  const long long tiles = (total + kRows - 1) / kRows;
+
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long base = tile * kRows;
+    // ---- 1. HexPlane features (Eq. 5) -> A1 [128 x HL] BF16
+    for (int item = tid; item < kRows * L; item += kThreads) {
+      const int r = item % kRows, l = item / kRows;
+      const long long gi = base + r;
+      float f[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) f[k] = 0.f;
+      if (gi < total) {
+        const int ti = (int)(gi / a.n);
+        const int g = (int)(gi - (long long)ti * a.n);
+        const float t = a.ts ? a.ts[ti] : a.t0;
+        float c[4];
+        c[0] = (a.means[3 * g] - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
+        c[1] = (a.means[3 * g + 1] - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f;
+        c[2] = (a.means[3 * g + 2] - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
+        c[3] = 2.f * t - 1.f;
+#pragma unroll
+        for (int k = 0; k < H; ++k) f[k] = 1.f;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);  // xy xz yz xt yt zt
+          const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+          const int Ra = ax < 3 ? pg.res[l] : pg.res_time;
+          const int Rb = bx < 3 ? pg.res[l] : pg.res_time;
+          int i0, j0;
+          float fa, fb;
+          axis_setup(c[ax], Ra, i0, fa);
+          axis_setup(c[bx], Rb, j0, fb);
+          const uint4* v00 = reinterpret_cast<const uint4*>(a.planes_bf16 + pg.off[l][p] + ((long long)j0 * Ra + i0) * H);
+          const uint4* v10 = v00 + H / 8;
+          const uint4* v01 = v00 + (long long)Ra * (H / 8);
+          const uint4* v11 = v01 + H / 8;
+          const float w00 = (1.f - fa) * (1.f - fb), w10 = fa * (1.f - fb), w01 = (1.f - fa) * fb, w11 = fa * fb;
+#pragma unroll
+          for (int q = 0; q < H / 8; ++q) {
+            const uint4 A = __ldg(v00 + q), B = __ldg(v10 + q), C = __ldg(v01 + q), D = __ldg(v11 + q);
+            const uint32_t wa[4] = {A.x, A.y, A.z, A.w}, wb[4] = {B.x, B.y, B.z, B.w},
+                           wc[4] = {C.x, C.y, C.z, C.w}, wd[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              f[8 * q + 2 * e] *= w00 * bf_lo(wa[e]) + w10 * bf_lo(wb[e]) + w01 * bf_lo(wc[e]) + w11 * bf_lo(wd[e]);
+              f[8 * q + 2 * e + 1] *=
+                  w00 * bf_hi(wa[e]) + w10 * bf_hi(wb[e]) + w01 * bf_hi(wc[e]) + w11 * bf_hi(wd[e]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < H / 8; ++q) {
+        uint4 v;
+        v.x = pack_bf16(f[8 * q + 0], f[8 * q + 1]);
+        v.y = pack_bf16(f[8 * q + 2], f[8 * q + 3]);
+        v.z = pack_bf16(f[8 * q + 4], f[8 * q + 5]);
+        v.w = pack_bf16(f[8 * q + 6], f[8 * q + 7]);
+        *reinterpret_cast<uint4*>(sX + a_off(r, l * H + 8 * q, HL)) = v;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    // ---- 2. phi_d layer 1: D1 (cols 0..63) = A1 . W_d1^T
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm(tmem, 0, x_addr, b_addr + tg.b1_off, HL, 64, mbar);
+    }
+    if (!mbar_wait(mbar, phase)) *sFail = 1;
+    phase ^= 1;
+    tc_fence_after();
+    {
+      float v[32];
+      tmem_ld32(tmem + lane_base + (uint32_t)(half * 32), v);
+      store_relu32(sX + kA2, row, half * 32, 64, v, sBias + 0 + half * 32);
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+
+    // ---- phi_d layer 2: D2 (cols 64..127) = A2 . W_d2^T  -> f_d in A3 (X offset 0)
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm(tmem, 64, x_addr + kA2, b_addr + tg.b2_off, 64, 64, mbar);
+    }
+    if (!mbar_wait(mbar, phase)) *sFail = 1;
+    phase ^= 1;
+    tc_fence_after();
+    {
+      float v[32];
+      tmem_ld32(tmem + lane_base + 64u + (uint32_t)(half * 32), v);
+      store_relu32(sX, row, half * 32, 64, v, sBias + 64 + half * 32);
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+
+    // ---- heads, hidden layers: D3 (cols 0..191) = A3 . [W_x1; W_r1; W_s1]^T -> A4 [128 x 192]
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm(tmem, 0, x_addr, b_addr + tg.b3_off, 64, 192, mbar);
+    }
+    if (!mbar_wait(mbar, phase)) *sFail = 1;
+    phase ^= 1;
+    tc_fence_after();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float v[32];
+      const int c0 = half * 96 + 32 * j;
+      tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+      store_relu32(sX, row, c0, 192, v, sBias + 128 + c0);
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+
+    // ---- heads, output layers: D4 (cols 192..207) = A4 . blockdiag(W_x2, W_r2, W_s2)^T
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm(tmem, 192, x_addr, b_addr + tg.b4_off, 192, 16, mbar);
+    }
+    if (!mbar_wait(mbar, phase)) *sFail = 1;
+    phase ^= 1;
+    tc_fence_after();
+    if (warp < 4) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + 192u, v);
+      const long long gi = base + row;
+      if (gi < total) {
+        const int ti = (int)(gi / a.n);
+        const int g = (int)(gi - (long long)ti * a.n);
+        const float* bo = sBias + 320;
+        a.out_means[3 * gi + 0] = a.means[3 * g + 0] + (v[0] + bo[0]);
+        a.out_means[3 * gi + 1] = a.means[3 * g + 1] + (v[1] + bo[1]);
+        a.out_means[3 * gi + 2] = a.means[3 * g + 2] + (v[2] + bo[2]);
+        const float4 q = reinterpret_cast<const float4*>(a.quats)[g];
+        reinterpret_cast<float4*>(a.out_quats)[gi] =
+            make_float4(q.x + (v[3] + bo[3]), q.y + (v[4] + bo[4]), q.z + (v[5] + bo[5]), q.w + (v[6] + bo[6]));
+        a.out_log_scales[3 * gi + 0] = a.log_scales[3 * g + 0] + (v[7] + bo[7]);
+        a.out_log_scales[3 * gi + 1] = a.log_scales[3 * g + 1] + (v[8] + bo[8]);
+        a.out_log_scales[3 * gi + 2] = a.log_scales[3 * g + 2] + (v[9] + bo[9]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*sFail) break;  // uniform: read after the barrier
+  }
+  tc_fence_after();
+  if (*sFail && tid == 0) atomicOr(a.status, kStatusTimeout);
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int H, int L>
+cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(deform_tc_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long tiles = ((long long)a.n * a.n_t + kRows - 1) / kRows;
+  const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
+  deform_tc_kernel<H, L><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool deform_bf16_supported(int feat_dim, int n_levels) {
+  return (feat_dim == 16 || feat_dim == 32) && n_levels >= 1 && n_levels <= 3;
+}
+
 cudaError_t launch_deform_bf16(const DeformArgs& a, cudaStream_t s) {
-  (void)a;
-  (void)s;
-  return cudaErrorNotSupported;
+  if ((long long)a.n * a.n_t == 0) return cudaSuccess;
+  const int h = a.pg.feat_dim, L = a.pg.n_levels;
+  if (h == 16 && L == 1) return launch_t<16, 1>(a, s);
+  if (h == 16 && L == 2) return launch_t<16, 2>(a, s);
+  if (h == 16 && L == 3) return launch_t<16, 3>(a, s);
+  if (h == 32 && L == 1) return launch_t<32, 1>(a, s);
+  if (h == 32 && L == 2) return launch_t<32, 2>(a, s);
+  if (h == 32 && L == 3) return launch_t<32, 3>(a, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace fs4d

@@ -331,3 +331,66 @@ def test_capacity_overflow_sets_status_not_fault(ctx):
     assert e.value.status == 3
     ctx.check_device_status()  # cleared
     ctx.unload_scene(sid)
+
+
+# ------------------------------------------------------------------ BF16 tensor-core path
+
+def bf16_tol(s, X, Q, S):
+    """BF16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3).  Planes, every
+    layer input and every weight are rounded once: ~6 roundings into f_h and ~2
+    per layer over 4 layers, so the deltas carry a relative error of a few 1e-2
+    of their scale; the bound is 5e-2 of max |delta| (+1e-6)."""
+    d = max(float(np.abs(X - s.means).max()), float(np.abs(Q - s.quats).max()), float(np.abs(S - s.log_scales).max()))
+    return 5e-2 * d + 1e-6
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: sg.make_tiny(0, mlp_std=0.1),
+    lambda: sg.make_tiny(1, n=129, mlp_std=0.1, bias_std=0.05),
+    lambda: sg.make_object(2, n=5000, mlp_std=0.1),
+    lambda: sg.make_object(3, n=3001, res_spatial=(16, 32, 64), res_time=9, mlp_std=0.1),
+])
+def test_deform_bf16_matches_oracle(ctx, maker):
+    s = maker()
+    sid = ctx.load_scene(s)
+    ts = [0.0, 0.61]
+    m, q, ls = ctx.deform(sid, ts, fs4d.BF16)
+    torch.cuda.synchronize()
+    for i, t in enumerate(ts):
+        X, Q, S = oracle.deform(s, t)
+        tol = bf16_tol(s, X, Q, S)
+        errs = [np.abs(m[i].cpu().numpy() - X).max(), np.abs(q[i].cpu().numpy() - Q).max(),
+                np.abs(ls[i].cpu().numpy() - S).max()]
+        print(f"bf16 deform t={t}: max|dX|={errs[0]:.2e} max|dr|={errs[1]:.2e} max|ds|={errs[2]:.2e} tol={tol:.2e}")
+        assert max(errs) <= tol
+    ctx.unload_scene(sid)
+
+
+def psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def test_render_bf16_psnr_object_800(ctx):
+    """BF16 MLP/planes on tcgen05: image PSNR against the FP64 oracle >= 50 dB."""
+    s = sg.make_object(0)
+    sid = ctx.load_scene(s)
+    oracle.set_threads(oracle.default_threads())
+    for ci, t in ((7, 0.35), (31, 0.9)):
+        cam = sg.hemisphere_cameras(50, seed=0)[ci]
+        img = ctx.render(sid, cam, t, fs4d.BF16).cpu().numpy()
+        want, *_ = oracle.render(s, cam, t)
+        p = psnr(img, want)
+        print(f"bf16 frame cam {ci} t={t}: PSNR {p:.1f} dB, max abs {np.abs(img - want).max():.2e}")
+        assert p >= 50.0
+    ctx.unload_scene(sid)
+
+
+def test_render_bf16_tiny_psnr(ctx):
+    s = sg.make_tiny(2, mlp_std=0.1)
+    cam = sg.tiny_camera()
+    sid = ctx.load_scene(s)
+    img = ctx.render(sid, cam, 0.5, fs4d.BF16).cpu().numpy()
+    want, *_ = oracle.render(s, cam, 0.5)
+    assert psnr(img, want) >= 50.0
+    ctx.unload_scene(sid)
