@@ -481,8 +481,380 @@ int64_t orc_render(const orc_scene* s, const orc_camera* cam, double t, int32_t 
 
 }  // extern "C"
 
+// ============================================================================
+// Backward: the chain rule of every step above, in double precision, written
+// step by step in reverse order (training, Sec. 4.3).  The loss is
+// L = sum(dl_dimage * image); non-differentiable decisions (culling, tile
+// rectangles, the 1/255 skip, the transmittance stop, the 0.99 clamp, ReLU and
+// border clamps at their kinks) are held fixed.
+// ============================================================================
+namespace {
+
+// Derivative of the real SH basis with respect to the direction components
+// (x, y, z), differentiating each basis formula exactly as written above.
+void sh_basis_grad(int degree, const double d[3], double dY[16][3]) {
+  const double x = d[0], y = d[1], z = d[2];
+  const double PI = 3.14159265358979323846;
+  for (int k = 0; k < 16; ++k) dY[k][0] = dY[k][1] = dY[k][2] = 0.0;
+  if (degree < 1) return;
+  const double c1 = std::sqrt(3.0 / (4.0 * PI));
+  dY[1][1] = c1; dY[2][2] = c1; dY[3][0] = c1;
+  if (degree < 2) return;
+  const double a = 0.5 * std::sqrt(15.0 / PI), b = 0.25 * std::sqrt(5.0 / PI), dd = 0.25 * std::sqrt(15.0 / PI);
+  dY[4][0] = a * y; dY[4][1] = a * x;
+  dY[5][1] = a * z; dY[5][2] = a * y;
+  dY[6][2] = 6.0 * b * z;
+  dY[7][0] = a * z; dY[7][2] = a * x;
+  dY[8][0] = 2.0 * dd * x; dY[8][1] = -2.0 * dd * y;
+  if (degree < 3) return;
+  const double e = 0.25 * std::sqrt(35.0 / (2.0 * PI)), f = 0.5 * std::sqrt(105.0 / PI);
+  const double g = 0.25 * std::sqrt(21.0 / (2.0 * PI)), h = 0.25 * std::sqrt(7.0 / PI), m = 0.25 * std::sqrt(105.0 / PI);
+  dY[9][0] = 6.0 * e * x * y; dY[9][1] = e * (3.0 * x * x - 3.0 * y * y);
+  dY[10][0] = f * y * z; dY[10][1] = f * x * z; dY[10][2] = f * x * y;
+  dY[11][1] = g * (5.0 * z * z - 1.0); dY[11][2] = 10.0 * g * y * z;
+  dY[12][2] = h * (15.0 * z * z - 3.0);
+  dY[13][0] = g * (5.0 * z * z - 1.0); dY[13][2] = 10.0 * g * x * z;
+  dY[14][0] = 2.0 * m * x * z; dY[14][1] = -2.0 * m * y * z; dY[14][2] = m * (x * x - y * y);
+  dY[15][0] = e * (3.0 * x * x - 3.0 * y * y); dY[15][1] = -6.0 * e * x * y;
+}
+
+// d R(q) / d q for the rotation matrix of quat_to_rot, q = (w, x, y, z).
+void quat_rot_grad(const double q[4], double dR[4][3][3]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  const double Rw[3][3] = {{0, -2 * z, 2 * y}, {2 * z, 0, -2 * x}, {-2 * y, 2 * x, 0}};
+  const double Rx[3][3] = {{0, 2 * y, 2 * z}, {2 * y, -4 * x, -2 * w}, {2 * z, 2 * w, -4 * x}};
+  const double Ry[3][3] = {{-4 * y, 2 * x, 2 * w}, {2 * x, 0, 2 * z}, {-2 * w, 2 * z, -4 * y}};
+  const double Rz[3][3] = {{-4 * z, -2 * w, 2 * x}, {2 * w, -4 * z, 2 * y}, {2 * x, 2 * y, 0}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      dR[0][i][j] = Rw[i][j]; dR[1][i][j] = Rx[i][j]; dR[2][i][j] = Ry[i][j]; dR[3][i][j] = Rz[i][j];
+    }
+}
+
+}  // namespace
+
 extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,
-                                       int32_t tile, const double* dl_dimage, orc_grads* grads) {
-  (void)s; (void)cam; (void)t; (void)deform; (void)tile; (void)dl_dimage; (void)grads;
-  return 1;
+                                       int32_t tile, const double* dl_dimage, orc_grads* G) {
+  const int n = s->n, W = s->mlp_width, L = s->n_levels, h = s->feat_dim, hin = h * L;
+  const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
+  const MlpLayout Lo = mlp_layout(s);
+  // ---------------------------------------------------------------- forward, keeping what the backward needs
+  std::vector<double> X(3 * (int64_t)n), Q(4 * (int64_t)n), Sc(3 * (int64_t)n);
+  std::vector<double> fh((int64_t)n * hin, 0.0), a1((int64_t)n * W), fd((int64_t)n * W), hid((int64_t)n * 3 * W);
+  std::vector<double> xyz(3 * (int64_t)n);
+  for (int64_t i = 0; i < 3 * (int64_t)n; ++i) xyz[i] = s->means[i];
+  if (deform) {
+    orc_features(s, xyz.data(), n, t, fh.data());
+    for (int g = 0; g < n; ++g) {
+      double* A1 = &a1[(int64_t)g * W];
+      double* FD = &fd[(int64_t)g * W];
+      linear(s, Lo, 0, &fh[(int64_t)g * hin], A1);
+      for (int o = 0; o < W; ++o) A1[o] = relu(A1[o]);
+      linear(s, Lo, 1, A1, FD);
+      for (int o = 0; o < W; ++o) FD[o] = relu(FD[o]);
+      double out[4];
+      int col = 0;
+      for (int hd = 0; hd < 3; ++hd) {
+        double* HID = &hid[((int64_t)g * 3 + hd) * W];
+        linear(s, Lo, 2 + 2 * hd, FD, HID);
+        for (int o = 0; o < W; ++o) HID[o] = relu(HID[o]);
+        linear(s, Lo, 3 + 2 * hd, HID, out);
+        for (int o = 0; o < kHeadOut[hd]; ++o) {
+          double base = col + o < 3 ? s->means[3 * (int64_t)g + col + o]
+                        : col + o < 7 ? s->quats[4 * (int64_t)g + col + o - 3]
+                                      : s->log_scales[3 * (int64_t)g + col + o - 7];
+          double* dst = col + o < 3 ? &X[3 * (int64_t)g + col + o]
+                        : col + o < 7 ? &Q[4 * (int64_t)g + col + o - 3]
+                                      : &Sc[3 * (int64_t)g + col + o - 7];
+          *dst = base + out[o];
+        }
+        col += kHeadOut[hd];
+      }
+    }
+  } else {
+    for (int64_t i = 0; i < 3 * (int64_t)n; ++i) { X[i] = s->means[i]; Sc[i] = s->log_scales[i]; }
+    for (int64_t i = 0; i < 4 * (int64_t)n; ++i) Q[i] = s->quats[i];
+  }
+  std::vector<double> xy(2 * (int64_t)n, 0.0), conic(3 * (int64_t)n, 0.0), cov(3 * (int64_t)n, 0.0), op(n),
+      rgb(3 * (int64_t)n, 0.0), depth(n), mg(n);
+  std::vector<int32_t> radius(n), rect(4 * (int64_t)n);
+  orc_projected P{xy.data(), conic.data(), cov.data(), op.data(), rgb.data(), depth.data(), radius.data(),
+                  rect.data(), mg.data()};
+  orc_project(s, X.data(), Q.data(), Sc.data(), cam, tile, &P);
+  const int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+  std::vector<uint32_t> dbits(n);
+  int64_t KP = 0;
+  for (int g = 0; g < n; ++g) {
+    float f = (float)depth[g];
+    std::memcpy(&dbits[g], &f, 4);
+    KP += (int64_t)(rect[4 * g + 2] - rect[4 * g]) * (rect[4 * g + 3] - rect[4 * g + 1]);
+  }
+  std::vector<uint64_t> keys(std::max<int64_t>(KP, 1));
+  std::vector<uint32_t> values(std::max<int64_t>(KP, 1)), ranges(2 * (size_t)tiles_x * tiles_y);
+  orc_bin_sort(n, dbits.data(), rect.data(), tiles_x, tiles_y, KP, keys.data(), values.data(), ranges.data());
+  const int npix = cam->width * cam->height;
+  std::vector<double> img(3 * (size_t)npix), Tfin(npix), marg(npix);
+  std::vector<int32_t> ncon(npix);
+  orc_composite(cam->width, cam->height, tile, ranges.data(), values.data(), xy.data(), conic.data(), op.data(),
+                rgb.data(), depth.data(), img.data(), Tfin.data(), ncon.data(), marg.data());
+
+  // ---------------------------------------------------------------- Eq. 4 backward, per pixel, back to front
+  std::vector<double> g_xy(2 * (int64_t)n, 0.0), g_conic(3 * (int64_t)n, 0.0), g_op(n, 0.0),
+      g_rgb(3 * (int64_t)n, 0.0);
+  for (int pix = 0; pix < npix; ++pix) {
+    const int px = pix % cam->width, py = pix / cam->width;
+    const int tid = (py / tile) * tiles_x + (px / tile);
+    const uint32_t start = ranges[2 * tid];
+    const double cx = px + 0.5, cy = py + 0.5;
+    const double* dC = dl_dimage + 3 * (int64_t)pix;
+    double T = Tfin[pix];          // transmittance after the last blended term
+    double behind[3] = {0, 0, 0};  // sum of c_j a_j T_j over the terms behind the current one
+    for (int k = ncon[pix] - 1; k >= 0; --k) {
+      const uint32_t g = values[start + k];
+      const double dx = xy[2 * g] - cx, dy = xy[2 * g + 1] - cy;
+      const double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
+      const double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+      if (power > 0.0) continue;
+      const double Gv = std::exp(power);
+      const double a_raw = op[g] * Gv;
+      const double alpha = std::min(kAlphaMax, a_raw);
+      if (alpha < kAlphaMin) continue;
+      const double Ti = T / (1.0 - alpha);  // transmittance in front of this term
+      double dL_dalpha = 0.0;
+      for (int ch = 0; ch < 3; ++ch) {
+        g_rgb[3 * g + ch] += dC[ch] * alpha * Ti;
+        dL_dalpha += dC[ch] * (rgb[3 * g + ch] * Ti - behind[ch] / (1.0 - alpha));
+      }
+      for (int ch = 0; ch < 3; ++ch) behind[ch] += rgb[3 * g + ch] * alpha * Ti;
+      T = Ti;
+      if (a_raw > kAlphaMax) continue;  // clamped: no gradient to opacity or shape
+      g_op[g] += dL_dalpha * Gv;
+      const double dpow = dL_dalpha * op[g] * Gv;
+      g_xy[2 * g] += dpow * (-(A * dx + B * dy));
+      g_xy[2 * g + 1] += dpow * (-(Cc * dy + B * dx));
+      g_conic[3 * g] += dpow * (-0.5 * dx * dx);
+      g_conic[3 * g + 1] += dpow * (-dx * dy);
+      g_conic[3 * g + 2] += dpow * (-0.5 * dy * dy);
+    }
+  }
+
+  // ---------------------------------------------------------------- Eq. 2 / Eq. 3 / SH backward, per Gaussian
+  const double* M = cam->world_to_cam;
+  double Rc[3][3], tc[3], campos[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) Rc[r][c] = M[4 * r + c];
+    tc[r] = M[4 * r + 3];
+  }
+  for (int c = 0; c < 3; ++c) campos[c] = -(Rc[0][c] * tc[0] + Rc[1][c] * tc[1] + Rc[2][c] * tc[2]);
+  const double limx = kGuard * cam->width / (2.0 * cam->fx), limy = kGuard * cam->height / (2.0 * cam->fy);
+  std::vector<double> gX(3 * (int64_t)n, 0.0), gQ(4 * (int64_t)n, 0.0), gS(3 * (int64_t)n, 0.0);
+  for (int g = 0; g < n; ++g) {
+    if (G->opacity_logits) G->opacity_logits[g] += g_op[g] * op[g] * (1.0 - op[g]);
+    if (radius[g] == 0) continue;
+    const double* Xg = &X[3 * (int64_t)g];
+    // colour
+    double v[3], vn = 0;
+    for (int k = 0; k < 3; ++k) { v[k] = Xg[k] - campos[k]; vn += v[k] * v[k]; }
+    vn = std::sqrt(vn);
+    double dir[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+    double Y[16], dY[16][3];
+    sh_basis(s->sh_degree, dir, Y);
+    sh_basis_grad(s->sh_degree, dir, dY);
+    double g_dir[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+      double raw = 0.5;
+      for (int k = 0; k < K; ++k) raw += Y[k] * (double)s->sh[((int64_t)g * K + k) * 3 + ch];
+      if (!(raw > 0.0)) continue;  // clamped at 0
+      const double gr = g_rgb[3 * g + ch];
+      for (int k = 0; k < K; ++k) {
+        if (G->sh) G->sh[((int64_t)g * K + k) * 3 + ch] += gr * Y[k];
+        for (int a = 0; a < 3; ++a) g_dir[a] += gr * (double)s->sh[((int64_t)g * K + k) * 3 + ch] * dY[k][a];
+      }
+    }
+    const double dd = dir[0] * g_dir[0] + dir[1] * g_dir[1] + dir[2] * g_dir[2];
+    for (int a = 0; a < 3; ++a) gX[3 * (int64_t)g + a] += (g_dir[a] - dir[a] * dd) / vn;
+    // camera-space mean
+    double p[3];
+    for (int r = 0; r < 3; ++r) p[r] = Rc[r][0] * Xg[0] + Rc[r][1] * Xg[1] + Rc[r][2] * Xg[2] + tc[r];
+    double gp[3] = {0, 0, 0};
+    // mean2D: u = fx px/pz + cx, v = fy py/pz + cy
+    gp[0] += g_xy[2 * g] * cam->fx / p[2];
+    gp[1] += g_xy[2 * g + 1] * cam->fy / p[2];
+    gp[2] += -g_xy[2 * g] * cam->fx * p[0] / (p[2] * p[2]) - g_xy[2 * g + 1] * cam->fy * p[1] / (p[2] * p[2]);
+    // conic = Sigma2D^-1: dL/dSigma2D = -K G_K K with G_K the symmetric gradient of K
+    const double ka = conic[3 * g], kb = conic[3 * g + 1], kc = conic[3 * g + 2];
+    const double Km[2][2] = {{ka, kb}, {kb, kc}};
+    const double GK[2][2] = {{g_conic[3 * g], 0.5 * g_conic[3 * g + 1]}, {0.5 * g_conic[3 * g + 1], g_conic[3 * g + 2]}};
+    double GS2[2][2];  // dL/dSigma2D (symmetric matrix gradient)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        double acc = 0;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) acc += Km[i][a] * GK[a][b] * Km[b][j];
+        GS2[i][j] = -acc;
+      }
+    // Sigma2D = T Sigma T^T + 0.3 I, T = J W, Sigma = (R S)(R S)^T
+    double qv[4], qn = 0;
+    for (int k = 0; k < 4; ++k) { qv[k] = Q[4 * (int64_t)g + k]; qn += qv[k] * qv[k]; }
+    qn = std::sqrt(qn);
+    double qh[4] = {qv[0] / qn, qv[1] / qn, qv[2] / qn, qv[3] / qn};
+    double R[3][3];
+    quat_to_rot(qh, R);
+    double sc[3];
+    for (int k = 0; k < 3; ++k) sc[k] = std::exp(Sc[3 * (int64_t)g + k]);
+    double RS[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) RS[i][j] = R[i][j] * sc[j];
+    const bool clx = std::fabs(p[0] / p[2]) > limx, cly = std::fabs(p[1] / p[2]) > limy;
+    const double rx = std::min(limx, std::max(-limx, p[0] / p[2])), ry = std::min(limy, std::max(-limy, p[1] / p[2]));
+    double J[2][3] = {{cam->fx / p[2], 0.0, -cam->fx * rx / p[2]}, {0.0, cam->fy / p[2], -cam->fy * ry / p[2]}};
+    double T[2][3];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) T[i][j] = J[i][0] * Rc[0][j] + J[i][1] * Rc[1][j] + J[i][2] * Rc[2][j];
+    double Am[2][3];  // A = T R S
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) Am[i][j] = T[i][0] * RS[0][j] + T[i][1] * RS[1][j] + T[i][2] * RS[2][j];
+    double gA[2][3];  // dL/dA = (GS2 + GS2^T) A = 2 GS2 A
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) gA[i][j] = 2.0 * (GS2[i][0] * Am[0][j] + GS2[i][1] * Am[1][j]);
+    double gT[2][3], gRS[3][3];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) gT[i][j] = gA[i][0] * RS[j][0] + gA[i][1] * RS[j][1] + gA[i][2] * RS[j][2];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) gRS[i][j] = T[0][i] * gA[0][j] + T[1][i] * gA[1][j];
+    double gR[3][3], gsc[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        gR[i][j] = gRS[i][j] * sc[j];
+        gsc[j] += gRS[i][j] * R[i][j];
+      }
+    for (int k = 0; k < 3; ++k) gS[3 * (int64_t)g + k] += gsc[k] * sc[k];
+    double dR[4][3][3], gqh[4] = {0, 0, 0, 0};
+    quat_rot_grad(qh, dR);
+    for (int c = 0; c < 4; ++c)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) gqh[c] += gR[i][j] * dR[c][i][j];
+    const double qd = qh[0] * gqh[0] + qh[1] * gqh[1] + qh[2] * gqh[2] + qh[3] * gqh[3];
+    for (int c = 0; c < 4; ++c) gQ[4 * (int64_t)g + c] += (gqh[c] - qh[c] * qd) / qn;
+    // T = J W: dL/dJ = dL/dT W^T
+    double gJ[2][3];
+    for (int i = 0; i < 2; ++i)
+      for (int a = 0; a < 3; ++a) gJ[i][a] = gT[i][0] * Rc[a][0] + gT[i][1] * Rc[a][1] + gT[i][2] * Rc[a][2];
+    const double pz = p[2], pz2 = pz * pz;
+    gp[2] += gJ[0][0] * (-cam->fx / pz2) + gJ[1][1] * (-cam->fy / pz2);
+    if (!clx) {  // J02 = -fx px / pz^2
+      gp[0] += gJ[0][2] * (-cam->fx / pz2);
+      gp[2] += gJ[0][2] * (2.0 * cam->fx * p[0] / (pz2 * pz));
+    } else {     // J02 = -fx rx / pz with rx held at the guard band
+      gp[2] += gJ[0][2] * (cam->fx * rx / pz2);
+    }
+    if (!cly) {
+      gp[1] += gJ[1][2] * (-cam->fy / pz2);
+      gp[2] += gJ[1][2] * (2.0 * cam->fy * p[1] / (pz2 * pz));
+    } else {
+      gp[2] += gJ[1][2] * (cam->fy * ry / pz2);
+    }
+    // p = W X' + t
+    for (int a = 0; a < 3; ++a) gX[3 * (int64_t)g + a] += Rc[0][a] * gp[0] + Rc[1][a] * gp[1] + Rc[2][a] * gp[2];
+  }
+
+  // ---------------------------------------------------------------- Eq. 6: X' = X + dX, r' = r + dr, s' = s + ds
+  for (int64_t i = 0; i < 3 * (int64_t)n; ++i) {
+    if (G->means) G->means[i] += gX[i];
+    if (G->log_scales) G->log_scales[i] += gS[i];
+  }
+  for (int64_t i = 0; i < 4 * (int64_t)n; ++i)
+    if (G->quats) G->quats[i] += gQ[i];
+  if (!deform) return 0;
+
+  // ---------------------------------------------------------------- heads, phi_d and Eq. 5 backward
+  for (int g = 0; g < n; ++g) {
+    const double* FD = &fd[(int64_t)g * W];
+    const double* A1 = &a1[(int64_t)g * W];
+    std::vector<double> gfd(W, 0.0), ga1(W, 0.0), gfh(hin, 0.0);
+    int col = 0;
+    for (int hd = 0; hd < 3; ++hd) {
+      const double* HID = &hid[((int64_t)g * 3 + hd) * W];
+      const int ko = 3 + 2 * hd, kh = 2 + 2 * hd;
+      std::vector<double> ghid(W, 0.0);
+      for (int o = 0; o < kHeadOut[hd]; ++o) {
+        const double gout = col + o < 3 ? gX[3 * (int64_t)g + col + o]
+                            : col + o < 7 ? gQ[4 * (int64_t)g + col + o - 3]
+                                          : gS[3 * (int64_t)g + col + o - 7];
+        if (G->mlp) {
+          G->mlp[Lo.b[ko] + o] += gout;
+          for (int i = 0; i < W; ++i) G->mlp[Lo.w[ko] + (int64_t)o * W + i] += gout * HID[i];
+        }
+        for (int i = 0; i < W; ++i) ghid[i] += gout * (double)s->mlp[Lo.w[ko] + (int64_t)o * W + i];
+      }
+      col += kHeadOut[hd];
+      for (int o = 0; o < W; ++o) {
+        const double gpre = HID[o] > 0.0 ? ghid[o] : 0.0;
+        if (G->mlp) {
+          G->mlp[Lo.b[kh] + o] += gpre;
+          for (int i = 0; i < W; ++i) G->mlp[Lo.w[kh] + (int64_t)o * W + i] += gpre * FD[i];
+        }
+        for (int i = 0; i < W; ++i) gfd[i] += gpre * (double)s->mlp[Lo.w[kh] + (int64_t)o * W + i];
+      }
+    }
+    for (int o = 0; o < W; ++o) {
+      const double gpre = FD[o] > 0.0 ? gfd[o] : 0.0;
+      if (G->mlp) {
+        G->mlp[Lo.b[1] + o] += gpre;
+        for (int i = 0; i < W; ++i) G->mlp[Lo.w[1] + (int64_t)o * W + i] += gpre * A1[i];
+      }
+      for (int i = 0; i < W; ++i) ga1[i] += gpre * (double)s->mlp[Lo.w[1] + (int64_t)o * W + i];
+    }
+    const double* FH = &fh[(int64_t)g * hin];
+    for (int o = 0; o < W; ++o) {
+      const double gpre = A1[o] > 0.0 ? ga1[o] : 0.0;
+      if (G->mlp) {
+        G->mlp[Lo.b[0] + o] += gpre;
+        for (int i = 0; i < hin; ++i) G->mlp[Lo.w[0] + (int64_t)o * hin + i] += gpre * FH[i];
+      }
+      for (int i = 0; i < hin; ++i) gfh[i] += gpre * (double)s->mlp[Lo.w[0] + (int64_t)o * hin + i];
+    }
+    // Eq. 5: f_l[c] = prod_p v_p[c]; v_p = bilinear(R_{l,p}) at (c_a, c_b)
+    double c4[4];
+    normalise(s, &xyz[3 * (int64_t)g], t, c4);
+    for (int l = 0; l < L; ++l) {
+      std::vector<std::vector<double>> vp(6, std::vector<double>(h));
+      int i0[6], j0[6], Ra[6], Rb[6];
+      double fa[6], fb[6], da[6], db[6];
+      for (int p = 0; p < 6; ++p) {
+        Ra[p] = plane_res(s, l, kPlaneAxes[p][0]);
+        Rb[p] = plane_res(s, l, kPlaneAxes[p][1]);
+        axis_setup(c4[kPlaneAxes[p][0]], Ra[p], &i0[p], &fa[p], &da[p]);
+        axis_setup(c4[kPlaneAxes[p][1]], Rb[p], &j0[p], &fb[p], &db[p]);
+        orc_plane_sample(s, l, p, c4[kPlaneAxes[p][0]], c4[kPlaneAxes[p][1]], vp[p].data());
+      }
+      for (int p = 0; p < 6; ++p) {
+        const int64_t off = plane_offset(s, l, p);
+        const float* Pl = s->planes + off;
+        for (int c = 0; c < h; ++c) {
+          double others = 1.0;
+          for (int q = 0; q < 6; ++q)
+            if (q != p) others *= vp[q][c];
+          const double gv = gfh[l * h + c] * others;
+          const int64_t e00 = ((int64_t)j0[p] * Ra[p] + i0[p]) * h + c, e10 = e00 + h;
+          const int64_t e01 = e00 + (int64_t)Ra[p] * h, e11 = e01 + h;
+          if (G->planes) {
+            G->planes[off + e00] += gv * (1 - fa[p]) * (1 - fb[p]);
+            G->planes[off + e10] += gv * fa[p] * (1 - fb[p]);
+            G->planes[off + e01] += gv * (1 - fa[p]) * fb[p];
+            G->planes[off + e11] += gv * fa[p] * fb[p];
+          }
+          const double dv_dfa = (1 - fb[p]) * ((double)Pl[e10] - Pl[e00]) + fb[p] * ((double)Pl[e11] - Pl[e01]);
+          const double dv_dfb = (1 - fa[p]) * ((double)Pl[e01] - Pl[e00]) + fa[p] * ((double)Pl[e11] - Pl[e10]);
+          const int a = kPlaneAxes[p][0], b = kPlaneAxes[p][1];
+          // the canonical mean moves the sampling point (time has no gradient)
+          if (G->means && a < 3)
+            G->means[3 * (int64_t)g + a] += gv * dv_dfa * da[p] * 2.0 / (s->aabb_max[a] - s->aabb_min[a]);
+          if (G->means && b < 3)
+            G->means[3 * (int64_t)g + b] += gv * dv_dfb * db[p] * 2.0 / (s->aabb_max[b] - s->aabb_min[b]);
+        }
+      }
+    }
+  }
+  return 0;
 }
