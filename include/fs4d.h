@@ -142,6 +142,12 @@ FS4D_API fs4d_status fs4d_check_device_status(fs4d_ctx* ctx);
  * planes/MLP and the bfloat16 tensor-core operand layouts).  Synchronous. */
 FS4D_API fs4d_status fs4d_load_scene(fs4d_ctx* ctx, const fs4d_scene_desc* desc, fs4d_scene_id* out);
 FS4D_API fs4d_status fs4d_unload_scene(fs4d_ctx* ctx, fs4d_scene_id id);
+/* Overwrite the parameters of a loaded scene (same n, SH degree, plane and MLP
+ * shapes; the box may not change).  Array pointers are DEVICE pointers when
+ * on_device != 0, else HOST pointers; a NULL array keeps its current values.
+ * Re-derives the BF16 and transposed MLP copies.  Synchronises the stream. */
+FS4D_API fs4d_status fs4d_update_scene(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_scene_desc* desc,
+                                       int32_t on_device);
 /* Bytes the scene holds resident on the device, and the per-frame work memory a
  * render at (width, height) needs with `pairs_per_gaussian` tile pairs per
  * Gaussian (used for admission by device-memory footprint). */

@@ -70,6 +70,7 @@ struct Work {
   DevBuf ranges;
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
+  DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
   long long cap_pairs = 0;
   long long sort_parts_cap = 0;
   int cap_n = 0, cap_tiles = 0;
@@ -80,10 +81,18 @@ constexpr int kCounters = 16;  // [0] emit ticket, [8..15] unused
 
 }  // namespace
 
+// Forward state of one rendered frame, owned by the frame (device copies), so
+// that the context's work memory can be reused before the backward runs.
 struct fs4d_frame {
   int scene = -1;
-  int width = 0, height = 0;
+  fs4d_camera cam{};
+  float t = 0.f;
+  int n = 0;
   long long pairs = 0;
+  DevBuf dmeans, dquats, dscales;              // deformed Gaussians
+  DevBuf xy, co, rgb, radius, rect, offsets;   // projection and emission offsets
+  DevBuf values, ranges;                       // sorted Gaussian indices, per-tile ranges
+  DevBuf t_final, n_contrib;                   // per pixel
 };
 
 struct fs4d_ctx {
@@ -96,6 +105,7 @@ struct fs4d_ctx {
   DevBuf status;
   uint32_t* h_pinned = nullptr;  // [4] readback slots
   long long last_pairs = 0;
+  uint32_t* last_values = nullptr;  // sorted Gaussian indices of the last frame (work memory)
   bool timing = false;
   cudaEvent_t ev[8] = {};        // deform, project, emit, emit end, sort, ranges, composite, end
 };
@@ -443,6 +453,7 @@ fs4d_status frame_back(fs4d_ctx* c, const fs4d_camera& shape, long long n_bound,
                            P<uint32_t>(c->status), c->stream, &alt));
   unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
+  c->last_values = values;
   mark(c, 5);
   FS4D_CUDA(c, launch_ranges(keys, n_dev, n_bound, P<uint2>(w.ranges), tx * ty, c->stream));
   mark(c, 6);
@@ -513,7 +524,8 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     Work& w = c->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.ts, &w.host_img};
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.ts, &w.host_img,
+                     &w.grad_pair, &w.gd, &w.acts, &w.wpartial};
     for (DevBuf* b : all) release(*b);
     release(c->status);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -657,12 +669,47 @@ fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, cons
   fs4d_status st = get_scene(c, id, &s);
   if (st != FS4D_OK) return st;
   DeviceGuard g(c->device);
-  st = render_sync(c, s, prec, cam, t, d_image, d_t_final, d_n_contrib);
-  if (st != FS4D_OK) return st;
-  if (saved) {
-    *saved = nullptr;
-    return fail(c, FS4D_ERR_UNIMPLEMENTED, "render: saving frames for the backward is not built yet");
+  if (!saved) return render_sync(c, s, prec, cam, t, d_image, d_t_final, d_n_contrib);
+  *saved = nullptr;
+  fs4d_frame* f = new (std::nothrow) fs4d_frame();
+  if (!f) return fail(c, FS4D_ERR_OOM, "render: frame allocation failed");
+  const size_t npix = (size_t)cam->width * cam->height;
+  auto drop = [&](fs4d_status e) {
+    fs4d_frame_free(c, f);
+    return e;
+  };
+  if (ensure(f->t_final, 4 * npix) != cudaSuccess || ensure(f->n_contrib, 4 * npix) != cudaSuccess)
+    return drop(fail(c, FS4D_ERR_OOM, "render: frame allocation failed"));
+  st = render_sync(c, s, prec, cam, t, d_image, P<float>(f->t_final), P<int32_t>(f->n_contrib));
+  if (st != FS4D_OK) return drop(st);
+  Work& w = c->w;
+  const size_t n = (size_t)s->n, K = (size_t)c->last_pairs;
+  const size_t tiles = (size_t)tiles_of(cam->width) * tiles_of(cam->height);
+  struct Item {
+    DevBuf* dst;
+    const void* src;
+    size_t bytes;
+  } items[] = {{&f->dmeans, w.dmeans.p, 12 * n}, {&f->dquats, w.dquats.p, 16 * n}, {&f->dscales, w.dscales.p, 12 * n},
+               {&f->xy, w.xy.p, 8 * n},          {&f->co, w.co.p, 16 * n},         {&f->rgb, w.rgb.p, 12 * n},
+               {&f->radius, w.radius.p, 4 * n},  {&f->rect, w.rect.p, 16 * n},     {&f->offsets, w.offsets.p, 4 * n},
+               {&f->values, c->last_values, 4 * std::max<size_t>(K, 1)},           {&f->ranges, w.ranges.p, 8 * tiles}};
+  for (Item& it : items) {
+    if (ensure(*it.dst, it.bytes) != cudaSuccess) return drop(fail(c, FS4D_ERR_OOM, "render: frame allocation failed"));
+    if (cudaMemcpyAsync(it.dst->p, it.src, it.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return drop(fail(c, FS4D_ERR_CUDA, "render: saving the frame failed"));
   }
+  if (d_t_final &&
+      cudaMemcpyAsync(d_t_final, f->t_final.p, 4 * npix, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return drop(fail(c, FS4D_ERR_CUDA, "render: copy of T failed"));
+  if (d_n_contrib &&
+      cudaMemcpyAsync(d_n_contrib, f->n_contrib.p, 4 * npix, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return drop(fail(c, FS4D_ERR_CUDA, "render: copy of n_contrib failed"));
+  f->scene = id;
+  f->cam = *cam;
+  f->t = t;
+  f->n = s->n;
+  f->pairs = c->last_pairs;
+  *saved = f;
   return FS4D_OK;
 }
 
@@ -740,14 +787,139 @@ fs4d_status fs4d_stage_times(fs4d_ctx* c, float* h_ms) {
   return FS4D_OK;
 }
 
-fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* saved, const float* d_dl_dimage, const fs4d_grads* g) {
-  (void)saved; (void)d_dl_dimage; (void)g;
-  return fail(c, FS4D_ERR_UNIMPLEMENTED, "render_backward: not built yet");
+fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!f || !d_dl_dimage || !gr) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: frame, dL/dI, grads needed");
+  Scene* s;
+  fs4d_status st = get_scene(c, f->scene, &s);
+  if (st != FS4D_OK) return st;
+  if (s->n != f->n) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: the scene changed size since the frame");
+  DeviceGuard g(c->device);
+  Work& w = c->w;
+  const long long n = s->n, K = f->pairs;
+  const int hin = s->mg.hin;
+  const size_t act_floats = (size_t)n * (hin + 64 + 64 + 192 + 10 + 192 + 64 + 64);
+  size_t wp = 0;
+  for (int O : {64, 4})
+    for (int I : {std::max(hin, 64), 64}) wp = std::max<size_t>(wp, (size_t)wgrad_partial_floats(n, O, I));
+  if (w.grad_pair.bytes < 4 * kPairGrad * (size_t)std::max(K, 1ll) || w.gd.bytes < 40 * (size_t)n ||
+      w.acts.bytes < 4 * act_floats || w.wpartial.bytes < 4 * wp) {
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+    FS4D_CUDA(c, ensure(w.grad_pair, 4 * kPairGrad * (size_t)std::max(K, 1ll)));
+    FS4D_CUDA(c, ensure(w.gd, 40 * (size_t)n));
+    FS4D_CUDA(c, ensure(w.acts, 4 * act_floats));
+    FS4D_CUDA(c, ensure(w.wpartial, 4 * wp));
+  }
+  const int tx = tiles_of(f->cam.width);
+  // 1. compositing backward into per-pair slots
+  FS4D_CUDA(c, cudaMemsetAsync(w.grad_pair.p, 0, 4 * kPairGrad * (size_t)std::max(K, 1ll), c->stream));
+  CompositeBwdArgs cb{};
+  cb.width = f->cam.width; cb.height = f->cam.height; cb.tiles_x = tx;
+  cb.ranges = P<uint2>(f->ranges); cb.values = P<uint32_t>(f->values);
+  cb.xy = P<float2>(f->xy); cb.conic_opacity = P<float4>(f->co); cb.rgb = P<float>(f->rgb);
+  cb.rect = P<int4>(f->rect); cb.offsets = P<uint32_t>(f->offsets);
+  cb.t_final = P<float>(f->t_final); cb.n_contrib = P<int>(f->n_contrib);
+  cb.dl_dimage = d_dl_dimage; cb.grad_pair = P<float>(w.grad_pair);
+  FS4D_CUDA(c, launch_composite_bwd(cb, c->stream));
+  // 2. projection, SH and Eq. 6 identity part
+  ProjectBwdArgs pb{};
+  pb.n = (int)n;
+  pb.means = P<float>(f->dmeans); pb.quats = P<float>(f->dquats); pb.log_scales = P<float>(f->dscales);
+  pb.sh = P<float>(s->sh); pb.sh_degree = s->sh_degree; pb.cam = cam_params(f->cam);
+  pb.conic_opacity = P<float4>(f->co); pb.radius = P<int>(f->radius); pb.rect = P<int4>(f->rect);
+  pb.offsets = P<uint32_t>(f->offsets); pb.grad_pair = P<float>(w.grad_pair); pb.gd = P<float>(w.gd);
+  pb.g_means = gr->means; pb.g_quats = gr->quats; pb.g_log_scales = gr->log_scales;
+  pb.g_opacity = gr->opacity_logits; pb.g_sh = gr->sh;
+  FS4D_CUDA(c, launch_project_bwd(pb, c->stream));
+  // 3. MLP heads, phi_d and HexPlane sampling (float32 recompute of the deformation)
+  MlpBwdArgs mb{};
+  mb.f = deform_args(s, nullptr, f->t, 1, nullptr, nullptr, nullptr);
+  mb.gd = P<float>(w.gd);
+  float* A = P<float>(w.acts);
+  mb.act.fh = A; A += (size_t)n * hin;
+  mb.act.a1 = A; A += (size_t)n * 64;
+  mb.act.fd = A; A += (size_t)n * 64;
+  mb.act.hid = A; A += (size_t)n * 192;
+  mb.act.dout = A; A += (size_t)n * 10;
+  mb.act.dh = A; A += (size_t)n * 192;
+  mb.act.d2 = A; A += (size_t)n * 64;
+  mb.act.d1 = A;
+  mb.g_planes = gr->planes;
+  mb.g_means = gr->means;
+  FS4D_CUDA(c, launch_mlp_bwd(mb, c->stream));
+  // 4. weight gradients, deterministic two-stage reductions, source layout
+  if (gr->mlp) {
+    size_t tot;
+    auto L = src_layers(hin, kWidth, &tot);
+    float* wp_buf = P<float>(w.wpartial);
+    const int col0[3] = {0, 3, 7};
+    FS4D_CUDA(c, launch_wgrad(mb.act.d1, mb.act.fh, n, 64, hin, wp_buf, gr->mlp + L[0].w, gr->mlp + L[0].b, c->stream));
+    FS4D_CUDA(c, launch_wgrad(mb.act.d2, mb.act.a1, n, 64, 64, wp_buf, gr->mlp + L[1].w, gr->mlp + L[1].b, c->stream));
+    for (int h = 0; h < 3; ++h) {
+      const SrcLayer& l1 = L[2 + 2 * h];
+      const SrcLayer& l2 = L[3 + 2 * h];
+      FS4D_CUDA(c, launch_wgrad(mb.act.dh + (size_t)64 * h * n, mb.act.fd, n, 64, 64, wp_buf, gr->mlp + l1.w,
+                                gr->mlp + l1.b, c->stream));
+      FS4D_CUDA(c, launch_wgrad(mb.act.dout + (size_t)col0[h] * n, mb.act.hid + (size_t)64 * h * n, n, l2.out, 64,
+                                wp_buf, gr->mlp + l2.w, gr->mlp + l2.b, c->stream));
+    }
+  }
+  return FS4D_OK;
 }
 
 fs4d_status fs4d_frame_free(fs4d_ctx* c, fs4d_frame* f) {
-  (void)c;
+  if (!f) return FS4D_OK;
+  {
+    DeviceGuard g(c ? c->device : 0);
+    if (c) cudaStreamSynchronize(c->stream);
+    DevBuf* all[] = {&f->dmeans, &f->dquats, &f->dscales, &f->xy, &f->co, &f->rgb, &f->radius,
+                     &f->rect, &f->offsets, &f->values, &f->ranges, &f->t_final, &f->n_contrib};
+    for (DevBuf* b : all) release(*b);
+  }
   delete f;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_update_scene(fs4d_ctx* c, fs4d_scene_id id, const fs4d_scene_desc* d, int32_t on_device) {
+  if (!c || !d) return FS4D_ERR_INVALID_ARG;
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  if (d->n != s->n || d->sh_degree != s->sh_degree || d->n_levels != s->pg.n_levels || d->feat_dim != s->pg.feat_dim ||
+      d->res_time != s->pg.res_time || d->mlp_width != kWidth)
+    return fail(c, FS4D_ERR_INVALID_ARG, "update_scene: shapes must match the loaded scene");
+  DeviceGuard g(c->device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t n = (size_t)s->n;
+  struct Item {
+    DevBuf* dst;
+    const float* src;
+    size_t floats;
+  } items[] = {{&s->means, d->means, 3 * n},         {&s->log_scales, d->log_scales, 3 * n},
+               {&s->quats, d->quats, 4 * n},         {&s->opacity_logits, d->opacity_logits, n},
+               {&s->sh, d->sh, 3 * n * s->K},        {&s->planes, d->planes, s->planes_floats},
+               {&s->mlp, d->mlp, s->mlp_floats}};
+  for (Item& it : items) {
+    if (!it.src) continue;
+    FS4D_CUDA(c, cudaMemcpyAsync(it.dst->p, it.src, 4 * it.floats, kind, c->stream));
+  }
+  // derived copies: BF16 planes and the two MLP layouts (small; prepared on the host)
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<float> planes(s->planes_floats), mlp(s->mlp_floats);
+  FS4D_CUDA(c, cudaMemcpy(planes.data(), s->planes.p, 4 * planes.size(), cudaMemcpyDeviceToHost));
+  FS4D_CUDA(c, cudaMemcpy(mlp.data(), s->mlp.p, 4 * mlp.size(), cudaMemcpyDeviceToHost));
+  std::vector<uint16_t> pb(planes.size());
+  for (size_t i = 0; i < planes.size(); ++i) pb[i] = f2bf(planes[i]);
+  FS4D_CUDA(c, cudaMemcpy(s->planes_bf16.p, pb.data(), 2 * pb.size(), cudaMemcpyHostToDevice));
+  std::vector<float> mt = transpose_mlp(mlp.data(), s->mg.hin, kWidth, s->mg);
+  FS4D_CUDA(c, cudaMemcpy(s->mlp_t.p, mt.data(), 4 * mt.size(), cudaMemcpyHostToDevice));
+  if (s->bf16_ok) {
+    std::vector<uint8_t> img;
+    std::vector<float> bias;
+    build_tc_image(mlp.data(), s->mg.hin, kWidth, s->tg, img, bias);
+    FS4D_CUDA(c, cudaMemcpy(s->tc_ops.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+    FS4D_CUDA(c, cudaMemcpy(s->tc_bias.p, bias.data(), 4 * bias.size(), cudaMemcpyHostToDevice));
+  }
   return FS4D_OK;
 }
 

@@ -1,0 +1,729 @@
+// Backward of the render path (training, Sec. 4.3): the chain rule of
+// compositing (Eq. 4 with Eq. 1), EWA projection (Eq. 2, Eq. 3) with SH colour,
+// the deformation update (Eq. 6), the MLP heads and phi_d, and the HexPlane
+// sampling (Eq. 5).  Float32 throughout.
+//
+//  composite_bwd_kernel  one CTA per tile, one pixel per thread, walking the
+//      tile's list back to front from each pixel's last blended term.  The
+//      contributions of the 256 pixels to each Gaussian are summed inside the
+//      CTA (warp shuffles, then shared-memory adds) and written ONCE per
+//      (tile, Gaussian) pair into that pair's emission slot, so no global
+//      atomics are needed: a Gaussian's slots are contiguous (offsets[g] ...
+//      offsets[g] + rect area).
+//  project_bwd_kernel    one thread per Gaussian: sums its pair slots, then
+//      back-propagates through the conic inverse, Sigma' = A A^T + 0.3 I with
+//      A = J W R S, the quaternion normalisation, the perspective Jacobian, the
+//      projected mean and the SH colour.
+//  mlp_bwd_kernel        one thread per Gaussian: recomputes the deformation
+//      forward, back-propagates through the heads and phi_d, stores the layer
+//      inputs and deltas feature-major for the weight gradients, and scatters
+//      the feature gradient into the plane cells (128-bit float atomics: many
+//      Gaussians share a cell).
+//  wgrad kernels         dW = D X^T over all Gaussians as per-chunk partial sums
+//      followed by a fixed-order reduction (deterministic).
+#include "fs4d_internal.cuh"
+
+namespace fs4d {
+namespace {
+
+constexpr int kBatch = kTile * kTile;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.f / 255.f;
+constexpr float kDilation = 0.3f;
+constexpr float kGuard = 1.3f;
+
+// ------------------------------------------------------------------ compositing
+
+__global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs a) {
+  __shared__ float2 s_xy[kBatch];
+  __shared__ float4 s_co[kBatch];
+  __shared__ float s_rgb[3 * kBatch];
+  __shared__ uint32_t s_slot[kBatch];
+  __shared__ float s_acc[kBatch][kPairGrad];
+  __shared__ int s_max_last;
+  const int tile = blockIdx.x;
+  const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < a.width && py < a.height;
+  const int pix = py * a.width + px;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const uint2 range = a.ranges[tile];
+  const int n = (int)(range.y - range.x);
+  const int last = inside ? a.n_contrib[pix] : 0;
+  float T = inside ? a.t_final[pix] : 1.f;
+  float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
+  if (inside) {
+    dC0 = a.dl_dimage[3 * pix];
+    dC1 = a.dl_dimage[3 * pix + 1];
+    dC2 = a.dl_dimage[3 * pix + 2];
+  }
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f;  // colour blended behind the current term
+  if (threadIdx.x == 0) s_max_last = 0;
+  __syncthreads();
+  atomicMax(&s_max_last, last);
+  __syncthreads();
+  const int max_last = min(s_max_last, n);
+  const unsigned lane = threadIdx.x & 31u;
+
+  for (int bstart = ((max_last - 1) / kBatch) * kBatch; bstart >= 0 && max_last > 0; bstart -= kBatch) {
+    __syncthreads();
+    const int j = bstart + (int)threadIdx.x;
+    if (j < n) {
+      const uint32_t g = a.values[range.x + j];
+      s_xy[threadIdx.x] = a.xy[g];
+      s_co[threadIdx.x] = a.conic_opacity[g];
+      s_rgb[3 * threadIdx.x] = a.rgb[3 * g];
+      s_rgb[3 * threadIdx.x + 1] = a.rgb[3 * g + 1];
+      s_rgb[3 * threadIdx.x + 2] = a.rgb[3 * g + 2];
+      const int4 r = a.rect[g];
+      s_slot[threadIdx.x] = a.offsets[g] + (uint32_t)((ty - r.y) * (r.z - r.x) + (tx - r.x));
+    }
+#pragma unroll
+    for (int k = 0; k < kPairGrad; ++k) s_acc[threadIdx.x][k] = 0.f;
+    __syncthreads();
+    const int jend = min(kBatch, max_last - bstart);
+    for (int jj = jend - 1; jj >= 0; --jj) {
+      float gr[kPairGrad];
+#pragma unroll
+      for (int k = 0; k < kPairGrad; ++k) gr[k] = 0.f;
+      bool contrib = false;
+      if (bstart + jj < last) {
+        const float2 p = s_xy[jj];
+        const float4 co = s_co[jj];
+        const float dx = p.x - fx, dy = p.y - fy;
+        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+        if (power <= 0.f) {
+          const float G = expf(power);
+          const float a_raw = co.w * G;
+          const float alpha = fminf(kAlphaMax, a_raw);
+          if (alpha >= kAlphaMin) {
+            contrib = true;
+            const float inv = 1.f / (1.f - alpha);
+            const float Ti = T * inv;
+            const float c0 = s_rgb[3 * jj], c1 = s_rgb[3 * jj + 1], c2 = s_rgb[3 * jj + 2];
+            const float dalpha =
+                dC0 * (c0 * Ti - b0 * inv) + dC1 * (c1 * Ti - b1 * inv) + dC2 * (c2 * Ti - b2 * inv);
+            const float w = alpha * Ti;
+            gr[6] = dC0 * w;
+            gr[7] = dC1 * w;
+            gr[8] = dC2 * w;
+            b0 += c0 * w;
+            b1 += c1 * w;
+            b2 += c2 * w;
+            T = Ti;
+            if (a_raw <= kAlphaMax) {
+              const float dpow = dalpha * co.w * G;
+              gr[0] = -dpow * (co.x * dx + co.y * dy);
+              gr[1] = -dpow * (co.z * dy + co.y * dx);
+              gr[2] = -0.5f * dpow * dx * dx;
+              gr[3] = -dpow * dx * dy;
+              gr[4] = -0.5f * dpow * dy * dy;
+              gr[5] = dalpha * G;
+            }
+          }
+        }
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, contrib);
+      if (mask == 0u) continue;
+      if (__popc(mask) > 4) {
+#pragma unroll
+        for (int k = 0; k < kPairGrad; ++k) {
+          float v = gr[k];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          gr[k] = v;
+        }
+        if (lane == 0u)
+#pragma unroll
+          for (int k = 0; k < kPairGrad; ++k) atomicAdd(&s_acc[jj][k], gr[k]);
+      } else if (contrib) {
+#pragma unroll
+        for (int k = 0; k < kPairGrad; ++k) atomicAdd(&s_acc[jj][k], gr[k]);
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < jend && bstart + (int)threadIdx.x < n) {
+      float* dst = a.grad_pair + (size_t)s_slot[threadIdx.x] * kPairGrad;
+#pragma unroll
+      for (int k = 0; k < kPairGrad; ++k) dst[k] = s_acc[threadIdx.x][k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ projection
+
+// Real SH basis and its derivative with respect to the direction components,
+// differentiating the same formulas the forward evaluates.
+constexpr float kY00 = 0.28209479177387814f, kY1 = 0.48860251190291992f, kY2a = 1.0925484305920792f,
+                kY20 = 0.31539156525252005f, kY22 = 0.54627421529603959f, kY33 = 0.59004358992664352f,
+                kY32 = 2.8906114426405538f, kY31 = 0.45704579946446572f, kY30 = 0.37317633259011540f,
+                kY32b = 1.4453057213202769f;
+
+__device__ void sh_basis_and_grad(int deg, float x, float y, float z, float* Y, float (*dY)[3]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) Y[k] = dY[k][0] = dY[k][1] = dY[k][2] = 0.f;
+  Y[0] = kY00;
+  if (deg < 1) return;
+  Y[1] = kY1 * y; Y[2] = kY1 * z; Y[3] = kY1 * x;
+  dY[1][1] = kY1; dY[2][2] = kY1; dY[3][0] = kY1;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y; dY[4][0] = kY2a * y; dY[4][1] = kY2a * x;
+  Y[5] = kY2a * y * z; dY[5][1] = kY2a * z; dY[5][2] = kY2a * y;
+  Y[6] = kY20 * (3.f * zz - 1.f); dY[6][2] = 6.f * kY20 * z;
+  Y[7] = kY2a * x * z; dY[7][0] = kY2a * z; dY[7][2] = kY2a * x;
+  Y[8] = kY22 * (xx - yy); dY[8][0] = 2.f * kY22 * x; dY[8][1] = -2.f * kY22 * y;
+  if (deg < 3) return;
+  Y[9] = kY33 * y * (3.f * xx - yy); dY[9][0] = 6.f * kY33 * x * y; dY[9][1] = kY33 * (3.f * xx - 3.f * yy);
+  Y[10] = kY32 * x * y * z; dY[10][0] = kY32 * y * z; dY[10][1] = kY32 * x * z; dY[10][2] = kY32 * x * y;
+  Y[11] = kY31 * y * (5.f * zz - 1.f); dY[11][1] = kY31 * (5.f * zz - 1.f); dY[11][2] = 10.f * kY31 * y * z;
+  Y[12] = kY30 * z * (5.f * zz - 3.f); dY[12][2] = kY30 * (15.f * zz - 3.f);
+  Y[13] = kY31 * x * (5.f * zz - 1.f); dY[13][0] = kY31 * (5.f * zz - 1.f); dY[13][2] = 10.f * kY31 * x * z;
+  Y[14] = kY32b * z * (xx - yy); dY[14][0] = 2.f * kY32b * x * z; dY[14][1] = -2.f * kY32b * y * z;
+  dY[14][2] = kY32b * (xx - yy);
+  Y[15] = kY33 * x * (xx - 3.f * yy); dY[15][0] = kY33 * (3.f * xx - 3.f * yy); dY[15][1] = -6.f * kY33 * x * y;
+}
+
+__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n) return;
+  float* gd = a.gd + 10 * (size_t)g;
+  if (a.radius[g] == 0) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) gd[k] = 0.f;
+    return;
+  }
+  // sum the pair slots of this Gaussian (contiguous by construction)
+  const int4 rc = a.rect[g];
+  const uint32_t e0 = a.offsets[g], cnt = (uint32_t)((rc.z - rc.x) * (rc.w - rc.y));
+  float G9[kPairGrad];
+#pragma unroll
+  for (int k = 0; k < kPairGrad; ++k) G9[k] = 0.f;
+  for (uint32_t e = 0; e < cnt; ++e) {
+    const float* src = a.grad_pair + (size_t)(e0 + e) * kPairGrad;
+#pragma unroll
+    for (int k = 0; k < kPairGrad; ++k) G9[k] += src[k];
+  }
+  const CamParams& c = a.cam;
+  const float4 co = a.conic_opacity[g];
+  if (a.g_opacity) a.g_opacity[g] += G9[5] * co.w * (1.f - co.w);
+
+  const float X0 = a.means[3 * g], X1 = a.means[3 * g + 1], X2 = a.means[3 * g + 2];
+  float gX0 = 0.f, gX1 = 0.f, gX2 = 0.f;
+  // ---- SH colour
+  {
+    const float cpx = -(c.m[0] * c.m[3] + c.m[4] * c.m[7] + c.m[8] * c.m[11]);
+    const float cpy = -(c.m[1] * c.m[3] + c.m[5] * c.m[7] + c.m[9] * c.m[11]);
+    const float cpz = -(c.m[2] * c.m[3] + c.m[6] * c.m[7] + c.m[10] * c.m[11]);
+    const float vx = X0 - cpx, vy = X1 - cpy, vz = X2 - cpz;
+    const float vn = sqrtf(vx * vx + vy * vy + vz * vz), vinv = 1.f / vn;
+    const float dx = vx * vinv, dy = vy * vinv, dz = vz * vinv;
+    float Y[16], dY[16][3];
+    sh_basis_and_grad(a.sh_degree, dx, dy, dz, Y, dY);
+    const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+    const float* sh = a.sh + (size_t)g * K * 3;
+    float gdir0 = 0.f, gdir1 = 0.f, gdir2 = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+      for (int k = 0; k < K; ++k) raw += Y[k] * sh[3 * k + ch];
+      if (!(raw > 0.f)) continue;
+      const float gr = G9[6 + ch];
+      for (int k = 0; k < K; ++k) {
+        if (a.g_sh) a.g_sh[((size_t)g * K + k) * 3 + ch] += gr * Y[k];
+        const float s = gr * sh[3 * k + ch];
+        gdir0 += s * dY[k][0];
+        gdir1 += s * dY[k][1];
+        gdir2 += s * dY[k][2];
+      }
+    }
+    const float dd = dx * gdir0 + dy * gdir1 + dz * gdir2;
+    gX0 += (gdir0 - dx * dd) * vinv;
+    gX1 += (gdir1 - dy * dd) * vinv;
+    gX2 += (gdir2 - dz * dd) * vinv;
+  }
+  // ---- camera-space mean and the projected mean
+  const float px = c.m[0] * X0 + c.m[1] * X1 + c.m[2] * X2 + c.m[3];
+  const float py = c.m[4] * X0 + c.m[5] * X1 + c.m[6] * X2 + c.m[7];
+  const float pz = c.m[8] * X0 + c.m[9] * X1 + c.m[10] * X2 + c.m[11];
+  const float iz = 1.f / pz, iz2 = iz * iz;
+  float gp0 = G9[0] * c.fx * iz, gp1 = G9[1] * c.fy * iz;
+  float gp2 = -G9[0] * c.fx * px * iz2 - G9[1] * c.fy * py * iz2;
+  // ---- conic = Sigma2D^-1: dL/dSigma2D = -K G_K K
+  const float ka = co.x, kb = co.y, kc = co.z;
+  const float gka = G9[2], gkb = 0.5f * G9[3], gkc = G9[4];
+  // M = K G_K, then -M K
+  const float m00 = ka * gka + kb * gkb, m01 = ka * gkb + kb * gkc;
+  const float m10 = kb * gka + kc * gkb, m11 = kb * gkb + kc * gkc;
+  const float S00 = -(m00 * ka + m01 * kb), S01 = -(m00 * kb + m01 * kc);
+  const float S10 = -(m10 * ka + m11 * kb), S11 = -(m10 * kb + m11 * kc);
+  // ---- Sigma2D = A A^T + 0.3 I, A = T R S, T = J W
+  const float4 q4 = reinterpret_cast<const float4*>(a.quats)[g];
+  const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w), qinv = 1.f / qn;
+  const float w = q4.x * qinv, x = q4.y * qinv, y = q4.z * qinv, z = q4.w * qinv;
+  float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                   {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                   {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+  const float sc[3] = {expf(a.log_scales[3 * g]), expf(a.log_scales[3 * g + 1]), expf(a.log_scales[3 * g + 2])};
+  const float limx = kGuard * (float)c.width / (2.f * c.fx), limy = kGuard * (float)c.height / (2.f * c.fy);
+  const float rx_raw = px * iz, ry_raw = py * iz;
+  const bool clx = fabsf(rx_raw) > limx, cly = fabsf(ry_raw) > limy;
+  const float rx = fminf(limx, fmaxf(-limx, rx_raw)), ry = fminf(limy, fmaxf(-limy, ry_raw));
+  const float J00 = c.fx * iz, J02 = -c.fx * rx * iz, J11 = c.fy * iz, J12 = -c.fy * ry * iz;
+  float T[2][3] = {{J00 * c.m[0] + J02 * c.m[8], J00 * c.m[1] + J02 * c.m[9], J00 * c.m[2] + J02 * c.m[10]},
+                   {J11 * c.m[4] + J12 * c.m[8], J11 * c.m[5] + J12 * c.m[9], J11 * c.m[6] + J12 * c.m[10]}};
+  float RS[3][3], A[2][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) RS[i][j] = R[i][j] * sc[j];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A[i][j] = T[i][0] * RS[0][j] + T[i][1] * RS[1][j] + T[i][2] * RS[2][j];
+  // dL/dA = (S + S^T) A
+  const float Ss00 = 2.f * S00, Ss01 = S01 + S10, Ss11 = 2.f * S11;
+  float gA[2][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    gA[0][j] = Ss00 * A[0][j] + Ss01 * A[1][j];
+    gA[1][j] = Ss01 * A[0][j] + Ss11 * A[1][j];
+  }
+  float gT[2][3], gRS[3][3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gT[i][j] = gA[i][0] * RS[j][0] + gA[i][1] * RS[j][1] + gA[i][2] * RS[j][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gRS[i][j] = T[0][i] * gA[0][j] + T[1][i] * gA[1][j];
+  float gR[3][3], gsc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      gR[i][j] = gRS[i][j] * sc[j];
+      gsc[j] += gRS[i][j] * R[i][j];
+    }
+  // dR/dq for the unit quaternion (w, x, y, z)
+  const float gw = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+  const float gx = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - w * gR[1][2] + z * gR[2][0] + w * gR[2][1]) -
+                   4.f * x * (gR[1][1] + gR[2][2]);
+  const float gy = 2.f * (x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] - w * gR[2][0] + z * gR[2][1]) -
+                   4.f * y * (gR[0][0] + gR[2][2]);
+  const float gz = 2.f * (-w * gR[0][1] + x * gR[0][2] + w * gR[1][0] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]) -
+                   4.f * z * (gR[0][0] + gR[1][1]);
+  const float qd = w * gw + x * gx + y * gy + z * gz;
+  // T = J W: dL/dJ = dL/dT W^T (only the non-zero entries of J matter)
+  const float gJ00 = gT[0][0] * c.m[0] + gT[0][1] * c.m[1] + gT[0][2] * c.m[2];
+  const float gJ02 = gT[0][0] * c.m[8] + gT[0][1] * c.m[9] + gT[0][2] * c.m[10];
+  const float gJ11 = gT[1][0] * c.m[4] + gT[1][1] * c.m[5] + gT[1][2] * c.m[6];
+  const float gJ12 = gT[1][0] * c.m[8] + gT[1][1] * c.m[9] + gT[1][2] * c.m[10];
+  gp2 += -gJ00 * c.fx * iz2 - gJ11 * c.fy * iz2;
+  if (!clx) {
+    gp0 += -gJ02 * c.fx * iz2;
+    gp2 += gJ02 * 2.f * c.fx * px * iz2 * iz;
+  } else {
+    gp2 += gJ02 * c.fx * rx * iz2;
+  }
+  if (!cly) {
+    gp1 += -gJ12 * c.fy * iz2;
+    gp2 += gJ12 * 2.f * c.fy * py * iz2 * iz;
+  } else {
+    gp2 += gJ12 * c.fy * ry * iz2;
+  }
+  gX0 += c.m[0] * gp0 + c.m[4] * gp1 + c.m[8] * gp2;
+  gX1 += c.m[1] * gp0 + c.m[5] * gp1 + c.m[9] * gp2;
+  gX2 += c.m[2] * gp0 + c.m[6] * gp1 + c.m[10] * gp2;
+  const float gq[4] = {(gw - w * qd) * qinv, (gx - x * qd) * qinv, (gy - y * qd) * qinv, (gz - z * qd) * qinv};
+  const float gs[3] = {gsc[0] * sc[0], gsc[1] * sc[1], gsc[2] * sc[2]};
+  gd[0] = gX0; gd[1] = gX1; gd[2] = gX2;
+  gd[3] = gq[0]; gd[4] = gq[1]; gd[5] = gq[2]; gd[6] = gq[3];
+  gd[7] = gs[0]; gd[8] = gs[1]; gd[9] = gs[2];
+  if (a.g_means) {
+    a.g_means[3 * g] += gX0; a.g_means[3 * g + 1] += gX1; a.g_means[3 * g + 2] += gX2;
+  }
+  if (a.g_quats)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.g_quats[4 * g + k] += gq[k];
+  if (a.g_log_scales)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.g_log_scales[3 * g + k] += gs[k];
+}
+
+// ------------------------------------------------------------------ MLP + HexPlane
+
+constexpr int kMT = 128;  // threads of the MLP backward CTA
+
+__device__ __forceinline__ void axis_setup(float u, int R, int& i0, float& f, float& dfdu) {
+  const float uc = fminf(1.f, fmaxf(-1.f, u));
+  const float g = (uc + 1.f) * 0.5f * (float)(R - 1);
+  int i = (int)floorf(g);
+  i = max(0, min(i, R - 2));
+  i0 = i;
+  f = g - (float)i;
+  dfdu = (u > -1.f && u < 1.f) ? 0.5f * (float)(R - 1) : 0.f;
+}
+
+// y = b + Wt^T x over IN inputs read from this thread's shared-memory column.
+template <int IN>
+__device__ __forceinline__ void dense64(const float* __restrict__ Wt, const float* __restrict__ b,
+                                        const float* __restrict__ col, float (&y)[kWidth]) {
+#pragma unroll
+  for (int o = 0; o < kWidth; ++o) y[o] = b[o];
+#pragma unroll 2
+  for (int i = 0; i < IN; ++i) {
+    const float x = col[i * kMT];
+    const float4* w4 = reinterpret_cast<const float4*>(Wt + i * kWidth);
+#pragma unroll
+    for (int q = 0; q < kWidth / 4; ++q) {
+      const float4 ww = w4[q];
+      y[4 * q + 0] = fmaf(ww.x, x, y[4 * q + 0]);
+      y[4 * q + 1] = fmaf(ww.y, x, y[4 * q + 1]);
+      y[4 * q + 2] = fmaf(ww.z, x, y[4 * q + 2]);
+      y[4 * q + 3] = fmaf(ww.w, x, y[4 * q + 3]);
+    }
+  }
+}
+
+// gcol[i] (+)= sum_o Wt[i][o] d[o] for i < IN.
+template <int IN, bool ACC>
+__device__ __forceinline__ void dense64_bwd(const float* __restrict__ Wt, const float (&d)[kWidth], float* gcol) {
+#pragma unroll 2
+  for (int i = 0; i < IN; ++i) {
+    const float4* w4 = reinterpret_cast<const float4*>(Wt + i * kWidth);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kWidth / 4; ++q) {
+      const float4 ww = w4[q];
+      s = fmaf(ww.x, d[4 * q], s);
+      s = fmaf(ww.y, d[4 * q + 1], s);
+      s = fmaf(ww.z, d[4 * q + 2], s);
+      s = fmaf(ww.w, d[4 * q + 3], s);
+    }
+    gcol[i * kMT] = ACC ? gcol[i * kMT] + s : s;
+  }
+}
+
+template <int OUT>
+__device__ __forceinline__ void head_bwd(const float* __restrict__ sw, const MlpGeomT& mg, int layer, float* col,
+                                         float* gcol, const float* dout, float* hid_out, float* dh_out,
+                                         long long n, long long g) {
+  float y[kWidth];
+  dense64<kWidth>(sw + mg.w[layer], sw + mg.b[layer], col, y);
+  const float* W2 = sw + mg.w[layer + 1];  // [64][OUT]
+  float d[kWidth];
+#pragma unroll
+  for (int o = 0; o < kWidth; ++o) {
+    hid_out[(long long)o * n + g] = fmaxf(y[o], 0.f);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < OUT; ++j) s = fmaf(W2[o * OUT + j], dout[j], s);
+    d[o] = y[o] > 0.f ? s : 0.f;
+    dh_out[(long long)o * n + g] = d[o];
+  }
+  dense64_bwd<kWidth, true>(sw + mg.w[layer], d, gcol);
+}
+
+template <int H, int L>
+__global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
+  constexpr int HL = H * L;
+  constexpr int ROWS = HL > kWidth ? HL : kWidth;
+  extern __shared__ float4 smem4[];
+  const DeformArgs& f = a.f;
+  float* sw = reinterpret_cast<float*>(smem4);
+  float* colbase = sw + f.mg.total;
+  float* gcolbase = colbase + ROWS * kMT;
+  for (int i = threadIdx.x; i < f.mg.total / 4; i += kMT)
+    smem4[i] = __ldg(reinterpret_cast<const float4*>(f.mlp_t) + i);
+  __syncthreads();
+  const PlaneGeom& pg = f.pg;
+  float* col = colbase + threadIdx.x;
+  float* gcol = gcolbase + threadIdx.x;
+  const long long n = f.n;
+  const MlpActs& act = a.act;
+  for (long long g = (long long)blockIdx.x * kMT + threadIdx.x; g < n; g += (long long)gridDim.x * kMT) {
+    const float X[3] = {f.means[3 * g], f.means[3 * g + 1], f.means[3 * g + 2]};
+    float c[4], dcdx[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      c[k] = (X[k] - pg.aabb_min[k]) * pg.aabb_scale[k] - 1.f;
+      dcdx[k] = pg.aabb_scale[k];
+    }
+    c[3] = 2.f * f.t0 - 1.f;
+    // ---- forward recompute (Eq. 5, phi_d)
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      float fv[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) fv[k] = 1.f;
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+        const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+        const int Ra = ax < 3 ? pg.res[l] : pg.res_time, Rb = bx < 3 ? pg.res[l] : pg.res_time;
+        int i0, j0;
+        float fa, fb, da, db;
+        axis_setup(c[ax], Ra, i0, fa, da);
+        axis_setup(c[bx], Rb, j0, fb, db);
+        const float4* v00 = reinterpret_cast<const float4*>(f.planes + pg.off[l][p] + ((long long)j0 * Ra + i0) * H);
+        const float4* v10 = v00 + H / 4;
+        const float4* v01 = v00 + (long long)Ra * (H / 4);
+        const float4* v11 = v01 + H / 4;
+        const float w00 = (1.f - fa) * (1.f - fb), w10 = fa * (1.f - fb), w01 = (1.f - fa) * fb, w11 = fa * fb;
+#pragma unroll
+        for (int q = 0; q < H / 4; ++q) {
+          const float4 A = __ldg(v00 + q), B = __ldg(v10 + q), C = __ldg(v01 + q), D = __ldg(v11 + q);
+          fv[4 * q + 0] *= w00 * A.x + w10 * B.x + w01 * C.x + w11 * D.x;
+          fv[4 * q + 1] *= w00 * A.y + w10 * B.y + w01 * C.y + w11 * D.y;
+          fv[4 * q + 2] *= w00 * A.z + w10 * B.z + w01 * C.z + w11 * D.z;
+          fv[4 * q + 3] *= w00 * A.w + w10 * B.w + w01 * C.w + w11 * D.w;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        col[(l * H + k) * kMT] = fv[k];
+        act.fh[(long long)(l * H + k) * n + g] = fv[k];
+      }
+    }
+    float y[kWidth];
+    dense64<HL>(sw + f.mg.w[0], sw + f.mg.b[0], col, y);
+#pragma unroll
+    for (int o = 0; o < kWidth; ++o) {
+      const float v = fmaxf(y[o], 0.f);
+      act.a1[(long long)o * n + g] = v;
+      col[o * kMT] = v;
+    }
+    dense64<kWidth>(sw + f.mg.w[1], sw + f.mg.b[1], col, y);
+#pragma unroll
+    for (int o = 0; o < kWidth; ++o) {
+      const float v = fmaxf(y[o], 0.f);
+      act.fd[(long long)o * n + g] = v;
+      col[o * kMT] = v;
+    }
+    // ---- heads backward (output deltas = dL/d(X', r', s'), Eq. 6)
+    float dout[kDeltaDim];
+#pragma unroll
+    for (int j = 0; j < kDeltaDim; ++j) {
+      dout[j] = a.gd[10 * g + j];
+      act.dout[(long long)j * n + g] = dout[j];
+    }
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) gcol[i * kMT] = 0.f;
+    head_bwd<3>(sw, f.mg, 2, col, gcol, dout, act.hid, act.dh, n, g);
+    head_bwd<4>(sw, f.mg, 4, col, gcol, dout + 3, act.hid + 64 * n, act.dh + 64 * n, n, g);
+    head_bwd<3>(sw, f.mg, 6, col, gcol, dout + 7, act.hid + 128 * n, act.dh + 128 * n, n, g);
+    // ---- phi_d backward
+    float d[kWidth];
+#pragma unroll
+    for (int o = 0; o < kWidth; ++o) {
+      d[o] = col[o * kMT] > 0.f ? gcol[o * kMT] : 0.f;
+      act.d2[(long long)o * n + g] = d[o];
+    }
+    dense64_bwd<kWidth, false>(sw + f.mg.w[1], d, gcol);
+#pragma unroll
+    for (int o = 0; o < kWidth; ++o) {
+      d[o] = act.a1[(long long)o * n + g] > 0.f ? gcol[o * kMT] : 0.f;
+      act.d1[(long long)o * n + g] = d[o];
+    }
+    dense64_bwd<HL, false>(sw + f.mg.w[0], d, gcol);  // gcol[0..HL) = dL/df_h
+    // ---- Eq. 5 backward: plane cells and the sampling position
+    float gx[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+      float v[6][H];
+      int i0[6], j0[6], Ra[6];
+      float fa[6], fb[6], da[6], db[6];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+        const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+        Ra[p] = ax < 3 ? pg.res[l] : pg.res_time;
+        const int Rb = bx < 3 ? pg.res[l] : pg.res_time;
+        axis_setup(c[ax], Ra[p], i0[p], fa[p], da[p]);
+        axis_setup(c[bx], Rb, j0[p], fb[p], db[p]);
+        const float* P = f.planes + pg.off[l][p] + ((long long)j0[p] * Ra[p] + i0[p]) * H;
+        const float w00 = (1.f - fa[p]) * (1.f - fb[p]), w10 = fa[p] * (1.f - fb[p]),
+                    w01 = (1.f - fa[p]) * fb[p], w11 = fa[p] * fb[p];
+#pragma unroll
+        for (int k = 0; k < H; ++k)
+          v[p][k] = w00 * __ldg(P + k) + w10 * __ldg(P + H + k) + w01 * __ldg(P + (long long)Ra[p] * H + k) +
+                    w11 * __ldg(P + (long long)Ra[p] * H + H + k);
+      }
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+        const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+        const float* P = f.planes + pg.off[l][p] + ((long long)j0[p] * Ra[p] + i0[p]) * H;
+        float* GP = a.g_planes ? a.g_planes + pg.off[l][p] + ((long long)j0[p] * Ra[p] + i0[p]) * H : nullptr;
+        const float w00 = (1.f - fa[p]) * (1.f - fb[p]), w10 = fa[p] * (1.f - fb[p]),
+                    w01 = (1.f - fa[p]) * fb[p], w11 = fa[p] * fb[p];
+        float sa = 0.f, sb = 0.f;
+#pragma unroll
+        for (int q = 0; q < H / 4; ++q) {
+          float gv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 4 * q + e;
+            float others = 1.f;
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+              if (r != p) others *= v[r][k];
+            gv[e] = gcol[(l * H + k) * kMT] * others;
+            const float p00 = __ldg(P + k), p10 = __ldg(P + H + k), p01 = __ldg(P + (long long)Ra[p] * H + k),
+                        p11 = __ldg(P + (long long)Ra[p] * H + H + k);
+            sa += gv[e] * ((1.f - fb[p]) * (p10 - p00) + fb[p] * (p11 - p01));
+            sb += gv[e] * ((1.f - fa[p]) * (p01 - p00) + fa[p] * (p11 - p10));
+          }
+          if (GP) {
+            atomicAdd(reinterpret_cast<float4*>(GP) + q, make_float4(w00 * gv[0], w00 * gv[1], w00 * gv[2], w00 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + H) + q,
+                      make_float4(w10 * gv[0], w10 * gv[1], w10 * gv[2], w10 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + (long long)Ra[p] * H) + q,
+                      make_float4(w01 * gv[0], w01 * gv[1], w01 * gv[2], w01 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + (long long)Ra[p] * H + H) + q,
+                      make_float4(w11 * gv[0], w11 * gv[1], w11 * gv[2], w11 * gv[3]));
+          }
+        }
+        if (ax < 3) gx[ax] += sa * da[p] * dcdx[ax];
+        if (bx < 3) gx[bx] += sb * db[p] * dcdx[bx];
+      }
+    }
+    if (a.g_means) {
+      a.g_means[3 * g] += gx[0];
+      a.g_means[3 * g + 1] += gx[1];
+      a.g_means[3 * g + 2] += gx[2];
+    }
+  }
+}
+
+template <int H, int L>
+cudaError_t launch_mlp_t(const MlpBwdArgs& a, cudaStream_t s) {
+  constexpr int HL = H * L;
+  constexpr int rows = HL > kWidth ? HL : kWidth;
+  const size_t smem = sizeof(float) * ((size_t)a.f.mg.total + 2 * (size_t)rows * kMT);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(mlp_bwd_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long need = ((long long)a.f.n + kMT - 1) / kMT;
+  const int grid = (int)(need < sms ? need : sms);
+  mlp_bwd_kernel<H, L><<<grid, kMT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ weight gradients
+
+constexpr int kWChunk = 1024;  // Gaussians per partial
+constexpr int kWStage = 32;    // Gaussians staged per step
+constexpr int kWMaxPer = 25;   // entries per thread: (64*96 + 64) / 256 rounded up
+
+__global__ void __launch_bounds__(256) wgrad_partial_kernel(const float* __restrict__ D, const float* __restrict__ X,
+                                                            long long n, int O, int I, float* __restrict__ partial) {
+  __shared__ float sD[kWStage][64];
+  __shared__ float sX[kWStage][97];
+  const int E = O * I + O;
+  const long long n0 = (long long)blockIdx.x * kWChunk;
+  const long long n1 = min(n, n0 + kWChunk);
+  float acc[kWMaxPer];
+#pragma unroll
+  for (int k = 0; k < kWMaxPer; ++k) acc[k] = 0.f;
+  for (long long b = n0; b < n1; b += kWStage) {
+    const int m = (int)min((long long)kWStage, n1 - b);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kWStage * O; t += 256) {
+      const int o = t / kWStage, j = t % kWStage;
+      sD[j][o] = j < m ? D[(long long)o * n + b + j] : 0.f;
+    }
+    for (int t = threadIdx.x; t < kWStage * I; t += 256) {
+      const int i = t / kWStage, j = t % kWStage;
+      sX[j][i] = j < m ? X[(long long)i * n + b + j] : 0.f;
+    }
+    for (int j = threadIdx.x; j < kWStage; j += 256) sX[j][I] = j < m ? 1.f : 0.f;  // bias column
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kWMaxPer; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      if (e >= E) break;
+      const int o = e < O * I ? e / I : e - O * I;
+      const int i = e < O * I ? e % I : I;
+      float s = acc[k];
+      for (int j = 0; j < kWStage; ++j) s = fmaf(sD[j][o], sX[j][i], s);
+      acc[k] = s;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kWMaxPer; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    if (e < E) partial[(long long)blockIdx.x * E + e] = acc[k];
+  }
+}
+
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int chunks, int O, int I, float* gW,
+                                    float* gb) {
+  const int E = O * I + O;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  float s = 0.f;
+  for (int c = 0; c < chunks; ++c) s += partial[(long long)c * E + e];  // fixed order: deterministic
+  if (e < O * I)
+    gW[e] += s;
+  else
+    gb[e - O * I] += s;
+}
+
+}  // namespace
+
+cudaError_t launch_composite_bwd(const CompositeBwdArgs& a, cudaStream_t s) {
+  const int tiles_y = (a.height + kTile - 1) / kTile;
+  if (a.tiles_x * tiles_y == 0) return cudaSuccess;
+  composite_bwd_kernel<<<a.tiles_x * tiles_y, kBatch, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const ProjectBwdArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  project_bwd_kernel<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd(const MlpBwdArgs& a, cudaStream_t s) {
+  if (a.f.n <= 0) return cudaSuccess;
+  const int h = a.f.pg.feat_dim, L = a.f.pg.n_levels;
+  if (h == 16 && L == 1) return launch_mlp_t<16, 1>(a, s);
+  if (h == 16 && L == 2) return launch_mlp_t<16, 2>(a, s);
+  if (h == 16 && L == 3) return launch_mlp_t<16, 3>(a, s);
+  if (h == 32 && L == 1) return launch_mlp_t<32, 1>(a, s);
+  if (h == 32 && L == 2) return launch_mlp_t<32, 2>(a, s);
+  if (h == 32 && L == 3) return launch_mlp_t<32, 3>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+long long wgrad_partial_floats(long long n, int O, int I) {
+  return ((n + kWChunk - 1) / kWChunk) * (long long)(O * I + O);
+}
+
+cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int I, float* partial, float* gW,
+                         float* gb, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (O > 64 || I > 96 || O * I + O > 256 * kWMaxPer) return cudaErrorInvalidValue;
+  const int chunks = (int)((n + kWChunk - 1) / kWChunk);
+  wgrad_partial_kernel<<<chunks, 256, 0, s>>>(D, X, n, O, I, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int E = O * I + O;
+  wgrad_reduce_kernel<<<(E + 255) / 256, 256, 0, s>>>(partial, chunks, O, I, gW, gb);
+  return cudaGetLastError();
+}
+
+}  // namespace fs4d

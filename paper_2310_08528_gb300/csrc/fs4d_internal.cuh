@@ -160,3 +160,76 @@ cudaError_t launch_composite(int width, int height, const uint2* ranges, const u
                              float* t_final, int* n_contrib, cudaStream_t s);
 
 }  // namespace fs4d
+
+// ================================================================ backward
+namespace fs4d {
+
+constexpr int kPairGrad = 9;  // per (tile, Gaussian) pair: du dv dconic(a b c) dopacity drgb(3)
+
+struct CompositeBwdArgs {
+  int width, height, tiles_x;
+  const uint2* ranges;
+  const uint32_t* values;
+  const float2* xy;
+  const float4* conic_opacity;
+  const float* rgb;
+  const int4* rect;
+  const uint32_t* offsets;
+  const float* t_final;
+  const int* n_contrib;
+  const float* dl_dimage;   // [H][W][3]
+  float* grad_pair;         // [K][9], indexed by emission slot; zeroed by the caller
+};
+
+struct ProjectBwdArgs {
+  int n;
+  const float* means;       // deformed [n][3]
+  const float* quats;       // deformed [n][4]
+  const float* log_scales;  // deformed [n][3]
+  const float* sh;          // [n][K][3]
+  int sh_degree;
+  CamParams cam;
+  const float4* conic_opacity;
+  const int* radius;
+  const int4* rect;
+  const uint32_t* offsets;
+  const float* grad_pair;
+  float* gd;                // out [n][10]: dL/d(X', r', s')
+  float* g_means;           // += (nullable)
+  float* g_quats;
+  float* g_log_scales;
+  float* g_opacity;
+  float* g_sh;
+};
+
+// Per-Gaussian activations and deltas of the deformation MLP, feature-major
+// ([feature][n]) so that each thread's writes coalesce across the warp.
+struct MlpActs {
+  float* fh;    // [HL][n]  layer d1 input
+  float* a1;    // [64][n]  layer d2 input
+  float* fd;    // [64][n]  head hidden-layer input
+  float* hid;   // [192][n] head output-layer inputs (x, r, s)
+  float* dout;  // [10][n]  output deltas
+  float* dh;    // [192][n] head hidden pre-activation deltas
+  float* d2;    // [64][n]
+  float* d1;    // [64][n]
+};
+
+struct MlpBwdArgs {
+  DeformArgs f;             // canonical scene, t0, planes, transposed MLP
+  const float* gd;          // [n][10]
+  MlpActs act;
+  float* g_planes;          // += (nullable)
+  float* g_means;           // += (nullable)
+};
+
+cudaError_t launch_composite_bwd(const CompositeBwdArgs& a, cudaStream_t s);
+cudaError_t launch_project_bwd(const ProjectBwdArgs& a, cudaStream_t s);
+cudaError_t launch_mlp_bwd(const MlpBwdArgs& a, cudaStream_t s);
+// dW[o][i] += sum_n D[o][n] X[i][n], db[o] += sum_n D[o][n], through a [chunks][O*I+O] partial buffer
+// (deterministic two-stage reduction).  W and b are in the source layout (W[out][in] then b).
+long long wgrad_partial_floats(long long n, int O, int I);
+cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int I, float* partial, float* gW,
+                         float* gb, cudaStream_t s);
+
+}  // namespace fs4d

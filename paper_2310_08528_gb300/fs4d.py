@@ -21,7 +21,7 @@ STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_E
 
 # Every symbol include/fs4d.h declares (checked by the tests against the .so).
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
-           "fs4d_load_scene", "fs4d_unload_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
+           "fs4d_load_scene", "fs4d_unload_scene", "fs4d_update_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
            "fs4d_render_host", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_composite")
@@ -74,6 +74,7 @@ def library(path: str = LIB_PATH):
         "fs4d_check_device_status": [vp],
         "fs4d_load_scene": [vp, C.POINTER(SceneDesc), C.POINTER(i32)],
         "fs4d_unload_scene": [vp, i32],
+        "fs4d_update_scene": [vp, i32, C.POINTER(SceneDesc), i32],
         "fs4d_scene_bytes": [vp, i32, i32, i32, f32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
         "fs4d_deform": [vp, i32, i32, vp, i32, vp, vp, vp],
         "fs4d_render": [vp, i32, i32, C.POINTER(Camera), f32, vp, vp, vp, C.POINTER(vp)],
@@ -209,6 +210,46 @@ class Context:
         self.call("fs4d_render", sid, prec, C.byref(cs), float(t), _ptr(image), _ptr(T), _ptr(nc), None)
         return (image, T, nc) if with_aux else image
 
+    def render_saved(self, sid: int, cam, t: float, prec: int = FP32):
+        """Render and keep the forward state for render_backward: (image, frame handle)."""
+        torch = self.torch
+        image = torch.empty((cam.height, cam.width, 3), device=torch.device("cuda", self.device))
+        cs = camera_struct(cam)
+        fr = C.c_void_p()
+        self.call("fs4d_render", sid, prec, C.byref(cs), float(t), _ptr(image), None, None, C.byref(fr))
+        return image, fr
+
+    def render_backward(self, frame, dl_dimage, grads: Dict[str, object]) -> None:
+        """Accumulate d(sum(dl_dimage * image))/d(parameter) into the given device tensors."""
+        g = Grads(**{k: _ptr(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                                       "planes", "mlp")})
+        self.call("fs4d_render_backward", frame, _ptr(dl_dimage.contiguous()), C.byref(g))
+
+    def frame_free(self, frame) -> None:
+        self.call("fs4d_frame_free", frame)
+
+    def update_scene(self, sid: int, params: Dict[str, object]) -> None:
+        """Overwrite scene parameters from CUDA tensors (same shapes as loaded)."""
+        scene = self._scenes[sid]
+        d = SceneDesc()
+        d.n = int(scene.means.shape[0])
+        d.sh_degree = int(scene.sh_degree)
+        keep = []
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp"):
+            v = params.get(k)
+            if v is not None:
+                v = v.detach().contiguous().float()
+                keep.append(v)
+                setattr(d, k, _ptr(v))
+        rs = list(scene.res_spatial)
+        d.n_levels = len(rs)
+        d.res_spatial = (C.c_int32 * 4)(*(rs + [0] * (4 - len(rs))))
+        d.aabb_min = (C.c_float * 3)(*map(float, scene.aabb_min))
+        d.aabb_max = (C.c_float * 3)(*map(float, scene.aabb_max))
+        d.res_time, d.feat_dim, d.mlp_width = int(scene.res_time), int(scene.feat_dim), int(scene.mlp_width)
+        self.call("fs4d_update_scene", sid, C.byref(d), 1)
+        del keep
+
     def render_host(self, sid: int, cam, t: float, prec: int = FP32, out: Optional[np.ndarray] = None):
         if out is None:
             out = np.empty((cam.height, cam.width, 3), np.float32)
@@ -274,3 +315,51 @@ class Context:
         self.call("fs4d_composite", width, height, _ptr(ranges), _ptr(values), _ptr(xy), _ptr(conic_opacity),
                   _ptr(rgb), _ptr(img), _ptr(T), _ptr(nc))
         return img, T, nc
+
+
+PARAMS = ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")
+
+
+def _render_function():
+    import torch
+
+    class RenderFunction(torch.autograd.Function):
+        """image = S(M, G + F(G, t)) with the hand-written CUDA backward.
+
+        forward(fs, sid, cam, t, prec, means, log_scales, quats, opacity_logits, sh, planes, mlp)
+        copies the parameter tensors into the library's scene, renders, and keeps
+        the frame; backward accumulates every parameter gradient with
+        fs4d_render_backward.  The backward recomputes the deformation in float32.
+        """
+
+        @staticmethod
+        def forward(ctx, fs, sid, cam, t, prec, *params):
+            fs.update_scene(sid, dict(zip(PARAMS, params)))
+            image, frame = fs.render_saved(sid, cam, t, prec)
+            ctx.fs, ctx.frame = fs, frame
+            ctx.shapes = [(p.shape, p.dtype, p.device) for p in params]
+            ctx.needs = ctx.needs_input_grad[5:]
+            return image
+
+        @staticmethod
+        def backward(ctx, dl_dimage):
+            grads = [torch.zeros(s, dtype=d, device=dev) if need else None
+                     for (s, d, dev), need in zip(ctx.shapes, ctx.needs)]
+            ctx.fs.render_backward(ctx.frame, dl_dimage, dict(zip(PARAMS, grads)))
+            ctx.fs.frame_free(ctx.frame)
+            ctx.frame = None
+            return (None, None, None, None, None, *grads)
+
+    return RenderFunction
+
+
+_RF = None
+
+
+def render_differentiable(fs: "Context", sid: int, cam, t: float, params: Dict[str, object], prec: int = FP32):
+    """Differentiable render: params maps means/log_scales/quats/opacity_logits/sh/
+    planes/mlp to CUDA float32 tensors (requires_grad as needed)."""
+    global _RF
+    if _RF is None:
+        _RF = _render_function()
+    return _RF.apply(fs, sid, cam, float(t), prec, *[params[k] for k in PARAMS])

@@ -1,0 +1,154 @@
+"""GPU backward (fs4d_render_backward, through the C ABI) against the FP64
+oracle's analytic gradient and against FP64 central finite differences.
+
+Bar: per parameter group, max |g_gpu - g_ref| <= 1e-3 * max |g_ref|.  Pixels
+whose forward contains a discrete decision within float32 rounding of its
+threshold (oracle.unstable_pixels) get dL/dI = 0, since the gradient is not
+defined across such a decision.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_08528_gb300 import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_08528_gb300 import fs4d  # noqa: E402
+
+GROUPS = fs4d.PARAMS
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fs4d.Context(0)
+    yield c
+    c.close()
+
+
+def small_scene(seed, deg=0, n=48):
+    if deg == 0:
+        s = sg.make_tiny(seed, n=n, mlp_std=0.15, bias_std=0.05)
+    else:
+        s = sg.make_object(seed, n=n, res_spatial=(6, 8), res_time=4, h=16, mlp_std=0.15)
+    s.means *= 0.8
+    s.log_scales += 1.2
+    return s
+
+
+def small_camera(w=40, h=36):
+    cam = sg.tiny_camera(w, h)
+    cam.fx = cam.fy = 40.0
+    return cam
+
+
+def gpu_grads(ctx, s, cam, t, dl, prec=fs4d.FP32):
+    sid = ctx.load_scene(s)
+    img, frame = ctx.render_saved(sid, cam, t, prec)
+    shapes = {k: getattr(s, k).shape for k in GROUPS}
+    g = {k: torch.zeros(shapes[k], device="cuda") for k in GROUPS}
+    ctx.render_backward(frame, torch.from_numpy(dl.astype(np.float32)).cuda(), g)
+    ctx.frame_free(frame)
+    torch.cuda.synchronize()
+    ctx.unload_scene(sid)
+    return img.cpu().numpy(), {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+
+
+def masked_dl(s, cam, t, seed):
+    rng = np.random.default_rng(seed)
+    dl = rng.normal(size=(cam.height, cam.width, 3))
+    unstable, *_ = oracle.unstable_pixels(s, cam, t)
+    dl[unstable] = 0.0
+    return dl
+
+
+def check_groups(g, ref, rel=REL):
+    for k in GROUPS:
+        scale = np.abs(ref[k]).max()
+        assert scale > 0, k
+        err = np.abs(g[k] - ref[k]).max()
+        print(f"{k:15s} max|ref| {scale:.3e}  max err {err:.3e}  rel {err / scale:.2e}")
+        assert err <= rel * scale, (k, err, scale)
+
+
+@pytest.mark.parametrize("seed,deg", [(0, 0), (1, 3), (4, 0)])
+def test_backward_matches_oracle_small(ctx, seed, deg):
+    s = small_scene(seed, deg)
+    cam = small_camera()
+    dl = masked_dl(s, cam, 0.4, seed)
+    _, g = gpu_grads(ctx, s, cam, 0.4, dl)
+    ref = oracle.render_backward(s, cam, 0.4, dl)
+    check_groups(g, ref)
+
+
+def test_backward_matches_oracle_tiny_scene(ctx):
+    """N=2000 at 128x128, several tiles per Gaussian and many per tile."""
+    s = sg.make_tiny(0, mlp_std=0.1)
+    cam = sg.tiny_camera()
+    dl = masked_dl(s, cam, 0.5, 7)
+    _, g = gpu_grads(ctx, s, cam, 0.5, dl)
+    ref = oracle.render_backward(s, cam, 0.5, dl)
+    check_groups(g, ref)
+
+
+def test_backward_matches_central_differences(ctx):
+    """GPU gradient against FP64 central differences of the oracle forward."""
+    s = small_scene(2, deg=3)
+    cam = small_camera()
+    t = 0.6
+    dl = masked_dl(s, cam, t, 2)
+    _, g = gpu_grads(ctx, s, cam, t, dl)
+    h = 2.0 ** -13
+    rng = np.random.default_rng(5)
+    n_ok = n_all = 0
+    for k in GROUPS:
+        flat = getattr(s, k).reshape(-1)
+        gk = g[k].reshape(-1)
+        idx = np.flatnonzero(np.abs(gk) > 1e-3 * np.abs(gk).max())
+        for i in rng.choice(idx, size=min(8, len(idx)), replace=False):
+            x0 = flat[i]
+            flat[i] = np.float32(x0 + h)
+            lp = float(np.sum(oracle.render(s, cam, t)[0] * dl))
+            flat[i] = np.float32(x0 - h)
+            lm = float(np.sum(oracle.render(s, cam, t)[0] * dl))
+            flat[i] = x0
+            fd = (lp - lm) / (2 * h)
+            n_all += 1
+            n_ok += abs(fd - gk[i]) <= REL * max(abs(fd), abs(gk[i])) + 1e-6 * np.abs(gk).max()
+    assert n_ok >= 0.95 * n_all, (n_ok, n_all)
+
+
+def test_autograd_function_matches_direct_call(ctx):
+    s = small_scene(3)
+    cam = small_camera()
+    sid = ctx.load_scene(s)
+    params = {k: torch.from_numpy(np.ascontiguousarray(getattr(s, k))).cuda().requires_grad_(True) for k in GROUPS}
+    dl = masked_dl(s, cam, 0.3, 3)
+    img = fs4d.render_differentiable(ctx, sid, cam, 0.3, params)
+    loss = (img * torch.from_numpy(dl.astype(np.float32)).cuda()).sum()
+    loss.backward()
+    ref = oracle.render_backward(s, cam, 0.3, dl)
+    check_groups({k: params[k].grad.cpu().numpy().astype(np.float64) for k in GROUPS}, ref)
+    # the update path: a parameter change reaches the render
+    with torch.no_grad():
+        params["opacity_logits"] -= 3.0
+    img2 = fs4d.render_differentiable(ctx, sid, cam, 0.3, params)
+    assert float(img2.detach().sum()) < float(img.detach().sum())
+    ctx.unload_scene(sid)
+
+
+def test_backward_repeatable(ctx):
+    """Two backward passes agree to float32 reassociation (per-pixel contributions
+    are summed in shared memory in arrival order; plane cells use atomics)."""
+    s = sg.make_tiny(5, mlp_std=0.1)
+    cam = sg.tiny_camera()
+    dl = np.random.default_rng(9).normal(size=(128, 128, 3))
+    _, g1 = gpu_grads(ctx, s, cam, 0.5, dl)
+    _, g2 = gpu_grads(ctx, s, cam, 0.5, dl)
+    for k in GROUPS:
+        assert np.abs(g1[k] - g2[k]).max() <= 1e-5 * np.abs(g1[k]).max(), k
