@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=60)
     return ap.parse_args()
 
@@ -216,6 +217,100 @@ def run_reference(args):
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ----------------------------------------------------------------- serving
+
+SERVE_RES = ((400, 400), (800, 800), (1352, 1014), (1920, 1080))
+
+
+def random_camera(rng, w, h):
+    from paper_2310_08528_gb300 import scenegen as sg
+    az = rng.uniform(0, 2 * np.pi)
+    z = rng.uniform(0.05, 0.9)
+    r = np.sqrt(1 - z * z)
+    eye = (4 * r * np.cos(az), 4 * r * np.sin(az), 4 * z)
+    return sg.look_at(eye, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), w, h, 50.0)
+
+
+def serving_bench(ctx, fs4d, torch, rates=(500.0, 2000.0), seconds=1.5, precs=("bf16", "fp32")):
+    """Continuous batching under Poisson arrivals: 8 resident scenes of 100k-500k
+    Gaussians, (scene, random hemisphere camera, t ~ U[0,1]), resolution uniform
+    over 400x400, 800x800, 1352x1014, 1920x1080; device-resident outputs."""
+    from paper_2310_08528_gb300 import scenegen as sg
+    sizes = [int(100_000 + i * 400_000 / 7) for i in range(8)]
+    sids = [ctx.load_scene(sg.make_object(i, n=n)) for i, n in enumerate(sizes)]
+    srv = fs4d.Server(ctx, max_inflight=8, max_batch=8, hbm_budget_bytes=24 << 30, pairs_per_gaussian=12.0)
+    pool = [torch.empty(1080 * 1920 * 3, device="cuda") for _ in range(96)]
+    free = list(range(len(pool)))
+    busy = {}
+
+    def reap():
+        out = srv.poll(4096)
+        for c in out:
+            free.append(busy.pop(c["ticket"]))
+        return out
+
+    rng = np.random.default_rng(123)
+    # warm-up: every (scene, resolution, precision) once, so graphs are captured
+    for p in precs:
+        pc = fs4d.BF16 if p == "bf16" else fs4d.FP32
+        items = []
+        for s in sids:
+            for (w, h) in SERVE_RES:
+                while not free:
+                    reap()
+                b = free.pop()
+                items.append((s, random_camera(rng, w, h), float(rng.uniform()), pool[b][: w * h * 3], pc, b))
+        for it in items:
+            tk = srv.submit(*it[:5])
+            busy[tk] = it[5]
+            while not free:
+                reap()
+        srv.drain()
+        reap()
+    results = {}
+    for p in precs:
+        pc = fs4d.BF16 if p == "bf16" else fs4d.FP32
+        for rate in rates:
+            lat, done_all = [], []
+            n_req = int(rate * seconds)
+            gaps = rng.exponential(1.0 / rate, n_req)
+            t0 = time.perf_counter()
+            due = t0
+            for i in range(n_req):
+                due += gaps[i]
+                s = sids[int(rng.integers(0, len(sids)))]
+                w, h = SERVE_RES[int(rng.integers(0, 4))]
+                cam = random_camera(rng, w, h)
+                while time.perf_counter() < due:
+                    done_all += reap()
+                while not free:
+                    done_all += reap()
+                b = free.pop()
+                tk = srv.submit(s, cam, float(rng.uniform()), pool[b][: w * h * 3], pc)
+                busy[tk] = b
+            srv.drain()
+            done_all += reap()
+            wall = time.perf_counter() - t0
+            ok = [c for c in done_all if c["status"] == 0]
+            lat = np.array([c["done_ms"] - c["submit_ms"] for c in ok])
+            span_ms = max(c["done_ms"] for c in ok) - min(c["submit_ms"] for c in ok)
+            results[f"{p}@{int(rate)}"] = {
+                "offered_req_s": rate, "requests": n_req, "completed": len(ok),
+                "failed": len(done_all) - len(ok), "throughput_req_s": len(ok) / (span_ms * 1e-3),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "wall_s": wall}
+    st = srv.stats()
+    srv.close()
+    for s in sids:
+        ctx.unload_scene(s)
+    return {"workload": "8 resident scenes (object generator, seeds 0-7, N=100k..500k), Poisson arrivals, "
+                        "random hemisphere camera, t~U[0,1], resolution uniform over 400x400/800x800/1352x1014/"
+                        "1920x1080; latency = host submit -> completion observed by the scheduler",
+            "config": {"max_inflight": 8, "max_batch": 8, "hbm_budget_gb": 24},
+            "results": results,
+            "server_stats": {k: int(v) for k, v in st.items()}}
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -392,6 +487,8 @@ def main():
         "gpu_launches": launches_per_frame * (args.steps * len(precs)),
         "clocks": clocks,
     }
+    if not args.no_serving:
+        line["serving"] = serving_bench(ctx, fs4d, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

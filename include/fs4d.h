@@ -54,7 +54,8 @@ typedef enum fs4d_status {
   FS4D_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the CUDA error) */
   FS4D_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (status word set) */
   FS4D_ERR_NOT_FOUND = 6,     /* unknown scene id or frame */
-  FS4D_ERR_UNIMPLEMENTED = 7  /* a shape this build does not support (message says which) */
+  FS4D_ERR_UNIMPLEMENTED = 7, /* a shape this build does not support (message says which) */
+  FS4D_ERR_CANCELLED = 8      /* a queued serving request was cancelled or its server stopped */
 } fs4d_status;
 
 typedef enum fs4d_precision {
@@ -204,6 +205,68 @@ FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
  * tile ranges, composite (milliseconds, that frame only). */
 FS4D_API fs4d_status fs4d_set_stage_timing(fs4d_ctx* ctx, int32_t enable);
 FS4D_API fs4d_status fs4d_stage_times(fs4d_ctx* ctx, float* h_ms);
+
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching request loop over the context's resident scenes, run by
+ * a native scheduler thread.  Requests (scene, camera, t) are admitted in FIFO
+ * order as work slots and device memory free up (a slot holds one in-flight
+ * frame's work memory; slots together stay within hbm_budget_bytes).  Admitted
+ * requests that share a scene and precision are deformed together in ONE
+ * persistent launch (one timestamp per request), then each request's
+ * project/bin/sort/composite sequence is replayed from a CUDA graph captured
+ * per (slot, scene, resolution, precision) on the slot's own stream, so frames
+ * of different requests overlap on the device.  A frame whose tile pairs
+ * overflow its slot's capacity is re-run with a larger capacity.  Results do
+ * not depend on what else is in flight.  While a server runs, unload a scene
+ * only after its requests completed (fs4d_unload_scene waits for in-flight
+ * ones; queued ones then complete with FS4D_ERR_NOT_FOUND). */
+typedef struct fs4d_server fs4d_server;
+typedef struct fs4d_server_config {
+  int32_t max_inflight;      /* work slots, i.e. requests on the GPU at once (>= 1) */
+  int32_t max_batch;         /* requests of one scene deformed by one launch (>= 1) */
+  int64_t hbm_budget_bytes;  /* device memory all slots may hold together */
+  float pairs_per_gaussian;  /* first tile-pair capacity guess per Gaussian (grown on overflow) */
+} fs4d_server_config;
+typedef struct fs4d_request {
+  fs4d_scene_id scene;
+  fs4d_precision prec;
+  fs4d_camera cam;
+  float t;
+  float* out;                /* [height][width][3]: DEVICE pointer if out_on_device, else HOST
+                                pointer (page-locked memory keeps the copy asynchronous) */
+  int32_t out_on_device;
+} fs4d_request;
+typedef struct fs4d_completion {
+  uint64_t ticket;
+  int32_t status;            /* FS4D_OK, or why this request failed */
+  int32_t slot;              /* work slot that ran it (-1 if none) */
+  int64_t pairs;             /* tile pairs of the frame */
+  double submit_ms, start_ms, done_ms; /* host clock, ms since the server started */
+} fs4d_completion;
+typedef struct fs4d_server_stats {
+  int64_t submitted, completed, failed, retried, batches, deformed;
+  int32_t slots, max_concurrent;
+  int64_t slot_bytes, peak_slot_bytes;
+} fs4d_server_stats;
+
+/* Start a server on the context (at most one per context). */
+FS4D_API fs4d_status fs4d_server_create(fs4d_ctx* ctx, const fs4d_server_config* cfg, fs4d_server** out);
+/* Queue a request; *ticket identifies its completion.  Thread-safe. */
+FS4D_API fs4d_status fs4d_server_submit(fs4d_server* srv, const fs4d_request* req, uint64_t* ticket);
+/* Queue n requests at once (they enter the queue together, so requests of one
+ * scene among them can share a deformation launch); tickets[n]. */
+FS4D_API fs4d_status fs4d_server_submit_batch(fs4d_server* srv, const fs4d_request* reqs, int32_t n,
+                                              uint64_t* tickets);
+/* Remove a still-queued request (it completes with FS4D_ERR_CANCELLED);
+ * FS4D_ERR_NOT_FOUND if it already started or finished. */
+FS4D_API fs4d_status fs4d_server_cancel(fs4d_server* srv, uint64_t ticket);
+/* Move up to max finished requests into out[]; *n_out = how many. */
+FS4D_API fs4d_status fs4d_server_poll(fs4d_server* srv, fs4d_completion* out, int32_t max, int32_t* n_out);
+/* Block until nothing is queued or in flight. */
+FS4D_API fs4d_status fs4d_server_drain(fs4d_server* srv);
+FS4D_API fs4d_status fs4d_server_stats_get(fs4d_server* srv, fs4d_server_stats* out);
+/* Stop: queued requests complete with FS4D_ERR_CANCELLED, in-flight ones finish. */
+FS4D_API fs4d_status fs4d_server_destroy(fs4d_server* srv);
 
 /* ---------------------------------------------------------------- stages
  * Stateless stages of the path on caller-owned device buffers, so that each can

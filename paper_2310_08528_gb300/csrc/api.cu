@@ -2,11 +2,18 @@
 // launch sequence deform -> project -> scan/emit -> radix sort -> ranges ->
 // composite.  See include/fs4d.h for the contract of every call.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "fs4d_internal.cuh"
@@ -55,6 +62,8 @@ struct Scene {
   size_t planes_floats = 0, mlp_floats = 0;
   size_t resident = 0;
   bool bf16_ok = false;
+  std::atomic<int> refs{0};   // serving requests in flight on this scene
+  bool dying = false;         // being unloaded: no new serving launches
   // capacity-mode reservation
   long long reserved_pairs = 0;
   int reserved_w = 0, reserved_h = 0;
@@ -95,7 +104,11 @@ struct fs4d_frame {
   DevBuf t_final, n_contrib;                   // per pixel
 };
 
+struct fs4d_server;
+
 struct fs4d_ctx {
+  std::mutex mu;                 // guards the scene map (the serving thread reads it)
+  fs4d_server* server = nullptr;
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -311,18 +324,19 @@ void free_scene(Scene* s) {
 }
 
 fs4d_status get_scene(fs4d_ctx* c, fs4d_scene_id id, Scene** out) {
+  std::lock_guard<std::mutex> lock(c->mu);
   auto it = c->scenes.find(id);
-  if (it == c->scenes.end()) return fail(c, FS4D_ERR_NOT_FOUND, "unknown scene id " + std::to_string(id));
+  if (it == c->scenes.end() || it->second->dying)
+    return fail(c, FS4D_ERR_NOT_FOUND, "unknown scene id " + std::to_string(id));
   *out = it->second;
   return FS4D_OK;
 }
 
 // Grow the per-Gaussian / per-tile / per-pair work buffers.
-fs4d_status ensure_work(fs4d_ctx* c, int n, int n_tiles, long long pairs) {
-  Work& w = c->w;
+fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_tiles, long long pairs) {
   bool grow = n > w.cap_n || n_tiles > w.cap_tiles || pairs > w.cap_pairs;
   if (!grow) return FS4D_OK;
-  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(stream));
   if (n > w.cap_n) {
     const size_t m = (size_t)n;
     FS4D_CUDA(c, ensure(w.dmeans, 12 * m));
@@ -358,13 +372,35 @@ fs4d_status ensure_work(fs4d_ctx* c, int n, int n_tiles, long long pairs) {
   return FS4D_OK;
 }
 
-SortWork sort_work(fs4d_ctx* c) {
+fs4d_status ensure_work(fs4d_ctx* c, int n, int n_tiles, long long pairs) {
+  return ensure_work(c, c->w, c->stream, n, n_tiles, pairs);
+}
+
+SortWork sort_work(Work& w) {
   SortWork sw;
-  sw.hist = P<uint32_t>(c->w.hist);
-  sw.lookback = P<uint32_t>(c->w.sort_lb);
-  sw.part_counters = P<uint32_t>(c->w.counters) + 8;
-  sw.max_parts = c->w.sort_parts_cap;
+  sw.hist = P<uint32_t>(w.hist);
+  sw.lookback = P<uint32_t>(w.sort_lb);
+  sw.part_counters = P<uint32_t>(w.counters) + 8;
+  sw.max_parts = w.sort_parts_cap;
   return sw;
+}
+
+SortWork sort_work(fs4d_ctx* c) { return sort_work(c->w); }
+
+// Where one frame's launches go: work memory, stream, status word, and whether
+// the context's stage-timing events are recorded.
+struct Env {
+  fs4d_ctx* c;
+  Work* w;
+  cudaStream_t s;
+  uint32_t* status;
+  bool timed;
+};
+
+Env env_of(fs4d_ctx* c) { return Env{c, &c->w, c->stream, P<uint32_t>(c->status), true}; }
+
+void mark(const Env& e, int i) {
+  if (e.timed) mark(e.c, i);
 }
 
 DeformArgs deform_args(Scene* s, const float* ts, float t0, int n_t, float* om, float* oq, float* os) {
@@ -383,28 +419,38 @@ DeformArgs deform_args(Scene* s, const float* ts, float t0, int n_t, float* om, 
   return a;
 }
 
-fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformArgs& a) {
+fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformArgs& a, cudaStream_t stream,
+                       uint32_t* status) {
   DeformArgs b = a;
-  b.status = P<uint32_t>(c->status);
+  b.status = status;
   if (prec == FS4D_BF16) {
     if (!s->bf16_ok) return fail(c, FS4D_ERR_UNIMPLEMENTED, "BF16 deformation does not support this scene shape");
-    FS4D_CUDA(c, launch_deform_bf16(b, c->stream));
+    FS4D_CUDA(c, launch_deform_bf16(b, stream));
   } else {
-    FS4D_CUDA(c, launch_deform_fp32(b, c->stream));
+    FS4D_CUDA(c, launch_deform_fp32(b, stream));
   }
   return FS4D_OK;
 }
 
+fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformArgs& a) {
+  return run_deform(c, s, prec, a, c->stream, P<uint32_t>(c->status));
+}
+
 // Everything of a frame up to (and including) the key emission.
-fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
-                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report) {
-  Work& w = c->w;
+fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
+                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
+                        bool deform = true) {
+  fs4d_ctx* c = e.c;
+  Work& w = *e.w;
+  const cudaStream_t stream = e.s;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
-  mark(c, 0);
-  DeformArgs da = deform_args(s, d_t, t, 1, P<float>(w.dmeans), P<float>(w.dquats), P<float>(w.dscales));
-  fs4d_status st = run_deform(c, s, prec, da);
-  if (st != FS4D_OK) return st;
-  mark(c, 1);
+  mark(e, 0);
+  if (deform) {
+    DeformArgs da = deform_args(s, d_t, t, 1, P<float>(w.dmeans), P<float>(w.dquats), P<float>(w.dscales));
+    fs4d_status st = run_deform(c, s, prec, da, stream, e.status);
+    if (st != FS4D_OK) return st;
+  }
+  mark(e, 1);
   ProjectArgs pa{};
   pa.n = s->n;
   pa.means = P<float>(w.dmeans); pa.quats = P<float>(w.dquats); pa.log_scales = P<float>(w.dscales);
@@ -414,13 +460,13 @@ fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   pa.tiles_x = tx; pa.tiles_y = ty;
   pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
   pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
-  FS4D_CUDA(c, launch_project(pa, c->stream));
-  mark(c, 2);
+  FS4D_CUDA(c, launch_project(pa, stream));
+  mark(e, 2);
   const int key_bits = 32 + ceil_log2((long long)tx * ty);
-  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, c->stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), stream));
   EmitArgs ea{};
   ea.n = s->n; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
   ea.capacity = cap;
@@ -432,35 +478,46 @@ fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
   ea.hist = P<uint32_t>(w.hist);
   ea.passes = sort_passes(key_bits);
-  ea.status = P<uint32_t>(c->status);
+  ea.status = e.status;
   ea.report_overflow = report ? 1 : 0;
-  FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
-  mark(c, 3);
+  FS4D_CUDA(c, launch_scan_emit(ea, stream));
+  mark(e, 3);
   return FS4D_OK;
 }
 
+fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
+                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report) {
+  return frame_front(env_of(c), s, prec, shape, d_cam, d_t, t, cap, report);
+}
+
 // Sort, ranges and composite with n_dev = the sortable pair count on device.
-fs4d_status frame_back(fs4d_ctx* c, const fs4d_camera& shape, long long n_bound, float* d_image, float* d_t_final,
-                       int* d_n_contrib) {
-  Work& w = c->w;
+fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound, float* d_image, float* d_t_final,
+                       int* d_n_contrib, uint32_t** values_out) {
+  fs4d_ctx* c = e.c;
+  Work& w = *e.w;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
   const int key_bits = 32 + ceil_log2((long long)tx * ty);
   const uint32_t* n_dev = P<uint32_t>(w.num_pairs) + 1;
   bool alt = false;
-  mark(c, 4);
+  mark(e, 4);
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), n_dev, n_bound, key_bits, true, sort_work(c),
-                           P<uint32_t>(c->status), c->stream, &alt));
+                           P<uint32_t>(w.values_alt), n_dev, n_bound, key_bits, true, sort_work(w), e.status, e.s,
+                           &alt));
   unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
-  c->last_values = values;
-  mark(c, 5);
-  FS4D_CUDA(c, launch_ranges(keys, n_dev, n_bound, P<uint2>(w.ranges), tx * ty, c->stream));
-  mark(c, 6);
+  if (values_out) *values_out = values;
+  mark(e, 5);
+  FS4D_CUDA(c, launch_ranges(keys, n_dev, n_bound, P<uint2>(w.ranges), tx * ty, e.s));
+  mark(e, 6);
   FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values, P<float2>(w.xy),
-                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, c->stream));
-  mark(c, 7);
+                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s));
+  mark(e, 7);
   return FS4D_OK;
+}
+
+fs4d_status frame_back(fs4d_ctx* c, const fs4d_camera& shape, long long n_bound, float* d_image, float* d_t_final,
+                       int* d_n_contrib) {
+  return frame_back(env_of(c), shape, n_bound, d_image, d_t_final, d_n_contrib, &c->last_values);
 }
 
 fs4d_status read_pairs(fs4d_ctx* c, long long* K) {
@@ -517,6 +574,7 @@ fs4d_status fs4d_create(int32_t device, void* cuda_stream, fs4d_ctx** out) {
 
 fs4d_status fs4d_destroy(fs4d_ctx* c) {
   if (!c) return FS4D_ERR_INVALID_ARG;
+  if (c->server) fs4d_server_destroy(c->server);
   {
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
@@ -607,6 +665,7 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
     if ((st = upload(c, s->tc_bias, bias.data(), bias.size(), &acc)) != FS4D_OK) return bail(st);
   }
   s->resident = acc;
+  std::lock_guard<std::mutex> lock(c->mu);
   const int id = c->next_id++;
   c->scenes[id] = s;
   *out = id;
@@ -619,9 +678,22 @@ fs4d_status fs4d_unload_scene(fs4d_ctx* c, fs4d_scene_id id) {
   fs4d_status st = get_scene(c, id, &s);
   if (st != FS4D_OK) return st;
   DeviceGuard g(c->device);
+  {
+    std::lock_guard<std::mutex> lock(c->mu);
+    s->dying = true;  // the serving thread launches nothing new on it
+  }
+  for (int i = 0; i < 200000 && s->refs.load() > 0; ++i) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  if (s->refs.load() > 0) {
+    std::lock_guard<std::mutex> lock(c->mu);
+    s->dying = false;
+    return fail(c, FS4D_ERR_TIMEOUT, "unload_scene: serving requests on this scene did not finish");
+  }
   cudaStreamSynchronize(c->stream);
+  {
+    std::lock_guard<std::mutex> lock(c->mu);
+    c->scenes.erase(id);
+  }
   free_scene(s);
-  c->scenes.erase(id);
   return FS4D_OK;
 }
 
@@ -1038,6 +1110,573 @@ fs4d_status fs4d_composite(fs4d_ctx* c, int32_t width, int32_t height, const uin
   FS4D_CUDA(c, launch_composite(width, height, reinterpret_cast<const uint2*>(d_ranges), d_values,
                                 reinterpret_cast<const float2*>(d_xy), reinterpret_cast<const float4*>(d_conic_opacity),
                                 d_rgb, d_image, d_t_final, d_n_contrib, c->stream));
+  return FS4D_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== serving
+// Continuous batching: a scheduler thread admits queued requests into work
+// slots (each with its own stream, work memory and cached CUDA graphs) while
+// device memory allows, deforms the admitted requests of one scene in one
+// launch, and retires slots as their completion events fire.
+
+namespace {
+
+struct SReq {
+  uint64_t ticket = 0;
+  fs4d_request r{};
+  double submit_ms = 0;
+  long long pairs_hint = 0;
+  int retries = 0;
+};
+
+struct GraphKey {
+  int scene, w, h, prec;
+  long long cap;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(scene, w, h, prec, cap) < std::tie(o.scene, o.w, o.h, o.prec, o.cap);
+  }
+};
+
+struct Slot {
+  int id = 0;
+  Work w;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  DevBuf status, dcam, dt, image;
+  fs4d_camera* h_cam = nullptr;  // pinned staging
+  float* h_t = nullptr;
+  uint32_t* h_out = nullptr;     // [0] status word, [1] tile pairs
+  int cap_w = 0, cap_h = 0;
+  size_t bytes = 0;
+  bool busy = false;
+  SReq req;
+  double start_ms = 0;
+  Scene* scene = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+struct Staging {
+  DevBuf ts, tab;
+  float* h_ts = nullptr;
+  float** h_tab = nullptr;
+  cudaEvent_t used = nullptr;
+};
+
+size_t slot_bytes_for(int n, int w, int h, long long pairs) {
+  const size_t tiles = (size_t)tiles_of(w) * tiles_of(h);
+  return (size_t)n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4) + 8 * (size_t)(emit_parts(n) + 1) +
+         (size_t)pairs * 24 + 4 * 256 * (size_t)kSortMaxPasses * sort_parts(pairs) + tiles * 8 +
+         (size_t)w * h * 12 + 4096;
+}
+
+}  // namespace
+
+struct fs4d_server {
+  fs4d_ctx* c = nullptr;
+  fs4d_server_config cfg{};
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<SReq> pending;
+  std::vector<fs4d_completion> done;
+  std::vector<Slot*> slots;
+  uint64_t next_ticket = 1;
+  std::chrono::steady_clock::time_point t0;
+  cudaStream_t dstream = nullptr;
+  DevBuf dstatus;  // status word of the batched deformation launches
+  std::vector<Staging> staging;
+  int staging_next = 0;
+  std::map<std::tuple<int, int, int>, double> ppg;  // observed pairs per Gaussian per (scene, w, h)
+  fs4d_server_stats stats{};
+  int busy = 0;
+  double now() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+void complete(fs4d_server* sv, const SReq& q, int32_t status, int slot, long long pairs, double start_ms) {
+  fs4d_completion d{};
+  d.ticket = q.ticket;
+  d.status = status;
+  d.slot = slot;
+  d.pairs = pairs;
+  d.submit_ms = q.submit_ms;
+  d.start_ms = start_ms;
+  d.done_ms = sv->now();
+  std::lock_guard<std::mutex> lock(sv->mu);
+  sv->done.push_back(d);
+  if (status == FS4D_OK)
+    sv->stats.completed++;
+  else
+    sv->stats.failed++;
+  sv->cv.notify_all();
+}
+
+// Retire finished slots; a frame that overflowed its pair capacity is queued again.
+void poll_slots(fs4d_server* sv) {
+  for (Slot* sl : sv->slots) {
+    if (!sl->busy) continue;
+    const cudaError_t e = cudaEventQuery(sl->done);
+    if (e == cudaErrorNotReady) continue;
+    const uint32_t st = sl->h_out[0];
+    const long long K = sl->h_out[1];
+    sl->scene->refs--;
+    sl->busy = false;
+    const std::tuple<int, int, int> key{sl->req.r.scene, sl->req.r.cam.width, sl->req.r.cam.height};
+    const double ratio = (double)K / std::max(1, sl->scene->n);
+    if (e != cudaSuccess) {
+      complete(sv, sl->req, FS4D_ERR_CUDA, sl->id, K, sl->start_ms);
+    } else if (st & kStatusCapacity) {
+      SReq q = sl->req;
+      q.retries++;
+      q.pairs_hint = std::max<long long>(K + K / 4, 2 * sl->w.cap_pairs);
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->ppg[key] = std::max(sv->ppg[key], ratio);
+        sv->stats.retried++;
+      }
+      if (q.retries > 4) {
+        complete(sv, q, FS4D_ERR_CAPACITY, sl->id, K, sl->start_ms);
+      } else {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->pending.push_front(q);
+      }
+    } else if (st & kStatusTimeout) {
+      complete(sv, sl->req, FS4D_ERR_TIMEOUT, sl->id, K, sl->start_ms);
+    } else {
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->ppg[key] = std::max(sv->ppg[key], ratio);
+      }
+      complete(sv, sl->req, FS4D_OK, sl->id, K, sl->start_ms);
+    }
+    std::lock_guard<std::mutex> lock(sv->mu);  // after the completion or the re-queue: drain sees no gap
+    sv->busy--;
+  }
+}
+
+Slot* new_slot(fs4d_server* sv) {
+  Slot* sl = new Slot();
+  sl->id = (int)sv->slots.size();
+  if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&sl->h_cam, sizeof(fs4d_camera)) != cudaSuccess ||
+      cudaMallocHost(&sl->h_t, sizeof(float)) != cudaSuccess ||
+      cudaMallocHost(&sl->h_out, 4 * sizeof(uint32_t)) != cudaSuccess || ensure(sl->status, 16) != cudaSuccess ||
+      ensure(sl->dcam, sizeof(fs4d_camera)) != cudaSuccess || ensure(sl->dt, 16) != cudaSuccess) {
+    return nullptr;  // (leaks a partly built slot only when the device is out of memory)
+  }
+  sv->slots.push_back(sl);
+  return sl;
+}
+
+// Make the slot hold a frame of n Gaussians at w x h with `pairs` capacity.
+fs4d_status fit_slot(fs4d_server* sv, Slot* sl, int n, int w, int h, long long pairs) {
+  fs4d_ctx* c = sv->c;
+  const void* before[4] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->image.p};
+  fs4d_status st = ensure_work(c, sl->w, sl->stream, n, tiles_of(w) * tiles_of(h), pairs);
+  if (st != FS4D_OK) return st;
+  if ((size_t)w * h * 12 > sl->image.bytes) FS4D_CUDA(c, ensure(sl->image, (size_t)w * h * 12));
+  const void* after[4] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->image.p};
+  if (std::memcmp(before, after, sizeof(before)) != 0) {  // graphs captured on old buffers are stale
+    cudaStreamSynchronize(sl->stream);
+    for (auto& kv : sl->graphs) cudaGraphExecDestroy(kv.second);
+    sl->graphs.clear();
+  }
+  sl->cap_w = std::max(sl->cap_w, w);
+  sl->cap_h = std::max(sl->cap_h, h);
+  const size_t b = slot_bytes_for(sl->w.cap_n, sl->cap_w, sl->cap_h, sl->w.cap_pairs);
+  sv->stats.slot_bytes += (int64_t)b - (int64_t)sl->bytes;
+  sl->bytes = b;
+  sv->stats.peak_slot_bytes = std::max(sv->stats.peak_slot_bytes, sv->stats.slot_bytes);
+  return FS4D_OK;
+}
+
+// The frame of one request, from its deformed Gaussians on, on the slot's stream
+// (graph replay once captured for this scene/resolution/precision/capacity).
+fs4d_status run_slot_frame(fs4d_server* sv, Slot* sl, Scene* s, const fs4d_request& r) {
+  fs4d_ctx* c = sv->c;
+  Env e{c, &sl->w, sl->stream, P<uint32_t>(sl->status), false};
+  const long long cap = sl->w.cap_pairs;
+  const GraphKey key{r.scene, r.cam.width, r.cam.height, (int)r.prec, cap};
+  auto it = sl->graphs.find(key);
+  if (it != sl->graphs.end()) {
+    FS4D_CUDA(c, cudaGraphLaunch(it->second, sl->stream));
+    return FS4D_OK;
+  }
+  // first frame of this kind on the slot: run it directly, then capture it
+  const fs4d_camera* dcam = P<fs4d_camera>(sl->dcam);
+  const float* dt = P<float>(sl->dt);
+  float* img = P<float>(sl->image);
+  fs4d_status st = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false);
+  if (st == FS4D_OK) st = frame_back(e, r.cam, cap, img, nullptr, nullptr, nullptr);
+  if (st != FS4D_OK) return st;
+  cudaGraph_t g = nullptr;
+  FS4D_CUDA(c, cudaStreamBeginCapture(sl->stream, cudaStreamCaptureModeThreadLocal));
+  fs4d_status st2 = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false);
+  if (st2 == FS4D_OK) st2 = frame_back(e, r.cam, cap, img, nullptr, nullptr, nullptr);
+  const cudaError_t ce = cudaStreamEndCapture(sl->stream, &g);
+  if (st2 != FS4D_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st2;
+  }
+  FS4D_CUDA(c, ce);
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  FS4D_CUDA(c, ie);
+  sl->graphs[key] = ex;
+  return FS4D_OK;
+}
+
+// Admit a batch of queued requests that share the head request's scene and
+// precision, as far as slots and the device-memory budget allow.
+void admit_and_launch(fs4d_server* sv) {
+  fs4d_ctx* c = sv->c;
+  std::vector<std::pair<SReq, Slot*>> batch;
+  Scene* scene = nullptr;
+  {
+    std::unique_lock<std::mutex> lock(sv->mu);
+    if (sv->pending.empty()) return;
+    const fs4d_scene_id sid = sv->pending.front().r.scene;
+    const fs4d_precision prec = sv->pending.front().r.prec;
+    {
+      std::lock_guard<std::mutex> cl(c->mu);
+      auto it = c->scenes.find(sid);
+      if (it != c->scenes.end() && !it->second->dying) {
+        scene = it->second;
+        scene->refs++;  // provisional: keeps the scene alive while the batch forms
+      }
+    }
+    if (!scene) {  // unknown or unloaded scene: fail every queued request on it
+      std::deque<SReq> keep;
+      std::vector<SReq> bad;
+      for (SReq& q : sv->pending) {
+        if (q.r.scene == sid)
+          bad.push_back(q);
+        else
+          keep.push_back(q);
+      }
+      sv->pending.swap(keep);
+      lock.unlock();
+      for (SReq& q : bad) complete(sv, q, FS4D_ERR_NOT_FOUND, -1, 0, sv->now());
+      return;
+    }
+    std::vector<bool> taken(sv->slots.size(), false);
+    int64_t projected = sv->stats.slot_bytes;
+    for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)batch.size() < sv->cfg.max_batch;) {
+      SReq& q = *it;
+      if (q.r.scene != sid || q.r.prec != prec) {
+        ++it;
+        continue;
+      }
+      const auto key = std::make_tuple(q.r.scene, q.r.cam.width, q.r.cam.height);
+      const double ratio = sv->ppg.count(key) ? sv->ppg[key] : (double)sv->cfg.pairs_per_gaussian;
+      const long long want = std::max<long long>(q.pairs_hint, (long long)(1.3 * ratio * scene->n) + 4096);
+      // a free slot that already fits, else a free slot to grow, else a new slot
+      Slot* pick = nullptr;
+      bool fits = false;
+      for (size_t i = 0; i < sv->slots.size(); ++i) {
+        Slot* sl = sv->slots[i];
+        if (sl->busy || taken[i]) continue;
+        if (sl->w.cap_n >= scene->n && sl->w.cap_pairs >= want && sl->cap_w >= q.r.cam.width &&
+            sl->cap_h >= q.r.cam.height) {
+          pick = sl;
+          fits = true;
+          break;
+        }
+        if (!pick) pick = sl;
+      }
+      if (!fits) {
+        const size_t need = slot_bytes_for(std::max(scene->n, pick ? pick->w.cap_n : 0),
+                                           std::max(q.r.cam.width, pick ? pick->cap_w : 0),
+                                           std::max(q.r.cam.height, pick ? pick->cap_h : 0),
+                                           std::max(want, pick ? pick->w.cap_pairs : 0));
+        const int64_t have = pick ? (int64_t)pick->bytes : 0;
+        const bool room = projected - have + (int64_t)need <= sv->cfg.hbm_budget_bytes;
+        if (!room && batch.empty() && sv->busy == 0 && (int64_t)need > sv->cfg.hbm_budget_bytes) {
+          SReq qq = q;  // can never fit: fail it instead of waiting forever
+          sv->pending.erase(it);
+          lock.unlock();
+          complete(sv, qq, FS4D_ERR_OOM, -1, 0, sv->now());
+          lock.lock();
+          break;
+        }
+        if (!room) break;  // wait until device memory frees up
+        if (!pick) {
+          if ((int)sv->slots.size() >= sv->cfg.max_inflight) break;  // wait for a slot
+          pick = new_slot(sv);
+          if (!pick) break;
+          taken.push_back(false);
+        }
+        projected += (int64_t)need - have;
+      }
+      taken[(size_t)pick->id] = true;
+      batch.emplace_back(q, pick);
+      it = sv->pending.erase(it);
+    }
+    scene->refs += (int)batch.size() - 1;  // the provisional reference becomes the batch's
+    sv->busy += (int)batch.size();          // in flight from now on (drain waits for them)
+  }
+  if (batch.empty()) return;
+  // grow the slots that need it (outside the queue lock)
+  for (size_t i = 0; i < batch.size();) {
+    const SReq& q = batch[i].first;
+    Slot* sl = batch[i].second;
+    const auto key = std::make_tuple(q.r.scene, q.r.cam.width, q.r.cam.height);
+    double ratio;
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      ratio = sv->ppg.count(key) ? sv->ppg[key] : (double)sv->cfg.pairs_per_gaussian;
+    }
+    const long long want = std::max<long long>(q.pairs_hint, (long long)(1.3 * ratio * scene->n) + 4096);
+    if (fit_slot(sv, sl, scene->n, q.r.cam.width, q.r.cam.height, want) != FS4D_OK) {
+      scene->refs--;
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->busy--;
+      }
+      complete(sv, q, FS4D_ERR_OOM, sl->id, 0, sv->now());
+      batch.erase(batch.begin() + (long)i);
+      continue;
+    }
+    ++i;
+  }
+  if (batch.empty()) return;
+  // one deformation launch for the whole batch, written into each slot
+  Staging& sg = sv->staging[(size_t)(sv->staging_next++ % (int)sv->staging.size())];
+  cudaEventSynchronize(sg.used);
+  const int nb = (int)batch.size();
+  for (int i = 0; i < nb; ++i) {
+    Slot* sl = batch[i].second;
+    sg.h_ts[i] = batch[i].first.r.t;
+    sg.h_tab[3 * i] = P<float>(sl->w.dmeans);
+    sg.h_tab[3 * i + 1] = P<float>(sl->w.dquats);
+    sg.h_tab[3 * i + 2] = P<float>(sl->w.dscales);
+  }
+  bool ok = cudaMemcpyAsync(sg.ts.p, sg.h_ts, 4 * (size_t)nb, cudaMemcpyHostToDevice, sv->dstream) == cudaSuccess &&
+            cudaMemcpyAsync(sg.tab.p, sg.h_tab, 3 * sizeof(float*) * (size_t)nb, cudaMemcpyHostToDevice,
+                            sv->dstream) == cudaSuccess;
+  DeformArgs da = deform_args(scene, P<float>(sg.ts), 0.f, nb, nullptr, nullptr, nullptr);
+  da.out_tab = P<float*>(sg.tab);
+  const fs4d_precision prec = batch[0].first.r.prec;
+  ok = ok && run_deform(c, scene, prec, da, sv->dstream, P<uint32_t>(sv->dstatus)) == FS4D_OK;
+  ok = ok && cudaEventRecord(sg.used, sv->dstream) == cudaSuccess;
+  sv->stats.batches++;
+  sv->stats.deformed += nb;
+  for (auto& bq : batch) {
+    Slot* sl = bq.second;
+    const fs4d_request& r = bq.first.r;
+    sl->req = bq.first;
+    sl->scene = scene;
+    sl->start_ms = sv->now();
+    *sl->h_cam = r.cam;
+    *sl->h_t = r.t;
+    bool sok = ok && cudaStreamWaitEvent(sl->stream, sg.used, 0) == cudaSuccess &&
+               cudaMemcpyAsync(sl->dcam.p, sl->h_cam, sizeof(fs4d_camera), cudaMemcpyHostToDevice, sl->stream) ==
+                   cudaSuccess &&
+               cudaMemcpyAsync(sl->dt.p, sl->h_t, 4, cudaMemcpyHostToDevice, sl->stream) == cudaSuccess &&
+               cudaMemsetAsync(sl->status.p, 0, 4, sl->stream) == cudaSuccess;
+    sok = sok && run_slot_frame(sv, sl, scene, r) == FS4D_OK;
+    const size_t bytes = (size_t)r.cam.width * r.cam.height * 12;
+    sok = sok && cudaMemcpyAsync(r.out, sl->image.p, bytes,
+                                 r.out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 sl->stream) == cudaSuccess;
+    sok = sok && cudaMemcpyAsync(sl->h_out, sl->status.p, 4, cudaMemcpyDeviceToHost, sl->stream) == cudaSuccess &&
+          cudaMemcpyAsync(sl->h_out + 1, sl->w.num_pairs.p, 4, cudaMemcpyDeviceToHost, sl->stream) == cudaSuccess &&
+          cudaEventRecord(sl->done, sl->stream) == cudaSuccess;
+    if (!sok) {
+      scene->refs--;
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->busy--;
+      }
+      complete(sv, bq.first, FS4D_ERR_CUDA, sl->id, 0, sl->start_ms);
+      continue;
+    }
+    sl->busy = true;
+    int on_gpu = 0;
+    for (Slot* x : sv->slots) on_gpu += x->busy ? 1 : 0;
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, on_gpu);
+  }
+}
+
+void serve_loop(fs4d_server* sv) {
+  cudaSetDevice(sv->c->device);
+  for (;;) {
+    poll_slots(sv);
+    admit_and_launch(sv);
+    std::unique_lock<std::mutex> lock(sv->mu);
+    if (sv->stop && !sv->pending.empty()) {  // stopping: cancel what never started
+      std::deque<SReq> q;
+      q.swap(sv->pending);
+      lock.unlock();
+      for (SReq& r : q) complete(sv, r, FS4D_ERR_CANCELLED, -1, 0, sv->now());
+      continue;
+    }
+    if (sv->stop && sv->busy == 0) break;
+    sv->cv.notify_all();
+    // sleep briefly: new work or a completion event will be there soon
+    sv->cv.wait_for(lock, std::chrono::microseconds(sv->busy ? 20 : 200));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+fs4d_status fs4d_server_create(fs4d_ctx* c, const fs4d_server_config* cfg, fs4d_server** out) {
+  if (!c || !cfg || !out) return FS4D_ERR_INVALID_ARG;
+  if (cfg->max_inflight < 1 || cfg->max_batch < 1 || cfg->hbm_budget_bytes <= 0 || !(cfg->pairs_per_gaussian > 0))
+    return fail(c, FS4D_ERR_INVALID_ARG, "server: max_inflight, max_batch, budget and pairs_per_gaussian > 0");
+  if (c->server) return fail(c, FS4D_ERR_INVALID_ARG, "server: this context already has one");
+  DeviceGuard g(c->device);
+  fs4d_server* sv = new fs4d_server();
+  sv->c = c;
+  sv->cfg = *cfg;
+  sv->t0 = std::chrono::steady_clock::now();
+  if (cudaStreamCreateWithFlags(&sv->dstream, cudaStreamNonBlocking) != cudaSuccess ||
+      ensure(sv->dstatus, 16) != cudaSuccess || cudaMemset(sv->dstatus.p, 0, 16) != cudaSuccess) {
+    delete sv;
+    return fail(c, FS4D_ERR_CUDA, "server: stream creation failed");
+  }
+  sv->staging.resize(8);
+  for (Staging& s : sv->staging) {
+    if (ensure(s.ts, 4 * (size_t)cfg->max_batch) != cudaSuccess ||
+        ensure(s.tab, 3 * sizeof(float*) * (size_t)cfg->max_batch) != cudaSuccess ||
+        cudaMallocHost(&s.h_ts, 4 * (size_t)cfg->max_batch) != cudaSuccess ||
+        cudaMallocHost(&s.h_tab, 3 * sizeof(float*) * (size_t)cfg->max_batch) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.used, cudaEventDisableTiming) != cudaSuccess) {
+      delete sv;
+      return fail(c, FS4D_ERR_OOM, "server: staging allocation failed");
+    }
+  }
+  c->server = sv;
+  sv->th = std::thread(serve_loop, sv);
+  *out = sv;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_submit(fs4d_server* sv, const fs4d_request* r, uint64_t* ticket) {
+  if (!sv || !r || !ticket) return FS4D_ERR_INVALID_ARG;
+  if (!valid_cam(&r->cam) || !r->out || (r->prec != FS4D_FP32 && r->prec != FS4D_BF16)) return FS4D_ERR_INVALID_ARG;
+  SReq q;
+  q.r = *r;
+  q.submit_ms = sv->now();
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stop) return FS4D_ERR_CANCELLED;
+  q.ticket = sv->next_ticket++;
+  *ticket = q.ticket;
+  sv->pending.push_back(q);
+  sv->stats.submitted++;
+  sv->cv.notify_all();
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_submit_batch(fs4d_server* sv, const fs4d_request* reqs, int32_t n, uint64_t* tickets) {
+  if (!sv || n < 0 || (n > 0 && (!reqs || !tickets))) return FS4D_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!valid_cam(&reqs[i].cam) || !reqs[i].out || (reqs[i].prec != FS4D_FP32 && reqs[i].prec != FS4D_BF16))
+      return FS4D_ERR_INVALID_ARG;
+  const double now = sv->now();
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stop) return FS4D_ERR_CANCELLED;
+  for (int i = 0; i < n; ++i) {
+    SReq q;
+    q.r = reqs[i];
+    q.submit_ms = now;
+    q.ticket = sv->next_ticket++;
+    tickets[i] = q.ticket;
+    sv->pending.push_back(q);
+  }
+  sv->stats.submitted += n;
+  sv->cv.notify_all();
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_cancel(fs4d_server* sv, uint64_t ticket) {
+  if (!sv) return FS4D_ERR_INVALID_ARG;
+  SReq q;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = std::find_if(sv->pending.begin(), sv->pending.end(), [&](const SReq& x) { return x.ticket == ticket; });
+    if (it == sv->pending.end()) return FS4D_ERR_NOT_FOUND;
+    q = *it;
+    sv->pending.erase(it);
+  }
+  complete(sv, q, FS4D_ERR_CANCELLED, -1, 0, sv->now());
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_poll(fs4d_server* sv, fs4d_completion* out, int32_t max, int32_t* n_out) {
+  if (!sv || !n_out || (max > 0 && !out)) return FS4D_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  const int n = std::min<int>(max, (int)sv->done.size());
+  for (int i = 0; i < n; ++i) out[i] = sv->done[i];
+  sv->done.erase(sv->done.begin(), sv->done.begin() + n);
+  *n_out = n;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_drain(fs4d_server* sv) {
+  if (!sv) return FS4D_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  const bool ok = sv->cv.wait_for(lock, std::chrono::seconds(120), [&] { return sv->pending.empty() && sv->busy == 0; });
+  return ok ? FS4D_OK : FS4D_ERR_TIMEOUT;
+}
+
+fs4d_status fs4d_server_stats_get(fs4d_server* sv, fs4d_server_stats* out) {
+  if (!sv || !out) return FS4D_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  *out = sv->stats;
+  out->slots = (int32_t)sv->slots.size();
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_server_destroy(fs4d_server* sv) {
+  if (!sv) return FS4D_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stop = true;
+    sv->cv.notify_all();
+  }
+  if (sv->th.joinable()) sv->th.join();
+  fs4d_ctx* c = sv->c;
+  DeviceGuard g(c->device);
+  for (Slot* sl : sv->slots) {
+    cudaStreamSynchronize(sl->stream);
+    for (auto& kv : sl->graphs) cudaGraphExecDestroy(kv.second);
+    Work& w = sl->w;
+    DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
+                     &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &sl->status, &sl->dcam, &sl->dt,
+                     &sl->image};
+    for (DevBuf* b : all) release(*b);
+    cudaFreeHost(sl->h_cam);
+    cudaFreeHost(sl->h_t);
+    cudaFreeHost(sl->h_out);
+    cudaEventDestroy(sl->done);
+    cudaStreamDestroy(sl->stream);
+    delete sl;
+  }
+  cudaStreamSynchronize(sv->dstream);
+  for (Staging& s : sv->staging) {
+    release(s.ts);
+    release(s.tab);
+    if (s.h_ts) cudaFreeHost(s.h_ts);
+    if (s.h_tab) cudaFreeHost(s.h_tab);
+    if (s.used) cudaEventDestroy(s.used);
+  }
+  cudaStreamDestroy(sv->dstream);
+  release(sv->dstatus);
+  c->server = nullptr;
+  delete sv;
   return FS4D_OK;
 }
 

@@ -139,15 +139,18 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
     head<3>(sw, a.mg, 2, col, d);
     head<4>(sw, a.mg, 4, col, d + 3);
     head<3>(sw, a.mg, 6, col, d + 7);
-    const long long o = (long long)ti * a.n + g;
-    a.out_means[3 * o + 0] = X0 + d[0];
-    a.out_means[3 * o + 1] = X1 + d[1];
-    a.out_means[3 * o + 2] = X2 + d[2];
+    const long long o = a.out_tab ? g : (long long)ti * a.n + g;
+    float* om = a.out_tab ? a.out_tab[3 * ti] : a.out_means;
+    float* oq = a.out_tab ? a.out_tab[3 * ti + 1] : a.out_quats;
+    float* os = a.out_tab ? a.out_tab[3 * ti + 2] : a.out_log_scales;
+    om[3 * o + 0] = X0 + d[0];
+    om[3 * o + 1] = X1 + d[1];
+    om[3 * o + 2] = X2 + d[2];
     const float4 q = reinterpret_cast<const float4*>(a.quats)[g];
-    reinterpret_cast<float4*>(a.out_quats)[o] = make_float4(q.x + d[3], q.y + d[4], q.z + d[5], q.w + d[6]);
-    a.out_log_scales[3 * o + 0] = a.log_scales[3 * g + 0] + d[7];
-    a.out_log_scales[3 * o + 1] = a.log_scales[3 * g + 1] + d[8];
-    a.out_log_scales[3 * o + 2] = a.log_scales[3 * g + 2] + d[9];
+    reinterpret_cast<float4*>(oq)[o] = make_float4(q.x + d[3], q.y + d[4], q.z + d[5], q.w + d[6]);
+    os[3 * o + 0] = a.log_scales[3 * g + 0] + d[7];
+    os[3 * o + 1] = a.log_scales[3 * g + 1] + d[8];
+    os[3 * o + 2] = a.log_scales[3 * g + 2] + d[9];
   }
 }
 

@@ -332,15 +332,19 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
         const int ti = (int)(gi / a.n);
         const int g = (int)(gi - (long long)ti * a.n);
         const float* bo = sBias + 320;
-        a.out_means[3 * gi + 0] = a.means[3 * g + 0] + (v[0] + bo[0]);
-        a.out_means[3 * gi + 1] = a.means[3 * g + 1] + (v[1] + bo[1]);
-        a.out_means[3 * gi + 2] = a.means[3 * g + 2] + (v[2] + bo[2]);
+        const long long o = a.out_tab ? (long long)g : gi;
+        float* om = a.out_tab ? a.out_tab[3 * ti] : a.out_means;
+        float* oq = a.out_tab ? a.out_tab[3 * ti + 1] : a.out_quats;
+        float* os = a.out_tab ? a.out_tab[3 * ti + 2] : a.out_log_scales;
+        om[3 * o + 0] = a.means[3 * g + 0] + (v[0] + bo[0]);
+        om[3 * o + 1] = a.means[3 * g + 1] + (v[1] + bo[1]);
+        om[3 * o + 2] = a.means[3 * g + 2] + (v[2] + bo[2]);
         const float4 q = reinterpret_cast<const float4*>(a.quats)[g];
-        reinterpret_cast<float4*>(a.out_quats)[gi] =
+        reinterpret_cast<float4*>(oq)[o] =
             make_float4(q.x + (v[3] + bo[3]), q.y + (v[4] + bo[4]), q.z + (v[5] + bo[5]), q.w + (v[6] + bo[6]));
-        a.out_log_scales[3 * gi + 0] = a.log_scales[3 * g + 0] + (v[7] + bo[7]);
-        a.out_log_scales[3 * gi + 1] = a.log_scales[3 * g + 1] + (v[8] + bo[8]);
-        a.out_log_scales[3 * gi + 2] = a.log_scales[3 * g + 2] + (v[9] + bo[9]);
+        os[3 * o + 0] = a.log_scales[3 * g + 0] + (v[7] + bo[7]);
+        os[3 * o + 1] = a.log_scales[3 * g + 1] + (v[8] + bo[8]);
+        os[3 * o + 2] = a.log_scales[3 * g + 2] + (v[9] + bo[9]);
       }
     }
     tc_fence_before();

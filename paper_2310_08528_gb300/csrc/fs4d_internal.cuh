@@ -67,6 +67,8 @@ struct DeformArgs {
   float* out_means;             // [n_t][n][3]
   float* out_quats;             // [n_t][n][4]
   float* out_log_scales;        // [n_t][n][3]
+  float* const* out_tab;        // optional [n_t][3] device table: per-timestamp output bases
+                                // (means [n][3], quats [n][4], log-scales [n][3]); overrides out_*
   const float* planes;          // float32 planes
   const __nv_bfloat16* planes_bf16;
   const float* mlp_t;           // FP32 transposed layout (MlpGeomT)

@@ -129,6 +129,7 @@ class Context:
         self._check(self.lib.fs4d_create(self.device, C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
         self.h = h
         self._scenes: Dict[int, object] = {}
+        self._servers = []
 
     def _check(self, rc: int, h) -> None:
         if rc != 0:
@@ -139,6 +140,8 @@ class Context:
         self._check(getattr(self.lib, name)(self.h, *args), self.h)
 
     def close(self) -> None:
+        for srv in getattr(self, "_servers", []):
+            srv.close()  # a server must stop before its context goes
         if getattr(self, "h", None):
             self.lib.fs4d_destroy(self.h)
             self.h = None
@@ -363,3 +366,133 @@ def render_differentiable(fs: "Context", sid: int, cam, t: float, params: Dict[s
     if _RF is None:
         _RF = _render_function()
     return _RF.apply(fs, sid, cam, float(t), prec, *[params[k] for k in PARAMS])
+
+
+# ---------------------------------------------------------------------- serving
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("max_batch", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("pairs_per_gaussian", C.c_float)]
+
+
+class Request(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("prec", C.c_int32), ("cam", Camera), ("t", C.c_float), ("out", C.c_void_p),
+                ("out_on_device", C.c_int32)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int32), ("slot", C.c_int32), ("pairs", C.c_int64),
+                ("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("retried", C.c_int64),
+                ("batches", C.c_int64), ("deformed", C.c_int64), ("slots", C.c_int32),
+                ("max_concurrent", C.c_int32), ("slot_bytes", C.c_int64), ("peak_slot_bytes", C.c_int64)]
+
+
+SERVER_EXPORTS = ("fs4d_server_create", "fs4d_server_submit", "fs4d_server_submit_batch", "fs4d_server_cancel",
+                  "fs4d_server_poll",
+                  "fs4d_server_drain", "fs4d_server_stats_get", "fs4d_server_destroy")
+EXPORTS = EXPORTS + SERVER_EXPORTS
+
+
+def _server_sigs(L):
+    vp = C.c_void_p
+    sig = {"fs4d_server_create": [vp, C.POINTER(ServerConfig), C.POINTER(vp)],
+           "fs4d_server_submit": [vp, C.POINTER(Request), C.POINTER(C.c_uint64)],
+           "fs4d_server_submit_batch": [vp, C.POINTER(Request), C.c_int32, C.POINTER(C.c_uint64)],
+           "fs4d_server_cancel": [vp, C.c_uint64],
+           "fs4d_server_poll": [vp, C.POINTER(Completion), C.c_int32, C.POINTER(C.c_int32)],
+           "fs4d_server_drain": [vp],
+           "fs4d_server_stats_get": [vp, C.POINTER(ServerStats)],
+           "fs4d_server_destroy": [vp]}
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+
+
+class Server:
+    """Continuous-batching render server on a Context (native scheduler thread)."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 8, max_batch: int = 8, hbm_budget_bytes: int = 16 << 30,
+                 pairs_per_gaussian: float = 16.0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        _server_sigs(self.lib)
+        cfg = ServerConfig(max_inflight, max_batch, hbm_budget_bytes, pairs_per_gaussian)
+        h = C.c_void_p()
+        ctx.call("fs4d_server_create", C.byref(cfg), C.byref(h))
+        self.h = h
+        self._keep: Dict[int, object] = {}
+        ctx._servers.append(self)
+
+    def _check(self, rc: int) -> None:
+        if rc != 0:
+            raise Fs4dError(rc, "server call failed")
+
+    def submit(self, sid: int, cam, t: float, out, prec: int = FP32) -> int:
+        """Queue a frame; out is a CUDA tensor (device output) or a numpy array (host output)."""
+        r = Request()
+        r.scene, r.prec, r.cam, r.t = sid, prec, camera_struct(cam), float(t)
+        if hasattr(out, "data_ptr"):
+            r.out, r.out_on_device = out.data_ptr(), 1
+        else:
+            r.out, r.out_on_device = out.ctypes.data, 0
+        tk = C.c_uint64()
+        self._check(self.lib.fs4d_server_submit(self.h, C.byref(r), C.byref(tk)))
+        self._keep[tk.value] = out
+        return tk.value
+
+    def _request(self, sid, cam, t, out, prec) -> Request:
+        r = Request()
+        r.scene, r.prec, r.cam, r.t = sid, prec, camera_struct(cam), float(t)
+        if hasattr(out, "data_ptr"):
+            r.out, r.out_on_device = out.data_ptr(), 1
+        else:
+            r.out, r.out_on_device = out.ctypes.data, 0
+        return r
+
+    def submit_batch(self, items):
+        """items: list of (sid, cam, t, out, prec); queued together.  Returns tickets."""
+        arr = (Request * len(items))(*[self._request(*it) for it in items])
+        tks = (C.c_uint64 * len(items))()
+        self._check(self.lib.fs4d_server_submit_batch(self.h, arr, len(items), tks))
+        for tk, it in zip(tks, items):
+            self._keep[tk] = it[3]
+        return list(tks)
+
+    def cancel(self, ticket: int) -> bool:
+        return self.lib.fs4d_server_cancel(self.h, C.c_uint64(ticket)) == 0
+
+    def poll(self, max_n: int = 256):
+        buf = (Completion * max_n)()
+        n = C.c_int32()
+        self._check(self.lib.fs4d_server_poll(self.h, buf, max_n, C.byref(n)))
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._keep.pop(c.ticket, None)
+            out.append(dict(ticket=c.ticket, status=c.status, slot=c.slot, pairs=c.pairs, submit_ms=c.submit_ms,
+                            start_ms=c.start_ms, done_ms=c.done_ms))
+        return out
+
+    def drain(self) -> None:
+        self._check(self.lib.fs4d_server_drain(self.h))
+
+    def stats(self) -> Dict[str, int]:
+        s = ServerStats()
+        self._check(self.lib.fs4d_server_stats_get(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.fs4d_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
