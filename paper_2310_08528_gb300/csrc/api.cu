@@ -74,6 +74,7 @@ struct Work {
   DevBuf dmeans, dquats, dscales;          // deformed Gaussians
   DevBuf xy, co, rgb, depth, radius, rect; // projected
   DevBuf offsets, emit_lb, counters, num_pairs, hist;
+  DevBuf dkeys, dvals, dkeys_alt, dvals_alt;  // per-Gaussian depth sort
   DevBuf keys, values, keys_alt, values_alt;
   DevBuf sort_lb;
   DevBuf ranges;
@@ -350,6 +351,10 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
     FS4D_CUDA(c, ensure(w.rect, 16 * m));
     FS4D_CUDA(c, ensure(w.offsets, 4 * m));
     FS4D_CUDA(c, ensure(w.emit_lb, 8 * (size_t)(emit_parts(n) + 1)));
+    FS4D_CUDA(c, ensure(w.dkeys, 8 * m));
+    FS4D_CUDA(c, ensure(w.dvals, 4 * m));
+    FS4D_CUDA(c, ensure(w.dkeys_alt, 8 * m));
+    FS4D_CUDA(c, ensure(w.dvals_alt, 4 * m));
     w.cap_n = n;
   }
   FS4D_CUDA(c, ensure(w.counters, 4 * kCounters));
@@ -365,9 +370,12 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
     FS4D_CUDA(c, ensure(w.values, 4 * (size_t)cap));
     FS4D_CUDA(c, ensure(w.keys_alt, 8 * (size_t)cap));
     FS4D_CUDA(c, ensure(w.values_alt, 4 * (size_t)cap));
-    w.sort_parts_cap = sort_parts(cap);
-    FS4D_CUDA(c, ensure(w.sort_lb, 4 * 256 * (size_t)kSortMaxPasses * w.sort_parts_cap));
     w.cap_pairs = cap;
+  }
+  const long long parts = std::max(sort_parts(std::max<long long>(w.cap_pairs, 4096)), sort_parts(w.cap_n));
+  if (parts > w.sort_parts_cap) {
+    FS4D_CUDA(c, ensure(w.sort_lb, 4 * 256 * (size_t)kSortMaxPasses * parts));
+    w.sort_parts_cap = parts;
   }
   return FS4D_OK;
 }
@@ -460,15 +468,22 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   pa.tiles_x = tx; pa.tiles_y = ty;
   pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
   pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
+  pa.depth_keys = P<unsigned long long>(w.dkeys); pa.depth_vals = P<uint32_t>(w.dvals);
   FS4D_CUDA(c, launch_project(pa, stream));
   mark(e, 2);
-  const int key_bits = 32 + ceil_log2((long long)tx * ty);
+  // Gaussians in (float32 depth, index) order: the emission order
+  bool dalt = false;
+  FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
+                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, false, sort_work(w), e.status, stream,
+                           &dalt));
+  const uint32_t* order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
+  const int tile_bits = ceil_log2((long long)tx * ty);
   FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), stream));
   EmitArgs ea{};
-  ea.n = s->n; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
+  ea.n = s->n; ea.order = order; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
   ea.capacity = cap;
   ea.keys = P<unsigned long long>(w.keys); ea.values = P<uint32_t>(w.values);
   ea.offsets = P<uint32_t>(w.offsets);
@@ -477,7 +492,8 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   ea.num_pairs = P<uint32_t>(w.num_pairs);
   ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
   ea.hist = P<uint32_t>(w.hist);
-  ea.passes = sort_passes(key_bits);
+  ea.hist_first_bit = 32;
+  ea.passes = sort_passes(tile_bits);
   ea.status = e.status;
   ea.report_overflow = report ? 1 : 0;
   FS4D_CUDA(c, launch_scan_emit(ea, stream));
@@ -496,13 +512,14 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   fs4d_ctx* c = e.c;
   Work& w = *e.w;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
-  const int key_bits = 32 + ceil_log2((long long)tx * ty);
+  const int tile_bits = ceil_log2((long long)tx * ty);
   const uint32_t* n_dev = P<uint32_t>(w.num_pairs) + 1;
   bool alt = false;
   mark(e, 4);
+  // pairs arrive in depth order: a stable sort on the tile bits gives (tile, depth, index)
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), n_dev, n_bound, key_bits, true, sort_work(w), e.status, e.s,
-                           &alt));
+                           P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, sort_work(w), e.status,
+                           e.s, &alt));
   unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
   if (values_out) *values_out = values;
@@ -708,7 +725,7 @@ fs4d_status fs4d_scene_bytes(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32
     const size_t n = (size_t)s->n;
     const size_t pairs = (size_t)(std::max(0.f, ppg) * (float)n) + 4096;
     const size_t tiles = (size_t)tiles_of(width) * tiles_of(height);
-    *per_frame = n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4) + pairs * 24 +
+    *per_frame = n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + pairs * 24 +
                  sort_parts((long long)pairs) * 256 * 4 * kSortMaxPasses + tiles * 8 +
                  (size_t)width * height * 12;
   }
@@ -1041,13 +1058,20 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   if (st != FS4D_OK) return st;
   Work& w = c->w;
   const int n_tiles = tiles_x * tiles_y;
-  const int key_bits = 32 + ceil_log2(n_tiles);
+  const int tile_bits = ceil_log2(n_tiles);
+  // emission order: Gaussians sorted by (float32 depth, index)
+  FS4D_CUDA(c, launch_depth_keys(d_depth, n, P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), c->stream));
+  bool dalt = false;
+  FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
+                           P<uint32_t>(w.dvals_alt), nullptr, n, 0, 32, false, sort_work(c), P<uint32_t>(c->status),
+                           c->stream, &dalt));
   FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(std::max(n, 1)), c->stream));
   EmitArgs ea{};
-  ea.n = n; ea.depth = d_depth; ea.rect = reinterpret_cast<const int4*>(d_rect); ea.tiles_x = tiles_x;
+  ea.n = n; ea.order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
+  ea.depth = d_depth; ea.rect = reinterpret_cast<const int4*>(d_rect); ea.tiles_x = tiles_x;
   ea.capacity = capacity;
   ea.keys = reinterpret_cast<unsigned long long*>(d_keys); ea.values = d_values;
   ea.offsets = P<uint32_t>(w.offsets);
@@ -1056,7 +1080,8 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   ea.num_pairs = P<uint32_t>(w.num_pairs);
   ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
   ea.hist = P<uint32_t>(w.hist);
-  ea.passes = sort_passes(key_bits);
+  ea.hist_first_bit = 32;
+  ea.passes = sort_passes(tile_bits);
   ea.status = P<uint32_t>(c->status);
   ea.report_overflow = 0;
   FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
@@ -1068,7 +1093,7 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   }
   bool alt = false;
   FS4D_CUDA(c, launch_sort(reinterpret_cast<unsigned long long*>(d_keys), d_values, P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), nullptr, K, key_bits, true, sort_work(c),
+                           P<uint32_t>(w.values_alt), nullptr, K, 32, tile_bits, true, sort_work(c),
                            P<uint32_t>(c->status), c->stream, &alt));
   if (alt && K > 0) {
     FS4D_CUDA(c, cudaMemcpyAsync(d_keys, w.keys_alt.p, 8 * (size_t)K, cudaMemcpyDeviceToDevice, c->stream));
@@ -1090,7 +1115,7 @@ fs4d_status fs4d_sort_pairs(fs4d_ctx* c, int64_t n, int32_t key_bits, uint64_t* 
   Work& w = c->w;
   bool alt = false;
   FS4D_CUDA(c, launch_sort(reinterpret_cast<unsigned long long*>(d_keys), d_values, P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), nullptr, n, key_bits, false, sort_work(c),
+                           P<uint32_t>(w.values_alt), nullptr, n, 0, key_bits, false, sort_work(c),
                            P<uint32_t>(c->status), c->stream, &alt));
   if (alt) {
     FS4D_CUDA(c, cudaMemcpyAsync(d_keys, w.keys_alt.p, 8 * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
@@ -1166,7 +1191,7 @@ struct Staging {
 
 size_t slot_bytes_for(int n, int w, int h, long long pairs) {
   const size_t tiles = (size_t)tiles_of(w) * tiles_of(h);
-  return (size_t)n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4) + 8 * (size_t)(emit_parts(n) + 1) +
+  return (size_t)n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + 8 * (size_t)(emit_parts(n) + 1) +
          (size_t)pairs * 24 + 4 * 256 * (size_t)kSortMaxPasses * sort_parts(pairs) + tiles * 8 +
          (size_t)w * h * 12 + 4096;
 }

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
   __shared__ float4 s_co[kBatch];
   __shared__ float s_rgb[3 * kBatch];
   __shared__ uint32_t s_slot[kBatch];
+  __shared__ float s_thr[kBatch];
   __shared__ float s_acc[kBatch][kPairGrad];
   __shared__ int s_max_last;
   const int tile = blockIdx.x;
@@ -71,7 +72,9 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
     if (j < n) {
       const uint32_t g = a.values[range.x + j];
       s_xy[threadIdx.x] = a.xy[g];
-      s_co[threadIdx.x] = a.conic_opacity[g];
+      const float4 cog = a.conic_opacity[g];
+      s_co[threadIdx.x] = cog;
+      s_thr[threadIdx.x] = composite_exp_threshold(cog.w);
       s_rgb[3 * threadIdx.x] = a.rgb[3 * g];
       s_rgb[3 * threadIdx.x + 1] = a.rgb[3 * g + 1];
       s_rgb[3 * threadIdx.x + 2] = a.rgb[3 * g + 2];
@@ -91,8 +94,10 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
         const float2 p = s_xy[jj];
         const float4 co = s_co[jj];
         const float dx = p.x - fx, dy = p.y - fy;
-        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-        if (power <= 0.f) {
+        const float4 g0 = make_float4(p.x, p.y, -0.5f * co.x, -0.5f * co.z);
+        const float4 g1 = make_float4(-co.y, s_thr[jj], co.w, 0.f);
+        const float power = composite_power(g0, g1, dx, dy);
+        if (power <= 0.f && power >= s_thr[jj]) {
           const float G = expf(power);
           const float a_raw = co.w * G;
           const float alpha = fminf(kAlphaMax, a_raw);

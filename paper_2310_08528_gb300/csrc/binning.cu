@@ -1,17 +1,17 @@
 // Tile binning: one (tile | depth) key per (Gaussian, touched tile).
 //
-// A single pass does three jobs per 2048-Gaussian partition:
-//   1. exclusive scan of the per-Gaussian tile counts, chained across CTAs by
-//      decoupled look-back (the partition index comes from an atomic ticket, so
-//      every predecessor a CTA waits on is already resident);
-//   2. emission of the keys (tile_id << 32 | float bits of depth) and values
-//      (Gaussian index) at the scanned offsets -- Gaussian order, then row-major
-//      tile order, which is what makes the later stable sort break depth ties by
-//      Gaussian index;
-//   3. the 256-bin digit histograms of every radix pass, accumulated in shared
-//      memory (depth digits once per Gaussian weighted by its count, tile digits
-//      once per run of equal digits along a rect row) and merged with one global
-//      atomic per non-empty bin.
+// Gaussians are visited in a given order (the depth-sorted order, so that a
+// stable sort on the tile bits alone yields (tile, depth, index) order).  One
+// pass per 256-Gaussian partition:
+//   1. exclusive scan of the tile counts, chained across CTAs by decoupled
+//      look-back (partition index from an atomic ticket, so every predecessor a
+//      CTA waits on is already resident; bounded spin);
+//   2. cooperative emission: the CTA's pairs [0, total) are produced by
+//      consecutive threads -- each finds its Gaussian by binary search over the
+//      CTA's offsets in shared memory -- so key/value stores are coalesced;
+//   3. the 256-bin digit histograms of the radix passes that follow, with
+//      warp-aggregated shared-memory counts (__match_any_sync) merged by one
+//      global atomic per non-empty bin.
 // A second small kernel turns the sorted keys into per-tile [start, end) ranges.
 #include "sync_util.cuh"
 
@@ -19,8 +19,8 @@ namespace fs4d {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
-constexpr int kPart = kThreads * kItems;
+constexpr int kItems = 1;
+constexpr int kPart = kThreads * kItems;  // Gaussians per partition
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -30,6 +30,10 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_warp[kThreads / 32];
   __shared__ unsigned long long s_prefix;
+  __shared__ uint32_t s_off[kPart + 1];   // local exclusive offsets; s_off[kPart] = partition total
+  __shared__ int4 s_rect[kPart];
+  __shared__ uint32_t s_dbits[kPart];
+  __shared__ uint32_t s_gid[kPart];
   __shared__ uint32_t s_hist[kMaxPasses][256];
   const int tid = threadIdx.x;
   if (tid == 0) s_part = atomicAdd(a.part_counter, 1u);
@@ -37,21 +41,29 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
     for (int i = tid; i < kMaxPasses * 256; i += kThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   const int part = (int)s_part;
-  const int g0 = part * kPart + tid * kItems;
+  const int base = part * kPart;
 
+  // ---- 1. counts and the partition-local scan (thread t owns item t)
   uint32_t cnt[kItems];
   uint32_t sum = 0;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
-    const int g = g0 + i;
+    const int li = tid * kItems + i;
+    const int pos = base + li;
     cnt[i] = 0;
-    if (g < a.n) {
-      const int4 r = a.rect[g];
+    int4 r = make_int4(0, 0, 0, 0);
+    uint32_t g = 0, db = 0;
+    if (pos < a.n) {
+      g = a.order ? a.order[pos] : (uint32_t)pos;
+      r = a.rect[g];
+      db = __float_as_uint(a.depth[g]);
       cnt[i] = (uint32_t)max(0, r.z - r.x) * (uint32_t)max(0, r.w - r.y);
     }
+    s_rect[li] = r;
+    s_dbits[li] = db;
+    s_gid[li] = g;
     sum += cnt[i];
   }
-  // Block-wide exclusive scan of the per-thread sums.
   const uint32_t lane = lane_id(), warp = tid / 32;
   uint32_t incl = sum;
 #pragma unroll
@@ -68,10 +80,15 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
     if ((uint32_t)w < warp) warp_excl += v;
     block_total += v;
   }
-  const uint32_t thread_excl = warp_excl + incl - sum;
+  uint32_t run = warp_excl + incl - sum;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    s_off[tid * kItems + i] = run;
+    run += cnt[i];
+  }
+  if (tid == 0) s_off[kPart] = block_total;
 
-  // Chain the partitions: publish this partition's total, then sum predecessors
-  // until one with an inclusive prefix is found.
+  // ---- chain the partitions
   if (tid == 0) {
     unsigned long long prefix = 0;
     if (part == 0) {
@@ -107,46 +124,46 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
     }
   }
   __syncthreads();
-
-  unsigned long long off = s_prefix + thread_excl;
-#pragma unroll 1
+  const unsigned long long prefix = s_prefix;
+#pragma unroll
   for (int i = 0; i < kItems; ++i) {
-    const int g = g0 + i;
-    if (g >= a.n) break;
-    a.offsets[g] = (uint32_t)off;
-    const uint32_t c = cnt[i];
-    if (c == 0) continue;
-    const int4 r = a.rect[g];
-    const uint32_t dbits = __float_as_uint(a.depth[g]);
+    const int pos = base + tid * kItems + i;
+    if (pos < a.n) a.offsets[s_gid[tid * kItems + i]] = (uint32_t)(prefix + s_off[tid * kItems + i]);
+  }
+
+  // ---- 2. cooperative emission, 3. histograms
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t j0 = 0; j0 < block_total; j0 += kThreads) {
+    const uint32_t j = j0 + (uint32_t)tid;
+    const bool valid = j < block_total;
+    unsigned long long key = 0;
+    if (valid) {
+      int lo = 0, hi = kPart - 1;  // last li with s_off[li] <= j; a Gaussian with no tiles never wins
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= j)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const int4 r = s_rect[lo];
+      const uint32_t k = j - s_off[lo];
+      const uint32_t w = (uint32_t)(r.z - r.x);
+      const uint32_t tile = (uint32_t)(r.y + (int)(k / w)) * (uint32_t)a.tiles_x + (uint32_t)(r.x + (int)(k % w));
+      key = ((unsigned long long)tile << 32) | s_dbits[lo];
+      const unsigned long long out = prefix + j;
+      if ((long long)out < a.capacity) {
+        a.keys[out] = key;
+        a.values[out] = s_gid[lo];
+      }
+    }
     if (a.hist) {
-      for (int p = 0; p < min(4, a.passes); ++p) atomicAdd(&s_hist[p][(dbits >> (8 * p)) & 255u], c);
-    }
-    const bool fits = (long long)(off + c) <= a.capacity;
-    unsigned long long o = off;
-    for (int ty = r.y; ty < r.w; ++ty) {
-      const uint32_t row0 = (uint32_t)(ty * a.tiles_x);
-      if (fits) {
-        for (int tx = r.x; tx < r.z; ++tx) {
-          const uint32_t tile = row0 + (uint32_t)tx;
-          a.keys[o] = ((unsigned long long)tile << 32) | dbits;
-          a.values[o] = (uint32_t)g;
-          ++o;
-        }
-      }
-      if (a.hist) {
-        for (int p = 4; p < a.passes; ++p) {
-          const int sh = 8 * (p - 4);
-          uint32_t t = row0 + (uint32_t)r.x;
-          const uint32_t t1 = row0 + (uint32_t)r.z - 1u;
-          while (t <= t1) {
-            const uint32_t run_end = min(t1, (((t >> sh) + 1u) << sh) - 1u);
-            atomicAdd(&s_hist[p][(t >> sh) & 255u], run_end - t + 1u);
-            t = run_end + 1u;
-          }
-        }
+      for (int p = 0; p < a.passes; ++p) {
+        const uint32_t d = valid ? (uint32_t)(key >> (a.hist_first_bit + 8 * p)) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
       }
     }
-    off += c;
   }
   if (a.hist) {
     __syncthreads();
@@ -185,6 +202,25 @@ cudaError_t launch_ranges(const unsigned long long* keys, const uint32_t* n_dev,
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
   if (e != cudaSuccess || n_bound <= 0) return e;
   ranges_kernel<<<(unsigned)((n_bound + 255) / 256), 256, 0, s>>>(keys, n_dev, n_bound, ranges, (uint32_t)n_tiles);
+  return cudaGetLastError();
+}
+
+}  // namespace fs4d
+
+namespace fs4d {
+namespace {
+__global__ void depth_keys_kernel(const float* __restrict__ depth, int n, unsigned long long* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = __float_as_uint(depth[i]);
+  vals[i] = (uint32_t)i;
+}
+}  // namespace
+
+cudaError_t launch_depth_keys(const float* depth, int n, unsigned long long* keys, uint32_t* vals, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(depth, n, keys, vals);
   return cudaGetLastError();
 }
 

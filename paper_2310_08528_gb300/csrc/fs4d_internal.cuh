@@ -103,12 +103,15 @@ struct ProjectArgs {
   float* depth;
   int* radius;
   int4* rect;
+  unsigned long long* depth_keys;  // optional [n]: float bits of depth, for the depth sort
+  uint32_t* depth_vals;            // optional [n]: Gaussian index
 };
 
 // Tile-pair emission fused with the exclusive scan of per-Gaussian tile counts
 // (decoupled look-back) and with the digit histograms of every radix pass.
 struct EmitArgs {
   int n;
+  const uint32_t* order;        // [n] Gaussian indices in emission order (NULL: index order)
   const float* depth;
   const int4* rect;
   int tiles_x;
@@ -122,6 +125,7 @@ struct EmitArgs {
   uint32_t* num_pairs_sort;     // out: K if K <= capacity, else 0 (what the sort may read)
   int report_overflow;          // set kStatusCapacity in *status when K > capacity
   uint32_t* hist;               // [passes][256] digit histograms (zeroed), or NULL
+  int hist_first_bit;           // key bit of the first histogram digit
   int passes;
   uint32_t* status;
 };
@@ -142,17 +146,19 @@ bool deform_bf16_supported(int feat_dim, int n_levels);
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s);
 
 int emit_parts(int n);          // scan partitions of the emit kernel
+// keys[i] = float bits of depth[i] (upper word 0), vals[i] = i: input of the depth sort
+cudaError_t launch_depth_keys(const float* depth, int n, unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s);
 
 int sort_passes(int key_bits);
 long long sort_parts(long long n);
-// Stable LSD sort of (keys, values) on the low key_bits bits.  n_dev (if non-NULL)
+// Stable LSD sort of (keys, values) on bits [first_bit, first_bit + key_bits).  n_dev (if non-NULL)
 // holds the live count on the device; n_bound is an upper bound used to size the
 // grids.  hist_ready = the per-pass histograms are already in work.hist.  Returns
 // in *result_in_alt whether the sorted pairs ended in the alternate buffers.
 cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
-                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int key_bits,
-                        bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
+                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
+                        int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
                         bool* result_in_alt);
 cudaError_t launch_ranges(const unsigned long long* keys, const uint32_t* n_dev, long long n_bound,
                           uint2* ranges, int n_tiles, cudaStream_t s);
@@ -234,4 +240,20 @@ long long wgrad_partial_floats(long long n, int O, int I);
 cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int I, float* partial, float* gW,
                          float* gb, cudaStream_t s);
 
+}  // namespace fs4d
+
+namespace fs4d {
+// Exponent of the Gaussian weight (Eq. 1) at offset (dx, dy) = mean - pixel
+// centre, with the Gaussian packed as g0 = (x, y, -a/2, -c/2), g1 = (-b, ., o, .)
+// for conic (a, b, c).  Forward and backward compositing share this exact
+// arithmetic, so the backward reproduces every forward decision bit for bit.
+__device__ __forceinline__ float composite_power(const float4& g0, const float4& g1, float dx, float dy) {
+  return fmaf(g0.z * dx, dx, fmaf(g0.w * dy, dy, (g1.x * dx) * dy));
+}
+// A term reaches alpha >= 1/255 only if its exponent is >= ln(1/(255 o)).  Terms
+// below that bound minus 1e-3 (0.1% in alpha, far above float32 rounding) are
+// skipped before exp without changing any decision.
+__device__ __forceinline__ float composite_exp_threshold(float opacity) {
+  return logf((1.f / 255.f) / opacity) - 1e-3f;
+}
 }  // namespace fs4d

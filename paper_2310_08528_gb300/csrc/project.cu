@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   const float pz = c.m[8] * X0 + c.m[9] * X1 + c.m[10] * X2 + c.m[11];
   const float opacity = 1.f / (1.f + expf(-a.opacity_logits[g]));
   a.depth[g] = pz;
+  if (a.depth_keys) {
+    a.depth_keys[g] = __float_as_uint(pz);
+    a.depth_vals[g] = (uint32_t)g;
+  }
   a.radius[g] = 0;
   a.rect[g] = make_int4(0, 0, 0, 0);
   a.xy[g] = make_float2(0.f, 0.f);

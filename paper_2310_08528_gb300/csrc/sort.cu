@@ -16,8 +16,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kPartPairs = kThreads * kItems;  // 4096
+constexpr int kItemsLarge = 16;  // keys per thread for large sorts (4096 per partition)
+constexpr int kItemsSmall = 4;   // ... and for sorts of a few 100k keys (1024 per partition)
+constexpr int kPartPairs = kThreads * kItemsLarge;
+constexpr int kPartPairsSmall = kThreads * kItemsSmall;
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
@@ -26,7 +28,7 @@ constexpr int kMaxPasses = 8;
 
 __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
                                                    const uint32_t* __restrict__ n_dev, long long n_bound,
-                                                   int passes, uint32_t* __restrict__ hist) {
+                                                   int first_bit, int passes, uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_hist[kMaxPasses][kRadix];
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __r
     const bool valid = i < n;
     const unsigned long long k = valid ? keys[i] : 0ull;
     for (int p = 0; p < passes; ++p) {
-      const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+      const uint32_t d = valid ? (uint32_t)(k >> (first_bit + 8 * p)) & 255u : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       if (d < 256u && (peers & lane_lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
     }
@@ -63,9 +65,10 @@ struct PassArgs {
   uint32_t* status;
 };
 
+template <int ITEMS>
 struct PassSmem {
-  unsigned long long keys[kPartPairs];
-  uint32_t values[kPartPairs];
+  unsigned long long keys[kThreads * ITEMS];
+  uint32_t values[kThreads * ITEMS];
   uint32_t warp_cnt[kWarps][kRadix];
   uint32_t global_off[kRadix];   // exclusive scan of the global histogram
   uint32_t block_off[kRadix];    // exclusive scan of this partition's counts
@@ -93,9 +96,12 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp) {
   return base + incl - v;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
+  constexpr int kItems = ITEMS;
+  constexpr int kPartPairs = kThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
+  PassSmem<ITEMS>& sm = *reinterpret_cast<PassSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
   if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
@@ -199,22 +205,31 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
 }  // namespace
 
 int sort_passes(int key_bits) { return (key_bits + 7) / 8; }
-long long sort_parts(long long n) { return (n + kPartPairs - 1) / kPartPairs; }
+// Partitions a sort of n keys may use (the small-partition count: an upper bound).
+long long sort_parts(long long n) { return (n + kPartPairsSmall - 1) / kPartPairsSmall; }
 
 cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
-                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int key_bits,
-                        bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
+                        uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
+                        int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
                         bool* result_in_alt) {
   *result_in_alt = false;
   const int passes = sort_passes(key_bits);
   if (n_bound <= 0 || passes == 0) return cudaSuccess;
   if (passes > kMaxPasses) return cudaErrorInvalidValue;
-  const long long parts = sort_parts(n_bound);
+  // small partitions keep enough CTAs in flight for a few 100k keys; large ones
+  // amortise the look-back for millions (and fit a fixed look-back table)
+  const long long parts_small = (n_bound + kPartPairsSmall - 1) / kPartPairsSmall;
+  const bool small = n_bound <= (1ll << 19) && parts_small <= work.max_parts;
+  const long long parts = small ? parts_small : (n_bound + kPartPairs - 1) / kPartPairs;
   if (parts > work.max_parts || n_bound > (long long)kValMask) return cudaErrorInvalidValue;
   static bool attr_done = false;
   cudaError_t e;
   if (!attr_done) {
-    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PassSmem));
+    e = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassSmem<kItemsLarge>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(onesweep_kernel<kItemsSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassSmem<kItemsSmall>));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -225,8 +240,8 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   if (!hist_ready) {
     e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     if (e != cudaSuccess) return e;
-    const int blocks = (int)min(parts * 4, (long long)152 * 8);
-    hist_kernel<<<blocks, 256, 0, s>>>(keys, n_dev, n_bound, passes, work.hist);
+    const int blocks = (int)min((n_bound + 1023) / 1024, (long long)152 * 8);
+    hist_kernel<<<blocks, 256, 0, s>>>(keys, n_dev, n_bound, first_bit, passes, work.hist);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   unsigned long long* kin = keys;
@@ -236,12 +251,15 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   for (int p = 0; p < passes; ++p) {
     PassArgs pa;
     pa.keys_in = kin; pa.values_in = vin; pa.keys_out = kout; pa.values_out = vout;
-    pa.n_dev = n_dev; pa.n_bound = n_bound; pa.shift = 8 * p;
+    pa.n_dev = n_dev; pa.n_bound = n_bound; pa.shift = first_bit + 8 * p;
     pa.hist = work.hist + p * kRadix;
     pa.lookback = work.lookback + (size_t)p * parts * kRadix;
     pa.part_counter = work.part_counters + p;
     pa.status = status;
-    onesweep_kernel<<<(unsigned)parts, kThreads, sizeof(PassSmem), s>>>(pa);
+    if (small)
+      onesweep_kernel<kItemsSmall><<<(unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s>>>(pa);
+    else
+      onesweep_kernel<kItemsLarge><<<(unsigned)parts, kThreads, sizeof(PassSmem<kItemsLarge>), s>>>(pa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     unsigned long long* tk = kin; kin = kout; kout = tk;
     uint32_t* tv = vin; vin = vout; vout = tv;
@@ -313,7 +331,7 @@ extern "C" fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int
   unsigned long long* keys_alt = reinterpret_cast<unsigned long long*>(base + kNaKeys);
   uint32_t* values_alt = reinterpret_cast<uint32_t*>(base + kNaValues);
   bool alt = false;
-  if (launch_sort(keys, d_values, keys_alt, values_alt, nullptr, n, key_bits, false, w, status, s, &alt) !=
+  if (launch_sort(keys, d_values, keys_alt, values_alt, nullptr, n, 0, key_bits, false, w, status, s, &alt) !=
       cudaSuccess)
     return FS4D_ERR_CUDA;
   if (alt) {
