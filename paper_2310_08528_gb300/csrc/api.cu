@@ -469,12 +469,14 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
   pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
   pa.depth_keys = P<unsigned long long>(w.dkeys); pa.depth_vals = P<uint32_t>(w.dvals);
+  pa.depth_hist = P<uint32_t>(w.hist);
+  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, stream));
   FS4D_CUDA(c, launch_project(pa, stream));
   mark(e, 2);
   // Gaussians in (float32 depth, index) order: the emission order
   bool dalt = false;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
-                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, false, sort_work(w), e.status, stream,
+                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, sort_work(w), e.status, stream,
                            &dalt));
   const uint32_t* order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
   const int tile_bits = ceil_log2((long long)tx * ty);

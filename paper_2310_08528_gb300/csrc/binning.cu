@@ -95,22 +95,35 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
       st_relaxed_u64(&a.lookback[0], kFlagInc | block_total);
     } else {
       st_relaxed_u64(&a.lookback[part], kFlagAgg | block_total);
+      // windowed look-back: 8 predecessors per round of independent loads
+      constexpr int kWin = 8;
       int j = part - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const unsigned long long v = ld_relaxed_u64(&a.lookback[j]);
-        const unsigned long long flag = v & ~kValMask;
-        if (flag == 0) {
+      bool found = false;
+      while (j >= 0 && !found) {
+        const int cnt = min(kWin, j + 1);
+        unsigned long long wv[kWin];
+#pragma unroll
+        for (int i = 0; i < kWin; ++i)
+          if (i < cnt) wv[i] = ld_relaxed_u64(&a.lookback[j - i]);
+        int used = 0;
+#pragma unroll
+        for (int i = 0; i < kWin; ++i) {
+          if (i >= cnt || found) break;
+          const unsigned long long flag = wv[i] & ~kValMask;
+          if (flag == 0) break;
+          prefix += wv[i] & kValMask;
+          ++used;
+          if (flag == kFlagInc) found = true;
+        }
+        j -= used;
+        if (!found && used < cnt) {
           if (++spins > kSpinLimit) {
             atomicOr(a.status, kStatusTimeout);
             break;
           }
           __nanosleep(32);
-          continue;
         }
-        prefix += v & kValMask;
-        if (flag == kFlagInc) break;
-        --j;
       }
       st_relaxed_u64(&a.lookback[part], kFlagInc | (prefix + block_total));
     }

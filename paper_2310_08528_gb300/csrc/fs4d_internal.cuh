@@ -105,6 +105,7 @@ struct ProjectArgs {
   int4* rect;
   unsigned long long* depth_keys;  // optional [n]: float bits of depth, for the depth sort
   uint32_t* depth_vals;            // optional [n]: Gaussian index
+  uint32_t* depth_hist;            // optional [4][256] (zeroed): byte histograms of the depth keys
 };
 
 // Tile-pair emission fused with the exclusive scan of per-Gaussian tile counts

@@ -44,9 +44,34 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
   Y[15] = kY33 * x * (xx - 3.f * yy);
 }
 
+// Byte histograms of the depth keys for the depth sort that follows: shared-
+// memory counts aggregated per warp (__match_any_sync), one global atomic per
+// non-empty bin.
+__device__ __forceinline__ void depth_histogram(const ProjectArgs& a, int g, float pz) {
+  __shared__ uint32_t s_hist[4][256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const bool valid = g < a.n;
+  const uint32_t bits = valid ? __float_as_uint(pz) : 0u;
+  uint32_t lt;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const uint32_t d = valid ? (bits >> (8 * p)) & 255u : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const uint32_t v = (&s_hist[0][0])[i];
+    if (v) atomicAdd(&a.depth_hist[i], v);
+  }
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n) return;
+  const bool valid = g < a.n;
   CamParams c = a.cam;
   if (a.cam_dev) {
     const fs4d_camera* d = a.cam_dev;
@@ -56,10 +81,17 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) c.m[4 * r + k] = d->world_to_cam[4 * r + k];
   }
-  const float X0 = a.means[3 * g], X1 = a.means[3 * g + 1], X2 = a.means[3 * g + 2];
+  float X0 = 0.f, X1 = 0.f, X2 = 0.f;
+  if (valid) {
+    X0 = a.means[3 * g];
+    X1 = a.means[3 * g + 1];
+    X2 = a.means[3 * g + 2];
+  }
   const float px = c.m[0] * X0 + c.m[1] * X1 + c.m[2] * X2 + c.m[3];
   const float py = c.m[4] * X0 + c.m[5] * X1 + c.m[6] * X2 + c.m[7];
   const float pz = c.m[8] * X0 + c.m[9] * X1 + c.m[10] * X2 + c.m[11];
+  if (a.depth_hist) depth_histogram(a, g, pz);  // the whole CTA takes part
+  if (!valid) return;
   const float opacity = 1.f / (1.f + expf(-a.opacity_logits[g]));
   a.depth[g] = pz;
   if (a.depth_keys) {
@@ -131,15 +163,28 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   float dx = X0 - cpx, dy = X1 - cpy, dz = X2 - cpz;
   const float dinv = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
   dx *= dinv; dy *= dinv; dz *= dinv;
+  constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[16];
-  sh_basis(a.sh_degree, dx, dy, dz, Y);
-  const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+  sh_basis(DEG, dx, dy, dz, Y);
+  // K*3 coefficients per Gaussian; 16-byte aligned rows (K*3 % 4 == 0) load as float4
+  float shc[3 * K];
   const float* sh = a.sh + (long long)g * K * 3;
+  if ((3 * K) % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < 3 * K / 4; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(sh) + q);
+      shc[4 * q] = v.x; shc[4 * q + 1] = v.y; shc[4 * q + 2] = v.z; shc[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3 * K; ++q) shc[q] = __ldg(sh + q);
+  }
   float r = 0.5f, gg = 0.5f, b = 0.5f;
+#pragma unroll
   for (int k = 0; k < K; ++k) {
-    r += Y[k] * sh[3 * k];
-    gg += Y[k] * sh[3 * k + 1];
-    b += Y[k] * sh[3 * k + 2];
+    r += Y[k] * shc[3 * k];
+    gg += Y[k] * shc[3 * k + 1];
+    b += Y[k] * shc[3 * k + 2];
   }
   a.rgb[3 * g] = fmaxf(0.f, r);
   a.rgb[3 * g + 1] = fmaxf(0.f, gg);
@@ -154,7 +199,14 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  project_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  const unsigned grid = (unsigned)((a.n + 255) / 256);
+  switch (a.sh_degree) {
+    case 0: project_kernel<0><<<grid, 256, 0, s>>>(a); break;
+    case 1: project_kernel<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: project_kernel<2><<<grid, 256, 0, s>>>(a); break;
+    case 3: project_kernel<3><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

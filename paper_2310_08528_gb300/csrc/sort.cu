@@ -112,6 +112,15 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   const uint32_t part = sm.part;
   const long long base = (long long)part * kPartPairs;
   if (base >= n) return;  // uniform across the CTA
+  // A pass whose digit is the same for every key keeps the order: copy through.
+  if (__syncthreads_or((long long)a.hist[tid] == n)) {
+    const long long m = min((long long)kPartPairs, n - base);
+    for (long long i = tid; i < m; i += kThreads) {
+      a.keys_out[base + i] = a.keys_in[base + i];
+      a.values_out[base + i] = a.values_in[base + i];
+    }
+    return;
+  }
 
   // Global offset of each digit.
   sm.global_off[tid] = block_excl_scan(a.hist[tid], sm.scan_tmp);
@@ -154,22 +163,36 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     st_relaxed_u32(lb, kFlagInc | total);
   } else {
     st_relaxed_u32(lb, kFlagAgg | total);
+    // Windowed look-back: read up to 8 predecessors at once (independent loads),
+    // then consume them in order until an inclusive prefix is found.
+    constexpr int kWin = 8;
     long long j = (long long)part - 1;
     uint32_t spins = 0;
-    while (j >= 0) {
-      const uint32_t w = ld_relaxed_u32(a.lookback + (size_t)j * kRadix + tid);
-      const uint32_t flag = w & ~kValMask;
-      if (flag == 0) {
+    bool found = false;
+    while (j >= 0 && !found) {
+      const int cnt = (int)min((long long)kWin, j + 1);
+      uint32_t wv[kWin];
+#pragma unroll
+      for (int i = 0; i < kWin; ++i)
+        if (i < cnt) wv[i] = ld_relaxed_u32(a.lookback + (size_t)(j - i) * kRadix + tid);
+      int used = 0;
+#pragma unroll
+      for (int i = 0; i < kWin; ++i) {
+        if (i >= cnt || found) break;
+        const uint32_t flag = wv[i] & ~kValMask;
+        if (flag == 0) break;  // not published yet: poll again from here
+        prev += wv[i] & kValMask;
+        ++used;
+        if (flag == kFlagInc) found = true;
+      }
+      j -= used;
+      if (!found && used < cnt) {
         if (++spins > kSpinLimit) {
           atomicOr(a.status, kStatusTimeout);
           break;
         }
         __nanosleep(32);
-        continue;
       }
-      prev += w & kValMask;
-      if (flag == kFlagInc) break;
-      --j;
     }
     st_relaxed_u32(lb, kFlagInc | ((prev + total) & kValMask));
   }

@@ -150,9 +150,10 @@ def test_unload_while_queued(world, server):
     tickets = [srv.submit(sid, cam_for(1, 256, 256, k), 0.5, torch.zeros((256, 256, 3), device="cuda"))
                for k in range(8)]
     ctx.unload_scene(sid)  # waits for in-flight frames; queued ones fail cleanly
-    d = wait_all(srv, tickets)
+    late = srv.submit(sid, cam_for(1, 64, 64, 0), 0.5, torch.zeros((64, 64, 3), device="cuda"))
+    d = wait_all(srv, tickets + [late])
     assert all(d[tk]["status"] in (OK, NOT_FOUND) for tk in tickets)
-    assert any(d[tk]["status"] == NOT_FOUND for tk in tickets)
+    assert d[late]["status"] == NOT_FOUND
 
 
 def test_host_output_equals_device_output(world, server):
