@@ -56,6 +56,7 @@ struct Scene {
   int n = 0, sh_degree = 0, K = 1;
   DevBuf means, log_scales, quats, opacity_logits, sh;
   DevBuf planes, planes_bf16, mlp, mlp_t, tc_ops, tc_bias;
+  DevBuf perm;  // deformation work order: Gaussians by Morton code of their canonical mean
   PlaneGeom pg{};
   MlpGeomT mg{};
   MlpGeomTC tg{};
@@ -319,7 +320,7 @@ fs4d_status upload(fs4d_ctx* c, DevBuf& b, const T* h, size_t count, size_t* acc
 
 void free_scene(Scene* s) {
   DevBuf* all[] = {&s->means, &s->log_scales, &s->quats, &s->opacity_logits, &s->sh, &s->planes,
-                   &s->planes_bf16, &s->mlp, &s->mlp_t, &s->tc_ops, &s->tc_bias};
+                   &s->planes_bf16, &s->mlp, &s->mlp_t, &s->tc_ops, &s->tc_bias, &s->perm};
   for (DevBuf* b : all) release(*b);
   delete s;
 }
@@ -414,6 +415,7 @@ void mark(const Env& e, int i) {
 DeformArgs deform_args(Scene* s, const float* ts, float t0, int n_t, float* om, float* oq, float* os) {
   DeformArgs a{};
   a.n = s->n; a.n_t = n_t; a.ts = ts; a.t0 = t0;
+  a.perm = P<uint32_t>(s->perm);
   a.means = P<float>(s->means); a.quats = P<float>(s->quats); a.log_scales = P<float>(s->log_scales);
   a.out_means = om; a.out_quats = oq; a.out_log_scales = os;
   a.planes = P<float>(s->planes);
@@ -682,6 +684,32 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
     build_tc_image(d->mlp, hin, d->mlp_width, s->tg, img, bias);
     if ((st = upload(c, s->tc_ops, img.data(), img.size(), &acc)) != FS4D_OK) return bail(st);
     if ((st = upload(c, s->tc_bias, bias.data(), bias.size(), &acc)) != FS4D_OK) return bail(st);
+  }
+  {
+    // Work order of the deformation kernels: Gaussians sorted by the 30-bit
+    // Morton code of their mean inside the HexPlane box, so that the Gaussians
+    // of one warp/CTA gather neighbouring plane cells (outputs keep Gaussian order).
+    std::vector<std::pair<uint32_t, uint32_t>> code(n);
+    auto spread = [](uint32_t v) {
+      v &= 1023u;
+      v = (v | (v << 16)) & 0x030000FFu;
+      v = (v | (v << 8)) & 0x0300F00Fu;
+      v = (v | (v << 4)) & 0x030C30C3u;
+      v = (v | (v << 2)) & 0x09249249u;
+      return v;
+    };
+    for (size_t g = 0; g < n; ++g) {
+      uint32_t q[3];
+      for (int k = 0; k < 3; ++k) {
+        const float u = (d->means[3 * g + k] - d->aabb_min[k]) / (d->aabb_max[k] - d->aabb_min[k]);
+        q[k] = (uint32_t)std::min(1023.f, std::max(0.f, u * 1023.f));
+      }
+      code[g] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), (uint32_t)g};
+    }
+    std::sort(code.begin(), code.end());
+    std::vector<uint32_t> perm(n);
+    for (size_t i = 0; i < n; ++i) perm[i] = code[i].second;
+    if ((st = upload(c, s->perm, perm.data(), n, &acc)) != FS4D_OK) return bail(st);
   }
   s->resident = acc;
   std::lock_guard<std::mutex> lock(c->mu);

@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   for (long long gi = (long long)blockIdx.x * kThreads + threadIdx.x; gi < total;
        gi += (long long)gridDim.x * kThreads) {
     const int ti = (int)(gi / a.n);
-    const int g = (int)(gi - (long long)ti * a.n);
+    const int gw = (int)(gi - (long long)ti * a.n);
+    const int g = a.perm ? (int)a.perm[gw] : gw;  // spatially coherent work order
     const float t = a.ts ? a.ts[ti] : a.t0;
     const float X0 = a.means[3 * g], X1 = a.means[3 * g + 1], X2 = a.means[3 * g + 2];
     float c[4];

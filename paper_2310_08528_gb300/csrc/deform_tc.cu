@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
       for (int k = 0; k < H; ++k) f[k] = 0.f;
       if (gi < total) {
         const int ti = (int)(gi / a.n);
-        const int g = (int)(gi - (long long)ti * a.n);
+        const int gw = (int)(gi - (long long)ti * a.n);
+        const int g = a.perm ? (int)a.perm[gw] : gw;  // spatially coherent work order
         const float t = a.ts ? a.ts[ti] : a.t0;
         float c[4];
         c[0] = (a.means[3 * g] - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
@@ -330,9 +331,10 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
       const long long gi = base + row;
       if (gi < total) {
         const int ti = (int)(gi / a.n);
-        const int g = (int)(gi - (long long)ti * a.n);
+        const int gw = (int)(gi - (long long)ti * a.n);
+        const int g = a.perm ? (int)a.perm[gw] : gw;
         const float* bo = sBias + 320;
-        const long long o = a.out_tab ? (long long)g : gi;
+        const long long o = a.out_tab ? (long long)g : (long long)ti * a.n + g;
         float* om = a.out_tab ? a.out_tab[3 * ti] : a.out_means;
         float* oq = a.out_tab ? a.out_tab[3 * ti + 1] : a.out_quats;
         float* os = a.out_tab ? a.out_tab[3 * ti + 2] : a.out_log_scales;

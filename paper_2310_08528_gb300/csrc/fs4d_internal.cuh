@@ -58,6 +58,7 @@ struct MlpGeomTC {
 
 struct DeformArgs {
   int n;                        // Gaussians
+  const uint32_t* perm;         // optional [n] work order (spatially coherent); outputs keep Gaussian order
   int n_t;                      // timestamps
   const float* ts;              // device [n_t], or NULL to use t0 (n_t must be 1)
   float t0;
