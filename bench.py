@@ -129,37 +129,48 @@ def load_peaks():
             "source": "fallback"}
 
 
-def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str):
+def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, evals: int = 0):
     """Algorithmic bytes or FLOPs of one launch of each stage (per-unit figures
-    times the units one launch processes)."""
+    times the units one launch processes).  Returns a list of (bound, work, unit);
+    the first entry is the stage's primary bound."""
     if stage == "deform":
         flops = 2 * (64 * 64 + 64 * 64 + 3 * 64 * 64 + 64 * 10) * n   # MLP contraction, 42,240 FLOP/Gaussian
-        return ("tensor" if prec == "bf16" else "alu"), flops, "FLOP"
+        return [(("tensor" if prec == "bf16" else "alu"), flops, "FLOP"), ("hbm", 80 * n, "B")]
     if stage == "project":
-        return "hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16), "B"
+        return [("hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 12), "B")]
     if stage == "scan_emit":
-        return "hbm", n * (16 + 4 + 4) + K * 12, "B"
+        # depth sort: 4 passes of 32-bit keys, each reading and writing 8 B key + 4 B value per Gaussian;
+        # emission: order, rect, depth in + offset out per Gaussian, 12 B per pair out
+        return [("hbm", 4 * n * 24 + n * (4 + 16 + 4 + 4) + K * 12, "B")]
     if stage == "sort":
-        return "hbm", passes * K * 24, "B"                             # read + write 12 B per pair per pass
+        return [("hbm", passes * K * 24, "B")]                         # read + write 12 B per pair per pass
     if stage == "ranges":
-        return "hbm", K * 8 + 0, "B"
+        return [("hbm", K * 8, "B")]
     if stage == "composite":
-        return "hbm", K * 40 + pixels * 12, "B"                        # gather idx + 36 B, write rgb
+        # gather (idx + xy, conic/opacity, rgb) per pair and the rgb write per pixel; ~15 FLOP per tested
+        # (pixel, Gaussian) up to each pixel's last contributor
+        return [("hbm", K * 40 + pixels * 12, "B"), ("alu", 15 * evals, "FLOP")]
     raise KeyError(stage)
 
 
-def roofline(stage_ms, n, K, pixels, passes, prec, peaks, clocks_mhz):
+def _frac(bound, work, sec, peaks):
+    if bound == "hbm":
+        ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
+    elif bound == "tensor":
+        ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
+    else:  # float32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+        ach, peak, u = work / sec / 1e12, 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s"
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": u, "frac": ach / peak}
+
+
+def roofline(stage_ms, n, K, pixels, passes, prec, peaks, evals):
     out = {}
     for st, ms in stage_ms.items():
-        bound, work, unit = stage_work(st, n, K, pixels, passes, prec)
-        sec = ms * 1e-3
-        if bound == "hbm":
-            ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
-        elif bound == "tensor":
-            ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
-        else:  # float32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
-            ach, peak, u = work / sec / 1e12, 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s"
-        out[st] = {"bound": bound, "achieved": ach, "peak": peak, "unit": u, "frac": ach / peak, "ms": ms}
+        items = [_frac(b, w, ms * 1e-3, peaks) for b, w, _ in stage_work(st, n, K, pixels, passes, prec, evals)]
+        best = max(items, key=lambda r: r["frac"]) if st == "composite" else items[0]
+        out[st] = dict(best, ms=ms)
+        if len(items) > 1:
+            out[st]["also"] = [r for r in items if r is not best]
     return out
 
 
@@ -393,8 +404,19 @@ def main():
     cap = int(kmax * 1.25) + 4096
     ctx.reserve(sid, WIDTH, HEIGHT, cap)
     tiles = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
-    passes = (32 + int(np.ceil(np.log2(tiles))) + 7) // 8
-    launches_per_frame = 5 + passes  # deform, project, scan/emit, sort passes, ranges, composite
+    passes = (int(np.ceil(np.log2(tiles))) + 7) // 8   # the pair sort keys on the tile bits only
+    # deform, project, 4 depth-sort passes, scan/emit, pair-sort passes, ranges, composite
+    launches_per_frame = 8 + passes
+    # (pixel, Gaussian) tests the compositing must make: each pixel walks its tile's list up to its
+    # last contributor (summed over the frames of the view set)
+    evals, pairs = [], []
+    with torch.cuda.stream(stream):
+        for c in range(0, N_CAMS * N_TIMES, 97):
+            cam, t = views(c, 0, 1)
+            _, _, nc = ctx.render(sid, cam, t, with_aux=True)
+            evals.append(int(nc.sum().item()))
+            pairs.append(ctx.last_pairs())
+    evals, mean_pairs = int(np.mean(evals)), int(np.mean(pairs))
 
     bf16_ok = True
     try:
@@ -458,9 +480,8 @@ def main():
         return 0
 
     peaks = load_peaks()
-    K = ctx.last_pairs()
-    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks,
-                  clocks["sm_mhz"] if clocks else None)
+    K = mean_pairs
+    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks, evals)
     dom = max(rf, key=lambda k: rf[k]["ms"])
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
@@ -473,7 +494,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "resolution": [WIDTH, HEIGHT],
-                   "tile_pairs_last_frame": K, "pair_capacity": cap, "parallelism": f"replicas x{world}",
+                   "tile_pairs_mean": K, "pixel_gaussian_tests_mean": evals, "pair_capacity": cap, "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed frame (256 MB device write, outside the timed interval)",
                    "timing": "CUDA events around camera upload + CUDA-graph replay of one frame"},
         "roofline": {"kernel": dom, "bound": rf[dom]["bound"], "achieved": rf[dom]["achieved"], "peak": rf[dom]["peak"],

@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kBatch = kTile * kTile;
 constexpr float kAlphaMax = 0.99f;
-constexpr float kAlphaMin = 1.f / 255.f;
 constexpr float kDilation = 0.3f;
 constexpr float kGuard = 1.3f;
 
@@ -39,7 +38,6 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
   __shared__ float4 s_co[kBatch];
   __shared__ float s_rgb[3 * kBatch];
   __shared__ uint32_t s_slot[kBatch];
-  __shared__ float s_thr[kBatch];
   __shared__ float s_acc[kBatch][kPairGrad];
   __shared__ int s_max_last;
   const int tile = blockIdx.x;
@@ -74,7 +72,6 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
       s_xy[threadIdx.x] = a.xy[g];
       const float4 cog = a.conic_opacity[g];
       s_co[threadIdx.x] = cog;
-      s_thr[threadIdx.x] = composite_exp_threshold(cog.w);
       s_rgb[3 * threadIdx.x] = a.rgb[3 * g];
       s_rgb[3 * threadIdx.x + 1] = a.rgb[3 * g + 1];
       s_rgb[3 * threadIdx.x + 2] = a.rgb[3 * g + 2];
@@ -93,38 +90,34 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
       if (bstart + jj < last) {
         const float2 p = s_xy[jj];
         const float4 co = s_co[jj];
-        const float dx = p.x - fx, dy = p.y - fy;
-        const float4 g0 = make_float4(p.x, p.y, -0.5f * co.x, -0.5f * co.z);
-        const float4 g1 = make_float4(-co.y, s_thr[jj], co.w, 0.f);
-        const float power = composite_power(g0, g1, dx, dy);
-        if (power <= 0.f && power >= s_thr[jj]) {
-          const float G = expf(power);
+        const float4 g0 = composite_coeffs(p, co);
+        const float dx = g0.x - fx, dy = g0.y - fy;
+        float G;
+        const float alpha = composite_alpha(g0, composite_b2(co), co.w, dx, dy, G);
+        if (alpha > 0.f) {
           const float a_raw = co.w * G;
-          const float alpha = fminf(kAlphaMax, a_raw);
-          if (alpha >= kAlphaMin) {
-            contrib = true;
-            const float inv = 1.f / (1.f - alpha);
-            const float Ti = T * inv;
-            const float c0 = s_rgb[3 * jj], c1 = s_rgb[3 * jj + 1], c2 = s_rgb[3 * jj + 2];
-            const float dalpha =
-                dC0 * (c0 * Ti - b0 * inv) + dC1 * (c1 * Ti - b1 * inv) + dC2 * (c2 * Ti - b2 * inv);
-            const float w = alpha * Ti;
-            gr[6] = dC0 * w;
-            gr[7] = dC1 * w;
-            gr[8] = dC2 * w;
-            b0 += c0 * w;
-            b1 += c1 * w;
-            b2 += c2 * w;
-            T = Ti;
-            if (a_raw <= kAlphaMax) {
-              const float dpow = dalpha * co.w * G;
-              gr[0] = -dpow * (co.x * dx + co.y * dy);
-              gr[1] = -dpow * (co.z * dy + co.y * dx);
-              gr[2] = -0.5f * dpow * dx * dx;
-              gr[3] = -dpow * dx * dy;
-              gr[4] = -0.5f * dpow * dy * dy;
-              gr[5] = dalpha * G;
-            }
+          contrib = true;
+          const float inv = 1.f / (1.f - alpha);
+          const float Ti = T * inv;
+          const float c0 = s_rgb[3 * jj], c1 = s_rgb[3 * jj + 1], c2 = s_rgb[3 * jj + 2];
+          const float dalpha =
+              dC0 * (c0 * Ti - b0 * inv) + dC1 * (c1 * Ti - b1 * inv) + dC2 * (c2 * Ti - b2 * inv);
+          const float w = alpha * Ti;
+          gr[6] = dC0 * w;
+          gr[7] = dC1 * w;
+          gr[8] = dC2 * w;
+          b0 += c0 * w;
+          b1 += c1 * w;
+          b2 += c2 * w;
+          T = Ti;
+          if (a_raw <= kAlphaMax) {
+            const float dpow = dalpha * co.w * G;
+            gr[0] = -dpow * (co.x * dx + co.y * dy);
+            gr[1] = -dpow * (co.z * dy + co.y * dx);
+            gr[2] = -0.5f * dpow * dx * dx;
+            gr[3] = -dpow * dx * dy;
+            gr[4] = -0.5f * dpow * dy * dy;
+            gr[5] = dalpha * G;
           }
         }
       }

@@ -2,12 +2,13 @@
 // Eq. 1).  One 256-thread CTA per 16x16 screen tile, one pixel per thread; warp
 // w owns the 8x4 pixel block (w % 2, w / 2) of the tile.  The tile's depth-
 // sorted list is walked in batches of 256: each thread gathers one Gaussian into
-// shared memory as two 128-bit words -- (x, y, -a/2, -c/2) and (-b, exponent
-// threshold, opacity, block mask) -- plus its colour, where the mask says which
-// of the eight warp blocks the ellipse {alpha >= 1/255} can reach.  A warp skips
-// a Gaussian outside its block with one uniform branch; pixels inside evaluate
-// Eq. 1 exactly.  The mask is conservative, so it never changes a decision.  A CTA stops as soon as all
-// of its pixels have saturated (__syncthreads_count).
+// shared memory -- position and log2-scaled conic, opacity and colour -- and the
+// 8-bit mask of the warp blocks that the ellipse {alpha >= 1/255} can reach.
+// Each warp then compacts the batch to the Gaussians whose mask holds its block
+// (ballot + popc, order kept) and walks only those; every pixel evaluates Eq. 1
+// exactly for them.  The mask is conservative, so it never changes a decision.
+// A warp whose pixels have all saturated skips the batch; a CTA stops as soon as
+// all of its pixels have (__syncthreads_count).
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
@@ -15,8 +16,7 @@ namespace {
 
 constexpr int kThreads = kTile * kTile;
 constexpr int kBatch = kThreads;
-constexpr float kAlphaMax = 0.99f;
-constexpr float kAlphaMin = 1.f / 255.f;
+constexpr int kWarps = kThreads / 32;
 constexpr float kTMin = 1e-4f;
 
 // Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0).
@@ -60,18 +60,22 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
                                                             const float4* __restrict__ conic_opacity,
                                                             const float* __restrict__ rgb, float* __restrict__ image,
                                                             float* __restrict__ t_final, int* __restrict__ n_contrib) {
-  __shared__ float4 s_g0[kBatch];
-  __shared__ float4 s_g1[kBatch];
-  __shared__ float s_rgb[3 * kBatch];
+  __shared__ float4 s_g0[kBatch];       // x, y, a2, c2
+  __shared__ float4 s_g1[kBatch];       // b2, opacity, red, green
+  __shared__ float s_blue[kBatch];
+  __shared__ uint32_t s_mask[kBatch];
+  __shared__ uint8_t s_list[kWarps][kBatch];
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lane_lt = (1u << lane) - 1u;
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < width && py < height;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   const uint2 range = ranges[tile];
   const int n = (int)(range.y - range.x);
+  uint8_t* list = s_list[warp];
 
   bool done = !inside;
   float T = 1.f, R = 0.f, G = 0.f, B = 0.f;
@@ -83,36 +87,44 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
       const uint32_t g = values[range.x + k];
       const float2 p = xy[g];
       const float4 co = conic_opacity[g];
-      const float thr = composite_exp_threshold(co.w);
-      s_g0[threadIdx.x] = make_float4(p.x, p.y, -0.5f * co.x, -0.5f * co.z);
-      s_g1[threadIdx.x] = make_float4(-co.y, thr, co.w, __uint_as_float(block_mask(p, co, thr, tx, ty)));
-      s_rgb[3 * threadIdx.x] = rgb[3 * g];
-      s_rgb[3 * threadIdx.x + 1] = rgb[3 * g + 1];
-      s_rgb[3 * threadIdx.x + 2] = rgb[3 * g + 2];
+      s_g0[threadIdx.x] = composite_coeffs(p, co);
+      s_g1[threadIdx.x] = make_float4(composite_b2(co), co.w, rgb[3 * g], rgb[3 * g + 1]);
+      s_blue[threadIdx.x] = rgb[3 * g + 2];
+      s_mask[threadIdx.x] = block_mask(p, co, composite_exp_threshold(co.w), tx, ty);
     }
     __syncthreads();
+    if (__all_sync(0xffffffffu, done)) continue;  // warp-uniform
     const int m = min(kBatch, n - base);
-    for (int j = 0; j < m; ++j) {
-      const float4 g1 = s_g1[j];
-      if (!((__float_as_uint(g1.w) >> warp) & 1u)) continue;  // warp-uniform: ellipse misses the block
+    int cnt = 0;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      const int j = c0 + lane;
+      const bool hit = j < m && ((s_mask[j] >> warp) & 1u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) list[cnt + __popc(bal & lane_lt)] = (uint8_t)j;
+      cnt += __popc(bal);
+    }
+    __syncwarp();
+    for (int i = 0; i < cnt; ++i) {
       if (done) continue;
+      const int j = list[i];
       const float4 g0 = s_g0[j];
-      const float power = composite_power(g0, g1, g0.x - fx, g0.y - fy);
-      if (power > 0.f || power < g1.y) continue;
-      const float alpha = fminf(kAlphaMax, g1.z * expf(power));
-      if (alpha < kAlphaMin) continue;
+      const float4 g1 = s_g1[j];
+      float gw;
+      const float alpha = composite_alpha(g0, g1.x, g1.y, g0.x - fx, g0.y - fy, gw);
+      if (alpha == 0.f) continue;
       const float Tn = T * (1.f - alpha);
       if (Tn < kTMin) {
         done = true;
         continue;
       }
       const float w = alpha * T;
-      R += s_rgb[3 * j] * w;
-      G += s_rgb[3 * j + 1] * w;
-      B += s_rgb[3 * j + 2] * w;
+      R += g1.z * w;
+      G += g1.w * w;
+      B += s_blue[j] * w;
       T = Tn;
       last = base + j + 1;
     }
+    __syncwarp();
   }
   if (inside) {
     const int pix = py * width + px;

@@ -245,16 +245,37 @@ cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int
 }  // namespace fs4d
 
 namespace fs4d {
-// Exponent of the Gaussian weight (Eq. 1) at offset (dx, dy) = mean - pixel
-// centre, with the Gaussian packed as g0 = (x, y, -a/2, -c/2), g1 = (-b, ., o, .)
-// for conic (a, b, c).  Forward and backward compositing share this exact
-// arithmetic, so the backward reproduces every forward decision bit for bit.
-__device__ __forceinline__ float composite_power(const float4& g0, const float4& g1, float dx, float dy) {
-  return fmaf(g0.z * dx, dx, fmaf(g0.w * dy, dy, (g1.x * dx) * dy));
+// Gaussian weight of Eq. 1 as a power of two: with the conic (a, b, c) scaled
+// once per Gaussian by log2(e) into (a2, b2, c2) = log2(e) * (-a/2, -b, -c/2),
+// exp(-d^T K d / 2) = 2^(a2 dx^2 + b2 dx dy + c2 dy^2), one SFU instruction.
+// Forward and backward compositing share this exact arithmetic, so the backward
+// reproduces every forward decision bit for bit.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float y) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
 }
-// A term reaches alpha >= 1/255 only if its exponent is >= ln(1/(255 o)).  Terms
-// below that bound minus 1e-3 (0.1% in alpha, far above float32 rounding) are
-// skipped before exp without changing any decision.
+
+__device__ __forceinline__ float4 composite_coeffs(float2 p, float4 conic_opacity) {
+  return make_float4(p.x, p.y, (-0.5f * kLog2e) * conic_opacity.x, (-0.5f * kLog2e) * conic_opacity.z);
+}
+__device__ __forceinline__ float composite_b2(float4 conic_opacity) { return -kLog2e * conic_opacity.y; }
+
+// alpha = min(0.99, o * G) of a term at offset (dx, dy) = mean - pixel centre,
+// or 0 when the term is skipped (exponent above 0, or alpha below 1/255).
+__device__ __forceinline__ float composite_alpha(const float4& g0, float b2, float opacity, float dx, float dy,
+                                                 float& G) {
+  const float p = fmaf(g0.z * dx, dx, fmaf(g0.w * dy, dy, (b2 * dx) * dy));
+  G = ex2_approx(p);
+  const float alpha = fminf(0.99f, opacity * G);
+  return (p > 0.f || alpha < 1.f / 255.f) ? 0.f : alpha;
+}
+
+// Natural-log exponent bound: a term reaches alpha >= 1/255 only where
+// -d^T K d / 2 >= ln(1/(255 o)); the bound minus 1e-3 (0.1% in alpha, far above
+// the rounding of either exponent form) is used for conservative culling.
 __device__ __forceinline__ float composite_exp_threshold(float opacity) {
   return logf((1.f / 255.f) / opacity) - 1e-3f;
 }
