@@ -203,13 +203,18 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long base = tile * kRows;
-    // ---- 1. HexPlane features (Eq. 5) -> A1 [128 x HL] BF16
-    for (int item = tid; item < kRows * L; item += kThreads) {
-      const int r = item % kRows, l = item / kRows;
+    // ---- 1. HexPlane features (Eq. 5) -> A1 [128 x HL] BF16.  Four (H = 32) or
+    // two (H = 16) consecutive lanes share one (Gaussian, level) item and each
+    // owns 8 features, so a warp's 16-byte loads cover whole 64-byte grid
+    // vertices of 8 Gaussians and few registers per plane keep many loads in flight.
+    constexpr int Q = H / 8;
+    for (int item = tid; item < kRows * L * Q; item += kThreads) {
+      const int q = item % Q, rl = item / Q;
+      const int r = rl % kRows, l = rl / kRows;
       const long long gi = base + r;
-      float f[H];
+      float f[8];
 #pragma unroll
-      for (int k = 0; k < H; ++k) f[k] = 0.f;
+      for (int k = 0; k < 8; ++k) f[k] = 0.f;
       if (gi < total) {
         const int ti = (int)(gi / a.n);
         const int gw = (int)(gi - (long long)ti * a.n);
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
         c[2] = (a.means[3 * g + 2] - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
         c[3] = 2.f * t - 1.f;
 #pragma unroll
-        for (int k = 0; k < H; ++k) f[k] = 1.f;
+        for (int k = 0; k < 8; ++k) f[k] = 1.f;
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
           const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);  // xy xz yz xt yt zt
@@ -232,34 +237,26 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
           float fa, fb;
           axis_setup(c[ax], Ra, i0, fa);
           axis_setup(c[bx], Rb, j0, fb);
-          const uint4* v00 = reinterpret_cast<const uint4*>(a.planes_bf16 + pg.off[l][p] + ((long long)j0 * Ra + i0) * H);
-          const uint4* v10 = v00 + H / 8;
-          const uint4* v01 = v00 + (long long)Ra * (H / 8);
-          const uint4* v11 = v01 + H / 8;
+          const uint4* v00 =
+              reinterpret_cast<const uint4*>(a.planes_bf16 + pg.off[l][p] + ((long long)j0 * Ra + i0) * H) + q;
+          const uint4 A = __ldg(v00), B = __ldg(v00 + Q), C = __ldg(v00 + (long long)Ra * Q),
+                      D = __ldg(v00 + (long long)Ra * Q + Q);
           const float w00 = (1.f - fa) * (1.f - fb), w10 = fa * (1.f - fb), w01 = (1.f - fa) * fb, w11 = fa * fb;
+          const uint32_t wa[4] = {A.x, A.y, A.z, A.w}, wb[4] = {B.x, B.y, B.z, B.w},
+                         wc[4] = {C.x, C.y, C.z, C.w}, wd[4] = {D.x, D.y, D.z, D.w};
 #pragma unroll
-          for (int q = 0; q < H / 8; ++q) {
-            const uint4 A = __ldg(v00 + q), B = __ldg(v10 + q), C = __ldg(v01 + q), D = __ldg(v11 + q);
-            const uint32_t wa[4] = {A.x, A.y, A.z, A.w}, wb[4] = {B.x, B.y, B.z, B.w},
-                           wc[4] = {C.x, C.y, C.z, C.w}, wd[4] = {D.x, D.y, D.z, D.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              f[8 * q + 2 * e] *= w00 * bf_lo(wa[e]) + w10 * bf_lo(wb[e]) + w01 * bf_lo(wc[e]) + w11 * bf_lo(wd[e]);
-              f[8 * q + 2 * e + 1] *=
-                  w00 * bf_hi(wa[e]) + w10 * bf_hi(wb[e]) + w01 * bf_hi(wc[e]) + w11 * bf_hi(wd[e]);
-            }
+          for (int e = 0; e < 4; ++e) {
+            f[2 * e] *= w00 * bf_lo(wa[e]) + w10 * bf_lo(wb[e]) + w01 * bf_lo(wc[e]) + w11 * bf_lo(wd[e]);
+            f[2 * e + 1] *= w00 * bf_hi(wa[e]) + w10 * bf_hi(wb[e]) + w01 * bf_hi(wc[e]) + w11 * bf_hi(wd[e]);
           }
         }
       }
-#pragma unroll
-      for (int q = 0; q < H / 8; ++q) {
-        uint4 v;
-        v.x = pack_bf16(f[8 * q + 0], f[8 * q + 1]);
-        v.y = pack_bf16(f[8 * q + 2], f[8 * q + 3]);
-        v.z = pack_bf16(f[8 * q + 4], f[8 * q + 5]);
-        v.w = pack_bf16(f[8 * q + 6], f[8 * q + 7]);
-        *reinterpret_cast<uint4*>(sX + a_off(r, l * H + 8 * q, HL)) = v;
-      }
+      uint4 v;
+      v.x = pack_bf16(f[0], f[1]);
+      v.y = pack_bf16(f[2], f[3]);
+      v.z = pack_bf16(f[4], f[5]);
+      v.w = pack_bf16(f[6], f[7]);
+      *reinterpret_cast<uint4*>(sX + a_off(r, l * H + 8 * q, HL)) = v;
     }
     fence_async_smem();
     __syncthreads();

@@ -131,14 +131,18 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   uint32_t v[kItems], rank[kItems];
   uint16_t dig[kItems];
   const uint32_t lt = lanemask_lt();
+  // all loads first, so that every thread has its kItems requests in flight at once
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const long long idx = base + (long long)warp * (kItems * 32) + i * 32 + lane;
     const bool valid = idx < n;
-    k[i] = valid ? a.keys_in[idx] : 0ull;
-    v[i] = valid ? a.values_in[idx] : 0u;
-    const uint32_t d = valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u;
-    dig[i] = (uint16_t)d;
+    k[i] = valid ? __ldg(a.keys_in + idx) : 0ull;
+    v[i] = valid ? __ldg(a.values_in + idx) : 0u;
+    dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u);
+  }
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t d = dig[i];
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (d < 256u) before = sm.warp_cnt[warp][d];
