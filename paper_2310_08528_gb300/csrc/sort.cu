@@ -2,7 +2,7 @@
 //  - one histogram pass produces the 256-bin digit counts of EVERY radix pass at
 //    once (skipped when the binning kernel already produced them);
 //  - then one kernel per 8-bit digit.  Each CTA takes a 4096-pair partition by
-//    atomic ticket, ranks its keys stably (warp-striped order, __match_any_sync
+//    atomic ticket, ranks its keys stably (warp-striped order, ballot-multisplit
 //    peers per digit, warp offsets chained through shared memory), publishes its
 //    per-digit counts and resolves its global per-digit offsets by decoupled
 //    look-back on its predecessors, then scatters through shared memory so that
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __r
     const unsigned long long k = valid ? keys[i] : 0ull;
     for (int p = 0; p < passes; ++p) {
       const uint32_t d = valid ? (uint32_t)(k >> (first_bit + 8 * p)) & 255u : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t peers = digit_peers(d, d < 256u);
       if (d < 256u && (peers & lane_lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
     }
   }
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const uint32_t d = dig[i];
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = digit_peers(d, d < 256u);
     uint32_t before = 0;
     if (d < 256u) before = sm.warp_cnt[warp][d];
     __syncwarp();
@@ -153,7 +153,9 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   }
   __syncthreads();
 
-  // Per digit (thread tid = digit): chain the warps, then the partitions.
+  // Per digit (thread tid = digit): chain the warps, publish this partition's
+  // count, then sort locally through shared memory before looking back, so the
+  // look-back runs with the keys already out of registers.
   uint32_t total = 0;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
@@ -162,14 +164,26 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     total += c;
   }
   uint32_t* lb = a.lookback + (size_t)part * kRadix + tid;
+  st_relaxed_u32(lb, (part == 0 ? kFlagInc : kFlagAgg) | total);
+  sm.block_off[tid] = block_excl_scan(total, sm.scan_tmp);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t d = dig[i];
+    if (d < 256u) {
+      const uint32_t pos = sm.block_off[d] + sm.warp_cnt[warp][d] + rank[i];
+      sm.keys[pos] = k[i];
+      sm.values[pos] = v[i];
+    }
+  }
+
+  // Look-back: read up to 32 predecessors at once (independent loads), then
+  // consume them nearest first until an inclusive prefix is found.  All
+  // partitions publish at about the same time, so a wide window keeps the
+  // number of dependent rounds small.
   uint32_t prev = 0;
-  if (part == 0) {
-    st_relaxed_u32(lb, kFlagInc | total);
-  } else {
-    st_relaxed_u32(lb, kFlagAgg | total);
-    // Windowed look-back: read up to 8 predecessors at once (independent loads),
-    // then consume them in order until an inclusive prefix is found.
-    constexpr int kWin = 8;
+  if (part > 0) {
+    constexpr int kWin = 32;
     long long j = (long long)part - 1;
     uint32_t spins = 0;
     bool found = false;
@@ -201,19 +215,6 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     st_relaxed_u32(lb, kFlagInc | ((prev + total) & kValMask));
   }
   sm.prev_off[tid] = prev;
-  sm.block_off[tid] = block_excl_scan(total, sm.scan_tmp);
-  __syncthreads();
-
-  // Local sort through shared memory.
-#pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    const uint32_t d = dig[i];
-    if (d < 256u) {
-      const uint32_t pos = sm.block_off[d] + sm.warp_cnt[warp][d] + rank[i];
-      sm.keys[pos] = k[i];
-      sm.values[pos] = v[i];
-    }
-  }
   __syncthreads();
 
   // Scatter: consecutive slots of one digit go to consecutive addresses.

@@ -36,4 +36,18 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Lanes of the warp that hold the same 8-bit digit as this lane (a warp
+// multisplit from eight ballots, one per digit bit); lanes with valid == false
+// are in no lane's mask.  Every lane of the warp must call it.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+  uint32_t m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
+
 }  // namespace fs4d

@@ -155,6 +155,26 @@ def test_bin_sort_bit_exact(ctx, n, tx, ty):
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
 
 
+@pytest.mark.parametrize("n,tx,ty,max_w", [(30000, 4, 4, 4),     # tiles of ~7k pairs: the long-tile sort
+                                           (60000, 2, 2, 2),     # tiles of ~30k: chunk sort + merges
+                                           (50000, 40, 3, 3)])   # one hot tile among short ones
+def test_bin_sort_dense_tiles_bit_exact(ctx, n, tx, ty, max_w):
+    rng = np.random.default_rng(n + tx)
+    depth, rect = _random_bins(rng, n, tx, ty, max_w=max_w, tie_every=7)
+    if tx == 40:  # half of the Gaussians on tile 0 only (several merge rounds, odd last run)
+        rect[: n // 2] = (0, 0, 1, 1)
+    keys_o, vals_o, ranges_o = oracle.bin_sort(depth.view(np.uint32), rect, tx, ty)
+    lens = ranges_o[1::2].astype(np.int64) - ranges_o[0::2]
+    assert lens.max() > 2048
+    K = len(keys_o)
+    keys, vals, ranges, Kg = ctx.bin_sort(dev(depth), dev(rect), tx, ty, K)
+    torch.cuda.synchronize()
+    assert Kg == K
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_o)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_o)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
+
+
 def test_bin_sort_empty_and_capacity(ctx):
     depth = np.ones(10, np.float32)
     rect = np.zeros((10, 4), np.int32)  # every Gaussian culled
