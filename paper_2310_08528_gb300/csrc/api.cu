@@ -78,7 +78,7 @@ struct Work {
   DevBuf dkeys, dvals, dkeys_alt, dvals_alt;  // per-Gaussian depth sort
   DevBuf keys, values, keys_alt, values_alt;
   DevBuf sort_lb;
-  DevBuf ranges;
+  DevBuf ranges, tile_count;
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
   DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
@@ -363,6 +363,7 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
   FS4D_CUDA(c, ensure(w.hist, 4 * 256 * kSortMaxPasses));
   if (n_tiles > w.cap_tiles) {
     FS4D_CUDA(c, ensure(w.ranges, 8 * (size_t)n_tiles));
+    FS4D_CUDA(c, ensure(w.tile_count, 4 * (size_t)n_tiles));
     w.cap_tiles = n_tiles;
   }
   if (pairs > w.cap_pairs) {
@@ -484,7 +485,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   const int tile_bits = ceil_log2((long long)tx * ty);
   FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.tile_count.p, 0, 4 * (size_t)tx * ty, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), stream));
   EmitArgs ea{};
   ea.n = s->n; ea.order = order; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
@@ -495,12 +496,14 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   ea.part_counter = P<uint32_t>(w.counters);
   ea.num_pairs = P<uint32_t>(w.num_pairs);
   ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
-  ea.hist = P<uint32_t>(w.hist);
-  ea.hist_first_bit = 32;
-  ea.passes = sort_passes(tile_bits);
+  ea.tile_count = P<uint32_t>(w.tile_count);
+  ea.n_tiles = tx * ty;
   ea.status = e.status;
   ea.report_overflow = report ? 1 : 0;
   FS4D_CUDA(c, launch_scan_emit(ea, stream));
+  // tile ranges and the pair sort's digit histograms straight from the tile counts
+  FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), tx * ty, P<uint32_t>(w.num_pairs), P<uint2>(w.ranges),
+                                P<uint32_t>(w.hist), sort_passes(tile_bits), stream));
   mark(e, 3);
   return FS4D_OK;
 }
@@ -527,8 +530,7 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
   if (values_out) *values_out = values;
-  mark(e, 5);
-  FS4D_CUDA(c, launch_ranges(keys, n_dev, n_bound, P<uint2>(w.ranges), tx * ty, e.s));
+  mark(e, 5);  // the ranges came with the tile scan: an empty stage
   mark(e, 6);
   FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values, P<float2>(w.xy),
                                 P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s));
@@ -603,7 +605,7 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     Work& w = c->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.ts, &w.host_img,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.ts, &w.host_img,
                      &w.grad_pair, &w.gd, &w.acts, &w.wpartial};
     for (DevBuf* b : all) release(*b);
     release(c->status);
@@ -1084,10 +1086,10 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
       !h_num_pairs || !d_ranges || (n > 0 && (!d_depth || !d_rect)) || (capacity > 0 && (!d_keys || !d_values)))
     return fail(c, FS4D_ERR_INVALID_ARG, "bin_sort: bad argument");
   DeviceGuard g(c->device);
-  fs4d_status st = ensure_work(c, std::max(n, 1), 1, capacity);
+  const int n_tiles = tiles_x * tiles_y;
+  fs4d_status st = ensure_work(c, std::max(n, 1), n_tiles, capacity);
   if (st != FS4D_OK) return st;
   Work& w = c->w;
-  const int n_tiles = tiles_x * tiles_y;
   const int tile_bits = ceil_log2(n_tiles);
   // emission order: Gaussians sorted by (float32 depth, index)
   FS4D_CUDA(c, launch_depth_keys(d_depth, n, P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), c->stream));
@@ -1097,7 +1099,7 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
                            c->stream, &dalt));
   FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.tile_count.p, 0, 4 * (size_t)n_tiles, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(std::max(n, 1)), c->stream));
   EmitArgs ea{};
   ea.n = n; ea.order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
@@ -1109,12 +1111,14 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   ea.part_counter = P<uint32_t>(w.counters);
   ea.num_pairs = P<uint32_t>(w.num_pairs);
   ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
-  ea.hist = P<uint32_t>(w.hist);
-  ea.hist_first_bit = 32;
-  ea.passes = sort_passes(tile_bits);
+  ea.tile_count = P<uint32_t>(w.tile_count);
+  ea.n_tiles = n_tiles;
   ea.status = P<uint32_t>(c->status);
   ea.report_overflow = 0;
   FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
+  FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
+                                reinterpret_cast<uint2*>(d_ranges), P<uint32_t>(w.hist), sort_passes(tile_bits),
+                                c->stream));
   long long K = 0;
   if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
   *h_num_pairs = K;
@@ -1129,8 +1133,6 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
     FS4D_CUDA(c, cudaMemcpyAsync(d_keys, w.keys_alt.p, 8 * (size_t)K, cudaMemcpyDeviceToDevice, c->stream));
     FS4D_CUDA(c, cudaMemcpyAsync(d_values, w.values_alt.p, 4 * (size_t)K, cudaMemcpyDeviceToDevice, c->stream));
   }
-  FS4D_CUDA(c, launch_ranges(reinterpret_cast<unsigned long long*>(d_keys), nullptr, K,
-                             reinterpret_cast<uint2*>(d_ranges), n_tiles, c->stream));
   return FS4D_OK;
 }
 
@@ -1710,7 +1712,7 @@ fs4d_status fs4d_server_destroy(fs4d_server* sv) {
     Work& w = sl->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &sl->status, &sl->dcam, &sl->dt,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &sl->status, &sl->dcam, &sl->dt,
                      &sl->image};
     for (DevBuf* b : all) release(*b);
     cudaFreeHost(sl->h_cam);

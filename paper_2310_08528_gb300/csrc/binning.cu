@@ -9,10 +9,10 @@
 //   2. cooperative emission: the CTA's pairs [0, total) are produced by
 //      consecutive threads -- each finds its Gaussian by binary search over the
 //      CTA's offsets in shared memory -- so key/value stores are coalesced;
-//   3. the 256-bin digit histograms of the radix passes that follow, with
-//      warp-aggregated shared-memory counts (__match_any_sync) merged by one
-//      global atomic per non-empty bin.
-// A second small kernel turns the sorted keys into per-tile [start, end) ranges.
+//   3. per-tile pair counts in shared memory, merged by one global atomic per
+//      non-empty tile.
+// A one-CTA kernel scans the tile counts into the tile [start, end) ranges and
+// the digit histograms of the pair sort that follows (no pass over the keys).
 #include "sync_util.cuh"
 
 namespace fs4d {
@@ -25,8 +25,10 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kMaxPasses = 8;
+constexpr int kEmitSmemTiles = 16384;     // tiles counted in shared memory (more: global atomics)
 
-__global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
+__global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int smem_tiles) {
+  extern __shared__ uint32_t s_tc[];      // per-tile pair counts of this partition (smem_tiles != 0)
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_warp[kThreads / 32];
   __shared__ unsigned long long s_prefix;
@@ -34,11 +36,9 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
   __shared__ int4 s_rect[kPart];
   __shared__ uint32_t s_dbits[kPart];
   __shared__ uint32_t s_gid[kPart];
-  __shared__ uint32_t s_hist[kMaxPasses][256];
   const int tid = threadIdx.x;
   if (tid == 0) s_part = atomicAdd(a.part_counter, 1u);
-  if (a.hist)
-    for (int i = tid; i < kMaxPasses * 256; i += kThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = tid; i < smem_tiles; i += kThreads) s_tc[i] = 0;
   __syncthreads();
   const int part = (int)s_part;
   const int base = part * kPart;
@@ -144,8 +144,7 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
     if (pos < a.n) a.offsets[s_gid[tid * kItems + i]] = (uint32_t)(prefix + s_off[tid * kItems + i]);
   }
 
-  // ---- 2. cooperative emission, 3. histograms
-  const uint32_t lt = lanemask_lt();
+  // ---- 2. cooperative emission, 3. per-tile pair counts
   for (uint32_t j0 = 0; j0 < block_total; j0 += kThreads) {
     const uint32_t j = j0 + (uint32_t)tid;
     const bool valid = j < block_total;
@@ -169,34 +168,63 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a) {
         a.keys[out] = key;
         a.values[out] = s_gid[lo];
       }
-    }
-    if (a.hist) {
-      for (int p = 0; p < a.passes; ++p) {
-        const uint32_t d = valid ? (uint32_t)(key >> (a.hist_first_bit + 8 * p)) & 255u : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
-      }
+      if (smem_tiles)
+        atomicAdd(&s_tc[tile], 1u);
+      else
+        atomicAdd(&a.tile_count[tile], 1u);
     }
   }
-  if (a.hist) {
+  if (smem_tiles) {
     __syncthreads();
-    for (int i = tid; i < a.passes * 256; i += kThreads) {
-      const uint32_t v = (&s_hist[0][0])[i];
-      if (v) atomicAdd(&a.hist[i], v);
+    for (int t = tid; t < smem_tiles; t += kThreads) {
+      const uint32_t v = s_tc[t];
+      if (v) atomicAdd(&a.tile_count[t], v);
     }
   }
 }
 
-__global__ void __launch_bounds__(256) ranges_kernel(const unsigned long long* __restrict__ keys,
-                                                     const uint32_t* __restrict__ n_dev, long long n_bound,
-                                                     uint2* __restrict__ ranges, uint32_t n_tiles) {
-  const long long n = n_dev ? (long long)*n_dev : n_bound;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || i >= n_bound) return;
-  const uint32_t tile = (uint32_t)(keys[i] >> 32);
-  if (tile >= n_tiles) return;
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != tile) ranges[tile].x = (uint32_t)i;
-  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != tile) ranges[tile].y = (uint32_t)(i + 1);
+// One CTA: exclusive scan of the per-tile pair counts.  A stable sort of the
+// pairs on their tile bits puts tile t at [scan(t), scan(t) + count(t)), so this
+// IS the tile range table (0, 0 for an empty tile, and for every tile when the
+// pairs overflowed the buffers); the digit histograms of the pair sort's passes
+// (digit p of tile t is (t >> 8p) & 255) come from the same counts.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t* __restrict__ tile_count, int n_tiles,
+                                                                 const uint32_t* __restrict__ num_pairs,
+                                                                 uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
+                                                                 int passes) {
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_hist[kMaxPasses][256];
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id(), warp = tid / 32;
+  for (int i = tid; i < kMaxPasses * 256; i += kScanThreads) (&s_hist[0][0])[i] = 0;
+  const bool overflow = num_pairs[1] == 0u && num_pairs[0] != 0u;
+  const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
+  const int t0 = min(tid * per, n_tiles), t1 = min(t0 + per, n_tiles);
+  uint32_t sum = 0;
+  for (int t = t0; t < t1; ++t) sum += tile_count[t];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - sum;
+  for (int w = 0; w < (int)warp; ++w) run += s_warp[w];
+  for (int t = t0; t < t1; ++t) {
+    const uint32_t c = tile_count[t];
+    ranges[t] = (overflow || c == 0) ? make_uint2(0u, 0u) : make_uint2(run, run + c);
+    if (c && hist)
+      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][((uint32_t)t >> (8 * p)) & 255u], c);
+    run += c;
+  }
+  if (hist) {
+    __syncthreads();
+    for (int i = tid; i < passes * 256; i += kScanThreads) hist[i] = (&s_hist[0][0])[i];
+  }
 }
 
 }  // namespace
@@ -205,16 +233,22 @@ int emit_parts(int n) { return (n + kPart - 1) / kPart; }
 
 cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (a.passes > kMaxPasses) return cudaErrorInvalidValue;
-  scan_emit_kernel<<<emit_parts(a.n), kThreads, 0, s>>>(a);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(scan_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
+  scan_emit_kernel<<<emit_parts(a.n), kThreads, 4 * (size_t)st, s>>>(a, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const unsigned long long* keys, const uint32_t* n_dev, long long n_bound, uint2* ranges,
-                          int n_tiles, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
-  if (e != cudaSuccess || n_bound <= 0) return e;
-  ranges_kernel<<<(unsigned)((n_bound + 255) / 256), 256, 0, s>>>(keys, n_dev, n_bound, ranges, (uint32_t)n_tiles);
+cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
+                             uint32_t* hist, int passes, cudaStream_t s) {
+  if (passes > kMaxPasses || n_tiles < 1) return cudaErrorInvalidValue;
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes);
   return cudaGetLastError();
 }
 

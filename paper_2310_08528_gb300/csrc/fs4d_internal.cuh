@@ -126,9 +126,8 @@ struct EmitArgs {
   uint32_t* num_pairs;          // out: K (clamped to 2^32-1)
   uint32_t* num_pairs_sort;     // out: K if K <= capacity, else 0 (what the sort may read)
   int report_overflow;          // set kStatusCapacity in *status when K > capacity
-  uint32_t* hist;               // [passes][256] digit histograms (zeroed), or NULL
-  int hist_first_bit;           // key bit of the first histogram digit
-  int passes;
+  uint32_t* tile_count;         // [n_tiles] (zeroed): pairs per tile
+  int n_tiles;
   uint32_t* status;
 };
 
@@ -151,6 +150,10 @@ int emit_parts(int n);          // scan partitions of the emit kernel
 // keys[i] = float bits of depth[i] (upper word 0), vals[i] = i: input of the depth sort
 cudaError_t launch_depth_keys(const float* depth, int n, unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s);
+// tile ranges (from the per-tile counts; all (0, 0) when num_pairs[1] == 0 < num_pairs[0])
+// and, if hist != NULL, the [passes][256] digit histograms of the pair sort on the tile bits
+cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
+                             uint32_t* hist, int passes, cudaStream_t s);
 
 int sort_passes(int key_bits);
 long long sort_parts(long long n);
@@ -162,9 +165,6 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
                         int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
                         bool* result_in_alt);
-cudaError_t launch_ranges(const unsigned long long* keys, const uint32_t* n_dev, long long n_bound,
-                          uint2* ranges, int n_tiles, cudaStream_t s);
-
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
                              const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
                              float* t_final, int* n_contrib, cudaStream_t s);
