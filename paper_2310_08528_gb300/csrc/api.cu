@@ -88,7 +88,8 @@ struct Work {
 };
 
 constexpr int kSortMaxPasses = 8;
-constexpr int kCounters = 16;  // [0] emit ticket, [8..15] unused
+constexpr int kCounters = 32;  // [0] emit ticket, [8, 25) radix-sort tickets and selection words
+constexpr int kEmitCounters = 8;  // the words reset before an emission (the sort's words stay)
 
 }  // namespace
 
@@ -478,17 +479,18 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   mark(e, 2);
   // Gaussians in (float32 depth, index) order: the emission order
   bool dalt = false;
+  const uint32_t* dsel = nullptr;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
                            P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, sort_work(w), e.status, stream,
-                           &dalt));
-  const uint32_t* order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
+                           &dalt, &dsel));
   const int tile_bits = ceil_log2((long long)tx * ty);
-  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kEmitCounters, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.tile_count.p, 0, 4 * (size_t)tx * ty, stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), stream));
   EmitArgs ea{};
-  ea.n = s->n; ea.order = order; ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
+  ea.n = s->n; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
+  ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
   ea.capacity = cap;
   ea.keys = P<unsigned long long>(w.keys); ea.values = P<uint32_t>(w.values);
   ea.offsets = P<uint32_t>(w.offsets);
@@ -1094,15 +1096,16 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   // emission order: Gaussians sorted by (float32 depth, index)
   FS4D_CUDA(c, launch_depth_keys(d_depth, n, P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), c->stream));
   bool dalt = false;
+  const uint32_t* dsel = nullptr;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
                            P<uint32_t>(w.dvals_alt), nullptr, n, 0, 32, false, sort_work(c), P<uint32_t>(c->status),
-                           c->stream, &dalt));
-  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kCounters, c->stream));
+                           c->stream, &dalt, &dsel));
+  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kEmitCounters, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.tile_count.p, 0, 4 * (size_t)n_tiles, c->stream));
   FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(std::max(n, 1)), c->stream));
   EmitArgs ea{};
-  ea.n = n; ea.order = dalt ? P<uint32_t>(w.dvals_alt) : P<uint32_t>(w.dvals);
+  ea.n = n; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
   ea.depth = d_depth; ea.rect = reinterpret_cast<const int4*>(d_rect); ea.tiles_x = tiles_x;
   ea.capacity = capacity;
   ea.keys = reinterpret_cast<unsigned long long*>(d_keys); ea.values = d_values;

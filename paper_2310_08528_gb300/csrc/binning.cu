@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int sme
   __syncthreads();
   const int part = (int)s_part;
   const int base = part * kPart;
+  const uint32_t* order = (a.order_sel && *a.order_sel) ? a.order_alt : a.order;
 
   // ---- 1. counts and the partition-local scan (thread t owns item t)
   uint32_t cnt[kItems];
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int sme
     int4 r = make_int4(0, 0, 0, 0);
     uint32_t g = 0, db = 0;
     if (pos < a.n) {
-      g = a.order ? a.order[pos] : (uint32_t)pos;
+      g = order ? order[pos] : (uint32_t)pos;
       r = a.rect[g];
       db = __float_as_uint(a.depth[g]);
       cnt[i] = (uint32_t)max(0, r.z - r.x) * (uint32_t)max(0, r.w - r.y);

@@ -114,6 +114,8 @@ struct ProjectArgs {
 struct EmitArgs {
   int n;
   const uint32_t* order;        // [n] Gaussian indices in emission order (NULL: index order)
+  const uint32_t* order_alt;    // with order_sel: the order is here when *order_sel != 0
+  const uint32_t* order_sel;
   const float* depth;
   const int4* rect;
   int tiles_x;
@@ -134,7 +136,7 @@ struct EmitArgs {
 struct SortWork {
   uint32_t* hist;               // [8][256]
   uint32_t* lookback;           // [8][max_parts][256]
-  uint32_t* part_counters;      // [8]
+  uint32_t* part_counters;      // [2 * 8 + 1]: pass tickets, then selection words
   long long max_parts;
 };
 
@@ -160,11 +162,15 @@ long long sort_parts(long long n);
 // Stable LSD sort of (keys, values) on bits [first_bit, first_bit + key_bits).  n_dev (if non-NULL)
 // holds the live count on the device; n_bound is an upper bound used to size the
 // grids.  hist_ready = the per-pass histograms are already in work.hist.  Returns
-// in *result_in_alt whether the sorted pairs ended in the alternate buffers.
+// in *result_in_alt whether the sorted pairs ended in the alternate buffers.  With
+// result_sel non-NULL, a pass whose digit is the same for every key copies nothing
+// and the side that holds the result is known only on the device: *result_sel then
+// points to a word that is 1 when it is the alternate buffers (*result_in_alt = false).
+// work.part_counters must have 2 * 8 + 1 words.
 cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
                         int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
-                        bool* result_in_alt);
+                        bool* result_in_alt, const uint32_t** result_sel = nullptr);
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
                              const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
                              float* t_final, int* n_contrib, cudaStream_t s);

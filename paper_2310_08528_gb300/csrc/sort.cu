@@ -52,10 +52,12 @@ __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __r
 }
 
 struct PassArgs {
-  const unsigned long long* keys_in;
+  const unsigned long long* keys_in;   // with sel_in: buffer A, the other one is B
   const uint32_t* values_in;
   unsigned long long* keys_out;
   uint32_t* values_out;
+  const uint32_t* sel_in;   // optional: 1 if this pass's input is in B (the *_out pointers)
+  uint32_t* sel_out;        //   where the pass records where its output is
   const uint32_t* n_dev;
   long long n_bound;
   int shift;
@@ -105,25 +107,36 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
   if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
+  // independent of the ticket: issued while it is in flight
+  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
+  const uint32_t h = a.hist[tid];
+  const bool in_b = a.sel_in && *a.sel_in;
+  const unsigned long long* keys_in = in_b ? a.keys_out : a.keys_in;
+  const uint32_t* values_in = in_b ? a.values_out : a.values_in;
+  unsigned long long* keys_out = in_b ? const_cast<unsigned long long*>(a.keys_in) : a.keys_out;
+  uint32_t* values_out = in_b ? const_cast<uint32_t*>(a.values_in) : a.values_out;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
   __syncthreads();
-  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
   const uint32_t part = sm.part;
   const long long base = (long long)part * kPartPairs;
   if (base >= n) return;  // uniform across the CTA
-  // A pass whose digit is the same for every key keeps the order: copy through.
-  if (__syncthreads_or((long long)a.hist[tid] == n)) {
+  // A pass whose digit is the same for every key keeps the order: with a
+  // selection word it only records that the data stayed put, else it copies.
+  const bool trivial = __syncthreads_or((long long)h == n);
+  if (a.sel_out && part == 0 && tid == 0) *a.sel_out = (uint32_t)in_b ^ (trivial ? 0u : 1u);
+  if (trivial) {
+    if (a.sel_out) return;
     const long long m = min((long long)kPartPairs, n - base);
     for (long long i = tid; i < m; i += kThreads) {
-      a.keys_out[base + i] = a.keys_in[base + i];
-      a.values_out[base + i] = a.values_in[base + i];
+      keys_out[base + i] = keys_in[base + i];
+      values_out[base + i] = values_in[base + i];
     }
     return;
   }
 
   // Global offset of each digit.
-  sm.global_off[tid] = block_excl_scan(a.hist[tid], sm.scan_tmp);
+  sm.global_off[tid] = block_excl_scan(h, sm.scan_tmp);
 
   // Load (warp-striped: item i of lane l is element base + warp*512 + i*32 + l)
   // and rank within the warp.
@@ -136,8 +149,8 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   for (int i = 0; i < kItems; ++i) {
     const long long idx = base + (long long)warp * (kItems * 32) + i * 32 + lane;
     const bool valid = idx < n;
-    k[i] = valid ? __ldg(a.keys_in + idx) : 0ull;
-    v[i] = valid ? __ldg(a.values_in + idx) : 0u;
+    k[i] = valid ? keys_in[idx] : 0ull;
+    v[i] = valid ? values_in[idx] : 0u;
     dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u);
   }
 #pragma unroll
@@ -224,8 +237,8 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     const uint32_t d = (uint32_t)(key >> a.shift) & 255u;
     const uint32_t out = sm.global_off[d] + sm.prev_off[d] + ((uint32_t)j - sm.block_off[d]);
     if ((long long)out < n) {  // always true when the histogram matches the keys
-      a.keys_out[out] = key;
-      a.values_out[out] = sm.values[j];
+      keys_out[out] = key;
+      values_out[out] = sm.values[j];
     }
   }
 }
@@ -239,8 +252,9 @@ long long sort_parts(long long n) { return (n + kPartPairsSmall - 1) / kPartPair
 cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
                         int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
-                        bool* result_in_alt) {
+                        bool* result_in_alt, const uint32_t** result_sel) {
   *result_in_alt = false;
+  if (result_sel) *result_sel = nullptr;
   const int passes = sort_passes(key_bits);
   if (n_bound <= 0 || passes == 0) return cudaSuccess;
   if (passes > kMaxPasses) return cudaErrorInvalidValue;
@@ -261,7 +275,8 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * kMaxPasses, s);
+  // tickets [0, kMaxPasses) and selection words [kMaxPasses, 2 kMaxPasses + 1)
+  e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * (2 * kMaxPasses + 1), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(work.lookback, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
   if (e != cudaSuccess) return e;
@@ -276,9 +291,18 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   uint32_t* vin = values;
   unsigned long long* kout = keys_alt;
   uint32_t* vout = values_alt;
+  uint32_t* sel = result_sel ? work.part_counters + kMaxPasses : nullptr;
   for (int p = 0; p < passes; ++p) {
     PassArgs pa;
-    pa.keys_in = kin; pa.values_in = vin; pa.keys_out = kout; pa.values_out = vout;
+    if (sel) {  // buffers fixed as A = (keys, values), B = alt; the device tracks where the data is
+      pa.keys_in = keys; pa.values_in = values; pa.keys_out = keys_alt; pa.values_out = values_alt;
+      pa.sel_in = sel + p;
+      pa.sel_out = sel + p + 1;
+    } else {
+      pa.keys_in = kin; pa.values_in = vin; pa.keys_out = kout; pa.values_out = vout;
+      pa.sel_in = nullptr;
+      pa.sel_out = nullptr;
+    }
     pa.n_dev = n_dev; pa.n_bound = n_bound; pa.shift = first_bit + 8 * p;
     pa.hist = work.hist + p * kRadix;
     pa.lookback = work.lookback + (size_t)p * parts * kRadix;
@@ -293,6 +317,10 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     uint32_t* tv = vin; vin = vout; vout = tv;
   }
   *result_in_alt = (passes & 1) != 0;
+  if (sel) {
+    *result_in_alt = false;
+    *result_sel = sel + passes;
+  }
   return cudaSuccess;
 }
 
@@ -314,7 +342,7 @@ constexpr size_t kNaKeys = 0;
 constexpr size_t kNaValues = kNaKeys + 8 * (size_t)kNaMaxPairs;
 constexpr size_t kNaHist = kNaValues + 4 * (size_t)kNaMaxPairs;
 constexpr size_t kNaCounters = kNaHist + 4 * (size_t)kMaxPasses * kRadix;
-constexpr size_t kNaStatus = kNaCounters + 4 * (size_t)kMaxPasses;
+constexpr size_t kNaStatus = kNaCounters + 4 * (size_t)(2 * kMaxPasses + 1);  // tickets + selection words
 constexpr size_t kNaLookback = (kNaStatus + 4 + 255) / 256 * 256;
 constexpr size_t kNaBytes = kNaLookback + 4 * (size_t)kMaxPasses * kNaParts * kRadix;
 constexpr int kNaMaxDevices = 64;
@@ -359,8 +387,8 @@ extern "C" fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int
   unsigned long long* keys_alt = reinterpret_cast<unsigned long long*>(base + kNaKeys);
   uint32_t* values_alt = reinterpret_cast<uint32_t*>(base + kNaValues);
   bool alt = false;
-  if (launch_sort(keys, d_values, keys_alt, values_alt, nullptr, n, 0, key_bits, false, w, status, s, &alt) !=
-      cudaSuccess)
+  if (launch_sort(keys, d_values, keys_alt, values_alt, nullptr, n, 0, key_bits, false, w, status, s, &alt,
+                  nullptr) != cudaSuccess)
     return FS4D_ERR_CUDA;
   if (alt) {
     if (cudaMemcpyAsync(d_keys, keys_alt, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
