@@ -78,7 +78,7 @@ struct Work {
   DevBuf dkeys, dvals, dkeys_alt, dvals_alt;  // per-Gaussian depth sort
   DevBuf keys, values, keys_alt, values_alt;
   DevBuf sort_lb;
-  DevBuf ranges, tile_count;
+  DevBuf ranges, tile_count, tile_order;
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
   DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
@@ -365,6 +365,7 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
   if (n_tiles > w.cap_tiles) {
     FS4D_CUDA(c, ensure(w.ranges, 8 * (size_t)n_tiles));
     FS4D_CUDA(c, ensure(w.tile_count, 4 * (size_t)n_tiles));
+    FS4D_CUDA(c, ensure(w.tile_order, 4 * (size_t)n_tiles));
     w.cap_tiles = n_tiles;
   }
   if (pairs > w.cap_pairs) {
@@ -505,7 +506,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   FS4D_CUDA(c, launch_scan_emit(ea, stream));
   // tile ranges and the pair sort's digit histograms straight from the tile counts
   FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), tx * ty, P<uint32_t>(w.num_pairs), P<uint2>(w.ranges),
-                                P<uint32_t>(w.hist), sort_passes(tile_bits), stream));
+                                P<uint32_t>(w.hist), sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
   mark(e, 3);
   return FS4D_OK;
 }
@@ -535,7 +536,8 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   mark(e, 5);  // the ranges came with the tile scan: an empty stage
   mark(e, 6);
   FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values, P<float2>(w.xy),
-                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s));
+                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s,
+                                P<uint32_t>(w.tile_order)));
   mark(e, 7);
   return FS4D_OK;
 }
@@ -607,7 +609,7 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     Work& w = c->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.ts, &w.host_img,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.ts, &w.host_img,
                      &w.grad_pair, &w.gd, &w.acts, &w.wpartial};
     for (DevBuf* b : all) release(*b);
     release(c->status);
@@ -1121,7 +1123,7 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
   FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
                                 reinterpret_cast<uint2*>(d_ranges), P<uint32_t>(w.hist), sort_passes(tile_bits),
-                                c->stream));
+                                nullptr, c->stream));
   long long K = 0;
   if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
   *h_num_pairs = K;
@@ -1715,7 +1717,7 @@ fs4d_status fs4d_server_destroy(fs4d_server* sv) {
     Work& w = sl->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &sl->status, &sl->dcam, &sl->dt,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &sl->status, &sl->dcam, &sl->dt,
                      &sl->image};
     for (DevBuf* b : all) release(*b);
     cudaFreeHost(sl->h_cam);

@@ -194,12 +194,14 @@ constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t* __restrict__ tile_count, int n_tiles,
                                                                  const uint32_t* __restrict__ num_pairs,
                                                                  uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
-                                                                 int passes) {
+                                                                 int passes, uint32_t* __restrict__ order) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_hist[kMaxPasses][256];
+  __shared__ uint32_t s_len[33];          // tiles per length class floor(log2(count)) + 1 (0: empty)
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
   for (int i = tid; i < kMaxPasses * 256; i += kScanThreads) (&s_hist[0][0])[i] = 0;
+  if (tid < 33) s_len[tid] = 0;
   const bool overflow = num_pairs[1] == 0u && num_pairs[0] != 0u;
   const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
   const int t0 = min(tid * per, n_tiles), t1 = min(t0 + per, n_tiles);
@@ -226,6 +228,28 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
     __syncthreads();
     for (int i = tid; i < passes * 256; i += kScanThreads) hist[i] = (&s_hist[0][0])[i];
   }
+  if (order) {
+    // Launch order for the compositing: tiles by length class, longest first, so
+    // the longest lists start first and do not form the tail.
+    for (int t = t0; t < t1; ++t) {
+      const uint32_t c = overflow ? 0u : tile_count[t];
+      atomicAdd(&s_len[32 - (c ? 32 - __clz(c) : 0)], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t run2 = 0;
+      for (int b = 0; b < 33; ++b) {
+        const uint32_t v = s_len[b];
+        s_len[b] = run2;
+        run2 += v;
+      }
+    }
+    __syncthreads();
+    for (int t = t0; t < t1; ++t) {
+      const uint32_t c = overflow ? 0u : tile_count[t];
+      order[atomicAdd(&s_len[32 - (c ? 32 - __clz(c) : 0)], 1u)] = (uint32_t)t;
+    }
+  }
 }
 
 }  // namespace
@@ -247,9 +271,9 @@ cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
-                             uint32_t* hist, int passes, cudaStream_t s) {
+                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s) {
   if (passes > kMaxPasses || n_tiles < 1) return cudaErrorInvalidValue;
-  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes);
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes, order);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Per-tile front-to-back alpha compositing (Eq. 4 with the Gaussian weight of
-// Eq. 1).  One 256-thread CTA per 16x16 screen tile, one pixel per thread; warp
+// Eq. 1).  One 256-thread CTA per 16x16 screen tile (optionally in a given launch
+// order, longest lists first), one pixel per thread; warp
 // w owns the 8x4 pixel block (w % 2, w / 2) of the tile.  The tile's depth-
 // sorted list is walked in batches of 256: each thread gathers one Gaussian into
 // shared memory -- position and log2-scaled conic, opacity and colour -- and the
@@ -59,13 +60,14 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
                                                             const float2* __restrict__ xy,
                                                             const float4* __restrict__ conic_opacity,
                                                             const float* __restrict__ rgb, float* __restrict__ image,
-                                                            float* __restrict__ t_final, int* __restrict__ n_contrib) {
+                                                            float* __restrict__ t_final, int* __restrict__ n_contrib,
+                                                            const uint32_t* __restrict__ order) {
   __shared__ float4 s_g0[kBatch];       // x, y, a2, c2
   __shared__ float4 s_g1[kBatch];       // b2, opacity, red, green
   __shared__ float s_blue[kBatch];
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kWarps][kBatch];
-  const int tile = blockIdx.x;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lane_lt = (1u << lane) - 1u;
@@ -140,11 +142,11 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
 
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values, const float2* xy,
                              const float4* conic_opacity, const float* rgb, float* image, float* t_final,
-                             int* n_contrib, cudaStream_t s) {
+                             int* n_contrib, cudaStream_t s, const uint32_t* order) {
   const int tiles_x = (width + kTile - 1) / kTile, tiles_y = (height + kTile - 1) / kTile;
   if (tiles_x * tiles_y == 0) return cudaSuccess;
   composite_kernel<<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy, conic_opacity,
-                                                          rgb, image, t_final, n_contrib);
+                                                          rgb, image, t_final, n_contrib, order);
   return cudaGetLastError();
 }
 

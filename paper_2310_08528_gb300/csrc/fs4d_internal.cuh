@@ -152,10 +152,11 @@ int emit_parts(int n);          // scan partitions of the emit kernel
 // keys[i] = float bits of depth[i] (upper word 0), vals[i] = i: input of the depth sort
 cudaError_t launch_depth_keys(const float* depth, int n, unsigned long long* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s);
-// tile ranges (from the per-tile counts; all (0, 0) when num_pairs[1] == 0 < num_pairs[0])
-// and, if hist != NULL, the [passes][256] digit histograms of the pair sort on the tile bits
+// tile ranges (from the per-tile counts; all (0, 0) when num_pairs[1] == 0 < num_pairs[0]),
+// if hist != NULL the [passes][256] digit histograms of the pair sort on the tile bits, and
+// if order != NULL a permutation of the tiles, longest lists first (compositing launch order)
 cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
-                             uint32_t* hist, int passes, cudaStream_t s);
+                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s);
 
 int sort_passes(int key_bits);
 long long sort_parts(long long n);
@@ -171,9 +172,10 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
                         int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
                         bool* result_in_alt, const uint32_t** result_sel = nullptr);
+// order (optional): CTA i composites tile order[i]
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
                              const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
-                             float* t_final, int* n_contrib, cudaStream_t s);
+                             float* t_final, int* n_contrib, cudaStream_t s, const uint32_t* order = nullptr);
 
 }  // namespace fs4d
 
