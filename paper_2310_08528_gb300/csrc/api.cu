@@ -71,7 +71,24 @@ struct Scene {
 };
 
 // Per-context work memory, grown on demand (never during a capture).
+// Per-frame state that must start at zero (histograms, tickets, selection words,
+// pair count, tile counts, look-back tables), carved out of one allocation that
+// ONE memset clears at the start of a frame.
+struct FrameZero {
+  uint32_t* hist = nullptr;              // [8][256]: depth-key byte histograms, then the pair sort's
+  uint32_t* counters = nullptr;          // [64]: [0] emission ticket, [8, 25) depth sort, [32, 49) pair sort
+  uint32_t* num_pairs = nullptr;         // [4]
+  uint32_t* tile_count = nullptr;        // [n_tiles]
+  unsigned long long* emit_lb = nullptr; // [emit_parts(n) + 1]
+  uint32_t* dlb = nullptr;               // depth-sort look-back [4][dparts][256]
+  uint32_t* plb = nullptr;               // pair-sort look-back [passes][pparts][256]
+  long long dparts = 0, pparts = 0;
+  size_t bytes = 0;
+};
+
 struct Work {
+  DevBuf zero;                             // FrameZero's allocation
+  FrameZero z;                             // its layout for the frame in flight
   DevBuf dmeans, dquats, dscales;          // deformed Gaussians
   DevBuf xy, co, rgb, depth, radius, rect; // projected
   DevBuf offsets, emit_lb, counters, num_pairs, hist;
@@ -90,6 +107,38 @@ struct Work {
 constexpr int kSortMaxPasses = 8;
 constexpr int kCounters = 32;  // [0] emit ticket, [8, 25) radix-sort tickets and selection words
 constexpr int kEmitCounters = 8;  // the words reset before an emission (the sort's words stay)
+
+// Byte layout of FrameZero for n Gaussians, n_tiles tiles, cap pairs and a pair
+// sort of pair_passes passes (256-byte aligned blocks); fills z when base != NULL.
+size_t frame_zero_layout(int n, int n_tiles, long long cap, int pair_passes, unsigned char* base, FrameZero* z) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const long long dparts = sort_parts(std::max(n, 1)), pparts = sort_parts(std::max<long long>(cap, 1));
+  const size_t o_hist = take(4 * 256 * (size_t)kSortMaxPasses);
+  const size_t o_cnt = take(4 * 64);
+  const size_t o_np = take(16);
+  const size_t o_tc = take(4 * (size_t)n_tiles);
+  const size_t o_elb = take(8 * (size_t)(emit_parts(std::max(n, 1)) + 1));
+  const size_t o_dlb = take(4 * 256 * 4 * (size_t)dparts);
+  const size_t o_plb = take(4 * 256 * (size_t)pair_passes * pparts);
+  if (base && z) {
+    z->hist = reinterpret_cast<uint32_t*>(base + o_hist);
+    z->counters = reinterpret_cast<uint32_t*>(base + o_cnt);
+    z->num_pairs = reinterpret_cast<uint32_t*>(base + o_np);
+    z->tile_count = reinterpret_cast<uint32_t*>(base + o_tc);
+    z->emit_lb = reinterpret_cast<unsigned long long*>(base + o_elb);
+    z->dlb = reinterpret_cast<uint32_t*>(base + o_dlb);
+    z->plb = reinterpret_cast<uint32_t*>(base + o_plb);
+    z->dparts = dparts;
+    z->pparts = pparts;
+    z->bytes = off;
+  }
+  return off;
+}
 
 }  // namespace
 
@@ -381,6 +430,9 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
     FS4D_CUDA(c, ensure(w.sort_lb, 4 * 256 * (size_t)kSortMaxPasses * parts));
     w.sort_parts_cap = parts;
   }
+  const size_t zb = frame_zero_layout(w.cap_n, w.cap_tiles, w.cap_pairs,
+                                      sort_passes(ceil_log2(std::max(w.cap_tiles, 1))), nullptr, nullptr);
+  FS4D_CUDA(c, ensure(w.zero, zb));
   return FS4D_OK;
 }
 
@@ -457,7 +509,13 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   Work& w = *e.w;
   const cudaStream_t stream = e.s;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
+  const int tile_bits = ceil_log2((long long)tx * ty);
+  // every buffer the frame needs at zero, in one memset
+  FrameZero& z = w.z;
+  frame_zero_layout(s->n, tx * ty, cap, sort_passes(tile_bits), static_cast<unsigned char*>(w.zero.p), &z);
+  if (z.bytes > w.zero.bytes) return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory was not reserved");
   mark(e, 0);
+  FS4D_CUDA(c, cudaMemsetAsync(w.zero.p, 0, z.bytes, stream));
   if (deform) {
     DeformArgs da = deform_args(s, d_t, t, 1, P<float>(w.dmeans), P<float>(w.dquats), P<float>(w.dscales));
     fs4d_status st = run_deform(c, s, prec, da, stream, e.status);
@@ -474,39 +532,36 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
   pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
   pa.depth_keys = P<unsigned long long>(w.dkeys); pa.depth_vals = P<uint32_t>(w.dvals);
-  pa.depth_hist = P<uint32_t>(w.hist);
-  FS4D_CUDA(c, cudaMemsetAsync(w.hist.p, 0, 4 * 256 * kSortMaxPasses, stream));
+  pa.depth_hist = z.hist;
   FS4D_CUDA(c, launch_project(pa, stream));
   mark(e, 2);
   // Gaussians in (float32 depth, index) order: the emission order
   bool dalt = false;
   const uint32_t* dsel = nullptr;
+  SortWork dsw;
+  dsw.hist = z.hist; dsw.lookback = z.dlb; dsw.part_counters = z.counters + 8; dsw.max_parts = z.dparts;
+  dsw.prezeroed = true;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
-                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, sort_work(w), e.status, stream,
-                           &dalt, &dsel));
-  const int tile_bits = ceil_log2((long long)tx * ty);
-  FS4D_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * kEmitCounters, stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.num_pairs.p, 0, 16, stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.tile_count.p, 0, 4 * (size_t)tx * ty, stream));
-  FS4D_CUDA(c, cudaMemsetAsync(w.emit_lb.p, 0, 8 * (size_t)emit_parts(s->n), stream));
+                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, dsw, e.status, stream, &dalt,
+                           &dsel));
   EmitArgs ea{};
   ea.n = s->n; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
   ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
   ea.capacity = cap;
   ea.keys = P<unsigned long long>(w.keys); ea.values = P<uint32_t>(w.values);
   ea.offsets = P<uint32_t>(w.offsets);
-  ea.lookback = P<unsigned long long>(w.emit_lb);
-  ea.part_counter = P<uint32_t>(w.counters);
-  ea.num_pairs = P<uint32_t>(w.num_pairs);
-  ea.num_pairs_sort = P<uint32_t>(w.num_pairs) + 1;
-  ea.tile_count = P<uint32_t>(w.tile_count);
+  ea.lookback = z.emit_lb;
+  ea.part_counter = z.counters;
+  ea.num_pairs = z.num_pairs;
+  ea.num_pairs_sort = z.num_pairs + 1;
+  ea.tile_count = z.tile_count;
   ea.n_tiles = tx * ty;
   ea.status = e.status;
   ea.report_overflow = report ? 1 : 0;
   FS4D_CUDA(c, launch_scan_emit(ea, stream));
   // tile ranges and the pair sort's digit histograms straight from the tile counts
-  FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), tx * ty, P<uint32_t>(w.num_pairs), P<uint2>(w.ranges),
-                                P<uint32_t>(w.hist), sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
+  FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), z.hist,
+                                sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
   mark(e, 3);
   return FS4D_OK;
 }
@@ -523,13 +578,18 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   Work& w = *e.w;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
   const int tile_bits = ceil_log2((long long)tx * ty);
-  const uint32_t* n_dev = P<uint32_t>(w.num_pairs) + 1;
+  const FrameZero& z = w.z;
+  const uint32_t* n_dev = z.num_pairs + 1;
   bool alt = false;
   mark(e, 4);
   // pairs arrive in depth order: a stable sort on the tile bits gives (tile, depth, index)
+  SortWork psw;
+  psw.hist = z.hist; psw.lookback = z.plb; psw.part_counters = z.counters + 32; psw.max_parts = z.pparts;
+  psw.prezeroed = true;
+  if (n_bound > z.pparts * 1024) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, sort_work(w), e.status,
-                           e.s, &alt));
+                           P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
+                           &alt));
   unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
   if (values_out) *values_out = values;
@@ -547,8 +607,8 @@ fs4d_status frame_back(fs4d_ctx* c, const fs4d_camera& shape, long long n_bound,
   return frame_back(env_of(c), shape, n_bound, d_image, d_t_final, d_n_contrib, &c->last_values);
 }
 
-fs4d_status read_pairs(fs4d_ctx* c, long long* K) {
-  FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->w.num_pairs.p, 8, cudaMemcpyDeviceToHost, c->stream));
+fs4d_status read_pairs(fs4d_ctx* c, const uint32_t* d_num_pairs, long long* K) {
+  FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned, d_num_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
   FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
   *K = (long long)c->h_pinned[0];
   return FS4D_OK;
@@ -562,7 +622,7 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false);
   if (st != FS4D_OK) return st;
   long long K = 0;
-  if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
+  if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
   if (K >= 0xffffffffll) return fail(c, FS4D_ERR_CAPACITY, "more than 2^32-1 tile pairs in one frame");
   if (K > c->w.cap_pairs) {
     if ((st = ensure_work(c, s->n, n_tiles, K + K / 4)) != FS4D_OK) return st;
@@ -609,7 +669,7 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     Work& w = c->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.ts, &w.host_img,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &w.ts, &w.host_img,
                      &w.grad_pair, &w.gd, &w.acts, &w.wpartial};
     for (DevBuf* b : all) release(*b);
     release(c->status);
@@ -1125,7 +1185,7 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
                                 reinterpret_cast<uint2*>(d_ranges), P<uint32_t>(w.hist), sort_passes(tile_bits),
                                 nullptr, c->stream));
   long long K = 0;
-  if ((st = read_pairs(c, &K)) != FS4D_OK) return st;
+  if ((st = read_pairs(c, P<uint32_t>(w.num_pairs), &K)) != FS4D_OK) return st;
   *h_num_pairs = K;
   if (K > capacity) {
     return fail(c, FS4D_ERR_CAPACITY, "bin_sort: " + std::to_string(K) + " pairs exceed the capacity");
@@ -1340,11 +1400,11 @@ Slot* new_slot(fs4d_server* sv) {
 // Make the slot hold a frame of n Gaussians at w x h with `pairs` capacity.
 fs4d_status fit_slot(fs4d_server* sv, Slot* sl, int n, int w, int h, long long pairs) {
   fs4d_ctx* c = sv->c;
-  const void* before[4] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->image.p};
+  const void* before[5] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p};
   fs4d_status st = ensure_work(c, sl->w, sl->stream, n, tiles_of(w) * tiles_of(h), pairs);
   if (st != FS4D_OK) return st;
   if ((size_t)w * h * 12 > sl->image.bytes) FS4D_CUDA(c, ensure(sl->image, (size_t)w * h * 12));
-  const void* after[4] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->image.p};
+  const void* after[5] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p};
   if (std::memcmp(before, after, sizeof(before)) != 0) {  // graphs captured on old buffers are stale
     cudaStreamSynchronize(sl->stream);
     for (auto& kv : sl->graphs) cudaGraphExecDestroy(kv.second);
@@ -1550,7 +1610,7 @@ void admit_and_launch(fs4d_server* sv) {
                                  r.out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  sl->stream) == cudaSuccess;
     sok = sok && cudaMemcpyAsync(sl->h_out, sl->status.p, 4, cudaMemcpyDeviceToHost, sl->stream) == cudaSuccess &&
-          cudaMemcpyAsync(sl->h_out + 1, sl->w.num_pairs.p, 4, cudaMemcpyDeviceToHost, sl->stream) == cudaSuccess &&
+          cudaMemcpyAsync(sl->h_out + 1, sl->w.z.num_pairs, 4, cudaMemcpyDeviceToHost, sl->stream) == cudaSuccess &&
           cudaEventRecord(sl->done, sl->stream) == cudaSuccess;
     if (!sok) {
       scene->refs--;
@@ -1717,7 +1777,7 @@ fs4d_status fs4d_server_destroy(fs4d_server* sv) {
     Work& w = sl->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &sl->status, &sl->dcam, &sl->dt,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &sl->status, &sl->dcam, &sl->dt,
                      &sl->image};
     for (DevBuf* b : all) release(*b);
     cudaFreeHost(sl->h_cam);

@@ -135,9 +135,10 @@ struct EmitArgs {
 
 struct SortWork {
   uint32_t* hist;               // [8][256]
-  uint32_t* lookback;           // [8][max_parts][256]
+  uint32_t* lookback;           // [passes][max_parts][256]
   uint32_t* part_counters;      // [2 * 8 + 1]: pass tickets, then selection words
-  long long max_parts;
+  long long max_parts;          // >= sort_parts(n_bound) lets every partition size be chosen
+  bool prezeroed = false;       // tickets, selection words and look-back already zero
 };
 
 // ---------------------------------------------------------------- launchers

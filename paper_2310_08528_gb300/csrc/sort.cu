@@ -275,11 +275,13 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  // tickets [0, kMaxPasses) and selection words [kMaxPasses, 2 kMaxPasses + 1)
-  e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * (2 * kMaxPasses + 1), s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(work.lookback, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
-  if (e != cudaSuccess) return e;
+  if (!work.prezeroed) {
+    // tickets [0, kMaxPasses) and selection words [kMaxPasses, 2 kMaxPasses + 1)
+    e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * (2 * kMaxPasses + 1), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(work.lookback, 0, sizeof(uint32_t) * (size_t)passes * parts * kRadix, s);
+    if (e != cudaSuccess) return e;
+  }
   if (!hist_ready) {
     e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     if (e != cudaSuccess) return e;
