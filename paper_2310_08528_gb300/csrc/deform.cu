@@ -88,6 +88,10 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   float* X = sw + a.mg.total;   // [XR][kGS]: f_h, then a1, then f_d (in place)
   float* Hd = X + XR * kGS;     // [64][kGS]: hidden layer of the current head
   float* D = Hd + kWidth * kGS; // [10][kGS]: deltas
+  // the tile's rows: (X, t), quaternion, (log-scales, Gaussian index as bits)
+  float4* sRowX = reinterpret_cast<float4*>(D + kDeltaDim * kGS);
+  float4* sRowQ = sRowX + kTileG;
+  float4* sRowS = sRowQ + kTileG;
   for (int i = threadIdx.x; i < a.mg.total / 4; i += kThreads)
     smem4[i] = __ldg(reinterpret_cast<const float4*>(a.mlp_t) + i);
 
@@ -100,6 +104,25 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long base = tile * kTileG;
     __syncthreads();  // weights loaded / the previous tile fully written out
+    // ---- 0. the tile's rows gathered once into shared memory (the work-order
+    // index, then position, t, quaternion and log-scales in one round of loads)
+    if (threadIdx.x < kTileG) {
+      const long long gi = base + threadIdx.x;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), q4 = x, sc = x;
+      if (gi < total) {
+        const int ti = (int)(gi / a.n);
+        const int gw = (int)(gi - (long long)ti * a.n);
+        const int g = a.perm ? (int)a.perm[gw] : gw;  // spatially coherent work order
+        const float t = a.ts ? a.ts[ti] : a.t0;
+        x = make_float4(a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2], t);
+        q4 = reinterpret_cast<const float4*>(a.quats)[g];
+        sc = make_float4(a.log_scales[3 * g], a.log_scales[3 * g + 1], a.log_scales[3 * g + 2], __int_as_float(g));
+      }
+      sRowX[threadIdx.x] = x;
+      sRowQ[threadIdx.x] = q4;
+      sRowS[threadIdx.x] = sc;
+    }
+    __syncthreads();
     // ---- 1. Eq. 5 into X[0..HL)
     for (int item = threadIdx.x; item < kTileG * L * Q; item += kThreads) {
       const int q = item % Q, rl = item / Q;
@@ -107,15 +130,12 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
       const long long gi = base + r;
       float f[4] = {0.f, 0.f, 0.f, 0.f};
       if (gi < total) {
-        const int ti = (int)(gi / a.n);
-        const int gw = (int)(gi - (long long)ti * a.n);
-        const int g = a.perm ? (int)a.perm[gw] : gw;  // spatially coherent work order
-        const float t = a.ts ? a.ts[ti] : a.t0;
+        const float4 xr = sRowX[r];
         float c[4];
-        c[0] = (a.means[3 * g] - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
-        c[1] = (a.means[3 * g + 1] - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f;
-        c[2] = (a.means[3 * g + 2] - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
-        c[3] = 2.f * t - 1.f;
+        c[0] = (xr.x - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
+        c[1] = (xr.y - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f;
+        c[2] = (xr.z - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
+        c[3] = 2.f * xr.w - 1.f;
         f[0] = f[1] = f[2] = f[3] = 1.f;
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
@@ -183,8 +203,8 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
       const long long gi = base + r;
       if (gi < total) {
         const int ti = (int)(gi / a.n);
-        const int gw = (int)(gi - (long long)ti * a.n);
-        const int g = a.perm ? (int)a.perm[gw] : gw;
+        const float4 xr = sRowX[r], qv = sRowQ[r], sr = sRowS[r];
+        const int g = __float_as_int(sr.w);
         float d[kDeltaDim];
 #pragma unroll
         for (int k = 0; k < kDeltaDim; ++k) d[k] = D[k * kGS + r];
@@ -192,14 +212,13 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
         float* om = a.out_tab ? a.out_tab[3 * ti] : a.out_means;
         float* oq = a.out_tab ? a.out_tab[3 * ti + 1] : a.out_quats;
         float* os = a.out_tab ? a.out_tab[3 * ti + 2] : a.out_log_scales;
-        om[3 * o + 0] = a.means[3 * g + 0] + d[0];
-        om[3 * o + 1] = a.means[3 * g + 1] + d[1];
-        om[3 * o + 2] = a.means[3 * g + 2] + d[2];
-        const float4 qv = reinterpret_cast<const float4*>(a.quats)[g];
+        om[3 * o + 0] = xr.x + d[0];
+        om[3 * o + 1] = xr.y + d[1];
+        om[3 * o + 2] = xr.z + d[2];
         reinterpret_cast<float4*>(oq)[o] = make_float4(qv.x + d[3], qv.y + d[4], qv.z + d[5], qv.w + d[6]);
-        os[3 * o + 0] = a.log_scales[3 * g + 0] + d[7];
-        os[3 * o + 1] = a.log_scales[3 * g + 1] + d[8];
-        os[3 * o + 2] = a.log_scales[3 * g + 2] + d[9];
+        os[3 * o + 0] = sr.x + d[7];
+        os[3 * o + 1] = sr.y + d[8];
+        os[3 * o + 2] = sr.z + d[9];
       }
     }
   }
@@ -209,7 +228,8 @@ template <int H, int L>
 cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
   constexpr int HL = H * L;
   constexpr int XR = HL > kWidth ? HL : kWidth;
-  const size_t smem = sizeof(float) * ((size_t)a.mg.total + (size_t)(XR + kWidth + kDeltaDim) * kGS);
+  const size_t smem = sizeof(float) * ((size_t)a.mg.total + (size_t)(XR + kWidth + kDeltaDim) * kGS) +
+                      3 * kTileG * sizeof(float4);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(deform_fp32_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,

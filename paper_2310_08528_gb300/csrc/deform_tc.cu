@@ -176,6 +176,10 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   uint64_t* sMbar = reinterpret_cast<uint64_t*>(sBias + kBiasFloats);
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(sMbar + 1);
   uint32_t* sFail = sTmem + 1;
+  // the tile's rows: (X, t), quaternion, (log-scales, Gaussian index as bits)
+  float4* sRowX = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(sMbar) + 16);
+  float4* sRowQ = sRowX + kRows;
+  float4* sRowS = sRowQ + kRows;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < tg.bytes / 16; i += kThreads)
@@ -203,6 +207,26 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long base = tile * kRows;
+    // ---- 0. the tile's rows gathered once into shared memory (the work-order
+    // index, then position, t, quaternion and log-scales in one round of loads),
+    // so the sampling and the last epilogue chase no indices
+    if (tid < kRows) {
+      const long long gi = base + tid;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), q = x, sc = x;
+      if (gi < total) {
+        const int ti = (int)(gi / a.n);
+        const int gw = (int)(gi - (long long)ti * a.n);
+        const int g = a.perm ? (int)a.perm[gw] : gw;
+        const float t = a.ts ? a.ts[ti] : a.t0;
+        x = make_float4(a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2], t);
+        q = reinterpret_cast<const float4*>(a.quats)[g];
+        sc = make_float4(a.log_scales[3 * g], a.log_scales[3 * g + 1], a.log_scales[3 * g + 2], __int_as_float(g));
+      }
+      sRowX[tid] = x;
+      sRowQ[tid] = q;
+      sRowS[tid] = sc;
+    }
+    __syncthreads();
     // ---- 1. HexPlane features (Eq. 5) -> A1 [128 x HL] BF16.  Four (H = 32) or
     // two (H = 16) consecutive lanes share one (Gaussian, level) item and each
     // owns 8 features, so a warp's 16-byte loads cover whole 64-byte grid
@@ -216,15 +240,12 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) f[k] = 0.f;
       if (gi < total) {
-        const int ti = (int)(gi / a.n);
-        const int gw = (int)(gi - (long long)ti * a.n);
-        const int g = a.perm ? (int)a.perm[gw] : gw;  // spatially coherent work order
-        const float t = a.ts ? a.ts[ti] : a.t0;
+        const float4 xr = sRowX[r];
         float c[4];
-        c[0] = (a.means[3 * g] - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
-        c[1] = (a.means[3 * g + 1] - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f;
-        c[2] = (a.means[3 * g + 2] - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
-        c[3] = 2.f * t - 1.f;
+        c[0] = (xr.x - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f;
+        c[1] = (xr.y - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f;
+        c[2] = (xr.z - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f;
+        c[3] = 2.f * xr.w - 1.f;
 #pragma unroll
         for (int k = 0; k < 8; ++k) f[k] = 1.f;
 #pragma unroll
@@ -328,22 +349,21 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
       const long long gi = base + row;
       if (gi < total) {
         const int ti = (int)(gi / a.n);
-        const int gw = (int)(gi - (long long)ti * a.n);
-        const int g = a.perm ? (int)a.perm[gw] : gw;
+        const float4 xr = sRowX[row], q = sRowQ[row], sr = sRowS[row];
+        const int g = __float_as_int(sr.w);
         const float* bo = sBias + 320;
         const long long o = a.out_tab ? (long long)g : (long long)ti * a.n + g;
         float* om = a.out_tab ? a.out_tab[3 * ti] : a.out_means;
         float* oq = a.out_tab ? a.out_tab[3 * ti + 1] : a.out_quats;
         float* os = a.out_tab ? a.out_tab[3 * ti + 2] : a.out_log_scales;
-        om[3 * o + 0] = a.means[3 * g + 0] + (v[0] + bo[0]);
-        om[3 * o + 1] = a.means[3 * g + 1] + (v[1] + bo[1]);
-        om[3 * o + 2] = a.means[3 * g + 2] + (v[2] + bo[2]);
-        const float4 q = reinterpret_cast<const float4*>(a.quats)[g];
+        om[3 * o + 0] = xr.x + (v[0] + bo[0]);
+        om[3 * o + 1] = xr.y + (v[1] + bo[1]);
+        om[3 * o + 2] = xr.z + (v[2] + bo[2]);
         reinterpret_cast<float4*>(oq)[o] =
             make_float4(q.x + (v[3] + bo[3]), q.y + (v[4] + bo[4]), q.z + (v[5] + bo[5]), q.w + (v[6] + bo[6]));
-        os[3 * o + 0] = a.log_scales[3 * g + 0] + (v[7] + bo[7]);
-        os[3 * o + 1] = a.log_scales[3 * g + 1] + (v[8] + bo[8]);
-        os[3 * o + 2] = a.log_scales[3 * g + 2] + (v[9] + bo[9]);
+        os[3 * o + 0] = sr.x + (v[7] + bo[7]);
+        os[3 * o + 1] = sr.y + (v[8] + bo[8]);
+        os[3 * o + 2] = sr.z + (v[9] + bo[9]);
       }
     }
     tc_fence_before();
@@ -358,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 
 template <int H, int L>
 cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16;
+  const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16 + 3 * kRows * 16;
   static bool attr = false;
   if (!attr) {
     cudaError_t e =
