@@ -54,6 +54,8 @@ __device__ __forceinline__ uint32_t block_mask(float2 p, float4 co, float thr, i
   return mask;
 }
 
+// AUX: also write each pixel's final transmittance and last contributor.
+template <bool AUX>
 __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int height, int tiles_x,
                                                             const uint2* __restrict__ ranges,
                                                             const uint32_t* __restrict__ values,
@@ -106,25 +108,44 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
       cnt += __popc(bal);
     }
     __syncwarp();
-    for (int i = 0; i < cnt; ++i) {
-      if (done) continue;
-      const int j = list[i];
-      const float4 g0 = s_g0[j];
-      const float4 g1 = s_g1[j];
-      float gw;
-      const float alpha = composite_alpha(g0, g1.x, g1.y, g0.x - fx, g0.y - fy, gw);
-      if (alpha == 0.f) continue;
-      const float Tn = T * (1.f - alpha);
-      if (Tn < kTMin) {
-        done = true;
-        continue;
+    // two Gaussians per step: both weights are evaluated before the two
+    // (sequential, front-to-back) transmittance updates
+    for (int i = 0; i < cnt && !done; i += 2) {
+      const int ja = list[i];
+      const bool has_b = i + 1 < cnt;
+      const int jb = has_b ? list[i + 1] : ja;
+      const float4 a0 = s_g0[ja], a1 = s_g1[ja];
+      const float4 b0 = s_g0[jb], b1 = s_g1[jb];
+      float ga, gb;
+      const float alpha_a = composite_alpha(a0, a1.x, a1.y, a0.x - fx, a0.y - fy, ga);
+      float alpha_b = composite_alpha(b0, b1.x, b1.y, b0.x - fx, b0.y - fy, gb);
+      if (!has_b) alpha_b = 0.f;
+      if (alpha_a > 0.f) {
+        const float Tn = T * (1.f - alpha_a);
+        if (Tn < kTMin) {
+          done = true;
+          break;
+        }
+        const float w = alpha_a * T;
+        R += a1.z * w;
+        G += a1.w * w;
+        B += s_blue[ja] * w;
+        T = Tn;
+        if (AUX) last = base + ja + 1;
       }
-      const float w = alpha * T;
-      R += g1.z * w;
-      G += g1.w * w;
-      B += s_blue[j] * w;
-      T = Tn;
-      last = base + j + 1;
+      if (alpha_b > 0.f) {
+        const float Tn = T * (1.f - alpha_b);
+        if (Tn < kTMin) {
+          done = true;
+          break;
+        }
+        const float w = alpha_b * T;
+        R += b1.z * w;
+        G += b1.w * w;
+        B += s_blue[jb] * w;
+        T = Tn;
+        if (AUX) last = base + jb + 1;
+      }
     }
     __syncwarp();
   }
@@ -133,8 +154,10 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
     image[3 * pix] = R;
     image[3 * pix + 1] = G;
     image[3 * pix + 2] = B;
-    if (t_final) t_final[pix] = T;
-    if (n_contrib) n_contrib[pix] = last;
+    if (AUX) {
+      if (t_final) t_final[pix] = T;
+      if (n_contrib) n_contrib[pix] = last;
+    }
   }
 }
 
@@ -145,8 +168,13 @@ cudaError_t launch_composite(int width, int height, const uint2* ranges, const u
                              int* n_contrib, cudaStream_t s, const uint32_t* order) {
   const int tiles_x = (width + kTile - 1) / kTile, tiles_y = (height + kTile - 1) / kTile;
   if (tiles_x * tiles_y == 0) return cudaSuccess;
-  composite_kernel<<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy, conic_opacity,
-                                                          rgb, image, t_final, n_contrib, order);
+  if (t_final || n_contrib)
+    composite_kernel<true><<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy,
+                                                                  conic_opacity, rgb, image, t_final, n_contrib, order);
+  else
+    composite_kernel<false><<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy,
+                                                                   conic_opacity, rgb, image, t_final, n_contrib,
+                                                                   order);
   return cudaGetLastError();
 }
 
