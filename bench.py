@@ -50,10 +50,17 @@ def parse():
     return ap.parse_args()
 
 
+_VIEWS = None
+
+
 def views(step: int, rank: int, world: int):
-    from paper_2310_08528_gb300 import scenegen as sg
-    cams = sg.hemisphere_cameras(N_CAMS, width=WIDTH, height=HEIGHT, seed=0)
-    ts = np.linspace(0.0, 1.0, N_TIMES)
+    """View `step` of this rank: camera (step*world+rank) % 50, timestamp index
+    ((step*world+rank) // 50) % 20.  The camera list is built once."""
+    global _VIEWS
+    if _VIEWS is None:
+        from paper_2310_08528_gb300 import scenegen as sg
+        _VIEWS = (sg.hemisphere_cameras(N_CAMS, width=WIDTH, height=HEIGHT, seed=0), np.linspace(0.0, 1.0, N_TIMES))
+    cams, ts = _VIEWS
     i = step * world + rank
     return cams[i % N_CAMS], float(ts[(i // N_CAMS) % N_TIMES])
 
