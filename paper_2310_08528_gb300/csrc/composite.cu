@@ -9,7 +9,8 @@
 // (ballot + popc, order kept) and walks only those; every pixel evaluates Eq. 1
 // exactly for them.  The mask is conservative, so it never changes a decision.
 // A warp whose pixels have all saturated skips the batch; a CTA stops as soon as
-// all of its pixels have (__syncthreads_count).
+// all of its pixels have (__syncthreads_count).  Batches alternate between two
+// staging buffers, so one barrier per batch suffices.
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
@@ -64,10 +65,11 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
                                                             const float* __restrict__ rgb, float* __restrict__ image,
                                                             float* __restrict__ t_final, int* __restrict__ n_contrib,
                                                             const uint32_t* __restrict__ order) {
-  __shared__ float4 s_g0[kBatch];       // x, y, a2, c2
-  __shared__ float4 s_g1[kBatch];       // b2, opacity, red, green
-  __shared__ float s_blue[kBatch];
-  __shared__ uint32_t s_mask[kBatch];
+  // two staging buffers: batch i is staged while batch i - 1 may still be read
+  __shared__ float4 s_g0b[2][kBatch];   // x, y, a2, c2
+  __shared__ float4 s_g1b[2][kBatch];   // b2, opacity, red, green
+  __shared__ float s_blueb[2][kBatch];
+  __shared__ uint32_t s_maskb[2][kBatch];
   __shared__ uint8_t s_list[kWarps][kBatch];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -84,8 +86,11 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
   bool done = !inside;
   float T = 1.f, R = 0.f, G = 0.f, B = 0.f;
   int last = 0;
-  for (int base = 0; base < n; base += kBatch) {
-    if (__syncthreads_count(done) == kThreads) break;
+  for (int base = 0, it = 0; base < n; base += kBatch, ++it) {
+    float4* s_g0 = s_g0b[it & 1];
+    float4* s_g1 = s_g1b[it & 1];
+    float* s_blue = s_blueb[it & 1];
+    uint32_t* s_mask = s_maskb[it & 1];
     const int k = base + (int)threadIdx.x;
     if (k < n) {
       const uint32_t g = values[range.x + k];
@@ -96,7 +101,10 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
       s_blue[threadIdx.x] = rgb[3 * g + 2];
       s_mask[threadIdx.x] = block_mask(p, co, composite_exp_threshold(co.w), tx, ty);
     }
-    __syncthreads();
+    // one barrier per batch: this batch is staged, the buffer staged next was
+    // last read for batch i - 1, which every thread has finished; and if every
+    // pixel has saturated the tile is done
+    if (__syncthreads_count(done) == kThreads) break;
     if (__all_sync(0xffffffffu, done)) continue;  // warp-uniform
     const int m = min(kBatch, n - base);
     int cnt = 0;
