@@ -219,7 +219,7 @@ def run_reference(args):
     for i in range(min(args.warmup, 1)):
         cam, t = views(i, 0, 1)
         oracle.render(scene, cam, t)
-    budget = 150.0
+    budget = 60.0
     n, t0 = 0, time.perf_counter()
     while n < args.steps:
         cam, t = views(n, 0, 1)
