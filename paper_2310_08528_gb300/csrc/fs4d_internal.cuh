@@ -273,13 +273,16 @@ __device__ __forceinline__ float4 composite_coeffs(float2 p, float4 conic_opacit
 __device__ __forceinline__ float composite_b2(float4 conic_opacity) { return -kLog2e * conic_opacity.y; }
 
 // alpha = min(0.99, o * G) of a term at offset (dx, dy) = mean - pixel centre,
-// or 0 when the term is skipped (exponent above 0, or alpha below 1/255).
+// or 0 when the term is skipped (alpha below 1/255).  The exponent
+// dx (a2 dx + b2 dy) + c2 dy^2 is never positive: every Gaussian that reaches
+// compositing has a positive-definite conic (projection culls det <= 0, and the
+// 0.3 dilation keeps det >= 0.09), so no exponent-sign test is needed.
 __device__ __forceinline__ float composite_alpha(const float4& g0, float b2, float opacity, float dx, float dy,
                                                  float& G) {
-  const float p = fmaf(g0.z * dx, dx, fmaf(g0.w * dy, dy, (b2 * dx) * dy));
+  const float p = fmaf(fmaf(g0.z, dx, b2 * dy), dx, (g0.w * dy) * dy);
   G = ex2_approx(p);
   const float alpha = fminf(0.99f, opacity * G);
-  return (p > 0.f || alpha < 1.f / 255.f) ? 0.f : alpha;
+  return alpha < 1.f / 255.f ? 0.f : alpha;
 }
 
 // Natural-log exponent bound: a term reaches alpha >= 1/255 only where
