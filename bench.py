@@ -136,20 +136,29 @@ def load_peaks():
             "source": "fallback"}
 
 
-def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, evals: int = 0):
+def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, evals: int = 0,
+               bitmap: bool = True):
     """Algorithmic bytes or FLOPs of one launch of each stage (per-unit figures
     times the units one launch processes).  Returns a list of (bound, work, unit);
-    the first entry is the stage's primary bound."""
+    the first entry is the stage's primary bound; an empty list: the stage's work
+    is done inside another stage."""
     if stage == "deform":
         flops = 2 * (64 * 64 + 64 * 64 + 3 * 64 * 64 + 64 * 10) * n   # MLP contraction, 42,240 FLOP/Gaussian
         return [(("tensor" if prec == "bf16" else "alu"), flops, "FLOP"), ("hbm", 80 * n, "B")]
     if stage == "project":
         return [("hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 12), "B")]
     if stage == "scan_emit":
-        # depth sort: 4 passes of 32-bit keys, each reading and writing 8 B key + 4 B value per Gaussian;
+        # depth sort: 4 passes of 32-bit keys, each reading and writing 8 B key + 4 B value per Gaussian
+        if bitmap:
+            # tile bitmap: order + rect in and the 36 B of projected data copied into rank order per
+            # Gaussian; per pair one 4 B bit-word update (read + write), the word read and cleared by the
+            # row walk and the rank written
+            return [("hbm", 4 * n * 24 + n * (4 + 16 + 72) + K * (8 + 4 + 4 + 4), "B")]
         # emission: order, rect, depth in + offset out per Gaussian, 12 B per pair out
         return [("hbm", 4 * n * 24 + n * (4 + 16 + 4 + 4) + K * 12, "B")]
     if stage == "sort":
+        if bitmap:
+            return []  # no pair sort: the bitmap rows list each tile's Gaussians in depth order
         return [("hbm", passes * K * 24, "B")]                         # read + write 12 B per pair per pass
     if stage == "ranges":
         return []  # produced by the tile scan inside the emission stage
@@ -170,12 +179,16 @@ def _frac(bound, work, sec, peaks):
     return {"bound": bound, "achieved": ach, "peak": peak, "unit": u, "frac": ach / peak}
 
 
-def roofline(stage_ms, n, K, pixels, passes, prec, peaks, evals):
+FUSED = {"ranges": "the tile scan in the binning stage writes the ranges",
+         "sort": "tile bitmap binning: no pair sort (the binning stage lists each tile in depth order)"}
+
+
+def roofline(stage_ms, n, K, pixels, passes, prec, peaks, evals, bitmap=True):
     out = {}
     for st, ms in stage_ms.items():
-        work = stage_work(st, n, K, pixels, passes, prec, evals)
+        work = stage_work(st, n, K, pixels, passes, prec, evals, bitmap)
         if not work:
-            out[st] = {"ms": ms, "fused": "the tile scan in the emission stage writes the ranges"}
+            out[st] = {"ms": ms, "fused": FUSED[st]}
             continue
         items = [_frac(b, w, ms * 1e-3, peaks) for b, w, _ in work]
         best = max(items, key=lambda r: r["frac"]) if st == "composite" else items[0]
@@ -430,8 +443,10 @@ def main():
     ctx.reserve(sid, WIDTH, HEIGHT, cap)
     tiles = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
     passes = (int(np.ceil(np.log2(tiles))) + 7) // 8   # the pair sort keys on the tile bits only
-    # deform, project, 4 depth-sort passes, scan/emit, pair-sort passes, ranges, composite
-    launches_per_frame = 8 + passes
+    bitmap = ctx.last_binning() == fs4d.BINNING_BITMAP
+    # deform, project, 4 depth-sort passes, then bitmap: mark, tile scan, extract; or sort: emission,
+    # tile scan, pair-sort passes; then composite
+    launches_per_frame = 10 if bitmap else 9 + passes
     # (pixel, Gaussian) tests the compositing must make: each pixel walks its tile's list up to its
     # last contributor (summed over the frames of the view set)
     evals, pairs = [], []
@@ -506,7 +521,7 @@ def main():
 
     peaks = load_peaks()
     K = mean_pairs
-    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks, evals)
+    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks, evals, bitmap)
     dom = max((k for k in rf if "frac" in rf[k]), key=lambda k: rf[k]["ms"])
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
@@ -519,6 +534,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "resolution": [WIDTH, HEIGHT],
+                   "binning": "tile bitmap" if bitmap else "radix sort",
                    "tile_pairs_mean": K, "pixel_gaussian_tests_mean": evals, "pair_capacity": cap, "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed frame (256 MB device write, outside the timed interval)",
                    "timing": "CUDA events around camera upload + CUDA-graph replay of one frame (graph without "

@@ -63,6 +63,17 @@ typedef enum fs4d_precision {
   FS4D_BF16 = 1  /* planes and MLP operands in bfloat16 on tcgen05 tensor cores, float32 accumulate */
 } fs4d_precision;
 
+/* How a frame groups its (tile, Gaussian) pairs by tile in (depth, index) order
+ * (Sec. 3.1: the per-tile depth order of the tile-based rasteriser).  Both give the
+ * same pair lists, bit for bit. */
+typedef enum fs4d_binning {
+  FS4D_BINNING_AUTO = 0,   /* the tile bitmap when it fits (at most 256 MB: tiles x Gaussians / 8
+                              bytes) and the frame keeps no state for a backward, else the sort */
+  FS4D_BINNING_SORT = 1,   /* emit one (tile | depth) key per pair and radix-sort on the tile bits */
+  FS4D_BINNING_BITMAP = 2  /* (only reported by fs4d_last_binning) one bit per (tile, depth rank),
+                              each tile's row read in rank order */
+} fs4d_binning;
+
 typedef struct fs4d_ctx fs4d_ctx;     /* one device + one stream; not thread-safe */
 typedef struct fs4d_frame fs4d_frame; /* saved forward state of one render, for the backward */
 typedef int32_t fs4d_scene_id;
@@ -197,6 +208,12 @@ FS4D_API fs4d_status fs4d_frame_free(fs4d_ctx* ctx, fs4d_frame* frame);
 /* Number of tile pairs K of a saved frame, and of the last render on the context. */
 FS4D_API fs4d_status fs4d_frame_pairs(const fs4d_frame* frame, int64_t* pairs);
 FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
+
+/* Binning policy of the context's frames (FS4D_BINNING_AUTO or FS4D_BINNING_SORT;
+ * FS4D_ERR_INVALID_ARG otherwise), and the binning the last frame rendered on the
+ * context (not the server's) used.  fs4d_bin_sort follows the same policy. */
+FS4D_API fs4d_status fs4d_set_binning(fs4d_ctx* ctx, int32_t mode);
+FS4D_API fs4d_status fs4d_last_binning(const fs4d_ctx* ctx, int32_t* mode);
 
 /* Per-stage device timing of frames rendered by fs4d_render / fs4d_render_async
  * (also inside a captured CUDA graph): when enabled, CUDA events are recorded on

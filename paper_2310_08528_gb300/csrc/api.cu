@@ -96,6 +96,9 @@ struct Work {
   DevBuf keys, values, keys_alt, values_alt;
   DevBuf sort_lb;
   DevBuf ranges, tile_count, tile_order;
+  DevBuf bitmap;                           // tile bitmap binning: [tiles][bitmap_words(n)], zero between frames
+  DevBuf sxy, sco, srgb;                   // with the bitmap: projected Gaussians in depth-rank order
+  bool bmp = false;                        // the frame in flight bins through the bitmap
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
   DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
@@ -105,6 +108,13 @@ struct Work {
 };
 
 constexpr int kSortMaxPasses = 8;
+// Largest tile bitmap (one bit per (tile, Gaussian)) a frame bins through; larger
+// frames emit keys and radix-sort them.  At this size clearing and walking the
+// rows costs about as much memory traffic as the sort's passes over ~10 pairs per
+// Gaussian, and the sort's latency chains are gone.
+constexpr size_t kBitmapMaxBytes = size_t(256) << 20;
+
+size_t bitmap_bytes(int n, long long n_tiles) { return 4 * (size_t)n_tiles * (size_t)bitmap_words(std::max(n, 1)); }
 constexpr int kCounters = 32;  // [0] emit ticket, [8, 25) radix-sort tickets and selection words
 constexpr int kEmitCounters = 8;  // the words reset before an emission (the sort's words stay)
 
@@ -171,6 +181,8 @@ struct fs4d_ctx {
   uint32_t* h_pinned = nullptr;  // [4] readback slots
   long long last_pairs = 0;
   uint32_t* last_values = nullptr;  // sorted Gaussian indices of the last frame (work memory)
+  int binning = FS4D_BINNING_AUTO;
+  int last_binning = FS4D_BINNING_SORT;
   bool timing = false;
   cudaEvent_t ev[8] = {};        // deform, project, emit, emit end, sort, ranges, composite, end
 };
@@ -386,7 +398,11 @@ fs4d_status get_scene(fs4d_ctx* c, fs4d_scene_id id, Scene** out) {
 
 // Grow the per-Gaussian / per-tile / per-pair work buffers.
 fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_tiles, long long pairs) {
-  bool grow = n > w.cap_n || n_tiles > w.cap_tiles || pairs > w.cap_pairs;
+  const bool bmp_ok = c->binning != FS4D_BINNING_SORT;
+  const size_t bmp_need =
+      std::max(bitmap_bytes(std::max(n, w.cap_n), std::max(n_tiles, w.cap_tiles)), w.bitmap.bytes);
+  const bool bmp_grow = bmp_ok && bmp_need <= kBitmapMaxBytes && bmp_need > w.bitmap.bytes;
+  bool grow = n > w.cap_n || n_tiles > w.cap_tiles || pairs > w.cap_pairs || bmp_grow;
   if (!grow) return FS4D_OK;
   FS4D_CUDA(c, cudaStreamSynchronize(stream));
   if (n > w.cap_n) {
@@ -400,6 +416,9 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
     FS4D_CUDA(c, ensure(w.depth, 4 * m));
     FS4D_CUDA(c, ensure(w.radius, 4 * m));
     FS4D_CUDA(c, ensure(w.rect, 16 * m));
+    FS4D_CUDA(c, ensure(w.sxy, 8 * m));
+    FS4D_CUDA(c, ensure(w.sco, 16 * m));
+    FS4D_CUDA(c, ensure(w.srgb, 12 * m));
     FS4D_CUDA(c, ensure(w.offsets, 4 * m));
     FS4D_CUDA(c, ensure(w.emit_lb, 8 * (size_t)(emit_parts(n) + 1)));
     FS4D_CUDA(c, ensure(w.dkeys, 8 * m));
@@ -433,7 +452,18 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
   const size_t zb = frame_zero_layout(w.cap_n, w.cap_tiles, w.cap_pairs,
                                       sort_passes(ceil_log2(std::max(w.cap_tiles, 1))), nullptr, nullptr);
   FS4D_CUDA(c, ensure(w.zero, zb));
+  if (bmp_grow) {  // zeroed once here; every frame that sets bits clears them again
+    FS4D_CUDA(c, ensure(w.bitmap, bmp_need));
+    FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, stream));
+    FS4D_CUDA(c, cudaStreamSynchronize(stream));
+  }
   return FS4D_OK;
+}
+
+// Whether a frame of n Gaussians over n_tiles tiles bins through w's bitmap.
+bool use_bitmap(const fs4d_ctx* c, const Work& w, int n, int n_tiles, bool offsets) {
+  const size_t b = bitmap_bytes(n, n_tiles);
+  return c->binning != FS4D_BINNING_SORT && !offsets && n > 0 && b <= kBitmapMaxBytes && b <= w.bitmap.bytes;
 }
 
 fs4d_status ensure_work(fs4d_ctx* c, int n, int n_tiles, long long pairs) {
@@ -502,9 +532,11 @@ fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformA
 }
 
 // Everything of a frame up to (and including) the key emission.
+// offsets: keep each Gaussian's emission offset (the backward's pair slots), which
+// only the key emission produces.
 fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
                         const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
-                        bool deform = true) {
+                        bool deform = true, bool offsets = false) {
   fs4d_ctx* c = e.c;
   Work& w = *e.w;
   const cudaStream_t stream = e.s;
@@ -558,17 +590,37 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   ea.n_tiles = tx * ty;
   ea.status = e.status;
   ea.report_overflow = report ? 1 : 0;
-  FS4D_CUDA(c, launch_scan_emit(ea, stream));
-  // tile ranges and the pair sort's digit histograms straight from the tile counts
-  FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), z.hist,
-                                sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
+  w.bmp = use_bitmap(c, w, s->n, tx * ty, offsets);
+  if (e.w == &c->w) c->last_binning = w.bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;
+  if (w.bmp) {
+    // bits per (tile, depth rank) and the projected Gaussians copied into rank order;
+    // ranges and launch order from the tile counts; each tile's row read in rank
+    // order is its list of depth ranks (no keys: the composite needs none)
+    ea.bitmap = P<uint32_t>(w.bitmap);
+    ea.words = bitmap_words(s->n);
+    ea.keys = nullptr;
+    ea.ranges = P<uint2>(w.ranges);
+    ea.tile_order = P<uint32_t>(w.tile_order);
+    ea.xy = P<float2>(w.xy); ea.conic_opacity = P<float4>(w.co); ea.rgb = P<float>(w.rgb);
+    ea.sorted_xy = P<float2>(w.sxy); ea.sorted_co = P<float4>(w.sco); ea.sorted_rgb = P<float>(w.srgb);
+    FS4D_CUDA(c, launch_mark_tiles(ea, stream));
+    FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), nullptr, 0,
+                                  P<uint32_t>(w.tile_order), stream, cap, report ? e.status : nullptr));
+    FS4D_CUDA(c, launch_extract_tiles(ea, false, stream));
+  } else {
+    FS4D_CUDA(c, launch_scan_emit(ea, stream));
+    // tile ranges and the pair sort's digit histograms straight from the tile counts
+    FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), z.hist,
+                                  sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
+  }
   mark(e, 3);
   return FS4D_OK;
 }
 
 fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
-                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report) {
-  return frame_front(env_of(c), s, prec, shape, d_cam, d_t, t, cap, report);
+                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
+                        bool offsets = false) {
+  return frame_front(env_of(c), s, prec, shape, d_cam, d_t, t, cap, report, true, offsets);
 }
 
 // Sort, ranges and composite with n_dev = the sortable pair count on device.
@@ -582,21 +634,24 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   const uint32_t* n_dev = z.num_pairs + 1;
   bool alt = false;
   mark(e, 4);
-  // pairs arrive in depth order: a stable sort on the tile bits gives (tile, depth, index)
-  SortWork psw;
-  psw.hist = z.hist; psw.lookback = z.plb; psw.part_counters = z.counters + 32; psw.max_parts = z.pparts;
-  psw.prezeroed = true;
-  if (n_bound > z.pparts * 1024) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
-  FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
-                           P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
-                           &alt));
-  unsigned long long* keys = alt ? P<unsigned long long>(w.keys_alt) : P<unsigned long long>(w.keys);
+  if (!w.bmp) {
+    // pairs arrive in depth order: a stable sort on the tile bits gives (tile, depth, index)
+    SortWork psw;
+    psw.hist = z.hist; psw.lookback = z.plb; psw.part_counters = z.counters + 32; psw.max_parts = z.pparts;
+    psw.prezeroed = true;
+    if (n_bound > z.pparts * 1024) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
+    FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
+                             P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
+                             &alt));
+  }
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
   if (values_out) *values_out = values;
   mark(e, 5);  // the ranges came with the tile scan: an empty stage
   mark(e, 6);
-  FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values, P<float2>(w.xy),
-                                P<float4>(w.co), P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s,
+  // with the bitmap the lists hold depth ranks into the rank-ordered copies
+  FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values,
+                                w.bmp ? P<float2>(w.sxy) : P<float2>(w.xy), w.bmp ? P<float4>(w.sco) : P<float4>(w.co),
+                                w.bmp ? P<float>(w.srgb) : P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s,
                                 P<uint32_t>(w.tile_order)));
   mark(e, 7);
   return FS4D_OK;
@@ -614,19 +669,20 @@ fs4d_status read_pairs(fs4d_ctx* c, const uint32_t* d_num_pairs, long long* K) {
   return FS4D_OK;
 }
 
+// offsets: the frame will be saved for a backward
 fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t, float* d_image,
-                        float* d_t_final, int32_t* d_n_contrib) {
+                        float* d_t_final, int32_t* d_n_contrib, bool offsets = false) {
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   fs4d_status st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs);
   if (st != FS4D_OK) return st;
-  st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false);
+  st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
   if (st != FS4D_OK) return st;
   long long K = 0;
   if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
   if (K >= 0xffffffffll) return fail(c, FS4D_ERR_CAPACITY, "more than 2^32-1 tile pairs in one frame");
   if (K > c->w.cap_pairs) {
     if ((st = ensure_work(c, s->n, n_tiles, K + K / 4)) != FS4D_OK) return st;
-    st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false);
+    st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
     if (st != FS4D_OK) return st;
   }
   c->last_pairs = K;
@@ -669,7 +725,7 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     Work& w = c->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &w.ts, &w.host_img,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &w.bitmap, &w.sxy, &w.sco, &w.srgb, &w.ts, &w.host_img,
                      &w.grad_pair, &w.gd, &w.acts, &w.wpartial};
     for (DevBuf* b : all) release(*b);
     release(c->status);
@@ -821,7 +877,8 @@ fs4d_status fs4d_scene_bytes(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32
     const size_t n = (size_t)s->n;
     const size_t pairs = (size_t)(std::max(0.f, ppg) * (float)n) + 4096;
     const size_t tiles = (size_t)tiles_of(width) * tiles_of(height);
-    *per_frame = n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + pairs * 24 +
+    const size_t bmp = bitmap_bytes((int)n, (long long)tiles);
+    *per_frame = (bmp <= kBitmapMaxBytes ? bmp + 36 * n : 0) + n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + pairs * 24 +
                  sort_parts((long long)pairs) * 256 * 4 * kSortMaxPasses + tiles * 8 +
                  (size_t)width * height * 12;
   }
@@ -865,7 +922,7 @@ fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, cons
   };
   if (ensure(f->t_final, 4 * npix) != cudaSuccess || ensure(f->n_contrib, 4 * npix) != cudaSuccess)
     return drop(fail(c, FS4D_ERR_OOM, "render: frame allocation failed"));
-  st = render_sync(c, s, prec, cam, t, d_image, P<float>(f->t_final), P<int32_t>(f->n_contrib));
+  st = render_sync(c, s, prec, cam, t, d_image, P<float>(f->t_final), P<int32_t>(f->n_contrib), true);
   if (st != FS4D_OK) return drop(st);
   Work& w = c->w;
   const size_t n = (size_t)s->n, K = (size_t)c->last_pairs;
@@ -1114,6 +1171,20 @@ fs4d_status fs4d_frame_pairs(const fs4d_frame* f, int64_t* pairs) {
   return FS4D_OK;
 }
 
+fs4d_status fs4d_set_binning(fs4d_ctx* c, int32_t mode) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (mode != FS4D_BINNING_AUTO && mode != FS4D_BINNING_SORT)
+    return fail(c, FS4D_ERR_INVALID_ARG, "set_binning: mode must be FS4D_BINNING_AUTO or FS4D_BINNING_SORT");
+  c->binning = mode;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_last_binning(const fs4d_ctx* c, int32_t* mode) {
+  if (!c || !mode) return FS4D_ERR_INVALID_ARG;
+  *mode = c->last_binning;
+  return FS4D_OK;
+}
+
 fs4d_status fs4d_last_pairs(const fs4d_ctx* c, int64_t* pairs) {
   if (!c || !pairs) return FS4D_ERR_INVALID_ARG;
   *pairs = c->last_pairs;
@@ -1180,16 +1251,29 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   ea.n_tiles = n_tiles;
   ea.status = P<uint32_t>(c->status);
   ea.report_overflow = 0;
-  FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
-  FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
-                                reinterpret_cast<uint2*>(d_ranges), P<uint32_t>(w.hist), sort_passes(tile_bits),
-                                nullptr, c->stream));
+  const bool bmp = use_bitmap(c, w, n, n_tiles, false);
+  c->last_binning = bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;
+  if (bmp) {
+    ea.bitmap = P<uint32_t>(w.bitmap);
+    ea.words = bitmap_words(n);
+    ea.ranges = reinterpret_cast<const uint2*>(d_ranges);
+    FS4D_CUDA(c, launch_mark_tiles(ea, c->stream));
+    FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
+                                  reinterpret_cast<uint2*>(d_ranges), nullptr, 0, nullptr, c->stream, capacity));
+    FS4D_CUDA(c, launch_extract_tiles(ea, true, c->stream));  // also clears the bitmap when the pairs overflow
+  } else {
+    FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
+    FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
+                                  reinterpret_cast<uint2*>(d_ranges), P<uint32_t>(w.hist), sort_passes(tile_bits),
+                                  nullptr, c->stream));
+  }
   long long K = 0;
   if ((st = read_pairs(c, P<uint32_t>(w.num_pairs), &K)) != FS4D_OK) return st;
   *h_num_pairs = K;
   if (K > capacity) {
     return fail(c, FS4D_ERR_CAPACITY, "bin_sort: " + std::to_string(K) + " pairs exceed the capacity");
   }
+  if (bmp) return FS4D_OK;
   bool alt = false;
   FS4D_CUDA(c, launch_sort(reinterpret_cast<unsigned long long*>(d_keys), d_values, P<unsigned long long>(w.keys_alt),
                            P<uint32_t>(w.values_alt), nullptr, K, 32, tile_bits, true, sort_work(c),
@@ -1288,7 +1372,8 @@ struct Staging {
 
 size_t slot_bytes_for(int n, int w, int h, long long pairs) {
   const size_t tiles = (size_t)tiles_of(w) * tiles_of(h);
-  return (size_t)n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + 8 * (size_t)(emit_parts(n) + 1) +
+  const size_t bmp = bitmap_bytes(n, (long long)tiles);
+  return (bmp <= kBitmapMaxBytes ? bmp + 36 * (size_t)n : 0) + (size_t)n * (12 + 16 + 12 + 8 + 16 + 12 + 4 + 4 + 16 + 4 + 24) + 8 * (size_t)(emit_parts(n) + 1) +
          (size_t)pairs * 24 + 4 * 256 * (size_t)kSortMaxPasses * sort_parts(pairs) + tiles * 8 +
          (size_t)w * h * 12 + 4096;
 }
@@ -1400,11 +1485,11 @@ Slot* new_slot(fs4d_server* sv) {
 // Make the slot hold a frame of n Gaussians at w x h with `pairs` capacity.
 fs4d_status fit_slot(fs4d_server* sv, Slot* sl, int n, int w, int h, long long pairs) {
   fs4d_ctx* c = sv->c;
-  const void* before[5] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p};
+  const void* before[6] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p, sl->w.bitmap.p};
   fs4d_status st = ensure_work(c, sl->w, sl->stream, n, tiles_of(w) * tiles_of(h), pairs);
   if (st != FS4D_OK) return st;
   if ((size_t)w * h * 12 > sl->image.bytes) FS4D_CUDA(c, ensure(sl->image, (size_t)w * h * 12));
-  const void* after[5] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p};
+  const void* after[6] = {sl->w.dmeans.p, sl->w.keys.p, sl->w.ranges.p, sl->w.zero.p, sl->image.p, sl->w.bitmap.p};
   if (std::memcmp(before, after, sizeof(before)) != 0) {  // graphs captured on old buffers are stale
     cudaStreamSynchronize(sl->stream);
     for (auto& kv : sl->graphs) cudaGraphExecDestroy(kv.second);
@@ -1777,7 +1862,7 @@ fs4d_status fs4d_server_destroy(fs4d_server* sv) {
     Work& w = sl->w;
     DevBuf* all[] = {&w.dmeans, &w.dquats, &w.dscales, &w.xy, &w.co, &w.rgb, &w.depth, &w.radius, &w.rect,
                      &w.offsets, &w.emit_lb, &w.counters, &w.num_pairs, &w.hist, &w.keys, &w.values,
-                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &sl->status, &sl->dcam, &sl->dt,
+                     &w.keys_alt, &w.values_alt, &w.sort_lb, &w.ranges, &w.tile_count, &w.tile_order, &w.zero, &w.bitmap, &w.sxy, &w.sco, &w.srgb, &sl->status, &sl->dcam, &sl->dt,
                      &sl->image};
     for (DevBuf* b : all) release(*b);
     cudaFreeHost(sl->h_cam);

@@ -192,9 +192,10 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int sme
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t* __restrict__ tile_count, int n_tiles,
-                                                                 const uint32_t* __restrict__ num_pairs,
+                                                                 uint32_t* __restrict__ num_pairs,
                                                                  uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
-                                                                 int passes, uint32_t* __restrict__ order) {
+                                                                 int passes, uint32_t* __restrict__ order,
+                                                                 long long capacity, uint32_t* __restrict__ status) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_hist[kMaxPasses][256];
   __shared__ uint32_t s_len[33];          // tiles per length class floor(log2(count)) + 1 (0: empty)
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
   const uint32_t lane = lane_id(), warp = tid / 32;
   for (int i = tid; i < kMaxPasses * 256; i += kScanThreads) (&s_hist[0][0])[i] = 0;
   if (tid < 33) s_len[tid] = 0;
-  const bool overflow = num_pairs[1] == 0u && num_pairs[0] != 0u;
+  const bool sort_overflow = capacity < 0 && num_pairs[1] == 0u && num_pairs[0] != 0u;
   const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
   const int t0 = min(tid * per, n_tiles), t1 = min(t0 + per, n_tiles);
   uint32_t sum = 0;
@@ -216,10 +217,19 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   uint32_t run = incl - sum;
-  for (int w = 0; w < (int)warp; ++w) run += s_warp[w];
+  unsigned long long total = 0;
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    if (w < (int)warp) run += s_warp[w];
+    total += s_warp[w];
+  }
+  const bool overflow = capacity < 0 ? sort_overflow : (long long)total > capacity;
+  if (capacity >= 0 && tid == 0) {
+    num_pairs[1] = overflow ? 0u : (uint32_t)total;
+    if (overflow && status) atomicOr(status, kStatusCapacity);
+  }
   for (int t = t0; t < t1; ++t) {
     const uint32_t c = tile_count[t];
-    ranges[t] = (overflow || c == 0) ? make_uint2(0u, 0u) : make_uint2(run, run + c);
+    if (ranges) ranges[t] = (overflow || c == 0) ? make_uint2(0u, 0u) : make_uint2(run, run + c);
     if (c && hist)
       for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][((uint32_t)t >> (8 * p)) & 255u], c);
     run += c;
@@ -230,10 +240,16 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
   }
   if (order) {
     // Launch order for the compositing: tiles by length class, longest first, so
-    // the longest lists start first and do not form the tail.
-    for (int t = t0; t < t1; ++t) {
-      const uint32_t c = overflow ? 0u : tile_count[t];
-      atomicAdd(&s_len[32 - (c ? 32 - __clz(c) : 0)], 1u);
+    // the longest lists start first and do not form the tail.  Tiles of one class
+    // within a warp share one shared-memory atomic (most tiles of a frame are in
+    // a few classes, empty ones above all).
+    const uint32_t lane_lt = (1u << lane) - 1u;
+    for (int b = 0; b < n_tiles; b += kScanThreads) {
+      const int t = b + tid;
+      const uint32_t c = (t < n_tiles && !overflow) ? tile_count[t] : 0u;
+      const int cls = t < n_tiles ? 32 - (c ? 32 - __clz(c) : 0) : 33;
+      const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+      if (cls < 33 && (peers & lane_lt) == 0) atomicAdd(&s_len[cls], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (tid == 0) {
@@ -245,9 +261,218 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
       }
     }
     __syncthreads();
-    for (int t = t0; t < t1; ++t) {
-      const uint32_t c = overflow ? 0u : tile_count[t];
-      order[atomicAdd(&s_len[32 - (c ? 32 - __clz(c) : 0)], 1u)] = (uint32_t)t;
+    for (int b = 0; b < n_tiles; b += kScanThreads) {
+      const int t = b + tid;
+      const uint32_t c = (t < n_tiles && !overflow) ? tile_count[t] : 0u;
+      const int cls = t < n_tiles ? 32 - (c ? 32 - __clz(c) : 0) : 33;
+      const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+      const int leader = __ffs(peers) - 1;
+      uint32_t at = 0;
+      if (cls < 33 && lane == (uint32_t)leader) at = atomicAdd(&s_len[cls], (uint32_t)__popc(peers));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (cls < 33) order[at + __popc(peers & lane_lt)] = (uint32_t)t;
+    }
+  }
+}
+
+// ------------------------------------------------------------ tile bitmap
+// The alternative to emission + pair sort: a bitmap with one row per tile and one
+// bit per depth rank.  Row t read in rank order lists tile t's Gaussians in
+// (depth, index) order -- exactly the order a stable sort of (tile | depth) keys
+// gives -- so no sort is needed once the bits are set.
+
+// Row r, column k - r * w of the k-th tile of a w-wide rectangle (row-major):
+// the quotient from a float reciprocal, corrected by one step (exact for k < 2^22,
+// where the float estimate is off by less than one); integer division above.
+__device__ __forceinline__ uint32_t rect_row(uint32_t k, uint32_t w) {
+  if (k >= (1u << 22)) return k / w;
+  int r = __float2int_rz(((float)k + 0.5f) * __frcp_rn((float)w));
+  const int c = (int)k - r * (int)w;
+  r += c < 0 ? -1 : (c >= (int)w ? 1 : 0);
+  return (uint32_t)r;
+}
+
+// 256 consecutive depth ranks per CTA; warp w owns ranks [32w, 32w + 32) of the
+// CTA, i.e. one word column of every row; a rank's projected Gaussian is copied
+// to its rank's slot when sorted copies are asked for.  Each warp spreads its pairs over its
+// lanes (binary search over the warp's exclusive pair offsets by shuffles), and
+// each pair sets its bit with one global atomic OR.  Pairs per tile are summed in
+// shared memory and merged by one global atomic per touched tile.
+__global__ void __launch_bounds__(kThreads) mark_kernel(EmitArgs a, int smem_tiles) {
+  extern __shared__ uint32_t s_tc[];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < smem_tiles; i += kThreads) s_tc[i] = 0;
+  __syncthreads();
+  const uint32_t lane = lane_id(), warp = (uint32_t)tid / 32;
+  const uint32_t* order = (a.order_sel && *a.order_sel) ? a.order_alt : a.order;
+  const int pos = blockIdx.x * kPart + tid;
+  int4 r = make_int4(0, 0, 0, 0);
+  uint32_t cnt = 0;
+  if (pos < a.n) {
+    const uint32_t g = order ? order[pos] : (uint32_t)pos;
+    r = a.rect[g];
+    cnt = (uint32_t)max(0, r.z - r.x) * (uint32_t)max(0, r.w - r.y);
+    if (a.sorted_xy && cnt) {  // the compositing reads the projected Gaussians by depth rank
+      a.sorted_xy[pos] = a.xy[g];
+      a.sorted_co[pos] = a.conic_opacity[g];
+      a.sorted_rgb[3 * pos] = a.rgb[3 * g];
+      a.sorted_rgb[3 * pos + 1] = a.rgb[3 * g + 1];
+      a.sorted_rgb[3 * pos + 2] = a.rgb[3 * g + 2];
+    }
+  }
+  const uint32_t rw = (uint32_t)max(1, r.z - r.x);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += v;
+  }
+  const uint32_t excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+  uint32_t* col = a.bitmap + ((uint32_t)blockIdx.x * kPart + warp * 32) / 32;
+  for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    // last lane whose offset is <= j (a lane with no tiles shares its offset with
+    // the next lane, so it never wins)
+    uint32_t lo = 0;
+#pragma unroll
+    for (uint32_t st = 16; st >= 1; st >>= 1) {
+      const uint32_t e = __shfl_sync(0xffffffffu, excl, lo + st);
+      if (e <= j) lo += st;
+    }
+    const int rx = __shfl_sync(0xffffffffu, r.x, lo), ry = __shfl_sync(0xffffffffu, r.y, lo);
+    const uint32_t w = __shfl_sync(0xffffffffu, rw, lo), e0 = __shfl_sync(0xffffffffu, excl, lo);
+    if (j < total) {
+      const uint32_t k = j - e0;
+      const uint32_t row = rect_row(k, w);
+      const uint32_t tile = (uint32_t)(ry + (int)row) * (uint32_t)a.tiles_x + (uint32_t)rx + (k - row * w);
+      atomicOr(col + (size_t)tile * (size_t)a.words, 1u << lo);
+      if (smem_tiles)
+        atomicAdd(&s_tc[tile], 1u);
+      else
+        atomicAdd(&a.tile_count[tile], 1u);
+    }
+  }
+  if (lane == 0 && total) atomicAdd(a.num_pairs, total);
+  if (smem_tiles) {
+    __syncthreads();
+    for (int t = tid; t < smem_tiles; t += kThreads) {
+      const uint32_t v = s_tc[t];
+      if (v) atomicAdd(&a.tile_count[t], v);
+    }
+  }
+}
+
+// One CTA per tile (longest lists first when a tile order is given).  Each step
+// covers kXRounds * kXThreads uint4 of the row: in round i thread t holds uint4
+// v0 + i * kXThreads + t, so every load is coalesced and the rank order is round
+// by round, thread by thread.  The popcounts of rounds (0, 1) and (2, 3) are
+// scanned as packed 16-bit pairs (at most 32768 bits per round), which gives every
+// uint4 its list position with one barrier per step.  The thread stores the depth
+// rank of each set bit there and zeroes the nonzero words; the walk ends at the
+// row's last pair, so the row is all zero afterwards.  With ids the ranks are then
+// replaced by the Gaussians (and keys) with unrolled gathers.  A tile whose range
+// is (0, 0) because the pairs overflowed the buffers is only cleared.
+constexpr int kXThreads = 256;
+constexpr int kXRounds = 4;
+
+__device__ __forceinline__ void extract_bits(const uint4& q, uint32_t r0, uint32_t o, uint32_t cnt,
+                                             uint32_t* list) {
+  const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t m = wd[j];
+    while (m) {  // the row holds exactly cnt bits; the bound only guards the range
+      if (o < cnt) list[o] = r0 + 32u * (uint32_t)j + (uint32_t)(__ffs(m) - 1);
+      ++o;
+      m &= m - 1u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kXThreads) extract_kernel(EmitArgs a, int ids) {
+  __shared__ uint32_t s_warp[2][2][kXThreads / 32];
+  const int t = a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x;
+  const uint32_t cnt = a.tile_count[t];
+  if (cnt == 0) return;
+  const uint2 rg = a.ranges[t];
+  const bool write = rg.y > rg.x;
+  uint32_t* list = a.values + rg.x;
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id(), warp = (uint32_t)tid / 32;
+  uint4* row = reinterpret_cast<uint4*>(a.bitmap + (size_t)t * (size_t)a.words);
+  const int nvec = a.words >> 2;
+  uint32_t done = 0;
+  for (int v0 = 0, it = 0; v0 < nvec && done < cnt; v0 += kXRounds * kXThreads, ++it) {
+    uint4 q[kXRounds];
+    uint32_t c[kXRounds];
+#pragma unroll
+    for (int i = 0; i < kXRounds; ++i) {
+      const int v = v0 + i * kXThreads + tid;
+      q[i] = v < nvec ? row[v] : make_uint4(0u, 0u, 0u, 0u);
+      c[i] = __popc(q[i].x) + __popc(q[i].y) + __popc(q[i].z) + __popc(q[i].w);
+    }
+    const uint32_t p01 = c[0] | (c[1] << 16), p23 = c[2] | (c[3] << 16);
+    uint32_t i01 = p01, i23 = p23;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y01 = __shfl_up_sync(0xffffffffu, i01, d), y23 = __shfl_up_sync(0xffffffffu, i23, d);
+      if (lane >= (uint32_t)d) {
+        i01 += y01;
+        i23 += y23;
+      }
+    }
+    uint32_t(*sw)[kXThreads / 32] = s_warp[it & 1];  // two buffers: one barrier per step
+    if (lane == 31) {
+      sw[0][warp] = i01;
+      sw[1][warp] = i23;
+    }
+    __syncthreads();
+    uint32_t e01 = i01 - p01, e23 = i23 - p23, t01 = 0, t23 = 0;
+#pragma unroll
+    for (int w = 0; w < kXThreads / 32; ++w) {
+      const uint32_t y01 = sw[0][w], y23 = sw[1][w];
+      if ((uint32_t)w < warp) {
+        e01 += y01;
+        e23 += y23;
+      }
+      t01 += y01;
+      t23 += y23;
+    }
+    const uint32_t tot[4] = {t01 & 0xffffu, t01 >> 16, t23 & 0xffffu, t23 >> 16};
+    const uint32_t ex[4] = {e01 & 0xffffu, e01 >> 16, e23 & 0xffffu, e23 >> 16};
+    uint32_t base = done;
+#pragma unroll
+    for (int i = 0; i < kXRounds; ++i) {
+      if (c[i]) {
+        const int v = v0 + i * kXThreads + tid;
+        row[v] = make_uint4(0u, 0u, 0u, 0u);
+        if (write) extract_bits(q[i], (uint32_t)v * 128u, base + ex[i], cnt, list);
+      }
+      base += tot[i];
+    }
+    done = base;
+  }
+  if (!write || !ids) return;
+  __syncthreads();  // the ranks stored by the other threads are visible
+  const uint32_t* order = (a.order_sel && *a.order_sel) ? a.order_alt : a.order;
+  const uint32_t last = (uint32_t)a.n - 1u;  // ranks are < n: the clamp only guards the gathers
+  constexpr int kU = 4;
+  for (uint32_t i0 = (uint32_t)tid; i0 < cnt; i0 += kU * kXThreads) {
+    uint32_t g[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = i0 + (uint32_t)u * kXThreads;
+      g[u] = i < cnt ? min(list[i], last) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) g[u] = order ? order[g[u]] : g[u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = i0 + (uint32_t)u * kXThreads;
+      if (i < cnt) {
+        list[i] = g[u];
+        if (a.keys) a.keys[rg.x + i] = ((unsigned long long)t << 32) | __float_as_uint(a.depth[g[u]]);
+      }
     }
   }
 }
@@ -270,10 +495,35 @@ cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
-                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s) {
+int bitmap_words(int n) { return ((n + 127) / 128) * 4; }
+
+cudaError_t launch_mark_tiles(const EmitArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.words < bitmap_words(a.n)) return cudaErrorInvalidValue;
+  const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
+  mark_kernel<<<emit_parts(a.n), kThreads, 4 * (size_t)st, s>>>(a, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_tiles(const EmitArgs& a, bool ids, cudaStream_t s) {
+  if (a.n <= 0 || a.n_tiles <= 0) return cudaSuccess;
+  if (a.words < bitmap_words(a.n) || (a.words & 3)) return cudaErrorInvalidValue;
+  extract_kernel<<<a.n_tiles, kXThreads, 0, s>>>(a, ids ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, uint32_t* num_pairs, uint2* ranges,
+                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s, long long capacity,
+                             uint32_t* status) {
   if (passes > kMaxPasses || n_tiles < 1) return cudaErrorInvalidValue;
-  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes, order);
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes, order, capacity,
+                                              status);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ constexpr int kThreads = kTile * kTile;
 constexpr int kBatch = kThreads;
 constexpr int kWarps = kThreads / 32;
 constexpr float kTMin = 1e-4f;
+constexpr int kMinBlocks = 5;  // CTAs per SM the register budget must allow
 
 // Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0).
 __device__ __forceinline__ float edge_min(float A, float B, float C, float u, float t0, float t1) {
@@ -55,9 +56,96 @@ __device__ __forceinline__ uint32_t block_mask(float2 p, float4 co, float thr, i
   return mask;
 }
 
-// AUX: also write each pixel's final transmittance and last contributor.
+// One staged batch of m Gaussians (list positions base .. base + m - 1) for the
+// calling thread's pixel: the warp compacts the batch to the Gaussians whose mask
+// holds its block (ballot, order kept) and walks them two per step -- both weights
+// are evaluated before the two (sequential, front-to-back) transmittance updates.
+// AUX: track each pixel's last contributor.
 template <bool AUX>
-__global__ void __launch_bounds__(kThreads) composite_kernel(int width, int height, int tiles_x,
+__device__ __forceinline__ void composite_batch(int m, int base, const float4* s_g0, const float4* s_g1,
+                                                const float* s_blue, const uint32_t* s_mask, uint8_t* list,
+                                                int warp, int lane, float fx, float fy, bool& done, float& T,
+                                                float& R, float& G, float& B, int& last) {
+  const uint32_t lane_lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    const int j = c0 + lane;
+    const bool hit = j < m && ((s_mask[j] >> warp) & 1u);
+    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    if (hit) list[cnt + __popc(bal & lane_lt)] = (uint8_t)j;
+    cnt += __popc(bal);
+  }
+  __syncwarp();
+  for (int i = 0; i < cnt && !done; i += 2) {
+    const int ja = list[i];
+    const bool has_b = i + 1 < cnt;
+    const int jb = has_b ? list[i + 1] : ja;
+    const float4 a0 = s_g0[ja], a1 = s_g1[ja];
+    const float4 b0 = s_g0[jb], b1 = s_g1[jb];
+    float ga, gb;
+    const float alpha_a = composite_alpha(a0, a1.x, a1.y, a0.x - fx, a0.y - fy, ga);
+    float alpha_b = composite_alpha(b0, b1.x, b1.y, b0.x - fx, b0.y - fy, gb);
+    if (!has_b) alpha_b = 0.f;
+    if (alpha_a > 0.f) {
+      const float Tn = T * (1.f - alpha_a);
+      if (Tn < kTMin) {
+        done = true;
+        break;
+      }
+      const float w = alpha_a * T;
+      R += a1.z * w;
+      G += a1.w * w;
+      B += s_blue[ja] * w;
+      T = Tn;
+      if (AUX) last = base + ja + 1;
+    }
+    if (alpha_b > 0.f) {
+      const float Tn = T * (1.f - alpha_b);
+      if (Tn < kTMin) {
+        done = true;
+        break;
+      }
+      const float w = alpha_b * T;
+      R += b1.z * w;
+      G += b1.w * w;
+      B += s_blue[jb] * w;
+      T = Tn;
+      if (AUX) last = base + jb + 1;
+    }
+  }
+  __syncwarp();
+}
+
+// Stage Gaussian g of a batch into slot k.
+__device__ __forceinline__ void stage_gaussian(int k, uint32_t g, const float2* __restrict__ xy,
+                                               const float4* __restrict__ conic_opacity,
+                                               const float* __restrict__ rgb, int tx, int ty, float4* s_g0,
+                                               float4* s_g1, float* s_blue, uint32_t* s_mask) {
+  const float2 p = xy[g];
+  const float4 co = conic_opacity[g];
+  s_g0[k] = composite_coeffs(p, co);
+  s_g1[k] = make_float4(composite_b2(co), co.w, rgb[3 * g], rgb[3 * g + 1]);
+  s_blue[k] = rgb[3 * g + 2];
+  s_mask[k] = block_mask(p, co, composite_exp_threshold(co.w), tx, ty);
+}
+
+__device__ __forceinline__ void write_pixel(bool inside, int px, int py, int width, float R, float G, float B,
+                                            float T, int last, float* image, float* t_final, int* n_contrib,
+                                            bool aux) {
+  if (!inside) return;
+  const int pix = py * width + px;
+  image[3 * pix] = R;
+  image[3 * pix + 1] = G;
+  image[3 * pix + 2] = B;
+  if (aux) {
+    if (t_final) t_final[pix] = T;
+    if (n_contrib) n_contrib[pix] = last;
+  }
+}
+
+// Tile lists as [start, end) ranges into a list of Gaussian indices.
+template <bool AUX>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) composite_kernel(int width, int height, int tiles_x,
                                                             const uint2* __restrict__ ranges,
                                                             const uint32_t* __restrict__ values,
                                                             const float2* __restrict__ xy,
@@ -74,99 +162,31 @@ __global__ void __launch_bounds__(kThreads) composite_kernel(int width, int heig
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t lane_lt = (1u << lane) - 1u;
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < width && py < height;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   const uint2 range = ranges[tile];
   const int n = (int)(range.y - range.x);
-  uint8_t* list = s_list[warp];
 
   bool done = !inside;
   float T = 1.f, R = 0.f, G = 0.f, B = 0.f;
   int last = 0;
   for (int base = 0, it = 0; base < n; base += kBatch, ++it) {
-    float4* s_g0 = s_g0b[it & 1];
-    float4* s_g1 = s_g1b[it & 1];
-    float* s_blue = s_blueb[it & 1];
-    uint32_t* s_mask = s_maskb[it & 1];
+    const int b = it & 1;
     const int k = base + (int)threadIdx.x;
-    if (k < n) {
-      const uint32_t g = values[range.x + k];
-      const float2 p = xy[g];
-      const float4 co = conic_opacity[g];
-      s_g0[threadIdx.x] = composite_coeffs(p, co);
-      s_g1[threadIdx.x] = make_float4(composite_b2(co), co.w, rgb[3 * g], rgb[3 * g + 1]);
-      s_blue[threadIdx.x] = rgb[3 * g + 2];
-      s_mask[threadIdx.x] = block_mask(p, co, composite_exp_threshold(co.w), tx, ty);
-    }
+    if (k < n)
+      stage_gaussian(threadIdx.x, values[range.x + k], xy, conic_opacity, rgb, tx, ty, s_g0b[b], s_g1b[b],
+                     s_blueb[b], s_maskb[b]);
     // one barrier per batch: this batch is staged, the buffer staged next was
     // last read for batch i - 1, which every thread has finished; and if every
     // pixel has saturated the tile is done
     if (__syncthreads_count(done) == kThreads) break;
     if (__all_sync(0xffffffffu, done)) continue;  // warp-uniform
-    const int m = min(kBatch, n - base);
-    int cnt = 0;
-    for (int c0 = 0; c0 < m; c0 += 32) {
-      const int j = c0 + lane;
-      const bool hit = j < m && ((s_mask[j] >> warp) & 1u);
-      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) list[cnt + __popc(bal & lane_lt)] = (uint8_t)j;
-      cnt += __popc(bal);
-    }
-    __syncwarp();
-    // two Gaussians per step: both weights are evaluated before the two
-    // (sequential, front-to-back) transmittance updates
-    for (int i = 0; i < cnt && !done; i += 2) {
-      const int ja = list[i];
-      const bool has_b = i + 1 < cnt;
-      const int jb = has_b ? list[i + 1] : ja;
-      const float4 a0 = s_g0[ja], a1 = s_g1[ja];
-      const float4 b0 = s_g0[jb], b1 = s_g1[jb];
-      float ga, gb;
-      const float alpha_a = composite_alpha(a0, a1.x, a1.y, a0.x - fx, a0.y - fy, ga);
-      float alpha_b = composite_alpha(b0, b1.x, b1.y, b0.x - fx, b0.y - fy, gb);
-      if (!has_b) alpha_b = 0.f;
-      if (alpha_a > 0.f) {
-        const float Tn = T * (1.f - alpha_a);
-        if (Tn < kTMin) {
-          done = true;
-          break;
-        }
-        const float w = alpha_a * T;
-        R += a1.z * w;
-        G += a1.w * w;
-        B += s_blue[ja] * w;
-        T = Tn;
-        if (AUX) last = base + ja + 1;
-      }
-      if (alpha_b > 0.f) {
-        const float Tn = T * (1.f - alpha_b);
-        if (Tn < kTMin) {
-          done = true;
-          break;
-        }
-        const float w = alpha_b * T;
-        R += b1.z * w;
-        G += b1.w * w;
-        B += s_blue[jb] * w;
-        T = Tn;
-        if (AUX) last = base + jb + 1;
-      }
-    }
-    __syncwarp();
+    composite_batch<AUX>(min(kBatch, n - base), base, s_g0b[b], s_g1b[b], s_blueb[b], s_maskb[b], s_list[warp],
+                         warp, lane, fx, fy, done, T, R, G, B, last);
   }
-  if (inside) {
-    const int pix = py * width + px;
-    image[3 * pix] = R;
-    image[3 * pix + 1] = G;
-    image[3 * pix + 2] = B;
-    if (AUX) {
-      if (t_final) t_final[pix] = T;
-      if (n_contrib) n_contrib[pix] = last;
-    }
-  }
+  write_pixel(inside, px, py, width, R, G, B, T, last, image, t_final, n_contrib, AUX);
 }
 
 }  // namespace

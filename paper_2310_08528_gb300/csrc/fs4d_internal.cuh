@@ -131,6 +131,19 @@ struct EmitArgs {
   uint32_t* tile_count;         // [n_tiles] (zeroed): pairs per tile
   int n_tiles;
   uint32_t* status;
+  // tile bitmap binning (launch_mark_tiles / launch_extract_tiles)
+  uint32_t* bitmap;             // [n_tiles][words], bit (i & 31) of word i >> 5 of row t: the
+                                // Gaussian of depth rank i touches tile t (all zero between frames)
+  int words;                    // words per row: bitmap_words(n)
+  const uint2* ranges;          // [n_tiles] tile [start, end) from the tile scan
+  const uint32_t* tile_order;   // NULL or a permutation of the tiles: extraction order
+  // with sorted_xy non-NULL, mark also copies the projected Gaussians into depth-rank order
+  const float2* xy;
+  const float4* conic_opacity;
+  const float* rgb;
+  float2* sorted_xy;            // [n]
+  float4* sorted_co;            // [n]
+  float* sorted_rgb;            // [n][3]
 };
 
 struct SortWork {
@@ -156,8 +169,19 @@ cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s);
 // tile ranges (from the per-tile counts; all (0, 0) when num_pairs[1] == 0 < num_pairs[0]),
 // if hist != NULL the [passes][256] digit histograms of the pair sort on the tile bits, and
 // if order != NULL a permutation of the tiles, longest lists first (compositing launch order)
-cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, const uint32_t* num_pairs, uint2* ranges,
-                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s);
+// capacity >= 0: the overflow test is the tiles' total > capacity instead (num_pairs[1] is then
+// written as the total, or 0 on overflow, and status, if non-NULL, gets kStatusCapacity)
+cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, uint32_t* num_pairs, uint2* ranges,
+                             uint32_t* hist, int passes, uint32_t* order, cudaStream_t s, long long capacity = -1,
+                             uint32_t* status = nullptr);
+// Tile bitmap binning (the alternative to emission + pair sort when the bitmap is small):
+// mark sets the bit of every (tile, depth rank) pair and counts the pairs per tile
+// (tile_count, num_pairs[0]); after the tile scan, extract walks each tile's row in rank
+// order, writes the depth ranks at the tile's range -- or with ids the Gaussians (and
+// keys if non-NULL) -- and clears the row.
+int bitmap_words(int n);        // words per tile row (a multiple of 4)
+cudaError_t launch_mark_tiles(const EmitArgs& a, cudaStream_t s);
+cudaError_t launch_extract_tiles(const EmitArgs& a, bool ids, cudaStream_t s);
 
 int sort_passes(int key_bits);
 long long sort_parts(long long n);
@@ -177,7 +201,6 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
                              const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
                              float* t_final, int* n_contrib, cudaStream_t s, const uint32_t* order = nullptr);
-
 }  // namespace fs4d
 
 // ================================================================ backward

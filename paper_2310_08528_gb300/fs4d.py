@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfs4d.so")
 
 FP32, BF16 = 0, 1
+BINNING_AUTO, BINNING_SORT, BINNING_BITMAP = 0, 1, 2
 STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_ERR_CAPACITY",
           4: "FS4D_ERR_CUDA", 5: "FS4D_ERR_TIMEOUT", 6: "FS4D_ERR_NOT_FOUND", 7: "FS4D_ERR_UNIMPLEMENTED"}
 
@@ -23,7 +24,7 @@ STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_E
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
            "fs4d_load_scene", "fs4d_unload_scene", "fs4d_update_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
            "fs4d_render_host", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
-           "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
+           "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_composite")
 STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
 
@@ -85,6 +86,8 @@ def library(path: str = LIB_PATH):
         "fs4d_frame_free": [vp, vp],
         "fs4d_frame_pairs": [vp, C.POINTER(i64)],
         "fs4d_last_pairs": [vp, C.POINTER(i64)],
+        "fs4d_set_binning": [vp, i32],
+        "fs4d_last_binning": [vp, C.POINTER(i32)],
         "fs4d_set_stage_timing": [vp, i32],
         "fs4d_stage_times": [vp, C.POINTER(C.c_float)],
         "fs4d_project": [vp, i32, vp, vp, vp, vp, vp, i32, C.POINTER(Camera), C.POINTER(Projected)],
@@ -279,6 +282,16 @@ class Context:
         k = C.c_int64()
         self.call("fs4d_last_pairs", C.byref(k))
         return k.value
+
+    def set_binning(self, mode: int) -> None:
+        """BINNING_AUTO (tile bitmap when it fits) or BINNING_SORT (keys + radix sort)."""
+        self.call("fs4d_set_binning", int(mode))
+
+    def last_binning(self) -> int:
+        """BINNING_BITMAP or BINNING_SORT: how the last frame on this context was binned."""
+        m = C.c_int32()
+        self.call("fs4d_last_binning", C.byref(m))
+        return m.value
 
     # ------------------------------------------------------------------ stages
     def project(self, means, quats, log_scales, opacity_logits, sh, sh_degree: int, cam):

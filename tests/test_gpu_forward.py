@@ -140,15 +140,32 @@ def _random_bins(rng, n, tx, ty, max_w=4, tie_every=17):
     return depth, rect
 
 
+BITMAP_MAX = 256 << 20
+
+
+def _expect_binning(mode, n, tx, ty):
+    """The binning a frame of n Gaussians over tx x ty tiles gets under `mode`."""
+    fits = tx * ty * ((n + 127) // 128) * 16 <= BITMAP_MAX
+    return fs4d.BINNING_BITMAP if mode == fs4d.BINNING_AUTO and fits else fs4d.BINNING_SORT
+
+
+@pytest.fixture(params=[fs4d.BINNING_AUTO, fs4d.BINNING_SORT], ids=["auto", "sort"])
+def binning(ctx, request):
+    ctx.set_binning(request.param)
+    yield request.param
+    ctx.set_binning(fs4d.BINNING_AUTO)
+
+
 @pytest.mark.parametrize("n,tx,ty", [(1, 1, 1), (7, 3, 2), (2047, 8, 8), (2049, 50, 50), (40000, 50, 50),
                                      (150001, 240, 135)])
-def test_bin_sort_bit_exact(ctx, n, tx, ty):
+def test_bin_sort_bit_exact(ctx, binning, n, tx, ty):
     rng = np.random.default_rng(n)
     depth, rect = _random_bins(rng, n, tx, ty)
     keys_o, vals_o, ranges_o = oracle.bin_sort(depth.view(np.uint32), rect, tx, ty)
     K = len(keys_o)
     keys, vals, ranges, Kg = ctx.bin_sort(dev(depth), dev(rect), tx, ty, K + 100)
     torch.cuda.synchronize()
+    assert ctx.last_binning() == _expect_binning(binning, n, tx, ty)
     assert Kg == K
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_o)
     assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_o)
@@ -158,7 +175,7 @@ def test_bin_sort_bit_exact(ctx, n, tx, ty):
 @pytest.mark.parametrize("n,tx,ty,max_w", [(30000, 4, 4, 4),     # tiles of ~7k pairs: the long-tile sort
                                            (60000, 2, 2, 2),     # tiles of ~30k: chunk sort + merges
                                            (50000, 40, 3, 3)])   # one hot tile among short ones
-def test_bin_sort_dense_tiles_bit_exact(ctx, n, tx, ty, max_w):
+def test_bin_sort_dense_tiles_bit_exact(ctx, binning, n, tx, ty, max_w):
     rng = np.random.default_rng(n + tx)
     depth, rect = _random_bins(rng, n, tx, ty, max_w=max_w, tie_every=7)
     if tx == 40:  # half of the Gaussians on tile 0 only (several merge rounds, odd last run)
@@ -169,13 +186,14 @@ def test_bin_sort_dense_tiles_bit_exact(ctx, n, tx, ty, max_w):
     K = len(keys_o)
     keys, vals, ranges, Kg = ctx.bin_sort(dev(depth), dev(rect), tx, ty, K)
     torch.cuda.synchronize()
+    assert ctx.last_binning() == _expect_binning(binning, n, tx, ty)
     assert Kg == K
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_o)
     assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_o)
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
 
 
-def test_bin_sort_empty_and_capacity(ctx):
+def test_bin_sort_empty_and_capacity(ctx, binning):
     depth = np.ones(10, np.float32)
     rect = np.zeros((10, 4), np.int32)  # every Gaussian culled
     keys, vals, ranges, K = ctx.bin_sort(dev(depth), dev(rect), 4, 4, 16)
@@ -184,6 +202,16 @@ def test_bin_sort_empty_and_capacity(ctx):
     with pytest.raises(fs4d.Fs4dError) as e:
         ctx.bin_sort(dev(depth), dev(rect), 4, 4, 100)
     assert e.value.status == 3
+    # the overflowed call leaves no state behind (the tile bitmap is cleared)
+    depth = np.random.default_rng(3).uniform(1, 2, 10).astype(np.float32)
+    rect[5:] = (1, 1, 3, 2)
+    keys_o, vals_o, ranges_o = oracle.bin_sort(depth.view(np.uint32), rect, 4, 4)
+    keys, vals, ranges, K = ctx.bin_sort(dev(depth), dev(rect), 4, 4, 200)
+    torch.cuda.synchronize()
+    assert K == len(keys_o)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_o)
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), vals_o)
+    assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
 
 
 @pytest.mark.parametrize("n,bits", [(1, 8), (4095, 12), (4097, 33), (100000, 44), (262145, 64), (30000, 1)])
@@ -332,7 +360,9 @@ def test_render_async_and_graph_replay_equal_sync(ctx):
     ctx.unload_scene(sid)
 
 
-def test_capacity_overflow_sets_status_not_fault(ctx):
+def test_capacity_overflow_sets_status_not_fault(ctx, binning):
+    """A frame with more tile pairs than the reserved capacity must report, not
+    fault, and leave nothing behind (the tile bitmap is cleared)."""
     s = sg.make_tiny(7)
     cam = sg.tiny_camera()
     sid = ctx.load_scene(s)
@@ -349,8 +379,41 @@ def test_capacity_overflow_sets_status_not_fault(ctx):
     with pytest.raises(fs4d.Fs4dError) as e:
         ctx.check_device_status()
     assert e.value.status == 3
+    assert ctx.last_binning() == _expect_binning(binning, s.n, 8, 8)
     ctx.check_device_status()  # cleared
+    # nothing of the overflowed frame stays behind: the next one is exact
+    ctx.call("fs4d_reserve", sid, 128, 128, 2 * K)
+    ctx.render_async(sid, cam, d_cam, d_t, out)
+    ref = ctx.render(sid, cam, 0.5)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    ctx.check_device_status()
     ctx.unload_scene(sid)
+
+
+@pytest.mark.parametrize("prec", [fs4d.FP32, fs4d.BF16])
+@pytest.mark.parametrize("w,h", [(800, 800), (333, 517)])
+def test_bitmap_and_sort_binning_render_identical_images(ctx, prec, w, h):
+    """Both binnings give the same per-tile lists, so the images are bit-identical
+    (Sec. 3.1: per-tile depth order), also for ragged tile grids and views whose
+    Gaussians leave the image."""
+    s = sg.make_object(4, n=30011)
+    sid = ctx.load_scene(s)
+    cams = sg.hemisphere_cameras(3, width=w, height=h, seed=5)
+    try:
+        for i, cam in enumerate(cams):
+            ctx.set_binning(fs4d.BINNING_SORT)
+            a = ctx.render(sid, cam, 0.3 * i, prec=prec, with_aux=True)
+            assert ctx.last_binning() == fs4d.BINNING_SORT
+            ctx.set_binning(fs4d.BINNING_AUTO)
+            b = ctx.render(sid, cam, 0.3 * i, prec=prec, with_aux=True)
+            assert ctx.last_binning() == fs4d.BINNING_BITMAP
+            torch.cuda.synchronize()
+            for x, y in zip(a, b):  # image, final transmittance, last contributor
+                assert torch.equal(x, y)
+    finally:
+        ctx.set_binning(fs4d.BINNING_AUTO)
+        ctx.unload_scene(sid)
 
 
 # ------------------------------------------------------------------ BF16 tensor-core path

@@ -101,18 +101,25 @@ def test_alone_equals_mix(world, server):
     assert st["max_concurrent"] > 1        # frames of several requests were on the GPU together
 
 
-def test_capacity_overflow_is_retried(world, server):
+@pytest.mark.parametrize("binning", ["sort", "auto"])
+def test_capacity_overflow_is_retried(world, server, binning):
+    """A frame whose pairs overflow the slot's first capacity guess is re-run with
+    a larger one (either binning), and gives the reference image."""
     ctx, scenes = world
-    srv = server(max_inflight=2, max_batch=2, pairs_per_gaussian=0.01)
-    cam = cam_for(1, 256, 256, 2)
-    out = torch.zeros((256, 256, 3), device="cuda")
-    tk = srv.submit(scenes[1], cam, 0.4, out)
-    d = wait_all(srv, [tk])
-    assert d[tk]["status"] == OK
-    assert srv.stats()["retried"] >= 1
-    ref = ctx.render(scenes[1], cam, 0.4)
-    torch.cuda.synchronize()
-    assert torch.equal(out, ref)
+    ctx.set_binning(fs4d.BINNING_SORT if binning == "sort" else fs4d.BINNING_AUTO)
+    try:
+        srv = server(max_inflight=2, max_batch=2, pairs_per_gaussian=0.01)
+        cam = cam_for(1, 256, 256, 2)
+        out = torch.zeros((256, 256, 3), device="cuda")
+        tk = srv.submit(scenes[1], cam, 0.4, out)
+        d = wait_all(srv, [tk])
+        assert d[tk]["status"] == OK
+        assert srv.stats()["retried"] >= 1
+        ref = ctx.render(scenes[1], cam, 0.4)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    finally:
+        ctx.set_binning(fs4d.BINNING_AUTO)
 
 
 def test_admission_respects_the_device_memory_budget(world, server):
