@@ -1,7 +1,10 @@
 // EWA projection of the deformed Gaussians (Eq. 2, Eq. 3) with view-dependent
 // SH colour.  One thread per Gaussian; the structure-of-arrays inputs are read
 // with coalesced loads (quaternions as one 128-bit load) and every output is a
-// coalesced store.  Float32 throughout.
+// coalesced store.  Every input load is issued at the start: the SH rows (the
+// bulk of the bytes) go to shared memory by cp.async and are waited for only
+// when the colour is evaluated, so their latency overlaps the geometry.  Float32
+// throughout.
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
@@ -68,10 +71,29 @@ __device__ __forceinline__ void depth_histogram(const ProjectArgs& a, int g, flo
   }
 }
 
+// float4 per Gaussian of SH coefficients when a row is 16-byte aligned (K*3 % 4 == 0),
+// else 0 (read directly)
+template <int DEG>
+__host__ __device__ constexpr int sh_vec4() {
+  return (3 * (DEG + 1) * (DEG + 1)) % 4 == 0 ? 3 * (DEG + 1) * (DEG + 1) / 4 : 0;
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int SHQ = sh_vec4<DEG>();
+  extern __shared__ float4 s_sh[];  // [SHQ][256]: the CTA's SH rows, conflict-free per q
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = g < a.n;
+  if (SHQ > 0 && valid) {
+    const float4* src = reinterpret_cast<const float4*>(a.sh + (long long)g * K * 3);
+#pragma unroll
+    for (int q = 0; q < SHQ; ++q) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_sh[q * 256 + threadIdx.x]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + q) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   CamParams c = a.cam;
   if (a.cam_dev) {
     const fs4d_camera* d = a.cam_dev;
@@ -81,18 +103,27 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) c.m[4 * r + k] = d->world_to_cam[4 * r + k];
   }
-  float X0 = 0.f, X1 = 0.f, X2 = 0.f;
+  float X0 = 0.f, X1 = 0.f, X2 = 0.f, logit = 0.f, ls0 = 0.f, ls1 = 0.f, ls2 = 0.f;
+  float4 q4 = make_float4(1.f, 0.f, 0.f, 0.f);
   if (valid) {
     X0 = a.means[3 * g];
     X1 = a.means[3 * g + 1];
     X2 = a.means[3 * g + 2];
+    logit = a.opacity_logits[g];
+    q4 = reinterpret_cast<const float4*>(a.quats)[g];
+    ls0 = a.log_scales[3 * g];
+    ls1 = a.log_scales[3 * g + 1];
+    ls2 = a.log_scales[3 * g + 2];
   }
   const float px = c.m[0] * X0 + c.m[1] * X1 + c.m[2] * X2 + c.m[3];
   const float py = c.m[4] * X0 + c.m[5] * X1 + c.m[6] * X2 + c.m[7];
   const float pz = c.m[8] * X0 + c.m[9] * X1 + c.m[10] * X2 + c.m[11];
   if (a.depth_hist) depth_histogram(a, g, pz);  // the whole CTA takes part
-  if (!valid) return;
-  const float opacity = 1.f / (1.f + expf(-a.opacity_logits[g]));
+  if (!valid) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
+  const float opacity = 1.f / (1.f + expf(-logit));
   a.depth[g] = pz;
   if (a.depth_keys) {
     a.depth_keys[g] = __float_as_uint(pz);
@@ -105,17 +136,19 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   a.rgb[3 * g] = 0.f;
   a.rgb[3 * g + 1] = 0.f;
   a.rgb[3 * g + 2] = 0.f;
-  if (!(pz > c.znear)) return;
+  // (every exit below first waits for this thread's SH copies)
+  if (!(pz > c.znear)) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
 
   // Sigma = R S S^T R^T (Eq. 2), R from the normalised quaternion, S = diag(exp(s)).
-  const float4 q4 = reinterpret_cast<const float4*>(a.quats)[g];
   const float qinv = 1.f / sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
   const float w = q4.x * qinv, x = q4.y * qinv, y = q4.z * qinv, z = q4.w * qinv;
   const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z), R02 = 2.f * (x * z + w * y);
   const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z), R12 = 2.f * (y * z - w * x);
   const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x), R22 = 1.f - 2.f * (x * x + y * y);
-  const float s0 = expf(a.log_scales[3 * g]), s1 = expf(a.log_scales[3 * g + 1]),
-              s2 = expf(a.log_scales[3 * g + 2]);
+  const float s0 = expf(ls0), s1 = expf(ls1), s2 = expf(ls2);
 
   // Sigma' = J W Sigma W^T J^T (Eq. 3) with the perspective Jacobian at the mean.
   // With Sigma = (R S)(R S)^T this is A A^T for the 2x3 matrix A = J W R S, which
@@ -143,7 +176,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   const float m01 = A00 * A11 - A01 * A10, m02 = A00 * A12 - A02 * A10, m12 = A01 * A12 - A02 * A11;
   const float ca = aa + kDilation, cb = bb, cc = dd + kDilation;
   const float det = (m01 * m01 + m02 * m02 + m12 * m12) + kDilation * (aa + dd) + kDilation * kDilation;
-  if (!(det > 0.f)) return;
+  if (!(det > 0.f)) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
   const float idet = 1.f / det;
   const float hd = 0.5f * (aa - dd);
   const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + bb * bb);
@@ -154,7 +190,10 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   int y0 = (int)floorf((v - fr) * (1.f / kTile)), y1 = (int)floorf((v + fr) * (1.f / kTile)) + 1;
   x0 = min(a.tiles_x, max(0, x0)); x1 = min(a.tiles_x, max(0, x1));
   y0 = min(a.tiles_y, max(0, y0)); y1 = min(a.tiles_y, max(0, y1));
-  if (x1 <= x0 || y1 <= y0) return;
+  if (x1 <= x0 || y1 <= y0) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
 
   // View-dependent colour: SH along the direction from the camera centre.
   const float cpx = -(c.m[0] * c.m[3] + c.m[4] * c.m[7] + c.m[8] * c.m[11]);
@@ -163,16 +202,17 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   float dx = X0 - cpx, dy = X1 - cpy, dz = X2 - cpz;
   const float dinv = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
   dx *= dinv; dy *= dinv; dz *= dinv;
-  constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[16];
   sh_basis(DEG, dx, dy, dz, Y);
-  // K*3 coefficients per Gaussian; 16-byte aligned rows (K*3 % 4 == 0) load as float4
+  // K*3 coefficients per Gaussian: from the shared-memory copy (16-byte aligned
+  // rows), else read directly
   float shc[3 * K];
   const float* sh = a.sh + (long long)g * K * 3;
-  if ((3 * K) % 4 == 0) {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if (SHQ > 0) {
 #pragma unroll
-    for (int q = 0; q < 3 * K / 4; ++q) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(sh) + q);
+    for (int q = 0; q < SHQ; ++q) {
+      const float4 v = s_sh[q * 256 + threadIdx.x];
       shc[4 * q] = v.x; shc[4 * q + 1] = v.y; shc[4 * q + 2] = v.z; shc[4 * q + 3] = v.w;
     }
   } else {
@@ -197,17 +237,29 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 
 }  // namespace
 
+template <int DEG>
+cudaError_t launch_project_deg(const ProjectArgs& a, unsigned grid, cudaStream_t s) {
+  constexpr size_t smem = 16 * 256 * (size_t)sh_vec4<DEG>();
+  static bool attr = false;
+  if (!attr && smem > 0) {  // (with the 4 KB of static histogram the total can pass the 48 KB default)
+    cudaError_t e = cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  attr = true;
+  project_kernel<DEG><<<grid, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.n + 255) / 256);
   switch (a.sh_degree) {
-    case 0: project_kernel<0><<<grid, 256, 0, s>>>(a); break;
-    case 1: project_kernel<1><<<grid, 256, 0, s>>>(a); break;
-    case 2: project_kernel<2><<<grid, 256, 0, s>>>(a); break;
-    case 3: project_kernel<3><<<grid, 256, 0, s>>>(a); break;
+    case 0: return launch_project_deg<0>(a, grid, s);
+    case 1: return launch_project_deg<1>(a, grid, s);
+    case 2: return launch_project_deg<2>(a, grid, s);
+    case 3: return launch_project_deg<3>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace fs4d
