@@ -292,27 +292,32 @@ __device__ __forceinline__ uint32_t rect_row(uint32_t k, uint32_t w) {
   return (uint32_t)r;
 }
 
-// 256 consecutive depth ranks per CTA; warp w owns ranks [32w, 32w + 32) of the
-// CTA, i.e. one word column of every row; a rank's projected Gaussian is copied
-// to its rank's slot when sorted copies are asked for.  Each warp spreads its pairs over its
-// lanes (binary search over the warp's exclusive pair offsets by shuffles), and
-// each pair sets its bit with one global atomic OR.  Pairs per tile are summed in
-// shared memory and merged by one global atomic per touched tile.
-__global__ void __launch_bounds__(kThreads) mark_kernel(EmitArgs a, int smem_tiles) {
+// 256 consecutive depth ranks per CTA; warps w and w + 8 own ranks [32w, 32w + 32)
+// of the CTA, i.e. one word column of every row, and each takes every other chunk
+// of 32 of the column's pairs (half the chain of dependent steps per warp).  A
+// warp spreads a chunk over its lanes (binary search over the column's exclusive
+// pair offsets by shuffles), and each pair sets its bit with one global atomic OR.
+// Pairs per tile are summed in shared memory and merged by one global atomic per
+// touched tile.  A rank's projected Gaussian is copied to its rank's slot when
+// sorted copies are asked for.
+constexpr int kMarkHalves = 2;  // warps per word column: each takes every other 32-pair chunk
+constexpr int kMarkThreads = kPart * kMarkHalves;
+
+__global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem_tiles) {
   extern __shared__ uint32_t s_tc[];
   const int tid = threadIdx.x;
-  for (int i = tid; i < smem_tiles; i += kThreads) s_tc[i] = 0;
+  for (int i = tid; i < smem_tiles; i += kMarkThreads) s_tc[i] = 0;
   __syncthreads();
-  const uint32_t lane = lane_id(), warp = (uint32_t)tid / 32;
+  const uint32_t lane = lane_id(), warp = ((uint32_t)tid / 32) % (kPart / 32), half = (uint32_t)tid / kPart;
   const uint32_t* order = (a.order_sel && *a.order_sel) ? a.order_alt : a.order;
-  const int pos = blockIdx.x * kPart + tid;
+  const int pos = blockIdx.x * kPart + (int)(warp * 32 + lane);
   int4 r = make_int4(0, 0, 0, 0);
   uint32_t cnt = 0;
   if (pos < a.n) {
     const uint32_t g = order ? order[pos] : (uint32_t)pos;
     r = a.rect[g];
     cnt = (uint32_t)max(0, r.z - r.x) * (uint32_t)max(0, r.w - r.y);
-    if (a.sorted_xy && cnt) {  // the compositing reads the projected Gaussians by depth rank
+    if (a.sorted_xy && cnt && half == 0) {  // the compositing reads the projected Gaussians by depth rank
       a.sorted_xy[pos] = a.xy[g];
       a.sorted_co[pos] = a.conic_opacity[g];
       a.sorted_rgb[3 * pos] = a.rgb[3 * g];
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) mark_kernel(EmitArgs a, int smem_til
   }
   const uint32_t excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
   uint32_t* col = a.bitmap + ((uint32_t)blockIdx.x * kPart + warp * 32) / 32;
-  for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+  for (uint32_t j0 = 32 * half; j0 < total; j0 += 32 * kMarkHalves) {
     const uint32_t j = j0 + lane;
     // last lane whose offset is <= j (a lane with no tiles shares its offset with
     // the next lane, so it never wins)
@@ -352,10 +357,10 @@ __global__ void __launch_bounds__(kThreads) mark_kernel(EmitArgs a, int smem_til
         atomicAdd(&a.tile_count[tile], 1u);
     }
   }
-  if (lane == 0 && total) atomicAdd(a.num_pairs, total);
+  if (lane == 0 && half == 0 && total) atomicAdd(a.num_pairs, total);
   if (smem_tiles) {
     __syncthreads();
-    for (int t = tid; t < smem_tiles; t += kThreads) {
+    for (int t = tid; t < smem_tiles; t += kMarkThreads) {
       const uint32_t v = s_tc[t];
       if (v) atomicAdd(&a.tile_count[t], v);
     }
@@ -507,7 +512,7 @@ cudaError_t launch_mark_tiles(const EmitArgs& a, cudaStream_t s) {
   }
   if (a.words < bitmap_words(a.n)) return cudaErrorInvalidValue;
   const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
-  mark_kernel<<<emit_parts(a.n), kThreads, 4 * (size_t)st, s>>>(a, st);
+  mark_kernel<<<emit_parts(a.n), kMarkThreads, 4 * (size_t)st, s>>>(a, st);
   return cudaGetLastError();
 }
 
