@@ -22,9 +22,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr float kTMin = 1e-4f;
 constexpr int kMinBlocks = 5;  // CTAs per SM the register budget must allow
 
-// Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0).
-__device__ __forceinline__ float edge_min(float A, float B, float C, float u, float t0, float t1) {
-  const float t = fminf(t1, fmaxf(t0, -B * u / C));
+// Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0), whose
+// unconstrained minimiser is t = k u with k = -B / C.
+__device__ __forceinline__ float edge_min(float A, float B, float C, float k, float u, float t0, float t1) {
+  const float t = fminf(t1, fmaxf(t0, k * u));
   return A * u * u + 2.f * B * u * t + C * t * t;
 }
 
@@ -32,26 +33,34 @@ __device__ __forceinline__ float edge_min(float A, float B, float C, float u, fl
 // of tile (tx, ty)) may reach alpha >= 1/255: the minimum of q(d) = d^T K d over
 // the block's pixel-centre rectangle (d relative to the mean) is compared with
 // s = -2 * thr.  The minimum of a positive-definite quadratic over a rectangle is
-// 0 if the mean lies inside, else on one of the four edges.  A 0.2% + 1e-3
-// margin keeps the test conservative against float32 rounding.
+// 0 if the mean lies inside, else on one of the four edges (each minimised in
+// closed form; a rounded minimiser only raises q by a second-order amount).  If
+// all four corner pixel centres of the tile lie in the ellipse q <= s, so does the
+// whole tile (the ellipse is convex) and every block is set at once.  A 0.2% +
+// 1e-3 margin keeps the test conservative against float32 rounding.
 __device__ __forceinline__ uint32_t block_mask(float2 p, float4 co, float thr, int tx, int ty) {
   if (!(thr < 0.f)) return 0u;                         // alpha can never reach 1/255
   const float A = co.x, B = co.y, C = co.z;
   if (!(A > 0.f && C > 0.f && A * C - B * B > 0.f)) return 0xffu;  // no usable bound: test every pixel
   const float s = -2.f * thr * 1.002f + 1e-3f;
+  const float X0 = (float)(tx * kTile) + 0.5f - p.x, X1 = X0 + (float)(kTile - 1);
+  const float Y0 = (float)(ty * kTile) + 0.5f - p.y, Y1 = Y0 + (float)(kTile - 1);
+  auto q = [&](float x, float y) { return A * x * x + 2.f * B * x * y + C * y * y; };
+  if (fmaxf(fmaxf(q(X0, Y0), q(X1, Y0)), fmaxf(q(X0, Y1), q(X1, Y1))) <= s) return 0xffu;
+  const float kx = -B / C, ky = -B / A;
   uint32_t mask = 0u;
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
-    const float x0 = (float)(tx * kTile + (b & 1) * 8) + 0.5f - p.x, x1 = x0 + 7.f;
-    const float y0 = (float)(ty * kTile + (b >> 1) * 4) + 0.5f - p.y, y1 = y0 + 3.f;
-    float q;
+    const float x0 = X0 + (float)((b & 1) * 8), x1 = x0 + 7.f;
+    const float y0 = Y0 + (float)((b >> 1) * 4), y1 = y0 + 3.f;
+    float qm;
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) {
-      q = 0.f;
+      qm = 0.f;
     } else {
-      q = fminf(fminf(edge_min(A, B, C, x0, y0, y1), edge_min(A, B, C, x1, y0, y1)),
-                fminf(edge_min(C, B, A, y0, x0, x1), edge_min(C, B, A, y1, x0, x1)));
+      qm = fminf(fminf(edge_min(A, B, C, kx, x0, y0, y1), edge_min(A, B, C, kx, x1, y0, y1)),
+                 fminf(edge_min(C, B, A, ky, y0, x0, x1), edge_min(C, B, A, ky, y1, x0, x1)));
     }
-    if (q <= s) mask |= 1u << b;
+    if (qm <= s) mask |= 1u << b;
   }
   return mask;
 }
