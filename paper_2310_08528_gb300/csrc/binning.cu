@@ -28,6 +28,8 @@ constexpr int kMaxPasses = 8;
 constexpr int kEmitSmemTiles = 16384;     // tiles counted in shared memory (more: global atomics)
 
 __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int smem_tiles) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ uint32_t s_tc[];      // per-tile pair counts of this partition (smem_tiles != 0)
   __shared__ uint32_t s_part;
   __shared__ uint32_t s_warp[kThreads / 32];
@@ -199,6 +201,8 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_hist[kMaxPasses][256];
   __shared__ uint32_t s_len[33];          // tiles per length class floor(log2(count)) + 1 (0: empty)
+  pdl_wait();
+  pdl_trigger();
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
   for (int i = tid; i < kMaxPasses * 256; i += kScanThreads) (&s_hist[0][0])[i] = 0;
@@ -305,6 +309,8 @@ constexpr int kMarkThreads = kPart * kMarkHalves;
 
 __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem_tiles) {
   extern __shared__ uint32_t s_tc[];
+  pdl_wait();
+  pdl_trigger();
   const int tid = threadIdx.x;
   for (int i = tid; i < smem_tiles; i += kMarkThreads) s_tc[i] = 0;
   __syncthreads();
@@ -395,6 +401,8 @@ __device__ __forceinline__ void extract_bits(const uint4& q, uint32_t r0, uint32
 }
 
 __global__ void __launch_bounds__(kXThreads) extract_kernel(EmitArgs a, int ids) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_warp[2][2][kXThreads / 32];
   const int t = a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x;
   const uint32_t cnt = a.tile_count[t];
@@ -496,8 +504,7 @@ cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s) {
     attr = true;
   }
   const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
-  scan_emit_kernel<<<emit_parts(a.n), kThreads, 4 * (size_t)st, s>>>(a, st);
-  return cudaGetLastError();
+  return launch_pdl(scan_emit_kernel, emit_parts(a.n), kThreads, 4 * (size_t)st, s, a, st);
 }
 
 int bitmap_words(int n) { return ((n + 127) / 128) * 4; }
@@ -512,24 +519,21 @@ cudaError_t launch_mark_tiles(const EmitArgs& a, cudaStream_t s) {
   }
   if (a.words < bitmap_words(a.n)) return cudaErrorInvalidValue;
   const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
-  mark_kernel<<<emit_parts(a.n), kMarkThreads, 4 * (size_t)st, s>>>(a, st);
-  return cudaGetLastError();
+  return launch_pdl(mark_kernel, emit_parts(a.n), kMarkThreads, 4 * (size_t)st, s, a, st);
 }
 
 cudaError_t launch_extract_tiles(const EmitArgs& a, bool ids, cudaStream_t s) {
   if (a.n <= 0 || a.n_tiles <= 0) return cudaSuccess;
   if (a.words < bitmap_words(a.n) || (a.words & 3)) return cudaErrorInvalidValue;
-  extract_kernel<<<a.n_tiles, kXThreads, 0, s>>>(a, ids ? 1 : 0);
-  return cudaGetLastError();
+  return launch_pdl(extract_kernel, a.n_tiles, kXThreads, 0, s, a, ids ? 1 : 0);
 }
 
 cudaError_t launch_tile_scan(const uint32_t* tile_count, int n_tiles, uint32_t* num_pairs, uint2* ranges,
                              uint32_t* hist, int passes, uint32_t* order, cudaStream_t s, long long capacity,
                              uint32_t* status) {
   if (passes > kMaxPasses || n_tiles < 1) return cudaErrorInvalidValue;
-  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, num_pairs, ranges, hist, passes, order, capacity,
-                                              status);
-  return cudaGetLastError();
+  return launch_pdl(tile_scan_kernel, 1, kScanThreads, 0, s, tile_count, n_tiles, num_pairs, ranges, hist, passes, order,
+                    capacity, status);
 }
 
 }  // namespace fs4d
@@ -538,6 +542,8 @@ namespace fs4d {
 namespace {
 __global__ void depth_keys_kernel(const float* __restrict__ depth, int n, unsigned long long* __restrict__ keys,
                                   uint32_t* __restrict__ vals) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   keys[i] = __float_as_uint(depth[i]);
@@ -547,8 +553,7 @@ __global__ void depth_keys_kernel(const float* __restrict__ depth, int n, unsign
 
 cudaError_t launch_depth_keys(const float* depth, int n, unsigned long long* keys, uint32_t* vals, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  depth_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(depth, n, keys, vals);
-  return cudaGetLastError();
+  return launch_pdl(depth_keys_kernel, (n + 255) / 256, 256, 0, s, depth, n, keys, vals);
 }
 
 }  // namespace fs4d

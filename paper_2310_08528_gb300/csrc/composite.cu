@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) composite_kernel(int wid
   __shared__ float s_blueb[2][kBatch];
   __shared__ uint32_t s_maskb[2][kBatch];
   __shared__ uint8_t s_list[kWarps][kBatch];
+  pdl_wait();
+  pdl_trigger();
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -206,13 +208,10 @@ cudaError_t launch_composite(int width, int height, const uint2* ranges, const u
   const int tiles_x = (width + kTile - 1) / kTile, tiles_y = (height + kTile - 1) / kTile;
   if (tiles_x * tiles_y == 0) return cudaSuccess;
   if (t_final || n_contrib)
-    composite_kernel<true><<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy,
-                                                                  conic_opacity, rgb, image, t_final, n_contrib, order);
-  else
-    composite_kernel<false><<<tiles_x * tiles_y, kThreads, 0, s>>>(width, height, tiles_x, ranges, values, xy,
-                                                                   conic_opacity, rgb, image, t_final, n_contrib,
-                                                                   order);
-  return cudaGetLastError();
+    return launch_pdl(composite_kernel<true>, tiles_x * tiles_y, kThreads, 0, s, width, height, tiles_x, ranges, values,
+                      xy, conic_opacity, rgb, image, t_final, n_contrib, order);
+  return launch_pdl(composite_kernel<false>, tiles_x * tiles_y, kThreads, 0, s, width, height, tiles_x, ranges, values,
+                    xy, conic_opacity, rgb, image, t_final, n_contrib, order);
 }
 
 }  // namespace fs4d

@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   float4* sRowS = sRowQ + kTileG;
   for (int i = threadIdx.x; i < a.mg.total / 4; i += kThreads)
     smem4[i] = __ldg(reinterpret_cast<const float4*>(a.mlp_t) + i);
+  // the weights above are the scene's; the rows below may come from earlier work
+  pdl_wait();
+  pdl_trigger();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g4 = lane * 4, o8 = warp * 8;
@@ -247,8 +250,7 @@ cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
   const long long total = (long long)a.n * a.n_t;
   const long long need = (total + kTileG - 1) / kTileG;
   const int grid = (int)(need < sms ? need : sms);
-  deform_fp32_kernel<H, L><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(deform_fp32_kernel<H, L>, grid, kThreads, smem, s, a);
 }
 
 }  // namespace

@@ -195,6 +195,10 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the prologue above reads only the scene's weights; the rows below may come
+  // from earlier work on the stream
+  pdl_wait();
+  pdl_trigger();
   const uint32_t tmem = *sTmem;
   const uint32_t b_addr = smem_u32(sB), x_addr = smem_u32(sX);
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
@@ -395,8 +399,7 @@ cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
   }
   const long long tiles = ((long long)a.n * a.n_t + kRows - 1) / kRows;
   const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
-  deform_tc_kernel<H, L><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(deform_tc_kernel<H, L>, grid, kThreads, smem, s, a);
 }
 
 }  // namespace

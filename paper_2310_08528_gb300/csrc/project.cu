@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) c.m[4 * r + k] = d->world_to_cam[4 * r + k];
   }
+  pdl_wait();  // (the SH rows and the camera are inputs of the frame; the Gaussians come from the deformation)
+  pdl_trigger();
   float X0 = 0.f, X1 = 0.f, X2 = 0.f, logit = 0.f, ls0 = 0.f, ls1 = 0.f, ls2 = 0.f;
   float4 q4 = make_float4(1.f, 0.f, 0.f, 0.f);
   if (valid) {
@@ -246,8 +248,7 @@ cudaError_t launch_project_deg(const ProjectArgs& a, unsigned grid, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   attr = true;
-  project_kernel<DEG><<<grid, 256, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(project_kernel<DEG>, grid, 256, smem, s, a);
 }
 
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s) {

@@ -29,6 +29,8 @@ constexpr int kMaxPasses = 8;
 __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
                                                    const uint32_t* __restrict__ n_dev, long long n_bound,
                                                    int first_bit, int passes, uint32_t* __restrict__ hist) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_hist[kMaxPasses][kRadix];
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   PassSmem<ITEMS>& sm = *reinterpret_cast<PassSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
+  pdl_wait();
+  pdl_trigger();
   if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
   // independent of the ticket: issued while it is in flight
   const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
@@ -286,8 +290,8 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     if (e != cudaSuccess) return e;
     const int blocks = (int)min((n_bound + 1023) / 1024, (long long)152 * 8);
-    hist_kernel<<<blocks, 256, 0, s>>>(keys, n_dev, n_bound, first_bit, passes, work.hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_pdl(hist_kernel, blocks, 256, 0, s, keys, n_dev, n_bound, first_bit, passes, work.hist);
+    if (e != cudaSuccess) return e;
   }
   unsigned long long* kin = keys;
   uint32_t* vin = values;
@@ -311,10 +315,10 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     pa.part_counter = work.part_counters + p;
     pa.status = status;
     if (small)
-      onesweep_kernel<kItemsSmall><<<(unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s>>>(pa);
+      e = launch_pdl(onesweep_kernel<kItemsSmall>, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s, pa);
     else
-      onesweep_kernel<kItemsLarge><<<(unsigned)parts, kThreads, sizeof(PassSmem<kItemsLarge>), s>>>(pa);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      e = launch_pdl(onesweep_kernel<kItemsLarge>, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsLarge>), s, pa);
+    if (e != cudaSuccess) return e;
     unsigned long long* tk = kin; kin = kout; kout = tk;
     uint32_t* tv = vin; vin = vout; vout = tv;
   }
