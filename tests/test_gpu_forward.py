@@ -157,7 +157,8 @@ def binning(ctx, request):
 
 
 @pytest.mark.parametrize("n,tx,ty", [(1, 1, 1), (7, 3, 2), (2047, 8, 8), (2049, 50, 50), (40000, 50, 50),
-                                     (150001, 240, 135)])
+                                     (3001, 200, 100),     # more tiles than the per-CTA shared-memory counts
+                                     (150001, 240, 135)])  # bitmap above its size limit: sort binning
 def test_bin_sort_bit_exact(ctx, binning, n, tx, ty):
     rng = np.random.default_rng(n)
     depth, rect = _random_bins(rng, n, tx, ty)
