@@ -99,6 +99,7 @@ struct Work {
   DevBuf bitmap;                           // tile bitmap binning: [tiles][bitmap_words(n)], zero between frames
   DevBuf sxy, sco, srgb;                   // with the bitmap: projected Gaussians in depth-rank order
   bool bmp = false;                        // the frame in flight bins through the bitmap
+  bool bmp_dirty = false;                  // a frame set bits whose extraction was not launched
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
   DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
@@ -455,6 +456,7 @@ fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_
   if (bmp_grow) {  // zeroed once here; every frame that sets bits clears them again
     FS4D_CUDA(c, ensure(w.bitmap, bmp_need));
     FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, stream));
+    w.bmp_dirty = false;
     FS4D_CUDA(c, cudaStreamSynchronize(stream));
   }
   return FS4D_OK;
@@ -603,10 +605,13 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
     ea.tile_order = P<uint32_t>(w.tile_order);
     ea.xy = P<float2>(w.xy); ea.conic_opacity = P<float4>(w.co); ea.rgb = P<float>(w.rgb);
     ea.sorted_xy = P<float2>(w.sxy); ea.sorted_co = P<float4>(w.sco); ea.sorted_rgb = P<float>(w.srgb);
+    if (w.bmp_dirty) FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, stream));
+    w.bmp_dirty = true;  // until the extraction (which clears every bit it reads) is launched
     FS4D_CUDA(c, launch_mark_tiles(ea, stream));
     FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), nullptr, 0,
                                   P<uint32_t>(w.tile_order), stream, cap, report ? e.status : nullptr));
     FS4D_CUDA(c, launch_extract_tiles(ea, false, stream));
+    w.bmp_dirty = false;
   } else {
     FS4D_CUDA(c, launch_scan_emit(ea, stream));
     // tile ranges and the pair sort's digit histograms straight from the tile counts
@@ -1257,10 +1262,13 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
     ea.bitmap = P<uint32_t>(w.bitmap);
     ea.words = bitmap_words(n);
     ea.ranges = reinterpret_cast<const uint2*>(d_ranges);
+    if (w.bmp_dirty) FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, c->stream));
+    w.bmp_dirty = true;
     FS4D_CUDA(c, launch_mark_tiles(ea, c->stream));
     FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
                                   reinterpret_cast<uint2*>(d_ranges), nullptr, 0, nullptr, c->stream, capacity));
     FS4D_CUDA(c, launch_extract_tiles(ea, true, c->stream));  // also clears the bitmap when the pairs overflow
+    w.bmp_dirty = false;
   } else {
     FS4D_CUDA(c, launch_scan_emit(ea, c->stream));
     FS4D_CUDA(c, launch_tile_scan(P<uint32_t>(w.tile_count), n_tiles, P<uint32_t>(w.num_pairs),
