@@ -550,7 +550,7 @@ def main():
         "precisions": results,
         "e2e": {"value": e2e_steps * world / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 96,
                 "d2h_bytes_per_step": WIDTH * HEIGHT * 12 + 8,
-                "call": "fs4d_render_host (host camera in, host image out, one stream sync for the pair count)"},
+                "call": "fs4d_render_host (host camera in, host image out, one stream sync per frame)"},
         "gpu_launches": launches_per_frame * (args.steps * len(precs)),
         "clocks": clocks,
     }

@@ -184,7 +184,9 @@ FS4D_API fs4d_status fs4d_render(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision
 
 /* The same frame end to end with HOST buffers: the camera and t go host->device,
  * the image comes back into h_image [height][width][3] (pinned memory is fastest).
- * Returns after the image is on the host. */
+ * One host synchronisation per frame: the pair count comes back with the image, and
+ * a frame whose pairs overflowed the context's capacity is rendered again with the
+ * capacity grown.  Returns after the image is on the host. */
 FS4D_API fs4d_status fs4d_render_host(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam,
                              float t, float* h_image);
 

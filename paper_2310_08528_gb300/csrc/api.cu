@@ -974,6 +974,21 @@ fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec,
     FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
     FS4D_CUDA(c, ensure(img, bytes));
   }
+  // The whole frame is queued at the current pair capacity and the pair count comes
+  // back with the image, so one host synchronisation per frame suffices; a frame
+  // whose pairs overflowed the capacity (its image is incomplete) is rendered again
+  // with the capacity grown.
+  const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
+  if ((st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs)) != FS4D_OK) return st;
+  const long long cap = c->w.cap_pairs;
+  if ((st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, cap, false)) != FS4D_OK) return st;
+  if ((st = frame_back(c, *cam, cap, P<float>(img), nullptr, nullptr)) != FS4D_OK) return st;
+  FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->w.z.num_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaMemcpyAsync(h_image, img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  const long long K = (long long)c->h_pinned[0];
+  c->last_pairs = K;
+  if (K <= cap) return FS4D_OK;
   st = render_sync(c, s, prec, cam, t, P<float>(img), nullptr, nullptr);
   if (st != FS4D_OK) return st;
   FS4D_CUDA(c, cudaMemcpyAsync(h_image, img.p, bytes, cudaMemcpyDeviceToHost, c->stream));

@@ -322,6 +322,22 @@ def test_render_host_equals_device(ctx):
     ctx.unload_scene(sid)
 
 
+def test_render_host_first_frame_regrows_capacity():
+    """A fresh context has no pair capacity: its first host-buffer frame overflows,
+    is rendered again with the capacity grown, and equals the device render."""
+    c = fs4d.Context(0)
+    try:
+        s = sg.make_tiny(8, mlp_std=0.3)
+        cam = sg.tiny_camera(160, 96)
+        sid = c.load_scene(s)
+        b = c.render_host(sid, cam, 0.7)
+        assert c.last_pairs() > 0
+        a = c.render(sid, cam, 0.7).cpu().numpy()
+        assert np.array_equal(a, b)
+    finally:
+        c.close()
+
+
 def test_render_async_and_graph_replay_equal_sync(ctx):
     s = sg.make_tiny(6, mlp_std=0.3)
     cams = [sg.tiny_camera(), sg.hemisphere_cameras(4, width=128, height=128, seed=3)[2]]
