@@ -1,6 +1,8 @@
-// Tile binning: one (tile | depth) key per (Gaussian, touched tile).
+// Tile binning: the per-tile lists of Gaussians in (depth, index) order, from the
+// depth-sorted Gaussians and their tile rectangles, by one of two routes.
 //
-// Gaussians are visited in a given order (the depth-sorted order, so that a
+// Key emission (then a stable radix sort on the tile bits): one (tile | depth) key
+// per (Gaussian, touched tile).  Gaussians are visited in a given order (the depth-sorted order, so that a
 // stable sort on the tile bits alone yields (tile, depth, index) order).  One
 // pass per 256-Gaussian partition:
 //   1. exclusive scan of the tile counts, chained across CTAs by decoupled
@@ -13,6 +15,10 @@
 //      non-empty tile.
 // A one-CTA kernel scans the tile counts into the tile [start, end) ranges and
 // the digit histograms of the pair sort that follows (no pass over the keys).
+//
+// Tile bitmap (no pair sort): one bit per (tile, depth rank), set by mark_kernel;
+// after the same tile scan, extract_kernel reads each tile's row in rank order
+// into the tile's range (see the tile bitmap section below).
 #include "sync_util.cuh"
 
 namespace fs4d {
