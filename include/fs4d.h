@@ -189,6 +189,16 @@ FS4D_API fs4d_status fs4d_render(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision
  * capacity grown.  Returns after the image is on the host. */
 FS4D_API fs4d_status fs4d_render_host(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam,
                              float t, float* h_image);
+/* n frames to HOST images: frame k is (cams[k], ts[k]) into h_images[k] ([height]
+ * [width][3]; every camera of one size; host arrays of n entries).  Frames render
+ * into two device image buffers in turn, and each image's copy to the host overlaps
+ * the next frame's render (pinned destinations keep the copies asynchronous; the
+ * same destination may be given for several frames: they are written in order).
+ * Returns when every image is on the host; frames whose pairs overflowed the
+ * context's capacity are rendered again with the capacity grown. */
+FS4D_API fs4d_status fs4d_render_host_batch(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec,
+                                            const fs4d_camera* cams, const float* ts, int32_t n,
+                                            float* const* h_images);
 
 /* Capacity mode: render without any host synchronisation (so the call can be
  * captured into a CUDA graph).  The tile-pair buffers hold `pair_capacity` pairs;

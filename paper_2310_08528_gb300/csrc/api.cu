@@ -186,6 +186,11 @@ struct fs4d_ctx {
   int last_binning = FS4D_BINNING_SORT;
   bool timing = false;
   cudaEvent_t ev[8] = {};        // deform, project, emit, emit end, sort, ranges, composite, end
+  // fs4d_render_host_batch: image copies overlapped with the next frame
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t slot_rendered[2] = {}, slot_copied[2] = {};
+  unsigned long long* h_pairs = nullptr;  // pinned, [h_pairs_cap]: each frame's pair count
+  int h_pairs_cap = 0;
 };
 
 namespace {
@@ -737,6 +742,15 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     for (int i = 0; i < 8; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->copy_stream) {
+      cudaStreamSynchronize(c->copy_stream);
+      cudaStreamDestroy(c->copy_stream);
+    }
+    for (int i = 0; i < 2; ++i) {
+      if (c->slot_rendered[i]) cudaEventDestroy(c->slot_rendered[i]);
+      if (c->slot_copied[i]) cudaEventDestroy(c->slot_copied[i]);
+    }
+    if (c->h_pairs) cudaFreeHost(c->h_pairs);
   }
   delete c;
   return FS4D_OK;
@@ -993,6 +1007,69 @@ fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec,
   if (st != FS4D_OK) return st;
   FS4D_CUDA(c, cudaMemcpyAsync(h_image, img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
   FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_render_host_batch(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cams,
+                                   const float* ts, int32_t n, float* const* h_images) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (n < 1 || !cams || !ts || !h_images) return fail(c, FS4D_ERR_INVALID_ARG, "render_host_batch: bad argument");
+  for (int k = 0; k < n; ++k)
+    if (!valid_cam(&cams[k]) || !h_images[k] || cams[k].width != cams[0].width || cams[k].height != cams[0].height)
+      return fail(c, FS4D_ERR_INVALID_ARG, "render_host_batch: frames need valid cameras of one size and images");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  const size_t bytes = (size_t)cams[0].width * cams[0].height * 12;
+  DevBuf& img = c->w.host_img;  // two slots: a frame renders into one while the other is copied out
+  if (img.bytes < 2 * bytes || c->h_pairs_cap < n || !c->copy_stream) {
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->copy_stream) FS4D_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+    FS4D_CUDA(c, ensure(img, 2 * bytes));
+    if (c->h_pairs_cap < n) {
+      if (c->h_pairs) cudaFreeHost(c->h_pairs);
+      c->h_pairs = nullptr;
+      c->h_pairs_cap = 0;
+      FS4D_CUDA(c, cudaMallocHost(&c->h_pairs, sizeof(unsigned long long) * (size_t)n));
+      c->h_pairs_cap = n;
+    }
+    if (!c->copy_stream) {
+      FS4D_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      for (int i = 0; i < 2; ++i) {
+        FS4D_CUDA(c, cudaEventCreateWithFlags(&c->slot_rendered[i], cudaEventDisableTiming));
+        FS4D_CUDA(c, cudaEventCreateWithFlags(&c->slot_copied[i], cudaEventDisableTiming));
+      }
+    }
+  }
+  const int n_tiles = tiles_of(cams[0].width) * tiles_of(cams[0].height);
+  if ((st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs)) != FS4D_OK) return st;
+  const long long cap = c->w.cap_pairs;
+  float* slot_img[2] = {P<float>(img), P<float>(img) + bytes / 4};
+  for (int k = 0; k < n; ++k) {
+    const int sl = k & 1;
+    // the slot's previous image (frame k - 2) must be on the host before it is overwritten
+    if (k >= 2) FS4D_CUDA(c, cudaStreamWaitEvent(c->stream, c->slot_copied[sl], 0));
+    if ((st = frame_front(c, s, prec, cams[k], nullptr, nullptr, ts[k], cap, false)) != FS4D_OK) return st;
+    if ((st = frame_back(c, cams[k], cap, slot_img[sl], nullptr, nullptr)) != FS4D_OK) return st;
+    // (the count lives in the frame's zeroed state: read before the next frame clears it)
+    FS4D_CUDA(c, cudaMemcpyAsync(&c->h_pairs[k], c->w.z.num_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
+    FS4D_CUDA(c, cudaEventRecord(c->slot_rendered[sl], c->stream));
+    FS4D_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->slot_rendered[sl], 0));
+    FS4D_CUDA(c, cudaMemcpyAsync(h_images[k], slot_img[sl], bytes, cudaMemcpyDeviceToHost, c->copy_stream));
+    FS4D_CUDA(c, cudaEventRecord(c->slot_copied[sl], c->copy_stream));
+  }
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+  // frames whose pairs overflowed the capacity are rendered again (capacity grown)
+  for (int k = 0; k < n; ++k) {
+    const long long K = (long long)(c->h_pairs[k] & 0xffffffffull);
+    c->last_pairs = K;
+    if (K <= cap) continue;
+    if ((st = render_sync(c, s, prec, &cams[k], ts[k], P<float>(img), nullptr, nullptr)) != FS4D_OK) return st;
+    FS4D_CUDA(c, cudaMemcpyAsync(h_images[k], img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   return FS4D_OK;
 }
 

@@ -23,7 +23,7 @@ STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_E
 # Every symbol include/fs4d.h declares (checked by the tests against the .so).
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
            "fs4d_load_scene", "fs4d_unload_scene", "fs4d_update_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
-           "fs4d_render_host", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
+           "fs4d_render_host", "fs4d_render_host_batch", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_composite")
 STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
@@ -80,6 +80,7 @@ def library(path: str = LIB_PATH):
         "fs4d_deform": [vp, i32, i32, vp, i32, vp, vp, vp],
         "fs4d_render": [vp, i32, i32, C.POINTER(Camera), f32, vp, vp, vp, C.POINTER(vp)],
         "fs4d_render_host": [vp, i32, i32, C.POINTER(Camera), f32, vp],
+        "fs4d_render_host_batch": [vp, i32, i32, C.POINTER(Camera), C.POINTER(f32), i32, C.POINTER(vp)],
         "fs4d_reserve": [vp, i32, i32, i32, i64],
         "fs4d_render_async": [vp, i32, i32, C.POINTER(Camera), vp, vp, vp],
         "fs4d_render_backward": [vp, vp, vp, C.POINTER(Grads)],
@@ -262,6 +263,18 @@ class Context:
         cs = camera_struct(cam)
         self.call("fs4d_render_host", sid, prec, C.byref(cs), float(t), out.ctypes.data)
         return out
+
+    def render_host_batch(self, sid: int, cams, ts, prec: int = FP32, outs=None):
+        """Frames (cams[k], ts[k]) into host images outs[k] (numpy float32 [H][W][3]; the
+        same array may repeat), each copy overlapped with the next frame's render."""
+        n = len(cams)
+        if outs is None:
+            outs = [np.empty((cams[0].height, cams[0].width, 3), np.float32) for _ in range(n)]
+        carr = (Camera * n)(*[camera_struct(cm) for cm in cams])
+        tarr = (C.c_float * n)(*[float(t) for t in ts])
+        parr = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+        self.call("fs4d_render_host_batch", sid, prec, carr, tarr, n, parr)
+        return outs
 
     def reserve(self, sid: int, width: int, height: int, pair_capacity: int) -> None:
         self.call("fs4d_reserve", sid, width, height, int(pair_capacity))

@@ -338,6 +338,31 @@ def test_render_host_first_frame_regrows_capacity():
         c.close()
 
 
+@pytest.mark.parametrize("fresh", [True, False])
+def test_render_host_batch_equals_single_frames(ctx, fresh):
+    """The batched host render (two device image slots, copies overlapped with the
+    next frame) gives each frame's image exactly; on a fresh context the first
+    frames overflow the empty pair capacity and are rendered again."""
+    c = fs4d.Context(0) if fresh else ctx
+    try:
+        s = sg.make_object(9, n=20000)
+        sid = c.load_scene(s)
+        cams = sg.hemisphere_cameras(5, width=200, height=136, seed=4)
+        ts = [0.1, 0.9, 0.3, 0.5, 0.7]
+        for prec in (fs4d.FP32, fs4d.BF16):
+            got = c.render_host_batch(sid, cams, ts, prec)
+            for cam, t, g in zip(cams, ts, got):
+                assert np.array_equal(g, c.render_host(sid, cam, t, prec))
+            # one destination for every frame: the last frame's image
+            one = np.zeros((136, 200, 3), np.float32)
+            c.render_host_batch(sid, cams, ts, prec, [one] * len(cams))
+            assert np.array_equal(one, got[-1])
+        c.unload_scene(sid)
+    finally:
+        if fresh:
+            c.close()
+
+
 def test_render_async_and_graph_replay_equal_sync(ctx):
     s = sg.make_tiny(6, mlp_std=0.3)
     cams = [sg.tiny_camera(), sg.hemisphere_cameras(4, width=128, height=128, seed=3)[2]]
