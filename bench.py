@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=500)
     return ap.parse_args()
 
@@ -268,6 +269,40 @@ def random_camera(rng, w, h):
     r = np.sqrt(1 - z * z)
     eye = (4 * r * np.cos(az), 4 * r * np.sin(az), 4 * z)
     return sg.look_at(eye, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), w, h, 50.0)
+
+
+def training_bench(ctx, fs4d, torch, sid, scene, stream, steps=10, warmup=3):
+    """The backward row: one training view at 800x800 / 100k = a forward that keeps its state
+    (fs4d_render with a saved frame) + fs4d_render_backward of a dense dL/dI into every parameter
+    group, timed with CUDA events on the context's stream (FP32 arithmetic in both)."""
+    try:
+        shapes = {"means": scene.means.shape, "log_scales": scene.log_scales.shape, "quats": scene.quats.shape,
+                  "opacity_logits": scene.opacity_logits.shape, "sh": scene.sh.shape, "planes": scene.planes.shape,
+                  "mlp": scene.mlp.shape}
+        g = {k: torch.zeros(v, device="cuda") for k, v in shapes.items()}
+        dl = torch.randn((HEIGHT, WIDTH, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        fwd, bwd = [], []
+        with torch.cuda.stream(stream):
+            for i in range(warmup + steps):
+                cam, t = views(i, 0, 1)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                _, frame = ctx.render_saved(sid, cam, t, fs4d.FP32)
+                e1.record(stream)
+                ctx.render_backward(frame, dl, g)
+                e2.record(stream)
+                ctx.frame_free(frame)
+                stream.synchronize()
+                if i >= warmup:
+                    fwd.append(e0.elapsed_time(e1))
+                    bwd.append(e1.elapsed_time(e2))
+        f, b = float(np.median(fwd)), float(np.median(bwd))
+        return {"workload": "one view of the 800x800 / 100k object, dL/dI ~ N(0,1), gradients of every parameter "
+                            "group", "steps": steps, "forward_saved_ms": f, "backward_ms": b, "step_ms": f + b,
+                "views_per_s": 1e3 / (f + b),
+                "note": "the forward keeps the backward's state (sort binning, emission offsets, copies)"}
+    except Exception as exc:  # the headline line must still be printed
+        return {"error": f"{type(exc).__name__}: {exc}"}
 
 
 def serving_bench(ctx, fs4d, torch, rates=(500.0, 2000.0), seconds=1.5, precs=("bf16", "fp32")):
@@ -555,6 +590,8 @@ def main():
         "gpu_launches": launches_per_frame * (args.steps * len(precs)),
         "clocks": clocks,
     }
+    if not args.no_training:
+        line["training"] = training_bench(ctx, fs4d, torch, sid, scene, stream)
     if not args.no_serving:
         line["serving"] = serving_bench(ctx, fs4d, torch)
     if world == 1 and not args.no_cpu_baseline:
