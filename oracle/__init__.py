@@ -56,7 +56,9 @@ class OrcGrads(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # FS4D_ORACLE_LIB names another build of fs4d_oracle.cpp; the planted-mistake
+        # test uses it to run the pins against copies of the oracle with one error each.
+        path = os.environ.get("FS4D_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_plane_sample.argtypes = [C.POINTER(OrcScene), C.c_int32, C.c_int32, C.c_double, C.c_double, F64P]

@@ -121,6 +121,79 @@ def test_ewa_covariance_rotated_against_scipy_rotation():
     assert p["radius"][0] == math.ceil(3 * math.sqrt(lam))
 
 
+def _scipy_sigma(quat_wxyz, log_scale):
+    """Sigma = R S S^T R^T (Eq. 2) with R from scipy's rotation of the normalised quaternion."""
+    from scipy.spatial.transform import Rotation
+    q = np.array(quat_wxyz, np.float32).astype(np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy takes (x, y, z, w), normalises
+    S = np.diag(np.exp(np.array(log_scale, np.float32).astype(np.float64)))
+    return R @ S @ S @ R.T
+
+
+def test_ewa_covariance_general_unnormalised_quaternion():
+    """A rotation with all four quaternion components non-zero, stored with norm 1.7
+    (Eq. 6 adds dr to r and the rotation uses r / |r|), against scipy's rotation."""
+    q = tuple(1.7 * v / math.sqrt(0.8 ** 2 + 0.3 ** 2 + 0.4 ** 2 + 0.5 ** 2) for v in (0.8, 0.3, -0.4, 0.5))
+    ls = (-3.1, -2.4, -2.7)
+    s = one_gaussian_scene(log_scale=ls, quat=q)
+    cam = centred_camera()
+    p = oracle.project(s, cam)
+    W = np.asarray(cam.world_to_cam, np.float64)[:3, :3]
+    J = np.array([[cam.fx / 4.0, 0, 0], [0, cam.fy / 4.0, 0]])
+    want = J @ W @ _scipy_sigma(q, ls) @ W.T @ J.T + 0.3 * np.eye(2)
+    assert abs(want[0, 1]) > 0.5
+    assert p["cov2d"][0] == pytest.approx([want[0, 0], want[0, 1], want[1, 1]], rel=1e-9, abs=1e-12)
+    assert p["radius"][0] == math.ceil(3 * math.sqrt(np.linalg.eigvalsh(want).max()))
+
+
+def test_ewa_covariance_off_axis_jacobian():
+    """Off the optical axis the Jacobian of the perspective map (Eq. 3's J) has the
+    third column (-f p_x / p_z^2, -f p_y / p_z^2) at the camera-space mean p."""
+    mean, q, ls = (0.5, 0.3, -0.4), (0.9, -0.2, 0.3, 0.25), (-2.9, -2.3, -3.2)
+    s = one_gaussian_scene(mean=mean, log_scale=ls, quat=q)
+    cam = sg.tiny_camera()
+    out = oracle.project(s, cam)
+    M = np.asarray(cam.world_to_cam, np.float64)
+    W = M[:3, :3]
+    p = W @ np.array(mean, np.float32).astype(np.float64) + M[:3, 3]
+    assert abs(p[0] / p[2]) > 0.1 and abs(p[1] / p[2]) > 0.05  # off axis, inside the guard band
+    J = np.array([[cam.fx / p[2], 0, -cam.fx * p[0] / p[2] ** 2],
+                  [0, cam.fy / p[2], -cam.fy * p[1] / p[2] ** 2]])
+    want = J @ W @ _scipy_sigma(q, ls) @ W.T @ J.T + 0.3 * np.eye(2)
+    assert out["cov2d"][0] == pytest.approx([want[0, 0], want[0, 1], want[1, 1]], rel=1e-9, abs=1e-12)
+    assert out["xy"][0] == pytest.approx([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy],
+                                         rel=1e-12)
+    assert out["depth"][0] == pytest.approx(p[2], rel=1e-12)
+
+
+def test_single_anisotropic_gaussian_image_closed_form():
+    """Eq. 1 with a full 2-D covariance: every pixel is colour * alpha with
+    alpha = min(0.99, o exp(-1/2 d^T Sigma'^-1 d)), d from the projected mean to the
+    pixel centre, and 0 where alpha < 1/255.  With o < 255^-1 e^4.5 nothing beyond
+    the 3-sigma tile rectangle could pass the 1/255 test, so the whole image is fixed."""
+    q, ls, logit = (0.9, 0.1, 0.4, 0.1), (-2.0, -3.2, -3.0), -1.2
+    s = one_gaussian_scene(log_scale=ls, quat=q, logit=logit)
+    cam = centred_camera()
+    img, T, nc, _, _ = oracle.render(s, cam, 0.5, deform=False)
+    W = np.asarray(cam.world_to_cam, np.float64)[:3, :3]
+    J = np.array([[cam.fx / 4.0, 0, 0], [0, cam.fy / 4.0, 0]])
+    cov = J @ W @ _scipy_sigma(q, ls) @ W.T @ J.T + 0.3 * np.eye(2)
+    assert abs(cov[0, 1]) > 0.3 * math.sqrt(cov[0, 0] * cov[1, 1])
+    conic = np.linalg.inv(cov)
+    o = sigmoid(float(np.float32(logit)))
+    assert o * math.exp(-4.5) < 1 / 255
+    ys, xs = np.mgrid[0:128, 0:128]
+    dx, dy = xs + 0.5 - 64.5, ys + 0.5 - 64.5
+    q2 = conic[0, 0] * dx * dx + 2 * conic[0, 1] * dx * dy + conic[1, 1] * dy * dy
+    alpha = np.minimum(0.99, o * np.exp(-0.5 * q2))
+    keep = alpha >= 1 / 255
+    near = np.abs(alpha - 1 / 255) < 1e-9
+    want = np.where(keep, 0.5 * alpha, 0.0)
+    assert keep.sum() > 50
+    assert np.allclose(img[~near, 0], want[~near], rtol=1e-10, atol=1e-14)
+    assert np.array_equal(nc[~near], keep[~near].astype(nc.dtype))
+
+
 def test_projection_of_offaxis_mean_and_rect():
     s = one_gaussian_scene(mean=(0.4, 0.0, -0.2), log_scale=(-3.0,) * 3)
     cam = sg.tiny_camera()
@@ -241,6 +314,41 @@ def test_features_concat_levels_and_time_axis():
         off += rb * ra * h
     assert np.allclose(oracle.features(s3, X, 0.1), oracle.features(s3, X, 0.9), rtol=1e-13)
     assert not np.allclose(oracle.features(s, X, 0.1), oracle.features(s, X, 0.9))
+
+
+def test_features_of_bilinear_planes_closed_form():
+    """Planes filled with bilinear functions of their own two grid coordinates are
+    reproduced exactly by corner-aligned interpolation, so Eq. 5 has a closed form:
+    f_l[c] = prod over the six planes of (k0 + k1 u_a + k2 u_b + k3 u_a u_b) at the
+    normalised coordinates u = 2 (x - box_min) / (box_max - box_min) - 1 and
+    tau = 2 t - 1.  This fixes the axis pair each plane reads (xy xz yz xt yt zt),
+    the box and time normalisation and the level blocks.  Vertex coordinates and
+    coefficients are dyadic, so the float32 plane values hold them exactly."""
+    axes = [(0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3)]
+    s = sg.make_tiny(0, n=8)
+    s.res_spatial, s.res_time, s.feat_dim = (5, 9), 5, 3
+    lo, hi = np.array([0.0, -2.0, 1.0]), np.array([4.0, 2.0, 1.5])
+    s.aabb_min, s.aabb_max = tuple(lo), tuple(hi)
+    rng = np.random.default_rng(11)
+    coef = rng.integers(-3, 4, (2, 6, 4, 3)) / 8.0   # level, plane, (1, u_a, u_b, u_a u_b), channel
+    coef[:, :, 0, :] = rng.integers(6, 11, (2, 6, 3)) / 8.0
+    parts = []
+    for i, (rb, ra, h) in enumerate(sg.plane_shapes(s.res_spatial, s.res_time, s.feat_dim)):
+        c = coef[i // 6, i % 6]
+        ua = np.linspace(-1, 1, ra)[None, :, None]
+        ub = np.linspace(-1, 1, rb)[:, None, None]
+        parts.append((c[0] + c[1] * ua + c[2] * ub + c[3] * ua * ub).astype(np.float32).ravel())
+    s.planes = np.concatenate(parts)
+    X = lo + (hi - lo) * rng.uniform(0.02, 0.98, (40, 3))
+    for t in (0.0, 0.37, 1.0):
+        u = np.concatenate([2 * (X - lo) / (hi - lo) - 1, np.full((len(X), 1), 2 * t - 1)], 1)
+        want = np.ones((len(X), 2, 3))
+        for lvl in range(2):
+            for p, (a, b) in enumerate(axes):
+                c = coef[lvl, p]
+                ua, ub = u[:, a:a + 1], u[:, b:b + 1]
+                want[:, lvl] *= c[0] + c[1] * ua + c[2] * ub + c[3] * ua * ub
+        assert oracle.features(s, X, t) == pytest.approx(want.reshape(len(X), 6), rel=1e-12, abs=1e-14)
 
 
 # --------------------------------------------------------------------- MLP heads (Sec. 4.2)
