@@ -66,6 +66,19 @@ def views(step: int, rank: int, world: int):
     return cams[i % N_CAMS], float(ts[(i // N_CAMS) % N_TIMES])
 
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """The slowest replica's time: every rank renders its own views (weak scaling)
+    and the job ends when the last one does.  `dist` is None on one GPU; with a
+    process group the value is all-reduced (MAX) and the ranks leave together."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -521,12 +534,7 @@ def main():
         else:
             frame_ms, st = measure(ctx, fs4d, torch, sid, pc, args.steps, args.warmup, rank, world, stream, cap)
         torch.cuda.synchronize()
-        total = float(np.sum(frame_ms))
-        if dist:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-            dist.barrier()
+        total = max_over_ranks(dist, float(np.sum(frame_ms)), "cuda")
         results[p] = {"fps": world * args.steps / (total * 1e-3), "ms_per_step": total / args.steps,
                       "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
                       "stages_ms": st}
@@ -546,10 +554,7 @@ def main():
         t0 = time.perf_counter()
         ctx.render_host_batch(sid, e2e_cams, e2e_ts, pc, e2e_outs)
         e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, e2e_s, "cuda")
 
     if rank != 0:
         if dist:
