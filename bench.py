@@ -536,6 +536,7 @@ def main():
         torch.cuda.synchronize()
         total = max_over_ranks(dist, float(np.sum(frame_ms)), "cuda")
         results[p] = {"fps": world * args.steps / (total * 1e-3), "ms_per_step": total / args.steps,
+                      "gaussians_per_s": scene.n * world * args.steps / (total * 1e-3),
                       "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
                       "stages_ms": st}
 
@@ -575,6 +576,7 @@ def main():
             traffic = tr.get("bytes_per_launch")
     line = {
         "metric": METRIC, "value": results[head]["fps"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "gaussians_per_s": results[head]["gaussians_per_s"],
         "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "resolution": [WIDTH, HEIGHT],

@@ -37,3 +37,51 @@ def test_errors_without_gpu_are_reported_not_raised():
     rc = lib.fs4d_create(10_000, None, ctypes.byref(h))
     assert rc == 1 and not h.value
     assert lib.fs4d_destroy(None) == 1
+
+
+def _null_args(fn):
+    out = []
+    for a in fn.argtypes:
+        if a in (ctypes.c_float, ctypes.c_double):
+            out.append(0.0)
+        elif a in (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t):
+            out.append(0)
+        else:
+            out.append(None)
+    return out
+
+
+def test_every_entry_point_rejects_null_handles_without_a_device():
+    """Status codes, not crashes, for null handles and pointers: every call checks
+    its handle before it touches the device (FS4D_ERR_INVALID_ARG = 1)."""
+    from paper_2310_08528_gb300 import build, fs4d
+    build.build()
+    lib = fs4d.library()
+    fs4d._server_sigs(lib)
+    checked = 0
+    for name in declared_symbols():
+        fn = getattr(lib, name)
+        if name in ("fs4d_last_error", "fs4d_sort_pairs_noalloc") or fn.argtypes is None:
+            continue
+        rc = fn(*_null_args(fn))
+        # freeing a null frame is a no-op, like free(NULL)
+        assert rc == (0 if name == "fs4d_frame_free" else 1), name
+        checked += 1
+    assert checked == len(declared_symbols()) - 2
+    assert lib.fs4d_last_error(None) == b"null context"
+
+
+def test_noalloc_sort_checks_sizes_before_any_device_call():
+    """The allocation-free sort rejects bad sizes and returns early for n = 0
+    without touching a device (FS4D_OK = 0, INVALID_ARG = 1, CAPACITY = 3)."""
+    from paper_2310_08528_gb300 import build, fs4d
+    build.build()
+    lib = fs4d.library()
+    f = lib.fs4d_sort_pairs_noalloc
+    assert f(None, 0, 32, None, None) == 0
+    assert f(None, -1, 32, None, None) == 1
+    assert f(None, 10, 0, None, None) == 1
+    assert f(None, 10, 65, None, None) == 1
+    assert f(None, 10, 32, None, None) == 1
+    big = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
+    assert f(None, (1 << 20) + 1, 32, big, big) == 3
