@@ -7,8 +7,8 @@ sphere, SH degree 3, HexPlane spatial {64,128} x temporal 25 x 32 features, MLP
 width 64 -- rendered at 800x800 from 50 hemisphere cameras x 20 timestamps in
 [0,1] (view i = camera i % 50, timestamp (i // 50) % 20).  The scene stays
 resident in HBM; each timed frame uploads its camera and t, then replays one
-captured CUDA graph of deform -> project -> scan/emit -> radix sort -> ranges ->
-composite.  L2 is flushed (a 256 MB device write) before every timed frame, and
+captured CUDA graph of deform -> project -> depth sort -> tile binning (tile
+bitmap: mark, tile scan, extract) -> composite.  L2 is flushed (a 256 MB device write) before every timed frame, and
 the flush is outside the timed interval.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on

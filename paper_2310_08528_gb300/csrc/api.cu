@@ -1,6 +1,8 @@
 // C ABI of libfs4d.so: contexts, resident scenes, work memory and the per-frame
-// launch sequence deform -> project -> scan/emit -> radix sort -> ranges ->
-// composite.  See include/fs4d.h for the contract of every call.
+// launch sequence: deform -> project -> depth sort of the N Gaussians -> tile
+// binning (tile bitmap: mark -> tile scan -> extract; or key emission -> tile
+// scan -> stable pair sort on the tile bits) -> composite.  See include/fs4d.h
+// for the contract of every call.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

@@ -7,8 +7,10 @@
 //    per-digit counts and resolves its global per-digit offsets by decoupled
 //    look-back on its predecessors, then scatters through shared memory so that
 //    runs of equal digits are written contiguously.
-// Only the key bits that can differ are sorted (tile bits + 32 depth bits), so a
-// frame with 2500 tiles sorts 44 bits in 6 passes.
+// Only the key bits that can differ are sorted.  A frame sorts the N float32
+// depths (32 bits in 4 passes; a pass whose digit is the same for every key exits
+// at once) and, on the key-emission route, the pairs on their tile bits only (the
+// pairs are emitted in depth order, so 2500 tiles sort 12 bits in 2 passes).
 #include "sync_util.cuh"
 
 namespace fs4d {
