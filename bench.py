@@ -245,7 +245,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
     scene = sg.make_object(0)
-    for i in range(min(args.warmup, 1)):
+    for i in range(min(args.warmup, 3)):
         cam, t = views(i, 0, 1)
         oracle.render(scene, cam, t)
     budget = 60.0
@@ -261,7 +261,7 @@ def run_reference(args):
     sample = (f"{n} of {args.steps} requested frames (full 800x800 frames; capped at {budget:.0f} s), "
               f"FP64 C++ oracle on {threads} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": n, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+            "steps": n, "warmup": min(args.warmup, 3), "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": threads, "kind": "oracle", "sample": sample},
