@@ -276,6 +276,21 @@ def test_bilinear_matches_scipy_regular_grid():
         assert oracle.plane_sample(s, 0, p, 1.0, -1.0) == pytest.approx(grid[0, ra - 1], abs=0)
 
 
+def test_bilinear_on_2x2_grids_by_hand():
+    """The smallest grid (R = 2 on every axis): the four stored corners weighted by
+    (1-a)(1-b), a(1-b), (1-a)b, ab with a = (u_a+1)/2, b = (u_b+1)/2 (corner-aligned)."""
+    s = sg.make_tiny(9, n=4)
+    s.res_spatial, s.res_time, s.feat_dim = (2,), 2, 4
+    rng = np.random.default_rng(9)
+    s.planes = rng.normal(1.0, 0.3, 6 * 2 * 2 * 4).astype(np.float32)
+    for p in range(6):
+        g = s.planes[16 * p:16 * (p + 1)].reshape(2, 2, 4).astype(np.float64)  # [b][a][h]
+        for ua, ub in ((-1.0, -1.0), (1.0, 1.0), (0.3, -0.6), (-0.9, 0.95), (0.0, 0.0)):
+            a, b = (ua + 1) / 2, (ub + 1) / 2
+            want = (1 - a) * (1 - b) * g[0, 0] + a * (1 - b) * g[0, 1] + (1 - a) * b * g[1, 0] + a * b * g[1, 1]
+            assert oracle.plane_sample(s, 0, p, ua, ub) == pytest.approx(want, rel=1e-14, abs=1e-15)
+
+
 def test_hadamard_of_constant_planes_is_v_to_the_sixth():
     s = sg.make_object(0, n=50, res_spatial=(8, 16), res_time=5, h=8)
     shapes = sg.plane_shapes(s.res_spatial, s.res_time, s.feat_dim)
