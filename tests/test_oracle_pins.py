@@ -166,6 +166,28 @@ def test_ewa_covariance_off_axis_jacobian():
     assert out["depth"][0] == pytest.approx(p[2], rel=1e-12)
 
 
+def test_ewa_jacobian_guard_band():
+    """Far off the optical axis the Jacobian uses p_x/p_z and p_y/p_z clamped to
+    +-1.3 tan(fov/2) (the guard band read from differentiable splatting; the mean
+    itself is not clamped).  The covariance is written even when the rectangle
+    falls outside the image."""
+    mean, q, ls = (3.2, 0.6, -2.9), (0.8, 0.3, -0.1, 0.5), (-2.5, -2.1, -2.8)
+    s = one_gaussian_scene(mean=mean, log_scale=ls, quat=q)
+    cam = sg.tiny_camera()
+    out = oracle.project(s, cam)
+    M = np.asarray(cam.world_to_cam, np.float64)
+    W = M[:3, :3]
+    p = W @ np.array(mean, np.float32).astype(np.float64) + M[:3, 3]
+    lim_x, lim_y = 1.3 * cam.width / (2 * cam.fx), 1.3 * cam.height / (2 * cam.fy)
+    assert abs(p[0] / p[2]) > lim_x and abs(p[1] / p[2]) > lim_y  # both ratios are clamped
+    rx, ry = np.clip(p[0] / p[2], -lim_x, lim_x), np.clip(p[1] / p[2], -lim_y, lim_y)
+    J = np.array([[cam.fx / p[2], 0, -cam.fx * rx / p[2]], [0, cam.fy / p[2], -cam.fy * ry / p[2]]])
+    want = J @ W @ _scipy_sigma(q, ls) @ W.T @ J.T + 0.3 * np.eye(2)
+    assert out["cov2d"][0] == pytest.approx([want[0, 0], want[0, 1], want[1, 1]], rel=1e-9, abs=1e-12)
+    assert out["xy"][0] == pytest.approx([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy],
+                                         rel=1e-12)
+
+
 def test_single_anisotropic_gaussian_image_closed_form():
     """Eq. 1 with a full 2-D covariance: every pixel is colour * alpha with
     alpha = min(0.99, o exp(-1/2 d^T Sigma'^-1 d)), d from the projected mean to the

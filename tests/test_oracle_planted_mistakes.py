@@ -34,6 +34,7 @@ MISTAKES = [
      "v10 = P[((int64_t)(j0 + 1) * Ra + i0) * h + c]", 0),
     ("bilinear weights transposed", "fa * (1 - fb) * v10 + (1 - fa) * fb * v01",
      "(1 - fa) * fb * v10 + fa * (1 - fb) * v01", 0),
+    ("border clamping dropped", "double uc = std::min(1.0, std::max(-1.0, u));", "double uc = u;", 0),
     ("planes summed instead of multiplied", "for (int k = 0; k < h; ++k) f[k] *= v[k];",
      "for (int k = 0; k < h; ++k) f[k] += v[k];", 0),
     # Sec. 4.2: MLP and heads; Eq. 6
@@ -55,6 +56,12 @@ MISTAKES = [
     ("2-sigma radius", "double r3 = 3.0 * std::sqrt(lmax);", "double r3 = 2.0 * std::sqrt(lmax);", 0),
     ("tile rectangle end not exclusive", "x1 = (int)std::floor((u + radius) / tile) + 1;",
      "x1 = (int)std::floor((u + radius) / tile);", 0),
+    ("no guard band on the Jacobian", "const double kGuard = 1.3;", "const double kGuard = 1e9;", 0),
+    ("view direction reversed", "dir[k] = X[k] - campos[k];", "dir[k] = campos[k] - X[k];", 0),
+    ("view direction from the canonical mean", "dir[k] = X[k] - campos[k];",
+     "dir[k] = (double)s->means[3 * (int64_t)g + k] - campos[k];", 0),
+    ("frame deformed at a fixed time", "orc_deform(s, t, X.data(), Q.data(), Sc.data());",
+     "orc_deform(s, 0.5, X.data(), Q.data(), Sc.data());", 0),
     ("opacity sigmoid sign", "1.0 / (1.0 + std::exp(-(double)s->opacity_logits[g]))",
      "1.0 / (1.0 + std::exp((double)s->opacity_logits[g]))", 0),
     ("camera centre sign", "campos[c] = -(Rc[0][c] * tc[0]", "campos[c] = (Rc[0][c] * tc[0]", 0),
