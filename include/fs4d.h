@@ -90,7 +90,9 @@ typedef struct fs4d_scene_desc {
   const float* sh;             /* [n][K][3] real-SH coefficients (degree-major, m = -l..l) */
   float aabb_min[3];           /* box mapped onto the HexPlane grid [-1,1]^3 */
   float aabb_max[3];
-  int32_t n_levels;            /* 1..4 multi-resolution levels */
+  int32_t n_levels;            /* multi-resolution levels: the layout holds up to 4; the
+                                  kernels of this build run 1..3 (4 returns
+                                  FS4D_ERR_UNIMPLEMENTED from fs4d_load_scene) */
   int32_t res_spatial[4];      /* spatial grid resolution per level (>= 2) */
   int32_t res_time;            /* temporal grid resolution (>= 2), the same at every level */
   int32_t feat_dim;            /* h, features per plane: 16 or 32 */
