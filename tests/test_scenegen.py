@@ -29,8 +29,7 @@ def _check_common(s, n, deg, res_spatial, res_time, h, log_scale_mean, mlp_std):
         assert a.dtype == np.float32
     assert tuple(s.res_spatial) == tuple(res_spatial) and s.res_time == res_time and s.feat_dim == h
     assert s.planes.size == sum(int(np.prod(x)) for x in sg.plane_shapes(res_spatial, res_time, h))
-    se = 5.0 / math.sqrt(3 * n)
-    assert abs(s.log_scales.mean() - log_scale_mean) < 0.5 * se * 2 + 0.01
+    assert abs(s.log_scales.mean() - log_scale_mean) < 5 * 0.5 / math.sqrt(3 * n)  # 5 standard errors
     assert abs(s.log_scales.std() - 0.5) < 0.02
     assert np.allclose(np.linalg.norm(s.quats.astype(np.float64), axis=1), 1.0, atol=1e-6)
     assert abs(s.opacity_logits.mean()) < 5.0 / math.sqrt(n) + 0.01 and abs(s.opacity_logits.std() - 1.0) < 0.05
