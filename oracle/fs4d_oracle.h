@@ -26,8 +26,11 @@
  *   orc_*_backward                   chain rule of all of the above (training,
  *                                    Sec. 4.3)
  *
- * Parity pins: see tests/test_oracle_*.py.  Agreement with the paper's trained
- * results is parity unpinned (no trained weights or datasets exist here).
+ * Parity pins: tests/test_oracle_pins.py and tests/test_oracle_backward.py;
+ * tests/test_oracle_planted_mistakes.py builds copies of this oracle with one
+ * plausible mistake each and checks that some pin fails for every one.
+ * Agreement with the paper's trained results is parity unpinned (no trained
+ * weights or datasets exist here).
  */
 #ifndef FS4D_ORACLE_H
 #define FS4D_ORACLE_H
