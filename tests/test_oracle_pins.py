@@ -560,3 +560,19 @@ def test_image_is_convex_combination_bound():
     img, T, *_ = oracle.render(s, sg.tiny_camera(), 0.5)
     p = oracle.project(s, sg.tiny_camera(), *oracle.deform(s, 0.5))
     assert (img <= (1.0 - T)[..., None] * p["rgb"].max(0)[None, None, :] + 1e-12).all()
+
+
+def test_unstable_pixels_flags_threshold_decisions_only():
+    """The pixels a float32 implementation may decide differently are those whose
+    alpha lies within the margin of 1/255 (or T of 1e-4, or a depth tie, or a tile
+    edge); with one Gaussian placed so that a neighbour's alpha is 1/255 to 1e-7,
+    that pixel and no pixel far from every threshold is flagged."""
+    ls, d = -3.0, 3
+    cam = centred_camera()
+    var = (cam.fx * math.exp(float(np.float32(ls))) / 4.0) ** 2 + 0.3
+    o = (1 / 255) * (1 + 1e-7) / math.exp(-0.5 * d * d / var)
+    s = one_gaussian_scene(log_scale=(ls,) * 3, logit=math.log(o / (1 - o)))
+    mask, img, T, nc, _ = oracle.unstable_pixels(s, cam, 0.5, deform=False)
+    assert mask[64, 64 + d] and mask[64 + d, 64]
+    assert not mask[64, 64] and not mask[64, 64 + 1] and not mask[10, 10]
+    assert mask.sum() < 0.01 * mask.size
