@@ -85,3 +85,32 @@ def test_noalloc_sort_checks_sizes_before_any_device_call():
     assert f(None, 10, 32, None, None) == 1
     big = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
     assert f(None, (1 << 20) + 1, 32, big, big) == 3
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes across the boundary has the size, field
+    names and field offsets that a C compiler gives the declaration in
+    include/fs4d.h (compiled here with gcc; no GPU)."""
+    import subprocess
+    from paper_2310_08528_gb300 import fs4d
+    pairs = [("fs4d_scene_desc", fs4d.SceneDesc), ("fs4d_camera", fs4d.Camera), ("fs4d_projected", fs4d.Projected),
+             ("fs4d_grads", fs4d.Grads), ("fs4d_server_config", fs4d.ServerConfig), ("fs4d_request", fs4d.Request),
+             ("fs4d_completion", fs4d.Completion), ("fs4d_server_stats", fs4d.ServerStats)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fs4d.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = ln.split()
+        got[(name, field)] = int(val)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
