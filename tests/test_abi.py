@@ -114,3 +114,31 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_argument_types_match_the_prototypes():
+    """Each ctypes signature in the binding has the prototype's argument count,
+    with a pointer where the header has one and the same integer or float width
+    elsewhere (enums and fs4d_scene_id are 32-bit)."""
+    from paper_2310_08528_gb300 import build, fs4d
+    build.build()
+    lib = fs4d.library()
+    fs4d._server_sigs(lib)
+    src = open(os.path.join(ROOT, "include", "fs4d.h")).read()
+    scalar = {"int32_t": ctypes.c_int32, "int": ctypes.c_int32, "fs4d_scene_id": ctypes.c_int32,
+              "fs4d_precision": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+              "float": ctypes.c_float, "size_t": ctypes.c_size_t}
+    protos = re.findall(r"FS4D_API\s+[\w\s\*]+?\b(fs4d_\w+)\s*\(([^)]*)\)\s*;", src)
+    assert len(protos) == len(declared_symbols())
+    for name, args in protos:
+        fn = getattr(lib, name)
+        decl = [a.strip() for a in " ".join(args.split()).split(",") if a.strip() and a.strip() != "void"]
+        assert fn.argtypes is not None and len(fn.argtypes) == len(decl), name
+        for a, t in zip(decl, fn.argtypes):
+            if "*" in a:
+                assert t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and \
+                    issubclass(t, ctypes._Pointer), (name, a, t)
+            else:
+                base = a.replace("const ", "").split()[0]
+                assert ctypes.sizeof(t) == ctypes.sizeof(scalar[base]), (name, a, t)
+                assert (t in (ctypes.c_float, ctypes.c_double)) == (base == "float"), (name, a, t)
