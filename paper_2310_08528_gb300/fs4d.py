@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libfs4d.so")
 FP32, BF16 = 0, 1
 BINNING_AUTO, BINNING_SORT, BINNING_BITMAP = 0, 1, 2
 STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_ERR_CAPACITY",
-          4: "FS4D_ERR_CUDA", 5: "FS4D_ERR_TIMEOUT", 6: "FS4D_ERR_NOT_FOUND", 7: "FS4D_ERR_UNIMPLEMENTED"}
+          4: "FS4D_ERR_CUDA", 5: "FS4D_ERR_TIMEOUT", 6: "FS4D_ERR_NOT_FOUND", 7: "FS4D_ERR_UNIMPLEMENTED",
+          8: "FS4D_ERR_CANCELLED"}
 
 # Every symbol include/fs4d.h declares (checked by the tests against the .so).
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",

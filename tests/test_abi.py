@@ -142,3 +142,25 @@ def test_binding_argument_types_match_the_prototypes():
                 base = a.replace("const ", "").split()[0]
                 assert ctypes.sizeof(t) == ctypes.sizeof(scalar[base]), (name, a, t)
                 assert (t in (ctypes.c_float, ctypes.c_double)) == (base == "float"), (name, a, t)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, precisions, binning modes and the allocation-free sort's limit
+    as the binding names them are the header's values."""
+    import subprocess
+    from paper_2310_08528_gb300 import fs4d
+    consts = {name: code for code, name in fs4d.STATUS.items()}
+    consts.update({"FS4D_FP32": fs4d.FP32, "FS4D_BF16": fs4d.BF16, "FS4D_BINNING_AUTO": fs4d.BINNING_AUTO,
+                   "FS4D_BINNING_SORT": fs4d.BINNING_SORT, "FS4D_BINNING_BITMAP": fs4d.BINNING_BITMAP})
+    src = tmp_path / "consts.c"
+    body = "\n".join(f'  printf("{k} %lld\\n", (long long){k});' for k in consts)
+    src.write_text(f'#include <stdio.h>\n#include "fs4d.h"\nint main(void) {{\n{body}\n'
+                   f'  printf("FS4D_NOALLOC_MAX_PAIRS %lld\\n", (long long)FS4D_NOALLOC_MAX_PAIRS);\n  return 0;\n}}\n')
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = dict((a, int(b)) for a, b in (ln.split() for ln in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()))
+    for k, v in consts.items():
+        assert got[k] == v, k
+    assert set(fs4d.STATUS) == set(range(9))  # every fs4d_status value has a name in the binding
+    assert got["FS4D_NOALLOC_MAX_PAIRS"] == 1 << 20
