@@ -164,3 +164,16 @@ def test_binding_constants_match_the_header(tmp_path):
         assert got[k] == v, k
     assert set(fs4d.STATUS) == set(range(9))  # every fs4d_status value has a name in the binding
     assert got["FS4D_NOALLOC_MAX_PAIRS"] == 1 << 20
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: with the shared library missing, loading it raises."""
+    import pytest
+    from paper_2310_08528_gb300 import fs4d
+    saved = fs4d._lib
+    fs4d._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="missing"):
+            fs4d.library(str(tmp_path / "libfs4d.so"))
+    finally:
+        fs4d._lib = saved
