@@ -160,7 +160,9 @@ def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, 
         flops = 2 * (64 * 64 + 64 * 64 + 3 * 64 * 64 + 64 * 10) * n   # MLP contraction, 42,240 FLOP/Gaussian
         return [(("tensor" if prec == "bf16" else "alu"), flops, "FLOP"), ("hbm", 80 * n, "B")]
     if stage == "project":
-        return [("hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 12), "B")]
+        # read: mean, quaternion, log-scale, opacity logit, 48 SH floats; written: xy, conic + opacity,
+        # rgb, depth, radius, tile rectangle, depth-sort key and index
+        return [("hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 4 + 4), "B")]
     if stage == "scan_emit":
         # depth sort: 4 passes of 32-bit keys, each reading and writing 8 B key + 4 B value per Gaussian
         if bitmap:
