@@ -74,6 +74,9 @@ def lib():
                                     F64P, F64P, I32P, F64P]
         L.orc_composite_bruteforce.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, I32P, I32P, F64P,
                                                F64P, F64P, F64P, F64P, F64P, F64P]
+        L.orc_pixel_outcomes.argtypes = [C.c_int32, U32P, C.c_double, C.c_double, F64P, F64P, F64P, F64P, F64P,
+                                         C.c_double, C.c_double, C.c_int32, C.c_int32, F64P]
+        L.orc_pixel_outcomes.restype = C.c_int32
         L.orc_render.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.c_double, C.c_int32, C.c_int32,
                                  F64P, F64P, I32P, F64P]
         L.orc_render.restype = C.c_int64
@@ -250,7 +253,43 @@ def unstable_pixels(scene, cam, t: float, deform: bool = True, px_tol: float = 1
         p = project(scene, cam, tile=tile)
     H, W = int(cam.height), int(cam.width)
     ty, tx = (H + tile - 1) // tile, (W + tile - 1) // tile
-    bad_tiles = np.zeros((ty, tx), bool)
+    bad_tiles = np.zeros(ty * tx, bool)
+    bad_tiles[list(uncertain_memberships(p, W, H, px_tol, tile).keys())] = True
+    bad_tiles = bad_tiles.reshape(ty, tx)
+    mask = np.kron(bad_tiles, np.ones((tile, tile), bool))[:H, :W] | (mg < margin_tol)
+    return mask, img, T, nc, K
+
+
+def pixel_outcomes(lst, px: int, py: int, proj, rel_tol: float = 5e-5, depth_tol: float = 1e-6,
+                   max_flip: int = 6):
+    """Every colour pixel (px, py)'s blend over the Gaussian list `lst` can take
+    when its decisions within rounding of their thresholds (alpha vs 1/255, T vs
+    1e-4 within rel_tol relative; blended depths within depth_tol relative) are
+    taken either way: array [m][5] of (colour, final T, last contributor), row 0
+    the blend as computed, or None when more than max_flip decisions are that
+    close."""
+    lst = np.ascontiguousarray(lst, np.uint32)
+    if lst.size == 0:
+        lst = np.zeros(1, np.uint32)
+        n = 0
+    else:
+        n = int(lst.size)
+    max_out = 1 << max_flip
+    out = np.zeros((max_out, 5))
+    m = lib().orc_pixel_outcomes(n, lst, float(px) + 0.5, float(py) + 0.5, proj["xy"], proj["conic"],
+                                 proj["opacity"], proj["rgb"], proj["depth"], float(rel_tol), float(depth_tol),
+                                 int(max_flip), max_out, out.reshape(-1))
+    return None if m < 0 else out[:m]
+
+
+def uncertain_memberships(proj, width: int, height: int, px_tol: float, tile: int = 16):
+    """Tile memberships a float32 projection may decide differently: for every
+    Gaussian whose rectangle or radius decision lies within px_tol pixels of its
+    integer boundary, the tiles inside some but not all of the rectangles its
+    centre (moved by up to px_tol) and its 3-sigma radius (rounded either way)
+    give.  Returns {tile index: [Gaussian indices]}."""
+    ty, tx = (height + tile - 1) // tile, (width + tile - 1) // tile
+    out = {}
 
     def rect_of(u, v, r):
         x0 = min(tx, max(0, int(np.floor((u - r) / tile))))
@@ -259,12 +298,12 @@ def unstable_pixels(scene, cam, t: float, deform: bool = True, px_tol: float = 1
         y1 = min(ty, max(0, int(np.floor((v + r) / tile)) + 1))
         return x0, y0, x1, y1
 
-    for g in np.flatnonzero((p["margin"] < px_tol) & (p["radius"] > 0)):
-        a, b, c = p["cov2d"][g]
+    for g in np.flatnonzero((proj["margin"] < px_tol) & (proj["radius"] > 0)):
+        a, b, c = proj["cov2d"][g]
         mid = 0.5 * (a + c)
         r3 = 3.0 * np.sqrt(mid + np.sqrt(max(0.0, mid * mid - (a * c - b * b))))
         radii = {int(np.ceil(r3 - px_tol)), int(np.ceil(r3 + px_tol))}
-        u0, v0 = p["xy"][g]
+        u0, v0 = proj["xy"][g]
         cover = np.zeros((ty, tx), int)
         n_cand = 0
         for r in radii:
@@ -273,9 +312,9 @@ def unstable_pixels(scene, cam, t: float, deform: bool = True, px_tol: float = 1
                     x0, y0, x1, y1 = rect_of(u0 + du, v0 + dv, r)
                     cover[y0:y1, x0:x1] += 1
                     n_cand += 1
-        bad_tiles |= (cover > 0) & (cover < n_cand)
-    mask = np.kron(bad_tiles, np.ones((tile, tile), bool))[:H, :W] | (mg < margin_tol)
-    return mask, img, T, nc, K
+        for yy, xx in zip(*np.nonzero((cover > 0) & (cover < n_cand))):
+            out.setdefault(int(yy) * tx + int(xx), []).append(int(g))
+    return out
 
 
 def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16):

@@ -409,6 +409,95 @@ void orc_composite(int32_t width, int32_t height, int32_t tile, const uint32_t* 
   }
 }
 
+// The blend of Eq. 4 for ONE pixel over a given list, with chosen decisions
+// taken the other way.  A float32 implementation may legitimately decide a
+// comparison differently from this float64 code when the compared quantities
+// lie within rounding of each other; the outcomes below are every result such
+// an implementation can produce (test support for parity checks, not part of
+// the method).  Decisions of the pass over the list:
+//   skip  -- alpha_i < 1/255 drops term i;
+//   stop  -- T (1 - alpha_i) < 1e-4 ends the blend before term i;
+//   order -- two blended terms whose depths tie to within rounding may swap.
+// flip_kind/flip_gid name the decisions to invert (kind 0 skip, 1 stop, 2 order
+// with the term that follows flip_gid in the list as blended).
+namespace {
+struct Decision { int kind; uint32_t gid; };
+
+// One pass; records the decisions within tolerance when `found` is non-null.
+void blend_pixel(int len, const uint32_t* list, double px, double py, const double* xy, const double* conic,
+                 const double* opacity, const double* rgb, const double* depth, const Decision* flips, int n_flips,
+                 double rel_tol, double depth_tol, double C[5], std::vector<Decision>* found) {
+  std::vector<uint32_t> order(list, list + len);
+  // order flips first: swap the named term with the next term that blends at this pixel
+  auto blends = [&](uint32_t g) {
+    const double dx = xy[2 * g] - px, dy = xy[2 * g + 1] - py;
+    const double power = -0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) - conic[3 * g + 1] * dx * dy;
+    return power <= 0.0 && std::min(kAlphaMax, opacity[g] * std::exp(power)) >= kAlphaMin;
+  };
+  for (int f = 0; f < n_flips; ++f) {
+    if (flips[f].kind != 2) continue;
+    for (int k = 0; k < len; ++k) {
+      if (order[k] != flips[f].gid) continue;
+      for (int j = k + 1; j < len; ++j)
+        if (blends(order[j])) { std::swap(order[k], order[j]); break; }
+      break;
+    }
+  }
+  auto flipped = [&](int kind, uint32_t g) {
+    for (int f = 0; f < n_flips; ++f)
+      if (flips[f].kind == kind && flips[f].gid == g) return true;
+    return false;
+  };
+  double T = 1.0, prev_depth = -1.0;
+  uint32_t prev = 0;
+  int last = 0;
+  C[0] = C[1] = C[2] = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const uint32_t g = order[k];
+    const double dx = xy[2 * g] - px, dy = xy[2 * g + 1] - py;
+    const double power = -0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) - conic[3 * g + 1] * dx * dy;
+    if (power > 0.0) continue;
+    const double alpha = std::min(kAlphaMax, opacity[g] * std::exp(power));
+    if (found && std::fabs(alpha - kAlphaMin) / kAlphaMin < rel_tol) found->push_back({0, g});
+    if ((alpha < kAlphaMin) != flipped(0, g)) continue;
+    if (found && prev_depth > 0.0 && std::fabs(depth[g] - prev_depth) / std::fabs(depth[g]) < depth_tol)
+      found->push_back({2, prev});
+    prev_depth = depth[g];
+    prev = g;
+    const double Tn = T * (1.0 - alpha);
+    if (found && std::fabs(Tn - kTMin) / kTMin < rel_tol) found->push_back({1, g});
+    if ((Tn < kTMin) != flipped(1, g)) break;
+    for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * alpha * T;
+    T = Tn;
+    last = k + 1;
+  }
+  C[3] = T;
+  C[4] = last;
+}
+}  // namespace
+
+int32_t orc_pixel_outcomes(int32_t len, const uint32_t* list, double px, double py, const double* xy,
+                           const double* conic, const double* opacity, const double* rgb, const double* depth,
+                           double rel_tol, double depth_tol, int32_t max_flip, int32_t max_out, double* out) {
+  std::vector<Decision> found;
+  double C[5];
+  blend_pixel(len, list, px, py, xy, conic, opacity, rgb, depth, nullptr, 0, rel_tol, depth_tol, C, &found);
+  if (max_out < 1) return -1;
+  for (int ch = 0; ch < 5; ++ch) out[ch] = C[ch];
+  const int m = (int)found.size();
+  if (m > max_flip || (1 << m) > max_out) return -1;
+  std::vector<Decision> sel;
+  for (int mask = 1; mask < (1 << m); ++mask) {
+    sel.clear();
+    for (int b = 0; b < m; ++b)
+      if (mask & (1 << b)) sel.push_back(found[b]);
+    blend_pixel(len, list, px, py, xy, conic, opacity, rgb, depth, sel.data(), (int)sel.size(), rel_tol,
+                depth_tol, C, nullptr);
+    for (int ch = 0; ch < 5; ++ch) out[5 * mask + ch] = C[ch];
+  }
+  return 1 << m;
+}
+
 // The same blend without tiling: every pixel walks all visible Gaussians in
 // (float32 depth, index) order and keeps those whose tile rectangle holds the
 // pixel's tile.

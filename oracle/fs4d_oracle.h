@@ -23,6 +23,8 @@
  *                                    (front-to-back alpha blending)
  *   orc_composite_bruteforce         the same blend as a per-pixel loop over all
  *                                    Gaussians (no tiling), used as a pin
+ *   orc_pixel_outcomes               Eq. 4 for one pixel with its near-threshold
+ *                                    decisions taken either way (parity support)
  *   orc_*_backward                   chain rule of all of the above (training,
  *                                    Sec. 4.3)
  *
@@ -96,6 +98,16 @@ void orc_composite_bruteforce(int32_t n, int32_t width, int32_t height, int32_t 
                               const int32_t* rect, const double* xy, const double* conic,
                               const double* opacity, const double* rgb, const double* depth,
                               double* image, double* t_final);
+/* Test support (not part of the method): every colour one pixel's blend over
+ * `list` can take when its discrete decisions within rounding of their thresholds
+ * (alpha vs 1/255 and T vs 1e-4 within rel_tol relative, blended depths within
+ * depth_tol relative) are taken either way.  Each outcome is 5 doubles: colour
+ * (3), final transmittance, 1 + list position of the last blended term; out[0..4]
+ * is the blend as computed.  Returns the number of outcomes (2^m for m such
+ * decisions), or -1 when m > max_flip or 2^m > max_out. */
+int32_t orc_pixel_outcomes(int32_t len, const uint32_t* list, double px, double py, const double* xy,
+                           const double* conic, const double* opacity, const double* rgb, const double* depth,
+                           double rel_tol, double depth_tol, int32_t max_flip, int32_t max_out, double* out);
 int64_t orc_render(const orc_scene* s, const orc_camera* cam, double t, int32_t deform, int32_t tile,
                    double* image, double* t_final, int32_t* n_contrib, double* margin);
 

@@ -576,3 +576,78 @@ def test_unstable_pixels_flags_threshold_decisions_only():
     assert mask[64, 64 + d] and mask[64 + d, 64]
     assert not mask[64, 64] and not mask[64, 64 + 1] and not mask[10, 10]
     assert mask.sum() < 0.01 * mask.size
+
+
+# --------------------------------------------------------------------- per-pixel outcomes (parity support)
+
+def _proj(rows):
+    """Projected Gaussians (u, v, conic a, b, c, opacity, rgb, depth) as the oracle's dict."""
+    r = np.array(rows, np.float64)
+    return dict(xy=np.ascontiguousarray(r[:, 0:2]), conic=np.ascontiguousarray(r[:, 2:5]),
+                opacity=np.ascontiguousarray(r[:, 5]), rgb=np.ascontiguousarray(r[:, 6:9]),
+                depth=np.ascontiguousarray(r[:, 9]))
+
+
+def test_pixel_outcomes_single_term_closed_form():
+    """One Gaussian centred on the pixel, far from every threshold: the only
+    outcome is colour * min(0.99, o), T = 1 - alpha, one contributor (Eq. 4)."""
+    p = _proj([(10.5, 7.5, 0.2, 0.0, 0.2, 0.6, 0.3, 0.5, 0.9, 2.0)])
+    out = oracle.pixel_outcomes([0], 10, 7, p)
+    assert out.shape == (1, 5)
+    np.testing.assert_allclose(out[0, :3], 0.6 * np.array([0.3, 0.5, 0.9]), rtol=0, atol=1e-15)
+    assert out[0, 3] == pytest.approx(0.4, abs=1e-15) and out[0, 4] == 1
+
+
+def test_pixel_outcomes_alpha_at_skip_threshold_both_ways():
+    """alpha = (1/255)(1 + 1e-7): the term is blended, and the outcome with it
+    skipped (black, T = 1, no contributor) is listed too."""
+    d = 2.0
+    a = (1 / 255) * (1 + 1e-7)
+    o = a / math.exp(-0.5 * 0.5 * d * d)
+    p = _proj([(10.5 + d, 7.5, 0.5, 0.0, 0.5, o, 1.0, 0.2, 0.4, 2.0)])
+    out = oracle.pixel_outcomes([0], 10, 7, p)
+    assert out.shape == (2, 5)
+    np.testing.assert_allclose(out[0, :3], a * np.array([1.0, 0.2, 0.4]), rtol=1e-12)
+    assert out[0, 4] == 1 and out[0, 3] == pytest.approx(1 - a, rel=1e-12)
+    np.testing.assert_array_equal(out[1], [0, 0, 0, 1, 0])
+    # far from the threshold: one outcome only
+    assert oracle.pixel_outcomes([0], 10, 7, _proj([(10.5 + d, 7.5, 0.5, 0.0, 0.5, 10 * o, 1, 1, 1, 2.0)])
+                                 ).shape == (1, 5)
+
+
+def test_pixel_outcomes_depth_tie_both_orders():
+    """Two blended terms at equal depth: both front-to-back orders are outcomes,
+    c1 a1 + c2 a2 (1 - a1) and c2 a2 + c1 a1 (1 - a2)."""
+    a1, a2 = 0.5, 0.3
+    c1, c2 = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    p = _proj([(3.5, 3.5, 0.1, 0.0, 0.1, a1, *c1, 5.0), (3.5, 3.5, 0.1, 0.0, 0.1, a2, *c2, 5.0)])
+    out = oracle.pixel_outcomes([0, 1], 3, 3, p)
+    assert out.shape == (2, 5)
+    np.testing.assert_allclose(out[0, :3], c1 * a1 + c2 * a2 * (1 - a1), atol=1e-15)
+    np.testing.assert_allclose(out[1, :3], c2 * a2 + c1 * a1 * (1 - a2), atol=1e-15)
+    assert out[0, 3] == pytest.approx(out[1, 3], abs=1e-15)  # T does not depend on the order
+    # well-separated depths: one order only
+    p2 = _proj([(3.5, 3.5, 0.1, 0.0, 0.1, a1, *c1, 5.0), (3.5, 3.5, 0.1, 0.0, 0.1, a2, *c2, 5.1)])
+    assert oracle.pixel_outcomes([0, 1], 3, 3, p2).shape == (1, 5)
+
+
+def test_pixel_outcomes_transmittance_stop_both_ways():
+    """T after two terms is 1e-4 (1 + 1e-6): the second term is blended; the
+    outcome that stops before it (the stop rule of Eq. 4's reading) is listed too."""
+    a1 = 0.99
+    a2 = 1.0 - 1e-2 * (1 + 1e-6)
+    c1, c2 = np.array([0.2, 0.4, 0.6]), np.array([1.0, 1.0, 1.0])
+    p = _proj([(0.5, 0.5, 0.1, 0.0, 0.1, 1.0, *c1, 1.0), (0.5, 0.5, 0.1, 0.0, 0.1, a2, *c2, 2.0)])
+    out = oracle.pixel_outcomes([0, 1], 0, 0, p)
+    assert out.shape == (2, 5)
+    np.testing.assert_allclose(out[0, :3], c1 * a1 + c2 * a2 * (1 - a1), rtol=1e-12)
+    assert out[0, 4] == 2
+    np.testing.assert_allclose(out[1, :3], c1 * a1, rtol=1e-12)
+    assert out[1, 4] == 1 and out[1, 3] == pytest.approx(1 - a1, rel=1e-12)
+
+
+def test_pixel_outcomes_limit_on_flips():
+    """More near-threshold decisions than max_flip: not enumerated (None)."""
+    rows = [(0.5, 0.5, 0.1, 0.0, 0.1, 0.2, 1, 1, 1, 3.0)] * 4
+    assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=2) is None
+    assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=3).shape == (8, 5)
