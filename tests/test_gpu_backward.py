@@ -1,9 +1,15 @@
 """GPU backward (fs4d_render_backward, through the C ABI) against the FP64
 oracle's analytic gradient and against FP64 central finite differences.
 
-Bar: per parameter group, max |g_gpu - g_ref| <= 1e-3 * max |g_ref|.  Pixels
-whose forward contains a discrete decision within float32 rounding of its
-threshold (oracle.unstable_pixels) get dL/dI = 0, since the gradient is not
+Bar, element by element: |g_gpu - g_ref| <= 1e-3 |g_ref| + 1e-5 max |g_ref| of
+the parameter group, and 1e-3 relative for every element above 1% of the
+group's largest.  The floor covers elements that are float32 sums of up to ~1e4
+per-pixel terms of either sign cancelling to near zero: their rounding error
+(~sqrt(n) 2^-24 of the terms' absolute sum, and the float32 forward values'
+~1e-6 relative error times that sum) is relative to the terms, not to the sum;
+it is also the bound on the GPU's own run-to-run variation (summation order).
+Pixels whose forward contains a discrete decision within float32 rounding of
+its threshold (oracle.unstable_pixels) get dL/dI = 0, since the gradient is not
 defined across such a decision.
 """
 import numpy as np
@@ -67,13 +73,23 @@ def masked_dl(s, cam, t, seed):
     return dl
 
 
-def check_groups(g, ref, rel=REL):
+def check_groups(g, ref, rel=REL, floor=1e-5):
+    """Element-wise: |g - ref| <= rel |ref| + floor max|ref| per parameter group,
+    and |g - ref| <= rel |ref| where |ref| > 1% of the group's max."""
+    worst = {}
     for k in GROUPS:
         scale = np.abs(ref[k]).max()
         assert scale > 0, k
-        err = np.abs(g[k] - ref[k]).max()
-        print(f"{k:15s} max|ref| {scale:.3e}  max err {err:.3e}  rel {err / scale:.2e}")
-        assert err <= rel * scale, (k, err, scale)
+        err = np.abs(g[k] - ref[k])
+        bound = rel * np.abs(ref[k]) + floor * scale
+        big = np.abs(ref[k]) > 1e-2 * scale
+        worst_rel = float((err[big] / np.abs(ref[k][big])).max())
+        worst[k] = worst_rel
+        print(f"{k:15s} max|ref| {scale:.3e}  max err/bound {float((err / bound).max()):.3f}  "
+              f"worst rel (|ref| > 1% of max) {worst_rel:.2e}")
+        assert (err <= bound).all(), (k, float((err / bound).max()))
+        assert worst_rel <= rel, (k, worst_rel)
+    return worst
 
 
 @pytest.mark.parametrize("seed,deg", [(0, 0), (1, 3), (4, 0)])
@@ -97,30 +113,46 @@ def test_backward_matches_oracle_tiny_scene(ctx):
 
 
 def test_backward_matches_central_differences(ctx):
-    """GPU gradient against FP64 central differences of the oracle forward."""
+    """GPU gradient against FP64 central differences of the oracle forward.  A
+    sample counts where the loss is smooth over [x - h, x + h]: its central
+    differences at h and h/2 agree to 1e-4 (no decision flips in between); every
+    such sample must pass, and every group must have at least four."""
     s = small_scene(2, deg=3)
     cam = small_camera()
     t = 0.6
     dl = masked_dl(s, cam, t, 2)
     _, g = gpu_grads(ctx, s, cam, t, dl)
-    h = 2.0 ** -13
+    h = 2.0 ** -12
     rng = np.random.default_rng(5)
-    n_ok = n_all = 0
+
+    def loss():
+        return float(np.sum(oracle.render(s, cam, t)[0] * dl))
+
+    def central(flat, i, step):
+        x0 = flat[i]
+        flat[i] = np.float32(x0 + step)
+        lp = loss()
+        flat[i] = np.float32(x0 - step)
+        lm = loss()
+        flat[i] = x0
+        return (lp - lm) / (np.float64(np.float32(x0 + step)) - np.float64(np.float32(x0 - step)))
+
     for k in GROUPS:
         flat = getattr(s, k).reshape(-1)
         gk = g[k].reshape(-1)
         idx = np.flatnonzero(np.abs(gk) > 1e-3 * np.abs(gk).max())
-        for i in rng.choice(idx, size=min(8, len(idx)), replace=False):
-            x0 = flat[i]
-            flat[i] = np.float32(x0 + h)
-            lp = float(np.sum(oracle.render(s, cam, t)[0] * dl))
-            flat[i] = np.float32(x0 - h)
-            lm = float(np.sum(oracle.render(s, cam, t)[0] * dl))
-            flat[i] = x0
-            fd = (lp - lm) / (2 * h)
-            n_all += 1
-            n_ok += abs(fd - gk[i]) <= REL * max(abs(fd), abs(gk[i])) + 1e-6 * np.abs(gk).max()
-    assert n_ok >= 0.95 * n_all, (n_ok, n_all)
+        checked = 0
+        for i in rng.permutation(idx)[:24]:
+            fd = central(flat, i, h)
+            fd2 = central(flat, i, h / 2)
+            if abs(fd - fd2) > 1e-4 * max(abs(fd), abs(fd2)) + 1e-9 * np.abs(gk).max():
+                continue  # a decision flips inside [x - h, x + h]: no derivative to compare
+            assert abs(fd2 - gk[i]) <= REL * abs(fd2) + 1e-6 * np.abs(gk).max(), (k, int(i), fd2, gk[i])
+            checked += 1
+            if checked == 8:
+                break
+        print(f"{k}: {checked} central-difference samples")
+        assert checked >= 4, k
 
 
 def test_autograd_function_matches_direct_call(ctx):
@@ -140,6 +172,34 @@ def test_autograd_function_matches_direct_call(ctx):
     img2 = fs4d.render_differentiable(ctx, sid, cam, 0.3, params)
     assert float(img2.detach().sum()) < float(img.detach().sum())
     ctx.unload_scene(sid)
+
+
+def test_backward_matches_oracle_object_256(ctx):
+    """20k Gaussians (SH 3, two HexPlane levels) at 256x256: many Gaussians per
+    tile and tiles per Gaussian, plane cells shared by many Gaussians."""
+    s = sg.make_object(5, n=20000, mlp_std=0.05)
+    cam = sg.hemisphere_cameras(4, width=256, height=256, seed=1)[2]
+    oracle.set_threads(oracle.default_threads())
+    rng = np.random.default_rng(11)
+    dl = rng.normal(size=(256, 256, 3))
+    dl[oracle.unstable_pixels(s, cam, 0.4, px_tol=5e-4, margin_tol=5e-5)[0]] = 0.0
+    _, g = gpu_grads(ctx, s, cam, 0.4, dl)
+    ref = oracle.render_backward(s, cam, 0.4, dl)
+    check_groups(g, ref)
+
+
+def test_backward_matches_oracle_object_800(ctx):
+    """The full-size training view: 100k Gaussians at 800x800 (the bench's
+    backward workload), every element of every gradient group."""
+    s = sg.make_object(0)
+    cam = sg.hemisphere_cameras(50, seed=0)[7]
+    oracle.set_threads(oracle.default_threads())
+    rng = np.random.default_rng(12)
+    dl = rng.normal(size=(800, 800, 3))
+    dl[oracle.unstable_pixels(s, cam, 0.35, px_tol=2e-4, margin_tol=5e-5)[0]] = 0.0
+    _, g = gpu_grads(ctx, s, cam, 0.35, dl)
+    ref = oracle.render_backward(s, cam, 0.35, dl)
+    check_groups(g, ref)
 
 
 def test_backward_repeatable(ctx):

@@ -1,15 +1,18 @@
 """GPU parity of the forward render path against the FP64 oracle, through the C ABI.
 
-Tolerances (float32 path): deformed Gaussians within 1e-5 absolute; projection
-outputs within 1e-5 relative; tile keys, sorted values and ranges bit-exact on
-identical inputs; images within 1e-4 max-abs per channel, except pixels where
-the oracle records a threshold decision (alpha vs 1/255, T vs 1e-4, a depth tie)
-within float32 rounding of its boundary, which are counted and bounded.
+Tolerances (float32 path): deformed Gaussians within 2e-5 of their scale;
+projection outputs within 1e-5 relative; tile keys, sorted values and ranges
+bit-exact on identical inputs; every pixel of a frame within 1e-4 max-abs per
+channel of the oracle's frame, or of one of the outcomes the oracle enumerates
+for that pixel when one of its decisions (alpha vs 1/255, T vs 1e-4, a depth
+tie, a tile-rectangle edge) lies within float32 rounding of its threshold.  No
+pixel is excluded; the pixels that took another outcome are counted.
 """
 import numpy as np
 import pytest
 
 import oracle
+import parity
 from paper_2310_08528_gb300 import scenegen as sg
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +24,6 @@ if not torch.cuda.is_available():
 from paper_2310_08528_gb300 import fs4d  # noqa: E402
 
 IMG_TOL = 1e-4
-MARGIN = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -247,35 +249,54 @@ def test_composite_matches_oracle_on_same_inputs(ctx, seed):
                                dev(p32["xy"].astype(np.float32)), dev(co.astype(np.float32)),
                                dev(p32["rgb"].astype(np.float32)))
     torch.cuda.synchronize()
-    ok = mg >= MARGIN
-    assert ok.mean() > 0.99
-    assert np.abs(img.cpu().numpy() - img_o)[ok].max() <= 1e-5
-    assert np.abs(T.cpu().numpy() - T_o)[ok].max() <= 1e-5
-    assert np.array_equal(nc.cpu().numpy()[ok], nc_o[ok])
+    fr = dict(img=img_o, T=T_o, nc=nc_o, margin=mg, proj=p32, values=vals, ranges=ranges,
+              dbits=oracle.depth_bits(p32["depth"]), tx=9, tile=16)
+    # same float32 inputs: only the blend's own rounding can flip a decision
+    st = parity.check_frame(img.cpu().numpy(), fr, T.cpu().numpy(), nc.cpu().numpy(), tol=1e-5, rel_tol=1e-5,
+                            px_tol=0.0)
+    assert st["unresolved"] == 0 and st["other_outcome"] == 0
 
 
 # ------------------------------------------------------------------ full frame
 
-def _frame_check(img, want, unstable, tol=IMG_TOL, max_flagged=0.08):
-    ok = ~unstable
-    assert (1 - ok.mean()) <= max_flagged
-    err = np.abs(img - want)[ok]
-    assert err.max() <= tol, err.max()
-    return err.max()
+def _gpu_rects(ctx, sid, s, cam, t):
+    """The GPU's own tile rectangles and radii of the frame at t: fs4d_deform (FP32)
+    then fs4d_project, the kernels the frame runs on the same inputs."""
+    m, q, ls = ctx.deform(sid, [t], fs4d.FP32)
+    p = ctx.project(m[0], q[0], ls[0], dev(s.opacity_logits), dev(s.sh), s.sh_degree, cam)
+    torch.cuda.synchronize()
+    return p["rect"].cpu().numpy(), p["radius"].cpu().numpy()
+
+
+def _rect_decisions(ctx, sid, s, cam, t, fr, px_tol):
+    """Every tile rectangle the GPU decides differently from the oracle must be a
+    decision within px_tol of its boundary in the oracle; the frame's pair count
+    is the sum of the GPU rectangles' areas.  Returns the number that differ."""
+    rect, radius = _gpu_rects(ctx, sid, s, cam, t)
+    ro = fr["proj"]["rect"]
+    diff = np.any(rect != ro, axis=1)
+    assert (fr["proj"]["margin"][diff] < px_tol).all()
+    area = (np.maximum(rect[:, 2] - rect[:, 0], 0) * np.maximum(rect[:, 3] - rect[:, 1], 0)).sum()
+    assert int(area) == ctx.last_pairs()
+    print(f"tile rectangles decided differently: {int(diff.sum())} of {s.n}")
+    return int(diff.sum())
 
 
 @pytest.mark.parametrize("seed,std", [(0, 0.1), (1, 0.1), (2, 0.05), (3, 0.02)])
 def test_render_fp32_tiny_matches_oracle(ctx, seed, std):
+    """Every pixel, its final transmittance and its last contributor against the
+    oracle (1e-4); at these seeds the GPU takes every decision as the oracle does."""
     s = sg.make_tiny(seed, mlp_std=std)
     cam = sg.tiny_camera()
     sid = ctx.load_scene(s)
     img, T, nc = ctx.render(sid, cam, 0.5, fs4d.FP32, with_aux=True)
     torch.cuda.synchronize()
-    unstable, want, T_o, nc_o, K = oracle.unstable_pixels(s, cam, 0.5)
-    _frame_check(img.cpu().numpy(), want, unstable)
-    ok = ~unstable
-    assert np.abs(T.cpu().numpy() - T_o)[ok].max() <= IMG_TOL
-    assert np.array_equal(nc.cpu().numpy()[ok], nc_o[ok])
+    fr = parity.oracle_frame(s, cam, 0.5)
+    st = parity.check_frame(img.cpu().numpy(), fr, T.cpu().numpy(), nc.cpu().numpy(), tol=IMG_TOL,
+                            px_tol=1e-3)
+    assert st["unresolved"] == 0
+    assert st["other_outcome"] == 0
+    assert _rect_decisions(ctx, sid, s, cam, 0.5, fr, 1e-3) == 0
     ctx.unload_scene(sid)
 
 
@@ -291,24 +312,31 @@ def test_render_static_special_case(ctx):
     cam = sg.tiny_camera()
     sid = ctx.load_scene(s)
     img = ctx.render(sid, cam, 0.9, fs4d.FP32).cpu().numpy()
-    unstable, want, _, _, _ = oracle.unstable_pixels(s, cam, 0.9, deform=False)
-    _frame_check(img, want, unstable)
+    st = parity.check_frame(img, parity.oracle_frame(s, cam, 0.9, deform=False), tol=IMG_TOL, px_tol=1e-3)
+    assert st["unresolved"] == 0 and st["other_outcome"] == 0
     ctx.unload_scene(sid)
 
 
-def test_render_object_800_matches_oracle(ctx):
-    """The 100k-Gaussian 800x800 object frame, every pixel against the oracle."""
+@pytest.mark.parametrize("ci,t", [(7, 0.35), (31, 0.9)])
+def test_render_object_800_matches_oracle(ctx, ci, t):
+    """The 100k-Gaussian 800x800 object frame, every pixel against the oracle.
+    At 800 px one float32 ulp of a pixel coordinate is 6e-5 px, which moves alpha
+    by up to ~|grad power| * 6e-5 ~ 3e-5 relative: decisions within 5e-5 of their
+    threshold, and tile rectangles within 2e-4 px of an integer boundary, may go
+    either way; such a pixel must equal one of the oracle's outcomes for it."""
     s = sg.make_object(0)
-    cam = sg.hemisphere_cameras(50, seed=0)[7]
+    cam = sg.hemisphere_cameras(50, seed=0)[ci]
     sid = ctx.load_scene(s)
-    img = ctx.render(sid, cam, 0.35, fs4d.FP32).cpu().numpy()
+    img = ctx.render(sid, cam, t, fs4d.FP32).cpu().numpy()
     oracle.set_threads(oracle.default_threads())
-    # at 800 px one float32 ulp of a pixel coordinate is 6e-5 px, which moves
-    # alpha by up to ~|grad power| * 6e-5 ~ 3e-5 relative: blend decisions within
-    # 5e-5 of their threshold are resolution-limited, not errors
-    unstable, want, _, _, K = oracle.unstable_pixels(s, cam, 0.35, px_tol=2e-4, margin_tol=5e-5)
-    assert abs(ctx.last_pairs() - K) <= 1e-4 * K
-    _frame_check(img, want, unstable)
+    fr = parity.oracle_frame(s, cam, t)
+    K_gpu = ctx.last_pairs()
+    st = parity.check_frame(img, fr, tol=IMG_TOL, rel_tol=5e-5, px_tol=2e-4)
+    assert st["unresolved"] == 0
+    assert st["other_outcome_frac"] <= 5e-3
+    assert abs(K_gpu - fr["K"]) <= 1e-4 * fr["K"]
+    n_diff = _rect_decisions(ctx, sid, s, cam, t, fr, 2e-4)
+    assert n_diff <= 1e-3 * s.n
     ctx.unload_scene(sid)
 
 
