@@ -147,8 +147,16 @@ FS4D_API const char* fs4d_last_error(const fs4d_ctx* ctx);
 FS4D_API fs4d_status fs4d_set_stream(fs4d_ctx* ctx, void* cuda_stream);
 /* Read and clear the device status word (bounded waits that timed out, pair
  * capacity overflow in capacity mode).  Synchronises the context's stream.
- * Returns FS4D_OK, FS4D_ERR_TIMEOUT or FS4D_ERR_CAPACITY. */
+ * Returns FS4D_OK, FS4D_ERR_TIMEOUT or FS4D_ERR_CAPACITY.  A frame in which a
+ * wait timed out has an unreliable image; the context stays usable and the next
+ * frame is computed afresh. */
 FS4D_API fs4d_status fs4d_check_device_status(fs4d_ctx* ctx);
+/* Polls a look-back wait (radix sort, key emission) of this context's later
+ * launches makes before it gives up and sets the timeout bit of the status word;
+ * 0 restores the default (2^22 polls of ~100 ns).  A diagnostic for exercising
+ * the timeout path: a small limit makes waits give up while their predecessors
+ * are still running, so results are wrong but every access stays in bounds. */
+FS4D_API fs4d_status fs4d_set_wait_limit(fs4d_ctx* ctx, uint32_t polls);
 
 /* ---------------------------------------------------------------- scenes */
 
@@ -176,7 +184,8 @@ FS4D_API fs4d_status fs4d_scene_bytes(fs4d_ctx* ctx, fs4d_scene_id id, int32_t w
 FS4D_API fs4d_status fs4d_deform(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const float* h_ts, int32_t n_t,
                         float* d_means, float* d_quats, float* d_log_scales);
 
-/* Render one frame: deform at t, project, bin, sort, composite.  d_image:
+/* Render one frame, I = S(M, G') with G' = G + F(G, t) (Sec. 4.1): deform at t
+ * (Eq. 5, Eq. 6), project (Eq. 2, Eq. 3), bin, sort, composite (Eq. 1, Eq. 4).  d_image:
  * device [height][width][3]; d_t_final [height][width] and d_n_contrib
  * [height][width] may be NULL.  If `saved` is non-NULL, *saved receives the
  * forward state needed by fs4d_render_backward (free it with fs4d_frame_free).
@@ -343,10 +352,21 @@ FS4D_API fs4d_status fs4d_sort_pairs(fs4d_ctx* ctx, int64_t n, int32_t key_bits,
  *  - All calls on a device share the one work area (it keeps the last call's
  *    contents; every call clears what must start at zero).  Calls whose work
  *    overlaps on the GPU race with each other: serialise them (one stream, or
- *    events between streams). */
+ *    events between streams).
+ *  - The device address of the work area is cached per device for the life of
+ *    the process: do not call it again on a device after cudaDeviceReset.
+ *  - The sort's look-back waits are bounded; a wait that gives up sets a status
+ *    word instead of hanging, and the call still returns FS4D_OK (it does not
+ *    synchronise).  fs4d_sort_pairs_noalloc_status reads that word. */
 #define FS4D_NOALLOC_MAX_PAIRS (1 << 20)
 FS4D_API fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int32_t key_bits, uint64_t* d_keys,
                                              uint32_t* d_values);
+/* Queue on cuda_stream a copy of the status word of the last
+ * fs4d_sort_pairs_noalloc queued on the current device into *out (4 bytes of
+ * device or page-locked host memory; valid once the stream has been
+ * synchronised): 0 when the sort completed, bit 0 set when one of its bounded
+ * waits gave up (the sorted output is then unreliable).  Allocates nothing. */
+FS4D_API fs4d_status fs4d_sort_pairs_noalloc_status(void* cuda_stream, uint32_t* out);
 
 /* Eq. 4 per 16x16 tile over the sorted lists: d_ranges [tiles][2], d_values [K]
  * Gaussian indices, per-Gaussian d_xy [n][2], d_conic_opacity [n][4], d_rgb [n][3].

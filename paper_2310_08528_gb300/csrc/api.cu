@@ -193,6 +193,7 @@ struct fs4d_ctx {
   cudaEvent_t slot_rendered[2] = {}, slot_copied[2] = {};
   unsigned long long* h_pairs = nullptr;  // pinned, [h_pairs_cap]: each frame's pair count
   int h_pairs_cap = 0;
+  uint32_t spin_limit = kSpinLimit;       // polls of a look-back wait (fs4d_set_wait_limit)
 };
 
 namespace {
@@ -488,7 +489,11 @@ SortWork sort_work(Work& w) {
   return sw;
 }
 
-SortWork sort_work(fs4d_ctx* c) { return sort_work(c->w); }
+SortWork sort_work(fs4d_ctx* c) {
+  SortWork sw = sort_work(c->w);
+  sw.spin_limit = c->spin_limit;
+  return sw;
+}
 
 // Where one frame's launches go: work memory, stream, status word, and whether
 // the context's stage-timing events are recorded.
@@ -582,6 +587,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   SortWork dsw;
   dsw.hist = z.hist; dsw.lookback = z.dlb; dsw.part_counters = z.counters + 8; dsw.max_parts = z.dparts;
   dsw.prezeroed = true;
+  dsw.spin_limit = c->spin_limit;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
                            P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, dsw, e.status, stream, &dalt,
                            &dsel));
@@ -598,6 +604,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   ea.tile_count = z.tile_count;
   ea.n_tiles = tx * ty;
   ea.status = e.status;
+  ea.spin_limit = c->spin_limit;
   ea.report_overflow = report ? 1 : 0;
   w.bmp = use_bitmap(c, w, s->n, tx * ty, offsets);
   if (e.w == &c->w) c->last_binning = w.bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;
@@ -651,6 +658,7 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
     SortWork psw;
     psw.hist = z.hist; psw.lookback = z.plb; psw.part_counters = z.counters + 32; psw.max_parts = z.pparts;
     psw.prezeroed = true;
+    psw.spin_limit = c->spin_limit;
     if (n_bound > z.pparts * 1024) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
     FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
                              P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
@@ -763,6 +771,12 @@ const char* fs4d_last_error(const fs4d_ctx* c) { return c ? c->err.c_str() : "nu
 fs4d_status fs4d_set_stream(fs4d_ctx* c, void* cuda_stream) {
   if (!c) return FS4D_ERR_INVALID_ARG;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_set_wait_limit(fs4d_ctx* c, uint32_t polls) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  c->spin_limit = polls == 0 ? kSpinLimit : polls;
   return FS4D_OK;
 }
 
@@ -1349,6 +1363,7 @@ fs4d_status fs4d_bin_sort(fs4d_ctx* c, int32_t n, const float* d_depth, const in
   ea.tile_count = P<uint32_t>(w.tile_count);
   ea.n_tiles = n_tiles;
   ea.status = P<uint32_t>(c->status);
+  ea.spin_limit = c->spin_limit;
   ea.report_overflow = 0;
   const bool bmp = use_bitmap(c, w, n, n_tiles, false);
   c->last_binning = bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;

@@ -600,20 +600,12 @@ cudaError_t launch_mlp_t(const MlpBwdArgs& a, cudaStream_t s) {
   constexpr int HL = H * L;
   constexpr int rows = HL > kWidth ? HL : kWidth;
   const size_t smem = sizeof(float) * ((size_t)a.f.mg.total + 2 * (size_t)rows * kMT);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(mlp_bwd_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [&] {
+    return cudaFuncSetAttribute(mlp_bwd_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
   const long long need = ((long long)a.f.n + kMT - 1) / kMT;
   const int grid = (int)(need < sms ? need : sms);
   mlp_bwd_kernel<H, L><<<grid, kMT, smem, s>>>(a);

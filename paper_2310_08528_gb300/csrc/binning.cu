@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int sme
         }
         j -= used;
         if (!found && used < cnt) {
-          if (++spins > kSpinLimit) {
+          if (++spins > a.spin_limit) {
             atomicOr(a.status, kStatusTimeout);
             break;
           }
@@ -502,13 +502,11 @@ int emit_parts(int n) { return (n + kPart - 1) / kPart; }
 
 cudaError_t launch_scan_emit(const EmitArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(scan_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [] {
+    return cudaFuncSetAttribute(scan_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
+  });
+  if (e != cudaSuccess) return e;
   const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
   return launch_pdl(scan_emit_kernel, emit_parts(a.n), kThreads, 4 * (size_t)st, s, a, st);
 }
@@ -517,12 +515,11 @@ int bitmap_words(int n) { return ((n + 127) / 128) * 4; }
 
 cudaError_t launch_mark_tiles(const EmitArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [] {
+    return cudaFuncSetAttribute(mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kEmitSmemTiles);
+  });
+  if (e != cudaSuccess) return e;
   if (a.words < bitmap_words(a.n)) return cudaErrorInvalidValue;
   const int st = a.n_tiles <= kEmitSmemTiles ? a.n_tiles : 0;
   return launch_pdl(mark_kernel, emit_parts(a.n), kMarkThreads, 4 * (size_t)st, s, a, st);

@@ -233,20 +233,12 @@ cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
   constexpr int XR = HL > kWidth ? HL : kWidth;
   const size_t smem = sizeof(float) * ((size_t)a.mg.total + (size_t)(XR + kWidth + kDeltaDim) * kGS) +
                       3 * kTileG * sizeof(float4);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(deform_fp32_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [&] {
+    return cudaFuncSetAttribute(deform_fp32_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
   const long long total = (long long)a.n * a.n_t;
   const long long need = (total + kTileG - 1) / kTileG;
   const int grid = (int)(need < sms ? need : sms);

@@ -383,20 +383,12 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 template <int H, int L>
 cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16 + 3 * kRows * 16;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(deform_tc_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [&] {
+    return cudaFuncSetAttribute(deform_tc_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
   const long long tiles = ((long long)a.n * a.n_t + kRows - 1) / kRows;
   const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
   return launch_pdl(deform_tc_kernel<H, L>, grid, kThreads, smem, s, a);

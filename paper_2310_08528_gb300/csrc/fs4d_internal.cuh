@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "fs4d.h"
 
 namespace fs4d {
@@ -52,8 +54,31 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Bounded spin limit for decoupled look-back waits (iterations of ~100 ns).
+// Bounded spin limit for decoupled look-back waits (iterations of ~100 ns).  The
+// limit a launch uses is an argument (SortWork::spin_limit, EmitArgs::spin_limit)
+// so that a context can lower it to exercise the timeout path (fs4d_set_wait_limit).
 constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Per-device launcher state: whether a kernel's dynamic shared-memory attribute
+// has been set on a device (cudaFuncSetAttribute applies to the current device
+// only), and the SM count of the current device.
+constexpr int kMaxDevices = 64;
+struct PerDeviceFlag {
+  std::atomic<bool> done[kMaxDevices] = {};
+};
+// Runs set() once per device for the flag; returns its error, or success.
+template <typename F>
+inline cudaError_t once_per_device(PerDeviceFlag& f, F set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (f.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = set();  // two threads may both set it: the attribute is the same
+  if (e == cudaSuccess) f.done[dev].store(true, std::memory_order_release);
+  return e;
+}
+int device_sm_count();  // SMs of the current device (cached per device; >= 1)
 
 // ---------------------------------------------------------------- HexPlane geometry
 struct PlaneGeom {
@@ -164,6 +189,7 @@ struct EmitArgs {
   uint32_t* tile_count;         // [n_tiles] (zeroed): pairs per tile
   int n_tiles;
   uint32_t* status;
+  uint32_t spin_limit;          // polls of the look-back wait before it gives up
   // tile bitmap binning (launch_mark_tiles / launch_extract_tiles)
   uint32_t* bitmap;             // [n_tiles][words], bit (i & 31) of word i >> 5 of row t: the
                                 // Gaussian of depth rank i touches tile t (all zero between frames)
@@ -185,6 +211,7 @@ struct SortWork {
   uint32_t* part_counters;      // [2 * 8 + 1]: pass tickets, then selection words
   long long max_parts;          // >= sort_parts(n_bound) lets every partition size be chosen
   bool prezeroed = false;       // tickets, selection words and look-back already zero
+  uint32_t spin_limit = kSpinLimit;  // polls of a look-back wait before it gives up
 };
 
 // ---------------------------------------------------------------- launchers

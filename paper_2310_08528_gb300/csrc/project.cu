@@ -242,12 +242,13 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 template <int DEG>
 cudaError_t launch_project_deg(const ProjectArgs& a, unsigned grid, cudaStream_t s) {
   constexpr size_t smem = 16 * 256 * (size_t)sh_vec4<DEG>();
-  static bool attr = false;
-  if (!attr && smem > 0) {  // (with the 4 KB of static histogram the total can pass the 48 KB default)
-    cudaError_t e = cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 0) {  // (with the 4 KB of static histogram the total can pass the 48 KB default)
+    static PerDeviceFlag attr;
+    cudaError_t e = once_per_device(attr, [] {
+      return cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
     if (e != cudaSuccess) return e;
   }
-  attr = true;
   return launch_pdl(project_kernel<DEG>, grid, 256, smem, s, a);
 }
 

@@ -69,6 +69,7 @@ struct PassArgs {
   uint32_t* lookback;       // this pass's [parts][256], zeroed
   uint32_t* part_counter;   // this pass's ticket, zeroed
   uint32_t* status;
+  uint32_t spin_limit;      // polls of the look-back wait before it gives up
 };
 
 template <int ITEMS>
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
       }
       j -= used;
       if (!found && used < cnt) {
-        if (++spins > kSpinLimit) {
+        if (++spins > a.spin_limit) {
           atomicOr(a.status, kStatusTimeout);
           break;
         }
@@ -252,6 +253,19 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
 }  // namespace
 
 int sort_passes(int key_bits) { return (key_bits + 7) / 8; }
+
+int device_sm_count() {
+  static std::atomic<int> sms[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  int v = sms[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    sms[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
 // Partitions a sort of n keys may use (the small-partition count: an upper bound).
 long long sort_parts(long long n) { return (n + kPartPairsSmall - 1) / kPartPairsSmall; }
 
@@ -270,17 +284,15 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   const bool small = n_bound <= (1ll << 19) && parts_small <= work.max_parts;
   const long long parts = small ? parts_small : (n_bound + kPartPairs - 1) / kPartPairs;
   if (parts > work.max_parts || n_bound > (long long)kValMask) return cudaErrorInvalidValue;
-  static bool attr_done = false;
-  cudaError_t e;
-  if (!attr_done) {
-    e = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(PassSmem<kItemsLarge>));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(onesweep_kernel<kItemsSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(PassSmem<kItemsSmall>));
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [] {
+    cudaError_t r = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PassSmem<kItemsLarge>));
+    if (r != cudaSuccess) return r;
+    return cudaFuncSetAttribute(onesweep_kernel<kItemsSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(PassSmem<kItemsSmall>));
+  });
+  if (e != cudaSuccess) return e;
   if (!work.prezeroed) {
     // tickets [0, kMaxPasses) and selection words [kMaxPasses, 2 kMaxPasses + 1)
     e = cudaMemsetAsync(work.part_counters, 0, sizeof(uint32_t) * (2 * kMaxPasses + 1), s);
@@ -291,7 +303,7 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   if (!hist_ready) {
     e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     if (e != cudaSuccess) return e;
-    const int blocks = (int)min((n_bound + 1023) / 1024, (long long)152 * 8);
+    const int blocks = (int)min((n_bound + 1023) / 1024, (long long)device_sm_count() * 8);
     e = launch_pdl(hist_kernel, blocks, 256, 0, s, keys, n_dev, n_bound, first_bit, passes, work.hist);
     if (e != cudaSuccess) return e;
   }
@@ -316,6 +328,7 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     pa.lookback = work.lookback + (size_t)p * parts * kRadix;
     pa.part_counter = work.part_counters + p;
     pa.status = status;
+    pa.spin_limit = work.spin_limit;
     if (small)
       e = launch_pdl(onesweep_kernel<kItemsSmall>, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s, pa);
     else
@@ -362,6 +375,20 @@ static __device__ __align__(256) unsigned char g_sort_scratch[kNaBytes];
 std::mutex g_na_mutex;
 unsigned char* g_na_base[kNaMaxDevices] = {};
 
+// Device address of the work area on the current device (looked up once per device).
+fs4d_status na_base(unsigned char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return FS4D_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_base[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return FS4D_ERR_CUDA;
+    g_na_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_na_base[dev];
+  return FS4D_OK;
+}
+
 }  // namespace
 }  // namespace fs4d
 
@@ -371,18 +398,9 @@ extern "C" fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int
   if (n < 0 || key_bits < 1 || key_bits > 64 || (n > 0 && (!d_keys || !d_values))) return FS4D_ERR_INVALID_ARG;
   if (n > kNaMaxPairs) return FS4D_ERR_CAPACITY;
   if (n == 0) return FS4D_OK;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return FS4D_ERR_CUDA;
   unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_base[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return FS4D_ERR_CUDA;
-      g_na_base[dev] = static_cast<unsigned char*>(p);
-    }
-    base = g_na_base[dev];
-  }
+  const fs4d_status bs = na_base(&base);
+  if (bs != FS4D_OK) return bs;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   uint32_t* status = reinterpret_cast<uint32_t*>(base + kNaStatus);
   if (cudaMemsetAsync(status, 0, 4, s) != cudaSuccess) return FS4D_ERR_CUDA;
@@ -403,5 +421,17 @@ extern "C" fs4d_status fs4d_sort_pairs_noalloc(void* cuda_stream, int64_t n, int
         cudaMemcpyAsync(d_values, values_alt, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return FS4D_ERR_CUDA;
   }
+  return FS4D_OK;
+}
+
+extern "C" fs4d_status fs4d_sort_pairs_noalloc_status(void* cuda_stream, uint32_t* out) {
+  using namespace fs4d;
+  if (!out) return FS4D_ERR_INVALID_ARG;
+  unsigned char* base = nullptr;
+  const fs4d_status bs = na_base(&base);
+  if (bs != FS4D_OK) return bs;
+  if (cudaMemcpyAsync(out, base + kNaStatus, 4, cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(cuda_stream)) !=
+      cudaSuccess)
+    return FS4D_ERR_CUDA;
   return FS4D_OK;
 }

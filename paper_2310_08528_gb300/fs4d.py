@@ -26,7 +26,8 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_load_scene", "fs4d_unload_scene", "fs4d_update_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
            "fs4d_render_host", "fs4d_render_host_batch", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
-           "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_composite")
+           "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_sort_pairs_noalloc_status",
+           "fs4d_composite", "fs4d_set_wait_limit")
 STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
 
 
@@ -74,6 +75,7 @@ def library(path: str = LIB_PATH):
         "fs4d_destroy": [vp],
         "fs4d_set_stream": [vp, vp],
         "fs4d_check_device_status": [vp],
+        "fs4d_set_wait_limit": [vp, C.c_uint32],
         "fs4d_load_scene": [vp, C.POINTER(SceneDesc), C.POINTER(i32)],
         "fs4d_unload_scene": [vp, i32],
         "fs4d_update_scene": [vp, i32, C.POINTER(SceneDesc), i32],
@@ -103,6 +105,8 @@ def library(path: str = LIB_PATH):
         fn.restype = C.c_int
     L.fs4d_sort_pairs_noalloc.argtypes = [vp, i64, i32, vp, vp]
     L.fs4d_sort_pairs_noalloc.restype = C.c_int
+    L.fs4d_sort_pairs_noalloc_status.argtypes = [vp, vp]
+    L.fs4d_sort_pairs_noalloc_status.restype = C.c_int
     L.fs4d_last_error.argtypes = [vp]
     L.fs4d_last_error.restype = C.c_char_p
     _lib = L
@@ -163,6 +167,10 @@ class Context:
 
     def check_device_status(self) -> None:
         self.call("fs4d_check_device_status")
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of the look-back waits of later launches (0 = default); a diagnostic."""
+        self.call("fs4d_set_wait_limit", int(polls))
 
     # ------------------------------------------------------------------ scenes
     def load_scene(self, scene) -> int:

@@ -44,7 +44,7 @@ def _null_args(fn):
     for a in fn.argtypes:
         if a in (ctypes.c_float, ctypes.c_double):
             out.append(0.0)
-        elif a in (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t):
+        elif a in (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t):
             out.append(0)
         else:
             out.append(None)
@@ -127,6 +127,7 @@ def test_binding_argument_types_match_the_prototypes():
     src = open(os.path.join(ROOT, "include", "fs4d.h")).read()
     scalar = {"int32_t": ctypes.c_int32, "int": ctypes.c_int32, "fs4d_scene_id": ctypes.c_int32,
               "fs4d_precision": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+              "uint32_t": ctypes.c_uint32,
               "float": ctypes.c_float, "size_t": ctypes.c_size_t}
     protos = re.findall(r"FS4D_API\s+[\w\s\*]+?\b(fs4d_\w+)\s*\(([^)]*)\)\s*;", src)
     assert len(protos) == len(declared_symbols())
