@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=500)
     return ap.parse_args()
 
@@ -139,49 +140,55 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- roofline
 
-def load_peaks():
+def load_peaks(sms: int = 152):
+    """Roofline denominators: the measured copy bandwidth and bf16 GEMM rate of this
+    pool's GB300s when present, else the fallback figures; sms = the device's SM count."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
         return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
                 "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
-                "source": "measured"}
+                "sms": sms, "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
-            "source": "fallback"}
+            "sms": sms, "source": "fallback"}
 
 
 def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, evals: int = 0,
-               bitmap: bool = True):
-    """Algorithmic bytes or FLOPs of one launch of each stage (per-unit figures
-    times the units one launch processes).  Returns a list of (bound, work, unit);
-    the first entry is the stage's primary bound; an empty list: the stage's work
-    is done inside another stage."""
+               bitmap: bool = True, visited: int = None, bands: int = 1):
+    """Algorithmic bytes or FLOPs of one frame's launches of each stage (per-unit
+    figures times the units processed).  Returns a list of (bound, work, unit);
+    the first entry is the stage's primary bound; an empty list: the stage does
+    no work of its own.  visited: tile pairs the compositing must read (each
+    tile's list up to its last contributing Gaussian); bands: passes of the
+    per-Gaussian stages (a frame rendered in bands projects and depth-sorts once
+    per band)."""
     if stage == "deform":
         flops = 2 * (64 * 64 + 64 * 64 + 3 * 64 * 64 + 64 * 10) * n   # MLP contraction, 42,240 FLOP/Gaussian
         return [(("tensor" if prec == "bf16" else "alu"), flops, "FLOP"), ("hbm", 80 * n, "B")]
     if stage == "project":
         # read: mean, quaternion, log-scale, opacity logit, 48 SH floats; written: xy, conic + opacity,
         # rgb, depth, radius, tile rectangle, depth-sort key and index
-        return [("hbm", n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 4 + 4), "B")]
-    if stage == "scan_emit":
-        # depth sort: 4 passes of 32-bit keys, each reading and writing 8 B key + 4 B value per Gaussian
+        return [("hbm", bands * (n * (12 + 16 + 12 + 4 + 48 * 4) + n * (8 + 16 + 12 + 4 + 4 + 16 + 4 + 4)), "B")]
+    if stage == "depth_sort":
+        # 4 passes over 32-bit keys, each reading and writing an 8 B key and a 4 B index per Gaussian
+        return [("hbm", bands * 4 * n * 24, "B")]
+    if stage == "binning":
         if bitmap:
             # tile bitmap: order + rect in and the 36 B of projected data copied into rank order per
             # Gaussian; per pair one 4 B bit-word update (read + write), the word read and cleared by the
             # row walk and the rank written
-            return [("hbm", 4 * n * 24 + n * (4 + 16 + 72) + K * (8 + 4 + 4 + 4), "B")]
+            return [("hbm", bands * n * (4 + 16 + 72) + K * (8 + 4 + 4 + 4), "B")]
         # emission: order, rect, depth in + offset out per Gaussian, 12 B per pair out
-        return [("hbm", 4 * n * 24 + n * (4 + 16 + 4 + 4) + K * 12, "B")]
+        return [("hbm", bands * n * (4 + 16 + 4 + 4) + K * 12, "B")]
     if stage == "sort":
         if bitmap:
             return []  # no pair sort: the bitmap rows list each tile's Gaussians in depth order
         return [("hbm", passes * K * 24, "B")]                         # read + write 12 B per pair per pass
-    if stage == "ranges":
-        return []  # produced by the tile scan inside the emission stage
     if stage == "composite":
-        # gather (idx + xy, conic/opacity, rgb) per pair and the rgb write per pixel; ~15 FLOP per tested
-        # (pixel, Gaussian) up to each pixel's last contributor
-        return [("hbm", K * 40 + pixels * 12, "B"), ("alu", 15 * evals, "FLOP")]
+        # gather (idx + xy, conic/opacity, rgb) per visited pair and the rgb write per pixel; ~15 FLOP per
+        # tested (pixel, Gaussian) up to each pixel's last contributor
+        v = K if visited is None else visited
+        return [("hbm", v * 40 + pixels * 12, "B"), ("alu", 15 * evals, "FLOP")]
     raise KeyError(stage)
 
 
@@ -190,21 +197,30 @@ def _frac(bound, work, sec, peaks):
         ach, peak, u = work / sec / 1e9, peaks["hbm_gbs"], "GB/s"
     elif bound == "tensor":
         ach, peak, u = work / sec / 1e12, peaks["bf16_tflops"], "TFLOP/s"
-    else:  # float32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
-        ach, peak, u = work / sec / 1e12, 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s"
+    else:  # float32 FMA pipe: SMs x 128 lanes x 2 FLOP x max SM clock
+        ach, peak, u = work / sec / 1e12, peaks["sms"] * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s"
     return {"bound": bound, "achieved": ach, "peak": peak, "unit": u, "frac": ach / peak}
 
 
 SINGLE_KERNEL = {"deform": "deform_tc_kernel / deform_fp32_kernel", "project": "project_kernel",
                  "composite": "composite_kernel"}
-FUSED = {"ranges": "the tile scan in the binning stage writes the ranges",
-         "sort": "tile bitmap binning: no pair sort (the binning stage lists each tile in depth order)"}
+FUSED = {"sort": "tile bitmap binning: no pair sort (the binning stage lists each tile in depth order)"}
 
 
-def roofline(stage_ms, n, K, pixels, passes, prec, peaks, evals, bitmap=True):
+def visited_pairs(torch, nc, tile: int = 16) -> int:
+    """Tile pairs the compositing must read: per tile, its list up to the last
+    contributing Gaussian of any of its pixels (nc = last contributor per pixel)."""
+    H, W = nc.shape
+    ty, tx = (H + tile - 1) // tile, (W + tile - 1) // tile
+    pad = torch.zeros((ty * tile, tx * tile), dtype=nc.dtype, device=nc.device)
+    pad[:H, :W] = nc
+    return int(pad.view(ty, tile, tx, tile).amax(dim=(1, 3)).sum().item())
+
+
+def roofline(stage_ms, n, K, pixels, passes, prec, peaks, evals, bitmap=True, visited=None, bands=1):
     out = {}
     for st, ms in stage_ms.items():
-        work = stage_work(st, n, K, pixels, passes, prec, evals, bitmap)
+        work = stage_work(st, n, K, pixels, passes, prec, evals, bitmap, visited, bands)
         if not work:
             out[st] = {"ms": ms, "fused": FUSED[st]}
             continue
@@ -400,6 +416,121 @@ def serving_bench(ctx, fs4d, torch, rates=(500.0, 2000.0), seconds=1.5, precs=("
             "server_stats": {k: int(v) for k, v in st.items()}}
 
 
+# ----------------------------------------------------------------- stress workload
+
+STRESS_RES = ((1920, 1080), (3840, 2160))
+STRESS_WORKLOAD = ("stress: N=2M Gaussians (32-component mixture in the unit sphere) with log-scales N(-2.5,0.5), "
+                   "SH degree 3, HexPlane spatial {64,128,256} x temporal 300 x 32 features, MLP width 64; 16 "
+                   "timestamps deformed in one launch; frames at 1920x1080 and 3840x2160 from a hemisphere camera")
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _sort_passes(width, height, bands):
+    tx, ty = (width + 15) // 16, (height + 15) // 16
+    tiles = tx * ((ty + bands - 1) // bands)
+    return (int(np.ceil(np.log2(max(tiles, 2)))) + 7) // 8
+
+
+def stress_bench(ctx, fs4d, torch, stream, peaks, frames=3):
+    """The stress workload: the batched deformation of 16 timestamps (both
+    precisions) and frames at 1080p and 4K.  Every input is far larger than L2
+    (2M Gaussians; 1.3e9 and 5e9 tile pairs per frame), so no flush is needed.
+    Frames with more pairs than one pair-sort pass counts render in bands of
+    tile rows (each band projects and depth-sorts the 2M Gaussians again)."""
+    from paper_2310_08528_gb300 import scenegen as sg
+    try:
+        scene = sg.make_stress(0)
+        sid = ctx.load_scene(scene)
+        n = scene.n
+        ts = [float(v) for v in np.linspace(0.0, 1.0, 16)]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {"workload": STRESS_WORKLOAD, "n_gaussians": n,
+               "l2": "inputs larger than L2 (no flush)", "timing": "CUDA events on the context's stream"}
+        bufs = (torch.empty((16, n, 3), device=dev), torch.empty((16, n, 4), device=dev),
+                torch.empty((16, n, 3), device=dev))
+        deform = {}
+        with torch.cuda.stream(stream):
+            for p in ("bf16", "fp32"):
+                pc = fs4d.BF16 if p == "bf16" else fs4d.FP32
+                ctx.deform(sid, ts, pc, out=bufs)
+                ms = []
+                for _ in range(frames):
+                    e0, e1 = _events(torch)
+                    e0.record(stream)
+                    ctx.deform(sid, ts, pc, out=bufs)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                t = float(np.median(ms))
+                work = stage_work("deform", 16 * n, 0, 0, 0, p)
+                deform[p] = {"ms": t, "gaussian_timesteps_per_s": 16 * n / (t * 1e-3),
+                             "roofline": _frac(work[0][0], work[0][1], t * 1e-3, peaks),
+                             "streamed": _frac("hbm", work[1][1], t * 1e-3, peaks)}
+        out["deform_16t"] = deform
+        del bufs
+        res = {}
+        for (w, h) in STRESS_RES:
+            cam = sg.hemisphere_cameras(4, width=w, height=h, seed=7)[1]
+            image = torch.empty((h, w, 3), device=dev)
+            r = {}
+            with torch.cuda.stream(stream):
+                for p in ("bf16", "fp32"):
+                    pc = fs4d.BF16 if p == "bf16" else fs4d.FP32
+                    ctx.render(sid, cam, 0.5, pc, image=image)  # finds the bands, sizes the buffers
+                    ms = []
+                    for i in range(frames):
+                        e0, e1 = _events(torch)
+                        e0.record(stream)
+                        ctx.render(sid, cam, ts[(5 * i) % 16], pc, image=image)
+                        e1.record(stream)
+                        stream.synchronize()
+                        ms.append(e0.elapsed_time(e1))
+                    t = float(np.median(ms))
+                    r[p] = {"ms": t, "fps": 1e3 / t, "gaussians_per_s": n / (t * 1e-3),
+                            "tile_pairs": ctx.last_pairs(), "bands": ctx.last_bands()}
+                ctx.set_stage_timing(True)
+                _, _, nc = ctx.render(sid, cam, 0.5, fs4d.BF16, with_aux=True)
+                st = ctx.stage_times()
+                ctx.set_stage_timing(False)
+                K, bands = ctx.last_pairs(), ctx.last_bands()
+                vis, evals = visited_pairs(torch, nc), int(nc.sum().item())
+            r["stages"] = roofline(st, n, K, w * h, _sort_passes(w, h, bands), "bf16", peaks, evals, bitmap=False,
+                                   visited=vis, bands=bands)
+            r["tile_pairs"], r["tile_pairs_visited"], r["bands"] = K, vis, bands
+            res[f"{w}x{h}"] = r
+            del image, nc
+        out["frames"] = res
+        ctx.unload_scene(sid)
+        return out
+    except Exception as exc:  # the headline line must still be printed
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def bf16_vs_fp32(ctx, fs4d, torch, sid, scene, stream):
+    """The BF16 path against the FP32 path (itself within 2e-5 of the FP64 oracle) on
+    the benchmark scene: max |dX|, |dr|, |ds| of the deformation at 5 timestamps,
+    and the image PSNR over 5 views."""
+    ts = [0.0, 0.25, 0.5, 0.75, 1.0]
+    with torch.cuda.stream(stream):
+        a = ctx.deform(sid, ts, fs4d.BF16)
+        b = ctx.deform(sid, ts, fs4d.FP32)
+        errs = [float((x - y).abs().max().item()) for x, y in zip(a, b)]
+        mse = []
+        for i in range(5):
+            cam, t = views(97 * i, 0, 1)
+            x = ctx.render(sid, cam, t, fs4d.BF16)
+            y = ctx.render(sid, cam, t, fs4d.FP32)
+            mse.append(float(((x - y) ** 2).mean().item()))
+    stream.synchronize()
+    psnr = [float(10 * np.log10(1.0 / m)) if m > 0 else float("inf") for m in mse]
+    return {"max_abs_dx": errs[0], "max_abs_dr": errs[1], "max_abs_ds": errs[2], "psnr_db_min": min(psnr),
+            "psnr_db_mean": float(np.mean(psnr)), "views": 5, "timestamps": ts,
+            "reference": "the FP32 path (within 2e-5 of the FP64 oracle in the parity tests)"}
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def measure(ctx, fs4d, torch, sid, prec, steps, warmup, rank, world, stream, cap):
@@ -501,14 +632,15 @@ def main():
     launches_per_frame = 10 if bitmap else 9 + passes
     # (pixel, Gaussian) tests the compositing must make: each pixel walks its tile's list up to its
     # last contributor (summed over the frames of the view set)
-    evals, pairs = [], []
+    evals, pairs, visited = [], [], []
     with torch.cuda.stream(stream):
         for c in range(0, N_CAMS * N_TIMES, 97):
             cam, t = views(c, 0, 1)
             _, _, nc = ctx.render(sid, cam, t, with_aux=True)
             evals.append(int(nc.sum().item()))
+            visited.append(visited_pairs(torch, nc))
             pairs.append(ctx.last_pairs())
-    evals, mean_pairs = int(np.mean(evals)), int(np.mean(pairs))
+    evals, mean_pairs, visited = int(np.mean(evals)), int(np.mean(pairs)), int(np.mean(visited))
 
     bf16_ok = True
     try:
@@ -564,9 +696,10 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    peaks = load_peaks()
+    peaks = load_peaks(torch.cuda.get_device_properties(local).multi_processor_count)
     K = mean_pairs
-    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks, evals, bitmap)
+    rf = roofline(results[head]["stages_ms"], scene.n, K, WIDTH * HEIGHT, passes, head, peaks, evals, bitmap,
+                  visited)
     # the dominant KERNEL: the longest single-kernel stage (the binning stage is a chain of
     # depth-sort passes and binning kernels, reported under "stages")
     dom = max((k for k in rf if "frac" in rf[k] and k in SINGLE_KERNEL), key=lambda k: rf[k]["ms"])
@@ -583,7 +716,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "resolution": [WIDTH, HEIGHT],
                    "binning": "tile bitmap" if bitmap else "radix sort",
-                   "tile_pairs_mean": K, "pixel_gaussian_tests_mean": evals, "pair_capacity": cap, "parallelism": f"replicas x{world}",
+                   "tile_pairs_mean": K, "tile_pairs_visited_mean": visited, "pixel_gaussian_tests_mean": evals, "pair_capacity": cap, "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed frame (256 MB device write, outside the timed interval)",
                    "timing": "CUDA events around camera upload + CUDA-graph replay of one frame (graph without "
                              "the stage-timing events; stages from a second graph replayed separately)"},
@@ -591,6 +724,7 @@ def main():
                      "unit": rf[dom]["unit"], "frac": rf[dom]["frac"], "traffic": traffic,
                      "peak_source": peaks["source"]},
         "stages": rf,
+        "fp32_fps": results.get("fp32", {}).get("fps"),
         "precisions": results,
         "e2e": {"value": e2e_steps * world / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 96,
                 "d2h_bytes_per_step": WIDTH * HEIGHT * 12 + 8,
@@ -599,10 +733,14 @@ def main():
         "gpu_launches": launches_per_frame * (args.steps * len(precs)),
         "clocks": clocks,
     }
+    if bf16_ok:
+        line["bf16_vs_fp32"] = bf16_vs_fp32(ctx, fs4d, torch, sid, scene, stream)
     if not args.no_training:
         line["training"] = training_bench(ctx, fs4d, torch, sid, scene, stream)
     if not args.no_serving:
         line["serving"] = serving_bench(ctx, fs4d, torch)
+    if not args.no_stress:
+        line["stress"] = stress_bench(ctx, fs4d, torch, stream, peaks)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -185,7 +185,12 @@ FS4D_API fs4d_status fs4d_deform(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision
                         float* d_means, float* d_quats, float* d_log_scales);
 
 /* Render one frame, I = S(M, G') with G' = G + F(G, t) (Sec. 4.1): deform at t
- * (Eq. 5, Eq. 6), project (Eq. 2, Eq. 3), bin, sort, composite (Eq. 1, Eq. 4).  d_image:
+ * (Eq. 5, Eq. 6), project (Eq. 2, Eq. 3), bin, sort, composite (Eq. 1, Eq. 4).
+ * A frame with more than 2^30 - 1 tile pairs (what one pair-sort pass counts) is
+ * rendered in horizontal bands of whole tile rows, each binned, sorted and
+ * composited on its own over the same deformed Gaussians (fs4d_last_pairs then
+ * gives the pairs of all bands); a frame saved for the backward must fit one
+ * pass (FS4D_ERR_CAPACITY otherwise).  d_image:
  * device [height][width][3]; d_t_final [height][width] and d_n_contrib
  * [height][width] may be NULL.  If `saved` is non-NULL, *saved receives the
  * forward state needed by fs4d_render_backward (free it with fs4d_frame_free).
@@ -231,6 +236,13 @@ FS4D_API fs4d_status fs4d_frame_free(fs4d_ctx* ctx, fs4d_frame* frame);
 /* Number of tile pairs K of a saved frame, and of the last render on the context. */
 FS4D_API fs4d_status fs4d_frame_pairs(const fs4d_frame* frame, int64_t* pairs);
 FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
+/* Number of bands of tile rows the last fs4d_render / fs4d_render_host frame on the
+ * context was rendered in (1 unless its pairs exceeded one pair-sort pass). */
+FS4D_API fs4d_status fs4d_last_bands(const fs4d_ctx* ctx, int32_t* bands);
+/* Most tile pairs one band of a frame may hold (0 = the default and maximum,
+ * 2^30 - 1).  A smaller value bounds the pair buffers' device memory (24 bytes per
+ * pair with the sort's second buffer) at the cost of more bands. */
+FS4D_API fs4d_status fs4d_set_band_pairs(fs4d_ctx* ctx, int64_t max_pairs);
 
 /* Binning policy of the context's frames (FS4D_BINNING_AUTO or FS4D_BINNING_SORT;
  * FS4D_ERR_INVALID_ARG otherwise), and the binning the last frame rendered on the
@@ -241,8 +253,10 @@ FS4D_API fs4d_status fs4d_last_binning(const fs4d_ctx* ctx, int32_t* mode);
 /* Per-stage device timing of frames rendered by fs4d_render / fs4d_render_async
  * (also inside a captured CUDA graph): when enabled, CUDA events are recorded on
  * the context's stream around each stage.  fs4d_stage_times waits for the last
- * recorded frame and writes ms[6] = deform, project, scan+emit, radix sort,
- * tile ranges, composite (milliseconds, that frame only). */
+ * recorded frame and writes ms[6] = deform, project, depth sort, binning (key
+ * emission or tile bitmap, with the tile scan that writes the ranges), pair sort,
+ * composite (milliseconds, that frame only; for a frame rendered in bands of tile
+ * rows, each stage summed over the bands). */
 FS4D_API fs4d_status fs4d_set_stage_timing(fs4d_ctx* ctx, int32_t enable);
 FS4D_API fs4d_status fs4d_stage_times(fs4d_ctx* ctx, float* h_ms);
 

@@ -83,6 +83,14 @@ def lib():
         L.orc_render_backward.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.c_double, C.c_int32,
                                           C.c_int32, F64P, C.POINTER(OrcGrads)]
         L.orc_render_backward.restype = C.c_int32
+        L.orc_l1_loss.argtypes = [C.c_int64, F64P, F64P, C.c_void_p]
+        L.orc_l1_loss.restype = C.c_double
+        L.orc_tv_loss.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_void_p]
+        L.orc_tv_loss.restype = C.c_double
+        L.orc_lr.argtypes = [C.c_double, C.c_double, C.c_int64, C.c_int64]
+        L.orc_lr.restype = C.c_double
+        L.orc_adam_step.argtypes = [C.c_int64, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_int64]
         _lib = L
     return _lib
 
@@ -330,6 +338,83 @@ def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = 
     if rc != 0:
         raise RuntimeError(f"orc_render_backward failed: {rc}")
     return g
+
+
+# ----------------------------------------------------------------- training step (Sec. 4.3, App. A)
+
+def l1_loss(image, target):
+    """Mean absolute difference over every pixel and channel, and its gradient."""
+    a = np.ascontiguousarray(image, np.float64).ravel()
+    b = np.ascontiguousarray(target, np.float64).ravel()
+    g = np.zeros_like(a)
+    loss = lib().orc_l1_loss(a.size, a, b, g.ctypes.data)
+    return loss, g.reshape(np.shape(image))
+
+
+def tv_loss(scene, weight: float):
+    """Grid TV loss over the HexPlane planes and its gradient (planes layout)."""
+    h = _SceneHandle(scene)
+    g = np.zeros(h.arrays["planes"].shape[0])
+    loss = lib().orc_tv_loss(C.byref(h.struct), float(weight), g.ctypes.data)
+    return loss, g
+
+
+def lr_at(lr0: float, lr1: float, k: int, total: int) -> float:
+    return lib().orc_lr(float(lr0), float(lr1), int(k), int(total))
+
+
+def adam_step(param, grad, m, v, lr, beta1, beta2, eps, step):
+    """In place on float64 arrays: one bias-corrected Adam update."""
+    for a in (param, grad, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    lib().orc_adam_step(param.size, param.reshape(-1), grad.reshape(-1), m.reshape(-1), v.reshape(-1), float(lr),
+                        float(beta1), float(beta2), float(eps), int(step))
+
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")
+
+
+def train_step(scene, cam, t: float, target, cfg, state, tile: int = 16):
+    """One training step (Sec. 4.3): render the frame, L = |I^ - I| + L_tv, the
+    gradient of L by the chain rule of the render (the backward above) plus the TV
+    gradient on the planes, then one Adam update per parameter group at the step's
+    decayed learning rate (App. A).  cfg: dict with 'lr' {group: (lr0, lr1)} ('sh'
+    takes 'sh_dc' for the degree-0 coefficients and 'sh_rest' for the others),
+    'total_steps', 'beta1', 'beta2', 'eps', 'tv_weight'.  state: dict with 'step'
+    (updates done) and per-group float64 'm', 'v', 'param' (created on the first
+    call from the scene).  Returns (l1, tv); the updated parameters are in
+    state['param']."""
+    if "param" not in state:
+        state["param"] = {k: np.array(getattr(scene, k), np.float64) for k in GROUPS}
+        state["m"] = {k: np.zeros_like(v) for k, v in state["param"].items()}
+        state["v"] = {k: np.zeros_like(v) for k, v in state["param"].items()}
+        state["step"] = 0
+    cur = scene.copy()
+    for k in GROUPS:
+        setattr(cur, k, state["param"][k].astype(np.float32))
+    img, *_ = render(cur, cam, t, tile=tile)
+    l1, dl = l1_loss(img, target)
+    g = render_backward(cur, cam, t, dl, tile=tile)
+    tv, gtv = tv_loss(cur, cfg["tv_weight"])
+    g["planes"] = g["planes"] + gtv
+    k = state["step"]
+    step = k + 1
+    for grp in GROUPS:
+        p, m, v, gg = state["param"][grp], state["m"][grp], state["v"][grp], np.ascontiguousarray(g[grp], np.float64)
+        if grp == "sh":
+            dc = np.zeros(p.shape, bool)
+            dc[:, 0, :] = True
+            for part, key in ((dc, "sh_dc"), (~dc, "sh_rest")):
+                lr = lr_at(*cfg["lr"][key], k, cfg["total_steps"])
+                pp, mm, vv = p[part].copy(), m[part].copy(), v[part].copy()
+                adam_step(pp, np.ascontiguousarray(gg[part]), mm, vv, lr, cfg["beta1"], cfg["beta2"], cfg["eps"],
+                          step)
+                p[part], m[part], v[part] = pp, mm, vv
+        else:
+            lr = lr_at(*cfg["lr"][grp], k, cfg["total_steps"])
+            adam_step(p, gg, m, v, lr, cfg["beta1"], cfg["beta2"], cfg["eps"], step)
+    state["step"] = step
+    return l1, tv
 
 
 def kind() -> str:

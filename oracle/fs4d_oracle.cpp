@@ -947,3 +947,89 @@ extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam
   }
   return 0;
 }
+
+// ============================================================================
+// Training step (Sec. 4.3, App. A): the loss L = |I^ - I| + L_tv and one Adam
+// update of the parameters with learning rates decayed over the training run.
+// ============================================================================
+extern "C" {
+
+// L1 colour loss: the mean absolute difference over every pixel and channel
+// (reading of |I^ - I|), and its gradient sign(I^ - I) / count (0 where equal).
+double orc_l1_loss(int64_t count, const double* image, const double* target, double* grad) {
+  double sum = 0.0;
+  for (int64_t i = 0; i < count; ++i) {
+    const double d = image[i] - target[i];
+    sum += std::fabs(d);
+    if (grad) grad[i] = d > 0.0 ? 1.0 / (double)count : (d < 0.0 ? -1.0 / (double)count : 0.0);
+  }
+  return count > 0 ? sum / (double)count : 0.0;
+}
+
+// Grid total-variation loss over the HexPlane (reading of L_tv, which the paper
+// names without a formula): for every level and every one of the six planes, the
+// mean over all neighbouring cell pairs along each of the plane's two axes of the
+// squared feature difference (every channel), the two axes' means added, summed
+// over planes and levels, times `weight`.  grad (if non-null) receives the
+// gradient with respect to every plane value (planes layout).  Returns the loss.
+double orc_tv_loss(const orc_scene* s, double weight, double* grad) {
+  const int h = s->feat_dim;
+  double total = 0.0;
+  for (int l = 0; l < s->n_levels; ++l) {
+    for (int p = 0; p < 6; ++p) {
+      const int Ra = plane_res(s, l, kPlaneAxes[p][0]);
+      const int Rb = plane_res(s, l, kPlaneAxes[p][1]);
+      const int64_t off = plane_offset(s, l, p);
+      const float* P = s->planes + off;
+      auto at = [&](int b, int a, int c) { return (double)P[((int64_t)b * Ra + a) * h + c]; };
+      const double na = (double)Rb * (Ra - 1) * h, nb = (double)(Rb - 1) * Ra * h;
+      double sa = 0.0, sb = 0.0;
+      for (int b = 0; b < Rb; ++b)
+        for (int a = 0; a < Ra; ++a)
+          for (int c = 0; c < h; ++c) {
+            if (a + 1 < Ra) {
+              const double d = at(b, a + 1, c) - at(b, a, c);
+              sa += d * d;
+              if (grad) {
+                grad[off + ((int64_t)b * Ra + a + 1) * h + c] += weight * 2.0 * d / na;
+                grad[off + ((int64_t)b * Ra + a) * h + c] -= weight * 2.0 * d / na;
+              }
+            }
+            if (b + 1 < Rb) {
+              const double d = at(b + 1, a, c) - at(b, a, c);
+              sb += d * d;
+              if (grad) {
+                grad[off + ((int64_t)(b + 1) * Ra + a) * h + c] += weight * 2.0 * d / nb;
+                grad[off + ((int64_t)b * Ra + a) * h + c] -= weight * 2.0 * d / nb;
+              }
+            }
+          }
+      total += sa / na + sb / nb;
+    }
+  }
+  return weight * total;
+}
+
+// Learning rate of step k (0-based) of a run of `total` steps, decayed from lr0 to
+// lr1 (App. A: "decayed to ... at the end of training"); reading: log-linear
+// (exponential) interpolation, lr1 from step `total` on.
+double orc_lr(double lr0, double lr1, int64_t k, int64_t total) {
+  if (total <= 0 || lr0 <= 0.0 || lr1 <= 0.0) return lr0;
+  const double f = std::min(1.0, (double)k / (double)total);
+  return std::exp((1.0 - f) * std::log(lr0) + f * std::log(lr1));
+}
+
+// One Adam step (bias-corrected first and second moments; step = 1 for the first
+// update) of `count` parameters with gradient g at learning rate lr.
+void orc_adam_step(int64_t count, double* param, const double* g, double* m, double* v, double lr, double beta1,
+                   double beta2, double eps, int64_t step) {
+  const double c1 = 1.0 - std::pow(beta1, (double)step), c2 = 1.0 - std::pow(beta2, (double)step);
+  for (int64_t i = 0; i < count; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    const double mh = m[i] / c1, vh = v[i] / c2;
+    param[i] -= lr * mh / (std::sqrt(vh) + eps);
+  }
+}
+
+}  // extern "C"

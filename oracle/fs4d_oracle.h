@@ -27,6 +27,8 @@
  *                                    decisions taken either way (parity support)
  *   orc_*_backward                   chain rule of all of the above (training,
  *                                    Sec. 4.3)
+ *   orc_l1_loss / orc_tv_loss        the training loss L = |I^ - I| + L_tv (Sec. 4.3)
+ *   orc_lr / orc_adam_step           learning-rate decay and Adam update (App. A)
  *
  * Parity pins: tests/test_oracle_pins.py and tests/test_oracle_backward.py;
  * tests/test_oracle_planted_mistakes.py builds copies of this oracle with one
@@ -125,6 +127,13 @@ typedef struct orc_grads {
 
 int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,
                             int32_t tile, const double* dl_dimage, orc_grads* grads);
+
+/* Training step (Sec. 4.3, App. A). */
+double orc_l1_loss(int64_t count, const double* image, const double* target, double* grad);
+double orc_tv_loss(const orc_scene* s, double weight, double* grad);
+double orc_lr(double lr0, double lr1, int64_t k, int64_t total);
+void orc_adam_step(int64_t count, double* param, const double* g, double* m, double* v, double lr, double beta1,
+                   double beta2, double eps, int64_t step);
 
 #ifdef __cplusplus
 }

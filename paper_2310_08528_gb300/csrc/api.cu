@@ -55,6 +55,7 @@ T* P(DevBuf& b) {
 }
 
 struct Scene {
+  int id = 0;
   int n = 0, sh_degree = 0, K = 1;
   DevBuf means, log_scales, quats, opacity_logits, sh;
   DevBuf planes, planes_bf16, mlp, mlp_t, tc_ops, tc_bias;
@@ -187,13 +188,19 @@ struct fs4d_ctx {
   int binning = FS4D_BINNING_AUTO;
   int last_binning = FS4D_BINNING_SORT;
   bool timing = false;
-  cudaEvent_t ev[8] = {};        // deform, project, emit, emit end, sort, ranges, composite, end
+  cudaEvent_t ev[8] = {};        // start, deformed, projected, depth-sorted, binned | pair sort, sorted, composited
   // fs4d_render_host_batch: image copies overlapped with the next frame
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t slot_rendered[2] = {}, slot_copied[2] = {};
   unsigned long long* h_pairs = nullptr;  // pinned, [h_pairs_cap]: each frame's pair count
   int h_pairs_cap = 0;
   uint32_t spin_limit = kSpinLimit;       // polls of a look-back wait (fs4d_set_wait_limit)
+  // frames rendered in bands of tile rows (more pairs than one sort pass counts)
+  int band_scene = -1, band_w = 0, band_h = 0, band_hint = 0;  // bands the last such frame used
+  int last_bands = 1;
+  long long band_pairs = (1ll << 30) - 1;  // most pairs one band may hold (fs4d_set_band_pairs)
+  float stage_acc[6] = {};                // stage times summed over a banded frame's passes
+  bool stage_acc_valid = false;
 };
 
 namespace {
@@ -591,6 +598,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
                            P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, dsw, e.status, stream, &dalt,
                            &dsel));
+  mark(e, 3);
   EmitArgs ea{};
   ea.n = s->n; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
   ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
@@ -632,7 +640,7 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
     FS4D_CUDA(c, launch_tile_scan(z.tile_count, tx * ty, z.num_pairs, P<uint2>(w.ranges), z.hist,
                                   sort_passes(tile_bits), P<uint32_t>(w.tile_order), stream));
   }
-  mark(e, 3);
+  mark(e, 4);
   return FS4D_OK;
 }
 
@@ -652,21 +660,20 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
   const FrameZero& z = w.z;
   const uint32_t* n_dev = z.num_pairs + 1;
   bool alt = false;
-  mark(e, 4);
+  mark(e, 5);
   if (!w.bmp) {
     // pairs arrive in depth order: a stable sort on the tile bits gives (tile, depth, index)
     SortWork psw;
     psw.hist = z.hist; psw.lookback = z.plb; psw.part_counters = z.counters + 32; psw.max_parts = z.pparts;
     psw.prezeroed = true;
     psw.spin_limit = c->spin_limit;
-    if (n_bound > z.pparts * 1024) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
+    if (sort_parts(n_bound) > z.pparts) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
     FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
                              P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
                              &alt));
   }
   uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
   if (values_out) *values_out = values;
-  mark(e, 5);  // the ranges came with the tile scan: an empty stage
   mark(e, 6);
   // with the bitmap the lists hold depth ranks into the rank-ordered copies
   FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values,
@@ -689,23 +696,117 @@ fs4d_status read_pairs(fs4d_ctx* c, const uint32_t* d_num_pairs, long long* K) {
   return FS4D_OK;
 }
 
+// One pair-sort pass counts at most 2^30 - 1 pairs (30-bit look-back values).  A
+// frame with more pairs renders in horizontal bands of tile rows: each band is a
+// frame of its own on the same deformed Gaussians, with the camera's principal
+// point moved by the band's offset (a whole number of tiles, so every pixel keeps
+// its tile), composited into the band's rows of the image.
+constexpr long long kMaxBandPairs = (1ll << 30) - 1;
+
+// Adds the stage times of the pass that just ended (timing on) to c->stage_acc.
+fs4d_status add_stage_times(fs4d_ctx* c, bool with_deform) {
+  if (!c->timing) return FS4D_OK;
+  FS4D_CUDA(c, cudaEventSynchronize(c->ev[7]));
+  const int from[6] = {0, 1, 2, 3, 5, 6}, to[6] = {1, 2, 3, 4, 6, 7};
+  for (int k = with_deform ? 0 : 1; k < 6; ++k) {
+    float ms = 0.f;
+    FS4D_CUDA(c, cudaEventElapsedTime(&ms, c->ev[from[k]], c->ev[to[k]]));
+    c->stage_acc[k] += ms;
+  }
+  return FS4D_OK;
+}
+
+// Bands of tile rows over the deformed Gaussians already in the work memory.
+fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t, int n_bands,
+                         float* d_image, float* d_t_final, int32_t* d_n_contrib) {
+  const int rows = tiles_of(cam->height), tx = tiles_of(cam->width);
+  n_bands = std::max(1, std::min(n_bands, rows));
+  std::vector<std::pair<int, int>> todo;  // tile-row ranges [r0, r1), taken from the back
+  for (int b = n_bands - 1; b >= 0; --b) todo.push_back({rows * b / n_bands, rows * (b + 1) / n_bands});
+  long long total = 0;
+  int done = 0;
+  fs4d_status st;
+  while (!todo.empty()) {
+    const std::pair<int, int> band = todo.back();
+    todo.pop_back();
+    const int r0 = band.first, r1 = band.second;
+    fs4d_camera bc = *cam;
+    bc.height = std::min(cam->height, kTile * r1) - kTile * r0;
+    bc.cy = cam->cy - (float)(kTile * r0);
+    if ((st = ensure_work(c, s->n, tx * (r1 - r0), c->w.cap_pairs)) != FS4D_OK) return st;
+    if ((st = frame_front(env_of(c), s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+      return st;
+    long long K = 0;
+    if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
+    if (K > c->band_pairs) {
+      if (r1 - r0 == 1) return fail(c, FS4D_ERR_CAPACITY, "one tile row of the frame holds more pairs than a band may");
+      const int mid = (r0 + r1) / 2;
+      todo.push_back({mid, r1});
+      todo.push_back({r0, mid});
+      continue;
+    }
+    if (K > c->w.cap_pairs) {
+      if ((st = ensure_work(c, s->n, tx * (r1 - r0), std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
+      if ((st = frame_front(env_of(c), s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+        return st;
+    }
+    const size_t off = (size_t)kTile * r0 * cam->width;
+    if ((st = frame_back(c, bc, K, d_image + 3 * off, d_t_final ? d_t_final + off : nullptr,
+                         d_n_contrib ? d_n_contrib + off : nullptr)) != FS4D_OK)
+      return st;
+    if ((st = add_stage_times(c, false)) != FS4D_OK) return st;
+    total += K;
+    ++done;
+  }
+  c->last_pairs = total;
+  c->last_bands = done;
+  // the next frame of this scene and size starts with as many bands, unless one would do
+  c->band_scene = s->id; c->band_w = cam->width; c->band_h = cam->height;
+  c->band_hint = total > c->band_pairs ? done : 0;
+  c->stage_acc_valid = c->timing;
+  return FS4D_OK;
+}
+
 // offsets: the frame will be saved for a backward
 fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t, float* d_image,
                         float* d_t_final, int32_t* d_n_contrib, bool offsets = false) {
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   fs4d_status st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs);
   if (st != FS4D_OK) return st;
+  std::fill(c->stage_acc, c->stage_acc + 6, 0.f);
+  c->stage_acc_valid = false;
+  c->last_bands = 1;
+  if (!offsets && c->band_hint > 1 && c->band_scene == s->id && c->band_w == cam->width && c->band_h == cam->height) {
+    // the last frame of this scene and size needed bands: deform, then bands straight away
+    mark(c, 0);
+    DeformArgs da = deform_args(s, nullptr, t, 1, P<float>(c->w.dmeans), P<float>(c->w.dquats), P<float>(c->w.dscales));
+    if ((st = run_deform(c, s, prec, da)) != FS4D_OK) return st;
+    mark(c, 1);
+    if (c->timing) {
+      FS4D_CUDA(c, cudaEventSynchronize(c->ev[1]));
+      FS4D_CUDA(c, cudaEventElapsedTime(&c->stage_acc[0], c->ev[0], c->ev[1]));
+    }
+    return render_bands(c, s, prec, cam, t, c->band_hint, d_image, d_t_final, d_n_contrib);
+  }
   st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
   if (st != FS4D_OK) return st;
   long long K = 0;
   if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
-  if (K >= 0xffffffffll) return fail(c, FS4D_ERR_CAPACITY, "more than 2^32-1 tile pairs in one frame");
+  if (K > c->band_pairs) {
+    if (offsets) return fail(c, FS4D_ERR_CAPACITY, "a frame saved for the backward must fit one band of tile pairs");
+    if ((st = add_stage_times(c, true)) != FS4D_OK) return st;
+    // K saturates at 2^32 - 1; a band that still holds too many pairs is split again
+    const long long per = std::max(c->band_pairs / 2, 1ll);
+    return render_bands(c, s, prec, cam, t, (int)std::min<long long>((K + per - 1) / per, 1 << 20), d_image,
+                        d_t_final, d_n_contrib);
+  }
   if (K > c->w.cap_pairs) {
-    if ((st = ensure_work(c, s->n, n_tiles, K + K / 4)) != FS4D_OK) return st;
+    if ((st = ensure_work(c, s->n, n_tiles, std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
     st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
     if (st != FS4D_OK) return st;
   }
   c->last_pairs = K;
+  c->last_bands = 1;
   return frame_back(c, *cam, K, d_image, d_t_final, d_n_contrib);
 }
 
@@ -871,6 +972,7 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
   s->resident = acc;
   std::lock_guard<std::mutex> lock(c->mu);
   const int id = c->next_id++;
+  s->id = id;
   c->scenes[id] = s;
   *out = id;
   return FS4D_OK;
@@ -1018,6 +1120,7 @@ fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec,
   FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
   const long long K = (long long)c->h_pinned[0];
   c->last_pairs = K;
+  c->last_bands = 1;
   if (K <= cap) return FS4D_OK;
   st = render_sync(c, s, prec, cam, t, P<float>(img), nullptr, nullptr);
   if (st != FS4D_OK) return st;
@@ -1081,6 +1184,7 @@ fs4d_status fs4d_render_host_batch(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision
   for (int k = 0; k < n; ++k) {
     const long long K = (long long)(c->h_pairs[k] & 0xffffffffull);
     c->last_pairs = K;
+    c->last_bands = 1;
     if (K <= cap) continue;
     if ((st = render_sync(c, s, prec, &cams[k], ts[k], P<float>(img), nullptr, nullptr)) != FS4D_OK) return st;
     FS4D_CUDA(c, cudaMemcpyAsync(h_images[k], img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1136,8 +1240,12 @@ fs4d_status fs4d_stage_times(fs4d_ctx* c, float* h_ms) {
   if (!c || !h_ms) return FS4D_ERR_INVALID_ARG;
   if (!c->ev[0]) return fail(c, FS4D_ERR_INVALID_ARG, "stage_times: timing was never enabled");
   DeviceGuard g(c->device);
+  if (c->stage_acc_valid) {  // a frame rendered in bands: the sum over its passes
+    for (int k = 0; k < 6; ++k) h_ms[k] = c->stage_acc[k];
+    return FS4D_OK;
+  }
   FS4D_CUDA(c, cudaEventSynchronize(c->ev[7]));
-  const int from[6] = {0, 1, 2, 4, 5, 6}, to[6] = {1, 2, 3, 5, 6, 7};
+  const int from[6] = {0, 1, 2, 3, 5, 6}, to[6] = {1, 2, 3, 4, 6, 7};
   for (int k = 0; k < 6; ++k) FS4D_CUDA(c, cudaEventElapsedTime(&h_ms[k], c->ev[from[k]], c->ev[to[k]]));
   return FS4D_OK;
 }
@@ -1295,6 +1403,19 @@ fs4d_status fs4d_set_binning(fs4d_ctx* c, int32_t mode) {
 fs4d_status fs4d_last_binning(const fs4d_ctx* c, int32_t* mode) {
   if (!c || !mode) return FS4D_ERR_INVALID_ARG;
   *mode = c->last_binning;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_set_band_pairs(fs4d_ctx* c, int64_t max_pairs) {
+  if (!c || max_pairs < 0) return FS4D_ERR_INVALID_ARG;
+  c->band_pairs = max_pairs == 0 ? kMaxBandPairs : std::min<long long>(max_pairs, kMaxBandPairs);
+  c->band_hint = 0;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_last_bands(const fs4d_ctx* c, int32_t* bands) {
+  if (!c || !bands) return FS4D_ERR_INVALID_ARG;
+  *bands = c->last_bands;
   return FS4D_OK;
 }
 

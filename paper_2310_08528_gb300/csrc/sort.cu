@@ -11,6 +11,8 @@
 // depths (32 bits in 4 passes; a pass whose digit is the same for every key exits
 // at once) and, on the key-emission route, the pairs on their tile bits only (the
 // pairs are emitted in depth order, so 2500 tiles sort 12 bits in 2 passes).
+#include <algorithm>
+
 #include "sync_util.cuh"
 
 namespace fs4d {
@@ -266,8 +268,12 @@ int device_sm_count() {
   }
   return v;
 }
-// Partitions a sort of n keys may use (the small-partition count: an upper bound).
-long long sort_parts(long long n) { return (n + kPartPairsSmall - 1) / kPartPairsSmall; }
+// Partitions a sort of n keys may use: small partitions up to 2^19 keys, large
+// ones above (the look-back tables are sized by this).
+long long sort_parts(long long n) {
+  const long long small = (std::min(n, 1ll << 19) + kPartPairsSmall - 1) / kPartPairsSmall;
+  return std::max(small, (n + kPartPairs - 1) / kPartPairs);
+}
 
 cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned long long* keys_alt,
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,

@@ -27,8 +27,8 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_render_host", "fs4d_render_host_batch", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_sort_pairs_noalloc_status",
-           "fs4d_composite", "fs4d_set_wait_limit")
-STAGES = ("deform", "project", "scan_emit", "sort", "ranges", "composite")
+           "fs4d_composite", "fs4d_set_wait_limit", "fs4d_last_bands", "fs4d_set_band_pairs")
+STAGES = ("deform", "project", "depth_sort", "binning", "sort", "composite")
 
 
 class Fs4dError(RuntimeError):
@@ -90,6 +90,8 @@ def library(path: str = LIB_PATH):
         "fs4d_frame_free": [vp, vp],
         "fs4d_frame_pairs": [vp, C.POINTER(i64)],
         "fs4d_last_pairs": [vp, C.POINTER(i64)],
+        "fs4d_last_bands": [vp, C.POINTER(i32)],
+        "fs4d_set_band_pairs": [vp, i64],
         "fs4d_set_binning": [vp, i32],
         "fs4d_last_binning": [vp, C.POINTER(i32)],
         "fs4d_set_stage_timing": [vp, i32],
@@ -304,6 +306,17 @@ class Context:
         k = C.c_int64()
         self.call("fs4d_last_pairs", C.byref(k))
         return k.value
+
+    def last_bands(self) -> int:
+        """Bands of tile rows the last frame was rendered in (1 unless it had more
+        tile pairs than one pair-sort pass counts)."""
+        b = C.c_int32()
+        self.call("fs4d_last_bands", C.byref(b))
+        return b.value
+
+    def set_band_pairs(self, max_pairs: int) -> None:
+        """Most tile pairs one band of a frame may hold (0 = default, 2^30 - 1)."""
+        self.call("fs4d_set_band_pairs", int(max_pairs))
 
     def set_binning(self, mode: int) -> None:
         """BINNING_AUTO (tile bitmap when it fits) or BINNING_SORT (keys + radix sort)."""

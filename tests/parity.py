@@ -38,6 +38,34 @@ def _toggled(base, gs, mask, dbits):
     return np.array(sorted(s, key=lambda g: (int(dbits[g]), g)), np.uint32)
 
 
+def pixel_matches(value, px, py, base, gs, proj, dbits, tol, rel_tol, depth_tol, T=None, nc=None):
+    """Whether `value` (with T, nc if given) equals, within tol, one of the oracle's
+    outcomes for pixel (px, py) over its tile list `base`, with the Gaussians gs
+    (uncertain members of the tile) in or out of the list."""
+    for mask in range(1 << len(gs)):
+        lst = base if mask == 0 else _toggled(base, gs, mask, dbits)
+        outs = oracle.pixel_outcomes(lst, px, py, proj, rel_tol, depth_tol)
+        if outs is None:
+            continue
+        good = np.abs(outs[:, :3] - value).max(1) <= tol
+        if T is not None:
+            good &= np.abs(outs[:, 3] - T) <= tol
+        if nc is not None:
+            good &= outs[:, 4] == nc
+        if good.any():
+            return True
+    return False
+
+
+def tile_list(proj, dbits, tiles_x, t_id):
+    """The oracle's list of tile t_id: the Gaussians whose rectangle holds it, in
+    (float32 depth, index) order."""
+    r = proj["rect"]
+    tx, ty = t_id % tiles_x, t_id // tiles_x
+    g = np.flatnonzero((r[:, 0] <= tx) & (tx < r[:, 2]) & (r[:, 1] <= ty) & (ty < r[:, 3]))
+    return g[np.lexsort((g, dbits[g]))].astype(np.uint32)
+
+
 def check_frame(img, fr, T=None, nc=None, tol=1e-4, rel_tol=5e-5, px_tol=2e-4, depth_tol=1e-6,
                 max_members=4):
     """Checks every pixel of img ([H][W][3]; T, nc optional) against the oracle
@@ -51,27 +79,15 @@ def check_frame(img, fr, T=None, nc=None, tol=1e-4, rel_tol=5e-5, px_tol=2e-4, d
         off |= np.abs(T - fr["T"]) > tol
     if nc is not None:
         off |= nc != fr["nc"]
-    members = oracle.uncertain_memberships(p, W, H, px_tol, tile) if off.any() else {}
+    members = oracle.uncertain_memberships(p, W, H, px_tol, tile)
     resolved = unresolved = 0
     worst = 0.0
     for py, px in zip(*np.nonzero(off)):
         t_id = (py // tile) * tx + px // tile
         base = vals[ranges[t_id, 0]:ranges[t_id, 1]]
         gs = members.get(int(t_id), [])[:max_members]
-        ok = False
-        for mask in range(1 << len(gs)):
-            lst = base if mask == 0 else _toggled(base, gs, mask, dbits)
-            outs = oracle.pixel_outcomes(lst, px, py, p, rel_tol, depth_tol)
-            if outs is None:
-                continue
-            good = np.abs(outs[:, :3] - img[py, px]).max(1) <= tol
-            if T is not None:
-                good &= np.abs(outs[:, 3] - T[py, px]) <= tol
-            if nc is not None:
-                good &= outs[:, 4] == nc[py, px]
-            if good.any():
-                ok = True
-                break
+        ok = pixel_matches(img[py, px], px, py, base, gs, p, dbits, tol, rel_tol, depth_tol,
+                           None if T is None else T[py, px], None if nc is None else nc[py, px])
         if ok:
             resolved += 1
         else:

@@ -651,3 +651,98 @@ def test_pixel_outcomes_limit_on_flips():
     rows = [(0.5, 0.5, 0.1, 0.0, 0.1, 0.2, 1, 1, 1, 3.0)] * 4
     assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=2) is None
     assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=3).shape == (8, 5)
+
+
+# --------------------------------------------------------------------- training step (Sec. 4.3, App. A)
+
+def test_l1_loss_closed_form():
+    img = np.array([[0.5, 0.2, 0.9], [0.1, 0.1, 0.4]])
+    tgt = np.array([[0.4, 0.2, 1.0], [0.3, 0.0, 0.4]])
+    loss, g = oracle.l1_loss(img, tgt)
+    assert loss == pytest.approx((0.1 + 0 + 0.1 + 0.2 + 0.1 + 0) / 6, abs=1e-15)
+    np.testing.assert_array_equal(g * 6, [[1, 0, -1], [-1, 1, 0]])
+
+
+def _plane_scene(fill):
+    """A scene whose every plane value is fill(level, plane, b, a, c)."""
+    s = sg.make_object(0, n=10, res_spatial=(4, 6), res_time=5, h=16)
+    out = []
+    for lvl, R in enumerate(s.res_spatial):
+        for p, (ax, bx) in enumerate([(0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3)]):
+            Ra = R if ax < 3 else s.res_time
+            Rb = R if bx < 3 else s.res_time
+            b, a, c = np.meshgrid(np.arange(Rb), np.arange(Ra), np.arange(s.feat_dim), indexing="ij")
+            out.append(fill(lvl, p, b, a, c).astype(np.float32).ravel())
+    s.planes = np.concatenate(out)
+    return s
+
+
+def test_tv_loss_of_linear_planes_closed_form():
+    """P = alpha a + beta b (+ any per-channel offset): every neighbour difference
+    along a is alpha and along b is beta, so each plane adds alpha^2 + beta^2; 12
+    planes in all; the gradient vanishes at interior cells."""
+    al, be = 0.25, -0.5
+    s = _plane_scene(lambda lvl, p, b, a, c: al * a + be * b + 0.0625 * c)  # exact in float32
+    loss, g = oracle.tv_loss(s, 0.3)
+    assert loss == pytest.approx(0.3 * 12 * (al ** 2 + be ** 2), rel=1e-12)
+    P0 = s.res_spatial[0]
+    h = s.feat_dim
+    g0 = g[:P0 * P0 * h].reshape(P0, P0, h)     # level 0, plane xy
+    np.testing.assert_allclose(g0[1:-1, 1:-1], 0.0, atol=1e-15)
+    # a corner cell (b=0, a=0): -2 alpha / n_a - 2 beta / n_b per channel, times the weight
+    na, nb = P0 * (P0 - 1) * h, (P0 - 1) * P0 * h
+    np.testing.assert_allclose(g0[0, 0], 0.3 * (-2 * al / na - 2 * be / nb), rtol=1e-12)
+
+
+def test_tv_loss_of_checkerboard_planes_closed_form():
+    """P = (-1)^(a+b): every neighbour difference is +-2 (squared 4), so each plane
+    adds 8; an interior cell's gradient is w * 8 P (1/n_a + 1/n_b) per channel."""
+    s = _plane_scene(lambda lvl, p, b, a, c: (-1.0) ** (a + b))
+    loss, g = oracle.tv_loss(s, 1.0)
+    assert loss == pytest.approx(12 * 8.0, rel=1e-12)
+    P0, h = s.res_spatial[0], s.feat_dim
+    na, nb = P0 * (P0 - 1) * h, (P0 - 1) * P0 * h
+    g0 = g[:P0 * P0 * h].reshape(P0, P0, h)
+    np.testing.assert_allclose(g0[1, 2], 8.0 * (-1.0) ** 3 * (1 / na + 1 / nb), rtol=1e-12)
+
+
+def test_tv_gradient_matches_central_differences():
+    s = _plane_scene(lambda lvl, p, b, a, c: np.sin(0.7 * a + 1.3 * b + 0.1 * c + p + lvl))
+    _, g = oracle.tv_loss(s, 0.7)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(s.planes.size, 12, replace=False):
+        x0 = s.planes[i]
+        h = 2.0 ** -10
+        s.planes[i] = x0 + h
+        lp, _ = oracle.tv_loss(s, 0.7)
+        s.planes[i] = x0 - h
+        lm, _ = oracle.tv_loss(s, 0.7)
+        s.planes[i] = x0
+        assert (lp - lm) / (2 * h) == pytest.approx(g[i], rel=1e-6, abs=1e-12)
+
+
+def test_lr_schedule_endpoints_and_geometric_midpoint():
+    assert oracle.lr_at(1.6e-3, 1.6e-4, 0, 1000) == pytest.approx(1.6e-3, rel=1e-15)
+    assert oracle.lr_at(1.6e-3, 1.6e-4, 1000, 1000) == pytest.approx(1.6e-4, rel=1e-13)
+    assert oracle.lr_at(1.6e-3, 1.6e-4, 5000, 1000) == pytest.approx(1.6e-4, rel=1e-13)
+    assert oracle.lr_at(1.6e-3, 1.6e-4, 500, 1000) == pytest.approx(math.sqrt(1.6e-3 * 1.6e-4), rel=1e-13)
+
+
+def test_adam_against_torch_optim_adam():
+    """Three bias-corrected Adam steps against torch.optim.Adam; the first step
+    moves each parameter by lr * g / (|g| + eps)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    p = rng.normal(size=50)
+    grads = [rng.normal(size=50) for _ in range(3)]
+    tp = torch.tensor(p.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    m, v = np.zeros(50), np.zeros(50)
+    q = p.copy()
+    for k, g in enumerate(grads):
+        oracle.adam_step(q, g.copy(), m, v, 1e-2, 0.9, 0.999, 1e-15, k + 1)
+        if k == 0:
+            np.testing.assert_allclose(p - q, 1e-2 * g / (np.abs(g) + 1e-15), rtol=1e-12)
+        tp.grad = torch.tensor(g)
+        opt.step()
+    np.testing.assert_allclose(q, tp.detach().numpy(), rtol=1e-12, atol=1e-15)
