@@ -178,12 +178,13 @@ def stage_work(stage: str, n: int, K: int, pixels: int, passes: int, prec: str, 
             # Gaussian; per pair one 4 B bit-word update (read + write), the word read and cleared by the
             # row walk and the rank written
             return [("hbm", bands * n * (4 + 16 + 72) + K * (8 + 4 + 4 + 4), "B")]
-        # emission: order, rect, depth in + offset out per Gaussian, 12 B per pair out
-        return [("hbm", bands * n * (4 + 16 + 4 + 4) + K * 12, "B")]
+        # emission: order, rect, depth in + offset out per Gaussian; one 8 B (tile | index) word per pair
+        # out (frames that keep no backward state sort these words without a value array)
+        return [("hbm", bands * n * (4 + 16 + 4 + 4) + K * 8, "B")]
     if stage == "sort":
         if bitmap:
             return []  # no pair sort: the bitmap rows list each tile's Gaussians in depth order
-        return [("hbm", passes * K * 24, "B")]                         # read + write 12 B per pair per pass
+        return [("hbm", passes * K * 16, "B")]                         # read + write 8 B per pair per pass
     if stage == "composite":
         # gather (idx + xy, conic/opacity, rgb) per visited pair and the rgb write per pixel; ~15 FLOP per
         # tested (pixel, Gaussian) up to each pixel's last contributor
@@ -312,7 +313,7 @@ def training_bench(ctx, fs4d, torch, sid, scene, stream, steps=10, warmup=3):
                   "mlp": scene.mlp.shape}
         g = {k: torch.zeros(v, device="cuda") for k, v in shapes.items()}
         dl = torch.randn((HEIGHT, WIDTH, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-        fwd, bwd = [], []
+        fwd, bwd, parts = [], [], []
         with torch.cuda.stream(stream):
             for i in range(warmup + steps):
                 cam, t = views(i, 0, 1)
@@ -327,11 +328,67 @@ def training_bench(ctx, fs4d, torch, sid, scene, stream, steps=10, warmup=3):
                 if i >= warmup:
                     fwd.append(e0.elapsed_time(e1))
                     bwd.append(e1.elapsed_time(e2))
+            # per-kernel times of the backward, from a separate timed pass
+            ctx.set_stage_timing(True)
+            for i in range(3):
+                cam, t = views(i, 0, 1)
+                _, frame = ctx.render_saved(sid, cam, t, fs4d.FP32)
+                ctx.render_backward(frame, dl, g)
+                parts.append(ctx.backward_times())
+                ctx.frame_free(frame)
+            ctx.set_stage_timing(False)
         f, b = float(np.median(fwd)), float(np.median(bwd))
+        per = {k: float(np.median([p[k] for p in parts])) for k in parts[0]}
         return {"workload": "one view of the 800x800 / 100k object, dL/dI ~ N(0,1), gradients of every parameter "
                             "group", "steps": steps, "forward_saved_ms": f, "backward_ms": b, "step_ms": f + b,
-                "views_per_s": 1e3 / (f + b),
+                "views_per_s": 1e3 / (f + b), "backward_kernels_ms": per,
                 "note": "the forward keeps the backward's state (sort binning, emission offsets, copies)"}
+    except Exception as exc:  # the headline line must still be printed
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def training_c2_bench(ctx, fs4d, torch, stream, steps=12, warmup=3):
+    """Config 2's training step: the Neu3D-shaped room (300k Gaussians in a 6x4x6
+    box, SH 3, HexPlane {64,128} x 150 x 32) at 1352x1014 from forward-facing
+    cameras, L1 against targets rendered from the same scene with the planes
+    perturbed by N(0, 0.01), BF16 forward, float32 backward, TV loss and Adam
+    (fs4d_train_step), timed with CUDA events per step."""
+    from paper_2310_08528_gb300 import scenegen as sg
+    try:
+        scene = sg.make_room(0)
+        sid = ctx.load_scene(scene)
+        sid_t = ctx.load_scene(sg.perturb_planes(scene, 0))
+        cams = sg.forward_cameras(8, seed=0)
+        ts = [float(k) / 149.0 for k in range(0, 150, 19)]
+        with torch.cuda.stream(stream):
+            targets = [ctx.render(sid_t, cams[i % 8], ts[i % len(ts)], fs4d.FP32) for i in range(8)]
+        ctx.unload_scene(sid_t)
+        tr = fs4d.Trainer(ctx, sid, warmup + steps)
+        ms, l1s = [], []
+        losses = torch.zeros(2, device="cuda")
+        with torch.cuda.stream(stream):
+            for i in range(warmup + steps):
+                e0, e1 = _events(torch)
+                e0.record(stream)
+                tr.step(cams[i % 8], ts[i % len(ts)], targets[i % 8], fs4d.BF16, losses)
+                e1.record(stream)
+                stream.synchronize()
+                l1s.append(float(losses[0].item()))
+                if i >= warmup:
+                    ms.append(e0.elapsed_time(e1))
+            ctx.set_stage_timing(True)
+            tr.step(cams[0], ts[0], targets[0], fs4d.BF16, losses)
+            fwd = ctx.stage_times()
+            bwd = ctx.backward_times()
+            ctx.set_stage_timing(False)
+        tr.close()
+        ctx.unload_scene(sid)
+        t = float(np.median(ms))
+        return {"workload": "room: N=300k (64-cluster mixture in a 6x4x6 box), SH 3, HexPlane {64,128} x 150 x 32, "
+                            "1352x1014 forward-facing cameras, L1 to targets rendered with planes + N(0,0.01), "
+                            "TV weight 1e-4, Adam (App. A rates)",
+                "steps": steps, "step_ms": t, "steps_per_s": 1e3 / t, "forward": "bf16", "backward": "fp32",
+                "l1_first": l1s[0], "l1_last": l1s[-1], "forward_stages_ms": fwd, "backward_kernels_ms": bwd}
     except Exception as exc:  # the headline line must still be printed
         return {"error": f"{type(exc).__name__}: {exc}"}
 
@@ -737,6 +794,7 @@ def main():
         line["bf16_vs_fp32"] = bf16_vs_fp32(ctx, fs4d, torch, sid, scene, stream)
     if not args.no_training:
         line["training"] = training_bench(ctx, fs4d, torch, sid, scene, stream)
+        line["training_c2"] = training_c2_bench(ctx, fs4d, torch, stream)
     if not args.no_serving:
         line["serving"] = serving_bench(ctx, fs4d, torch)
     if not args.no_stress:

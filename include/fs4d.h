@@ -170,6 +170,20 @@ FS4D_API fs4d_status fs4d_unload_scene(fs4d_ctx* ctx, fs4d_scene_id id);
  * Re-derives the BF16 and transposed MLP copies.  Synchronises the stream. */
 FS4D_API fs4d_status fs4d_update_scene(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_scene_desc* desc,
                                        int32_t on_device);
+/* Copy the scene's current parameters (after any training steps) into the
+ * non-NULL arrays of *out, in the layouts of fs4d_scene_desc: HOST memory when
+ * to_device == 0, else DEVICE memory.  Synchronises the context's stream. */
+FS4D_API fs4d_status fs4d_read_scene(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_grads* out, int32_t to_device);
+/* Write the scene (sizes, box and current parameters) to a binary file: an
+ * 8-byte magic "FS4DSCN1", ten int32 (n, sh_degree, n_levels, res_spatial[4],
+ * res_time, feat_dim, mlp_width), the box (6 float32), the arrays means,
+ * log_scales, quats, opacity_logits, sh, planes, mlp as little-endian float32,
+ * and a 64-bit FNV-1a checksum of everything after the magic.  The file is
+ * written under path + ".tmp" and renamed, so a reader never sees half a file. */
+FS4D_API fs4d_status fs4d_save_scene(fs4d_ctx* ctx, fs4d_scene_id id, const char* path);
+/* Load a file written by fs4d_save_scene as a new scene (FS4D_ERR_NOT_FOUND if it
+ * cannot be opened, FS4D_ERR_INVALID_ARG if it is not a complete scene file). */
+FS4D_API fs4d_status fs4d_load_scene_file(fs4d_ctx* ctx, const char* path, fs4d_scene_id* out);
 /* Bytes the scene holds resident on the device, and the per-frame work memory a
  * render at (width, height) needs with `pairs_per_gaussian` tile pairs per
  * Gaussian (used for admission by device-memory footprint). */
@@ -197,6 +211,17 @@ FS4D_API fs4d_status fs4d_deform(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision
  * The number of tile pairs is read back once per call (one stream sync). */
 FS4D_API fs4d_status fs4d_render(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
                         float* d_image, float* d_t_final, int32_t* d_n_contrib, fs4d_frame** saved);
+
+/* Composition (Sec. 5.4): one frame of several loaded scenes, I = S(M, G') with
+ * G' = {G'_1, ..., G'_n} the union of every scene's Gaussians deformed at t (each
+ * by its own HexPlane and MLP), binned, sorted and composited together, so that
+ * their Gaussians interleave in depth.  h_shifts (host [n_scenes][3], or NULL)
+ * translates each scene in the world (its SH colour sees the view direction from
+ * the camera to the translated mean).  Outputs as fs4d_render; the frame must fit
+ * one band of tile pairs (FS4D_ERR_CAPACITY otherwise). */
+FS4D_API fs4d_status fs4d_render_composed(fs4d_ctx* ctx, const fs4d_scene_id* ids, const float* h_shifts,
+                                          int32_t n_scenes, fs4d_precision prec, const fs4d_camera* cam, float t,
+                                          float* d_image, float* d_t_final, int32_t* d_n_contrib);
 
 /* The same frame end to end with HOST buffers: the camera and t go host->device,
  * the image comes back into h_image [height][width][3] (pinned memory is fastest).
@@ -259,6 +284,57 @@ FS4D_API fs4d_status fs4d_last_binning(const fs4d_ctx* ctx, int32_t* mode);
  * rows, each stage summed over the bands). */
 FS4D_API fs4d_status fs4d_set_stage_timing(fs4d_ctx* ctx, int32_t enable);
 FS4D_API fs4d_status fs4d_stage_times(fs4d_ctx* ctx, float* h_ms);
+/* With stage timing enabled, the last fs4d_render_backward's stages: h_ms[4] =
+ * compositing backward, projection + SH backward, MLP + HexPlane backward,
+ * weight-gradient reductions (milliseconds; waits for that backward). */
+FS4D_API fs4d_status fs4d_backward_times(fs4d_ctx* ctx, float* h_ms);
+
+/* ---------------------------------------------------------------- training
+ * One training step (Sec. 4.3) on a loaded scene, on the device: render the view
+ * keeping the backward's state, the loss L = |I^ - I| + L_tv, its gradient with
+ * respect to every parameter group (the backward of fs4d_render_backward plus
+ * the TV gradient on the planes), and one Adam update of each group at a learning
+ * rate decayed over the run (App. A gives the HexPlane rate 1.6e-3 -> 1.6e-4 and
+ * the MLP rate 1.6e-4 -> 1.6e-5).  The scene's parameters are updated in place and
+ * its derived copies (BF16 planes and MLP operands) refreshed, so the next frame
+ * of any call renders the updated scene.  Readings where the paper is silent:
+ *  - |I^ - I| is the mean absolute difference over every pixel and channel;
+ *  - L_tv = tv_weight x sum over levels and planes of the mean squared difference
+ *    of neighbouring cells along each of the plane's two axes (every channel);
+ *  - the decay is log-linear: lr(k) = lr0 (lr1 / lr0)^min(1, k / total_steps);
+ *  - Adam is bias-corrected (step k + 1 for the k-th update, k from 0). */
+typedef struct fs4d_train_config {
+  int32_t total_steps;     /* steps over which every rate decays from [0] to [1] */
+  float lr_means[2];       /* initial and final learning rate of each group */
+  float lr_log_scales[2];
+  float lr_quats[2];
+  float lr_opacity[2];
+  float lr_sh_dc[2];       /* the degree-0 SH coefficients */
+  float lr_sh_rest[2];     /* the higher-degree SH coefficients */
+  float lr_planes[2];
+  float lr_mlp[2];
+  float beta1, beta2, eps; /* Adam */
+  float tv_weight;         /* weight of L_tv */
+} fs4d_train_config;
+typedef struct fs4d_trainer fs4d_trainer;
+
+/* Optimiser state (Adam moments and gradients of every group, zeroed) for scene
+ * `id` of the context.  The scene must stay loaded while the trainer exists. */
+FS4D_API fs4d_status fs4d_train_create(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_train_config* cfg,
+                                       fs4d_trainer** out);
+/* One step on view (cam, t) against d_target (device [height][width][3]): the
+ * frame renders with `prec` (the backward is float32 either way).  d_losses
+ * (device float[2], or NULL for the trainer's own) receives the L1 and TV losses
+ * of this step's frame, before the update.  One host synchronisation (the
+ * frame's pair count).  A frame whose pairs exceed one band returns
+ * FS4D_ERR_CAPACITY before any update. */
+FS4D_API fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, const fs4d_camera* cam, float t,
+                                     const float* d_target, float* d_losses);
+/* The L1 and TV losses of the last step into h_losses[2] (when the step wrote
+ * them to the trainer's own buffer); synchronises the context's stream. */
+FS4D_API fs4d_status fs4d_train_losses(fs4d_trainer* tr, float* h_losses);
+FS4D_API fs4d_status fs4d_train_steps_done(const fs4d_trainer* tr, int64_t* steps);
+FS4D_API fs4d_status fs4d_train_destroy(fs4d_trainer* tr);
 
 /* ---------------------------------------------------------------- serving
  * A continuous-batching request loop over the context's resident scenes, run by

@@ -50,7 +50,7 @@ class OrcProjected(C.Structure):
 
 class OrcGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes",
-                                          "mlp")]
+                                          "mlp", "planes_abs")]
 
 
 def lib():
@@ -245,6 +245,32 @@ def render(scene, cam, t: float, deform: bool = True, tile: int = 16):
     return img, T, nc, mg, int(K)
 
 
+def project_composed(scenes, shifts, cam, t: float, deform: bool = True, tile: int = 16):
+    """Composition (Sec. 5.4): G' = {G'_1, ..., G'_n}, every scene deformed at t by
+    its own field, translated by its shift, and projected; the projected sets are
+    concatenated in scene order (Gaussian index = offset of its scene + index)."""
+    parts = []
+    for scene, sh in zip(scenes, shifts if shifts is not None else [None] * len(scenes)):
+        if deform:
+            X, Q, S = _deform_fn(scene, t)
+        else:
+            X = np.array(scene.means, np.float64)
+            Q = np.array(scene.quats, np.float64)
+            S = np.array(scene.log_scales, np.float64)
+        if sh is not None:
+            X = X + np.asarray(sh, np.float64)[None, :]
+        parts.append(project(scene, cam, X, Q, S, tile=tile))
+    return {k: np.ascontiguousarray(np.concatenate([p[k] for p in parts])) for k in parts[0]}
+
+
+def composite_projected(proj, cam, tile: int = 16):
+    """Bin, sort and composite a projected set: (image, T, n_contrib, margin, values, ranges)."""
+    tx, ty = (cam.width + tile - 1) // tile, (cam.height + tile - 1) // tile
+    _, vals, ranges = bin_sort(depth_bits(proj["depth"]), proj["rect"], tx, ty)
+    img, T, nc, mg = composite(cam.width, cam.height, ranges, vals, proj, tile=tile)
+    return img, T, nc, mg, vals, ranges
+
+
 def unstable_pixels(scene, cam, t: float, deform: bool = True, px_tol: float = 1e-3, margin_tol: float = 1e-5,
                     tile: int = 16):
     """Pixels whose value a float32 implementation may legitimately decide
@@ -325,13 +351,18 @@ def uncertain_memberships(proj, width: int, height: int, px_tol: float, tile: in
     return out
 
 
-def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16):
-    """Gradients of sum(dl_dimage * image) w.r.t. every scene parameter (float64 dict)."""
+def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16,
+                    plane_terms: bool = False):
+    """Gradients of sum(dl_dimage * image) w.r.t. every scene parameter (float64 dict).
+    plane_terms: also 'planes_abs', per plane value the sum of the magnitudes of the
+    per-Gaussian terms its gradient adds up."""
     h = _SceneHandle(scene)
     cc = _camera(cam)
     g = dict(means=np.zeros((h.n, 3)), log_scales=np.zeros((h.n, 3)), quats=np.zeros((h.n, 4)),
              opacity_logits=np.zeros(h.n), sh=np.zeros((h.n, h.k, 3)),
              planes=np.zeros(h.arrays["planes"].shape[0]), mlp=np.zeros(h.arrays["mlp"].shape[0]))
+    if plane_terms:
+        g["planes_abs"] = np.zeros(h.arrays["planes"].shape[0])
     G = OrcGrads(**{k: v.ctypes.data for k, v in g.items()})
     rc = lib().orc_render_backward(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile),
                                    np.ascontiguousarray(dl_dimage, np.float64), C.byref(G))
@@ -382,8 +413,8 @@ def train_step(scene, cam, t: float, target, cfg, state, tile: int = 16):
     takes 'sh_dc' for the degree-0 coefficients and 'sh_rest' for the others),
     'total_steps', 'beta1', 'beta2', 'eps', 'tv_weight'.  state: dict with 'step'
     (updates done) and per-group float64 'm', 'v', 'param' (created on the first
-    call from the scene).  Returns (l1, tv); the updated parameters are in
-    state['param']."""
+    call from the scene).  Returns (l1, tv, gradient dict of this step); the
+    updated parameters are in state['param']."""
     if "param" not in state:
         state["param"] = {k: np.array(getattr(scene, k), np.float64) for k in GROUPS}
         state["m"] = {k: np.zeros_like(v) for k, v in state["param"].items()}
@@ -414,7 +445,7 @@ def train_step(scene, cam, t: float, target, cfg, state, tile: int = 16):
             lr = lr_at(*cfg["lr"][grp], k, cfg["total_steps"])
             adam_step(p, gg, m, v, lr, cfg["beta1"], cfg["beta2"], cfg["eps"], step)
     state["step"] = step
-    return l1, tv
+    return l1, tv, g
 
 
 def kind() -> str:

@@ -933,6 +933,12 @@ extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam
             G->planes[off + e01] += gv * (1 - fa[p]) * fb[p];
             G->planes[off + e11] += gv * fa[p] * fb[p];
           }
+          if (G->planes_abs) {  // magnitudes of the same terms (test support: conditioning of the sums)
+            G->planes_abs[off + e00] += std::fabs(gv * (1 - fa[p]) * (1 - fb[p]));
+            G->planes_abs[off + e10] += std::fabs(gv * fa[p] * (1 - fb[p]));
+            G->planes_abs[off + e01] += std::fabs(gv * (1 - fa[p]) * fb[p]);
+            G->planes_abs[off + e11] += std::fabs(gv * fa[p] * fb[p]);
+          }
           const double dv_dfa = (1 - fb[p]) * ((double)Pl[e10] - Pl[e00]) + fb[p] * ((double)Pl[e11] - Pl[e01]);
           const double dv_dfb = (1 - fa[p]) * ((double)Pl[e01] - Pl[e00]) + fa[p] * ((double)Pl[e11] - Pl[e10]);
           const int a = kPlaneAxes[p][0], b = kPlaneAxes[p][1];

@@ -123,6 +123,8 @@ typedef struct orc_grads {
   double* sh;             /* [n][k][3] */
   double* planes;         /* flat, like the scene's planes */
   double* mlp;            /* flat, like the scene's mlp */
+  double* planes_abs;     /* optional: per plane value, the sum over Gaussians of the
+                             magnitudes of the terms its gradient sums (test support) */
 } orc_grads;
 
 int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
@@ -56,9 +57,11 @@ T* P(DevBuf& b) {
 
 struct Scene {
   int id = 0;
+  fs4d_scene_desc shape{};  // the load call's sizes and box (its pointers cleared)
   int n = 0, sh_degree = 0, K = 1;
   DevBuf means, log_scales, quats, opacity_logits, sh;
   DevBuf planes, planes_bf16, mlp, mlp_t, tc_ops, tc_bias;
+  DevBuf derive_tab;  // per MLP value: its places in mlp_t, tc_ops and tc_bias (device-side refresh)
   DevBuf perm;  // deformation work order: Gaussians by Morton code of their canonical mean
   PlaneGeom pg{};
   MlpGeomT mg{};
@@ -102,6 +105,7 @@ struct Work {
   DevBuf bitmap;                           // tile bitmap binning: [tiles][bitmap_words(n)], zero between frames
   DevBuf sxy, sco, srgb;                   // with the bitmap: projected Gaussians in depth-rank order
   bool bmp = false;                        // the frame in flight bins through the bitmap
+  bool packed = false;                     // ... or sorts (tile | index) keys without values
   bool bmp_dirty = false;                  // a frame set bits whose extraction was not launched
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
@@ -189,6 +193,7 @@ struct fs4d_ctx {
   int last_binning = FS4D_BINNING_SORT;
   bool timing = false;
   cudaEvent_t ev[8] = {};        // start, deformed, projected, depth-sorted, binned | pair sort, sorted, composited
+  cudaEvent_t bev[5] = {};       // backward: start, compositing, projection, MLP + planes, weight gradients done
   // fs4d_render_host_batch: image copies overlapped with the next frame
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t slot_rendered[2] = {}, slot_copied[2] = {};
@@ -197,6 +202,7 @@ struct fs4d_ctx {
   uint32_t spin_limit = kSpinLimit;       // polls of a look-back wait (fs4d_set_wait_limit)
   // frames rendered in bands of tile rows (more pairs than one sort pass counts)
   int band_scene = -1, band_w = 0, band_h = 0, band_hint = 0;  // bands the last such frame used
+  std::vector<std::pair<int, int>> band_rows;  // ... and their tile rows (the next frame reuses them)
   int last_bands = 1;
   long long band_pairs = (1ll << 30) - 1;  // most pairs one band may hold (fs4d_set_band_pairs)
   float stage_acc[6] = {};                // stage times summed over a banded frame's passes
@@ -259,6 +265,7 @@ CamParams cam_params(const fs4d_camera& c) {
   p.width = c.width; p.height = c.height;
   p.fx = c.fx; p.fy = c.fy; p.cx = c.cx; p.cy = c.cy; p.znear = c.znear;
   for (int i = 0; i < 12; ++i) p.m[i] = c.world_to_cam[i];
+  p.guard_w = c.width; p.guard_h = c.height;
   return p;
 }
 
@@ -388,6 +395,37 @@ void build_tc_image(const float* src, int hin, int W, MlpGeomTC& tg, std::vector
     for (int j = 0; j < L[3 + 2 * h].out; ++j) bias[320 + col0[h] + j] = src[L[3 + 2 * h].b + j];
 }
 
+// For every value of the source-layout MLP, where transpose_mlp and
+// build_tc_image put it: (mlp_t index, tc_ops byte offset or -1, tc_bias index or
+// -1, 0).  Lets a kernel refresh both derived layouts after the MLP changes on
+// the device.
+std::vector<int4> build_derive_tab(int hin, int W, const MlpGeomT& mg, const MlpGeomTC& tg, bool with_tc) {
+  size_t tot;
+  auto L = src_layers(hin, W, &tot);
+  std::vector<int4> tab(tot, make_int4(0, -1, -1, 0));
+  const int col0[3] = {0, 3, 7};
+  for (int k = 0; k < 8; ++k) {
+    for (int o = 0; o < L[k].out; ++o) {
+      for (int i = 0; i < L[k].in; ++i) tab[L[k].w + (size_t)o * L[k].in + i].x = mg.w[k] + i * L[k].out + o;
+      tab[L[k].b + o].x = mg.b[k] + o;
+    }
+    if (!with_tc) continue;
+    const int h = (k - 2) / 2;  // head of layers 2..7
+    for (int o = 0; o < L[k].out; ++o) {
+      int4& b = tab[L[k].b + o];
+      b.z = k == 0 ? o : k == 1 ? 64 + o : (k % 2 == 0) ? 128 + 64 * h + o : 320 + col0[h] + o;
+      for (int i = 0; i < L[k].in; ++i) {
+        int4& e = tab[L[k].w + (size_t)o * L[k].in + i];
+        if (k == 0) e.y = tg.b1_off + (int)umma_off(o, i, hin);
+        else if (k == 1) e.y = tg.b2_off + (int)umma_off(o, i, 64);
+        else if (k % 2 == 0) e.y = tg.b3_off + (int)umma_off(64 * h + o, i, 64);
+        else e.y = tg.b4_off + (int)umma_off(col0[h] + o, 64 * h + i, 192);
+      }
+    }
+  }
+  return tab;
+}
+
 template <typename T>
 fs4d_status upload(fs4d_ctx* c, DevBuf& b, const T* h, size_t count, size_t* acc) {
   FS4D_CUDA(c, ensure(b, sizeof(T) * std::max<size_t>(count, 1)));
@@ -398,7 +436,7 @@ fs4d_status upload(fs4d_ctx* c, DevBuf& b, const T* h, size_t count, size_t* acc
 
 void free_scene(Scene* s) {
   DevBuf* all[] = {&s->means, &s->log_scales, &s->quats, &s->opacity_logits, &s->sh, &s->planes,
-                   &s->planes_bf16, &s->mlp, &s->mlp_t, &s->tc_ops, &s->tc_bias, &s->perm};
+                   &s->planes_bf16, &s->mlp, &s->mlp_t, &s->tc_ops, &s->tc_bias, &s->perm, &s->derive_tab};
   for (DevBuf* b : all) release(*b);
   delete s;
 }
@@ -510,6 +548,7 @@ struct Env {
   cudaStream_t s;
   uint32_t* status;
   bool timed;
+  int guard_w = 0, guard_h = 0;  // non-zero: the whole frame's size (a band's guard band is the frame's)
 };
 
 Env env_of(fs4d_ctx* c) { return Env{c, &c->w, c->stream, P<uint32_t>(c->status), true}; }
@@ -555,38 +594,74 @@ fs4d_status run_deform(fs4d_ctx* c, Scene* s, fs4d_precision prec, const DeformA
 // Everything of a frame up to (and including) the key emission.
 // offsets: keep each Gaussian's emission offset (the backward's pair slots), which
 // only the key emission produces.
-fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
-                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
-                        bool deform = true, bool offsets = false) {
+// One scene's share of a frame's Gaussian set: its deformed Gaussians and
+// projections sit at [off, off + n) of the work arrays; shift translates the
+// scene in the world (composition, Sec. 5.4: G' = {G'_1, ..., G'_n}).
+struct FramePart {
+  Scene* s;
+  long long off;
+  float shift[3];
+};
+
+long long parts_total(const FramePart* parts, int n_parts) {
+  long long n = 0;
+  for (int i = 0; i < n_parts; ++i) n += parts[i].s->n;
+  return n;
+}
+
+// Everything of a frame up to (and including) the key emission, over the union of
+// the parts' Gaussians.
+fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_precision prec,
+                        const fs4d_camera& shape, const fs4d_camera* d_cam, const float* d_t, float t, long long cap,
+                        bool report, bool deform, bool offsets) {
   fs4d_ctx* c = e.c;
   Work& w = *e.w;
   const cudaStream_t stream = e.s;
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
   const int tile_bits = ceil_log2((long long)tx * ty);
+  const int N = (int)parts_total(parts, n_parts);
   // every buffer the frame needs at zero, in one memset
   FrameZero& z = w.z;
-  frame_zero_layout(s->n, tx * ty, cap, sort_passes(tile_bits), static_cast<unsigned char*>(w.zero.p), &z);
+  frame_zero_layout(N, tx * ty, cap, sort_passes(tile_bits), static_cast<unsigned char*>(w.zero.p), &z);
   if (z.bytes > w.zero.bytes) return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory was not reserved");
   mark(e, 0);
   FS4D_CUDA(c, cudaMemsetAsync(w.zero.p, 0, z.bytes, stream));
   if (deform) {
-    DeformArgs da = deform_args(s, d_t, t, 1, P<float>(w.dmeans), P<float>(w.dquats), P<float>(w.dscales));
-    fs4d_status st = run_deform(c, s, prec, da, stream, e.status);
-    if (st != FS4D_OK) return st;
+    for (int i = 0; i < n_parts; ++i) {
+      const FramePart& q = parts[i];
+      DeformArgs da = deform_args(q.s, d_t, t, 1, P<float>(w.dmeans) + 3 * q.off, P<float>(w.dquats) + 4 * q.off,
+                                  P<float>(w.dscales) + 3 * q.off);
+      fs4d_status st = run_deform(c, q.s, prec, da, stream, e.status);
+      if (st != FS4D_OK) return st;
+    }
   }
   mark(e, 1);
-  ProjectArgs pa{};
-  pa.n = s->n;
-  pa.means = P<float>(w.dmeans); pa.quats = P<float>(w.dquats); pa.log_scales = P<float>(w.dscales);
-  pa.opacity_logits = P<float>(s->opacity_logits); pa.sh = P<float>(s->sh); pa.sh_degree = s->sh_degree;
-  pa.cam = cam_params(shape);
-  pa.cam_dev = d_cam;
-  pa.tiles_x = tx; pa.tiles_y = ty;
-  pa.xy = P<float2>(w.xy); pa.conic_opacity = P<float4>(w.co); pa.rgb = P<float>(w.rgb);
-  pa.depth = P<float>(w.depth); pa.radius = P<int>(w.radius); pa.rect = P<int4>(w.rect);
-  pa.depth_keys = P<unsigned long long>(w.dkeys); pa.depth_vals = P<uint32_t>(w.dvals);
-  pa.depth_hist = z.hist;
-  FS4D_CUDA(c, launch_project(pa, stream));
+  for (int i = 0; i < n_parts; ++i) {
+    const FramePart& q = parts[i];
+    Scene* s = q.s;
+    ProjectArgs pa{};
+    pa.n = s->n;
+    pa.means = P<float>(w.dmeans) + 3 * q.off; pa.quats = P<float>(w.dquats) + 4 * q.off;
+    pa.log_scales = P<float>(w.dscales) + 3 * q.off;
+    pa.opacity_logits = P<float>(s->opacity_logits); pa.sh = P<float>(s->sh); pa.sh_degree = s->sh_degree;
+    pa.cam = cam_params(shape);
+    if (e.guard_w > 0) {
+      pa.cam.guard_w = e.guard_w;
+      pa.cam.guard_h = e.guard_h;
+    }
+    // world_to_cam applied to X + shift: the translation column absorbs W shift
+    for (int r = 0; r < 3; ++r)
+      pa.cam.m[4 * r + 3] += pa.cam.m[4 * r] * q.shift[0] + pa.cam.m[4 * r + 1] * q.shift[1] +
+                             pa.cam.m[4 * r + 2] * q.shift[2];
+    pa.cam_dev = d_cam;
+    pa.tiles_x = tx; pa.tiles_y = ty;
+    pa.xy = P<float2>(w.xy) + q.off; pa.conic_opacity = P<float4>(w.co) + q.off; pa.rgb = P<float>(w.rgb) + 3 * q.off;
+    pa.depth = P<float>(w.depth) + q.off; pa.radius = P<int>(w.radius) + q.off; pa.rect = P<int4>(w.rect) + q.off;
+    pa.depth_keys = P<unsigned long long>(w.dkeys) + q.off; pa.depth_vals = P<uint32_t>(w.dvals) + q.off;
+    pa.index_base = (uint32_t)q.off;
+    pa.depth_hist = z.hist;
+    FS4D_CUDA(c, launch_project(pa, stream));
+  }
   mark(e, 2);
   // Gaussians in (float32 depth, index) order: the emission order
   bool dalt = false;
@@ -596,11 +671,11 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   dsw.prezeroed = true;
   dsw.spin_limit = c->spin_limit;
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
-                           P<uint32_t>(w.dvals_alt), nullptr, s->n, 0, 32, true, dsw, e.status, stream, &dalt,
+                           P<uint32_t>(w.dvals_alt), nullptr, N, 0, 32, true, dsw, e.status, stream, &dalt,
                            &dsel));
   mark(e, 3);
   EmitArgs ea{};
-  ea.n = s->n; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
+  ea.n = N; ea.order = P<uint32_t>(w.dvals); ea.order_alt = P<uint32_t>(w.dvals_alt); ea.order_sel = dsel;
   ea.depth = P<float>(w.depth); ea.rect = P<int4>(w.rect); ea.tiles_x = tx;
   ea.capacity = cap;
   ea.keys = P<unsigned long long>(w.keys); ea.values = P<uint32_t>(w.values);
@@ -614,14 +689,19 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   ea.status = e.status;
   ea.spin_limit = c->spin_limit;
   ea.report_overflow = report ? 1 : 0;
-  w.bmp = use_bitmap(c, w, s->n, tx * ty, offsets);
+  w.bmp = use_bitmap(c, w, N, tx * ty, offsets);
+  // a frame kept for the backward needs each pair's (key, value) slots; any other
+  // sorts one 8-byte (tile | Gaussian index) word per pair (16 instead of 24 bytes
+  // per pair per pass)
+  w.packed = !w.bmp && !offsets;
+  ea.packed = w.packed ? 1 : 0;
   if (e.w == &c->w) c->last_binning = w.bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;
   if (w.bmp) {
     // bits per (tile, depth rank) and the projected Gaussians copied into rank order;
     // ranges and launch order from the tile counts; each tile's row read in rank
     // order is its list of depth ranks (no keys: the composite needs none)
     ea.bitmap = P<uint32_t>(w.bitmap);
-    ea.words = bitmap_words(s->n);
+    ea.words = bitmap_words(N);
     ea.keys = nullptr;
     ea.ranges = P<uint2>(w.ranges);
     ea.tile_order = P<uint32_t>(w.tile_order);
@@ -642,6 +722,13 @@ fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_
   }
   mark(e, 4);
   return FS4D_OK;
+}
+
+fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
+                        const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
+                        bool deform = true, bool offsets = false) {
+  const FramePart part{s, 0, {0.f, 0.f, 0.f}};
+  return frame_front(e, &part, 1, prec, shape, d_cam, d_t, t, cap, report, deform, offsets);
 }
 
 fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
@@ -668,18 +755,21 @@ fs4d_status frame_back(const Env& e, const fs4d_camera& shape, long long n_bound
     psw.prezeroed = true;
     psw.spin_limit = c->spin_limit;
     if (sort_parts(n_bound) > z.pparts) return fail(c, FS4D_ERR_INVALID_ARG, "pair bound above the frame's capacity");
-    FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), P<uint32_t>(w.values), P<unsigned long long>(w.keys_alt),
-                             P<uint32_t>(w.values_alt), n_dev, n_bound, 32, tile_bits, true, psw, e.status, e.s,
-                             &alt));
+    FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.keys), w.packed ? nullptr : P<uint32_t>(w.values),
+                             P<unsigned long long>(w.keys_alt), w.packed ? nullptr : P<uint32_t>(w.values_alt), n_dev,
+                             n_bound, 32, tile_bits, true, psw, e.status, e.s, &alt));
   }
-  uint32_t* values = alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values);
-  if (values_out) *values_out = values;
+  // packed: the Gaussian index is the low word of each sorted 64-bit key
+  uint32_t* values = w.packed ? reinterpret_cast<uint32_t*>(alt ? P<unsigned long long>(w.keys_alt)
+                                                                : P<unsigned long long>(w.keys))
+                              : (alt ? P<uint32_t>(w.values_alt) : P<uint32_t>(w.values));
+  if (values_out) *values_out = w.packed ? nullptr : values;
   mark(e, 6);
   // with the bitmap the lists hold depth ranks into the rank-ordered copies
   FS4D_CUDA(c, launch_composite(shape.width, shape.height, P<uint2>(w.ranges), values,
                                 w.bmp ? P<float2>(w.sxy) : P<float2>(w.xy), w.bmp ? P<float4>(w.sco) : P<float4>(w.co),
                                 w.bmp ? P<float>(w.srgb) : P<float>(w.rgb), d_image, d_t_final, d_n_contrib, e.s,
-                                P<uint32_t>(w.tile_order)));
+                                P<uint32_t>(w.tile_order), w.packed ? 2 : 1));
   mark(e, 7);
   return FS4D_OK;
 }
@@ -717,15 +807,24 @@ fs4d_status add_stage_times(fs4d_ctx* c, bool with_deform) {
 }
 
 // Bands of tile rows over the deformed Gaussians already in the work memory.
+// n_bands equal bands, or (reuse) the last banded frame's bands of tile rows, so that
+// frames of one scene and size are cut alike and render alike.
 fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t, int n_bands,
-                         float* d_image, float* d_t_final, int32_t* d_n_contrib) {
+                         float* d_image, float* d_t_final, int32_t* d_n_contrib, bool reuse = false) {
   const int rows = tiles_of(cam->height), tx = tiles_of(cam->width);
   n_bands = std::max(1, std::min(n_bands, rows));
   std::vector<std::pair<int, int>> todo;  // tile-row ranges [r0, r1), taken from the back
-  for (int b = n_bands - 1; b >= 0; --b) todo.push_back({rows * b / n_bands, rows * (b + 1) / n_bands});
+  if (reuse)
+    todo.assign(c->band_rows.rbegin(), c->band_rows.rend());
+  else
+    for (int b = n_bands - 1; b >= 0; --b) todo.push_back({rows * b / n_bands, rows * (b + 1) / n_bands});
+  std::vector<std::pair<int, int>> used;
   long long total = 0;
   int done = 0;
   fs4d_status st;
+  Env be = env_of(c);
+  be.guard_w = cam->width;
+  be.guard_h = cam->height;
   while (!todo.empty()) {
     const std::pair<int, int> band = todo.back();
     todo.pop_back();
@@ -734,7 +833,7 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
     bc.height = std::min(cam->height, kTile * r1) - kTile * r0;
     bc.cy = cam->cy - (float)(kTile * r0);
     if ((st = ensure_work(c, s->n, tx * (r1 - r0), c->w.cap_pairs)) != FS4D_OK) return st;
-    if ((st = frame_front(env_of(c), s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+    if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
       return st;
     long long K = 0;
     if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
@@ -747,7 +846,7 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
     }
     if (K > c->w.cap_pairs) {
       if ((st = ensure_work(c, s->n, tx * (r1 - r0), std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
-      if ((st = frame_front(env_of(c), s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+      if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
         return st;
     }
     const size_t off = (size_t)kTile * r0 * cam->width;
@@ -757,12 +856,14 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
     if ((st = add_stage_times(c, false)) != FS4D_OK) return st;
     total += K;
     ++done;
+    used.push_back({r0, r1});
   }
   c->last_pairs = total;
   c->last_bands = done;
   // the next frame of this scene and size starts with as many bands, unless one would do
   c->band_scene = s->id; c->band_w = cam->width; c->band_h = cam->height;
   c->band_hint = total > c->band_pairs ? done : 0;
+  c->band_rows = used;
   c->stage_acc_valid = c->timing;
   return FS4D_OK;
 }
@@ -786,7 +887,7 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
       FS4D_CUDA(c, cudaEventSynchronize(c->ev[1]));
       FS4D_CUDA(c, cudaEventElapsedTime(&c->stage_acc[0], c->ev[0], c->ev[1]));
     }
-    return render_bands(c, s, prec, cam, t, c->band_hint, d_image, d_t_final, d_n_contrib);
+    return render_bands(c, s, prec, cam, t, c->band_hint, d_image, d_t_final, d_n_contrib, true);
   }
   st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
   if (st != FS4D_OK) return st;
@@ -808,6 +909,42 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   c->last_pairs = K;
   c->last_bands = 1;
   return frame_back(c, *cam, K, d_image, d_t_final, d_n_contrib);
+}
+
+// Render with the state the backward needs, into f (its buffers are reused and
+// grown when needed, so a frame object can serve one training step after another).
+fs4d_status render_into_frame(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera* cam, float t,
+                              float* d_image, fs4d_frame* f) {
+  const size_t npix = (size_t)cam->width * cam->height;
+  if (ensure(f->t_final, 4 * npix) != cudaSuccess || ensure(f->n_contrib, 4 * npix) != cudaSuccess)
+    return fail(c, FS4D_ERR_OOM, "render: frame allocation failed");
+  fs4d_status st = render_sync(c, s, prec, cam, t, d_image, P<float>(f->t_final), P<int32_t>(f->n_contrib), true);
+  if (st != FS4D_OK) return st;
+  Work& w = c->w;
+  const size_t n = (size_t)s->n, K = (size_t)c->last_pairs;
+  const size_t tiles = (size_t)tiles_of(cam->width) * tiles_of(cam->height);
+  struct Item {
+    DevBuf* dst;
+    const void* src;
+    size_t bytes;
+  } items[] = {{&f->dmeans, w.dmeans.p, 12 * n}, {&f->dquats, w.dquats.p, 16 * n}, {&f->dscales, w.dscales.p, 12 * n},
+               {&f->xy, w.xy.p, 8 * n},          {&f->co, w.co.p, 16 * n},         {&f->rgb, w.rgb.p, 12 * n},
+               {&f->radius, w.radius.p, 4 * n},  {&f->rect, w.rect.p, 16 * n},     {&f->offsets, w.offsets.p, 4 * n},
+               {&f->values, c->last_values, 4 * std::max<size_t>(K, 1)},           {&f->ranges, w.ranges.p, 8 * tiles}};
+  for (Item& it : items) {
+    if (it.dst->bytes < it.bytes) {
+      FS4D_CUDA(c, cudaStreamSynchronize(c->stream));  // the old buffer may still be read
+      if (ensure(*it.dst, it.bytes) != cudaSuccess) return fail(c, FS4D_ERR_OOM, "render: frame allocation failed");
+    }
+    if (cudaMemcpyAsync(it.dst->p, it.src, it.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return fail(c, FS4D_ERR_CUDA, "render: saving the frame failed");
+  }
+  f->scene = s->id;
+  f->cam = *cam;
+  f->t = t;
+  f->n = s->n;
+  f->pairs = c->last_pairs;
+  return FS4D_OK;
 }
 
 }  // namespace
@@ -853,6 +990,8 @@ fs4d_status fs4d_destroy(fs4d_ctx* c) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     for (int i = 0; i < 8; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 5; ++i)
+      if (c->bev[i]) cudaEventDestroy(c->bev[i]);
     if (c->copy_stream) {
       cudaStreamSynchronize(c->copy_stream);
       cudaStreamDestroy(c->copy_stream);
@@ -909,6 +1048,9 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
     return fail(c, FS4D_ERR_UNIMPLEMENTED, "scene: feat_dim must be 16 or 32 with 1..3 levels");
   DeviceGuard g(c->device);
   Scene* s = new Scene();
+  s->shape = *d;
+  s->shape.means = s->shape.log_scales = s->shape.quats = s->shape.opacity_logits = s->shape.sh = nullptr;
+  s->shape.planes = s->shape.mlp = nullptr;
   s->n = d->n;
   s->sh_degree = d->sh_degree;
   s->K = (d->sh_degree + 1) * (d->sh_degree + 1);
@@ -942,6 +1084,10 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
     build_tc_image(d->mlp, hin, d->mlp_width, s->tg, img, bias);
     if ((st = upload(c, s->tc_ops, img.data(), img.size(), &acc)) != FS4D_OK) return bail(st);
     if ((st = upload(c, s->tc_bias, bias.data(), bias.size(), &acc)) != FS4D_OK) return bail(st);
+  }
+  {
+    std::vector<int4> tab = build_derive_tab(hin, d->mlp_width, s->mg, s->tg, s->bf16_ok);
+    if ((st = upload(c, s->derive_tab, tab.data(), tab.size(), &acc)) != FS4D_OK) return bail(st);
   }
   {
     // Work order of the deformation kernels: Gaussians sorted by the 30-bit
@@ -1052,44 +1198,62 @@ fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, cons
   *saved = nullptr;
   fs4d_frame* f = new (std::nothrow) fs4d_frame();
   if (!f) return fail(c, FS4D_ERR_OOM, "render: frame allocation failed");
-  const size_t npix = (size_t)cam->width * cam->height;
-  auto drop = [&](fs4d_status e) {
+  st = render_into_frame(c, s, prec, cam, t, d_image, f);
+  if (st == FS4D_OK && d_t_final)
+    st = cudaMemcpyAsync(d_t_final, f->t_final.p, 4 * (size_t)cam->width * cam->height, cudaMemcpyDeviceToDevice,
+                         c->stream) == cudaSuccess ? FS4D_OK : fail(c, FS4D_ERR_CUDA, "render: copy of T failed");
+  if (st == FS4D_OK && d_n_contrib)
+    st = cudaMemcpyAsync(d_n_contrib, f->n_contrib.p, 4 * (size_t)cam->width * cam->height,
+                         cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
+             ? FS4D_OK
+             : fail(c, FS4D_ERR_CUDA, "render: copy of n_contrib failed");
+  if (st != FS4D_OK) {
     fs4d_frame_free(c, f);
-    return e;
-  };
-  if (ensure(f->t_final, 4 * npix) != cudaSuccess || ensure(f->n_contrib, 4 * npix) != cudaSuccess)
-    return drop(fail(c, FS4D_ERR_OOM, "render: frame allocation failed"));
-  st = render_sync(c, s, prec, cam, t, d_image, P<float>(f->t_final), P<int32_t>(f->n_contrib), true);
-  if (st != FS4D_OK) return drop(st);
-  Work& w = c->w;
-  const size_t n = (size_t)s->n, K = (size_t)c->last_pairs;
-  const size_t tiles = (size_t)tiles_of(cam->width) * tiles_of(cam->height);
-  struct Item {
-    DevBuf* dst;
-    const void* src;
-    size_t bytes;
-  } items[] = {{&f->dmeans, w.dmeans.p, 12 * n}, {&f->dquats, w.dquats.p, 16 * n}, {&f->dscales, w.dscales.p, 12 * n},
-               {&f->xy, w.xy.p, 8 * n},          {&f->co, w.co.p, 16 * n},         {&f->rgb, w.rgb.p, 12 * n},
-               {&f->radius, w.radius.p, 4 * n},  {&f->rect, w.rect.p, 16 * n},     {&f->offsets, w.offsets.p, 4 * n},
-               {&f->values, c->last_values, 4 * std::max<size_t>(K, 1)},           {&f->ranges, w.ranges.p, 8 * tiles}};
-  for (Item& it : items) {
-    if (ensure(*it.dst, it.bytes) != cudaSuccess) return drop(fail(c, FS4D_ERR_OOM, "render: frame allocation failed"));
-    if (cudaMemcpyAsync(it.dst->p, it.src, it.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-      return drop(fail(c, FS4D_ERR_CUDA, "render: saving the frame failed"));
+    return st;
   }
-  if (d_t_final &&
-      cudaMemcpyAsync(d_t_final, f->t_final.p, 4 * npix, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-    return drop(fail(c, FS4D_ERR_CUDA, "render: copy of T failed"));
-  if (d_n_contrib &&
-      cudaMemcpyAsync(d_n_contrib, f->n_contrib.p, 4 * npix, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-    return drop(fail(c, FS4D_ERR_CUDA, "render: copy of n_contrib failed"));
-  f->scene = id;
-  f->cam = *cam;
-  f->t = t;
-  f->n = s->n;
-  f->pairs = c->last_pairs;
   *saved = f;
   return FS4D_OK;
+}
+
+fs4d_status fs4d_render_composed(fs4d_ctx* c, const fs4d_scene_id* ids, const float* h_shifts, int32_t n_scenes,
+                                 fs4d_precision prec, const fs4d_camera* cam, float t, float* d_image,
+                                 float* d_t_final, int32_t* d_n_contrib) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!ids || n_scenes < 1 || !valid_cam(cam) || !d_image)
+    return fail(c, FS4D_ERR_INVALID_ARG, "render_composed: scenes, camera and image are required");
+  std::vector<FramePart> parts;
+  long long N = 0;
+  for (int i = 0; i < n_scenes; ++i) {
+    Scene* s;
+    fs4d_status st = get_scene(c, ids[i], &s);
+    if (st != FS4D_OK) return st;
+    FramePart q{s, N, {0.f, 0.f, 0.f}};
+    if (h_shifts)
+      for (int k = 0; k < 3; ++k) q.shift[k] = h_shifts[3 * i + k];
+    parts.push_back(q);
+    N += s->n;
+  }
+  if (N >= (1ll << 31) - 1) return fail(c, FS4D_ERR_CAPACITY, "render_composed: more than 2^31 - 2 Gaussians");
+  DeviceGuard g(c->device);
+  const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
+  fs4d_status st = ensure_work(c, (int)N, n_tiles, c->w.cap_pairs);
+  if (st != FS4D_OK) return st;
+  c->stage_acc_valid = false;
+  st = frame_front(env_of(c), parts.data(), n_scenes, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, true,
+                   false);
+  if (st != FS4D_OK) return st;
+  long long K = 0;
+  if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
+  if (K > c->band_pairs) return fail(c, FS4D_ERR_CAPACITY, "render_composed: the frame's pairs exceed one band");
+  if (K > c->w.cap_pairs) {
+    if ((st = ensure_work(c, (int)N, n_tiles, std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
+    st = frame_front(env_of(c), parts.data(), n_scenes, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, true,
+                     false);
+    if (st != FS4D_OK) return st;
+  }
+  c->last_pairs = K;
+  c->last_bands = 1;
+  return frame_back(c, *cam, K, d_image, d_t_final, d_n_contrib);
 }
 
 fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
@@ -1231,6 +1395,7 @@ fs4d_status fs4d_set_stage_timing(fs4d_ctx* c, int32_t enable) {
   DeviceGuard g(c->device);
   if (enable && !c->ev[0]) {
     for (int i = 0; i < 8; ++i) FS4D_CUDA(c, cudaEventCreate(&c->ev[i]));
+    for (int i = 0; i < 5; ++i) FS4D_CUDA(c, cudaEventCreate(&c->bev[i]));
   }
   c->timing = enable != 0;
   return FS4D_OK;
@@ -1247,6 +1412,15 @@ fs4d_status fs4d_stage_times(fs4d_ctx* c, float* h_ms) {
   FS4D_CUDA(c, cudaEventSynchronize(c->ev[7]));
   const int from[6] = {0, 1, 2, 3, 5, 6}, to[6] = {1, 2, 3, 4, 6, 7};
   for (int k = 0; k < 6; ++k) FS4D_CUDA(c, cudaEventElapsedTime(&h_ms[k], c->ev[from[k]], c->ev[to[k]]));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_backward_times(fs4d_ctx* c, float* h_ms) {
+  if (!c || !h_ms) return FS4D_ERR_INVALID_ARG;
+  if (!c->bev[0]) return fail(c, FS4D_ERR_INVALID_ARG, "backward_times: timing was never enabled");
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, cudaEventSynchronize(c->bev[4]));
+  for (int k = 0; k < 4; ++k) FS4D_CUDA(c, cudaEventElapsedTime(&h_ms[k], c->bev[k], c->bev[k + 1]));
   return FS4D_OK;
 }
 
@@ -1274,6 +1448,10 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
     FS4D_CUDA(c, ensure(w.wpartial, 4 * wp));
   }
   const int tx = tiles_of(f->cam.width);
+  auto bmark = [&](int i) {
+    if (c->timing) cudaEventRecord(c->bev[i], c->stream);
+  };
+  bmark(0);
   // 1. compositing backward into per-pair slots
   FS4D_CUDA(c, cudaMemsetAsync(w.grad_pair.p, 0, 4 * kPairGrad * (size_t)std::max(K, 1ll), c->stream));
   CompositeBwdArgs cb{};
@@ -1284,6 +1462,7 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   cb.t_final = P<float>(f->t_final); cb.n_contrib = P<int>(f->n_contrib);
   cb.dl_dimage = d_dl_dimage; cb.grad_pair = P<float>(w.grad_pair);
   FS4D_CUDA(c, launch_composite_bwd(cb, c->stream));
+  bmark(1);
   // 2. projection, SH and Eq. 6 identity part
   ProjectBwdArgs pb{};
   pb.n = (int)n;
@@ -1294,6 +1473,7 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   pb.g_means = gr->means; pb.g_quats = gr->quats; pb.g_log_scales = gr->log_scales;
   pb.g_opacity = gr->opacity_logits; pb.g_sh = gr->sh;
   FS4D_CUDA(c, launch_project_bwd(pb, c->stream));
+  bmark(2);
   // 3. MLP heads, phi_d and HexPlane sampling (float32 recompute of the deformation)
   MlpBwdArgs mb{};
   mb.f = deform_args(s, nullptr, f->t, 1, nullptr, nullptr, nullptr);
@@ -1310,6 +1490,7 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   mb.g_planes = gr->planes;
   mb.g_means = gr->means;
   FS4D_CUDA(c, launch_mlp_bwd(mb, c->stream));
+  bmark(3);
   // 4. weight gradients, deterministic two-stage reductions, source layout
   if (gr->mlp) {
     size_t tot;
@@ -1327,6 +1508,7 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
                                 wp_buf, gr->mlp + l2.w, gr->mlp + l2.b, c->stream));
     }
   }
+  bmark(4);
   return FS4D_OK;
 }
 
@@ -2123,6 +2305,298 @@ fs4d_status fs4d_server_destroy(fs4d_server* sv) {
   c->server = nullptr;
   delete sv;
   return FS4D_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== training step
+// L = |I^ - I| + L_tv (Sec. 4.3) and one Adam update of every parameter group at
+// learning rates decayed over the run (App. A), all on the device: render with the
+// backward's state, L1 loss and dL/dI, backward, TV loss and its plane gradient,
+// fused Adam (which also clears the gradients), refresh of the derived copies.
+
+struct fs4d_trainer {
+  fs4d_ctx* c = nullptr;
+  fs4d_scene_id scene = 0;
+  fs4d_train_config cfg{};
+  long long step = 0;
+  fs4d_frame frame;                          // reused from step to step
+  DevBuf image, dl, partial, losses;         // [H][W][3] x 2, loss partials, [2] losses
+  DevBuf grad, m, v;                         // every group, in the order of fs4d_scene_desc
+  size_t off[7] = {}, count[7] = {};         // float offset and count of each group
+};
+
+namespace {
+void release_frame(fs4d_frame& f) {
+  DevBuf* all[] = {&f.dmeans, &f.dquats, &f.dscales, &f.xy, &f.co, &f.rgb, &f.radius, &f.rect, &f.offsets,
+                   &f.values, &f.ranges, &f.t_final, &f.n_contrib};
+  for (DevBuf* b : all) release(*b);
+}
+
+double lr_at(const float lr[2], long long k, long long total) {
+  if (total <= 0 || !(lr[0] > 0.f) || !(lr[1] > 0.f)) return lr[0];
+  const double f = std::min(1.0, (double)k / (double)total);
+  return std::exp((1.0 - f) * std::log((double)lr[0]) + f * std::log((double)lr[1]));
+}
+}  // namespace
+
+extern "C" {
+
+fs4d_status fs4d_train_create(fs4d_ctx* c, fs4d_scene_id id, const fs4d_train_config* cfg, fs4d_trainer** out) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!cfg || !out) return fail(c, FS4D_ERR_INVALID_ARG, "train_create: config and output required");
+  *out = nullptr;
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f &&
+        cfg->tv_weight >= 0.f && cfg->total_steps >= 0))
+    return fail(c, FS4D_ERR_INVALID_ARG, "train_create: betas in [0,1), eps, tv_weight, total_steps >= 0");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  fs4d_trainer* tr = new (std::nothrow) fs4d_trainer();
+  if (!tr) return fail(c, FS4D_ERR_OOM, "train_create: allocation failed");
+  tr->c = c;
+  tr->scene = id;
+  tr->cfg = *cfg;
+  const size_t n = (size_t)s->n;
+  const size_t cnt[7] = {3 * n, 3 * n, 4 * n, n, 3 * n * s->K, s->planes_floats, s->mlp_floats};
+  size_t total = 0;
+  for (int k = 0; k < 7; ++k) {
+    tr->off[k] = total;
+    tr->count[k] = cnt[k];
+    total += (cnt[k] + 3) / 4 * 4;  // each group 16-byte aligned
+  }
+  const size_t parts = (size_t)train_partials();
+  if (ensure(tr->grad, 4 * total) != cudaSuccess || ensure(tr->m, 4 * total) != cudaSuccess ||
+      ensure(tr->v, 4 * total) != cudaSuccess || ensure(tr->partial, 4 * parts) != cudaSuccess ||
+      ensure(tr->losses, 16) != cudaSuccess) {
+    fs4d_train_destroy(tr);
+    return fail(c, FS4D_ERR_OOM, "train_create: device allocation failed");
+  }
+  if (cudaMemsetAsync(tr->grad.p, 0, 4 * total, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(tr->m.p, 0, 4 * total, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(tr->v.p, 0, 4 * total, c->stream) != cudaSuccess) {
+    fs4d_train_destroy(tr);
+    return fail(c, FS4D_ERR_CUDA, "train_create: clearing the optimiser state failed");
+  }
+  *out = tr;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, const fs4d_camera* cam, float t,
+                            const float* d_target, float* d_losses) {
+  if (!tr) return FS4D_ERR_INVALID_ARG;
+  fs4d_ctx* c = tr->c;
+  if (!valid_cam(cam) || !d_target) return fail(c, FS4D_ERR_INVALID_ARG, "train_step: camera and target required");
+  Scene* s;
+  fs4d_status st = get_scene(c, tr->scene, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  const size_t pix3 = 3 * (size_t)cam->width * cam->height;
+  if (tr->image.bytes < 4 * pix3 || tr->dl.bytes < 4 * pix3) {
+    FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+    FS4D_CUDA(c, ensure(tr->image, 4 * pix3));
+    FS4D_CUDA(c, ensure(tr->dl, 4 * pix3));
+  }
+  float* losses = d_losses ? d_losses : P<float>(tr->losses);
+  // 1. the frame, keeping the backward's state
+  if ((st = render_into_frame(c, s, prec, cam, t, P<float>(tr->image), &tr->frame)) != FS4D_OK) return st;
+  // 2. L1 loss and dL/dI (misaligned targets take the scalar path inside the kernel)
+  FS4D_CUDA(c, launch_l1(P<float>(tr->image), d_target, (long long)pix3, P<float>(tr->dl), P<float>(tr->partial),
+                         losses, c->stream));
+  // 3. backward into every group
+  float* G = P<float>(tr->grad);
+  fs4d_grads gr{G + tr->off[0], G + tr->off[1], G + tr->off[2], G + tr->off[3], G + tr->off[4], G + tr->off[5],
+                G + tr->off[6]};
+  if ((st = fs4d_render_backward(c, &tr->frame, P<float>(tr->dl), &gr)) != FS4D_OK) return st;
+  // 4. TV loss of the planes and its gradient
+  FS4D_CUDA(c, launch_tv(s->pg, P<float>(s->planes), tr->cfg.tv_weight, gr.planes, P<float>(tr->partial), losses + 1,
+                         c->stream));
+  // 5. Adam at this step's learning rates
+  const fs4d_train_config& q = tr->cfg;
+  const long long k = tr->step, step = k + 1;
+  AdamArgs a{};
+  a.beta1 = q.beta1; a.beta2 = q.beta2; a.eps = q.eps;
+  a.c1 = (float)(1.0 - std::pow((double)q.beta1, (double)step));
+  a.c2 = (float)(1.0 - std::pow((double)q.beta2, (double)step));
+  const float* lrs[7] = {q.lr_means, q.lr_log_scales, q.lr_quats, q.lr_opacity, q.lr_sh_rest, q.lr_planes, q.lr_mlp};
+  DevBuf* params[7] = {&s->means, &s->log_scales, &s->quats, &s->opacity_logits, &s->sh, &s->planes, &s->mlp};
+  for (int grp = 0; grp < 7; ++grp) {
+    AdamSeg& sg = a.seg[a.n_segs++];
+    sg.p = P<float>(*params[grp]);
+    sg.g = G + tr->off[grp];
+    sg.m = P<float>(tr->m) + tr->off[grp];
+    sg.v = P<float>(tr->v) + tr->off[grp];
+    sg.n = (long long)tr->count[grp];
+    sg.lr = (float)lr_at(lrs[grp], k, q.total_steps);
+    if (grp == 4) {  // SH: the degree-0 coefficients (3 of every 3K) take their own rate
+      sg.period = 3 * s->K;
+      sg.head = 3;
+      sg.lr_head = (float)lr_at(q.lr_sh_dc, k, q.total_steps);
+    }
+    a.total += sg.n;
+  }
+  FS4D_CUDA(c, launch_adam(a, c->stream));
+  // 6. the derived copies the next frame reads
+  FS4D_CUDA(c, launch_derive(P<float>(s->planes), (long long)s->planes_floats, P<__nv_bfloat16>(s->planes_bf16),
+                             P<float>(s->mlp), (int)s->mlp_floats, P<int4>(s->derive_tab), P<float>(s->mlp_t),
+                             s->bf16_ok ? P<uint8_t>(s->tc_ops) : nullptr, s->bf16_ok ? P<float>(s->tc_bias) : nullptr,
+                             c->stream));
+  tr->step = step;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_losses(fs4d_trainer* tr, float* h_losses) {
+  if (!tr || !h_losses) return FS4D_ERR_INVALID_ARG;
+  fs4d_ctx* c = tr->c;
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, cudaMemcpyAsync(h_losses, tr->losses.p, 8, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_steps_done(const fs4d_trainer* tr, int64_t* steps) {
+  if (!tr || !steps) return FS4D_ERR_INVALID_ARG;
+  *steps = tr->step;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_destroy(fs4d_trainer* tr) {
+  if (!tr) return FS4D_OK;
+  fs4d_ctx* c = tr->c;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  release_frame(tr->frame);
+  DevBuf* all[] = {&tr->image, &tr->dl, &tr->partial, &tr->losses, &tr->grad, &tr->m, &tr->v};
+  for (DevBuf* b : all) release(*b);
+  delete tr;
+  return FS4D_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== scene read-back and files
+namespace {
+constexpr char kSceneMagic[8] = {'F', 'S', '4', 'D', 'S', 'C', 'N', '1'};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+void group_sizes(const Scene* s, size_t cnt[7]) {
+  const size_t n = (size_t)s->n;
+  const size_t c[7] = {3 * n, 3 * n, 4 * n, n, 3 * n * s->K, s->planes_floats, s->mlp_floats};
+  for (int k = 0; k < 7; ++k) cnt[k] = c[k];
+}
+}  // namespace
+
+extern "C" {
+
+fs4d_status fs4d_read_scene(fs4d_ctx* c, fs4d_scene_id id, const fs4d_grads* out, int32_t to_device) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!out) return fail(c, FS4D_ERR_INVALID_ARG, "read_scene: output pointers required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  DeviceGuard g(c->device);
+  size_t cnt[7];
+  group_sizes(s, cnt);
+  float* dst[7] = {out->means, out->log_scales, out->quats, out->opacity_logits, out->sh, out->planes, out->mlp};
+  const DevBuf* src[7] = {&s->means, &s->log_scales, &s->quats, &s->opacity_logits, &s->sh, &s->planes, &s->mlp};
+  const cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int k = 0; k < 7; ++k) {
+    if (!dst[k]) continue;
+    FS4D_CUDA(c, cudaMemcpyAsync(dst[k], src[k]->p, 4 * cnt[k], kind, c->stream));
+  }
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_save_scene(fs4d_ctx* c, fs4d_scene_id id, const char* path) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!path) return fail(c, FS4D_ERR_INVALID_ARG, "save_scene: path required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  size_t cnt[7];
+  group_sizes(s, cnt);
+  std::vector<std::vector<float>> host(7);
+  for (int k = 0; k < 7; ++k) host[k].resize(cnt[k]);
+  fs4d_grads out{host[0].data(), host[1].data(), host[2].data(), host[3].data(), host[4].data(), host[5].data(),
+                 host[6].data()};
+  if ((st = fs4d_read_scene(c, id, &out, 0)) != FS4D_OK) return st;
+  const fs4d_scene_desc& d = s->shape;
+  const int32_t ints[10] = {d.n, d.sh_degree, d.n_levels, d.res_spatial[0], d.res_spatial[1], d.res_spatial[2],
+                            d.res_spatial[3], d.res_time, d.feat_dim, d.mlp_width};
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return fail(c, FS4D_ERR_INVALID_ARG, "save_scene: cannot open " + tmp);
+  uint64_t h = 14695981039346656037ull;
+  bool ok = std::fwrite(kSceneMagic, 1, 8, f) == 8;
+  auto put = [&](const void* p, size_t bytes) {
+    ok = ok && std::fwrite(p, 1, bytes, f) == bytes;
+    h = fnv1a(h, p, bytes);
+  };
+  put(ints, sizeof(ints));
+  put(d.aabb_min, sizeof(d.aabb_min));
+  put(d.aabb_max, sizeof(d.aabb_max));
+  for (int k = 0; k < 7; ++k) put(host[k].data(), 4 * cnt[k]);
+  ok = ok && std::fwrite(&h, 1, 8, f) == 8;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(c, FS4D_ERR_INVALID_ARG, std::string("save_scene: writing ") + path + " failed");
+  }
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_load_scene_file(fs4d_ctx* c, const char* path, fs4d_scene_id* out) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!path || !out) return fail(c, FS4D_ERR_INVALID_ARG, "load_scene_file: path and output required");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, FS4D_ERR_NOT_FOUND, std::string("load_scene_file: cannot open ") + path);
+  char magic[8];
+  int32_t ints[10];
+  fs4d_scene_desc d{};
+  uint64_t h = 14695981039346656037ull;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSceneMagic, 8) == 0;
+  auto get = [&](void* p, size_t bytes) {
+    ok = ok && std::fread(p, 1, bytes, f) == bytes;
+    if (ok) h = fnv1a(h, p, bytes);
+  };
+  get(ints, sizeof(ints));
+  get(d.aabb_min, sizeof(d.aabb_min));
+  get(d.aabb_max, sizeof(d.aabb_max));
+  d.n = ints[0]; d.sh_degree = ints[1]; d.n_levels = ints[2];
+  for (int l = 0; l < 4; ++l) d.res_spatial[l] = ints[3 + l];
+  d.res_time = ints[7]; d.feat_dim = ints[8]; d.mlp_width = ints[9];
+  ok = ok && d.n >= 1 && d.sh_degree >= 0 && d.sh_degree <= 3 && d.n_levels >= 1 && d.n_levels <= kMaxLevels &&
+       d.feat_dim > 0 && d.res_time >= 2 && d.mlp_width == kWidth;
+  std::vector<std::vector<float>> host(7);
+  if (ok) {
+    PlaneGeom pg{};
+    size_t planes_total = 0, mlp_total = 0;
+    plane_geom(d, pg, planes_total);
+    src_layers(d.feat_dim * d.n_levels, d.mlp_width, &mlp_total);
+    const size_t n = (size_t)d.n, K = (size_t)(d.sh_degree + 1) * (d.sh_degree + 1);
+    const size_t cnt[7] = {3 * n, 3 * n, 4 * n, n, 3 * n * K, planes_total, mlp_total};
+    for (int k = 0; k < 7 && ok; ++k) {
+      host[k].resize(cnt[k]);
+      get(host[k].data(), 4 * cnt[k]);
+    }
+  }
+  uint64_t stored = 0;
+  ok = ok && std::fread(&stored, 1, 8, f) == 8 && stored == h;
+  std::fclose(f);
+  if (!ok) return fail(c, FS4D_ERR_INVALID_ARG, std::string("load_scene_file: ") + path + " is not a valid scene file");
+  d.means = host[0].data(); d.log_scales = host[1].data(); d.quats = host[2].data();
+  d.opacity_logits = host[3].data(); d.sh = host[4].data(); d.planes = host[5].data(); d.mlp = host[6].data();
+  return fs4d_load_scene(c, &d, out);
 }
 
 }  // extern "C"

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
                    {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
                    {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
   const float sc[3] = {expf(a.log_scales[3 * g]), expf(a.log_scales[3 * g + 1]), expf(a.log_scales[3 * g + 2])};
-  const float limx = kGuard * (float)c.width / (2.f * c.fx), limy = kGuard * (float)c.height / (2.f * c.fy);
+  const float limx = kGuard * (float)c.guard_w / (2.f * c.fx), limy = kGuard * (float)c.guard_h / (2.f * c.fy);
   const float rx_raw = px * iz, ry_raw = py * iz;
   const bool clx = fabsf(rx_raw) > limx, cly = fabsf(ry_raw) > limy;
   const float rx = fminf(limx, fmaxf(-limx, rx_raw)), ry = fminf(limy, fmaxf(-limy, ry_raw));

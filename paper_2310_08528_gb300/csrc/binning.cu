@@ -171,11 +171,15 @@ __global__ void __launch_bounds__(kThreads) scan_emit_kernel(EmitArgs a, int sme
       const uint32_t k = j - s_off[lo];
       const uint32_t w = (uint32_t)(r.z - r.x);
       const uint32_t tile = (uint32_t)(r.y + (int)(k / w)) * (uint32_t)a.tiles_x + (uint32_t)(r.x + (int)(k % w));
-      key = ((unsigned long long)tile << 32) | s_dbits[lo];
       const unsigned long long out = prefix + j;
-      if ((long long)out < a.capacity) {
-        a.keys[out] = key;
-        a.values[out] = s_gid[lo];
+      if (a.packed) {  // (tile | Gaussian index): the sort carries the index in the key
+        if ((long long)out < a.capacity) a.keys[out] = ((unsigned long long)tile << 32) | s_gid[lo];
+      } else {
+        key = ((unsigned long long)tile << 32) | s_dbits[lo];
+        if ((long long)out < a.capacity) {
+          a.keys[out] = key;
+          a.values[out] = s_gid[lo];
+        }
       }
       if (smem_tiles)
         atomicAdd(&s_tc[tile], 1u);

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) composite_kernel(int wid
                                                             const float4* __restrict__ conic_opacity,
                                                             const float* __restrict__ rgb, float* __restrict__ image,
                                                             float* __restrict__ t_final, int* __restrict__ n_contrib,
-                                                            const uint32_t* __restrict__ order) {
+                                                            const uint32_t* __restrict__ order, int vstride) {
   // two staging buffers: batch i is staged while batch i - 1 may still be read
   __shared__ float4 s_g0b[2][kBatch];   // x, y, a2, c2
   __shared__ float4 s_g1b[2][kBatch];   // b2, opacity, red, green
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) composite_kernel(int wid
     const int b = it & 1;
     const int k = base + (int)threadIdx.x;
     if (k < n)
-      stage_gaussian(threadIdx.x, values[range.x + k], xy, conic_opacity, rgb, tx, ty, s_g0b[b], s_g1b[b],
+      stage_gaussian(threadIdx.x, values[(size_t)vstride * (range.x + k)], xy, conic_opacity, rgb, tx, ty, s_g0b[b], s_g1b[b],
                      s_blueb[b], s_maskb[b]);
     // one barrier per batch: this batch is staged, the buffer staged next was
     // last read for batch i - 1, which every thread has finished; and if every
@@ -204,14 +204,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) composite_kernel(int wid
 
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values, const float2* xy,
                              const float4* conic_opacity, const float* rgb, float* image, float* t_final,
-                             int* n_contrib, cudaStream_t s, const uint32_t* order) {
+                             int* n_contrib, cudaStream_t s, const uint32_t* order, int values_stride) {
   const int tiles_x = (width + kTile - 1) / kTile, tiles_y = (height + kTile - 1) / kTile;
   if (tiles_x * tiles_y == 0) return cudaSuccess;
   if (t_final || n_contrib)
     return launch_pdl(composite_kernel<true>, tiles_x * tiles_y, kThreads, 0, s, width, height, tiles_x, ranges, values,
-                      xy, conic_opacity, rgb, image, t_final, n_contrib, order);
+                      xy, conic_opacity, rgb, image, t_final, n_contrib, order, values_stride);
   return launch_pdl(composite_kernel<false>, tiles_x * tiles_y, kThreads, 0, s, width, height, tiles_x, ranges, values,
-                    xy, conic_opacity, rgb, image, t_final, n_contrib, order);
+                    xy, conic_opacity, rgb, image, t_final, n_contrib, order, values_stride);
 }
 
 }  // namespace fs4d

@@ -143,6 +143,8 @@ struct CamParams {
   int width, height;
   float fx, fy, cx, cy, znear;
   float m[12];                  // rows 0..2 of world_to_cam
+  int guard_w, guard_h;         // image extent the Jacobian's guard band refers to (the whole
+                                // frame's, also when this call renders one band of it)
 };
 
 struct ProjectArgs {
@@ -163,7 +165,8 @@ struct ProjectArgs {
   int* radius;
   int4* rect;
   unsigned long long* depth_keys;  // optional [n]: float bits of depth, for the depth sort
-  uint32_t* depth_vals;            // optional [n]: Gaussian index
+  uint32_t* depth_vals;            // optional [n]: Gaussian index (index_base + g)
+  uint32_t index_base;             // index of this call's first Gaussian in the frame's set
   uint32_t* depth_hist;            // optional [4][256] (zeroed): byte histograms of the depth keys
 };
 
@@ -190,6 +193,8 @@ struct EmitArgs {
   int n_tiles;
   uint32_t* status;
   uint32_t spin_limit;          // polls of the look-back wait before it gives up
+  int packed;                   // 1: keys = (tile << 32) | Gaussian index, no values (the pairs
+                                // are sorted on the tile bits only and the index travels along)
   // tile bitmap binning (launch_mark_tiles / launch_extract_tiles)
   uint32_t* bitmap;             // [n_tiles][words], bit (i & 31) of word i >> 5 of row t: the
                                 // Gaussian of depth rank i touches tile t (all zero between frames)
@@ -257,10 +262,46 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
                         uint32_t* values_alt, const uint32_t* n_dev, long long n_bound, int first_bit,
                         int key_bits, bool hist_ready, const SortWork& work, uint32_t* status, cudaStream_t s,
                         bool* result_in_alt, const uint32_t** result_sel = nullptr);
-// order (optional): CTA i composites tile order[i]
+// order (optional): CTA i composites tile order[i]; values_stride: 1 for a list of
+// uint32 indices, 2 for the low words of packed (tile | index) 64-bit keys
 cudaError_t launch_composite(int width, int height, const uint2* ranges, const uint32_t* values,
                              const float2* xy, const float4* conic_opacity, const float* rgb, float* image,
-                             float* t_final, int* n_contrib, cudaStream_t s, const uint32_t* order = nullptr);
+                             float* t_final, int* n_contrib, cudaStream_t s, const uint32_t* order = nullptr,
+                             int values_stride = 1);
+}  // namespace fs4d
+
+// ================================================================ training step
+namespace fs4d {
+// One Adam parameter segment: p -= lr m^ / (sqrt(v^) + eps), element i with
+// (i mod period) < head takes lr_head (period 0: every element takes lr).
+struct AdamSeg {
+  float* p;
+  float* g;
+  float* m;
+  float* v;
+  long long n;
+  float lr, lr_head;
+  int period, head;
+};
+struct AdamArgs {
+  AdamSeg seg[8];
+  int n_segs;
+  long long total;
+  float beta1, beta2, eps;
+  float c1, c2;   // bias corrections 1 - beta^step
+};
+int train_partials();  // size of the loss-partial buffers the launchers below need
+// L1 loss: dl = sign(img - tgt) / count, *out = mean |img - tgt| (device float)
+cudaError_t launch_l1(const float* img, const float* tgt, long long count, float* dl, float* partial, float* out,
+                      cudaStream_t s);
+// grid TV loss of the planes: g_planes += gradient, *out = loss
+cudaError_t launch_tv(const PlaneGeom& pg, const float* planes, float weight, float* g_planes, float* partial,
+                      float* out, cudaStream_t s);
+cudaError_t launch_adam(const AdamArgs& a, cudaStream_t s);
+// derived copies from planes and the source-layout MLP; tab[i] = (mlp_t index,
+// tc_ops byte offset or -1, tc_bias index or -1, 0) for MLP value i
+cudaError_t launch_derive(const float* planes, long long n_planes, __nv_bfloat16* planes_bf16, const float* mlp,
+                          int n_mlp, const int4* tab, float* mlp_t, uint8_t* tc_ops, float* tc_bias, cudaStream_t s);
 }  // namespace fs4d
 
 // ================================================================ backward

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   a.depth[g] = pz;
   if (a.depth_keys) {
     a.depth_keys[g] = __float_as_uint(pz);
-    a.depth_vals[g] = (uint32_t)g;
+    a.depth_vals[g] = a.index_base + (uint32_t)g;
   }
   a.radius[g] = 0;
   a.rect[g] = make_int4(0, 0, 0, 0);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
   // minors of A (Cauchy-Binet) plus the dilation terms, and the eigenvalue gap
   // from ((a - c)/2)^2 + b^2 -- sums of squares, so no float32 cancellation for
   // thin Gaussians (ac - b^2 would lose ~a*c/det ulps).
-  const float limx = kGuard * (float)c.width / (2.f * c.fx), limy = kGuard * (float)c.height / (2.f * c.fy);
+  const float limx = kGuard * (float)c.guard_w / (2.f * c.fx), limy = kGuard * (float)c.guard_h / (2.f * c.fy);
   const float iz = 1.f / pz;
   const float tx = fminf(limx, fmaxf(-limx, px * iz)) * pz;
   const float ty = fminf(limy, fmaxf(-limy, py * iz)) * pz;

@@ -105,7 +105,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp) {
   return base + incl - v;
 }
 
-template <int ITEMS>
+// VALS = false: keys only (values_* unused); the key carries its payload.
+template <int ITEMS, bool VALS>
 __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
   constexpr int kItems = ITEMS;
   constexpr int kPartPairs = kThreads * ITEMS;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     const long long m = min((long long)kPartPairs, n - base);
     for (long long i = tid; i < m; i += kThreads) {
       keys_out[base + i] = keys_in[base + i];
-      values_out[base + i] = values_in[base + i];
+      if (VALS) values_out[base + i] = values_in[base + i];
     }
     return;
   }
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     const long long idx = base + (long long)warp * (kItems * 32) + i * 32 + lane;
     const bool valid = idx < n;
     k[i] = valid ? keys_in[idx] : 0ull;
-    v[i] = valid ? values_in[idx] : 0u;
+    v[i] = (VALS && valid) ? values_in[idx] : 0u;
     dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u);
   }
 #pragma unroll
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     if (d < 256u) {
       const uint32_t pos = sm.block_off[d] + sm.warp_cnt[warp][d] + rank[i];
       sm.keys[pos] = k[i];
-      sm.values[pos] = v[i];
+      if (VALS) sm.values[pos] = v[i];
     }
   }
 
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     const uint32_t out = sm.global_off[d] + sm.prev_off[d] + ((uint32_t)j - sm.block_off[d]);
     if ((long long)out < n) {  // always true when the histogram matches the keys
       keys_out[out] = key;
-      values_out[out] = sm.values[j];
+      if (VALS) values_out[out] = sm.values[j];
     }
   }
 }
@@ -292,11 +293,19 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   if (parts > work.max_parts || n_bound > (long long)kValMask) return cudaErrorInvalidValue;
   static PerDeviceFlag attr;
   cudaError_t e = once_per_device(attr, [] {
-    cudaError_t r = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PassSmem<kItemsLarge>));
-    if (r != cudaSuccess) return r;
-    return cudaFuncSetAttribute(onesweep_kernel<kItemsSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(PassSmem<kItemsSmall>));
+    const int large = (int)sizeof(PassSmem<kItemsLarge>), small_b = (int)sizeof(PassSmem<kItemsSmall>);
+    cudaError_t r = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, large);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(onesweep_kernel<kItemsSmall, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               small_b);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(onesweep_kernel<kItemsLarge, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               large);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(onesweep_kernel<kItemsSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               small_b);
+    return r;
   });
   if (e != cudaSuccess) return e;
   if (!work.prezeroed) {
@@ -335,10 +344,17 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     pa.part_counter = work.part_counters + p;
     pa.status = status;
     pa.spin_limit = work.spin_limit;
+    const bool vals = values != nullptr;
     if (small)
-      e = launch_pdl(onesweep_kernel<kItemsSmall>, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s, pa);
+      e = vals ? launch_pdl(onesweep_kernel<kItemsSmall, true>, (unsigned)parts, kThreads,
+                            sizeof(PassSmem<kItemsSmall>), s, pa)
+               : launch_pdl(onesweep_kernel<kItemsSmall, false>, (unsigned)parts, kThreads,
+                            sizeof(PassSmem<kItemsSmall>), s, pa);
     else
-      e = launch_pdl(onesweep_kernel<kItemsLarge>, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsLarge>), s, pa);
+      e = vals ? launch_pdl(onesweep_kernel<kItemsLarge, true>, (unsigned)parts, kThreads,
+                            sizeof(PassSmem<kItemsLarge>), s, pa)
+               : launch_pdl(onesweep_kernel<kItemsLarge, false>, (unsigned)parts, kThreads,
+                            sizeof(PassSmem<kItemsLarge>), s, pa);
     if (e != cudaSuccess) return e;
     unsigned long long* tk = kin; kin = kout; kout = tk;
     uint32_t* tv = vin; vin = vout; vout = tv;

@@ -27,7 +27,10 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_render_host", "fs4d_render_host_batch", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
            "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_sort_pairs_noalloc_status",
-           "fs4d_composite", "fs4d_set_wait_limit", "fs4d_last_bands", "fs4d_set_band_pairs")
+           "fs4d_composite", "fs4d_set_wait_limit", "fs4d_last_bands", "fs4d_set_band_pairs",
+           "fs4d_train_create", "fs4d_train_step", "fs4d_train_losses", "fs4d_train_steps_done",
+           "fs4d_train_destroy", "fs4d_read_scene", "fs4d_save_scene", "fs4d_load_scene_file",
+           "fs4d_backward_times", "fs4d_render_composed")
 STAGES = ("deform", "project", "depth_sort", "binning", "sort", "composite")
 
 
@@ -52,6 +55,34 @@ class Camera(C.Structure):
 
 class Projected(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("xy", "conic_opacity", "rgb", "depth", "radius", "rect")]
+
+
+class TrainConfig(C.Structure):
+    _fields_ = [("total_steps", C.c_int32)] + [(k, C.c_float * 2) for k in (
+        "lr_means", "lr_log_scales", "lr_quats", "lr_opacity", "lr_sh_dc", "lr_sh_rest", "lr_planes", "lr_mlp")] + [
+        ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("tv_weight", C.c_float)]
+
+
+# Learning rates of the training step: App. A gives the HexPlane (1.6e-3 -> 1.6e-4)
+# and the MLP (1.6e-4 -> 1.6e-5); the Gaussian parameters follow the settings of
+# 3D Gaussian Splatting that the paper says it follows.
+TRAIN_DEFAULTS = dict(lr_means=(1.6e-4, 1.6e-6), lr_log_scales=(5e-3, 5e-3), lr_quats=(1e-3, 1e-3),
+                      lr_opacity=(5e-2, 5e-2), lr_sh_dc=(2.5e-3, 2.5e-3), lr_sh_rest=(1.25e-4, 1.25e-4),
+                      lr_planes=(1.6e-3, 1.6e-4), lr_mlp=(1.6e-4, 1.6e-5), beta1=0.9, beta2=0.999, eps=1e-15,
+                      tv_weight=1e-4)
+
+
+def train_config(total_steps: int, **kw) -> TrainConfig:
+    v = dict(TRAIN_DEFAULTS)
+    v.update(kw)
+    cfg = TrainConfig()
+    cfg.total_steps = int(total_steps)
+    for k, x in v.items():
+        if k.startswith("lr_"):
+            getattr(cfg, k)[0], getattr(cfg, k)[1] = float(x[0]), float(x[1])
+        else:
+            setattr(cfg, k, float(x))
+    return cfg
 
 
 class Grads(C.Structure):
@@ -83,6 +114,7 @@ def library(path: str = LIB_PATH):
         "fs4d_deform": [vp, i32, i32, vp, i32, vp, vp, vp],
         "fs4d_render": [vp, i32, i32, C.POINTER(Camera), f32, vp, vp, vp, C.POINTER(vp)],
         "fs4d_render_host": [vp, i32, i32, C.POINTER(Camera), f32, vp],
+        "fs4d_render_composed": [vp, C.POINTER(i32), C.POINTER(f32), i32, i32, C.POINTER(Camera), f32, vp, vp, vp],
         "fs4d_render_host_batch": [vp, i32, i32, C.POINTER(Camera), C.POINTER(f32), i32, C.POINTER(vp)],
         "fs4d_reserve": [vp, i32, i32, i32, i64],
         "fs4d_render_async": [vp, i32, i32, C.POINTER(Camera), vp, vp, vp],
@@ -91,11 +123,20 @@ def library(path: str = LIB_PATH):
         "fs4d_frame_pairs": [vp, C.POINTER(i64)],
         "fs4d_last_pairs": [vp, C.POINTER(i64)],
         "fs4d_last_bands": [vp, C.POINTER(i32)],
+        "fs4d_train_create": [vp, i32, C.POINTER(TrainConfig), C.POINTER(vp)],
+        "fs4d_train_step": [vp, i32, C.POINTER(Camera), f32, vp, vp],
+        "fs4d_train_losses": [vp, C.POINTER(f32)],
+        "fs4d_train_steps_done": [vp, C.POINTER(i64)],
+        "fs4d_train_destroy": [vp],
+        "fs4d_read_scene": [vp, i32, C.POINTER(Grads), i32],
+        "fs4d_save_scene": [vp, i32, C.c_char_p],
+        "fs4d_load_scene_file": [vp, C.c_char_p, C.POINTER(i32)],
         "fs4d_set_band_pairs": [vp, i64],
         "fs4d_set_binning": [vp, i32],
         "fs4d_last_binning": [vp, C.POINTER(i32)],
         "fs4d_set_stage_timing": [vp, i32],
         "fs4d_stage_times": [vp, C.POINTER(C.c_float)],
+        "fs4d_backward_times": [vp, C.POINTER(C.c_float)],
         "fs4d_project": [vp, i32, vp, vp, vp, vp, vp, i32, C.POINTER(Camera), C.POINTER(Projected)],
         "fs4d_bin_sort": [vp, i32, vp, vp, i32, i32, i64, vp, vp, vp, C.POINTER(i64)],
         "fs4d_sort_pairs": [vp, i64, i32, vp, vp],
@@ -194,6 +235,26 @@ class Context:
         self._scenes[sid.value] = scene
         return sid.value
 
+    def read_scene(self, sid: int) -> Dict[str, np.ndarray]:
+        """The scene's current parameters (host float32 arrays of the loaded shapes)."""
+        scene = self._scenes[sid]
+        out = {k: np.empty(np.shape(getattr(scene, k)), np.float32) for k in PARAMS}
+        g = Grads(**{k: v.ctypes.data for k, v in out.items()})
+        self.call("fs4d_read_scene", sid, C.byref(g), 0)
+        return out
+
+    def save_scene(self, sid: int, path: str) -> None:
+        self.call("fs4d_save_scene", sid, os.fsencode(path))
+
+    def load_scene_file(self, path: str, like=None) -> int:
+        """Load a scene file; `like` (a scene object of the same shapes) is kept as
+        the binding's record of the scene's sizes."""
+        sid = C.c_int32()
+        self.call("fs4d_load_scene_file", os.fsencode(path), C.byref(sid))
+        if like is not None:
+            self._scenes[sid.value] = like
+        return sid.value
+
     def unload_scene(self, sid: int) -> None:
         self.call("fs4d_unload_scene", sid)
         self._scenes.pop(sid, None)
@@ -226,6 +287,26 @@ class Context:
             nc = torch.empty((cam.height, cam.width), device=dev, dtype=torch.int32)
         cs = camera_struct(cam)
         self.call("fs4d_render", sid, prec, C.byref(cs), float(t), _ptr(image), _ptr(T), _ptr(nc), None)
+        return (image, T, nc) if with_aux else image
+
+    def render_composed(self, sids, cam, t: float, prec: int = FP32, shifts=None, with_aux: bool = False):
+        """One frame of the union of several scenes' deformed Gaussians (composition);
+        shifts: [n][3] world translations, or None."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        image = torch.empty((cam.height, cam.width, 3), device=dev)
+        T = nc = None
+        if with_aux:
+            T = torch.empty((cam.height, cam.width), device=dev)
+            nc = torch.empty((cam.height, cam.width), device=dev, dtype=torch.int32)
+        ids = (C.c_int32 * len(sids))(*[int(v) for v in sids])
+        sh = None
+        if shifts is not None:
+            flat = np.ascontiguousarray(shifts, np.float32).ravel()
+            sh = (C.c_float * flat.size)(*flat.tolist())
+        cs = camera_struct(cam)
+        self.call("fs4d_render_composed", ids, sh, len(sids), prec, C.byref(cs), float(t), _ptr(image), _ptr(T),
+                  _ptr(nc))
         return (image, T, nc) if with_aux else image
 
     def render_saved(self, sid: int, cam, t: float, prec: int = FP32):
@@ -301,6 +382,11 @@ class Context:
         ms = (C.c_float * 6)()
         self.call("fs4d_stage_times", ms)
         return dict(zip(STAGES, [float(v) for v in ms]))
+
+    def backward_times(self) -> Dict[str, float]:
+        ms = (C.c_float * 4)()
+        self.call("fs4d_backward_times", ms)
+        return dict(zip(("composite_bwd", "project_bwd", "mlp_planes_bwd", "weight_grads"), [float(v) for v in ms]))
 
     def last_pairs(self) -> int:
         k = C.c_int64()
@@ -437,6 +523,48 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("retried", C.c_int64),
                 ("batches", C.c_int64), ("deformed", C.c_int64), ("slots", C.c_int32),
                 ("max_concurrent", C.c_int32), ("slot_bytes", C.c_int64), ("peak_slot_bytes", C.c_int64)]
+
+
+class Trainer:
+    """The on-device training step of a loaded scene (fs4d_train_*)."""
+
+    def __init__(self, ctx: "Context", sid: int, total_steps: int, **cfg):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.cfg = train_config(total_steps, **cfg)
+        h = C.c_void_p()
+        ctx.call("fs4d_train_create", sid, C.byref(self.cfg), C.byref(h))
+        self.h = h
+
+    def step(self, cam, t: float, target, prec: int = FP32, losses=None) -> None:
+        cs = camera_struct(cam)
+        st = self.lib.fs4d_train_step(self.h, int(prec), C.byref(cs), float(t), _ptr(target.contiguous()),
+                                      _ptr(losses))
+        if st != 0:
+            raise Fs4dError(st, self.lib.fs4d_last_error(self.ctx.h).decode())
+
+    def losses(self) -> Tuple[float, float]:
+        out = (C.c_float * 2)()
+        st = self.lib.fs4d_train_losses(self.h, out)
+        if st != 0:
+            raise Fs4dError(st, "train_losses")
+        return float(out[0]), float(out[1])
+
+    def steps_done(self) -> int:
+        k = C.c_int64()
+        self.lib.fs4d_train_steps_done(self.h, C.byref(k))
+        return k.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.fs4d_train_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 SERVER_EXPORTS = ("fs4d_server_create", "fs4d_server_submit", "fs4d_server_submit_batch", "fs4d_server_cancel",

@@ -45,6 +45,8 @@ def pixel_matches(value, px, py, base, gs, proj, dbits, tol, rel_tol, depth_tol,
     for mask in range(1 << len(gs)):
         lst = base if mask == 0 else _toggled(base, gs, mask, dbits)
         outs = oracle.pixel_outcomes(lst, px, py, proj, rel_tol, depth_tol)
+        if outs is None:  # many near-threshold decisions (long lists): enumerate more of them
+            outs = oracle.pixel_outcomes(lst, px, py, proj, rel_tol, depth_tol, max_flip=12)
         if outs is None:
             continue
         good = np.abs(outs[:, :3] - value).max(1) <= tol
@@ -101,3 +103,12 @@ def check_frame(img, fr, T=None, nc=None, tol=1e-4, rel_tol=5e-5, px_tol=2e-4, d
              "uncertain_member_tiles": len(members)}
     print("frame parity:", stats)
     return stats
+
+
+def oracle_frame_composed(scenes, shifts, cam, t, tile=16):
+    """The oracle's frame of several scenes composed (Sec. 5.4), as oracle_frame."""
+    p = oracle.project_composed(scenes, shifts, cam, t, tile=tile)
+    img, T, nc, mg, vals, ranges = oracle.composite_projected(p, cam, tile=tile)
+    tx = (cam.width + tile - 1) // tile
+    return dict(img=img, T=T, nc=nc, margin=mg, K=len(vals), proj=p, values=vals, ranges=ranges,
+                dbits=oracle.depth_bits(p["depth"]), tx=tx, tile=tile)

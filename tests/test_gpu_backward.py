@@ -3,7 +3,9 @@ oracle's analytic gradient and against FP64 central finite differences.
 
 Bar, element by element: |g_gpu - g_ref| <= 1e-3 |g_ref| + 1e-5 max |g_ref| of
 the parameter group, and 1e-3 relative for every element above 1% of the
-group's largest.  The floor covers elements that are float32 sums of up to ~1e4
+group's largest; plane values, whose gradients sum one term per Gaussian that
+samples them, add 1e-3 of the sum of those terms' magnitudes (each term within
+1e-3).  The floor covers elements that are float32 sums of up to ~1e4
 per-pixel terms of either sign cancelling to near zero: their rounding error
 (~sqrt(n) 2^-24 of the terms' absolute sum, and the float32 forward values'
 ~1e-6 relative error times that sum) is relative to the terms, not to the sum;
@@ -75,7 +77,12 @@ def masked_dl(s, cam, t, seed):
 
 def check_groups(g, ref, rel=REL, floor=1e-5):
     """Element-wise: |g - ref| <= rel |ref| + floor max|ref| per parameter group,
-    and |g - ref| <= rel |ref| where |ref| > 1% of the group's max."""
+    and |g - ref| <= rel |ref| where |ref| > 1% of the group's max.  A plane value's
+    gradient sums one term per Gaussian that samples it (thousands at a time row
+    of the temporal planes, of either sign): its bound is rel times the sum of the
+    terms' magnitudes (ref['planes_abs'], from the oracle) -- each term within
+    rel -- and the 1%-of-max rule applies where the sum is not dominated by
+    cancellation (|ref| >= 10% of that magnitude)."""
     worst = {}
     for k in GROUPS:
         scale = np.abs(ref[k]).max()
@@ -83,7 +90,10 @@ def check_groups(g, ref, rel=REL, floor=1e-5):
         err = np.abs(g[k] - ref[k])
         bound = rel * np.abs(ref[k]) + floor * scale
         big = np.abs(ref[k]) > 1e-2 * scale
-        worst_rel = float((err[big] / np.abs(ref[k][big])).max())
+        if k == "planes" and "planes_abs" in ref:
+            bound = bound + rel * ref["planes_abs"]
+            big &= np.abs(ref[k]) >= 0.1 * ref["planes_abs"]
+        worst_rel = float((err[big] / np.abs(ref[k][big])).max()) if big.any() else 0.0
         worst[k] = worst_rel
         print(f"{k:15s} max|ref| {scale:.3e}  max err/bound {float((err / bound).max()):.3f}  "
               f"worst rel (|ref| > 1% of max) {worst_rel:.2e}")
@@ -98,7 +108,7 @@ def test_backward_matches_oracle_small(ctx, seed, deg):
     cam = small_camera()
     dl = masked_dl(s, cam, 0.4, seed)
     _, g = gpu_grads(ctx, s, cam, 0.4, dl)
-    ref = oracle.render_backward(s, cam, 0.4, dl)
+    ref = oracle.render_backward(s, cam, 0.4, dl, plane_terms=True)
     check_groups(g, ref)
 
 
@@ -108,7 +118,7 @@ def test_backward_matches_oracle_tiny_scene(ctx):
     cam = sg.tiny_camera()
     dl = masked_dl(s, cam, 0.5, 7)
     _, g = gpu_grads(ctx, s, cam, 0.5, dl)
-    ref = oracle.render_backward(s, cam, 0.5, dl)
+    ref = oracle.render_backward(s, cam, 0.5, dl, plane_terms=True)
     check_groups(g, ref)
 
 
@@ -164,7 +174,7 @@ def test_autograd_function_matches_direct_call(ctx):
     img = fs4d.render_differentiable(ctx, sid, cam, 0.3, params)
     loss = (img * torch.from_numpy(dl.astype(np.float32)).cuda()).sum()
     loss.backward()
-    ref = oracle.render_backward(s, cam, 0.3, dl)
+    ref = oracle.render_backward(s, cam, 0.3, dl, plane_terms=True)
     check_groups({k: params[k].grad.cpu().numpy().astype(np.float64) for k in GROUPS}, ref)
     # the update path: a parameter change reaches the render
     with torch.no_grad():
@@ -184,7 +194,7 @@ def test_backward_matches_oracle_object_256(ctx):
     dl = rng.normal(size=(256, 256, 3))
     dl[oracle.unstable_pixels(s, cam, 0.4, px_tol=5e-4, margin_tol=5e-5)[0]] = 0.0
     _, g = gpu_grads(ctx, s, cam, 0.4, dl)
-    ref = oracle.render_backward(s, cam, 0.4, dl)
+    ref = oracle.render_backward(s, cam, 0.4, dl, plane_terms=True)
     check_groups(g, ref)
 
 
@@ -198,7 +208,7 @@ def test_backward_matches_oracle_object_800(ctx):
     dl = rng.normal(size=(800, 800, 3))
     dl[oracle.unstable_pixels(s, cam, 0.35, px_tol=2e-4, margin_tol=5e-5)[0]] = 0.0
     _, g = gpu_grads(ctx, s, cam, 0.35, dl)
-    ref = oracle.render_backward(s, cam, 0.35, dl)
+    ref = oracle.render_backward(s, cam, 0.35, dl, plane_terms=True)
     check_groups(g, ref)
 
 

@@ -135,7 +135,7 @@ def test_stress_frame_sampled_pixels_match_oracle(ctx, stress, w, h):
         gs = members.get(t_id, [])[:4]
         if not parity.pixel_matches(img[py, px], px, py, base, gs, p, dbits, IMG_TOL, 5e-5, 1e-6):
             bad += 1
-        want = oracle.pixel_outcomes(base, px, py, p)[0, :3]
+        want = oracle.pixel_outcomes(base, px, py, p, 0.0, 0.0)[0, :3]  # the blend as computed
         sq_err += float(((bf[py, px] - want) ** 2).sum())
         n_bf += 3
     psnr = 10 * np.log10(1.0 / max(sq_err / n_bf, 1e-30))

@@ -746,3 +746,51 @@ def test_adam_against_torch_optim_adam():
         tp.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(q, tp.detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+# --------------------------------------------------------------------- composition (Sec. 5.4)
+
+def test_composition_of_one_scene_is_its_render():
+    s = sg.make_tiny(2, n=400, mlp_std=0.2)
+    cam = sg.tiny_camera()
+    p = oracle.project_composed([s], None, cam, 0.4)
+    img, T, nc, *_ = oracle.composite_projected(p, cam)
+    want, Tw, ncw, _, _ = oracle.render(s, cam, 0.4)
+    np.testing.assert_array_equal(img, want)
+    np.testing.assert_array_equal(nc, ncw)
+
+
+def test_composition_of_static_scenes_is_the_render_of_their_union():
+    """With zero head output layers no Gaussian moves, so composing two scenes is
+    the static render of one scene holding both sets of Gaussians (the second
+    translated by its shift)."""
+    a = sg.make_tiny(3, n=300, mlp_std=0.2)
+    b = sg.make_tiny(4, n=250, mlp_std=0.2)
+    shapes = sg.mlp_layer_shapes(16, 64)
+    for s in (a, b):
+        off = 0
+        for k, (o, i) in enumerate(shapes):
+            if k in (3, 5, 7):
+                s.mlp[off:off + o * i + o] = 0.0
+            off += o * i + o
+    b.means = (np.round(b.means * 1024) / 1024).astype(np.float32)  # b.means + shift exact in float32
+    shift = np.array([0.25, -0.125, 0.0625])
+    p = oracle.project_composed([a, b], [np.zeros(3), shift], cam := sg.tiny_camera(), 0.7)
+    img, T, nc, *_ = oracle.composite_projected(p, cam)
+    u = a.copy()
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        extra = getattr(b, k) + (shift.astype(np.float32) if k == "means" else 0)
+        setattr(u, k, np.concatenate([getattr(a, k), extra]).astype(np.float32))
+    want, Tw, ncw, _, _ = oracle.render(u, cam, 0.7, deform=False)
+    np.testing.assert_array_equal(img, want)
+    np.testing.assert_array_equal(nc, ncw)
+
+
+def test_composition_with_a_scene_out_of_view_is_the_scene_alone():
+    a = sg.make_tiny(5, n=300, mlp_std=0.2)
+    b = sg.make_tiny(6, n=300, mlp_std=0.2)
+    cam = sg.tiny_camera()
+    p = oracle.project_composed([a, b], [np.zeros(3), np.array([0.0, -50.0, 0.0])], cam, 0.5)  # behind the camera
+    img, *_ = oracle.composite_projected(p, cam)
+    want, *_ = oracle.render(a, cam, 0.5)
+    np.testing.assert_array_equal(img, want)
