@@ -50,7 +50,7 @@ class OrcProjected(C.Structure):
 
 class OrcGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes",
-                                          "mlp", "planes_abs")]
+                                          "mlp", "planes_abs", "planes_sens")]
 
 
 def lib():
@@ -355,7 +355,8 @@ def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = 
                     plane_terms: bool = False):
     """Gradients of sum(dl_dimage * image) w.r.t. every scene parameter (float64 dict).
     plane_terms: also 'planes_abs', per plane value the sum of the magnitudes of the
-    per-Gaussian terms its gradient adds up."""
+    per-Gaussian terms its gradient adds up, and 'planes_sens', the most a unit
+    error in every Gaussian's output gradients (dX', dr', ds') can change it."""
     h = _SceneHandle(scene)
     cc = _camera(cam)
     g = dict(means=np.zeros((h.n, 3)), log_scales=np.zeros((h.n, 3)), quats=np.zeros((h.n, 4)),
@@ -363,6 +364,7 @@ def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = 
              planes=np.zeros(h.arrays["planes"].shape[0]), mlp=np.zeros(h.arrays["mlp"].shape[0]))
     if plane_terms:
         g["planes_abs"] = np.zeros(h.arrays["planes"].shape[0])
+        g["planes_sens"] = np.zeros(h.arrays["planes"].shape[0])
     G = OrcGrads(**{k: v.ctypes.data for k, v in g.items()})
     rc = lib().orc_render_backward(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile),
                                    np.ascontiguousarray(dl_dimage, np.float64), C.byref(G))

@@ -903,6 +903,30 @@ extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam
       }
       for (int i = 0; i < hin; ++i) gfh[i] += gpre * (double)s->mlp[Lo.w[0] + (int64_t)o * hin + i];
     }
+    // Test support: |J|^T 1, the sensitivity of f_h's gradient to a unit error in each of
+    // this Gaussian's ten output gradients (dX', dr', ds'), through |W| with the same
+    // ReLU masks; propagated to the planes below as planes_sens.
+    std::vector<double> sfh;
+    if (G->planes_sens) {
+      std::vector<double> sfd(W, 0.0), sa1(W, 0.0);
+      sfh.assign(hin, 0.0);
+      for (int hd = 0; hd < 3; ++hd) {
+        const double* HID = &hid[((int64_t)g * 3 + hd) * W];
+        const int ko = 3 + 2 * hd, kh = 2 + 2 * hd;
+        std::vector<double> shid(W, 0.0);
+        for (int o = 0; o < kHeadOut[hd]; ++o)
+          for (int i = 0; i < W; ++i) shid[i] += std::fabs((double)s->mlp[Lo.w[ko] + (int64_t)o * W + i]);
+        for (int o = 0; o < W; ++o)
+          if (HID[o] > 0.0)
+            for (int i = 0; i < W; ++i) sfd[i] += shid[o] * std::fabs((double)s->mlp[Lo.w[kh] + (int64_t)o * W + i]);
+      }
+      for (int o = 0; o < W; ++o)
+        if (FD[o] > 0.0)
+          for (int i = 0; i < W; ++i) sa1[i] += sfd[o] * std::fabs((double)s->mlp[Lo.w[1] + (int64_t)o * W + i]);
+      for (int o = 0; o < W; ++o)
+        if (A1[o] > 0.0)
+          for (int i = 0; i < hin; ++i) sfh[i] += sa1[o] * std::fabs((double)s->mlp[Lo.w[0] + (int64_t)o * hin + i]);
+    }
     // Eq. 5: f_l[c] = prod_p v_p[c]; v_p = bilinear(R_{l,p}) at (c_a, c_b)
     double c4[4];
     normalise(s, &xyz[3 * (int64_t)g], t, c4);
@@ -932,6 +956,13 @@ extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam
             G->planes[off + e10] += gv * fa[p] * (1 - fb[p]);
             G->planes[off + e01] += gv * (1 - fa[p]) * fb[p];
             G->planes[off + e11] += gv * fa[p] * fb[p];
+          }
+          if (G->planes_sens) {
+            const double sv = sfh[l * h + c] * std::fabs(others);
+            G->planes_sens[off + e00] += sv * (1 - fa[p]) * (1 - fb[p]);
+            G->planes_sens[off + e10] += sv * fa[p] * (1 - fb[p]);
+            G->planes_sens[off + e01] += sv * (1 - fa[p]) * fb[p];
+            G->planes_sens[off + e11] += sv * fa[p] * fb[p];
           }
           if (G->planes_abs) {  // magnitudes of the same terms (test support: conditioning of the sums)
             G->planes_abs[off + e00] += std::fabs(gv * (1 - fa[p]) * (1 - fb[p]));

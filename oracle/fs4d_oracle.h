@@ -125,6 +125,10 @@ typedef struct orc_grads {
   double* mlp;            /* flat, like the scene's mlp */
   double* planes_abs;     /* optional: per plane value, the sum over Gaussians of the
                              magnitudes of the terms its gradient sums (test support) */
+  double* planes_sens;    /* optional: per plane value, the change of its gradient that a
+                             unit error in every Gaussian's ten output gradients (dX', dr',
+                             ds') can cause at most: sum over Gaussians of |J|^T 1 (test
+                             support: propagation of upstream float32 error) */
 } orc_grads;
 
 int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,

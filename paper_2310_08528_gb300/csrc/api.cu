@@ -1436,9 +1436,13 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   const long long n = s->n, K = f->pairs;
   const int hin = s->mg.hin;
   const size_t act_floats = (size_t)n * (hin + 64 + 64 + 192 + 10 + 192 + 64 + 64);
-  size_t wp = 0;
-  for (int O : {64, 4})
-    for (int I : {std::max(hin, 64), 64}) wp = std::max<size_t>(wp, (size_t)wgrad_partial_floats(n, O, I));
+  size_t wtot = 0;
+  {
+    size_t tot_floats;
+    auto Ls = src_layers(hin, kWidth, &tot_floats);
+    wtot = (size_t)tot_floats;  // every layer's O*I + O entries
+  }
+  const size_t wp = (size_t)wgrad_chunks(n) * wtot;
   if (w.grad_pair.bytes < 4 * kPairGrad * (size_t)std::max(K, 1ll) || w.gd.bytes < 40 * (size_t)n ||
       w.acts.bytes < 4 * act_floats || w.wpartial.bytes < 4 * wp) {
     FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1495,18 +1499,20 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   if (gr->mlp) {
     size_t tot;
     auto L = src_layers(hin, kWidth, &tot);
-    float* wp_buf = P<float>(w.wpartial);
     const int col0[3] = {0, 3, 7};
-    FS4D_CUDA(c, launch_wgrad(mb.act.d1, mb.act.fh, n, 64, hin, wp_buf, gr->mlp + L[0].w, gr->mlp + L[0].b, c->stream));
-    FS4D_CUDA(c, launch_wgrad(mb.act.d2, mb.act.a1, n, 64, 64, wp_buf, gr->mlp + L[1].w, gr->mlp + L[1].b, c->stream));
+    WgradArgs wa{};
+    wa.n = n;
+    wa.partial = P<float>(w.wpartial);
+    auto add = [&](const float* D, const float* X, int O, int I, const SrcLayer& l) {
+      wa.l[wa.n_layers++] = WgradLayer{D, X, O, I, gr->mlp + l.w, gr->mlp + l.b, 0};
+    };
+    add(mb.act.d1, mb.act.fh, 64, hin, L[0]);
+    add(mb.act.d2, mb.act.a1, 64, 64, L[1]);
     for (int h = 0; h < 3; ++h) {
-      const SrcLayer& l1 = L[2 + 2 * h];
-      const SrcLayer& l2 = L[3 + 2 * h];
-      FS4D_CUDA(c, launch_wgrad(mb.act.dh + (size_t)64 * h * n, mb.act.fd, n, 64, 64, wp_buf, gr->mlp + l1.w,
-                                gr->mlp + l1.b, c->stream));
-      FS4D_CUDA(c, launch_wgrad(mb.act.dout + (size_t)col0[h] * n, mb.act.hid + (size_t)64 * h * n, n, l2.out, 64,
-                                wp_buf, gr->mlp + l2.w, gr->mlp + l2.b, c->stream));
+      add(mb.act.dh + (size_t)64 * h * n, mb.act.fd, 64, 64, L[2 + 2 * h]);
+      add(mb.act.dout + (size_t)col0[h] * n, mb.act.hid + (size_t)64 * h * n, L[3 + 2 * h].out, 64, L[3 + 2 * h]);
     }
+    FS4D_CUDA(c, launch_wgrad(wa, c->stream));
   }
   bmark(4);
   return FS4D_OK;

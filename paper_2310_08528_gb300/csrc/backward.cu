@@ -21,6 +21,8 @@
 //      Gaussians share a cell).
 //  wgrad kernels         dW = D X^T over all Gaussians as per-chunk partial sums
 //      followed by a fixed-order reduction (deterministic).
+#include <algorithm>
+
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
@@ -351,7 +353,9 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
 
 // ------------------------------------------------------------------ MLP + HexPlane
 
-constexpr int kMT = 128;  // threads of the MLP backward CTA
+// Threads of the MLP backward CTA (one CTA per SM: the weights and the activation
+// columns fill shared memory): 256 where they fit, else 128.
+constexpr int kMTMax = 256;
 
 __device__ __forceinline__ void axis_setup(float u, int R, int& i0, float& f, float& dfdu) {
   const float uc = fminf(1.f, fmaxf(-1.f, u));
@@ -364,14 +368,14 @@ __device__ __forceinline__ void axis_setup(float u, int R, int& i0, float& f, fl
 }
 
 // y = b + Wt^T x over IN inputs read from this thread's shared-memory column.
-template <int IN>
+template <int IN, int MT>
 __device__ __forceinline__ void dense64(const float* __restrict__ Wt, const float* __restrict__ b,
                                         const float* __restrict__ col, float (&y)[kWidth]) {
 #pragma unroll
   for (int o = 0; o < kWidth; ++o) y[o] = b[o];
 #pragma unroll 2
   for (int i = 0; i < IN; ++i) {
-    const float x = col[i * kMT];
+    const float x = col[i * MT];
     const float4* w4 = reinterpret_cast<const float4*>(Wt + i * kWidth);
 #pragma unroll
     for (int q = 0; q < kWidth / 4; ++q) {
@@ -385,7 +389,7 @@ __device__ __forceinline__ void dense64(const float* __restrict__ Wt, const floa
 }
 
 // gcol[i] (+)= sum_o Wt[i][o] d[o] for i < IN.
-template <int IN, bool ACC>
+template <int IN, bool ACC, int MT>
 __device__ __forceinline__ void dense64_bwd(const float* __restrict__ Wt, const float (&d)[kWidth], float* gcol) {
 #pragma unroll 2
   for (int i = 0; i < IN; ++i) {
@@ -399,16 +403,16 @@ __device__ __forceinline__ void dense64_bwd(const float* __restrict__ Wt, const 
       s = fmaf(ww.z, d[4 * q + 2], s);
       s = fmaf(ww.w, d[4 * q + 3], s);
     }
-    gcol[i * kMT] = ACC ? gcol[i * kMT] + s : s;
+    gcol[i * MT] = ACC ? gcol[i * MT] + s : s;
   }
 }
 
-template <int OUT>
+template <int OUT, int MT>
 __device__ __forceinline__ void head_bwd(const float* __restrict__ sw, const MlpGeomT& mg, int layer, float* col,
                                          float* gcol, const float* dout, float* hid_out, float* dh_out,
                                          long long n, long long g) {
   float y[kWidth];
-  dense64<kWidth>(sw + mg.w[layer], sw + mg.b[layer], col, y);
+  dense64<kWidth, MT>(sw + mg.w[layer], sw + mg.b[layer], col, y);
   const float* W2 = sw + mg.w[layer + 1];  // [64][OUT]
   float d[kWidth];
 #pragma unroll
@@ -420,19 +424,19 @@ __device__ __forceinline__ void head_bwd(const float* __restrict__ sw, const Mlp
     d[o] = y[o] > 0.f ? s : 0.f;
     dh_out[(long long)o * n + g] = d[o];
   }
-  dense64_bwd<kWidth, true>(sw + mg.w[layer], d, gcol);
+  dense64_bwd<kWidth, true, MT>(sw + mg.w[layer], d, gcol);
 }
 
-template <int H, int L>
-__global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
+template <int H, int L, int MT>
+__global__ void __launch_bounds__(MT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
   constexpr int HL = H * L;
   constexpr int ROWS = HL > kWidth ? HL : kWidth;
   extern __shared__ float4 smem4[];
   const DeformArgs& f = a.f;
   float* sw = reinterpret_cast<float*>(smem4);
   float* colbase = sw + f.mg.total;
-  float* gcolbase = colbase + ROWS * kMT;
-  for (int i = threadIdx.x; i < f.mg.total / 4; i += kMT)
+  float* gcolbase = colbase + ROWS * MT;
+  for (int i = threadIdx.x; i < f.mg.total / 4; i += MT)
     smem4[i] = __ldg(reinterpret_cast<const float4*>(f.mlp_t) + i);
   __syncthreads();
   const PlaneGeom& pg = f.pg;
@@ -440,7 +444,11 @@ __global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
   float* gcol = gcolbase + threadIdx.x;
   const long long n = f.n;
   const MlpActs& act = a.act;
-  for (long long g = (long long)blockIdx.x * kMT + threadIdx.x; g < n; g += (long long)gridDim.x * kMT) {
+  // Gaussians in the scene's Morton work order (neighbouring plane cells for the
+  // taps and the gradient atomics of one warp); the activation columns are kept in
+  // that order too (the weight-gradient sums do not depend on the column order)
+  for (long long ii = (long long)blockIdx.x * MT + threadIdx.x; ii < n; ii += (long long)gridDim.x * MT) {
+    const long long g = f.perm ? (long long)f.perm[ii] : ii;
     const float X[3] = {f.means[3 * g], f.means[3 * g + 1], f.means[3 * g + 2]};
     float c[4], dcdx[3];
 #pragma unroll
@@ -480,51 +488,51 @@ __global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
       }
 #pragma unroll
       for (int k = 0; k < H; ++k) {
-        col[(l * H + k) * kMT] = fv[k];
-        act.fh[(long long)(l * H + k) * n + g] = fv[k];
+        col[(l * H + k) * MT] = fv[k];
+        act.fh[(long long)(l * H + k) * n + ii] = fv[k];
       }
     }
     float y[kWidth];
-    dense64<HL>(sw + f.mg.w[0], sw + f.mg.b[0], col, y);
+    dense64<HL, MT>(sw + f.mg.w[0], sw + f.mg.b[0], col, y);
 #pragma unroll
     for (int o = 0; o < kWidth; ++o) {
       const float v = fmaxf(y[o], 0.f);
-      act.a1[(long long)o * n + g] = v;
-      col[o * kMT] = v;
+      act.a1[(long long)o * n + ii] = v;
+      col[o * MT] = v;
     }
-    dense64<kWidth>(sw + f.mg.w[1], sw + f.mg.b[1], col, y);
+    dense64<kWidth, MT>(sw + f.mg.w[1], sw + f.mg.b[1], col, y);
 #pragma unroll
     for (int o = 0; o < kWidth; ++o) {
       const float v = fmaxf(y[o], 0.f);
-      act.fd[(long long)o * n + g] = v;
-      col[o * kMT] = v;
+      act.fd[(long long)o * n + ii] = v;
+      col[o * MT] = v;
     }
     // ---- heads backward (output deltas = dL/d(X', r', s'), Eq. 6)
     float dout[kDeltaDim];
 #pragma unroll
     for (int j = 0; j < kDeltaDim; ++j) {
       dout[j] = a.gd[10 * g + j];
-      act.dout[(long long)j * n + g] = dout[j];
+      act.dout[(long long)j * n + ii] = dout[j];
     }
 #pragma unroll
-    for (int i = 0; i < kWidth; ++i) gcol[i * kMT] = 0.f;
-    head_bwd<3>(sw, f.mg, 2, col, gcol, dout, act.hid, act.dh, n, g);
-    head_bwd<4>(sw, f.mg, 4, col, gcol, dout + 3, act.hid + 64 * n, act.dh + 64 * n, n, g);
-    head_bwd<3>(sw, f.mg, 6, col, gcol, dout + 7, act.hid + 128 * n, act.dh + 128 * n, n, g);
+    for (int i = 0; i < kWidth; ++i) gcol[i * MT] = 0.f;
+    head_bwd<3, MT>(sw, f.mg, 2, col, gcol, dout, act.hid, act.dh, n, ii);
+    head_bwd<4, MT>(sw, f.mg, 4, col, gcol, dout + 3, act.hid + 64 * n, act.dh + 64 * n, n, ii);
+    head_bwd<3, MT>(sw, f.mg, 6, col, gcol, dout + 7, act.hid + 128 * n, act.dh + 128 * n, n, ii);
     // ---- phi_d backward
     float d[kWidth];
 #pragma unroll
     for (int o = 0; o < kWidth; ++o) {
-      d[o] = col[o * kMT] > 0.f ? gcol[o * kMT] : 0.f;
-      act.d2[(long long)o * n + g] = d[o];
+      d[o] = col[o * MT] > 0.f ? gcol[o * MT] : 0.f;
+      act.d2[(long long)o * n + ii] = d[o];
     }
-    dense64_bwd<kWidth, false>(sw + f.mg.w[1], d, gcol);
+    dense64_bwd<kWidth, false, MT>(sw + f.mg.w[1], d, gcol);
 #pragma unroll
     for (int o = 0; o < kWidth; ++o) {
-      d[o] = act.a1[(long long)o * n + g] > 0.f ? gcol[o * kMT] : 0.f;
-      act.d1[(long long)o * n + g] = d[o];
+      d[o] = act.a1[(long long)o * n + ii] > 0.f ? gcol[o * MT] : 0.f;
+      act.d1[(long long)o * n + ii] = d[o];
     }
-    dense64_bwd<HL, false>(sw + f.mg.w[0], d, gcol);  // gcol[0..HL) = dL/df_h
+    dense64_bwd<HL, false, MT>(sw + f.mg.w[0], d, gcol);  // gcol[0..HL) = dL/df_h
     // ---- Eq. 5 backward: plane cells and the sampling position
     float gx[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -567,7 +575,7 @@ __global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
 #pragma unroll
             for (int r = 0; r < 6; ++r)
               if (r != p) others *= v[r][k];
-            gv[e] = gcol[(l * H + k) * kMT] * others;
+            gv[e] = gcol[(l * H + k) * MT] * others;
             const float p00 = __ldg(P + k), p10 = __ldg(P + H + k), p01 = __ldg(P + (long long)Ra[p] * H + k),
                         p11 = __ldg(P + (long long)Ra[p] * H + H + k);
             sa += gv[e] * ((1.f - fb[p]) * (p10 - p00) + fb[p] * (p11 - p01));
@@ -595,81 +603,119 @@ __global__ void __launch_bounds__(kMT, 1) mlp_bwd_kernel(MlpBwdArgs a) {
   }
 }
 
+template <int H, int L, int MT>
+cudaError_t launch_mlp_mt(const MlpBwdArgs& a, size_t smem, cudaStream_t s) {
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [&] {
+    return cudaFuncSetAttribute(mlp_bwd_kernel<H, L, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
+  const long long need = ((long long)a.f.n + MT - 1) / MT;
+  const int grid = (int)(need < sms ? need : sms);
+  mlp_bwd_kernel<H, L, MT><<<grid, MT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int H, int L>
 cudaError_t launch_mlp_t(const MlpBwdArgs& a, cudaStream_t s) {
   constexpr int HL = H * L;
   constexpr int rows = HL > kWidth ? HL : kWidth;
-  const size_t smem = sizeof(float) * ((size_t)a.f.mg.total + 2 * (size_t)rows * kMT);
-  static PerDeviceFlag attr;
-  cudaError_t e = once_per_device(attr, [&] {
-    return cudaFuncSetAttribute(mlp_bwd_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (e != cudaSuccess) return e;
-  const int sms = device_sm_count();
-  const long long need = ((long long)a.f.n + kMT - 1) / kMT;
-  const int grid = (int)(need < sms ? need : sms);
-  mlp_bwd_kernel<H, L><<<grid, kMT, smem, s>>>(a);
-  return cudaGetLastError();
+  const size_t big = sizeof(float) * ((size_t)a.f.mg.total + 2 * (size_t)rows * kMTMax);
+  if (big <= 227 * 1024) return launch_mlp_mt<H, L, kMTMax>(a, big, s);
+  return launch_mlp_mt<H, L, kMTMax / 2>(a, sizeof(float) * ((size_t)a.f.mg.total + 2 * (size_t)rows * (kMTMax / 2)),
+                                        s);
 }
 
 // ------------------------------------------------------------------ weight gradients
 
-constexpr int kWChunk = 1024;  // Gaussians per partial
+constexpr int kWChunk = 256;   // Gaussians per partial (~400 chunks per layer at 100k Gaussians)
 constexpr int kWStage = 32;    // Gaussians staged per step
-constexpr int kWMaxPer = 25;   // entries per thread: (64*96 + 64) / 256 rounded up
+constexpr int kWBlocks = 2;    // 4x4 output blocks per thread: (64/4) x ceil(97/4) = 400 <= 256 x 2
 
-__global__ void __launch_bounds__(256) wgrad_partial_kernel(const float* __restrict__ D, const float* __restrict__ X,
-                                                            long long n, int O, int I, float* __restrict__ partial) {
-  __shared__ float sD[kWStage][64];
-  __shared__ float sX[kWStage][97];
+// Partial sums over one chunk of Gaussians of dW[o][i] = sum_n D[o][n] X[i][n] and
+// db[o] = sum_n D[o][n] (the bias as an input column of ones), register-blocked:
+// each thread owns up to two 4x4 blocks of (o, i) and per staged Gaussian reads
+// 4 D and 4 X values (two 128-bit shared loads) for 16 FMAs per block.
+__global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constant__ WgradArgs wa) {
+  const WgradLayer& ly = wa.l[blockIdx.y];
+  const float* __restrict__ D = ly.D;
+  const float* __restrict__ X = ly.X;
+  const long long n = wa.n;
+  const int O = ly.O, I = ly.I;
+  float* __restrict__ partial = wa.partial + ly.part_off;
+  __shared__ __align__(16) float sD[kWStage][64];
+  __shared__ __align__(16) float sX[kWStage][100];  // I + 1 <= 97 columns, padded to a multiple of 4
   const int E = O * I + O;
+  const int IB = (I + 1 + 3) / 4, OB = (O + 3) / 4;  // column blocks include the bias column I
   const long long n0 = (long long)blockIdx.x * kWChunk;
   const long long n1 = min(n, n0 + kWChunk);
-  float acc[kWMaxPer];
+  float acc[kWBlocks][16];
 #pragma unroll
-  for (int k = 0; k < kWMaxPer; ++k) acc[k] = 0.f;
-  for (long long b = n0; b < n1; b += kWStage) {
-    const int m = (int)min((long long)kWStage, n1 - b);
+  for (int b = 0; b < kWBlocks; ++b)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[b][k] = 0.f;
+  for (long long b0 = n0; b0 < n1; b0 += kWStage) {
+    const int m = (int)min((long long)kWStage, n1 - b0);
     __syncthreads();
-    for (int t = threadIdx.x; t < kWStage * O; t += 256) {
+    for (int t = threadIdx.x; t < kWStage * 64; t += 256) {
       const int o = t / kWStage, j = t % kWStage;
-      sD[j][o] = j < m ? D[(long long)o * n + b + j] : 0.f;
+      sD[j][o] = (j < m && o < O) ? D[(long long)o * n + b0 + j] : 0.f;
     }
-    for (int t = threadIdx.x; t < kWStage * I; t += 256) {
+    for (int t = threadIdx.x; t < kWStage * 100; t += 256) {
       const int i = t / kWStage, j = t % kWStage;
-      sX[j][i] = j < m ? X[(long long)i * n + b + j] : 0.f;
+      sX[j][i] = j >= m ? 0.f : (i < I ? X[(long long)i * n + b0 + j] : (i == I ? 1.f : 0.f));
     }
-    for (int j = threadIdx.x; j < kWStage; j += 256) sX[j][I] = j < m ? 1.f : 0.f;  // bias column
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kWMaxPer; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      if (e >= E) break;
-      const int o = e < O * I ? e / I : e - O * I;
-      const int i = e < O * I ? e % I : I;
-      float s = acc[k];
-      for (int j = 0; j < kWStage; ++j) s = fmaf(sD[j][o], sX[j][i], s);
-      acc[k] = s;
+    for (int b = 0; b < kWBlocks; ++b) {
+      const int blk = threadIdx.x + 256 * b;
+      if (blk >= OB * IB) break;
+      const int ob = blk / IB, ib = blk % IB;
+      float* a = acc[b];
+#pragma unroll 4
+      for (int j = 0; j < kWStage; ++j) {
+        const float4 d4 = *reinterpret_cast<const float4*>(&sD[j][4 * ob]);
+        const float4 x4 = *reinterpret_cast<const float4*>(&sX[j][4 * ib]);
+        const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a[4 * r + c] = fmaf(dv[r], xv[c], a[4 * r + c]);
+      }
     }
   }
+  // entry layout: W[o][i] at o * I + i, then b[o] at O * I + o
 #pragma unroll
-  for (int k = 0; k < kWMaxPer; ++k) {
-    const int e = threadIdx.x + 256 * k;
-    if (e < E) partial[(long long)blockIdx.x * E + e] = acc[k];
+  for (int b = 0; b < kWBlocks; ++b) {
+    const int blk = threadIdx.x + 256 * b;
+    if (blk >= OB * IB) break;
+    const int ob = blk / IB, ib = blk % IB;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int o = 4 * ob + r, i = 4 * ib + c;
+        if (o >= O || i > I) continue;
+        const int e = i < I ? o * I + i : O * I + o;
+        partial[(long long)blockIdx.x * E + e] = acc[b][4 * r + c];
+      }
   }
 }
 
-__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int chunks, int O, int I, float* gW,
-                                    float* gb) {
+__global__ void wgrad_reduce_kernel(const __grid_constant__ WgradArgs wa) {
+  const WgradLayer& ly = wa.l[blockIdx.y];
+  const int O = ly.O, I = ly.I;
   const int E = O * I + O;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
+  const float* partial = wa.partial + ly.part_off;
   float s = 0.f;
-  for (int c = 0; c < chunks; ++c) s += partial[(long long)c * E + e];  // fixed order: deterministic
+  for (int c = 0; c < wa.chunks; ++c) s += partial[(long long)c * E + e];  // fixed order: deterministic
   if (e < O * I)
-    gW[e] += s;
+    ly.gW[e] += s;
   else
-    gb[e - O * I] += s;
+    ly.gb[e - O * I] += s;
 }
 
 }  // namespace
@@ -699,20 +745,24 @@ cudaError_t launch_mlp_bwd(const MlpBwdArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-long long wgrad_partial_floats(long long n, int O, int I) {
-  return ((n + kWChunk - 1) / kWChunk) * (long long)(O * I + O);
-}
+long long wgrad_chunks(long long n) { return (n + kWChunk - 1) / kWChunk; }
 
-cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int I, float* partial, float* gW,
-                         float* gb, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  if (O > 64 || I > 96 || O * I + O > 256 * kWMaxPer) return cudaErrorInvalidValue;
-  const int chunks = (int)((n + kWChunk - 1) / kWChunk);
-  wgrad_partial_kernel<<<chunks, 256, 0, s>>>(D, X, n, O, I, partial);
+cudaError_t launch_wgrad(WgradArgs& a, cudaStream_t s) {
+  if (a.n <= 0 || a.n_layers <= 0) return cudaSuccess;
+  a.chunks = (int)wgrad_chunks(a.n);
+  int maxE = 0;
+  long long off = 0;
+  for (int k = 0; k < a.n_layers; ++k) {
+    if (a.l[k].O > 64 || a.l[k].I > 96) return cudaErrorInvalidValue;
+    const int E = a.l[k].O * a.l[k].I + a.l[k].O;
+    a.l[k].part_off = off;
+    off += (long long)a.chunks * E;
+    maxE = std::max(maxE, E);
+  }
+  wgrad_partial_kernel<<<dim3(a.chunks, a.n_layers), 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int E = O * I + O;
-  wgrad_reduce_kernel<<<(E + 255) / 256, 256, 0, s>>>(partial, chunks, O, I, gW, gb);
+  wgrad_reduce_kernel<<<dim3((maxE + 255) / 256, a.n_layers), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

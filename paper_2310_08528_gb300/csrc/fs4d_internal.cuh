@@ -369,11 +369,26 @@ struct MlpBwdArgs {
 cudaError_t launch_composite_bwd(const CompositeBwdArgs& a, cudaStream_t s);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, cudaStream_t s);
 cudaError_t launch_mlp_bwd(const MlpBwdArgs& a, cudaStream_t s);
-// dW[o][i] += sum_n D[o][n] X[i][n], db[o] += sum_n D[o][n], through a [chunks][O*I+O] partial buffer
-// (deterministic two-stage reduction).  W and b are in the source layout (W[out][in] then b).
-long long wgrad_partial_floats(long long n, int O, int I);
-cudaError_t launch_wgrad(const float* D, const float* X, long long n, int O, int I, float* partial, float* gW,
-                         float* gb, cudaStream_t s);
+// dW[o][i] += sum_n D[o][n] X[i][n], db[o] += sum_n D[o][n] for up to 8 layers in one launch, through
+// per-chunk partial sums (deterministic two-stage reduction).  W and b in the source layout
+// (W[out][in] then b); D [O][n], X [I][n] feature-major.
+struct WgradLayer {
+  const float* D;
+  const float* X;
+  int O, I;
+  float* gW;
+  float* gb;
+  long long part_off;  // set by launch_wgrad
+};
+struct WgradArgs {
+  WgradLayer l[8];
+  int n_layers;
+  long long n;
+  int chunks;          // set by launch_wgrad
+  float* partial;      // wgrad_chunks(n) x sum of (O*I + O) floats
+};
+long long wgrad_chunks(long long n);
+cudaError_t launch_wgrad(WgradArgs& a, cudaStream_t s);
 
 }  // namespace fs4d
 

@@ -32,7 +32,8 @@ constexpr int kMaxPasses = 8;
 
 __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __restrict__ keys,
                                                    const uint32_t* __restrict__ n_dev, long long n_bound,
-                                                   int first_bit, int passes, uint32_t* __restrict__ hist) {
+                                                   int first_bit, int key_bits, int passes,
+                                                   uint32_t* __restrict__ hist) {
   pdl_wait();
   pdl_trigger();
   __shared__ uint32_t s_hist[kMaxPasses][kRadix];
@@ -45,8 +46,9 @@ __global__ void __launch_bounds__(256) hist_kernel(const unsigned long long* __r
     const bool valid = i < n;
     const unsigned long long k = valid ? keys[i] : 0ull;
     for (int p = 0; p < passes; ++p) {
-      const uint32_t d = valid ? (uint32_t)(k >> (first_bit + 8 * p)) & 255u : 256u;
-      const uint32_t peers = digit_peers(d, d < 256u);
+      const int bits = min(8, key_bits - 8 * p);
+      const uint32_t d = valid ? (uint32_t)(k >> (first_bit + 8 * p)) & ((1u << bits) - 1u) : 256u;
+      const uint32_t peers = digit_peers(d, d < 256u, bits);
       if (d < 256u && (peers & lane_lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
     }
   }
@@ -72,6 +74,7 @@ struct PassArgs {
   uint32_t* part_counter;   // this pass's ticket, zeroed
   uint32_t* status;
   uint32_t spin_limit;      // polls of the look-back wait before it gives up
+  int bits;                 // significant bits of this pass's digit (<= 8; the key's last bits)
 };
 
 template <int ITEMS>
@@ -161,12 +164,12 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     const bool valid = idx < n;
     k[i] = valid ? keys_in[idx] : 0ull;
     v[i] = (VALS && valid) ? values_in[idx] : 0u;
-    dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & 255u : 256u);
+    dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & ((1u << a.bits) - 1u) : 256u);
   }
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const uint32_t d = dig[i];
-    const uint32_t peers = digit_peers(d, d < 256u);
+    const uint32_t peers = digit_peers(d, d < 256u, a.bits);
     uint32_t before = 0;
     if (d < 256u) before = sm.warp_cnt[warp][d];
     __syncwarp();
@@ -237,20 +240,221 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
     }
     st_relaxed_u32(lb, kFlagInc | ((prev + total) & kValMask));
   }
-  sm.prev_off[tid] = prev;
+  sm.prev_off[tid] = sm.global_off[tid] + prev - sm.block_off[tid];
   __syncthreads();
 
-  // Scatter: consecutive slots of one digit go to consecutive addresses.
+  // Scatter: consecutive slots of one digit go to consecutive addresses
+  // (prev_off holds global + look-back - local offset of each digit).
   const int m = (int)min((long long)kPartPairs, n - base);
   for (int j = tid; j < m; j += kThreads) {
     const unsigned long long key = sm.keys[j];
-    const uint32_t d = (uint32_t)(key >> a.shift) & 255u;
-    const uint32_t out = sm.global_off[d] + sm.prev_off[d] + ((uint32_t)j - sm.block_off[d]);
+    const uint32_t d = (uint32_t)(key >> a.shift) & ((1u << a.bits) - 1u);
+    const uint32_t out = sm.prev_off[d] + (uint32_t)j;
     if ((long long)out < n) {  // always true when the histogram matches the keys
       keys_out[out] = key;
       if (VALS) values_out[out] = sm.values[j];
     }
   }
+}
+
+// ---------------------------------------------------------------- large sorts
+// The same pass as a persistent kernel for large sorts: one CTA per resident slot
+// loops over 4096-key partitions in ticket order and, while it ranks, looks back
+// and scatters partition p, the keys (and values) of its next partition are already
+// on their way into the other half of a double buffer in shared memory (cp.async),
+// so the DRAM latency of the loads overlaps the work of the previous partition.
+// The next ticket is taken before the current partition is finished; every ticket
+// below it belongs to a CTA that is running or done, and a CTA works through its
+// tickets in increasing order, so the lowest unfinished partition is always being
+// worked on and every look-back wait ends.
+constexpr int kPItems = 16;
+constexpr int kPPart = kThreads * kPItems;  // 4096
+
+template <bool VALS>
+struct PersistSmem {
+  unsigned long long keys[2][kPPart];  // loaded keys; the current half is reused for the local sort
+  uint32_t values[VALS ? 2 : 1][VALS ? kPPart : 1];
+  uint32_t warp_cnt[kWarps][kRadix];
+  uint32_t global_off[kRadix];
+  uint32_t block_off[kRadix];
+  uint32_t prev_off[kRadix];
+  uint32_t scan_tmp[kWarps];
+  uint32_t part[2];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, uint32_t src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+
+// Queue the loads of partition `part` (elements [base, base + m)) into half `b`:
+// 16-byte chunks, the ragged end zero-filled (its source address clamped to the
+// partition's first element, which is valid).
+template <bool VALS>
+__device__ __forceinline__ void persist_load(PersistSmem<VALS>& sm, int b, const unsigned long long* keys_in,
+                                             const uint32_t* values_in, long long base, int m) {
+  const int tid = threadIdx.x;
+  for (int c = tid; c < kPPart / 2; c += kThreads) {  // 2 keys per chunk
+    const int e = 2 * c;
+    const int valid = max(0, min(2, m - e));
+    const unsigned long long* src = keys_in + base + (valid ? e : 0);
+    cp_async16(&sm.keys[b][e], src, 8u * (uint32_t)valid);
+  }
+  if (VALS) {
+    for (int c = tid; c < kPPart / 4; c += kThreads) {  // 4 values per chunk
+      const int e = 4 * c;
+      const int valid = max(0, min(4, m - e));
+      const uint32_t* src = values_in + base + (valid ? e : 0);
+      cp_async16(&sm.values[b][e], src, 4u * (uint32_t)valid);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(kThreads, 2) onesweep_persist_kernel(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PersistSmem<VALS>& sm = *reinterpret_cast<PersistSmem<VALS>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id(), warp = tid / 32;
+  pdl_wait();
+  pdl_trigger();
+  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
+  const long long parts = (n + kPPart - 1) / kPPart;
+  if (tid == 0) sm.part[0] = atomicAdd(a.part_counter, 1u);
+  const uint32_t h = a.hist[tid];
+  sm.global_off[tid] = block_excl_scan(h, sm.scan_tmp);  // (its barriers publish sm.part[0])
+  long long cur = sm.part[0];
+  if (cur >= parts) return;  // uniform
+  if (__syncthreads_or((long long)h == n)) {
+    // every key has the same digit: the pass keeps the order (copy this CTA's partitions)
+    for (; cur < parts;) {
+      const long long base = cur * kPPart;
+      const long long m = min((long long)kPPart, n - base);
+      for (long long i = tid; i < m; i += kThreads) {
+        a.keys_out[base + i] = a.keys_in[base + i];
+        if (VALS) a.values_out[base + i] = a.values_in[base + i];
+      }
+      __syncthreads();
+      if (tid == 0) sm.part[0] = atomicAdd(a.part_counter, 1u);
+      __syncthreads();
+      cur = sm.part[0];
+    }
+    return;
+  }
+  persist_load<VALS>(sm, 0, a.keys_in, a.values_in, cur * kPPart, (int)min((long long)kPPart, n - cur * kPPart));
+  const uint32_t lt = lanemask_lt();
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    // the next partition's ticket, and its loads into the other half
+    if (tid == 0) sm.part[b ^ 1] = atomicAdd(a.part_counter, 1u);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
+    __syncthreads();  // the other half was last read by the previous partition's scatter
+    const long long next = sm.part[b ^ 1];
+    if (next < parts) {
+      persist_load<VALS>(sm, b ^ 1, a.keys_in, a.values_in, next * kPPart,
+                         (int)min((long long)kPPart, n - next * kPPart));
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // this partition's keys are in half b
+    const long long base = cur * kPPart;
+    const int m = (int)min((long long)kPPart, n - base);
+    // rank within the warp (warp-striped: item i of lane l is element warp*512 + i*32 + l)
+    unsigned long long k[kPItems];
+    uint32_t v[kPItems], rank[kPItems];
+    uint16_t dig[kPItems];
+#pragma unroll
+    for (int i = 0; i < kPItems; ++i) {
+      const int e = (int)warp * (kPItems * 32) + i * 32 + (int)lane;
+      const bool valid = e < m;
+      k[i] = sm.keys[b][e];
+      v[i] = VALS ? sm.values[b][e] : 0u;
+      dig[i] = (uint16_t)(valid ? (uint32_t)(k[i] >> a.shift) & ((1u << a.bits) - 1u) : 256u);
+    }
+#pragma unroll
+    for (int i = 0; i < kPItems; ++i) {
+      const uint32_t d = dig[i];
+      const uint32_t peers = digit_peers(d, d < 256u, a.bits);
+      uint32_t before = 0;
+      if (d < 256u) before = sm.warp_cnt[warp][d];
+      __syncwarp();
+      rank[i] = before + (uint32_t)__popc(peers & lt);
+      if (d < 256u && (peers & lt) == 0) sm.warp_cnt[warp][d] = before + (uint32_t)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();  // every key of half b is in registers: the half is free for the local sort
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = sm.warp_cnt[w][tid];
+      sm.warp_cnt[w][tid] = total;
+      total += c;
+    }
+    uint32_t* lb = a.lookback + (size_t)cur * kRadix + tid;
+    st_relaxed_u32(lb, (cur == 0 ? kFlagInc : kFlagAgg) | total);
+    sm.block_off[tid] = block_excl_scan(total, sm.scan_tmp);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPItems; ++i) {
+      const uint32_t d = dig[i];
+      if (d < 256u) {
+        const uint32_t pos = sm.block_off[d] + sm.warp_cnt[warp][d] + rank[i];
+        sm.keys[b][pos] = k[i];
+        if (VALS) sm.values[b][pos] = v[i];
+      }
+    }
+    // look-back (one thread per digit, 32 predecessors per round of independent loads)
+    uint32_t prev = 0;
+    if (cur > 0) {
+      constexpr int kWin = 32;
+      long long j = cur - 1;
+      uint32_t spins = 0;
+      bool found = false;
+      while (j >= 0 && !found) {
+        const int cnt = (int)min((long long)kWin, j + 1);
+        uint32_t wv[kWin];
+#pragma unroll
+        for (int i = 0; i < kWin; ++i)
+          if (i < cnt) wv[i] = ld_relaxed_u32(a.lookback + (size_t)(j - i) * kRadix + tid);
+        int used = 0;
+#pragma unroll
+        for (int i = 0; i < kWin; ++i) {
+          if (i >= cnt || found) break;
+          const uint32_t flag = wv[i] & ~kValMask;
+          if (flag == 0) break;
+          prev += wv[i] & kValMask;
+          ++used;
+          if (flag == kFlagInc) found = true;
+        }
+        j -= used;
+        if (!found && used < cnt) {
+          if (++spins > a.spin_limit) {
+            atomicOr(a.status, kStatusTimeout);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      st_relaxed_u32(lb, kFlagInc | ((prev + total) & kValMask));
+    }
+    sm.prev_off[tid] = sm.global_off[tid] + prev - sm.block_off[tid];  // global + look-back - local
+    __syncthreads();
+    for (int j2 = tid; j2 < m; j2 += kThreads) {
+      const unsigned long long key = sm.keys[b][j2];
+      const uint32_t d = (uint32_t)(key >> a.shift) & ((1u << a.bits) - 1u);
+      const uint32_t out = sm.prev_off[d] + (uint32_t)j2;
+      if ((long long)out < n) {  // always true when the histogram matches the keys
+        a.keys_out[out] = key;
+        if (VALS) a.values_out[out] = sm.values[b][j2];
+      }
+    }
+    cur = next;
+    if (cur >= parts) break;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 }  // namespace
@@ -319,7 +523,7 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
     e = cudaMemsetAsync(work.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     if (e != cudaSuccess) return e;
     const int blocks = (int)min((n_bound + 1023) / 1024, (long long)device_sm_count() * 8);
-    e = launch_pdl(hist_kernel, blocks, 256, 0, s, keys, n_dev, n_bound, first_bit, passes, work.hist);
+    e = launch_pdl(hist_kernel, blocks, 256, 0, s, keys, n_dev, n_bound, first_bit, key_bits, passes, work.hist);
     if (e != cudaSuccess) return e;
   }
   unsigned long long* kin = keys;
@@ -327,6 +531,28 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   unsigned long long* kout = keys_alt;
   uint32_t* vout = values_alt;
   uint32_t* sel = result_sel ? work.part_counters + kMaxPasses : nullptr;
+  // large sorts without device-side buffer selection: the persistent, prefetching pass
+  const bool persist = !small && !sel;
+  int persist_grid = 0;
+  if (persist) {
+    const bool vals = values != nullptr;
+    const size_t smem = vals ? sizeof(PersistSmem<true>) : sizeof(PersistSmem<false>);
+    static PerDeviceFlag pattr;
+    e = once_per_device(pattr, [] {
+      cudaError_t r = cudaFuncSetAttribute(onesweep_persist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(PersistSmem<true>));
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(onesweep_persist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PersistSmem<false>));
+      return r;
+    });
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = vals ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_persist_kernel<true>, kThreads, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_persist_kernel<false>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    persist_grid = (int)std::min<long long>(parts, (long long)std::max(per_sm, 1) * device_sm_count());
+  }
   for (int p = 0; p < passes; ++p) {
     PassArgs pa;
     if (sel) {  // buffers fixed as A = (keys, values), B = alt; the device tracks where the data is
@@ -339,13 +565,19 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
       pa.sel_out = nullptr;
     }
     pa.n_dev = n_dev; pa.n_bound = n_bound; pa.shift = first_bit + 8 * p;
+    pa.bits = std::min(8, key_bits - 8 * p);
     pa.hist = work.hist + p * kRadix;
     pa.lookback = work.lookback + (size_t)p * parts * kRadix;
     pa.part_counter = work.part_counters + p;
     pa.status = status;
     pa.spin_limit = work.spin_limit;
     const bool vals = values != nullptr;
-    if (small)
+    if (persist)
+      e = vals ? launch_pdl(onesweep_persist_kernel<true>, (unsigned)persist_grid, kThreads,
+                            sizeof(PersistSmem<true>), s, pa)
+               : launch_pdl(onesweep_persist_kernel<false>, (unsigned)persist_grid, kThreads,
+                            sizeof(PersistSmem<false>), s, pa);
+    else if (small)
       e = vals ? launch_pdl(onesweep_kernel<kItemsSmall, true>, (unsigned)parts, kThreads,
                             sizeof(PassSmem<kItemsSmall>), s, pa)
                : launch_pdl(onesweep_kernel<kItemsSmall, false>, (unsigned)parts, kThreads,

@@ -36,13 +36,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Lanes of the warp that hold the same 8-bit digit as this lane (a warp
-// multisplit from eight ballots, one per digit bit); lanes with valid == false
-// are in no lane's mask.  Every lane of the warp must call it.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+// Lanes of the warp that hold the same digit as this lane (a warp multisplit from
+// one ballot per digit bit; digits have `bits` <= 8 significant bits, the same in
+// every lane); lanes with valid == false are in no lane's mask.  Every lane of
+// the warp must call it.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid, int bits = 8) {
   uint32_t m = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
+    if (b >= bits) break;  // warp-uniform
     const bool bit = (d >> b) & 1u;
     const uint32_t bal = __ballot_sync(0xffffffffu, bit);
     m &= bit ? bal : ~bal;

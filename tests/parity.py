@@ -53,10 +53,23 @@ def pixel_matches(value, px, py, base, gs, proj, dbits, tol, rel_tol, depth_tol,
         if T is not None:
             good &= np.abs(outs[:, 3] - T) <= tol
         if nc is not None:
-            good &= outs[:, 4] == nc
+            good &= (outs[:, 4] == nc) | np.array([_position_tie(lst, int(o), int(nc), proj, depth_tol)
+                                                   for o in outs[:, 4]])
         if good.any():
             return True
     return False
+
+
+def _position_tie(lst, last, nc, proj, depth_tol):
+    """The last contributor's list position depends on the order of equal-depth
+    terms, including ones that do not blend at this pixel: position `last` (1-based)
+    may read as `nc` when the terms between them tie in depth with it."""
+    if last == nc or last < 1 or nc < 1 or abs(nc - last) > 2:
+        return False
+    d = proj["depth"][np.asarray(lst, np.int64)]
+    lo, hi = min(last, nc) - 1, max(last, nc) - 1
+    ref = d[last - 1]
+    return bool(np.all(np.abs(d[lo:hi + 1] - ref) <= depth_tol * abs(ref)))
 
 
 def tile_list(proj, dbits, tiles_x, t_id):

@@ -217,18 +217,20 @@ def test_bin_sort_empty_and_capacity(ctx, binning):
     assert np.array_equal(ranges.cpu().numpy().view(np.uint32), ranges_o)
 
 
-@pytest.mark.parametrize("n,bits", [(1, 8), (4095, 12), (4097, 33), (100000, 44), (262145, 64), (30000, 1)])
+@pytest.mark.parametrize("n,bits", [(1, 8), (4095, 12), (4097, 33), (100000, 44), (262145, 64), (30000, 1),
+                                    ((1 << 19) + 1, 20),     # above 2^19 keys: the persistent, prefetching pass
+                                    (3 * (1 << 20) + 7, 64)])
 def test_sort_pairs_matches_stable_numpy(ctx, n, bits):
     rng = np.random.default_rng(bits)
+    # bits above key_bits are not part of the key: they travel along and do not order
     keys = rng.integers(0, 2 ** 63, n, dtype=np.uint64) | (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
-    if bits < 64:
-        keys &= np.uint64((1 << bits) - 1)
     keys[::5] = keys[min(1, n - 1)]  # ties keep input order
+    low = keys & np.uint64((1 << bits) - 1) if bits < 64 else keys
     vals = np.arange(n, dtype=np.uint32)
     tk = dev(keys.view(np.int64))
     tv = dev(vals.view(np.int32))
     ctx.sort_pairs(tk, tv, bits)
-    order = np.argsort(keys, kind="stable")
+    order = np.argsort(low, kind="stable")
     assert np.array_equal(tk.cpu().numpy().view(np.uint64), keys[order])
     assert np.array_equal(tv.cpu().numpy().view(np.uint32), vals[order])
 

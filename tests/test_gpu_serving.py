@@ -174,3 +174,33 @@ def test_host_output_equals_device_output(world, server):
     d = wait_all(srv, [t1, t2])
     assert d[t1]["status"] == OK and d[t2]["status"] == OK
     assert np.array_equal(dev.cpu().numpy(), host)
+
+
+def test_served_frame_matches_oracle():
+    """A request served at a benchmark resolution (the 100k-Gaussian object at
+    800x800), in a mix with other requests, against the FP64 oracle: every pixel
+    equals the oracle's frame or one of its near-threshold outcomes."""
+    import oracle
+    import parity
+    ctx = fs4d.Context(0)
+    try:
+        s = sg.make_object(0)
+        sid = ctx.load_scene(s)
+        other = ctx.load_scene(sg.make_object(5, n=30000))
+        srv = fs4d.Server(ctx, max_inflight=4, max_batch=4)
+        cam = sg.hemisphere_cameras(50, seed=0)[7]
+        out = torch.zeros((800, 800, 3), device="cuda")
+        others = [torch.zeros((400, 400, 3), device="cuda") for _ in range(6)]
+        tickets = [srv.submit(other, sg.hemisphere_cameras(6, width=400, height=400, seed=3)[k], 0.1 * k, o,
+                              fs4d.BF16 if k % 2 else fs4d.FP32) for k, o in enumerate(others)]
+        tk = srv.submit(sid, cam, 0.35, out, fs4d.FP32)
+        done = wait_all(srv, tickets + [tk])
+        assert done[tk]["status"] == OK
+        srv.close()
+        oracle.set_threads(oracle.default_threads())
+        st = parity.check_frame(out.cpu().numpy(), parity.oracle_frame(s, cam, 0.35), tol=1e-4, rel_tol=5e-5,
+                                px_tol=2e-4)
+        assert st["unresolved"] == 0
+        assert st["other_outcome_frac"] <= 5e-3
+    finally:
+        ctx.close()
