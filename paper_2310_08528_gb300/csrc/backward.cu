@@ -627,6 +627,333 @@ cudaError_t launch_mlp_t(const MlpBwdArgs& a, cudaStream_t s) {
                                         s);
 }
 
+// ------------------------------------------------------------------ MLP + HexPlane, tiled
+// The same backward over tiles of 64 Gaussians (Morton work order), every layer
+// a register-blocked SIMT GEMM over activations held feature-major in shared
+// memory ([feature][68]): thread (tid & 15, tid >> 4) owns Gaussians 4(tid & 15)..+3
+// and outputs 4(tid >> 4)..+3, so two 128-bit shared loads feed 16 FMAs in the
+// forward layers (Wt[in][out] rows) and one 128-bit + four broadcast scalar loads
+// in the transposed backward layers.  The deltas overwrite the activations they
+// are masked by (ReLU'), and every activation/delta the weight gradients need is
+// copied out to the feature-major global arrays with coalesced stores.
+constexpr int kTT = 256;          // threads
+constexpr int kTG = 64;           // Gaussians per tile
+constexpr int kTS = kTG + 4;      // row stride (floats) of the shared activation arrays
+
+// acc[g][o] = b[o4 + o] + sum_i Wt[i][o4 + o] src[i][g4 + g]
+template <int IN>
+__device__ __forceinline__ void t_fwd(const float* __restrict__ Wt, int ldw, const float* __restrict__ b,
+                                      const float* __restrict__ src, int g4, int o4, float (&acc)[4][4]) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) acc[g][o] = b[o4 + o];
+#pragma unroll 4
+  for (int i = 0; i < IN; ++i) {
+    const float4 x = *reinterpret_cast<const float4*>(src + i * kTS + g4);
+    const float4 w = *reinterpret_cast<const float4*>(Wt + i * ldw + o4);
+    const float xs[4] = {x.x, x.y, x.z, x.w}, ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int o = 0; o < 4; ++o) acc[g][o] = fmaf(ws[o], xs[g], acc[g][o]);
+  }
+}
+
+// acc[g][i] += sum_{o < nout} Wt[(i4 + i) * ldw + o] d[o][g4 + g]  (the transposed layer)
+__device__ __forceinline__ void t_bwd(const float* __restrict__ Wt, int ldw, const float* __restrict__ d, int nout,
+                                      int g4, int i4, float (&acc)[4][4]) {
+#pragma unroll 4
+  for (int o = 0; o < nout; ++o) {
+    const float4 x = *reinterpret_cast<const float4*>(d + o * kTS + g4);
+    const float ws[4] = {Wt[(i4 + 0) * ldw + o], Wt[(i4 + 1) * ldw + o], Wt[(i4 + 2) * ldw + o],
+                         Wt[(i4 + 3) * ldw + o]};
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[g][i] = fmaf(ws[i], xs[g], acc[g][i]);
+  }
+}
+
+__device__ __forceinline__ void t_store(float* dst, int g4, int o4, const float (&acc)[4][4], bool relu) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    float4 v = make_float4(acc[0][o], acc[1][o], acc[2][o], acc[3][o]);
+    if (relu) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+    *reinterpret_cast<float4*>(dst + (o4 + o) * kTS + g4) = v;
+  }
+}
+
+// dst = acc where the activation `act` (same element) is positive, else 0 (ReLU'), in place
+__device__ __forceinline__ void t_store_masked(float* dst, int g4, int o4, const float (&acc)[4][4]) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    float4* p = reinterpret_cast<float4*>(dst + (o4 + o) * kTS + g4);
+    const float4 a = *p;
+    *p = make_float4(a.x > 0.f ? acc[0][o] : 0.f, a.y > 0.f ? acc[1][o] : 0.f, a.z > 0.f ? acc[2][o] : 0.f,
+                     a.w > 0.f ? acc[3][o] : 0.f);
+  }
+}
+
+// rows [0, rows) of a shared [rows][kTS] array to global [rows][n] at columns base.. (m valid)
+__device__ __forceinline__ void t_copy_out(const float* src, int rows, float* dst, long long n, long long base,
+                                           int m) {
+  for (int e = threadIdx.x; e < rows * kTG; e += kTT) {
+    const int r = e / kTG, c = e % kTG;
+    if (c < m) dst[(long long)r * n + base + c] = src[r * kTS + c];
+  }
+}
+
+template <int H, int L>
+__global__ void __launch_bounds__(kTT, 1) mlp_bwd_tile_kernel(MlpBwdArgs a) {
+  constexpr int HL = H * L;
+  constexpr int Q = H / 4;
+  extern __shared__ float4 smem4[];
+  const DeformArgs& f = a.f;
+  const MlpGeomT& mg = f.mg;
+  const PlaneGeom& pg = f.pg;
+  float* sw = reinterpret_cast<float*>(smem4);
+  float* FH = sw + mg.total;          // [HL][kTS]: f_h, later dL/df_h
+  float* A1 = FH + HL * kTS;          // [64]: a1, later its delta
+  float* FD = A1 + kWidth * kTS;      // [64]: f_d, later its delta
+  float* HID = FD + kWidth * kTS;     // [192]: head hidden activations, later their deltas
+  float* DO = HID + 3 * kWidth * kTS; // [10]: dL/d(X', r', s')
+  float4* sRow = reinterpret_cast<float4*>(DO + kDeltaDim * kTS);  // (X, t) per Gaussian
+  int* sG = reinterpret_cast<int*>(sRow + kTG);                     // Gaussian index per column
+  for (int i = threadIdx.x; i < mg.total / 4; i += kTT) smem4[i] = __ldg(reinterpret_cast<const float4*>(f.mlp_t) + i);
+  const int g4 = (threadIdx.x & 15) * 4, o4 = (threadIdx.x >> 4) * 4;
+  const long long n = f.n;
+  const MlpActs& act = a.act;
+  const long long tiles = (n + kTG - 1) / kTG;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long base = tile * kTG;
+    const int m = (int)min((long long)kTG, n - base);
+    __syncthreads();  // weights loaded / the previous tile done with every array
+    if (threadIdx.x < kTG) {
+      const int r = threadIdx.x;
+      float4 x = make_float4(0.f, 0.f, 0.f, f.t0);
+      int g = -1;
+      if (r < m) {
+        g = f.perm ? (int)f.perm[base + r] : (int)(base + r);
+        x = make_float4(f.means[3 * g], f.means[3 * g + 1], f.means[3 * g + 2], f.t0);
+      }
+      sRow[r] = x;
+      sG[r] = g;
+      for (int j = 0; j < kDeltaDim; ++j) DO[j * kTS + r] = g >= 0 ? a.gd[10 * (long long)g + j] : 0.f;
+    }
+    __syncthreads();
+    // ---- Eq. 5 recompute: f_h (lane-cooperative: Q lanes per (Gaussian, level), a float4 each)
+    for (int item = threadIdx.x; item < kTG * L * Q; item += kTT) {
+      const int q = item % Q, rl = item / Q, r = rl % kTG, l = rl / kTG;
+      float fv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (r < m) {
+        const float4 xr = sRow[r];
+        const float c[4] = {(xr.x - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f,
+                            (xr.y - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f,
+                            (xr.z - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f, 2.f * xr.w - 1.f};
+        fv[0] = fv[1] = fv[2] = fv[3] = 1.f;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+          const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+          const int Ra = ax < 3 ? pg.res[l] : pg.res_time, Rb = bx < 3 ? pg.res[l] : pg.res_time;
+          int i0, j0;
+          float fa, fb, da, db;
+          axis_setup(c[ax], Ra, i0, fa, da);
+          axis_setup(c[bx], Rb, j0, fb, db);
+          const float4* v00 =
+              reinterpret_cast<const float4*>(f.planes + pg.off[l][p] + ((long long)j0 * Ra + i0) * H) + q;
+          const float4 A = __ldg(v00), B = __ldg(v00 + Q), C = __ldg(v00 + (long long)Ra * Q),
+                       D = __ldg(v00 + (long long)Ra * Q + Q);
+          const float w00 = (1.f - fa) * (1.f - fb), w10 = fa * (1.f - fb), w01 = (1.f - fa) * fb, w11 = fa * fb;
+          fv[0] *= w00 * A.x + w10 * B.x + w01 * C.x + w11 * D.x;
+          fv[1] *= w00 * A.y + w10 * B.y + w01 * C.y + w11 * D.y;
+          fv[2] *= w00 * A.z + w10 * B.z + w01 * C.z + w11 * D.z;
+          fv[3] *= w00 * A.w + w10 * B.w + w01 * C.w + w11 * D.w;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) FH[(l * H + 4 * q + e) * kTS + r] = fv[e];
+    }
+    __syncthreads();
+    t_copy_out(FH, HL, act.fh, n, base, m);
+    t_copy_out(DO, kDeltaDim, act.dout, n, base, m);
+    // ---- forward recompute: a1, f_d, head hidden layers
+    float acc[4][4];
+    if (o4 < kWidth) {
+      t_fwd<HL>(sw + mg.w[0], kWidth, sw + mg.b[0], FH, g4, o4, acc);
+      t_store(A1, g4, o4, acc, true);
+    }
+    __syncthreads();
+    t_copy_out(A1, kWidth, act.a1, n, base, m);
+    t_fwd<kWidth>(sw + mg.w[1], kWidth, sw + mg.b[1], A1, g4, o4, acc);
+    t_store(FD, g4, o4, acc, true);
+    __syncthreads();
+    t_copy_out(FD, kWidth, act.fd, n, base, m);
+#pragma unroll 1
+    for (int h = 0; h < 3; ++h) {
+      t_fwd<kWidth>(sw + mg.w[2 + 2 * h], kWidth, sw + mg.b[2 + 2 * h], FD, g4, o4, acc);
+      t_store(HID + kWidth * h * kTS, g4, o4, acc, true);
+    }
+    __syncthreads();
+    t_copy_out(HID, 3 * kWidth, act.hid, n, base, m);
+    // ---- heads: d_hid = ReLU'(hid) (W_out^T dL/d(X', r', s')), in place over HID
+    {
+      const int col0[3] = {0, 3, 7}, outs[3] = {3, 4, 3};
+      for (int e = threadIdx.x; e < 3 * kWidth * kTG; e += kTT) {
+        const int r = e % kTG, ho = e / kTG, h = ho / kWidth, o = ho % kWidth;
+        const float* W2 = sw + mg.w[3 + 2 * h];  // Wt[o][j]
+        float sacc = 0.f;
+        for (int j = 0; j < outs[h]; ++j) sacc = fmaf(W2[o * outs[h] + j], DO[(col0[h] + j) * kTS + r], sacc);
+        float& hv = HID[ho * kTS + r];
+        hv = hv > 0.f ? sacc : 0.f;
+      }
+    }
+    __syncthreads();
+    t_copy_out(HID, 3 * kWidth, act.dh, n, base, m);
+    // ---- phi_d: d_fd = ReLU'(f_d) sum_h W_h1^T d_hid_h, in place over FD
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[g][i] = 0.f;
+#pragma unroll 1
+    for (int h = 0; h < 3; ++h) t_bwd(sw + mg.w[2 + 2 * h], kWidth, HID + kWidth * h * kTS, kWidth, g4, o4, acc);
+    t_store_masked(FD, g4, o4, acc);
+    __syncthreads();
+    t_copy_out(FD, kWidth, act.d2, n, base, m);
+    // d_a1 = ReLU'(a1) W2^T d_fd, in place over A1
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[g][i] = 0.f;
+    t_bwd(sw + mg.w[1], kWidth, FD, kWidth, g4, o4, acc);
+    t_store_masked(A1, g4, o4, acc);
+    __syncthreads();
+    t_copy_out(A1, kWidth, act.d1, n, base, m);
+    // dL/df_h = W1^T d_a1 (HL rows, 64 per pass), over FH
+#pragma unroll 1
+    for (int i0 = 0; i0 < HL; i0 += kWidth) {
+      if (i0 + o4 < HL) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[g][i] = 0.f;
+        t_bwd(sw + mg.w[0] + (long long)i0 * kWidth, kWidth, A1, kWidth, g4, o4, acc);
+        t_store(FH + i0 * kTS, g4, o4, acc, false);
+      }
+    }
+    __syncthreads();
+    // ---- Eq. 5 backward: plane cells (float4 atomics) and the sampling position
+    for (int item = threadIdx.x; item < kTG * L * Q; item += kTT) {
+      const int q = item % Q, rl = item / Q, r = rl % kTG, l = rl / kTG;
+      const bool live = r < m;
+      float gxs[3] = {0.f, 0.f, 0.f};
+      if (live) {
+        const float4 xr = sRow[r];
+        const float c[4] = {(xr.x - pg.aabb_min[0]) * pg.aabb_scale[0] - 1.f,
+                            (xr.y - pg.aabb_min[1]) * pg.aabb_scale[1] - 1.f,
+                            (xr.z - pg.aabb_min[2]) * pg.aabb_scale[2] - 1.f, 2.f * xr.w - 1.f};
+        float v[6][4];
+        int i0s[6], j0s[6], Ras[6];
+        float fas[6], fbs[6], das[6], dbs[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+          const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+          Ras[p] = ax < 3 ? pg.res[l] : pg.res_time;
+          const int Rb = bx < 3 ? pg.res[l] : pg.res_time;
+          axis_setup(c[ax], Ras[p], i0s[p], fas[p], das[p]);
+          axis_setup(c[bx], Rb, j0s[p], fbs[p], dbs[p]);
+          const float4* v00 =
+              reinterpret_cast<const float4*>(f.planes + pg.off[l][p] + ((long long)j0s[p] * Ras[p] + i0s[p]) * H) + q;
+          const float4 A = __ldg(v00), B = __ldg(v00 + Q), C = __ldg(v00 + (long long)Ras[p] * Q),
+                       D = __ldg(v00 + (long long)Ras[p] * Q + Q);
+          const float w00 = (1.f - fas[p]) * (1.f - fbs[p]), w10 = fas[p] * (1.f - fbs[p]),
+                      w01 = (1.f - fas[p]) * fbs[p], w11 = fas[p] * fbs[p];
+          v[p][0] = w00 * A.x + w10 * B.x + w01 * C.x + w11 * D.x;
+          v[p][1] = w00 * A.y + w10 * B.y + w01 * C.y + w11 * D.y;
+          v[p][2] = w00 * A.z + w10 * B.z + w01 * C.z + w11 * D.z;
+          v[p][3] = w00 * A.w + w10 * B.w + w01 * C.w + w11 * D.w;
+        }
+        float gf[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) gf[e] = FH[(l * H + 4 * q + e) * kTS + r];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const int ax = (p < 2) ? 0 : (p == 2 ? 1 : p - 3);
+          const int bx = (p == 0) ? 1 : (p <= 2 ? 2 : 3);
+          float gv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float others = 1.f;
+#pragma unroll
+            for (int r2 = 0; r2 < 6; ++r2)
+              if (r2 != p) others *= v[r2][e];
+            gv[e] = gf[e] * others;
+          }
+          const long long cell = pg.off[l][p] + ((long long)j0s[p] * Ras[p] + i0s[p]) * H + 4 * q;
+          const float* P = f.planes + cell;
+          const float4 A = __ldg(reinterpret_cast<const float4*>(P)), B = __ldg(reinterpret_cast<const float4*>(P + H)),
+                       C = __ldg(reinterpret_cast<const float4*>(P + (long long)Ras[p] * H)),
+                       D = __ldg(reinterpret_cast<const float4*>(P + (long long)Ras[p] * H + H));
+          const float fa = fas[p], fb = fbs[p];
+          const float As[4] = {A.x, A.y, A.z, A.w}, Bs[4] = {B.x, B.y, B.z, B.w}, Cs[4] = {C.x, C.y, C.z, C.w},
+                      Ds[4] = {D.x, D.y, D.z, D.w};
+          float sa = 0.f, sb = 0.f;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            sa += gv[e] * ((1.f - fb) * (Bs[e] - As[e]) + fb * (Ds[e] - Cs[e]));
+            sb += gv[e] * ((1.f - fa) * (Cs[e] - As[e]) + fa * (Ds[e] - Bs[e]));
+          }
+          if (a.g_planes) {
+            float* GP = a.g_planes + cell;
+            const float w00 = (1.f - fa) * (1.f - fb), w10 = fa * (1.f - fb), w01 = (1.f - fa) * fb, w11 = fa * fb;
+            atomicAdd(reinterpret_cast<float4*>(GP), make_float4(w00 * gv[0], w00 * gv[1], w00 * gv[2], w00 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + H),
+                      make_float4(w10 * gv[0], w10 * gv[1], w10 * gv[2], w10 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + (long long)Ras[p] * H),
+                      make_float4(w01 * gv[0], w01 * gv[1], w01 * gv[2], w01 * gv[3]));
+            atomicAdd(reinterpret_cast<float4*>(GP + (long long)Ras[p] * H + H),
+                      make_float4(w11 * gv[0], w11 * gv[1], w11 * gv[2], w11 * gv[3]));
+          }
+          if (ax < 3) gxs[ax] += sa * das[p] * pg.aabb_scale[ax];
+          if (bx < 3) gxs[bx] += sb * dbs[p] * pg.aabb_scale[bx];
+        }
+      }
+      // the Q lanes of one (Gaussian, level) are consecutive and Q divides 32
+#pragma unroll
+      for (int w = 1; w < Q; w <<= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gxs[k] += __shfl_xor_sync(0xffffffffu, gxs[k], w);
+      if (live && q == 0 && a.g_means) {
+        const int g = sG[r];
+        // levels of one Gaussian are different items: accumulate atomically
+        atomicAdd(&a.g_means[3 * (long long)g], gxs[0]);
+        atomicAdd(&a.g_means[3 * (long long)g + 1], gxs[1]);
+        atomicAdd(&a.g_means[3 * (long long)g + 2], gxs[2]);
+      }
+    }
+  }
+}
+
+template <int H, int L>
+cudaError_t launch_mlp_tile(const MlpBwdArgs& a, cudaStream_t s) {
+  constexpr int HL = H * L;
+  const size_t smem = sizeof(float) * ((size_t)a.f.mg.total + (size_t)(HL + 5 * kWidth + kDeltaDim) * kTS) +
+                      kTG * sizeof(float4) + kTG * sizeof(int);
+  static PerDeviceFlag attr;
+  cudaError_t e = once_per_device(attr, [&] {
+    return cudaFuncSetAttribute(mlp_bwd_tile_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
+  const long long need = ((long long)a.f.n + kTG - 1) / kTG;
+  const int grid = (int)(need < sms ? need : sms);
+  mlp_bwd_tile_kernel<H, L><<<grid, kTT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ weight gradients
 
 constexpr int kWChunk = 256;   // Gaussians per partial (~400 chunks per layer at 100k Gaussians)
@@ -736,12 +1063,12 @@ cudaError_t launch_project_bwd(const ProjectBwdArgs& a, cudaStream_t s) {
 cudaError_t launch_mlp_bwd(const MlpBwdArgs& a, cudaStream_t s) {
   if (a.f.n <= 0) return cudaSuccess;
   const int h = a.f.pg.feat_dim, L = a.f.pg.n_levels;
-  if (h == 16 && L == 1) return launch_mlp_t<16, 1>(a, s);
-  if (h == 16 && L == 2) return launch_mlp_t<16, 2>(a, s);
-  if (h == 16 && L == 3) return launch_mlp_t<16, 3>(a, s);
-  if (h == 32 && L == 1) return launch_mlp_t<32, 1>(a, s);
-  if (h == 32 && L == 2) return launch_mlp_t<32, 2>(a, s);
-  if (h == 32 && L == 3) return launch_mlp_t<32, 3>(a, s);
+  if (h == 16 && L == 1) return launch_mlp_tile<16, 1>(a, s);
+  if (h == 16 && L == 2) return launch_mlp_tile<16, 2>(a, s);
+  if (h == 16 && L == 3) return launch_mlp_tile<16, 3>(a, s);
+  if (h == 32 && L == 1) return launch_mlp_tile<32, 1>(a, s);
+  if (h == 32 && L == 2) return launch_mlp_tile<32, 2>(a, s);
+  if (h == 32 && L == 3) return launch_mlp_tile<32, 3>(a, s);
   return cudaErrorInvalidValue;
 }
 
