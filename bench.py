@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--sort-pairs", type=int, default=0,
+                    help="instead of the frame benchmark: time fs4d_sort_pairs on this many random pairs")
+    ap.add_argument("--sort-bits", type=int, default=13)
     ap.add_argument("--e2e-steps", type=int, default=500)
     return ap.parse_args()
 
@@ -651,10 +654,44 @@ def measure(ctx, fs4d, torch, sid, prec, steps, warmup, rank, world, stream, cap
     return frame_ms, mean_st
 
 
+def sort_only(args):
+    """Standalone radix sort of random (key, value) pairs on the low sort_bits bits
+    (the pair sort of a frame sorts tile bits only: 12-15 bits).  Prints one JSON
+    line with the sort's time and HBM bandwidth (24 B per pair per pass plus the
+    8 B per pair histogram pass)."""
+    import torch
+    from paper_2310_08528_gb300 import fs4d
+    n, bits = args.sort_pairs, args.sort_bits
+    ctx = fs4d.Context(0)
+    gen = torch.Generator("cuda").manual_seed(0)
+    v = torch.arange(n, dtype=torch.int32, device="cuda")
+    ms = []
+    for i in range(args.warmup + args.steps):
+        k = torch.randint(0, 1 << bits, (n,), dtype=torch.int64, device="cuda", generator=gen)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.sort_pairs(k, v, bits)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    passes = (bits + 7) // 8
+    byt = passes * 24 * n + 8 * n
+    peaks = load_peaks(torch.cuda.get_device_properties(0).multi_processor_count)
+    print(json.dumps({"metric": "radix sort of (64-bit key, 32-bit value) pairs", "pairs": n, "key_bits": bits,
+                      "ms": t, "pairs_per_s": n / (t * 1e-3), "hbm_gbs": byt / (t * 1e-3) / 1e9,
+                      "hbm_frac": byt / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], "steps": args.steps}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sort_pairs > 0:
+        return sort_only(args)
     import torch
     from paper_2310_08528_gb300 import fs4d, scenegen as sg
 

@@ -958,12 +958,15 @@ cudaError_t launch_mlp_tile(const MlpBwdArgs& a, cudaStream_t s) {
 
 constexpr int kWChunk = 256;   // Gaussians per partial (~400 chunks per layer at 100k Gaussians)
 constexpr int kWStage = 32;    // Gaussians staged per step
-constexpr int kWBlocks = 2;    // 4x4 output blocks per thread: (64/4) x ceil(97/4) = 400 <= 256 x 2
+constexpr int kWBlocks = 2;    // 4x4 output blocks per thread (a 96-input layer has 16 x 24 = 384)
 
 // Partial sums over one chunk of Gaussians of dW[o][i] = sum_n D[o][n] X[i][n] and
-// db[o] = sum_n D[o][n] (the bias as an input column of ones), register-blocked:
-// each thread owns up to two 4x4 blocks of (o, i) and per staged Gaussian reads
-// 4 D and 4 X values (two 128-bit shared loads) for 16 FMAs per block.
+// db[o] = sum_n D[o][n], register-blocked: the (O/4) x (I/4) blocks of 4x4 weights
+// are spread over the threads, each reading 4 D and 4 X values (two 128-bit shared
+// loads) per staged Gaussian for 16 FMAs; the threads of the first column block
+// also sum the bias.  A layer with fewer blocks than threads (the 3- and 4-output
+// head layers) splits the staged Gaussians among threads and adds the slices up
+// in shared memory at the end.
 __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constant__ WgradArgs wa) {
   const WgradLayer& ly = wa.l[blockIdx.y];
   const float* __restrict__ D = ly.D;
@@ -972,16 +975,22 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
   const int O = ly.O, I = ly.I;
   float* __restrict__ partial = wa.partial + ly.part_off;
   __shared__ __align__(16) float sD[kWStage][64];
-  __shared__ __align__(16) float sX[kWStage][100];  // I + 1 <= 97 columns, padded to a multiple of 4
+  __shared__ __align__(16) float sX[kWStage][100];
+  __shared__ float sRed[256][20];
   const int E = O * I + O;
-  const int IB = (I + 1 + 3) / 4, OB = (O + 3) / 4;  // column blocks include the bias column I
+  const int IB = I / 4, OB = (O + 3) / 4, NB = OB * IB;
+  const int ks = NB >= 256 ? 1 : 256 / NB;  // slices of the staged Gaussians
+  const int slice = threadIdx.x / (NB < 256 ? NB : 256);
   const long long n0 = (long long)blockIdx.x * kWChunk;
   const long long n1 = min(n, n0 + kWChunk);
-  float acc[kWBlocks][16];
+  float acc[kWBlocks][16], bacc[kWBlocks][4];
 #pragma unroll
-  for (int b = 0; b < kWBlocks; ++b)
+  for (int b = 0; b < kWBlocks; ++b) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[b][k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bacc[b][k] = 0.f;
+  }
   for (long long b0 = n0; b0 < n1; b0 += kWStage) {
     const int m = (int)min((long long)kWStage, n1 - b0);
     __syncthreads();
@@ -989,44 +998,64 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
       const int o = t / kWStage, j = t % kWStage;
       sD[j][o] = (j < m && o < O) ? D[(long long)o * n + b0 + j] : 0.f;
     }
-    for (int t = threadIdx.x; t < kWStage * 100; t += 256) {
+    for (int t = threadIdx.x; t < kWStage * I; t += 256) {
       const int i = t / kWStage, j = t % kWStage;
-      sX[j][i] = j >= m ? 0.f : (i < I ? X[(long long)i * n + b0 + j] : (i == I ? 1.f : 0.f));
+      sX[j][i] = j < m ? X[(long long)i * n + b0 + j] : 0.f;
     }
     __syncthreads();
+    if (slice < ks) {
 #pragma unroll
-    for (int b = 0; b < kWBlocks; ++b) {
-      const int blk = threadIdx.x + 256 * b;
-      if (blk >= OB * IB) break;
-      const int ob = blk / IB, ib = blk % IB;
-      float* a = acc[b];
+      for (int b = 0; b < kWBlocks; ++b) {
+        const int blk = (NB < 256 ? threadIdx.x % NB : threadIdx.x) + 256 * b;
+        if (blk >= NB || (b > 0 && NB < 256)) break;
+        const int ob = blk / IB, ib = blk % IB;
+        float* a = acc[b];
 #pragma unroll 4
-      for (int j = 0; j < kWStage; ++j) {
-        const float4 d4 = *reinterpret_cast<const float4*>(&sD[j][4 * ob]);
-        const float4 x4 = *reinterpret_cast<const float4*>(&sX[j][4 * ib]);
-        const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+        for (int j = slice; j < kWStage; j += ks) {
+          const float4 d4 = *reinterpret_cast<const float4*>(&sD[j][4 * ob]);
+          const float4 x4 = *reinterpret_cast<const float4*>(&sX[j][4 * ib]);
+          const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) a[4 * r + c] = fmaf(dv[r], xv[c], a[4 * r + c]);
+            for (int c = 0; c < 4; ++c) a[4 * r + c] = fmaf(dv[r], xv[c], a[4 * r + c]);
+          if (ib == 0)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) bacc[b][r] += dv[r];
+        }
       }
     }
   }
+  if (ks > 1) {  // add the slices up: slice 0 of each block collects the others
+    __syncthreads();
+    if (slice < ks) {
+      for (int k = 0; k < 16; ++k) sRed[threadIdx.x][k] = acc[0][k];
+      for (int k = 0; k < 4; ++k) sRed[threadIdx.x][16 + k] = bacc[0][k];
+    }
+    __syncthreads();
+    if (slice == 0) {
+      for (int sl = 1; sl < ks; ++sl) {
+        const int src = threadIdx.x + sl * NB;
+        for (int k = 0; k < 16; ++k) acc[0][k] += sRed[src][k];
+        for (int k = 0; k < 4; ++k) bacc[0][k] += sRed[src][16 + k];
+      }
+    }
+  }
+  if (slice != 0) return;
   // entry layout: W[o][i] at o * I + i, then b[o] at O * I + o
 #pragma unroll
   for (int b = 0; b < kWBlocks; ++b) {
-    const int blk = threadIdx.x + 256 * b;
-    if (blk >= OB * IB) break;
+    const int blk = (NB < 256 ? threadIdx.x % NB : threadIdx.x) + 256 * b;
+    if (blk >= NB || (b > 0 && NB < 256)) break;
     const int ob = blk / IB, ib = blk % IB;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r) {
+      const int o = 4 * ob + r;
+      if (o >= O) continue;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int o = 4 * ob + r, i = 4 * ib + c;
-        if (o >= O || i > I) continue;
-        const int e = i < I ? o * I + i : O * I + o;
-        partial[(long long)blockIdx.x * E + e] = acc[b][4 * r + c];
-      }
+      for (int c = 0; c < 4; ++c) partial[(long long)blockIdx.x * E + o * I + 4 * ib + c] = acc[b][4 * r + c];
+      if (ib == 0) partial[(long long)blockIdx.x * E + O * I + o] = bacc[b][r];
+    }
   }
 }
 
@@ -1080,7 +1109,7 @@ cudaError_t launch_wgrad(WgradArgs& a, cudaStream_t s) {
   int maxE = 0;
   long long off = 0;
   for (int k = 0; k < a.n_layers; ++k) {
-    if (a.l[k].O > 64 || a.l[k].I > 96) return cudaErrorInvalidValue;
+    if (a.l[k].O > 64 || a.l[k].I > 96 || (a.l[k].I & 3)) return cudaErrorInvalidValue;
     const int E = a.l[k].O * a.l[k].I + a.l[k].O;
     a.l[k].part_off = off;
     off += (long long)a.chunks * E;
