@@ -23,6 +23,7 @@ _lib = None
 F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 F64P = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 I32P = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+I64P = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 U32P = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
 U64P = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 
@@ -50,7 +51,7 @@ class OrcProjected(C.Structure):
 
 class OrcGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes",
-                                          "mlp", "planes_abs", "planes_sens")]
+                                          "mlp", "planes_abs", "planes_sens", "xy")]
 
 
 def lib():
@@ -91,6 +92,9 @@ def lib():
         L.orc_lr.restype = C.c_double
         L.orc_adam_step.argtypes = [C.c_int64, F64P, F64P, F64P, F64P, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.c_int64]
+        L.orc_densify.argtypes = [C.POINTER(OrcScene), F32P, F32P, F32P, C.c_float, C.c_float, C.c_float, C.c_int64,
+                                  I64P, I32P, F64P, F64P, F64P, F64P, F64P]
+        L.orc_densify.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -352,11 +356,12 @@ def uncertain_memberships(proj, width: int, height: int, px_tol: float, tile: in
 
 
 def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = True, tile: int = 16,
-                    plane_terms: bool = False):
+                    plane_terms: bool = False, xy: bool = False):
     """Gradients of sum(dl_dimage * image) w.r.t. every scene parameter (float64 dict).
     plane_terms: also 'planes_abs', per plane value the sum of the magnitudes of the
     per-Gaussian terms its gradient adds up, and 'planes_sens', the most a unit
-    error in every Gaussian's output gradients (dX', dr', ds') can change it."""
+    error in every Gaussian's output gradients (dX', dr', ds') can change it.
+    xy: also 'xy', the [n][2] gradient of the projected means (pixel units)."""
     h = _SceneHandle(scene)
     cc = _camera(cam)
     g = dict(means=np.zeros((h.n, 3)), log_scales=np.zeros((h.n, 3)), quats=np.zeros((h.n, 4)),
@@ -365,6 +370,8 @@ def render_backward(scene, cam, t: float, dl_dimage: np.ndarray, deform: bool = 
     if plane_terms:
         g["planes_abs"] = np.zeros(h.arrays["planes"].shape[0])
         g["planes_sens"] = np.zeros(h.arrays["planes"].shape[0])
+    if xy:
+        g["xy"] = np.zeros((h.n, 2))
     G = OrcGrads(**{k: v.ctypes.data for k, v in g.items()})
     rc = lib().orc_render_backward(C.byref(h.struct), C.byref(cc), float(t), int(bool(deform)), int(tile),
                                    np.ascontiguousarray(dl_dimage, np.float64), C.byref(G))
@@ -448,6 +455,35 @@ def train_step(scene, cam, t: float, target, cfg, state, tile: int = 16):
             adam_step(p, gg, m, v, lr, cfg["beta1"], cfg["beta2"], cfg["eps"], step)
     state["step"] = step
     return l1, tv, g
+
+
+# ----------------------------------------------------------------- densification and pruning (App. A)
+
+DENSIFY_KINDS = ("kept", "copy", "first child", "second child")
+
+
+def densify(scene, grad_sum, visible, normals, grad_threshold: float, split_log_scale: float, prune_logit: float):
+    """Adaptive density control on the canonical Gaussians (orc_densify): returns a
+    dict with the new float64 arrays (means, log_scales, quats, opacity_logits, sh)
+    and, per output Gaussian, 'src' (source index) and 'kind' (0 kept, 1 copy,
+    2 / 3 first / second child of a split).  The three decisions are taken in
+    float32, on float32 statistics and thresholds."""
+    h = _SceneHandle(scene)
+    n = h.n
+    cap = 2 * n + 1
+    k = h.k
+    out = dict(src=np.zeros(cap, np.int64), kind=np.zeros(cap, np.int32), means=np.zeros((cap, 3)),
+               log_scales=np.zeros((cap, 3)), quats=np.zeros((cap, 4)), opacity_logits=np.zeros(cap),
+               sh=np.zeros((cap, k, 3)))
+    m = lib().orc_densify(C.byref(h.struct), np.ascontiguousarray(grad_sum, np.float32),
+                          np.ascontiguousarray(visible, np.float32),
+                          np.ascontiguousarray(normals, np.float32).reshape(-1),
+                          np.float32(grad_threshold), np.float32(split_log_scale), np.float32(prune_logit), cap,
+                          out["src"], out["kind"], out["means"], out["log_scales"], out["quats"],
+                          out["opacity_logits"], out["sh"])
+    if m < 0:
+        raise RuntimeError("orc_densify: output capacity too small")
+    return {key: v[:m] for key, v in out.items()}
 
 
 def kind() -> str:

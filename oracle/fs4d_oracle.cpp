@@ -727,6 +727,9 @@ extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam
     }
   }
 
+  if (G->xy)
+    for (int64_t i = 0; i < 2 * (int64_t)n; ++i) G->xy[i] += g_xy[i];
+
   // ---------------------------------------------------------------- Eq. 2 / Eq. 3 / SH backward, per Gaussian
   const double* M = cam->world_to_cam;
   double Rc[3][3], tc[3], campos[3];
@@ -1067,6 +1070,72 @@ void orc_adam_step(int64_t count, double* param, const double* g, double* m, dou
     const double mh = m[i] / c1, vh = v[i] / c2;
     param[i] -= lr * mh / (std::sqrt(vh) + eps);
   }
+}
+
+// Adaptive density control (App. A keeps the densification and pruning of 3D
+// Gaussian splatting and stops the growth late in training).  Written out as
+// its definition: the Gaussians whose mean view-space gradient is at least the
+// threshold are densified -- copied when small (largest log-scale at or below
+// split_log_scale), replaced by two children drawn from N(mu, Sigma) with the
+// scales divided by 1.6 when large -- and every Gaussian whose opacity logit is
+// below prune_logit is removed together with whatever it would have produced.
+// The three decisions are taken in float32 on the float32 inputs.
+// Output order: the kept Gaussians, the copies, the first children, the second
+// children, each in source order; src/kind give each output's source Gaussian
+// and 0 kept, 1 copy, 2 first child, 3 second child.
+int64_t orc_densify(const orc_scene* s, const float* grad_sum, const float* visible, const float* normals,
+                    float grad_threshold, float split_log_scale, float prune_logit, int64_t cap, int64_t* src,
+                    int32_t* kind, double* means, double* log_scales, double* quats, double* opacity_logits,
+                    double* sh) {
+  const int64_t n = s->n, K = (int64_t)(s->sh_degree + 1) * (s->sh_degree + 1);
+  std::vector<int> cls(n);  // 0 removed, 1 kept, 2 kept and copied, 3 split
+  for (int64_t i = 0; i < n; ++i) {
+    const float avg = visible[i] > 0.f ? grad_sum[i] / visible[i] : 0.f;
+    const bool selected = avg >= grad_threshold;
+    float smax = s->log_scales[3 * i];
+    for (int k = 1; k < 3; ++k) smax = std::max(smax, s->log_scales[3 * i + k]);
+    const bool large = smax > split_log_scale;
+    if (s->opacity_logits[i] < prune_logit) cls[i] = 0;
+    else if (!selected) cls[i] = 1;
+    else cls[i] = large ? 3 : 2;
+  }
+  std::vector<std::pair<int64_t, int>> out;
+  for (int64_t i = 0; i < n; ++i)
+    if (cls[i] == 1 || cls[i] == 2) out.push_back({i, 0});
+  for (int64_t i = 0; i < n; ++i)
+    if (cls[i] == 2) out.push_back({i, 1});
+  for (int c = 0; c < 2; ++c)
+    for (int64_t i = 0; i < n; ++i)
+      if (cls[i] == 3) out.push_back({i, 2 + c});
+  if ((int64_t)out.size() > cap) return -1;
+  const double shrink = std::log(1.6);
+  for (size_t o = 0; o < out.size(); ++o) {
+    const int64_t i = out[o].first;
+    const int kd = out[o].second;
+    src[o] = i;
+    kind[o] = kd;
+    for (int k = 0; k < 3; ++k) {
+      means[3 * o + k] = s->means[3 * i + k];
+      log_scales[3 * o + k] = s->log_scales[3 * i + k];
+    }
+    for (int k = 0; k < 4; ++k) quats[4 * o + k] = s->quats[4 * i + k];
+    opacity_logits[o] = s->opacity_logits[i];
+    for (int64_t k = 0; k < 3 * K; ++k) sh[3 * K * o + k] = s->sh[3 * K * i + k];
+    if (kd >= 2) {
+      // child = mu + R S z, z ~ N(0, I): a draw from N(mu, R S S^T R^T) (Eq. 2)
+      double q[4], qn = 0.0, R[3][3];
+      for (int k = 0; k < 4; ++k) { q[k] = s->quats[4 * i + k]; qn += q[k] * q[k]; }
+      qn = std::sqrt(qn);
+      for (int k = 0; k < 4; ++k) q[k] /= qn;
+      quat_to_rot(q, R);
+      const float* z = normals + 6 * i + 3 * (kd - 2);
+      double sz[3];
+      for (int k = 0; k < 3; ++k) sz[k] = std::exp((double)s->log_scales[3 * i + k]) * (double)z[k];
+      for (int r = 0; r < 3; ++r) means[3 * o + r] += R[r][0] * sz[0] + R[r][1] * sz[1] + R[r][2] * sz[2];
+      for (int k = 0; k < 3; ++k) log_scales[3 * o + k] -= shrink;
+    }
+  }
+  return (int64_t)out.size();
 }
 
 }  // extern "C"

@@ -29,6 +29,8 @@
  *                                    Sec. 4.3)
  *   orc_l1_loss / orc_tv_loss        the training loss L = |I^ - I| + L_tv (Sec. 4.3)
  *   orc_lr / orc_adam_step           learning-rate decay and Adam update (App. A)
+ *   orc_densify                      densification and pruning (App. A, following
+ *                                    3D Gaussian splatting's adaptive density control)
  *
  * Parity pins: tests/test_oracle_pins.py and tests/test_oracle_backward.py;
  * tests/test_oracle_planted_mistakes.py builds copies of this oracle with one
@@ -129,6 +131,8 @@ typedef struct orc_grads {
                              unit error in every Gaussian's ten output gradients (dX', dr',
                              ds') can cause at most: sum over Gaussians of |J|^T 1 (test
                              support: propagation of upstream float32 error) */
+  double* xy;             /* optional: [n][2] gradient of the projected mean (pixels),
+                             the view-space gradient that densification accumulates */
 } orc_grads;
 
 int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,
@@ -140,6 +144,15 @@ double orc_tv_loss(const orc_scene* s, double weight, double* grad);
 double orc_lr(double lr0, double lr1, int64_t k, int64_t total);
 void orc_adam_step(int64_t count, double* param, const double* g, double* m, double* v, double lr, double beta1,
                    double beta2, double eps, int64_t step);
+
+/* Densification and pruning (App. A).  grad_sum[n]: summed |dL/d(projected mean)|
+ * over the views a Gaussian was visible in; visible[n]: that number of views;
+ * normals[n][2][3]: standard normal draws for the two children of a split.
+ * Writes at most cap outputs; returns their number, or -1 if cap is too small. */
+int64_t orc_densify(const orc_scene* s, const float* grad_sum, const float* visible, const float* normals,
+                    float grad_threshold, float split_log_scale, float prune_logit, int64_t cap, int64_t* src,
+                    int32_t* kind, double* means, double* log_scales, double* quats, double* opacity_logits,
+                    double* sh);
 
 #ifdef __cplusplus
 }

@@ -4,7 +4,7 @@ Each case copies ``oracle/fs4d_oracle.cpp``, plants one plausible mistake (a
 dropped term, a flipped sign, a transposed operand or index, a shifted offset, a
 threshold taken on the wrong side), builds the copy into a temporary library
 and runs the oracle's pin tests (``test_oracle_pins.py``,
-``test_oracle_backward.py``) against it.  A mistake that every pin lets through
+``test_oracle_backward.py``, ``test_oracle_densify.py``) against it.  A mistake that every pin lets through
 shows a pin that is missing.  The real oracle is never modified.
 """
 import concurrent.futures as cf
@@ -16,7 +16,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "fs4d_oracle.cpp")
-PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_backward.py"]
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_backward.py", "tests/test_oracle_densify.py"]
 
 # (name, text in the oracle, replacement, which occurrence of the text).  Texts that
 # the forward and the backward share are planted in their first occurrence, the
@@ -112,6 +112,25 @@ MISTAKES = [
      "G->planes[off + e10] += gv * (1 - fa[p]) * fb[p];", 0),
     ("backward: box scale of the sampling point", "G->means[3 * (int64_t)g + a] += gv * dv_dfa * da[p] * 2.0 /",
      "G->means[3 * (int64_t)g + a] += gv * dv_dfa * da[p] * 1.0 /", 0),
+    ("backward: projected-mean gradient sign", "G->xy[i] += g_xy[i];", "G->xy[i] -= g_xy[i];", 0),
+    # App. A: densification and pruning
+    ("densify: children keep the parent's scale", "for (int k = 0; k < 3; ++k) log_scales[3 * o + k] -= shrink;",
+     "", 0),
+    ("densify: copies not made", "if (cls[i] == 2) out.push_back({i, 1});", "if (cls[i] == 5) out.push_back({i, 1});",
+     0),
+    ("densify: threshold taken strictly", "const bool selected = avg >= grad_threshold;",
+     "const bool selected = avg > grad_threshold;", 0),
+    ("densify: child offset rotated by R^T",
+     "means[3 * o + r] += R[r][0] * sz[0] + R[r][1] * sz[1] + R[r][2] * sz[2];",
+     "means[3 * o + r] += R[0][r] * sz[0] + R[1][r] * sz[1] + R[2][r] * sz[2];", 0),
+    ("densify: log-scale used as the scale", "sz[k] = std::exp((double)s->log_scales[3 * i + k]) * (double)z[k];",
+     "sz[k] = (double)s->log_scales[3 * i + k] * (double)z[k];", 0),
+    ("densify: split Gaussian also kept", "if (cls[i] == 1 || cls[i] == 2) out.push_back({i, 0});",
+     "if (cls[i] >= 1) out.push_back({i, 0});", 0),
+    ("densify: transparent Gaussians still densified", "if (s->opacity_logits[i] < prune_logit) cls[i] = 0;",
+     "if (s->opacity_logits[i] < prune_logit && !selected) cls[i] = 0;", 0),
+    ("densify: both children from one draw", "const float* z = normals + 6 * i + 3 * (kd - 2);",
+     "const float* z = normals + 6 * i;", 0),
 ]
 
 
