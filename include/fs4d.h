@@ -335,6 +335,61 @@ FS4D_API fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, cons
 FS4D_API fs4d_status fs4d_train_losses(fs4d_trainer* tr, float* h_losses);
 FS4D_API fs4d_status fs4d_train_steps_done(const fs4d_trainer* tr, int64_t* steps);
 FS4D_API fs4d_status fs4d_train_destroy(fs4d_trainer* tr);
+/* Adam moments of parameter group `group` (0 means, 1 log_scales, 2 quats,
+ * 3 opacity_logits, 4 sh, 5 planes, 6 mlp; the layouts of fs4d_scene_desc) into
+ * the non-NULL host arrays h_m, h_v (the group's size in floats each).
+ * Synchronises the context's stream. */
+FS4D_API fs4d_status fs4d_train_read_state(fs4d_trainer* tr, int32_t group, float* h_m, float* h_v);
+
+/* ---------------------------------------------------------------- densification
+ * Adaptive density control (App. A: the paper keeps the densification and
+ * pruning of 3D Gaussian splatting, growing the set until late in training).
+ * Statistics: per Gaussian, the summed norm of the gradient of the loss with
+ * respect to its projected mean (pixel units) over the backward passes in which
+ * it was visible (radius > 0), and the number of those passes.  Readings where
+ * the paper is silent: the gradient is taken in pixel units (the threshold is the
+ * caller's); a Gaussian is densified when sum / count >= grad_threshold (count 0
+ * gives 0), copied when its largest log-scale is at or below split_log_scale,
+ * else replaced by two children drawn from N(mu, R S S^T R^T) (Eq. 2) with the
+ * scales divided by 1.6; a Gaussian whose opacity logit is below prune_logit is
+ * removed, and so is what it would have produced.  The three decisions are taken
+ * in float32.  The new set is the kept Gaussians, then the copies, then the first
+ * and the second children, each in the old order; copies and children start with
+ * zero Adam moments, kept Gaussians keep theirs. */
+typedef struct fs4d_view_stats {
+  float* grad_norm_sum;  /* device [n], accumulated (+=) */
+  float* visible;        /* device [n], accumulated (+=) */
+} fs4d_view_stats;
+typedef struct fs4d_densify_config {
+  float grad_threshold;
+  float split_log_scale;
+  float prune_logit;
+} fs4d_densify_config;
+
+/* fs4d_render_backward that also accumulates the statistics into *d_stats. */
+FS4D_API fs4d_status fs4d_render_backward_stats(fs4d_ctx* ctx, fs4d_frame* saved, const float* d_dl_dimage,
+                                                const fs4d_grads* d_grads, const fs4d_view_stats* d_stats);
+/* Densify and prune scene `id` in place from the statistics *d_stats (device, the
+ * scene's current n) and d_normals (device [n][2][3] standard normal draws; row i
+ * is read only if Gaussian i is split).  If `trainer` (of this scene) is not
+ * NULL its optimiser state follows the Gaussians and its statistics restart at
+ * zero (another trainer of the scene can then no longer step: FS4D_ERR_INVALID_ARG).
+ * *n_out receives the new
+ * number of Gaussians.  FS4D_ERR_INVALID_ARG (and the scene unchanged) if every
+ * Gaussian would be removed; FS4D_ERR_CANCELLED if serving requests on the scene
+ * are in flight; the scene's capacity reservation (fs4d_reserve) is dropped.
+ * Synchronises the context's stream (the new size decides the allocations). */
+FS4D_API fs4d_status fs4d_densify(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_densify_config* cfg,
+                                  const fs4d_view_stats* d_stats, const float* d_normals, fs4d_trainer* trainer,
+                                  int64_t* n_out);
+/* Copy the trainer's own statistics (accumulated by every fs4d_train_step since
+ * its creation or last densify) into the caller's non-NULL fields of *d_out
+ * (device arrays of the scene's current n floats each). */
+FS4D_API fs4d_status fs4d_train_stats(fs4d_trainer* tr, const fs4d_view_stats* d_out);
+/* fs4d_densify of the trainer's scene with the trainer's statistics, which then
+ * restart at zero. */
+FS4D_API fs4d_status fs4d_train_densify(fs4d_trainer* tr, const fs4d_densify_config* cfg, const float* d_normals,
+                                        int64_t* n_out);
 
 /* ---------------------------------------------------------------- serving
  * A continuous-batching request loop over the context's resident scenes, run by

@@ -611,9 +611,11 @@ long long parts_total(const FramePart* parts, int n_parts) {
 
 // Everything of a frame up to (and including) the key emission, over the union of
 // the parts' Gaussians.
+// cull: the tile lists may leave out Gaussians that no pixel of the tile blends
+// (same image; list positions, and so last-contributor indices, differ).
 fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_precision prec,
                         const fs4d_camera& shape, const fs4d_camera* d_cam, const float* d_t, float t, long long cap,
-                        bool report, bool deform, bool offsets) {
+                        bool report, bool deform, bool offsets, bool cull = false) {
   fs4d_ctx* c = e.c;
   Work& w = *e.w;
   const cudaStream_t stream = e.s;
@@ -707,6 +709,7 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
     ea.tile_order = P<uint32_t>(w.tile_order);
     ea.xy = P<float2>(w.xy); ea.conic_opacity = P<float4>(w.co); ea.rgb = P<float>(w.rgb);
     ea.sorted_xy = P<float2>(w.sxy); ea.sorted_co = P<float4>(w.sco); ea.sorted_rgb = P<float>(w.srgb);
+    ea.cull = cull ? 1 : 0;
     if (w.bmp_dirty) FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, stream));
     w.bmp_dirty = true;  // until the extraction (which clears every bit it reads) is launched
     FS4D_CUDA(c, launch_mark_tiles(ea, stream));
@@ -726,15 +729,15 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
 
 fs4d_status frame_front(const Env& e, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
                         const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
-                        bool deform = true, bool offsets = false) {
+                        bool deform = true, bool offsets = false, bool cull = false) {
   const FramePart part{s, 0, {0.f, 0.f, 0.f}};
-  return frame_front(e, &part, 1, prec, shape, d_cam, d_t, t, cap, report, deform, offsets);
+  return frame_front(e, &part, 1, prec, shape, d_cam, d_t, t, cap, report, deform, offsets, cull);
 }
 
 fs4d_status frame_front(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_camera& shape,
                         const fs4d_camera* d_cam, const float* d_t, float t, long long cap, bool report,
-                        bool offsets = false) {
-  return frame_front(env_of(c), s, prec, shape, d_cam, d_t, t, cap, report, true, offsets);
+                        bool offsets = false, bool cull = false) {
+  return frame_front(env_of(c), s, prec, shape, d_cam, d_t, t, cap, report, true, offsets, cull);
 }
 
 // Sort, ranges and composite with n_dev = the sortable pair count on device.
@@ -889,7 +892,10 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
     }
     return render_bands(c, s, prec, cam, t, c->band_hint, d_image, d_t_final, d_n_contrib, true);
   }
-  st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
+  // lists may drop Gaussians no pixel of their tile blends unless the frame reports
+  // list positions (last contributors) or keeps the backward's pair slots
+  const bool cull = !offsets && !d_n_contrib;
+  st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets, cull);
   if (st != FS4D_OK) return st;
   long long K = 0;
   if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
@@ -903,7 +909,7 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   }
   if (K > c->w.cap_pairs) {
     if ((st = ensure_work(c, s->n, n_tiles, std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
-    st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets);
+    st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, offsets, cull);
     if (st != FS4D_OK) return st;
   }
   c->last_pairs = K;
@@ -1240,7 +1246,7 @@ fs4d_status fs4d_render_composed(fs4d_ctx* c, const fs4d_scene_id* ids, const fl
   if (st != FS4D_OK) return st;
   c->stage_acc_valid = false;
   st = frame_front(env_of(c), parts.data(), n_scenes, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, true,
-                   false);
+                   false, !d_n_contrib);
   if (st != FS4D_OK) return st;
   long long K = 0;
   if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
@@ -1248,7 +1254,7 @@ fs4d_status fs4d_render_composed(fs4d_ctx* c, const fs4d_scene_id* ids, const fl
   if (K > c->w.cap_pairs) {
     if ((st = ensure_work(c, (int)N, n_tiles, std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
     st = frame_front(env_of(c), parts.data(), n_scenes, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, true,
-                     false);
+                     false, !d_n_contrib);
     if (st != FS4D_OK) return st;
   }
   c->last_pairs = K;
@@ -1277,7 +1283,7 @@ fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec,
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   if ((st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs)) != FS4D_OK) return st;
   const long long cap = c->w.cap_pairs;
-  if ((st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, cap, false)) != FS4D_OK) return st;
+  if ((st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, cap, false, false, true)) != FS4D_OK) return st;
   if ((st = frame_back(c, *cam, cap, P<float>(img), nullptr, nullptr)) != FS4D_OK) return st;
   FS4D_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->w.z.num_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
   FS4D_CUDA(c, cudaMemcpyAsync(h_image, img.p, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1333,7 +1339,8 @@ fs4d_status fs4d_render_host_batch(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision
     const int sl = k & 1;
     // the slot's previous image (frame k - 2) must be on the host before it is overwritten
     if (k >= 2) FS4D_CUDA(c, cudaStreamWaitEvent(c->stream, c->slot_copied[sl], 0));
-    if ((st = frame_front(c, s, prec, cams[k], nullptr, nullptr, ts[k], cap, false)) != FS4D_OK) return st;
+    if ((st = frame_front(c, s, prec, cams[k], nullptr, nullptr, ts[k], cap, false, false, true)) != FS4D_OK)
+      return st;
     if ((st = frame_back(c, cams[k], cap, slot_img[sl], nullptr, nullptr)) != FS4D_OK) return st;
     // (the count lives in the frame's zeroed state: read before the next frame clears it)
     FS4D_CUDA(c, cudaMemcpyAsync(&c->h_pairs[k], c->w.z.num_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1385,7 +1392,7 @@ fs4d_status fs4d_render_async(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec
     return fail(c, FS4D_ERR_INVALID_ARG, "render_async: call fs4d_reserve for this scene and size first");
   DeviceGuard g(c->device);
   const long long cap = s->reserved_pairs;
-  st = frame_front(c, s, prec, *shape, d_cam, d_t, 0.f, cap, true);
+  st = frame_front(c, s, prec, *shape, d_cam, d_t, 0.f, cap, true, false, true);
   if (st != FS4D_OK) return st;
   return frame_back(c, *shape, cap, d_image, nullptr, nullptr);
 }
@@ -1424,9 +1431,12 @@ fs4d_status fs4d_backward_times(fs4d_ctx* c, float* h_ms) {
   return FS4D_OK;
 }
 
-fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr) {
+static fs4d_status backward_impl(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr,
+                                 const fs4d_view_stats* stats) {
   if (!c) return FS4D_ERR_INVALID_ARG;
   if (!f || !d_dl_dimage || !gr) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: frame, dL/dI, grads needed");
+  if (stats && (!stats->grad_norm_sum || !stats->visible))
+    return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: both statistics arrays are needed");
   Scene* s;
   fs4d_status st = get_scene(c, f->scene, &s);
   if (st != FS4D_OK) return st;
@@ -1476,6 +1486,10 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   pb.offsets = P<uint32_t>(f->offsets); pb.grad_pair = P<float>(w.grad_pair); pb.gd = P<float>(w.gd);
   pb.g_means = gr->means; pb.g_quats = gr->quats; pb.g_log_scales = gr->log_scales;
   pb.g_opacity = gr->opacity_logits; pb.g_sh = gr->sh;
+  if (stats) {
+    pb.stat_grad = stats->grad_norm_sum;
+    pb.stat_visible = stats->visible;
+  }
   FS4D_CUDA(c, launch_project_bwd(pb, c->stream));
   bmark(2);
   // 3. MLP heads, phi_d and HexPlane sampling (float32 recompute of the deformation)
@@ -1516,6 +1530,16 @@ fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   }
   bmark(4);
   return FS4D_OK;
+}
+
+fs4d_status fs4d_render_backward(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr) {
+  return backward_impl(c, f, d_dl_dimage, gr, nullptr);
+}
+
+fs4d_status fs4d_render_backward_stats(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr,
+                                       const fs4d_view_stats* stats) {
+  if (c && !stats) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward_stats: statistics needed");
+  return backward_impl(c, f, d_dl_dimage, gr, stats);
 }
 
 fs4d_status fs4d_frame_free(fs4d_ctx* c, fs4d_frame* f) {
@@ -1946,12 +1970,12 @@ fs4d_status run_slot_frame(fs4d_server* sv, Slot* sl, Scene* s, const fs4d_reque
   const fs4d_camera* dcam = P<fs4d_camera>(sl->dcam);
   const float* dt = P<float>(sl->dt);
   float* img = P<float>(sl->image);
-  fs4d_status st = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false);
+  fs4d_status st = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false, false, true);
   if (st == FS4D_OK) st = frame_back(e, r.cam, cap, img, nullptr, nullptr, nullptr);
   if (st != FS4D_OK) return st;
   cudaGraph_t g = nullptr;
   FS4D_CUDA(c, cudaStreamBeginCapture(sl->stream, cudaStreamCaptureModeThreadLocal));
-  fs4d_status st2 = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false);
+  fs4d_status st2 = frame_front(e, s, r.prec, r.cam, dcam, dt, 0.f, cap, true, false, false, true);
   if (st2 == FS4D_OK) st2 = frame_back(e, r.cam, cap, img, nullptr, nullptr, nullptr);
   const cudaError_t ce = cudaStreamEndCapture(sl->stream, &g);
   if (st2 != FS4D_OK) {
@@ -2330,6 +2354,7 @@ struct fs4d_trainer {
   DevBuf image, dl, partial, losses;         // [H][W][3] x 2, loss partials, [2] losses
   DevBuf grad, m, v;                         // every group, in the order of fs4d_scene_desc
   size_t off[7] = {}, count[7] = {};         // float offset and count of each group
+  DevBuf stats;                              // densification statistics: [2][n] (gradient norm sum, views)
 };
 
 namespace {
@@ -2375,13 +2400,14 @@ fs4d_status fs4d_train_create(fs4d_ctx* c, fs4d_scene_id id, const fs4d_train_co
   const size_t parts = (size_t)train_partials();
   if (ensure(tr->grad, 4 * total) != cudaSuccess || ensure(tr->m, 4 * total) != cudaSuccess ||
       ensure(tr->v, 4 * total) != cudaSuccess || ensure(tr->partial, 4 * parts) != cudaSuccess ||
-      ensure(tr->losses, 16) != cudaSuccess) {
+      ensure(tr->losses, 16) != cudaSuccess || ensure(tr->stats, 8 * n) != cudaSuccess) {
     fs4d_train_destroy(tr);
     return fail(c, FS4D_ERR_OOM, "train_create: device allocation failed");
   }
   if (cudaMemsetAsync(tr->grad.p, 0, 4 * total, c->stream) != cudaSuccess ||
       cudaMemsetAsync(tr->m.p, 0, 4 * total, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(tr->v.p, 0, 4 * total, c->stream) != cudaSuccess) {
+      cudaMemsetAsync(tr->v.p, 0, 4 * total, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(tr->stats.p, 0, 8 * n, c->stream) != cudaSuccess) {
     fs4d_train_destroy(tr);
     return fail(c, FS4D_ERR_CUDA, "train_create: clearing the optimiser state failed");
   }
@@ -2397,6 +2423,8 @@ fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, const fs4d_ca
   Scene* s;
   fs4d_status st = get_scene(c, tr->scene, &s);
   if (st != FS4D_OK) return st;
+  if (tr->count[3] != (size_t)s->n)
+    return fail(c, FS4D_ERR_INVALID_ARG, "train_step: the scene changed size without this trainer (densify with it)");
   DeviceGuard g(c->device);
   const size_t pix3 = 3 * (size_t)cam->width * cam->height;
   if (tr->image.bytes < 4 * pix3 || tr->dl.bytes < 4 * pix3) {
@@ -2414,7 +2442,8 @@ fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, const fs4d_ca
   float* G = P<float>(tr->grad);
   fs4d_grads gr{G + tr->off[0], G + tr->off[1], G + tr->off[2], G + tr->off[3], G + tr->off[4], G + tr->off[5],
                 G + tr->off[6]};
-  if ((st = fs4d_render_backward(c, &tr->frame, P<float>(tr->dl), &gr)) != FS4D_OK) return st;
+  const fs4d_view_stats vs{P<float>(tr->stats), P<float>(tr->stats) + s->n};
+  if ((st = fs4d_render_backward_stats(c, &tr->frame, P<float>(tr->dl), &gr, &vs)) != FS4D_OK) return st;
   // 4. TV loss of the planes and its gradient
   FS4D_CUDA(c, launch_tv(s->pg, P<float>(s->planes), tr->cfg.tv_weight, gr.planes, P<float>(tr->partial), losses + 1,
                          c->stream));
@@ -2473,10 +2502,223 @@ fs4d_status fs4d_train_destroy(fs4d_trainer* tr) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   release_frame(tr->frame);
-  DevBuf* all[] = {&tr->image, &tr->dl, &tr->partial, &tr->losses, &tr->grad, &tr->m, &tr->v};
+  DevBuf* all[] = {&tr->image, &tr->dl, &tr->partial, &tr->losses, &tr->grad, &tr->m, &tr->v, &tr->stats};
   for (DevBuf* b : all) release(*b);
   delete tr;
   return FS4D_OK;
+}
+
+fs4d_status fs4d_train_read_state(fs4d_trainer* tr, int32_t group, float* h_m, float* h_v) {
+  if (!tr) return FS4D_ERR_INVALID_ARG;
+  fs4d_ctx* c = tr->c;
+  if (group < 0 || group > 6) return fail(c, FS4D_ERR_INVALID_ARG, "train_read_state: group 0..6");
+  DeviceGuard g(c->device);
+  const size_t bytes = 4 * tr->count[group];
+  if (h_m)
+    FS4D_CUDA(c, cudaMemcpyAsync(h_m, P<float>(tr->m) + tr->off[group], bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (h_v)
+    FS4D_CUDA(c, cudaMemcpyAsync(h_v, P<float>(tr->v) + tr->off[group], bytes, cudaMemcpyDeviceToHost, c->stream));
+  FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_stats(fs4d_trainer* tr, const fs4d_view_stats* out) {
+  if (!tr || !out) return FS4D_ERR_INVALID_ARG;
+  fs4d_ctx* c = tr->c;
+  DeviceGuard g(c->device);
+  const size_t n = tr->count[3];  // one opacity logit per Gaussian
+  if (out->grad_norm_sum)
+    FS4D_CUDA(c, cudaMemcpyAsync(out->grad_norm_sum, tr->stats.p, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
+  if (out->visible)
+    FS4D_CUDA(c, cudaMemcpyAsync(out->visible, P<float>(tr->stats) + n, 4 * n, cudaMemcpyDeviceToDevice, c->stream));
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_densify(fs4d_ctx* c, fs4d_scene_id id, const fs4d_densify_config* cfg, const fs4d_view_stats* vs,
+                         const float* d_normals, fs4d_trainer* tr, int64_t* n_out) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+  if (!cfg || !vs || !vs->grad_norm_sum || !vs->visible || !d_normals || !n_out)
+    return fail(c, FS4D_ERR_INVALID_ARG, "densify: config, statistics, normals and output required");
+  Scene* s;
+  fs4d_status st = get_scene(c, id, &s);
+  if (st != FS4D_OK) return st;
+  if (tr && (tr->c != c || tr->scene != id)) return fail(c, FS4D_ERR_INVALID_ARG, "densify: trainer of another scene");
+  {
+    std::lock_guard<std::mutex> lock(c->mu);
+    if (s->refs.load() > 0) return fail(c, FS4D_ERR_CANCELLED, "densify: serving requests on this scene in flight");
+    s->dying = true;  // no serving launch on the scene while it changes size
+  }
+  struct Restore {
+    fs4d_ctx* c;
+    Scene* s;
+    ~Restore() {
+      std::lock_guard<std::mutex> lock(c->mu);
+      s->dying = false;
+    }
+  } restore{c, s};
+  DeviceGuard g(c->device);
+  const int n = s->n;
+  const int K3 = 3 * s->K;
+  const int nb = densify_blocks(n);
+  DevBuf plan;  // block offsets [3][nb] and totals [3]
+  auto cleanup = [](std::initializer_list<DevBuf*> bufs) {
+    for (DevBuf* b : bufs) release(*b);
+  };
+  FS4D_CUDA(c, ensure(plan, 4 * (3 * (size_t)nb + 4)));
+  DensifyArgs a{};
+  a.n = n;
+  a.log_scales = P<float>(s->log_scales);
+  a.opacity = P<float>(s->opacity_logits);
+  a.grad_sum = vs->grad_norm_sum;
+  a.visible = vs->visible;
+  a.grad_threshold = cfg->grad_threshold;
+  a.split_log_scale = cfg->split_log_scale;
+  a.prune_logit = cfg->prune_logit;
+  a.block_off = P<uint32_t>(plan);
+  a.totals = P<uint32_t>(plan) + 3 * (size_t)nb;
+  uint32_t tot[3] = {0, 0, 0};
+  cudaError_t e = launch_densify_plan(a, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot, a.totals, 12, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cleanup({&plan});
+    return fail(c, FS4D_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
+  }
+  const long long m = (long long)tot[0] + tot[1] + 2LL * tot[2];
+  if (m == 0) {
+    cleanup({&plan});
+    return fail(c, FS4D_ERR_INVALID_ARG, "densify: every Gaussian would be removed");
+  }
+  if (m >= (1LL << 30)) {
+    cleanup({&plan});
+    return fail(c, FS4D_ERR_CAPACITY, "densify: more than 2^30 - 1 Gaussians");
+  }
+  // the new arrays, the output map and the work order's sort buffers
+  DevBuf map, nm, nls, nq, no, nsh, keys, perm;
+  std::initializer_list<DevBuf*> fresh = {&map, &nm, &nls, &nq, &no, &nsh, &keys, &perm};
+  if (ensure(map, 8 * (size_t)m) != cudaSuccess || ensure(nm, 12 * (size_t)m) != cudaSuccess ||
+      ensure(nls, 12 * (size_t)m) != cudaSuccess || ensure(nq, 16 * (size_t)m) != cudaSuccess ||
+      ensure(no, 4 * (size_t)m) != cudaSuccess || ensure(nsh, 4 * (size_t)K3 * m) != cudaSuccess ||
+      ensure(keys, 8 * (size_t)m) != cudaSuccess || ensure(perm, 4 * (size_t)m) != cudaSuccess) {
+    cleanup({&plan});
+    cleanup(fresh);
+    return fail(c, FS4D_ERR_OOM, "densify: device allocation failed");
+  }
+  a.src = P<int32_t>(map);
+  a.kind = P<int32_t>(map) + m;
+  e = launch_densify_map(a, c->stream);
+  const float* olds[5] = {P<float>(s->means), P<float>(s->log_scales), P<float>(s->quats), P<float>(s->opacity_logits),
+                          P<float>(s->sh)};
+  float* news[5] = {P<float>(nm), P<float>(nls), P<float>(nq), P<float>(no), P<float>(nsh)};
+  const int width[5] = {3, 3, 4, 1, K3};
+  for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+    e = launch_gather(olds[k], news[k], a.src, a.kind, m, width[k], false, c->stream);
+  if (e == cudaSuccess) {
+    ChildArgs ca{};
+    ca.first = (long long)tot[0] + tot[1];
+    ca.end = m;
+    ca.src = a.src;
+    ca.kind = a.kind;
+    ca.means = olds[0];
+    ca.log_scales = olds[1];
+    ca.quats = olds[2];
+    ca.normals = d_normals;
+    ca.out_means = news[0];
+    ca.out_log_scales = news[1];
+    e = launch_children(ca, c->stream);
+  }
+  if (e == cudaSuccess)
+    e = launch_morton(news[0], (int)m, s->shape.aabb_min, s->shape.aabb_max, P<unsigned long long>(keys),
+                      P<uint32_t>(perm), c->stream);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(c->stream);
+    cleanup({&plan});
+    cleanup(fresh);
+    return fail(c, FS4D_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
+  }
+  // the deformation work order of the new set: stable sort by Morton code
+  if ((st = fs4d_sort_pairs(c, m, 30, P<uint64_t>(keys), P<uint32_t>(perm))) != FS4D_OK) {
+    cudaStreamSynchronize(c->stream);
+    cleanup({&plan});
+    cleanup(fresh);
+    return st;
+  }
+  // the trainer's state follows the Gaussians
+  DevBuf tg, tm, tv, ts;
+  size_t toff[7] = {}, tcnt[7] = {};
+  if (tr) {
+    const size_t cnt[7] = {3 * (size_t)m, 3 * (size_t)m, 4 * (size_t)m, (size_t)m, (size_t)K3 * m, tr->count[5],
+                           tr->count[6]};
+    size_t total = 0;
+    for (int k = 0; k < 7; ++k) {
+      toff[k] = total;
+      tcnt[k] = cnt[k];
+      total += (cnt[k] + 3) / 4 * 4;
+    }
+    if (ensure(tg, 4 * total) != cudaSuccess || ensure(tm, 4 * total) != cudaSuccess ||
+        ensure(tv, 4 * total) != cudaSuccess || ensure(ts, 8 * (size_t)m) != cudaSuccess) {
+      cudaStreamSynchronize(c->stream);
+      cleanup({&plan, &tg, &tm, &tv, &ts});
+      cleanup(fresh);
+      return fail(c, FS4D_ERR_OOM, "densify: device allocation of the optimiser state failed");
+    }
+    e = cudaMemsetAsync(tg.p, 0, 4 * total, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ts.p, 0, 8 * (size_t)m, c->stream);
+    for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+      DevBuf* src[2] = {&tr->m, &tr->v};
+      DevBuf* dst[2] = {&tm, &tv};
+      for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        const float* from = P<float>(*src[q]) + tr->off[k];
+        float* to = P<float>(*dst[q]) + toff[k];
+        if (k < 5)
+          e = launch_gather(from, to, a.src, a.kind, m, width[k], true, c->stream);
+        else
+          e = cudaMemcpyAsync(to, from, 4 * tcnt[k], cudaMemcpyDeviceToDevice, c->stream);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(c->stream);
+    cleanup({&plan, &tg, &tm, &tv, &ts});
+    cleanup(fresh);
+    return fail(c, FS4D_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
+  }
+  // swap the new arrays in; the old ones are released with the temporaries
+  const size_t per = 4 * (3 + 3 + 4 + 1 + (size_t)K3 + 1);
+  std::swap(s->means, nm);
+  std::swap(s->log_scales, nls);
+  std::swap(s->quats, nq);
+  std::swap(s->opacity_logits, no);
+  std::swap(s->sh, nsh);
+  std::swap(s->perm, perm);
+  s->resident = s->resident - per * (size_t)n + per * (size_t)m;
+  s->n = (int)m;
+  s->shape.n = (int32_t)m;
+  s->reserved_pairs = 0;
+  s->reserved_w = s->reserved_h = 0;
+  if (tr) {
+    std::swap(tr->grad, tg);
+    std::swap(tr->m, tm);
+    std::swap(tr->v, tv);
+    std::swap(tr->stats, ts);
+    for (int k = 0; k < 7; ++k) {
+      tr->off[k] = toff[k];
+      tr->count[k] = tcnt[k];
+    }
+  }
+  cleanup({&plan, &tg, &tm, &tv, &ts});
+  cleanup(fresh);
+  *n_out = m;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_train_densify(fs4d_trainer* tr, const fs4d_densify_config* cfg, const float* d_normals,
+                               int64_t* n_out) {
+  if (!tr) return FS4D_ERR_INVALID_ARG;
+  const fs4d_view_stats vs{P<float>(tr->stats), P<float>(tr->stats) + tr->count[3]};
+  return fs4d_densify(tr->c, tr->scene, cfg, &vs, d_normals, tr, n_out);
 }
 
 }  // extern "C"

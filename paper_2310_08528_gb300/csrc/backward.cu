@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
 #pragma unroll
     for (int k = 0; k < kPairGrad; ++k) G9[k] += src[k];
   }
+  if (a.stat_grad) {  // densification statistics: view-space gradient norm of the visible Gaussian
+    a.stat_grad[g] += sqrtf(G9[0] * G9[0] + G9[1] * G9[1]);
+    a.stat_visible[g] += 1.f;
+  }
   const CamParams& c = a.cam;
   const float4 co = a.conic_opacity[g];
   if (a.g_opacity) a.g_opacity[g] += G9[5] * co.w * (1.f - co.w);

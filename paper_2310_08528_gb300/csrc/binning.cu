@@ -329,16 +329,39 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem
   const int pos = blockIdx.x * kPart + (int)(warp * 32 + lane);
   int4 r = make_int4(0, 0, 0, 0);
   uint32_t cnt = 0;
+  // with a.cull: the ellipse {alpha >= 1/255} of this lane's Gaussian, for the tile test
+  float eA = 0.f, eB = 0.f, eC = 0.f, eS = -1.f, ekx = 0.f, eky = 0.f, epx = 0.f, epy = 0.f;
   if (pos < a.n) {
     const uint32_t g = order ? order[pos] : (uint32_t)pos;
     r = a.rect[g];
     cnt = (uint32_t)max(0, r.z - r.x) * (uint32_t)max(0, r.w - r.y);
-    if (a.sorted_xy && cnt && half == 0) {  // the compositing reads the projected Gaussians by depth rank
-      a.sorted_xy[pos] = a.xy[g];
-      a.sorted_co[pos] = a.conic_opacity[g];
-      a.sorted_rgb[3 * pos] = a.rgb[3 * g];
-      a.sorted_rgb[3 * pos + 1] = a.rgb[3 * g + 1];
-      a.sorted_rgb[3 * pos + 2] = a.rgb[3 * g + 2];
+    if (cnt && (a.cull || (a.sorted_xy && half == 0))) {
+      const float2 p = a.xy[g];
+      const float4 co = a.conic_opacity[g];
+      if (a.sorted_xy && half == 0) {  // the compositing reads the projected Gaussians by depth rank
+        a.sorted_xy[pos] = p;
+        a.sorted_co[pos] = co;
+        a.sorted_rgb[3 * pos] = a.rgb[3 * g];
+        a.sorted_rgb[3 * pos + 1] = a.rgb[3 * g + 1];
+        a.sorted_rgb[3 * pos + 2] = a.rgb[3 * g + 2];
+      }
+      if (a.cull) {
+        // q(d) = d^T K d <= eS wherever alpha may reach 1/255 (a 0.4% + 2e-3 margin over
+        // the compositing's own bound); eS < 0: alpha never reaches it; no usable
+        // bound (not positive definite): every tile of the rectangle is kept
+        const float thr = composite_exp_threshold(co.w);
+        eA = co.x; eB = co.y; eC = co.z;
+        epx = p.x; epy = p.y;
+        if (!(thr < 0.f)) {
+          eS = -1.f;
+        } else if (!(eA > 0.f && eC > 0.f && eA * eC - eB * eB > 0.f)) {
+          eS = 3.0e38f;
+        } else {
+          eS = -2.f * thr * 1.004f + 2e-3f;
+          ekx = -eB / eC;
+          eky = -eB / eA;
+        }
+      }
     }
   }
   const uint32_t rw = (uint32_t)max(1, r.z - r.x);
@@ -362,9 +385,24 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem
     }
     const int rx = __shfl_sync(0xffffffffu, r.x, lo), ry = __shfl_sync(0xffffffffu, r.y, lo);
     const uint32_t w = __shfl_sync(0xffffffffu, rw, lo), e0 = __shfl_sync(0xffffffffu, excl, lo);
-    if (j < total) {
-      const uint32_t k = j - e0;
-      const uint32_t row = rect_row(k, w);
+    bool keep = j < total;
+    uint32_t k = 0, row = 0;
+    if (keep) {
+      k = j - e0;
+      row = rect_row(k, w);
+    }
+    if (a.cull) {  // uniform: the tile's pixel centres against the ellipse
+      const float A = __shfl_sync(0xffffffffu, eA, lo), B = __shfl_sync(0xffffffffu, eB, lo);
+      const float C = __shfl_sync(0xffffffffu, eC, lo), S = __shfl_sync(0xffffffffu, eS, lo);
+      const float kx = __shfl_sync(0xffffffffu, ekx, lo), ky = __shfl_sync(0xffffffffu, eky, lo);
+      const float px = __shfl_sync(0xffffffffu, epx, lo), py = __shfl_sync(0xffffffffu, epy, lo);
+      if (keep && S < 3.0e38f) {
+        const float x0 = (float)((rx + (int)(k - row * w)) * kTile) + 0.5f - px;
+        const float y0 = (float)((ry + (int)row) * kTile) + 0.5f - py;
+        keep = S >= 0.f && rect_min(A, B, C, kx, ky, x0, x0 + (float)(kTile - 1), y0, y0 + (float)(kTile - 1)) <= S;
+      }
+    }
+    if (keep) {
       const uint32_t tile = (uint32_t)(ry + (int)row) * (uint32_t)a.tiles_x + (uint32_t)rx + (k - row * w);
       atomicOr(col + (size_t)tile * (size_t)a.words, 1u << lo);
       if (smem_tiles)

@@ -22,19 +22,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr float kTMin = 1e-4f;
 constexpr int kMinBlocks = 5;  // CTAs per SM the register budget must allow
 
-// Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0), whose
-// unconstrained minimiser is t = k u with k = -B / C.
-__device__ __forceinline__ float edge_min(float A, float B, float C, float k, float u, float t0, float t1) {
-  const float t = fminf(t1, fmaxf(t0, k * u));
-  return A * u * u + 2.f * B * u * t + C * t * t;
-}
-
 // Bit b set iff some pixel centre of warp block b (8x4 pixels at ((b%2)*8, (b/2)*4)
 // of tile (tx, ty)) may reach alpha >= 1/255: the minimum of q(d) = d^T K d over
 // the block's pixel-centre rectangle (d relative to the mean) is compared with
 // s = -2 * thr.  The minimum of a positive-definite quadratic over a rectangle is
 // 0 if the mean lies inside, else on one of the four edges (each minimised in
-// closed form; a rounded minimiser only raises q by a second-order amount).  If
+// closed form, rect_min).  If
 // all four corner pixel centres of the tile lie in the ellipse q <= s, so does the
 // whole tile (the ellipse is convex) and every block is set at once.  A 0.2% +
 // 1e-3 margin keeps the test conservative against float32 rounding.
@@ -53,14 +46,7 @@ __device__ __forceinline__ uint32_t block_mask(float2 p, float4 co, float thr, i
   for (int b = 0; b < 8; ++b) {
     const float x0 = X0 + (float)((b & 1) * 8), x1 = x0 + 7.f;
     const float y0 = Y0 + (float)((b >> 1) * 4), y1 = y0 + 3.f;
-    float qm;
-    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) {
-      qm = 0.f;
-    } else {
-      qm = fminf(fminf(edge_min(A, B, C, kx, x0, y0, y1), edge_min(A, B, C, kx, x1, y0, y1)),
-                 fminf(edge_min(C, B, A, ky, y0, x0, x1), edge_min(C, B, A, ky, y1, x0, x1)));
-    }
-    if (qm <= s) mask |= 1u << b;
+    if (rect_min(A, B, C, kx, ky, x0, x1, y0, y1) <= s) mask |= 1u << b;
   }
   return mask;
 }

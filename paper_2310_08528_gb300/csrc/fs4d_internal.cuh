@@ -208,6 +208,10 @@ struct EmitArgs {
   float2* sorted_xy;            // [n]
   float4* sorted_co;            // [n]
   float* sorted_rgb;            // [n][3]
+  int cull;                     // 1: mark only the tiles whose pixel centres the ellipse
+                                // {alpha >= 1/255} can reach (the lists lose Gaussians that no
+                                // pixel of the tile blends: the image is unchanged, list
+                                // positions are not the full rectangle's)
 };
 
 struct SortWork {
@@ -343,6 +347,8 @@ struct ProjectBwdArgs {
   float* g_log_scales;
   float* g_opacity;
   float* g_sh;
+  float* stat_grad;         // += |dL/d(projected mean)| where visible (nullable)
+  float* stat_visible;      // += 1 where visible (nullable)
 };
 
 // Per-Gaussian activations and deltas of the deformation MLP, feature-major
@@ -390,6 +396,39 @@ struct WgradArgs {
 long long wgrad_chunks(long long n);
 cudaError_t launch_wgrad(WgradArgs& a, cudaStream_t s);
 
+// Densification and pruning (densify.cu).
+struct DensifyArgs {
+  int n;
+  const float* log_scales;  // [n][3]
+  const float* opacity;     // [n] logits
+  const float* grad_sum;    // [n]
+  const float* visible;     // [n]
+  float grad_threshold, split_log_scale, prune_logit;
+  uint32_t* block_off;      // [3][densify_blocks(n)]: per-block counts, then their exclusive prefixes
+  uint32_t* totals;         // [3]: kept, copied, split
+  int32_t* src;             // [n_out] (map): source Gaussian of each output
+  int32_t* kind;            // [n_out] (map): 0 kept, 1 copy, 2 first child, 3 second child
+};
+struct ChildArgs {
+  long long first, end;     // the children's output range
+  const int32_t* src;
+  const int32_t* kind;
+  const float* means;       // old [n][3]
+  const float* log_scales;  // old [n][3]
+  const float* quats;       // old [n][4]
+  const float* normals;     // [n][2][3]
+  float* out_means;         // new [n_out][3]
+  float* out_log_scales;    // new [n_out][3]
+};
+int densify_blocks(int n);
+cudaError_t launch_densify_plan(const DensifyArgs& a, cudaStream_t s);
+cudaError_t launch_densify_map(const DensifyArgs& a, cudaStream_t s);
+cudaError_t launch_gather(const float* in, float* out, const int32_t* src, const int32_t* kind, long long n_out,
+                          int width, bool zero_new, cudaStream_t s);
+cudaError_t launch_children(const ChildArgs& a, cudaStream_t s);
+cudaError_t launch_morton(const float* means, int n, const float lo[3], const float hi[3], unsigned long long* keys,
+                          uint32_t* values, cudaStream_t s);
+
 }  // namespace fs4d
 
 namespace fs4d {
@@ -422,6 +461,25 @@ __device__ __forceinline__ float composite_alpha(const float4& g0, float b2, flo
   G = ex2_approx(p);
   const float alpha = fminf(0.99f, opacity * G);
   return alpha < 1.f / 255.f ? 0.f : alpha;
+}
+
+// Minimum over t in [t0, t1] of A u^2 + 2 B u t + C t^2 for fixed u (C > 0), whose
+// unconstrained minimiser is t = k u with k = -B / C.
+__device__ __forceinline__ float edge_min(float A, float B, float C, float k, float u, float t0, float t1) {
+  const float t = fminf(t1, fmaxf(t0, k * u));
+  return A * u * u + 2.f * B * u * t + C * t * t;
+}
+
+// Minimum of the positive-definite quadratic q(x, y) = A x^2 + 2 B x y + C y^2 over
+// the rectangle [x0, x1] x [y0, y1] (coordinates relative to the mean): 0 if the
+// mean lies inside, else the least of the four edges' minima (each in closed form;
+// a rounded minimiser only raises q by a second-order amount).  kx = -B / C,
+// ky = -B / A.
+__device__ __forceinline__ float rect_min(float A, float B, float C, float kx, float ky, float x0, float x1,
+                                          float y0, float y1) {
+  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
+  return fminf(fminf(edge_min(A, B, C, kx, x0, y0, y1), edge_min(A, B, C, kx, x1, y0, y1)),
+               fminf(edge_min(C, B, A, ky, y0, x0, x1), edge_min(C, B, A, ky, y1, x0, x1)));
 }
 
 // Natural-log exponent bound: a term reaches alpha >= 1/255 only where

@@ -30,7 +30,8 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_composite", "fs4d_set_wait_limit", "fs4d_last_bands", "fs4d_set_band_pairs",
            "fs4d_train_create", "fs4d_train_step", "fs4d_train_losses", "fs4d_train_steps_done",
            "fs4d_train_destroy", "fs4d_read_scene", "fs4d_save_scene", "fs4d_load_scene_file",
-           "fs4d_backward_times", "fs4d_render_composed")
+           "fs4d_backward_times", "fs4d_render_composed", "fs4d_train_read_state", "fs4d_render_backward_stats",
+           "fs4d_densify", "fs4d_train_stats", "fs4d_train_densify")
 STAGES = ("deform", "project", "depth_sort", "binning", "sort", "composite")
 
 
@@ -89,6 +90,14 @@ class Grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")]
 
 
+class ViewStats(C.Structure):
+    _fields_ = [("grad_norm_sum", C.c_void_p), ("visible", C.c_void_p)]
+
+
+class DensifyConfig(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("split_log_scale", C.c_float), ("prune_logit", C.c_float)]
+
+
 _lib = None
 
 
@@ -128,6 +137,11 @@ def library(path: str = LIB_PATH):
         "fs4d_train_losses": [vp, C.POINTER(f32)],
         "fs4d_train_steps_done": [vp, C.POINTER(i64)],
         "fs4d_train_destroy": [vp],
+        "fs4d_train_read_state": [vp, i32, vp, vp],
+        "fs4d_render_backward_stats": [vp, vp, vp, C.POINTER(Grads), C.POINTER(ViewStats)],
+        "fs4d_densify": [vp, i32, C.POINTER(DensifyConfig), C.POINTER(ViewStats), vp, vp, C.POINTER(i64)],
+        "fs4d_train_stats": [vp, C.POINTER(ViewStats)],
+        "fs4d_train_densify": [vp, C.POINTER(DensifyConfig), vp, C.POINTER(i64)],
         "fs4d_read_scene": [vp, i32, C.POINTER(Grads), i32],
         "fs4d_save_scene": [vp, i32, C.c_char_p],
         "fs4d_load_scene_file": [vp, C.c_char_p, C.POINTER(i32)],
@@ -318,11 +332,41 @@ class Context:
         self.call("fs4d_render", sid, prec, C.byref(cs), float(t), _ptr(image), None, None, C.byref(fr))
         return image, fr
 
-    def render_backward(self, frame, dl_dimage, grads: Dict[str, object]) -> None:
-        """Accumulate d(sum(dl_dimage * image))/d(parameter) into the given device tensors."""
+    def render_backward(self, frame, dl_dimage, grads: Dict[str, object], stats=None) -> None:
+        """Accumulate d(sum(dl_dimage * image))/d(parameter) into the given device tensors;
+        stats = (grad_norm_sum, visible) device tensors [n] also accumulate the
+        densification statistics (fs4d_render_backward_stats)."""
         g = Grads(**{k: _ptr(grads.get(k)) for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
                                                        "planes", "mlp")})
-        self.call("fs4d_render_backward", frame, _ptr(dl_dimage.contiguous()), C.byref(g))
+        if stats is None:
+            self.call("fs4d_render_backward", frame, _ptr(dl_dimage.contiguous()), C.byref(g))
+        else:
+            vs = ViewStats(_ptr(stats[0]), _ptr(stats[1]))
+            self.call("fs4d_render_backward_stats", frame, _ptr(dl_dimage.contiguous()), C.byref(g), C.byref(vs))
+
+    def densify(self, sid: int, stats, normals, grad_threshold: float, split_log_scale: float, prune_logit: float,
+                trainer=None) -> int:
+        """Densify and prune scene sid (fs4d_densify) from stats = (grad_norm_sum,
+        visible) and normals [n][2][3] (device tensors); returns the new number of
+        Gaussians.  The binding's record of the scene takes the new parameters."""
+        vs = ViewStats(_ptr(stats[0]), _ptr(stats[1]))
+        cfg = DensifyConfig(grad_threshold, split_log_scale, prune_logit)
+        m = C.c_int64()
+        self.call("fs4d_densify", sid, C.byref(cfg), C.byref(vs), _ptr(normals.contiguous()),
+                  trainer.h if trainer is not None else None, C.byref(m))
+        self._resized(sid, m.value)
+        return m.value
+
+    def _resized(self, sid: int, n: int) -> None:
+        """Replace the record of scene sid by a host copy of its parameters at size n."""
+        rec = self._scenes[sid].copy()
+        k = int(rec.sh.shape[1])
+        shapes = {"means": (n, 3), "log_scales": (n, 3), "quats": (n, 4), "opacity_logits": (n,), "sh": (n, k, 3)}
+        for key, shp in shapes.items():
+            setattr(rec, key, np.empty(shp, np.float32))
+        self._scenes[sid] = rec
+        for key, v in self.read_scene(sid).items():
+            setattr(rec, key, v)
 
     def frame_free(self, frame) -> None:
         self.call("fs4d_frame_free", frame)
@@ -535,6 +579,7 @@ class Trainer:
         h = C.c_void_p()
         ctx.call("fs4d_train_create", sid, C.byref(self.cfg), C.byref(h))
         self.h = h
+        self.sid = sid
 
     def step(self, cam, t: float, target, prec: int = FP32, losses=None) -> None:
         cs = camera_struct(cam)
@@ -554,6 +599,39 @@ class Trainer:
         k = C.c_int64()
         self.lib.fs4d_train_steps_done(self.h, C.byref(k))
         return k.value
+
+    def read_state(self, group: int):
+        """Adam moments (m, v) of parameter group `group` (0 means .. 6 mlp) as host arrays."""
+        names = ("means", "log_scales", "quats", "opacity_logits", "sh", "planes", "mlp")
+        rec = self.ctx._scenes[self.sid]
+        size = int(np.prod(np.shape(getattr(rec, names[group]))))
+        m, v = np.empty(size, np.float32), np.empty(size, np.float32)
+        st = self.lib.fs4d_train_read_state(self.h, int(group), m.ctypes.data, v.ctypes.data)
+        if st != 0:
+            raise Fs4dError(st, self.lib.fs4d_last_error(self.ctx.h).decode())
+        return m, v
+
+    def stats(self):
+        """The densification statistics accumulated by the steps: (grad_norm_sum, visible), device tensors."""
+        import torch
+        n = int(self.ctx._scenes[self.sid].means.shape[0])
+        g = torch.empty(n, dtype=torch.float32, device="cuda")
+        vis = torch.empty(n, dtype=torch.float32, device="cuda")
+        vs = ViewStats(_ptr(g), _ptr(vis))
+        st = self.lib.fs4d_train_stats(self.h, C.byref(vs))
+        if st != 0:
+            raise Fs4dError(st, self.lib.fs4d_last_error(self.ctx.h).decode())
+        return g, vis
+
+    def densify(self, normals, grad_threshold: float, split_log_scale: float, prune_logit: float) -> int:
+        """fs4d_train_densify with the trainer's own statistics; returns the new n."""
+        cfg = DensifyConfig(grad_threshold, split_log_scale, prune_logit)
+        m = C.c_int64()
+        st = self.lib.fs4d_train_densify(self.h, C.byref(cfg), _ptr(normals.contiguous()), C.byref(m))
+        if st != 0:
+            raise Fs4dError(st, self.lib.fs4d_last_error(self.ctx.h).decode())
+        self.ctx._resized(self.sid, m.value)
+        return m.value
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -488,6 +488,28 @@ def test_bitmap_and_sort_binning_render_identical_images(ctx, prec, w, h):
         ctx.unload_scene(sid)
 
 
+@pytest.mark.parametrize("prec", [fs4d.FP32, fs4d.BF16])
+def test_culled_tile_lists_render_identical_images(ctx, prec):
+    """Frames that report no list positions leave out of each tile's list the
+    Gaussians whose ellipse {alpha >= 1/255} reaches none of the tile's pixel
+    centres; no pixel would blend them, so the image is bit-identical to the frame
+    over the full rectangles (a frame with last-contributor output), on the
+    800x800 object, a ragged frame, and through the host and capture calls."""
+    s = sg.make_object(0)
+    sid = ctx.load_scene(s)
+    try:
+        for cam in (sg.hemisphere_cameras(50, width=800, height=800)[7],
+                    sg.hemisphere_cameras(3, width=333, height=517, seed=2)[1]):
+            full, _, _ = ctx.render(sid, cam, 0.35, prec=prec, with_aux=True)
+            culled = ctx.render(sid, cam, 0.35, prec=prec)
+            host = ctx.render_host(sid, cam, 0.35, prec=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(full, culled)
+            assert np.array_equal(full.cpu().numpy(), host)
+    finally:
+        ctx.unload_scene(sid)
+
+
 # ------------------------------------------------------------------ BF16 tensor-core path
 
 def bf16_tol(s, X, Q, S):
