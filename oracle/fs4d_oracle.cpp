@@ -5,6 +5,8 @@
 #include "fs4d_oracle.h"
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -419,7 +421,11 @@ void orc_composite(int32_t width, int32_t height, int32_t tile, const uint32_t* 
 //   stop  -- T (1 - alpha_i) < 1e-4 ends the blend before term i;
 //   order -- two blended terms whose depths tie to within rounding may swap.
 // flip_kind/flip_gid name the decisions to invert (kind 0 skip, 1 stop, 2 order
-// with the term that follows flip_gid in the list as blended).
+// with the term that follows flip_gid in the list as blended).  Terms whose
+// projected attributes (position, conic, opacity, colour) are identical -- copies
+// made by densification -- take every decision alike in any implementation (the
+// same inputs through the same arithmetic) and are interchangeable in order: they
+// share one skip decision and never form an order decision with each other.
 namespace {
 struct Decision { int kind; uint32_t gid; };
 
@@ -448,6 +454,15 @@ void blend_pixel(int len, const uint32_t* list, double px, double py, const doub
       if (flips[f].kind == kind && flips[f].gid == g) return true;
     return false;
   };
+  // the first term of the list with the same projected attributes as each term
+  std::map<std::array<double, 9>, uint32_t> first;
+  std::map<uint32_t, uint32_t> rep;
+  for (int k = 0; k < len; ++k) {
+    const uint32_t g = order[k];
+    const std::array<double, 9> key = {xy[2 * g], xy[2 * g + 1], conic[3 * g], conic[3 * g + 1], conic[3 * g + 2],
+                                       opacity[g], rgb[3 * g], rgb[3 * g + 1], rgb[3 * g + 2]};
+    rep[g] = first.emplace(key, g).first->second;
+  }
   double T = 1.0, prev_depth = -1.0;
   uint32_t prev = 0;
   int last = 0;
@@ -458,9 +473,11 @@ void blend_pixel(int len, const uint32_t* list, double px, double py, const doub
     const double power = -0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) - conic[3 * g + 1] * dx * dy;
     if (power > 0.0) continue;
     const double alpha = std::min(kAlphaMax, opacity[g] * std::exp(power));
-    if (found && std::fabs(alpha - kAlphaMin) / kAlphaMin < rel_tol) found->push_back({0, g});
-    if ((alpha < kAlphaMin) != flipped(0, g)) continue;
-    if (found && prev_depth > 0.0 && std::fabs(depth[g] - prev_depth) / std::fabs(depth[g]) < depth_tol)
+    const uint32_t r = rep[g];
+    if (found && r == g && std::fabs(alpha - kAlphaMin) / kAlphaMin < rel_tol) found->push_back({0, g});
+    if ((alpha < kAlphaMin) != flipped(0, r)) continue;
+    if (found && prev_depth > 0.0 && rep[prev] != r &&
+        std::fabs(depth[g] - prev_depth) / std::fabs(depth[g]) < depth_tol)
       found->push_back({2, prev});
     prev_depth = depth[g];
     prev = g;

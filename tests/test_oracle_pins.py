@@ -646,9 +646,27 @@ def test_pixel_outcomes_transmittance_stop_both_ways():
     assert out[1, 4] == 1 and out[1, 3] == pytest.approx(1 - a1, rel=1e-12)
 
 
+def test_pixel_outcomes_identical_terms_decide_alike():
+    """Two identical terms (a Gaussian and its densification copy) at the skip
+    threshold: both are blended or both skipped -- two outcomes, not four -- and
+    their equal depths form no order decision (swapping them changes nothing)."""
+    d = 2.0
+    a = (1 / 255) * (1 + 1e-7)
+    o = a / math.exp(-0.5 * 0.5 * d * d)
+    g = (10.5 + d, 7.5, 0.5, 0.0, 0.5, o, 1.0, 0.2, 0.4, 2.0)
+    out = oracle.pixel_outcomes([0, 1], 10, 7, _proj([g, g]))
+    assert out.shape == (2, 5)
+    np.testing.assert_allclose(out[0, :3], (a + a * (1 - a)) * np.array([1.0, 0.2, 0.4]), rtol=1e-12)
+    assert out[0, 4] == 2
+    np.testing.assert_array_equal(out[1], [0, 0, 0, 1, 0])
+    # the same two terms with one colour changed are two decisions again
+    h = g[:6] + (0.5, 0.2, 0.4) + g[9:]
+    assert oracle.pixel_outcomes([0, 1], 10, 7, _proj([g, h])).shape[0] > 2
+
+
 def test_pixel_outcomes_limit_on_flips():
     """More near-threshold decisions than max_flip: not enumerated (None)."""
-    rows = [(0.5, 0.5, 0.1, 0.0, 0.1, 0.2, 1, 1, 1, 3.0)] * 4
+    rows = [(0.5, 0.5, 0.1, 0.0, 0.1, 0.2, 1 - 0.1 * k, 1, 1, 3.0) for k in range(4)]  # three depth ties
     assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=2) is None
     assert oracle.pixel_outcomes([0, 1, 2, 3], 0, 0, _proj(rows), max_flip=3).shape == (8, 5)
 
