@@ -35,7 +35,7 @@ class OrcScene(C.Structure):
                 ("aabb_min", C.c_double * 3), ("aabb_max", C.c_double * 3),
                 ("n_levels", C.c_int32), ("res_spatial", C.c_int32 * 4), ("res_time", C.c_int32),
                 ("feat_dim", C.c_int32), ("planes", C.c_void_p), ("mlp_width", C.c_int32),
-                ("mlp", C.c_void_p)]
+                ("mlp", C.c_void_p), ("color_heads", C.c_int32)]
 
 
 class OrcCamera(C.Structure):
@@ -69,6 +69,9 @@ def lib():
         L.orc_sh_basis.argtypes = [C.c_int32, F64P, F64P]
         L.orc_project.argtypes = [C.POINTER(OrcScene), F64P, F64P, F64P, C.POINTER(OrcCamera), C.c_int32,
                                   C.POINTER(OrcProjected)]
+        L.orc_project_appearance.argtypes = [C.POINTER(OrcScene), F64P, F64P, F64P, F64P, F64P,
+                                             C.POINTER(OrcCamera), C.c_int32, C.POINTER(OrcProjected)]
+        L.orc_appearance.argtypes = [C.POINTER(OrcScene), C.c_double, F64P, F64P]
         L.orc_bin_sort.argtypes = [C.c_int32, U32P, I32P, C.c_int32, C.c_int32, C.c_int64, U64P, U32P, U32P]
         L.orc_bin_sort.restype = C.c_int64
         L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, U32P, U32P, F64P, F64P, F64P, F64P, F64P,
@@ -126,6 +129,7 @@ class _SceneHandle:
         s.res_time = int(scene.res_time)
         s.feat_dim = int(scene.feat_dim)
         s.mlp_width = int(scene.mlp_width)
+        s.color_heads = int(bool(getattr(scene, "color_heads", False)))
         self.struct = s
         self.n = s.n
         self.hin = s.feat_dim * s.n_levels
@@ -182,7 +186,20 @@ def sh_basis(degree: int, direction) -> np.ndarray:
     return out[:(degree + 1) ** 2]
 
 
-def project(scene, cam, means=None, quats=None, log_scales=None, tile: int = 16) -> Dict[str, np.ndarray]:
+def appearance(scene, t: float):
+    """App. B: (sh [n][K][3], opacity_logits [n]) after the colour and opacity heads
+    at time t (float64; the scene's own values when it has no such heads)."""
+    h = _SceneHandle(scene)
+    sh = np.zeros((h.n, h.k, 3))
+    lg = np.zeros(h.n)
+    lib().orc_appearance(C.byref(h.struct), float(t), sh.reshape(-1), lg)
+    return sh, lg
+
+
+def project(scene, cam, means=None, quats=None, log_scales=None, tile: int = 16, sh=None,
+            opacity_logits=None) -> Dict[str, np.ndarray]:
+    """Eq. 2 / Eq. 3 and the SH colour; sh / opacity_logits (float64, e.g. from
+    appearance()) replace the scene's."""
     h = _SceneHandle(scene)
     n = h.n
     X = np.ascontiguousarray(scene.means if means is None else means, np.float64)
@@ -193,7 +210,12 @@ def project(scene, cam, means=None, quats=None, log_scales=None, tile: int = 16)
                rect=np.zeros((n, 4), np.int32), margin=np.zeros(n))
     P = OrcProjected(**{k: v.ctypes.data for k, v in out.items()})
     cc = _camera(cam)
-    lib().orc_project(C.byref(h.struct), X, Q, S, C.byref(cc), int(tile), C.byref(P))
+    if sh is None and opacity_logits is None:
+        lib().orc_project(C.byref(h.struct), X, Q, S, C.byref(cc), int(tile), C.byref(P))
+    else:
+        shd = np.ascontiguousarray(scene.sh if sh is None else sh, np.float64).reshape(-1)
+        lgd = np.ascontiguousarray(scene.opacity_logits if opacity_logits is None else opacity_logits, np.float64)
+        lib().orc_project_appearance(C.byref(h.struct), X, Q, S, shd, lgd, C.byref(cc), int(tile), C.byref(P))
     return out
 
 
@@ -263,7 +285,11 @@ def project_composed(scenes, shifts, cam, t: float, deform: bool = True, tile: i
             S = np.array(scene.log_scales, np.float64)
         if sh is not None:
             X = X + np.asarray(sh, np.float64)[None, :]
-        parts.append(project(scene, cam, X, Q, S, tile=tile))
+        if deform and getattr(scene, "color_heads", False):
+            shd, lgd = appearance(scene, t)
+            parts.append(project(scene, cam, X, Q, S, tile=tile, sh=shd, opacity_logits=lgd))
+        else:
+            parts.append(project(scene, cam, X, Q, S, tile=tile))
     return {k: np.ascontiguousarray(np.concatenate([p[k] for p in parts])) for k in parts[0]}
 
 

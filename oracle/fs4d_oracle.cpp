@@ -55,23 +55,32 @@ void axis_setup(double u, int R, int* i0, double* f, double* dgdu) {
 }
 
 // Layer (out, in) shapes d1 d2 x1 x2 r1 r2 s1 s2 and the float offset of each.
+// With colour heads (App. B) four more layers follow: c1 (W -> W), c2 (W -> 3K),
+// a1 (W -> W), a2 (W -> 1).
 struct MlpLayout {
-  int out[8], in[8];
-  int64_t w[8], b[8];
+  int out[12], in[12];
+  int64_t w[12], b[12];
+  int n_layers;
   int64_t total;
 };
 
 MlpLayout mlp_layout(const orc_scene* s) {
   MlpLayout L;
   int W = s->mlp_width, hin = s->feat_dim * s->n_levels;
+  const int K3 = 3 * (s->sh_degree + 1) * (s->sh_degree + 1);
   L.out[0] = W; L.in[0] = hin;
   L.out[1] = W; L.in[1] = W;
   for (int h = 0; h < 3; ++h) {
     L.out[2 + 2 * h] = W; L.in[2 + 2 * h] = W;
     L.out[3 + 2 * h] = kHeadOut[h]; L.in[3 + 2 * h] = W;
   }
+  L.n_layers = s->color_heads ? 12 : 8;
+  L.out[8] = W; L.in[8] = W;
+  L.out[9] = K3; L.in[9] = W;
+  L.out[10] = W; L.in[10] = W;
+  L.out[11] = 1; L.in[11] = W;
   int64_t off = 0;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < L.n_layers; ++k) {
     L.w[k] = off; off += (int64_t)L.out[k] * L.in[k];
     L.b[k] = off; off += L.out[k];
   }
@@ -227,11 +236,48 @@ void orc_deform(const orc_scene* s, double t, double* means, double* quats, doub
   }
 }
 
+// App. B: dC = phi_C(f_d), dalpha = phi_alpha(f_d), each head Lin(W->W), ReLU,
+// Lin(W->out) like the others; C' = C + dC over every SH coefficient, and the
+// opacity deformation is read as an addition to the stored logit.
+void orc_appearance(const orc_scene* s, double t, double* sh, double* opacity_logits) {
+  const int n = s->n, hin = s->feat_dim * s->n_levels, W = s->mlp_width;
+  const int K3 = 3 * (s->sh_degree + 1) * (s->sh_degree + 1);
+  for (int64_t i = 0; i < (int64_t)n * K3; ++i) sh[i] = s->sh[i];
+  for (int g = 0; g < n; ++g) opacity_logits[g] = s->opacity_logits[g];
+  if (!s->color_heads) return;
+  const MlpLayout Lo = mlp_layout(s);
+  std::vector<double> xyz(3 * (int64_t)n), fh((int64_t)n * hin);
+  for (int64_t i = 0; i < 3 * (int64_t)n; ++i) xyz[i] = s->means[i];
+  orc_features(s, xyz.data(), n, t, fh.data());
+#pragma omp parallel for schedule(static)
+  for (int g = 0; g < n; ++g) {
+    std::vector<double> a1(W), fd(W), hid(W), dc(K3), da(1);
+    linear(s, Lo, 0, fh.data() + (int64_t)g * hin, a1.data());
+    for (auto& v : a1) v = relu(v);
+    linear(s, Lo, 1, a1.data(), fd.data());
+    for (auto& v : fd) v = relu(v);
+    linear(s, Lo, 8, fd.data(), hid.data());
+    for (auto& v : hid) v = relu(v);
+    linear(s, Lo, 9, hid.data(), dc.data());
+    for (int j = 0; j < K3; ++j) sh[(int64_t)g * K3 + j] += dc[j];
+    linear(s, Lo, 10, fd.data(), hid.data());
+    for (auto& v : hid) v = relu(v);
+    linear(s, Lo, 11, hid.data(), da.data());
+    opacity_logits[g] += da[0];
+  }
+}
+
 void orc_sh_basis(int32_t degree, const double* dir, double* basis) { sh_basis(degree, dir, basis); }
 
 // Eq. 2 and Eq. 3 (EWA splatting), colour from SH, screen-space tile rectangle.
 void orc_project(const orc_scene* s, const double* means, const double* quats, const double* log_scales,
                  const orc_camera* cam, int32_t tile, orc_projected* out) {
+  orc_project_appearance(s, means, quats, log_scales, nullptr, nullptr, cam, tile, out);
+}
+
+void orc_project_appearance(const orc_scene* s, const double* means, const double* quats,
+                            const double* log_scales, const double* shd, const double* lgd,
+                            const orc_camera* cam, int32_t tile, orc_projected* out) {
   const int n = s->n;
   const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
   const int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
@@ -253,7 +299,8 @@ void orc_project(const orc_scene* s, const double* means, const double* quats, c
     double p[3];
     for (int r = 0; r < 3; ++r) p[r] = Rc[r][0] * X[0] + Rc[r][1] * X[1] + Rc[r][2] * X[2] + tc[r];
     out->depth[g] = p[2];
-    out->opacity[g] = 1.0 / (1.0 + std::exp(-(double)s->opacity_logits[g]));
+    const double logit = lgd ? lgd[g] : (double)s->opacity_logits[g];
+    out->opacity[g] = 1.0 / (1.0 + std::exp(-logit));
     out->margin[g] = std::min(out->margin[g], std::fabs(p[2] - cam->znear));
     if (!(p[2] > cam->znear)) continue;
     // Sigma = R S S^T R^T with R from the normalised quaternion, S = diag(exp(s')).
@@ -325,7 +372,10 @@ void orc_project(const orc_scene* s, const double* means, const double* quats, c
     sh_basis(s->sh_degree, dir, Y);
     for (int ch = 0; ch < 3; ++ch) {
       double acc = 0.5;
-      for (int k = 0; k < K; ++k) acc += Y[k] * (double)s->sh[((int64_t)g * K + k) * 3 + ch];
+      for (int k = 0; k < K; ++k) {
+        const int64_t e = ((int64_t)g * K + k) * 3 + ch;
+        acc += Y[k] * (shd ? shd[e] : (double)s->sh[e]);
+      }
       out->rgb[3 * (int64_t)g + ch] = std::max(0.0, acc);
     }
   }
@@ -568,7 +618,14 @@ int64_t orc_render(const orc_scene* s, const orc_camera* cam, double t, int32_t 
   std::vector<int32_t> radius(n), rect(4 * (int64_t)n);
   orc_projected P{xy.data(), conic.data(), cov.data(), op.data(), rgb.data(), depth.data(), radius.data(),
                   rect.data(), mg.data()};
-  orc_project(s, X.data(), Q.data(), Sc.data(), cam, tile, &P);
+  if (deform && s->color_heads) {  // App. B: the colour and opacity deformation
+    const int K3 = 3 * (s->sh_degree + 1) * (s->sh_degree + 1);
+    std::vector<double> shd((int64_t)n * K3), lgd(n);
+    orc_appearance(s, t, shd.data(), lgd.data());
+    orc_project_appearance(s, X.data(), Q.data(), Sc.data(), shd.data(), lgd.data(), cam, tile, &P);
+  } else {
+    orc_project(s, X.data(), Q.data(), Sc.data(), cam, tile, &P);
+  }
   const int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
   std::vector<uint32_t> dbits(n);
   for (int g = 0; g < n; ++g) {
@@ -641,6 +698,7 @@ void quat_rot_grad(const double q[4], double dR[4][3][3]) {
 
 extern "C" int32_t orc_render_backward(const orc_scene* s, const orc_camera* cam, double t, int32_t deform,
                                        int32_t tile, const double* dl_dimage, orc_grads* G) {
+  if (s->color_heads) return 3;  // the backward through the colour and opacity heads is not written
   const int n = s->n, W = s->mlp_width, L = s->n_levels, h = s->feat_dim, hin = h * L;
   const int K = (s->sh_degree + 1) * (s->sh_degree + 1);
   const MlpLayout Lo = mlp_layout(s);

@@ -15,6 +15,8 @@
  *                                    product over six planes, concat over levels)
  *   orc_mlp / orc_deform             Sec. 4.2 (tiny MLP phi_d, heads phi_x phi_r
  *                                    phi_s) and Eq. 6 (X'=X+dX, r'=r+dr, s'=s+ds)
+ *   orc_appearance                   App. B (heads phi_C, phi_alpha: C'=C+dC,
+ *                                    opacity logit' = logit + dalpha)
  *   orc_project                      Sec. 3.1, Eq. 2 (Sigma = R S S^T R^T) and
  *                                    Eq. 3 (Sigma' = J W Sigma W^T J^T), SH colour
  *   orc_bin_sort                     tile binning and (tile, depth) ordering of the
@@ -62,7 +64,8 @@ typedef struct orc_scene {
   int32_t feat_dim;
   const float* planes;      /* per level, per plane xy xz yz xt yt zt: [R_b][R_a][h] */
   int32_t mlp_width;
-  const float* mlp;         /* d1 d2 x1 x2 r1 r2 s1 s2: W[out][in] then b[out] */
+  const float* mlp;         /* d1 d2 x1 x2 r1 r2 s1 s2 [c1 c2 a1 a2]: W[out][in] then b[out] */
+  int32_t color_heads;      /* 1: the colour and opacity heads phi_C, phi_alpha (App. B) follow */
 } orc_scene;
 
 typedef struct orc_camera {
@@ -91,6 +94,14 @@ void orc_features(const orc_scene* s, const double* xyz, int32_t n, double t, do
 void orc_mlp(const orc_scene* s, const double* fh, int32_t n, double* delta);
 void orc_deform(const orc_scene* s, double t, double* means, double* quats, double* log_scales);
 void orc_sh_basis(int32_t degree, const double* dir, double* basis);
+/* App. B: SH coefficients [n][K][3] and opacity logits [n] after the colour and
+ * opacity heads at time t (the canonical values when the scene has none). */
+void orc_appearance(const orc_scene* s, double t, double* sh, double* opacity_logits);
+/* orc_project with the SH coefficients and opacity logits taken from sh / opacity_logits
+ * (double, the shapes of the scene's) instead of the scene's. */
+void orc_project_appearance(const orc_scene* s, const double* means, const double* quats,
+                            const double* log_scales, const double* sh, const double* opacity_logits,
+                            const orc_camera* cam, int32_t tile, orc_projected* out);
 void orc_project(const orc_scene* s, const double* means, const double* quats, const double* log_scales,
                  const orc_camera* cam, int32_t tile, orc_projected* out);
 int64_t orc_bin_sort(int32_t n, const uint32_t* depth_bits, const int32_t* rect, int32_t tiles_x,

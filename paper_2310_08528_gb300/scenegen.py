@@ -58,6 +58,7 @@ class Scene:
     planes: np.ndarray
     mlp_width: int
     mlp: np.ndarray
+    color_heads: bool = False  # the mlp also holds the colour and opacity heads (App. B)
 
     @property
     def n(self) -> int:
@@ -96,12 +97,32 @@ def plane_shapes(res_spatial: Sequence[int], res_time: int, h: int) -> List[Tupl
     return out
 
 
-def mlp_layer_shapes(in_dim: int, width: int) -> List[Tuple[int, int]]:
-    """(out, in) of the eight linear layers d1 d2 x1 x2 r1 r2 s1 s2."""
+def mlp_layer_shapes(in_dim: int, width: int, color_k: int = 0) -> List[Tuple[int, int]]:
+    """(out, in) of the eight linear layers d1 d2 x1 x2 r1 r2 s1 s2, and with
+    color_k = K > 0 SH coefficients per channel the colour and opacity heads' four
+    (c1 c2 a1 a2: W -> W -> 3K and W -> W -> 1) after them."""
     shapes = [(width, in_dim), (width, width)]
     for o in HEAD_OUT:
         shapes += [(width, width), (o, width)]
+    if color_k:
+        shapes += [(width, width), (3 * color_k, width), (width, width), (1, width)]
     return shapes
+
+
+def with_color_heads(scene: Scene, seed: int, std: float = 0.05, bias_std: float = 0.05) -> Scene:
+    """A copy of `scene` with colour and opacity heads (App. B) appended to its MLP:
+    weights N(0, std), biases N(0, bias_std)."""
+    rng = np.random.default_rng(seed)
+    width = scene.mlp_width
+    k = (scene.sh_degree + 1) ** 2
+    parts = [scene.mlp.astype(np.float32)]
+    for o, i in mlp_layer_shapes(width, width, k)[8:]:
+        parts.append(rng.normal(0.0, std, size=(o, i)).astype(np.float32).ravel())
+        parts.append(rng.normal(0.0, bias_std, size=o).astype(np.float32))
+    out = scene.copy()
+    out.mlp = np.concatenate(parts)
+    out.color_heads = True
+    return out
 
 
 def _unit_quats(rng: np.random.Generator, n: int) -> np.ndarray:

@@ -19,7 +19,11 @@ def oracle_frame(scene, cam, t, deform=True, tile=16):
     img, T, nc, mg, K = oracle.render(scene, cam, t, deform=deform, tile=tile)
     if deform:
         X, Q, S = oracle.deform(scene, t)
-        p = oracle.project(scene, cam, X, Q, S, tile=tile)
+        if getattr(scene, "color_heads", False):  # App. B: deformed colour and opacity
+            shd, lgd = oracle.appearance(scene, t)
+            p = oracle.project(scene, cam, X, Q, S, tile=tile, sh=shd, opacity_logits=lgd)
+        else:
+            p = oracle.project(scene, cam, X, Q, S, tile=tile)
     else:
         p = oracle.project(scene, cam, tile=tile)
     tx, ty = (cam.width + tile - 1) // tile, (cam.height + tile - 1) // tile

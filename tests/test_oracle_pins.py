@@ -450,6 +450,85 @@ def test_mlp_against_torch_linear_layers():
     assert oracle.mlp(s, fh) == pytest.approx(want, rel=1e-12, abs=1e-14)
 
 
+# --------------------------------------------------------------------- App. B: colour and opacity heads
+
+def _color_layers(s):
+    """(offset, out, in) of the colour and opacity heads c1 c2 a1 a2 after the 8 layers."""
+    k = (s.sh_degree + 1) ** 2
+    shapes = sg.mlp_layer_shapes(s.feat_dim * s.n_levels, s.mlp_width, k)
+    off, out = 0, []
+    for o, i in shapes:
+        out.append((off, o, i))
+        off += o * i + o
+    assert off == s.mlp.size
+    return out[8:]
+
+
+def test_color_heads_against_torch_linear_layers():
+    """dC = phi_C(f_d) and dalpha = phi_alpha(f_d) (App. B) with torch.nn.Linear
+    layers on the oracle's features: C' = C + dC (the 3K outputs in the [K][3]
+    layout), logit' = logit + dalpha."""
+    torch = pytest.importorskip("torch")
+    s = sg.with_color_heads(sg.make_object(3, n=30, res_spatial=(6, 8), res_time=4, h=16, mlp_std=0.2), 4, std=0.2)
+    lins = []
+    for off, o, i in _layers(s) + _color_layers(s):
+        lin = torch.nn.Linear(i, o).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(s.mlp[off:off + o * i].reshape(o, i).astype(np.float64)))
+            lin.bias.copy_(torch.from_numpy(s.mlp[off + o * i:off + o * i + o].astype(np.float64)))
+        lins.append(lin)
+    t = 0.6
+    x = torch.from_numpy(oracle.features(s, s.means.astype(np.float64), t))
+    relu = torch.relu
+    fd = relu(lins[1](relu(lins[0](x))))
+    dc = lins[9](relu(lins[8](fd))).detach().numpy().reshape(s.n, -1, 3)
+    da = lins[11](relu(lins[10](fd))).detach().numpy()[:, 0]
+    sh, lg = oracle.appearance(s, t)
+    assert sh == pytest.approx(s.sh.astype(np.float64) + dc, rel=1e-12, abs=1e-14)
+    assert lg == pytest.approx(s.opacity_logits.astype(np.float64) + da, rel=1e-12, abs=1e-14)
+    assert np.abs(dc).max() > 1e-3 and np.abs(da).max() > 1e-3
+
+
+def test_color_heads_zero_layers_change_nothing():
+    """Colour and opacity heads with all weights and biases 0 render exactly the scene without them."""
+    s = sg.make_tiny(5, n=300, mlp_std=0.2)
+    c = sg.with_color_heads(s, 1)
+    for off, o, i in _color_layers(c):
+        c.mlp[off:off + o * i + o] = 0.0
+    a, Ta, na, _, _ = oracle.render(s, sg.tiny_camera(), 0.4)
+    b, Tb, nb, _, _ = oracle.render(c, sg.tiny_camera(), 0.4)
+    assert np.array_equal(a, b) and np.array_equal(Ta, Tb) and np.array_equal(na, nb)
+
+
+def test_color_heads_output_bias_is_a_constant_shift():
+    """Only the output biases non-zero: every Gaussian's SH coefficients move by the
+    colour head's bias and its opacity logit by the opacity head's, so the frame is
+    the frame of the scene shifted that way without heads."""
+    s = sg.make_object(2, n=400, res_spatial=(6, 8), res_time=4, h=16, mlp_std=0.1)
+    c = sg.with_color_heads(s, 3)
+    (o1, n1, i1), (o2, n2, i2), (o3, n3, i3), (o4, n4, i4) = _color_layers(c)
+    for off, o, i in _color_layers(c):
+        c.mlp[off:off + o * i] = 0.0
+    beta = c.mlp[o2 + n2 * i2:o2 + n2 * i2 + n2].astype(np.float64)
+    gamma = float(c.mlp[o4 + n4 * i4])
+    sh, lg = oracle.appearance(c, 0.5)
+    assert np.array_equal(sh, s.sh.astype(np.float64) + beta.reshape(-1, 3)[None])
+    assert np.array_equal(lg, s.opacity_logits.astype(np.float64) + gamma)
+    shifted = s.copy()
+    shifted.sh = (s.sh.astype(np.float64) + beta.reshape(-1, 3)[None]).astype(np.float32)
+    shifted.opacity_logits = (s.opacity_logits.astype(np.float64) + gamma).astype(np.float32)
+    cam = sg.hemisphere_cameras(2, width=96, height=80, seed=1)[0]
+    X, Q, S = oracle.deform(c, 0.5)
+    p_heads = oracle.project(c, cam, X, Q, S, sh=sh, opacity_logits=lg)
+    p_shift = oracle.project(shifted, cam, X, Q, S, sh=shifted.sh.astype(np.float64),
+                             opacity_logits=shifted.opacity_logits.astype(np.float64))
+    np.testing.assert_allclose(p_heads["rgb"], p_shift["rgb"], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(p_heads["opacity"], p_shift["opacity"], rtol=1e-6)
+    img_c, *_ = oracle.render(c, cam, 0.5)
+    img_s, *_ = oracle.render(shifted, cam, 0.5)
+    np.testing.assert_allclose(img_c, img_s, atol=2e-6)
+
+
 def test_deform_is_eq6_addition():
     s = sg.make_tiny(2, mlp_std=0.3)
     X, Q, S = oracle.deform(s, 0.7)

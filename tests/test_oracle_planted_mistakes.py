@@ -62,8 +62,8 @@ MISTAKES = [
      "dir[k] = (double)s->means[3 * (int64_t)g + k] - campos[k];", 0),
     ("frame deformed at a fixed time", "orc_deform(s, t, X.data(), Q.data(), Sc.data());",
      "orc_deform(s, 0.5, X.data(), Q.data(), Sc.data());", 0),
-    ("opacity sigmoid sign", "1.0 / (1.0 + std::exp(-(double)s->opacity_logits[g]))",
-     "1.0 / (1.0 + std::exp((double)s->opacity_logits[g]))", 0),
+    ("opacity sigmoid sign", "out->opacity[g] = 1.0 / (1.0 + std::exp(-logit));",
+     "out->opacity[g] = 1.0 / (1.0 + std::exp(logit));", 0),
     ("camera centre sign", "campos[c] = -(Rc[0][c] * tc[0]", "campos[c] = (Rc[0][c] * tc[0]", 0),
     ("colour offset 0.5 dropped", "double acc = 0.5;", "double acc = 0.0;", 0),
     ("SH with the Condon-Shortley phase", "Y[1] = c1 * y; Y[2] = c1 * z; Y[3] = c1 * x;",
@@ -113,6 +113,13 @@ MISTAKES = [
     ("backward: box scale of the sampling point", "G->means[3 * (int64_t)g + a] += gv * dv_dfa * da[p] * 2.0 /",
      "G->means[3 * (int64_t)g + a] += gv * dv_dfa * da[p] * 1.0 /", 0),
     ("backward: projected-mean gradient sign", "G->xy[i] += g_xy[i];", "G->xy[i] -= g_xy[i];", 0),
+    # App. B: colour and opacity heads
+    ("colour head replaces the SH instead of adding", "for (int j = 0; j < K3; ++j) sh[(int64_t)g * K3 + j] += dc[j];",
+     "for (int j = 0; j < K3; ++j) sh[(int64_t)g * K3 + j] = dc[j];", 0),
+    ("opacity head reads the colour head's hidden layer", "    linear(s, Lo, 10, fd.data(), hid.data());\n", "", 0),
+    ("colour head without its ReLU", "for (auto& v : hid) v = relu(v);", "", 1),
+    ("projection ignores the deformed colour", "acc += Y[k] * (shd ? shd[e] : (double)s->sh[e]);",
+     "acc += Y[k] * (double)s->sh[e];", 0),
     # App. A: densification and pruning
     ("densify: children keep the parent's scale", "for (int k = 0; k < 3; ++k) log_scales[3 * o + k] -= shrink;",
      "", 0),
