@@ -100,7 +100,14 @@ typedef struct fs4d_scene_desc {
                                   R_a/R_b the resolutions of the plane's first/second axis */
   int32_t mlp_width;           /* hidden width W; this build supports 64 */
   const float* mlp;            /* layers d1 (W x h*L), d2 (W x W), x1, x2 (3 x W), r1, r2 (4 x W),
-                                  s1, s2 (3 x W); each weight [out][in] then bias [out] */
+                                  s1, s2 (3 x W), and with color_heads c1 (W x W), c2 (3K x W),
+                                  a1 (W x W), a2 (1 x W); each weight [out][in] then bias [out] */
+  int32_t color_heads;         /* 0, or 1: the colour and opacity heads of App. B, applied in
+                                  every frame: C' = C + phi_C(f_d) over the [K][3] SH
+                                  coefficients, logit' = logit + phi_alpha(f_d) (f_d the output of
+                                  phi_d).  Such scenes render (fs4d_render*, composition) but have
+                                  no backward, trainer or serving (FS4D_ERR_UNIMPLEMENTED), and
+                                  fs4d_deform returns only X', r', s'. */
 } fs4d_scene_desc;
 
 /* Pinhole camera.  world_to_cam maps world to camera coordinates (x right,
@@ -175,14 +182,15 @@ FS4D_API fs4d_status fs4d_update_scene(fs4d_ctx* ctx, fs4d_scene_id id, const fs
  * to_device == 0, else DEVICE memory.  Synchronises the context's stream. */
 FS4D_API fs4d_status fs4d_read_scene(fs4d_ctx* ctx, fs4d_scene_id id, const fs4d_grads* out, int32_t to_device);
 /* Write the scene (sizes, box and current parameters) to a binary file: an
- * 8-byte magic "FS4DSCN1", ten int32 (n, sh_degree, n_levels, res_spatial[4],
- * res_time, feat_dim, mlp_width), the box (6 float32), the arrays means,
+ * 8-byte magic "FS4DSCN2", eleven int32 (n, sh_degree, n_levels, res_spatial[4],
+ * res_time, feat_dim, mlp_width, color_heads), the box (6 float32), the arrays means,
  * log_scales, quats, opacity_logits, sh, planes, mlp as little-endian float32,
  * and a 64-bit FNV-1a checksum of everything after the magic.  The file is
  * written under path + ".tmp" and renamed, so a reader never sees half a file. */
 FS4D_API fs4d_status fs4d_save_scene(fs4d_ctx* ctx, fs4d_scene_id id, const char* path);
 /* Load a file written by fs4d_save_scene as a new scene (FS4D_ERR_NOT_FOUND if it
- * cannot be opened, FS4D_ERR_INVALID_ARG if it is not a complete scene file). */
+ * cannot be opened, FS4D_ERR_INVALID_ARG if it is not a complete scene file).  Files
+ * with the magic "FS4DSCN1" (ten int32, no color_heads) load as scenes without them. */
 FS4D_API fs4d_status fs4d_load_scene_file(fs4d_ctx* ctx, const char* path, fs4d_scene_id* out);
 /* Bytes the scene holds resident on the device, and the per-frame work memory a
  * render at (width, height) needs with `pairs_per_gaussian` tile pairs per

@@ -3,6 +3,7 @@
 // binning (tile bitmap: mark -> tile scan -> extract; or key emission -> tile
 // scan -> stable pair sort on the tile bits) -> composite.  See include/fs4d.h
 // for the contract of every call.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -69,6 +70,8 @@ struct Scene {
   size_t planes_floats = 0, mlp_floats = 0;
   size_t resident = 0;
   bool bf16_ok = false;
+  bool color_heads = false;   // App. B colour and opacity heads, at float offset color_off of mlp
+  size_t color_off = 0;
   std::atomic<int> refs{0};   // serving requests in flight on this scene
   bool dying = false;         // being unloaded: no new serving launches
   // capacity-mode reservation
@@ -110,6 +113,9 @@ struct Work {
   DevBuf ts;
   DevBuf host_img;                         // device staging image of fs4d_render_host
   DevBuf grad_pair, gd, acts, wpartial;    // backward work memory
+  DevBuf fd, dsh, dop;                     // colour and opacity heads: f_d [n][64] (work order),
+                                           // deformed SH [n][48] and opacity logits [n]
+  int cap_color = 0;
   long long cap_pairs = 0;
   long long sort_parts_cap = 0;
   int cap_n = 0, cap_tiles = 0;
@@ -318,6 +324,14 @@ std::vector<SrcLayer> src_layers(int hin, int W, size_t* total) {
   return L;
 }
 
+// Floats of a scene's MLP array: the eight layers, and the colour and opacity heads.
+size_t mlp_floats_of(const fs4d_scene_desc& d) {
+  size_t total = 0;
+  src_layers(d.feat_dim * d.n_levels, d.mlp_width, &total);
+  if (d.color_heads) total += (size_t)color_layer_floats(3 * (d.sh_degree + 1) * (d.sh_degree + 1));
+  return total;
+}
+
 // FP32 kernel layout: every layer transposed, Wt[in][out] then b[out], each
 // block padded to a multiple of 4 floats.
 std::vector<float> transpose_mlp(const float* src, int hin, int W, MlpGeomT& mg) {
@@ -451,6 +465,18 @@ fs4d_status get_scene(fs4d_ctx* c, fs4d_scene_id id, Scene** out) {
 }
 
 // Grow the per-Gaussian / per-tile / per-pair work buffers.
+// Work memory of the colour and opacity heads for frames of up to n Gaussians
+// (allocated on the first frame of a scene with them; never during a capture).
+fs4d_status ensure_color(fs4d_ctx* c, Work& w, cudaStream_t stream, int n) {
+  if (w.cap_color >= n) return FS4D_OK;
+  FS4D_CUDA(c, cudaStreamSynchronize(stream));
+  FS4D_CUDA(c, ensure(w.fd, 4 * 64 * (size_t)n));
+  FS4D_CUDA(c, ensure(w.dsh, 4 * 48 * (size_t)n));
+  FS4D_CUDA(c, ensure(w.dop, 4 * (size_t)n));
+  w.cap_color = n;
+  return FS4D_OK;
+}
+
 fs4d_status ensure_work(fs4d_ctx* c, Work& w, cudaStream_t stream, int n, int n_tiles, long long pairs) {
   const bool bmp_ok = c->binning != FS4D_BINNING_SORT;
   const size_t bmp_need =
@@ -553,9 +579,23 @@ struct Env {
 
 Env env_of(fs4d_ctx* c) { return Env{c, &c->w, c->stream, P<uint32_t>(c->status), true}; }
 
+// Stage boundaries of a frame (0 start, 1 deformed, 2 projected, 3 depth-sorted,
+// 4 binned, 5 pair sort start, 6 pair-sorted, 7 composited): CUDA events when stage
+// timing is on, and NVTX ranges named after the stages for profilers (a no-op
+// unless a tool is attached).
 void mark(const Env& e, int i) {
+  static const char* const kRange[8] = {"fs4d:deform", "fs4d:project", "fs4d:depth_sort", "fs4d:binning", nullptr,
+                                        "fs4d:pair_sort", "fs4d:composite", nullptr};
+  if (i != 0 && i != 5) nvtxRangePop();
+  if (kRange[i]) nvtxRangePushA(kRange[i]);
   if (e.timed) mark(e.c, i);
 }
+
+// An NVTX range over one call of the library.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+};
 
 DeformArgs deform_args(Scene* s, const float* ts, float t0, int n_t, float* om, float* oq, float* os) {
   DeformArgs a{};
@@ -609,6 +649,30 @@ long long parts_total(const FramePart* parts, int n_parts) {
   return n;
 }
 
+// Eq. 5 + Sec. 4.2 + Eq. 6 for one part of a frame into the work arrays at its
+// offset, and for a scene with them the colour and opacity heads (App. B) on the
+// f_d the deformation leaves.
+fs4d_status deform_part(fs4d_ctx* c, Work& w, const FramePart& q, fs4d_precision prec, const float* d_t, float t,
+                        cudaStream_t stream, uint32_t* status) {
+  DeformArgs da = deform_args(q.s, d_t, t, 1, P<float>(w.dmeans) + 3 * q.off, P<float>(w.dquats) + 4 * q.off,
+                              P<float>(w.dscales) + 3 * q.off);
+  if (q.s->color_heads) da.fd_out = P<float>(w.fd) + 64 * q.off;
+  fs4d_status st = run_deform(c, q.s, prec, da, stream, status);
+  if (st != FS4D_OK || !q.s->color_heads) return st;
+  ColorArgs ca{};
+  ca.n = q.s->n;
+  ca.perm = P<uint32_t>(q.s->perm);
+  ca.fd = da.fd_out;
+  ca.weights = P<float>(q.s->mlp) + q.s->color_off;
+  ca.k3 = 3 * q.s->K;
+  ca.sh = P<float>(q.s->sh);
+  ca.logits = P<float>(q.s->opacity_logits);
+  ca.sh_out = P<float>(w.dsh) + 48 * q.off;
+  ca.logit_out = P<float>(w.dop) + q.off;
+  FS4D_CUDA(c, launch_color_heads(ca, stream));
+  return FS4D_OK;
+}
+
 // Everything of a frame up to (and including) the key emission, over the union of
 // the parts' Gaussians.
 // cull: the tile lists may leave out Gaussians that no pixel of the tile blends
@@ -628,12 +692,12 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
   if (z.bytes > w.zero.bytes) return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory was not reserved");
   mark(e, 0);
   FS4D_CUDA(c, cudaMemsetAsync(w.zero.p, 0, z.bytes, stream));
+  for (int i = 0; i < n_parts; ++i)
+    if (parts[i].s->color_heads && w.cap_color < N)
+      return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory of the colour heads was not reserved");
   if (deform) {
     for (int i = 0; i < n_parts; ++i) {
-      const FramePart& q = parts[i];
-      DeformArgs da = deform_args(q.s, d_t, t, 1, P<float>(w.dmeans) + 3 * q.off, P<float>(w.dquats) + 4 * q.off,
-                                  P<float>(w.dscales) + 3 * q.off);
-      fs4d_status st = run_deform(c, q.s, prec, da, stream, e.status);
+      fs4d_status st = deform_part(c, w, parts[i], prec, d_t, t, stream, e.status);
       if (st != FS4D_OK) return st;
     }
   }
@@ -646,6 +710,10 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
     pa.means = P<float>(w.dmeans) + 3 * q.off; pa.quats = P<float>(w.dquats) + 4 * q.off;
     pa.log_scales = P<float>(w.dscales) + 3 * q.off;
     pa.opacity_logits = P<float>(s->opacity_logits); pa.sh = P<float>(s->sh); pa.sh_degree = s->sh_degree;
+    if (s->color_heads) {  // App. B: this frame's deformed colour and opacity
+      pa.opacity_logits = P<float>(w.dop) + q.off;
+      pa.sh = P<float>(w.dsh) + 48 * q.off;
+    }
     pa.cam = cam_params(shape);
     if (e.guard_w > 0) {
       pa.cam.guard_w = e.guard_w;
@@ -877,14 +945,15 @@ fs4d_status render_sync(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_c
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   fs4d_status st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs);
   if (st != FS4D_OK) return st;
+  if (s->color_heads && (st = ensure_color(c, c->w, c->stream, s->n)) != FS4D_OK) return st;
   std::fill(c->stage_acc, c->stage_acc + 6, 0.f);
   c->stage_acc_valid = false;
   c->last_bands = 1;
   if (!offsets && c->band_hint > 1 && c->band_scene == s->id && c->band_w == cam->width && c->band_h == cam->height) {
     // the last frame of this scene and size needed bands: deform, then bands straight away
     mark(c, 0);
-    DeformArgs da = deform_args(s, nullptr, t, 1, P<float>(c->w.dmeans), P<float>(c->w.dquats), P<float>(c->w.dscales));
-    if ((st = run_deform(c, s, prec, da)) != FS4D_OK) return st;
+    const FramePart part{s, 0, {0.f, 0.f, 0.f}};
+    if ((st = deform_part(c, c->w, part, prec, nullptr, t, c->stream, P<uint32_t>(c->status))) != FS4D_OK) return st;
     mark(c, 1);
     if (c->timing) {
       FS4D_CUDA(c, cudaEventSynchronize(c->ev[1]));
@@ -1050,6 +1119,8 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
   for (int a = 0; a < 3; ++a)
     if (!(d->aabb_max[a] > d->aabb_min[a])) return fail(c, FS4D_ERR_INVALID_ARG, "scene: empty bounding box");
   if (d->mlp_width != kWidth) return fail(c, FS4D_ERR_UNIMPLEMENTED, "scene: only MLP width 64 is supported");
+  if (d->color_heads != 0 && d->color_heads != 1)
+    return fail(c, FS4D_ERR_INVALID_ARG, "scene: color_heads is 0 or 1");
   if (!deform_fp32_supported(d->feat_dim, d->n_levels))
     return fail(c, FS4D_ERR_UNIMPLEMENTED, "scene: feat_dim must be 16 or 32 with 1..3 levels");
   DeviceGuard g(c->device);
@@ -1068,6 +1139,9 @@ fs4d_status fs4d_load_scene(fs4d_ctx* c, const fs4d_scene_desc* d, fs4d_scene_id
   const int hin = d->feat_dim * d->n_levels;
   size_t mlp_total;
   src_layers(hin, d->mlp_width, &mlp_total);
+  s->color_off = mlp_total;  // the colour and opacity heads follow the eight layers
+  s->color_heads = d->color_heads != 0;
+  mlp_total = mlp_floats_of(*d);
   s->mlp_floats = mlp_total;
   fs4d_status st;
   auto bail = [&](fs4d_status e) { free_scene(s); return e; };
@@ -1244,6 +1318,8 @@ fs4d_status fs4d_render_composed(fs4d_ctx* c, const fs4d_scene_id* ids, const fl
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   fs4d_status st = ensure_work(c, (int)N, n_tiles, c->w.cap_pairs);
   if (st != FS4D_OK) return st;
+  for (const FramePart& q : parts)
+    if (q.s->color_heads && (st = ensure_color(c, c->w, c->stream, (int)N)) != FS4D_OK) return st;
   c->stage_acc_valid = false;
   st = frame_front(env_of(c), parts.data(), n_scenes, prec, *cam, nullptr, nullptr, t, c->w.cap_pairs, false, true,
                    false, !d_n_contrib);
@@ -1282,6 +1358,7 @@ fs4d_status fs4d_render_host(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec,
   // with the capacity grown.
   const int n_tiles = tiles_of(cam->width) * tiles_of(cam->height);
   if ((st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs)) != FS4D_OK) return st;
+  if (s->color_heads && (st = ensure_color(c, c->w, c->stream, s->n)) != FS4D_OK) return st;
   const long long cap = c->w.cap_pairs;
   if ((st = frame_front(c, s, prec, *cam, nullptr, nullptr, t, cap, false, false, true)) != FS4D_OK) return st;
   if ((st = frame_back(c, *cam, cap, P<float>(img), nullptr, nullptr)) != FS4D_OK) return st;
@@ -1333,6 +1410,7 @@ fs4d_status fs4d_render_host_batch(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision
   }
   const int n_tiles = tiles_of(cams[0].width) * tiles_of(cams[0].height);
   if ((st = ensure_work(c, s->n, n_tiles, c->w.cap_pairs)) != FS4D_OK) return st;
+  if (s->color_heads && (st = ensure_color(c, c->w, c->stream, s->n)) != FS4D_OK) return st;
   const long long cap = c->w.cap_pairs;
   float* slot_img[2] = {P<float>(img), P<float>(img) + bytes / 4};
   for (int k = 0; k < n; ++k) {
@@ -1372,6 +1450,7 @@ fs4d_status fs4d_reserve(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32_t h
   if (st != FS4D_OK) return st;
   DeviceGuard g(c->device);
   st = ensure_work(c, s->n, tiles_of(width) * tiles_of(height), pair_capacity);
+  if (st == FS4D_OK && s->color_heads) st = ensure_color(c, c->w, c->stream, s->n);
   if (st != FS4D_OK) return st;
   s->reserved_pairs = pair_capacity;
   s->reserved_w = width;
@@ -1433,6 +1512,7 @@ fs4d_status fs4d_backward_times(fs4d_ctx* c, float* h_ms) {
 
 static fs4d_status backward_impl(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_dimage, const fs4d_grads* gr,
                                  const fs4d_view_stats* stats) {
+  NvtxScope nvtx_scope("fs4d:backward");
   if (!c) return FS4D_ERR_INVALID_ARG;
   if (!f || !d_dl_dimage || !gr) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: frame, dL/dI, grads needed");
   if (stats && (!stats->grad_norm_sum || !stats->visible))
@@ -1440,6 +1520,8 @@ static fs4d_status backward_impl(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   Scene* s;
   fs4d_status st = get_scene(c, f->scene, &s);
   if (st != FS4D_OK) return st;
+  if (s->color_heads)
+    return fail(c, FS4D_ERR_UNIMPLEMENTED, "render_backward: no backward through the colour and opacity heads");
   if (s->n != f->n) return fail(c, FS4D_ERR_INVALID_ARG, "render_backward: the scene changed size since the frame");
   DeviceGuard g(c->device);
   Work& w = c->w;
@@ -1561,7 +1643,7 @@ fs4d_status fs4d_update_scene(fs4d_ctx* c, fs4d_scene_id id, const fs4d_scene_de
   fs4d_status st = get_scene(c, id, &s);
   if (st != FS4D_OK) return st;
   if (d->n != s->n || d->sh_degree != s->sh_degree || d->n_levels != s->pg.n_levels || d->feat_dim != s->pg.feat_dim ||
-      d->res_time != s->pg.res_time || d->mlp_width != kWidth)
+      d->res_time != s->pg.res_time || d->mlp_width != kWidth || (d->color_heads != 0) != s->color_heads)
     return fail(c, FS4D_ERR_INVALID_ARG, "update_scene: shapes must match the loaded scene");
   DeviceGuard g(c->device);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -2002,15 +2084,17 @@ void admit_and_launch(fs4d_server* sv) {
     if (sv->pending.empty()) return;
     const fs4d_scene_id sid = sv->pending.front().r.scene;
     const fs4d_precision prec = sv->pending.front().r.prec;
+    bool unsupported = false;
     {
       std::lock_guard<std::mutex> cl(c->mu);
       auto it = c->scenes.find(sid);
-      if (it != c->scenes.end() && !it->second->dying) {
+      if (it != c->scenes.end() && !it->second->dying && !it->second->color_heads) {
         scene = it->second;
         scene->refs++;  // provisional: keeps the scene alive while the batch forms
       }
+      unsupported = it != c->scenes.end() && it->second->color_heads;
     }
-    if (!scene) {  // unknown or unloaded scene: fail every queued request on it
+    if (!scene) {  // unknown, unloaded or unsupported scene: fail every queued request on it
       std::deque<SReq> keep;
       std::vector<SReq> bad;
       for (SReq& q : sv->pending) {
@@ -2021,7 +2105,8 @@ void admit_and_launch(fs4d_server* sv) {
       }
       sv->pending.swap(keep);
       lock.unlock();
-      for (SReq& q : bad) complete(sv, q, FS4D_ERR_NOT_FOUND, -1, 0, sv->now());
+      // the batched deformation of the server does not run the colour and opacity heads
+      for (SReq& q : bad) complete(sv, q, unsupported ? FS4D_ERR_UNIMPLEMENTED : FS4D_ERR_NOT_FOUND, -1, 0, sv->now());
       return;
     }
     std::vector<bool> taken(sv->slots.size(), false);
@@ -2383,6 +2468,8 @@ fs4d_status fs4d_train_create(fs4d_ctx* c, fs4d_scene_id id, const fs4d_train_co
   Scene* s;
   fs4d_status st = get_scene(c, id, &s);
   if (st != FS4D_OK) return st;
+  if (s->color_heads)
+    return fail(c, FS4D_ERR_UNIMPLEMENTED, "train_create: no backward through the colour and opacity heads");
   DeviceGuard g(c->device);
   fs4d_trainer* tr = new (std::nothrow) fs4d_trainer();
   if (!tr) return fail(c, FS4D_ERR_OOM, "train_create: allocation failed");
@@ -2417,6 +2504,7 @@ fs4d_status fs4d_train_create(fs4d_ctx* c, fs4d_scene_id id, const fs4d_train_co
 
 fs4d_status fs4d_train_step(fs4d_trainer* tr, fs4d_precision prec, const fs4d_camera* cam, float t,
                             const float* d_target, float* d_losses) {
+  NvtxScope nvtx_scope("fs4d:train_step");
   if (!tr) return FS4D_ERR_INVALID_ARG;
   fs4d_ctx* c = tr->c;
   if (!valid_cam(cam) || !d_target) return fail(c, FS4D_ERR_INVALID_ARG, "train_step: camera and target required");
@@ -2536,6 +2624,7 @@ fs4d_status fs4d_train_stats(fs4d_trainer* tr, const fs4d_view_stats* out) {
 
 fs4d_status fs4d_densify(fs4d_ctx* c, fs4d_scene_id id, const fs4d_densify_config* cfg, const fs4d_view_stats* vs,
                          const float* d_normals, fs4d_trainer* tr, int64_t* n_out) {
+  NvtxScope nvtx_scope("fs4d:densify");
   if (!c) return FS4D_ERR_INVALID_ARG;
   if (!cfg || !vs || !vs->grad_norm_sum || !vs->visible || !d_normals || !n_out)
     return fail(c, FS4D_ERR_INVALID_ARG, "densify: config, statistics, normals and output required");
@@ -2725,7 +2814,8 @@ fs4d_status fs4d_train_densify(fs4d_trainer* tr, const fs4d_densify_config* cfg,
 
 // ============================================================== scene read-back and files
 namespace {
-constexpr char kSceneMagic[8] = {'F', 'S', '4', 'D', 'S', 'C', 'N', '1'};
+constexpr char kSceneMagic[8] = {'F', 'S', '4', 'D', 'S', 'C', 'N', '2'};    // 11 int32
+constexpr char kSceneMagicV1[8] = {'F', 'S', '4', 'D', 'S', 'C', 'N', '1'};  // 10 int32, no color_heads
 
 uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
   const unsigned char* b = static_cast<const unsigned char*>(p);
@@ -2779,8 +2869,8 @@ fs4d_status fs4d_save_scene(fs4d_ctx* c, fs4d_scene_id id, const char* path) {
                  host[6].data()};
   if ((st = fs4d_read_scene(c, id, &out, 0)) != FS4D_OK) return st;
   const fs4d_scene_desc& d = s->shape;
-  const int32_t ints[10] = {d.n, d.sh_degree, d.n_levels, d.res_spatial[0], d.res_spatial[1], d.res_spatial[2],
-                            d.res_spatial[3], d.res_time, d.feat_dim, d.mlp_width};
+  const int32_t ints[11] = {d.n, d.sh_degree, d.n_levels, d.res_spatial[0], d.res_spatial[1], d.res_spatial[2],
+                            d.res_spatial[3], d.res_time, d.feat_dim, d.mlp_width, d.color_heads};
   const std::string tmp = std::string(path) + ".tmp";
   FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return fail(c, FS4D_ERR_INVALID_ARG, "save_scene: cannot open " + tmp);
@@ -2809,28 +2899,30 @@ fs4d_status fs4d_load_scene_file(fs4d_ctx* c, const char* path, fs4d_scene_id* o
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(c, FS4D_ERR_NOT_FOUND, std::string("load_scene_file: cannot open ") + path);
   char magic[8];
-  int32_t ints[10];
+  int32_t ints[11] = {};
   fs4d_scene_desc d{};
   uint64_t h = 14695981039346656037ull;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSceneMagic, 8) == 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8;
+  const bool v1 = ok && std::memcmp(magic, kSceneMagicV1, 8) == 0;
+  ok = ok && (v1 || std::memcmp(magic, kSceneMagic, 8) == 0);
   auto get = [&](void* p, size_t bytes) {
     ok = ok && std::fread(p, 1, bytes, f) == bytes;
     if (ok) h = fnv1a(h, p, bytes);
   };
-  get(ints, sizeof(ints));
+  get(ints, v1 ? 10 * sizeof(int32_t) : sizeof(ints));
   get(d.aabb_min, sizeof(d.aabb_min));
   get(d.aabb_max, sizeof(d.aabb_max));
   d.n = ints[0]; d.sh_degree = ints[1]; d.n_levels = ints[2];
   for (int l = 0; l < 4; ++l) d.res_spatial[l] = ints[3 + l];
-  d.res_time = ints[7]; d.feat_dim = ints[8]; d.mlp_width = ints[9];
+  d.res_time = ints[7]; d.feat_dim = ints[8]; d.mlp_width = ints[9]; d.color_heads = ints[10];
   ok = ok && d.n >= 1 && d.sh_degree >= 0 && d.sh_degree <= 3 && d.n_levels >= 1 && d.n_levels <= kMaxLevels &&
-       d.feat_dim > 0 && d.res_time >= 2 && d.mlp_width == kWidth;
+       d.feat_dim > 0 && d.res_time >= 2 && d.mlp_width == kWidth && (d.color_heads == 0 || d.color_heads == 1);
   std::vector<std::vector<float>> host(7);
   if (ok) {
     PlaneGeom pg{};
     size_t planes_total = 0, mlp_total = 0;
     plane_geom(d, pg, planes_total);
-    src_layers(d.feat_dim * d.n_levels, d.mlp_width, &mlp_total);
+    mlp_total = mlp_floats_of(d);
     const size_t n = (size_t)d.n, K = (size_t)(d.sh_degree + 1) * (d.sh_degree + 1);
     const size_t cnt[7] = {3 * n, 3 * n, 4 * n, n, 3 * n * K, planes_total, mlp_total};
     for (int k = 0; k < 7 && ok; ++k) {

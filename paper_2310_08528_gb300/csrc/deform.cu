@@ -183,6 +183,12 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
     __syncthreads();
     store_relu(X, g4, o8, acc);
     __syncthreads();
+    if (a.fd_out) {  // f_d for the colour and opacity heads, rows in work order
+      for (int e = threadIdx.x; e < kTileG * kWidth; e += kThreads) {
+        const int r = e / kWidth, k = e - r * kWidth;
+        if (base + r < total) a.fd_out[(size_t)(base + r) * kWidth + k] = X[k * kGS + r];
+      }
+    }
     // heads phi_x, phi_r, phi_s: hidden layer into Hd, output layer into D
     layer64<kWidth>(sw + mg.w[2], sw + mg.b[2], X, g4, o8, acc);
     store_relu(Hd, g4, o8, acc);

@@ -315,6 +315,14 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
       float v[32];
       tmem_ld32(tmem + lane_base + 64u + (uint32_t)(half * 32), v);
       store_relu32(sX, row, half * 32, 64, v, sBias + 64 + half * 32);
+      if (a.fd_out && base + row < total) {  // f_d for the colour and opacity heads, work order
+        float4* dst = reinterpret_cast<float4*>(a.fd_out + (size_t)(base + row) * 64 + half * 32);
+        const float* b = sBias + 64 + half * 32;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          dst[j] = make_float4(fmaxf(v[4 * j] + b[4 * j], 0.f), fmaxf(v[4 * j + 1] + b[4 * j + 1], 0.f),
+                               fmaxf(v[4 * j + 2] + b[4 * j + 2], 0.f), fmaxf(v[4 * j + 3] + b[4 * j + 3], 0.f));
+      }
     }
     tc_fence_before();
     fence_async_smem();

@@ -137,7 +137,23 @@ struct DeformArgs {
   MlpGeomTC tg;
   PlaneGeom pg;
   uint32_t* status;
+  float* fd_out;                // optional [n][64]: f_d (after phi_d) in work order (n_t must be 1)
 };
+
+// Colour and opacity heads (App. B, color.cu): per Gaussian from f_d in work order.
+struct ColorArgs {
+  int n;
+  const uint32_t* perm;         // work order (NULL: index order)
+  const float* fd;              // [n][64] work order, 16-byte aligned
+  const float* weights;         // the four layers c1 c2 a1 a2 in the source layout (W[out][in] then b)
+  int k3;                       // 3 x SH coefficients per channel
+  const float* sh;              // [n][K][3] canonical
+  const float* logits;          // [n] canonical
+  float* sh_out;                // [n][K][3] deformed
+  float* logit_out;             // [n] deformed
+};
+int color_layer_floats(int k3);
+cudaError_t launch_color_heads(const ColorArgs& a, cudaStream_t s);
 
 struct CamParams {
   int width, height;

@@ -46,7 +46,8 @@ class SceneDesc(C.Structure):
                 ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("sh", C.c_void_p),
                 ("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3), ("n_levels", C.c_int32),
                 ("res_spatial", C.c_int32 * 4), ("res_time", C.c_int32), ("feat_dim", C.c_int32),
-                ("planes", C.c_void_p), ("mlp_width", C.c_int32), ("mlp", C.c_void_p)]
+                ("planes", C.c_void_p), ("mlp_width", C.c_int32), ("mlp", C.c_void_p),
+                ("color_heads", C.c_int32)]
 
 
 class Camera(C.Structure):
@@ -244,6 +245,7 @@ class Context:
         d.n_levels = len(rs)
         d.res_spatial = (C.c_int32 * 4)(*(rs + [0] * (4 - len(rs))))
         d.res_time, d.feat_dim, d.mlp_width = int(scene.res_time), int(scene.feat_dim), int(scene.mlp_width)
+        d.color_heads = int(bool(getattr(scene, "color_heads", False)))
         sid = C.c_int32()
         self.call("fs4d_load_scene", C.byref(d), C.byref(sid))
         self._scenes[sid.value] = scene
@@ -390,6 +392,7 @@ class Context:
         d.aabb_min = (C.c_float * 3)(*map(float, scene.aabb_min))
         d.aabb_max = (C.c_float * 3)(*map(float, scene.aabb_max))
         d.res_time, d.feat_dim, d.mlp_width = int(scene.res_time), int(scene.feat_dim), int(scene.mlp_width)
+        d.color_heads = int(bool(getattr(scene, "color_heads", False)))
         self.call("fs4d_update_scene", sid, C.byref(d), 1)
         del keep
 
