@@ -1535,10 +1535,10 @@ static fs4d_status backward_impl(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
     wtot = (size_t)tot_floats;  // every layer's O*I + O entries
   }
   const size_t wp = (size_t)wgrad_chunks(n) * wtot;
-  if (w.grad_pair.bytes < 4 * kPairGrad * (size_t)std::max(K, 1ll) || w.gd.bytes < 40 * (size_t)n ||
+  if (w.grad_pair.bytes < 4 * kPairStride * (size_t)std::max(K, 1ll) || w.gd.bytes < 40 * (size_t)n ||
       w.acts.bytes < 4 * act_floats || w.wpartial.bytes < 4 * wp) {
     FS4D_CUDA(c, cudaStreamSynchronize(c->stream));
-    FS4D_CUDA(c, ensure(w.grad_pair, 4 * kPairGrad * (size_t)std::max(K, 1ll)));
+    FS4D_CUDA(c, ensure(w.grad_pair, 4 * kPairStride * (size_t)std::max(K, 1ll)));
     FS4D_CUDA(c, ensure(w.gd, 40 * (size_t)n));
     FS4D_CUDA(c, ensure(w.acts, 4 * act_floats));
     FS4D_CUDA(c, ensure(w.wpartial, 4 * wp));
@@ -1549,7 +1549,7 @@ static fs4d_status backward_impl(fs4d_ctx* c, fs4d_frame* f, const float* d_dl_d
   };
   bmark(0);
   // 1. compositing backward into per-pair slots
-  FS4D_CUDA(c, cudaMemsetAsync(w.grad_pair.p, 0, 4 * kPairGrad * (size_t)std::max(K, 1ll), c->stream));
+  FS4D_CUDA(c, cudaMemsetAsync(w.grad_pair.p, 0, 4 * kPairStride * (size_t)std::max(K, 1ll), c->stream));
   CompositeBwdArgs cb{};
   cb.width = f->cam.width; cb.height = f->cam.height; cb.tiles_x = tx;
   cb.ranges = P<uint2>(f->ranges); cb.values = P<uint32_t>(f->values);

@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
     }
     __syncthreads();
     if ((int)threadIdx.x < jend && bstart + (int)threadIdx.x < n) {
-      float* dst = a.grad_pair + (size_t)s_slot[threadIdx.x] * kPairGrad;
-#pragma unroll
-      for (int k = 0; k < kPairGrad; ++k) dst[k] = s_acc[threadIdx.x][k];
+      float4* dst = reinterpret_cast<float4*>(a.grad_pair + (size_t)s_slot[threadIdx.x] * kPairStride);
+      const float* v = s_acc[threadIdx.x];
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+      dst[2] = make_float4(v[8], 0.f, 0.f, 0.f);
     }
   }
 }
@@ -184,6 +186,60 @@ __device__ void sh_basis_and_grad(int deg, float x, float y, float z, float* Y, 
   Y[15] = kY33 * x * (xx - 3.f * yy); dY[15][0] = kY33 * (3.f * xx - 3.f * yy); dY[15][1] = -6.f * kY33 * x * y;
 }
 
+// The SH colour's backward for one Gaussian with K coefficients per channel: the
+// row of 3K coefficients read once (128-bit loads where the rows are 16-byte
+// aligned: K = 4, 16), dL/dSH accumulated into g_sh with the same access width,
+// and the gradient with respect to the view direction.
+template <int K>
+__device__ __forceinline__ void sh_colour_bwd(const ProjectBwdArgs& a, int g, const float (&Y)[16],
+                                              const float (&dY)[16][3], const float (&G9)[kPairGrad],
+                                              float& gdir0, float& gdir1, float& gdir2) {
+  constexpr int F = 3 * K;
+  constexpr bool kVec = (F % 4) == 0;
+  float shv[F];
+  const float* row = a.sh + (size_t)g * F;
+  if (kVec) {
+#pragma unroll
+    for (int i = 0; i < F / 4; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(row)[i];
+      shv[4 * i] = v.x; shv[4 * i + 1] = v.y; shv[4 * i + 2] = v.z; shv[4 * i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < F; ++i) shv[i] = row[i];
+  }
+  float gsh[F];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float raw = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) raw += Y[k] * shv[3 * k + ch];
+    const bool live = raw > 0.f;  // clamped at 0: no gradient
+    const float gr = live ? G9[6 + ch] : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      gsh[3 * k + ch] = gr * Y[k];
+      const float s = gr * shv[3 * k + ch];
+      gdir0 += s * dY[k][0];
+      gdir1 += s * dY[k][1];
+      gdir2 += s * dY[k][2];
+    }
+  }
+  if (!a.g_sh) return;
+  float* out = a.g_sh + (size_t)g * F;
+  if (kVec) {
+#pragma unroll
+    for (int i = 0; i < F / 4; ++i) {
+      float4 v = reinterpret_cast<float4*>(out)[i];
+      v.x += gsh[4 * i]; v.y += gsh[4 * i + 1]; v.z += gsh[4 * i + 2]; v.w += gsh[4 * i + 3];
+      reinterpret_cast<float4*>(out)[i] = v;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < F; ++i) out[i] += gsh[i];
+  }
+}
+
 __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.n) return;
@@ -200,9 +256,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
 #pragma unroll
   for (int k = 0; k < kPairGrad; ++k) G9[k] = 0.f;
   for (uint32_t e = 0; e < cnt; ++e) {
-    const float* src = a.grad_pair + (size_t)(e0 + e) * kPairGrad;
-#pragma unroll
-    for (int k = 0; k < kPairGrad; ++k) G9[k] += src[k];
+    const float4* src = reinterpret_cast<const float4*>(a.grad_pair + (size_t)(e0 + e) * kPairStride);
+    const float4 u = src[0], w = src[1];
+    const float z = src[2].x;
+    G9[0] += u.x; G9[1] += u.y; G9[2] += u.z; G9[3] += u.w;
+    G9[4] += w.x; G9[5] += w.y; G9[6] += w.z; G9[7] += w.w;
+    G9[8] += z;
   }
   if (a.stat_grad) {  // densification statistics: view-space gradient norm of the visible Gaussian
     a.stat_grad[g] += sqrtf(G9[0] * G9[0] + G9[1] * G9[1]);
@@ -224,21 +283,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a) {
     const float dx = vx * vinv, dy = vy * vinv, dz = vz * vinv;
     float Y[16], dY[16][3];
     sh_basis_and_grad(a.sh_degree, dx, dy, dz, Y, dY);
-    const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
-    const float* sh = a.sh + (size_t)g * K * 3;
     float gdir0 = 0.f, gdir1 = 0.f, gdir2 = 0.f;
-    for (int ch = 0; ch < 3; ++ch) {
-      float raw = 0.5f;
-      for (int k = 0; k < K; ++k) raw += Y[k] * sh[3 * k + ch];
-      if (!(raw > 0.f)) continue;
-      const float gr = G9[6 + ch];
-      for (int k = 0; k < K; ++k) {
-        if (a.g_sh) a.g_sh[((size_t)g * K + k) * 3 + ch] += gr * Y[k];
-        const float s = gr * sh[3 * k + ch];
-        gdir0 += s * dY[k][0];
-        gdir1 += s * dY[k][1];
-        gdir2 += s * dY[k][2];
-      }
+    switch (a.sh_degree) {
+      case 0: sh_colour_bwd<1>(a, g, Y, dY, G9, gdir0, gdir1, gdir2); break;
+      case 1: sh_colour_bwd<4>(a, g, Y, dY, G9, gdir0, gdir1, gdir2); break;
+      case 2: sh_colour_bwd<9>(a, g, Y, dY, G9, gdir0, gdir1, gdir2); break;
+      default: sh_colour_bwd<16>(a, g, Y, dY, G9, gdir0, gdir1, gdir2); break;
     }
     const float dd = dx * gdir0 + dy * gdir1 + dz * gdir2;
     gX0 += (gdir0 - dx * dd) * vinv;

@@ -328,6 +328,7 @@ cudaError_t launch_derive(const float* planes, long long n_planes, __nv_bfloat16
 namespace fs4d {
 
 constexpr int kPairGrad = 9;  // per (tile, Gaussian) pair: du dv dconic(a b c) dopacity drgb(3)
+constexpr int kPairStride = 12;  // floats per pair slot in memory (16-byte aligned rows)
 
 struct CompositeBwdArgs {
   int width, height, tiles_x;
@@ -341,7 +342,7 @@ struct CompositeBwdArgs {
   const float* t_final;
   const int* n_contrib;
   const float* dl_dimage;   // [H][W][3]
-  float* grad_pair;         // [K][9], indexed by emission slot; zeroed by the caller
+  float* grad_pair;         // [K][kPairStride] (9 used), indexed by emission slot; zeroed by the caller
 };
 
 struct ProjectBwdArgs {
