@@ -35,11 +35,34 @@ constexpr float kGuard = 1.3f;
 
 // ------------------------------------------------------------------ compositing
 
+// Bit w set iff some pixel centre of the 16x2 pixel rows (2w, 2w + 1) of tile
+// (tx, ty) -- warp w's pixels -- may reach alpha >= 1/255 (the rectangle minimum of
+// d^T K d against -2 thr with a 0.2% + 1e-3 margin, as the forward's block masks):
+// a warp skips, as a whole, the terms whose bit is clear, which no lane of it blends.
+__device__ __forceinline__ uint32_t row_pair_mask(float2 p, float4 co, int tx, int ty) {
+  const float thr = composite_exp_threshold(co.w);
+  if (!(thr < 0.f)) return 0u;
+  const float A = co.x, B = co.y, C = co.z;
+  if (!(A > 0.f && C > 0.f && A * C - B * B > 0.f)) return 0xffu;
+  const float s = -2.f * thr * 1.002f + 1e-3f;
+  const float kx = -B / C, ky = -B / A;
+  const float X0 = (float)(tx * kTile) + 0.5f - p.x, X1 = X0 + (float)(kTile - 1);
+  const float Y0 = (float)(ty * kTile) + 0.5f - p.y;
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int w = 0; w < kBatch / 32; ++w) {
+    const float y0 = Y0 + 2.f * (float)w;
+    if (rect_min(A, B, C, kx, ky, X0, X1, y0, y0 + 1.f) <= s) mask |= 1u << w;
+  }
+  return mask;
+}
+
 __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs a) {
   __shared__ float2 s_xy[kBatch];
   __shared__ float4 s_co[kBatch];
   __shared__ float s_rgb[3 * kBatch];
   __shared__ uint32_t s_slot[kBatch];
+  __shared__ uint32_t s_mask[kBatch];
   __shared__ float s_acc[kBatch][kPairGrad];
   __shared__ int s_max_last;
   const int tile = blockIdx.x;
@@ -79,12 +102,15 @@ __global__ void __launch_bounds__(kBatch) composite_bwd_kernel(CompositeBwdArgs 
       s_rgb[3 * threadIdx.x + 2] = a.rgb[3 * g + 2];
       const int4 r = a.rect[g];
       s_slot[threadIdx.x] = a.offsets[g] + (uint32_t)((ty - r.y) * (r.z - r.x) + (tx - r.x));
+      s_mask[threadIdx.x] = row_pair_mask(s_xy[threadIdx.x], cog, tx, ty);
     }
 #pragma unroll
     for (int k = 0; k < kPairGrad; ++k) s_acc[threadIdx.x][k] = 0.f;
     __syncthreads();
     const int jend = min(kBatch, max_last - bstart);
+    const unsigned warp_bit = 1u << (threadIdx.x >> 5);
     for (int jj = jend - 1; jj >= 0; --jj) {
+      if (!(s_mask[jj] & warp_bit)) continue;  // warp-uniform: no pixel of this warp blends term jj
       float gr[kPairGrad];
 #pragma unroll
       for (int k = 0; k < kPairGrad; ++k) gr[k] = 0.f;
