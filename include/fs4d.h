@@ -55,7 +55,8 @@ typedef enum fs4d_status {
   FS4D_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (status word set) */
   FS4D_ERR_NOT_FOUND = 6,     /* unknown scene id or frame */
   FS4D_ERR_UNIMPLEMENTED = 7, /* a shape this build does not support (message says which) */
-  FS4D_ERR_CANCELLED = 8      /* a queued serving request was cancelled or its server stopped */
+  FS4D_ERR_CANCELLED = 8,     /* a queued serving request was cancelled or its server stopped */
+  FS4D_ERR_CORRUPT = 9        /* a canary word after a device buffer was overwritten (debug build) */
 } fs4d_status;
 
 typedef enum fs4d_precision {
@@ -158,6 +159,16 @@ FS4D_API fs4d_status fs4d_set_stream(fs4d_ctx* ctx, void* cuda_stream);
  * wait timed out has an unreliable image; the context stays usable and the next
  * frame is computed afresh. */
 FS4D_API fs4d_status fs4d_check_device_status(fs4d_ctx* ctx);
+/* Debug build (compiled with FS4D_CHECK_BOUNDS: libfs4d_debug.so): every device
+ * buffer the library allocates carries 256 canary bytes (0xA5) after its end.
+ * fs4d_check_canaries synchronises the device and checks them all (every context
+ * of the process): FS4D_OK, or FS4D_ERR_CORRUPT naming the first buffer whose
+ * canary was overwritten -- a kernel wrote past the end of it.  The release build
+ * returns FS4D_ERR_UNIMPLEMENTED.  fs4d_debug_corrupt_canary overwrites one canary
+ * byte of the most recently allocated buffer (a test of the check itself; release
+ * build: FS4D_ERR_UNIMPLEMENTED). */
+FS4D_API fs4d_status fs4d_check_canaries(fs4d_ctx* ctx);
+FS4D_API fs4d_status fs4d_debug_corrupt_canary(fs4d_ctx* ctx);
 /* Polls a look-back wait (radix sort, key emission) of this context's later
  * launches makes before it gives up and sets the timeout bit of the status word;
  * 0 restores the default (2^22 polls of ~100 ns).  A diagnostic for exercising
@@ -266,7 +277,10 @@ FS4D_API fs4d_status fs4d_render_async(fs4d_ctx* ctx, fs4d_scene_id id, fs4d_pre
 FS4D_API fs4d_status fs4d_render_backward(fs4d_ctx* ctx, fs4d_frame* saved, const float* d_dl_dimage,
                                  const fs4d_grads* d_grads);
 FS4D_API fs4d_status fs4d_frame_free(fs4d_ctx* ctx, fs4d_frame* frame);
-/* Number of tile pairs K of a saved frame, and of the last render on the context. */
+/* Number of tile pairs K of a saved frame, and of the last render on the context:
+ * the pairs of the Gaussians' tile rectangles (frames of the tile bitmap binning that
+ * report no list positions list a Gaussian only in the tiles its ellipse
+ * {alpha >= 1/255} reaches, which leaves the image unchanged and their lists shorter). */
 FS4D_API fs4d_status fs4d_frame_pairs(const fs4d_frame* frame, int64_t* pairs);
 FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
 /* Number of bands of tile rows the last fs4d_render / fs4d_render_host frame on the

@@ -31,24 +31,58 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+#ifdef FS4D_CHECK_BOUNDS
+// Debug build: canary bytes after every buffer, and the registry of live buffers.
+constexpr size_t kCanaryBytes = 256;
+constexpr unsigned char kCanary = 0xA5;
+std::mutex g_canary_mu;
+std::map<void*, size_t> g_canaries;  // buffer -> its size (the canary follows)
+void* g_last_buffer = nullptr;
+#else
+constexpr size_t kCanaryBytes = 0;
+#endif
+
+cudaError_t ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b) {
+#ifdef FS4D_CHECK_BOUNDS
+  if (b.p) {
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    g_canaries.erase(b.p);
+    if (g_last_buffer == b.p) g_last_buffer = nullptr;
+  }
+#endif
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return cudaSuccess;
   if (b.p) {
+#ifdef FS4D_CHECK_BOUNDS
+    {
+      std::lock_guard<std::mutex> lock(g_canary_mu);
+      g_canaries.erase(b.p);
+      if (g_last_buffer == b.p) g_last_buffer = nullptr;
+    }
+#endif
     cudaError_t e = cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
     if (e != cudaSuccess) return e;
   }
   if (bytes == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = cudaMalloc(&b.p, bytes + kCanaryBytes);
   if (e == cudaSuccess) b.bytes = bytes;
+#ifdef FS4D_CHECK_BOUNDS
+  if (e == cudaSuccess) {
+    e = cudaMemset(static_cast<unsigned char*>(b.p) + bytes, kCanary, kCanaryBytes);
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    g_canaries[b.p] = bytes;
+    g_last_buffer = b.p;
+  }
+#endif
   return e;
-}
-
-void release(DevBuf& b) {
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
 }
 
 template <typename T>
@@ -765,6 +799,7 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
   // per pair per pass)
   w.packed = !w.bmp && !offsets;
   ea.packed = w.packed ? 1 : 0;
+
   if (e.w == &c->w) c->last_binning = w.bmp ? FS4D_BINNING_BITMAP : FS4D_BINNING_SORT;
   if (w.bmp) {
     // bits per (tile, depth rank) and the projected Gaussians copied into rank order;
@@ -777,7 +812,7 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
     ea.tile_order = P<uint32_t>(w.tile_order);
     ea.xy = P<float2>(w.xy); ea.conic_opacity = P<float4>(w.co); ea.rgb = P<float>(w.rgb);
     ea.sorted_xy = P<float2>(w.sxy); ea.sorted_co = P<float4>(w.sco); ea.sorted_rgb = P<float>(w.srgb);
-    ea.cull = cull ? 1 : 0;
+    ea.cull = cull ? 1 : 0;  // bitmap frames only: the emission keeps the full rectangles
     if (w.bmp_dirty) FS4D_CUDA(c, cudaMemsetAsync(w.bitmap.p, 0, w.bitmap.bytes, stream));
     w.bmp_dirty = true;  // until the extraction (which clears every bit it reads) is launched
     FS4D_CUDA(c, launch_mark_tiles(ea, stream));
@@ -893,6 +928,7 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
   long long total = 0;
   int done = 0;
   fs4d_status st;
+  const bool cull = !d_n_contrib;  // bands are never saved for the backward
   Env be = env_of(c);
   be.guard_w = cam->width;
   be.guard_h = cam->height;
@@ -904,7 +940,7 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
     bc.height = std::min(cam->height, kTile * r1) - kTile * r0;
     bc.cy = cam->cy - (float)(kTile * r0);
     if ((st = ensure_work(c, s->n, tx * (r1 - r0), c->w.cap_pairs)) != FS4D_OK) return st;
-    if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+    if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false, false, cull)) != FS4D_OK)
       return st;
     long long K = 0;
     if ((st = read_pairs(c, c->w.z.num_pairs, &K)) != FS4D_OK) return st;
@@ -917,7 +953,8 @@ fs4d_status render_bands(fs4d_ctx* c, Scene* s, fs4d_precision prec, const fs4d_
     }
     if (K > c->w.cap_pairs) {
       if ((st = ensure_work(c, s->n, tx * (r1 - r0), std::min(K + K / 4, c->band_pairs))) != FS4D_OK) return st;
-      if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false)) != FS4D_OK)
+      if ((st = frame_front(be, s, prec, bc, nullptr, nullptr, t, c->w.cap_pairs, false, false, false, cull)) !=
+          FS4D_OK)
         return st;
     }
     const size_t off = (size_t)kTile * r0 * cam->width;
@@ -1093,6 +1130,40 @@ fs4d_status fs4d_set_wait_limit(fs4d_ctx* c, uint32_t polls) {
   if (!c) return FS4D_ERR_INVALID_ARG;
   c->spin_limit = polls == 0 ? kSpinLimit : polls;
   return FS4D_OK;
+}
+
+fs4d_status fs4d_check_canaries(fs4d_ctx* c) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+#ifdef FS4D_CHECK_BOUNDS
+  DeviceGuard g(c->device);
+  FS4D_CUDA(c, cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lock(g_canary_mu);
+  std::vector<unsigned char> host(kCanaryBytes);
+  for (const auto& kv : g_canaries) {
+    FS4D_CUDA(c, cudaMemcpy(host.data(), static_cast<unsigned char*>(kv.first) + kv.second, kCanaryBytes,
+                            cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < kCanaryBytes; ++i)
+      if (host[i] != kCanary)
+        return fail(c, FS4D_ERR_CORRUPT, "canary overwritten " + std::to_string(i) + " bytes after a buffer of " +
+                                             std::to_string(kv.second) + " bytes");
+  }
+  return FS4D_OK;
+#else
+  return fail(c, FS4D_ERR_UNIMPLEMENTED, "check_canaries: built without FS4D_CHECK_BOUNDS");
+#endif
+}
+
+fs4d_status fs4d_debug_corrupt_canary(fs4d_ctx* c) {
+  if (!c) return FS4D_ERR_INVALID_ARG;
+#ifdef FS4D_CHECK_BOUNDS
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lock(g_canary_mu);
+  if (!g_last_buffer) return fail(c, FS4D_ERR_NOT_FOUND, "debug_corrupt_canary: no buffer");
+  FS4D_CUDA(c, cudaMemset(static_cast<unsigned char*>(g_last_buffer) + g_canaries[g_last_buffer], 0, 1));
+  return FS4D_OK;
+#else
+  return fail(c, FS4D_ERR_UNIMPLEMENTED, "debug_corrupt_canary: built without FS4D_CHECK_BOUNDS");
+#endif
 }
 
 fs4d_status fs4d_check_device_status(fs4d_ctx* c) {

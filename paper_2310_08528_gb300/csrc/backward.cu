@@ -1146,8 +1146,16 @@ __global__ void wgrad_reduce_kernel(const __grid_constant__ WgradArgs wa) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const float* partial = wa.partial + ly.part_off;
-  float s = 0.f;
-  for (int c = 0; c < wa.chunks; ++c) s += partial[(long long)c * E + e];  // fixed order: deterministic
+  // eight running sums (eight loads in flight), each over a fixed set of chunks and
+  // combined in a fixed order: deterministic
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int c = 0;
+  for (; c + 8 <= wa.chunks; c += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += partial[(long long)(c + u) * E + e];
+  }
+  for (; c < wa.chunks; ++c) acc[c & 7] += partial[(long long)c * E + e];
+  const float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   if (e < O * I)
     ly.gW[e] += s;
   else

@@ -317,6 +317,36 @@ __device__ __forceinline__ uint32_t rect_row(uint32_t k, uint32_t w) {
 constexpr int kMarkHalves = 2;  // warps per word column: each takes every other 32-pair chunk
 constexpr int kMarkThreads = kPart * kMarkHalves;
 
+// The ellipse {alpha >= 1/255} of a projected Gaussian for the tile test of culled
+// lists: (A, B, C) its conic, S the bound on d^T K d wherever alpha may reach 1/255
+// (a 0.4% + 2e-3 margin over the compositing's own), (kx, ky) the edge minimisers'
+// slopes, (px, py) the mean.  S < 0: alpha never reaches 1/255; S = kNoBound: no
+// usable bound (not positive definite), every tile of the rectangle is kept.
+constexpr float kNoBound = 3.0e38f;
+struct TileEllipse {
+  float A, B, C, S, kx, ky, px, py;
+};
+__device__ __forceinline__ TileEllipse tile_ellipse(float2 p, float4 co) {
+  TileEllipse e{co.x, co.y, co.z, -1.f, 0.f, 0.f, p.x, p.y};
+  const float thr = composite_exp_threshold(co.w);
+  if (!(thr < 0.f)) return e;
+  if (!(e.A > 0.f && e.C > 0.f && e.A * e.C - e.B * e.B > 0.f)) {
+    e.S = kNoBound;
+    return e;
+  }
+  e.S = -2.f * thr * 1.004f + 2e-3f;
+  e.kx = -e.B / e.C;
+  e.ky = -e.B / e.A;
+  return e;
+}
+// Whether some pixel centre of tile (tx, ty) may blend the Gaussian.
+__device__ __forceinline__ bool tile_reached(const TileEllipse& e, int tx, int ty) {
+  if (e.S >= kNoBound) return true;
+  if (e.S < 0.f) return false;
+  const float x0 = (float)(tx * kTile) + 0.5f - e.px, y0 = (float)(ty * kTile) + 0.5f - e.py;
+  return rect_min(e.A, e.B, e.C, e.kx, e.ky, x0, x0 + (float)(kTile - 1), y0, y0 + (float)(kTile - 1)) <= e.S;
+}
+
 __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem_tiles) {
   extern __shared__ uint32_t s_tc[];
   pdl_wait();
@@ -330,7 +360,7 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem
   int4 r = make_int4(0, 0, 0, 0);
   uint32_t cnt = 0;
   // with a.cull: the ellipse {alpha >= 1/255} of this lane's Gaussian, for the tile test
-  float eA = 0.f, eB = 0.f, eC = 0.f, eS = -1.f, ekx = 0.f, eky = 0.f, epx = 0.f, epy = 0.f;
+  TileEllipse ell{0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f};
   if (pos < a.n) {
     const uint32_t g = order ? order[pos] : (uint32_t)pos;
     r = a.rect[g];
@@ -345,23 +375,7 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem
         a.sorted_rgb[3 * pos + 1] = a.rgb[3 * g + 1];
         a.sorted_rgb[3 * pos + 2] = a.rgb[3 * g + 2];
       }
-      if (a.cull) {
-        // q(d) = d^T K d <= eS wherever alpha may reach 1/255 (a 0.4% + 2e-3 margin over
-        // the compositing's own bound); eS < 0: alpha never reaches it; no usable
-        // bound (not positive definite): every tile of the rectangle is kept
-        const float thr = composite_exp_threshold(co.w);
-        eA = co.x; eB = co.y; eC = co.z;
-        epx = p.x; epy = p.y;
-        if (!(thr < 0.f)) {
-          eS = -1.f;
-        } else if (!(eA > 0.f && eC > 0.f && eA * eC - eB * eB > 0.f)) {
-          eS = 3.0e38f;
-        } else {
-          eS = -2.f * thr * 1.004f + 2e-3f;
-          ekx = -eB / eC;
-          eky = -eB / eA;
-        }
-      }
+      if (a.cull) ell = tile_ellipse(p, co);
     }
   }
   const uint32_t rw = (uint32_t)max(1, r.z - r.x);
@@ -391,16 +405,13 @@ __global__ void __launch_bounds__(kMarkThreads) mark_kernel(EmitArgs a, int smem
       k = j - e0;
       row = rect_row(k, w);
     }
-    if (a.cull) {  // uniform: the tile's pixel centres against the ellipse
-      const float A = __shfl_sync(0xffffffffu, eA, lo), B = __shfl_sync(0xffffffffu, eB, lo);
-      const float C = __shfl_sync(0xffffffffu, eC, lo), S = __shfl_sync(0xffffffffu, eS, lo);
-      const float kx = __shfl_sync(0xffffffffu, ekx, lo), ky = __shfl_sync(0xffffffffu, eky, lo);
-      const float px = __shfl_sync(0xffffffffu, epx, lo), py = __shfl_sync(0xffffffffu, epy, lo);
-      if (keep && S < 3.0e38f) {
-        const float x0 = (float)((rx + (int)(k - row * w)) * kTile) + 0.5f - px;
-        const float y0 = (float)((ry + (int)row) * kTile) + 0.5f - py;
-        keep = S >= 0.f && rect_min(A, B, C, kx, ky, x0, x0 + (float)(kTile - 1), y0, y0 + (float)(kTile - 1)) <= S;
-      }
+    if (a.cull) {  // uniform: the tile's pixel centres against the ellipse of the pair's Gaussian
+      TileEllipse e;
+      e.A = __shfl_sync(0xffffffffu, ell.A, lo); e.B = __shfl_sync(0xffffffffu, ell.B, lo);
+      e.C = __shfl_sync(0xffffffffu, ell.C, lo); e.S = __shfl_sync(0xffffffffu, ell.S, lo);
+      e.kx = __shfl_sync(0xffffffffu, ell.kx, lo); e.ky = __shfl_sync(0xffffffffu, ell.ky, lo);
+      e.px = __shfl_sync(0xffffffffu, ell.px, lo); e.py = __shfl_sync(0xffffffffu, ell.py, lo);
+      if (keep) keep = tile_reached(e, rx + (int)(k - row * w), ry + (int)row);
     }
     if (keep) {
       const uint32_t tile = (uint32_t)(ry + (int)row) * (uint32_t)a.tiles_x + (uint32_t)rx + (k - row * w);

@@ -224,10 +224,10 @@ struct EmitArgs {
   float2* sorted_xy;            // [n]
   float4* sorted_co;            // [n]
   float* sorted_rgb;            // [n][3]
-  int cull;                     // 1: mark only the tiles whose pixel centres the ellipse
-                                // {alpha >= 1/255} can reach (the lists lose Gaussians that no
-                                // pixel of the tile blends: the image is unchanged, list
-                                // positions are not the full rectangle's)
+  int cull;                     // 1 (mark): set a bit only for the tiles whose pixel centres the
+                                // Gaussian's ellipse {alpha >= 1/255} can reach.  The lists lose
+                                // Gaussians no pixel of the tile blends: the image is unchanged,
+                                // list positions are not the full rectangles'.
 };
 
 struct SortWork {

@@ -19,7 +19,7 @@ FP32, BF16 = 0, 1
 BINNING_AUTO, BINNING_SORT, BINNING_BITMAP = 0, 1, 2
 STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_ERR_CAPACITY",
           4: "FS4D_ERR_CUDA", 5: "FS4D_ERR_TIMEOUT", 6: "FS4D_ERR_NOT_FOUND", 7: "FS4D_ERR_UNIMPLEMENTED",
-          8: "FS4D_ERR_CANCELLED"}
+          8: "FS4D_ERR_CANCELLED", 9: "FS4D_ERR_CORRUPT"}
 
 # Every symbol include/fs4d.h declares (checked by the tests against the .so).
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
@@ -31,7 +31,8 @@ EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", 
            "fs4d_train_create", "fs4d_train_step", "fs4d_train_losses", "fs4d_train_steps_done",
            "fs4d_train_destroy", "fs4d_read_scene", "fs4d_save_scene", "fs4d_load_scene_file",
            "fs4d_backward_times", "fs4d_render_composed", "fs4d_train_read_state", "fs4d_render_backward_stats",
-           "fs4d_densify", "fs4d_train_stats", "fs4d_train_densify")
+           "fs4d_densify", "fs4d_train_stats", "fs4d_train_densify", "fs4d_check_canaries",
+           "fs4d_debug_corrupt_canary")
 STAGES = ("deform", "project", "depth_sort", "binning", "sort", "composite")
 
 
@@ -99,14 +100,15 @@ class DensifyConfig(C.Structure):
     _fields_ = [("grad_threshold", C.c_float), ("split_log_scale", C.c_float), ("prune_logit", C.c_float)]
 
 
-_lib = None
+_libs: Dict[str, object] = {}
+LIB_DEBUG_PATH = os.path.join(HERE, "libfs4d_debug.so")
 
 
 def library(path: str = LIB_PATH):
-    """Load libfs4d.so (raises if it is missing: there is no CPU fallback)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libfs4d.so (raises if it is missing: there is no CPU fallback); with
+    path=LIB_DEBUG_PATH the FS4D_CHECK_BOUNDS build."""
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
     L = C.CDLL(path)
@@ -167,7 +169,10 @@ def library(path: str = LIB_PATH):
     L.fs4d_sort_pairs_noalloc_status.restype = C.c_int
     L.fs4d_last_error.argtypes = [vp]
     L.fs4d_last_error.restype = C.c_char_p
-    _lib = L
+    for name in ("fs4d_check_canaries", "fs4d_debug_corrupt_canary"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = C.c_int
+    _libs[path] = L
     return L
 
 
@@ -186,10 +191,10 @@ def _ptr(t) -> Optional[int]:
 class Context:
     """One fs4d context: a CUDA device and the stream its work is queued on."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, lib=None):
         import torch
         self.torch = torch
-        self.lib = library()
+        self.lib = lib if lib is not None else library()
         self.device = int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()

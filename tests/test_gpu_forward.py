@@ -489,24 +489,31 @@ def test_bitmap_and_sort_binning_render_identical_images(ctx, prec, w, h):
 
 
 @pytest.mark.parametrize("prec", [fs4d.FP32, fs4d.BF16])
-def test_culled_tile_lists_render_identical_images(ctx, prec):
+@pytest.mark.parametrize("binning", ["auto", "sort"])
+def test_culled_tile_lists_render_identical_images(ctx, prec, binning):
     """Frames that report no list positions leave out of each tile's list the
     Gaussians whose ellipse {alpha >= 1/255} reaches none of the tile's pixel
-    centres; no pixel would blend them, so the image is bit-identical to the frame
-    over the full rectangles (a frame with last-contributor output), on the
-    800x800 object, a ragged frame, and through the host and capture calls."""
+    centres (the bitmap binning in its marks, the sort binning in its emission);
+    no pixel would blend them, so the image is bit-identical to the frame over the
+    full rectangles (a frame with last-contributor output), on the 800x800 object,
+    a ragged frame, and through the host call; both report the rectangles' pairs."""
     s = sg.make_object(0)
     sid = ctx.load_scene(s)
+    ctx.set_binning(fs4d.BINNING_SORT if binning == "sort" else fs4d.BINNING_AUTO)
     try:
         for cam in (sg.hemisphere_cameras(50, width=800, height=800)[7],
                     sg.hemisphere_cameras(3, width=333, height=517, seed=2)[1]):
             full, _, _ = ctx.render(sid, cam, 0.35, prec=prec, with_aux=True)
+            k_full = ctx.last_pairs()
             culled = ctx.render(sid, cam, 0.35, prec=prec)
+            k_culled = ctx.last_pairs()
             host = ctx.render_host(sid, cam, 0.35, prec=prec)
             torch.cuda.synchronize()
             assert torch.equal(full, culled)
             assert np.array_equal(full.cpu().numpy(), host)
+            assert k_full == k_culled
     finally:
+        ctx.set_binning(fs4d.BINNING_AUTO)
         ctx.unload_scene(sid)
 
 
