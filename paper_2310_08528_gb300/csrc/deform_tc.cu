@@ -163,6 +163,40 @@ __device__ __forceinline__ void axis_setup(float u, int R, int& i0, float& f) {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes_is16) {
+  const uint32_t d = smem_u32(smem);
+  if (bytes_is16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+// Row r = tid of a tile into the row buffers (rx: X and t, rq: quaternion, rs:
+// log-scales and the Gaussian index as bits): the work-order index is loaded, the
+// rows are copied by cp.async (waited for at the start of the tile that uses them).
+__device__ __forceinline__ void fetch_rows(const DeformArgs& a, long long base, long long total, int tid, float4* rx,
+                                           float4* rq, float4* rs) {
+  const long long gi = base + tid;
+  if (gi < total) {
+    const int ti = (int)(gi / a.n);
+    const int gw = (int)(gi - (long long)ti * a.n);
+    const int g = a.perm ? (int)a.perm[gw] : gw;
+    float* x = reinterpret_cast<float*>(rx + tid);
+    float* sc = reinterpret_cast<float*>(rs + tid);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cp_async(x + k, a.means + 3 * (size_t)g + k, 0);
+      cp_async(sc + k, a.log_scales + 3 * (size_t)g + k, 0);
+    }
+    cp_async(rq + tid, reinterpret_cast<const float4*>(a.quats) + g, 1);
+    x[3] = a.ts ? a.ts[ti] : a.t0;
+    sc[3] = __int_as_float(g);
+  } else {
+    rx[tid] = rq[tid] = rs[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 template <int H, int L>
 __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   constexpr int HL = H * L;
@@ -176,10 +210,9 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   uint64_t* sMbar = reinterpret_cast<uint64_t*>(sBias + kBiasFloats);
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(sMbar + 1);
   uint32_t* sFail = sTmem + 1;
-  // the tile's rows: (X, t), quaternion, (log-scales, Gaussian index as bits)
-  float4* sRowX = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(sMbar) + 16);
-  float4* sRowQ = sRowX + kRows;
-  float4* sRowS = sRowQ + kRows;
+  // the rows of two tiles (this one and the next, prefetched): (X, t), quaternion,
+  // (log-scales, Gaussian index as bits)
+  float4* sRows = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(sMbar) + 16);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < tg.bytes / 16; i += kThreads)
@@ -209,27 +242,17 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   const long long total = (long long)a.n * a.n_t;
   const long long tiles = (total + kRows - 1) / kRows;
 
-  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  int buf = 0;
+  if (tid < kRows && blockIdx.x < tiles)
+    fetch_rows(a, (long long)blockIdx.x * kRows, total, tid, sRows, sRows + kRows, sRows + 2 * kRows);
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, buf ^= 1) {
     const long long base = tile * kRows;
-    // ---- 0. the tile's rows gathered once into shared memory (the work-order
-    // index, then position, t, quaternion and log-scales in one round of loads),
-    // so the sampling and the last epilogue chase no indices
-    if (tid < kRows) {
-      const long long gi = base + tid;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), q = x, sc = x;
-      if (gi < total) {
-        const int ti = (int)(gi / a.n);
-        const int gw = (int)(gi - (long long)ti * a.n);
-        const int g = a.perm ? (int)a.perm[gw] : gw;
-        const float t = a.ts ? a.ts[ti] : a.t0;
-        x = make_float4(a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2], t);
-        q = reinterpret_cast<const float4*>(a.quats)[g];
-        sc = make_float4(a.log_scales[3 * g], a.log_scales[3 * g + 1], a.log_scales[3 * g + 2], __int_as_float(g));
-      }
-      sRowX[tid] = x;
-      sRowQ[tid] = q;
-      sRowS[tid] = sc;
-    }
+    // ---- 0. the tile's rows, gathered once into shared memory (prefetched during
+    // the previous tile's GEMMs), so the sampling and the last epilogue chase no indices
+    const float4* sRowX = sRows + 3 * kRows * buf;
+    const float4* sRowQ = sRowX + kRows;
+    const float4* sRowS = sRowQ + kRows;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     // ---- 1. HexPlane features (Eq. 5) -> A1 [128 x HL] BF16.  Four (H = 32) or
     // two (H = 16) consecutive lanes share one (Gaussian, level) item and each
@@ -285,6 +308,11 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
     }
     fence_async_smem();
     __syncthreads();
+    // the next tile's rows, into the other buffer (its last reader was the previous tile)
+    if (tid < kRows && tile + gridDim.x < tiles) {
+      float4* nx = sRows + 3 * kRows * (buf ^ 1);
+      fetch_rows(a, (tile + gridDim.x) * kRows, total, tid, nx, nx + kRows, nx + 2 * kRows);
+    }
 
     // ---- 2. phi_d layer 1: D1 (cols 0..63) = A1 . W_d1^T
     if (tid == 0) {
@@ -383,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
     if (*sFail) break;  // uniform: read after the barrier
   }
   tc_fence_after();
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // a prefetch of a tile not run (timeout)
   if (*sFail && tid == 0) atomicOr(a.status, kStatusTimeout);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
@@ -390,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
 
 template <int H, int L>
 cudaError_t launch_t(const DeformArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16 + 3 * kRows * 16;
+  const size_t smem = (size_t)((a.tg.bytes + 1023) / 1024 * 1024) + kXBytes + kBiasFloats * 4 + 16 + 6 * kRows * 16;
   static PerDeviceFlag attr;
   cudaError_t e = once_per_device(attr, [&] {
     return cudaFuncSetAttribute(deform_tc_kernel<H, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
