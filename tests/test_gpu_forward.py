@@ -218,6 +218,7 @@ def test_bin_sort_empty_and_capacity(ctx, binning):
 
 
 @pytest.mark.parametrize("n,bits", [(1, 8), (4095, 12), (4097, 33), (100000, 44), (262145, 64), (30000, 1),
+                                    (17, 3), (50001, 24), (100000, 32), (131072, 32), (131073, 32),
                                     ((1 << 19) + 1, 20),     # above 2^19 keys: the persistent, prefetching pass
                                     (3 * (1 << 20) + 7, 64)])
 def test_sort_pairs_matches_stable_numpy(ctx, n, bits):
@@ -233,6 +234,25 @@ def test_sort_pairs_matches_stable_numpy(ctx, n, bits):
     order = np.argsort(low, kind="stable")
     assert np.array_equal(tk.cpu().numpy().view(np.uint64), keys[order])
     assert np.array_equal(tv.cpu().numpy().view(np.uint32), vals[order])
+
+
+@pytest.mark.parametrize("n", [5, 100000, 131072])
+def test_sort_depth_keys_and_constant_digits(ctx, n):
+    """Depth-like keys (float32 bits of depths in [2, 4): the top byte is the same
+    for every key, so that pass moves nothing), all-equal keys (every pass keeps
+    the order) and bits above 32 that travel with the keys."""
+    rng = np.random.default_rng(n)
+    depth = rng.uniform(2.0, 4.0, n).astype(np.float32)
+    depth[::7] = depth[0]
+    hi = rng.integers(0, 2 ** 31, n, dtype=np.uint64) << np.uint64(32)
+    for keys in (depth.view(np.uint32).astype(np.uint64) | hi, np.full(n, 0xABCD00001234, np.uint64)):
+        vals = rng.permutation(n).astype(np.uint32)
+        tk = dev(keys.view(np.int64))
+        tv = dev(vals.view(np.int32))
+        ctx.sort_pairs(tk, tv, 32)
+        order = np.argsort(keys & np.uint64(0xFFFFFFFF), kind="stable")
+        assert np.array_equal(tk.cpu().numpy().view(np.uint64), keys[order])
+        assert np.array_equal(tv.cpu().numpy().view(np.uint32), vals[order])
 
 
 # ------------------------------------------------------------------ compositing (Eq. 4)
