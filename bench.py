@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true")
     ap.add_argument("--sort-pairs", type=int, default=0,
                     help="instead of the frame benchmark: time fs4d_sort_pairs on this many random pairs")
     ap.add_argument("--sort-bits", type=int, default=13)
@@ -654,6 +655,91 @@ def measure(ctx, fs4d, torch, sid, prec, steps, warmup, rank, world, stream, cap
     return frame_ms, mean_st
 
 
+def extensions_bench(ctx, fs4d, torch, sg, sid, scene, stream, cap, steps=300, warmup=10):
+    """The rows beyond the headline frame, on the same 800x800 / 100k object:
+    the colour and opacity heads (App. B) in graph-replayed frames, composition of
+    two objects in one frame, a tracking batch of 16 timestamps, and one
+    densification."""
+    out = {}
+    try:
+        cid = ctx.load_scene(sg.with_color_heads(scene, 5))
+        ctx.reserve(cid, WIDTH, HEIGHT, cap)
+        ch = {}
+        for p, pc in (("bf16", fs4d.BF16), ("fp32", fs4d.FP32)):
+            ms, st = measure(ctx, fs4d, torch, cid, pc, steps, warmup, 0, 1, stream, cap)
+            ch[p] = {"fps": 1e3 / float(np.mean(ms)), "p50_ms": float(np.percentile(ms, 50)),
+                     "stages_ms": st}
+        ch["note"] = "graph-replayed frames as in the headline; the deform stage includes the heads (FP32 SIMT)"
+        out["color_heads"] = ch
+        ctx.unload_scene(cid)
+    except Exception as exc:
+        out["color_heads"] = {"error": f"{type(exc).__name__}: {exc}"}
+    try:
+        oid = ctx.load_scene(sg.make_object(1))
+        shifts = np.array([[-0.6, 0.0, 0.0], [0.6, 0.0, 0.0]], np.float32)
+        comp = {}
+        with torch.cuda.stream(stream):
+            for p, pc in (("bf16", fs4d.BF16), ("fp32", fs4d.FP32)):
+                for i in range(3):
+                    cam, t = views(i, 0, 1)
+                    ctx.render_composed([sid, oid], cam, t, pc, shifts=shifts)
+                stream.synchronize()
+                k = 40
+                t0 = time.perf_counter()
+                for i in range(k):
+                    cam, t = views(i, 0, 1)
+                    ctx.render_composed([sid, oid], cam, t, pc, shifts=shifts)
+                stream.synchronize()
+                comp[p] = {"ms_per_frame": (time.perf_counter() - t0) * 1e3 / k}
+        comp["workload"] = "two 100k objects (200k Gaussians) in one 800x800 frame, eager host-synchronised calls"
+        out["composition"] = comp
+        trk = {}
+        ts = np.linspace(0.0, 1.0, 16).astype(np.float32)
+        outs = (torch.empty((16, scene.n, 3), device="cuda"), torch.empty((16, scene.n, 4), device="cuda"),
+                torch.empty((16, scene.n, 3), device="cuda"))
+        with torch.cuda.stream(stream):
+            for p, pc in (("bf16", fs4d.BF16), ("fp32", fs4d.FP32)):
+                ctx.deform(sid, ts, pc, outs)
+                ms = []
+                for _ in range(10):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.deform(sid, ts, pc, outs)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                m = float(np.median(ms))
+                trk[p] = {"ms": m, "gaussian_timestamps_per_s": 16 * scene.n / (m * 1e-3)}
+        trk["workload"] = "fs4d_deform of the 100k object at 16 timestamps in one call (trajectories)"
+        out["tracking"] = trk
+        ctx.unload_scene(oid)
+    except Exception as exc:
+        out["composition_tracking"] = {"error": f"{type(exc).__name__}: {exc}"}
+    try:
+        did = ctx.load_scene(scene)
+        n = scene.n
+        gen = torch.Generator("cuda").manual_seed(7)
+        vis = torch.full((n,), 20.0, device="cuda")
+        gsum = torch.rand(n, device="cuda", generator=gen) * 4e-3  # mean norm ~2e-4 per view
+        normals = torch.randn((n, 2, 3), device="cuda", generator=gen)
+        thr = float(np.quantile(np.linspace(0.0, 2e-4, 1001), 0.9))  # ~10% of the Gaussians densify
+        split = float(np.quantile(scene.log_scales.max(1), 0.5))
+        prune = float(np.quantile(scene.opacity_logits, 0.05))
+        stream.synchronize()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = ctx.densify_raw(did, (gsum, vis), normals, thr, split, prune)
+        ms = (time.perf_counter() - t0) * 1e3
+        out["densify"] = {"ms": ms, "n_before": n, "n_after": m,
+                          "workload": "fs4d_densify of a copy of the 100k object: ~10% over the gradient "
+                                      "threshold (half copied, half split), ~5% pruned; wall time of the "
+                                      "call (its result size is read back once)"}
+        ctx.unload_scene(did)
+    except Exception as exc:
+        out["densify"] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
+
+
 def sort_only(args):
     """Standalone radix sort of random (key, value) pairs on the low sort_bits bits
     (the pair sort of a frame sorts tile bits only: 12-15 bits).  Prints one JSON
@@ -836,6 +922,8 @@ def main():
         line["serving"] = serving_bench(ctx, fs4d, torch)
     if not args.no_stress:
         line["stress"] = stress_bench(ctx, fs4d, torch, stream, peaks)
+    if not args.no_extensions:
+        line["extensions"] = extensions_bench(ctx, fs4d, torch, sg, sid, scene, stream, cap)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

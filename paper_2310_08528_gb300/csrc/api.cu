@@ -703,7 +703,8 @@ fs4d_status deform_part(fs4d_ctx* c, Work& w, const FramePart& q, fs4d_precision
   ca.logits = P<float>(q.s->opacity_logits);
   ca.sh_out = P<float>(w.dsh) + 48 * q.off;
   ca.logit_out = P<float>(w.dop) + q.off;
-  FS4D_CUDA(c, launch_color_heads(ca, stream));
+  ca.status = status;
+  FS4D_CUDA(c, prec == FS4D_BF16 ? launch_color_heads_bf16(ca, stream) : launch_color_heads(ca, stream));
   return FS4D_OK;
 }
 

@@ -151,9 +151,13 @@ struct ColorArgs {
   const float* logits;          // [n] canonical
   float* sh_out;                // [n][K][3] deformed
   float* logit_out;             // [n] deformed
+  uint32_t* status;             // optional: kStatusTimeout if a bounded wait gave up (tensor-core form)
 };
 int color_layer_floats(int k3);
+// float32 SIMT form (the FP32 path)
 cudaError_t launch_color_heads(const ColorArgs& a, cudaStream_t s);
+// BF16 tcgen05 form (the BF16 path): k3 in {3, 12, 27, 48}; fd, sh, sh_out 16-byte aligned
+cudaError_t launch_color_heads_bf16(const ColorArgs& a, cudaStream_t s);
 
 struct CamParams {
   int width, height;

@@ -364,6 +364,17 @@ class Context:
         self._resized(sid, m.value)
         return m.value
 
+    def densify_raw(self, sid: int, stats, normals, grad_threshold: float, split_log_scale: float,
+                    prune_logit: float) -> int:
+        """fs4d_densify alone: returns the new n and leaves the binding's host
+        record of the scene stale (for timing; unload the scene afterwards)."""
+        vs = ViewStats(_ptr(stats[0]), _ptr(stats[1]))
+        cfg = DensifyConfig(grad_threshold, split_log_scale, prune_logit)
+        m = C.c_int64()
+        self.call("fs4d_densify", sid, C.byref(cfg), C.byref(vs), _ptr(normals.contiguous()), None, C.byref(m))
+        self._scenes[sid] = None
+        return m.value
+
     def _resized(self, sid: int, n: int) -> None:
         """Replace the record of scene sid by a host copy of its parameters at size n."""
         rec = self._scenes[sid].copy()

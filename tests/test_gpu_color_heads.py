@@ -3,7 +3,9 @@ phi_alpha(f_d)) on the GPU, through the C ABI, against the FP64 oracle.
 
 * FP32 frames, every pixel, against the oracle's frame of the same scene with the
   heads (its per-pixel outcome enumeration), for a degree-0 and a degree-3 scene;
-* BF16 frames (f_d from the tensor-core deformation, heads in float32): PSNR;
+* BF16 frames (f_d from the tensor-core deformation, both heads as two tcgen05
+  GEMMs per 128 Gaussians): PSNR, for SH degrees 0 to 3 (3K = 3, 12, 27, 48
+  outputs of the colour head);
 * heads with all weights and biases 0 give bit-identical frames to the scene
   without them, and composition with a scene that has heads matches the oracle;
 * what such scenes do not support fails loudly: the backward and the trainer
@@ -70,6 +72,29 @@ def test_color_heads_frame_matches_oracle(ctx, which):
         mse = float(np.mean((bf.cpu().numpy() - fr["img"]) ** 2))
         psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
         print(f"BF16 with colour heads: PSNR {psnr:.1f} dB")
+        assert psnr >= 50.0
+    finally:
+        ctx.unload_scene(sid)
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_color_heads_other_sh_degrees(ctx, degree):
+    """SH degrees 1 and 2 (colour heads of 12 and 27 outputs: the rows of 27 are
+    not 16-byte aligned): FP32 every pixel, BF16 by PSNR, against the oracle."""
+    s = sg.with_color_heads(sg.make_object(30 + degree, n=6000, sh_degree=degree, mlp_std=0.05), degree, std=0.08)
+    cam = sg.hemisphere_cameras(3, width=160, height=144, seed=degree)[0]
+    sid = ctx.load_scene(s)
+    try:
+        img, T, nc = ctx.render(sid, cam, 0.55, fs4d.FP32, with_aux=True)
+        bf = ctx.render(sid, cam, 0.55, fs4d.BF16)
+        torch.cuda.synchronize()
+        oracle.set_threads(oracle.default_threads())
+        fr = parity.oracle_frame(s, cam, 0.55)
+        st = parity.check_frame(img.cpu().numpy(), fr, T.cpu().numpy(), nc.cpu().numpy(), tol=1e-4, px_tol=5e-4)
+        assert st["unresolved"] == 0
+        mse = float(np.mean((bf.cpu().numpy() - fr["img"]) ** 2))
+        psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
+        print(f"degree {degree}, BF16 with colour heads: PSNR {psnr:.1f} dB")
         assert psnr >= 50.0
     finally:
         ctx.unload_scene(sid)

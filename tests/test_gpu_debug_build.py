@@ -65,6 +65,7 @@ def test_every_path_leaves_the_canaries_intact():
         c = sg.with_color_heads(sg.make_tiny(32, n=3000, mlp_std=0.1), 3)
         cid = ctx.load_scene(c)
         ctx.render(cid, sg.tiny_camera(), 0.3)
+        ctx.render(cid, sg.tiny_camera(), 0.3, fs4d.BF16)
         ctx.render_composed([sid, cid], cam, 0.4, shifts=np.array([[0, 0, 0], [0.4, 0.1, 0.0]]))
         torch.cuda.synchronize()
         rc = lib.fs4d_check_canaries(ctx.h)
