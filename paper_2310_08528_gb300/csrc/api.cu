@@ -504,7 +504,7 @@ fs4d_status get_scene(fs4d_ctx* c, fs4d_scene_id id, Scene** out) {
 fs4d_status ensure_color(fs4d_ctx* c, Work& w, cudaStream_t stream, int n) {
   if (w.cap_color >= n) return FS4D_OK;
   FS4D_CUDA(c, cudaStreamSynchronize(stream));
-  FS4D_CUDA(c, ensure(w.fd, 4 * 64 * (size_t)n));
+  FS4D_CUDA(c, ensure(w.fd, 4 * 64 * (size_t)n + 16384));  // + the last BF16 tile image's ragged end
   FS4D_CUDA(c, ensure(w.dsh, 4 * 48 * (size_t)n));
   FS4D_CUDA(c, ensure(w.dop, 4 * (size_t)n));
   w.cap_color = n;
@@ -690,13 +690,20 @@ fs4d_status deform_part(fs4d_ctx* c, Work& w, const FramePart& q, fs4d_precision
                         cudaStream_t stream, uint32_t* status) {
   DeformArgs da = deform_args(q.s, d_t, t, 1, P<float>(w.dmeans) + 3 * q.off, P<float>(w.dquats) + 4 * q.off,
                               P<float>(w.dscales) + 3 * q.off);
-  if (q.s->color_heads) da.fd_out = P<float>(w.fd) + 64 * q.off;
+  // f_d: float32 rows from the FP32 kernel; BF16 tile images from the tensor-core kernel (a part's
+  // images may run up to 16 KB past its 256 bytes per Gaussian, into the next part's share, which
+  // is written only after this part's heads have read them; the buffer has 16 KB to spare)
+  if (q.s->color_heads && prec == FS4D_BF16)
+    da.fd_tiles = reinterpret_cast<uint4*>(P<uint8_t>(w.fd) + 256 * (size_t)q.off);
+  else if (q.s->color_heads)
+    da.fd_out = P<float>(w.fd) + 64 * q.off;
   fs4d_status st = run_deform(c, q.s, prec, da, stream, status);
   if (st != FS4D_OK || !q.s->color_heads) return st;
   ColorArgs ca{};
   ca.n = q.s->n;
   ca.perm = P<uint32_t>(q.s->perm);
   ca.fd = da.fd_out;
+  ca.fd_tiles = da.fd_tiles;
   ca.weights = P<float>(q.s->mlp) + q.s->color_off;
   ca.k3 = 3 * q.s->K;
   ca.sh = P<float>(q.s->sh);

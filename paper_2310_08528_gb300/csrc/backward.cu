@@ -801,7 +801,13 @@ __global__ void __launch_bounds__(kTT, 1) mlp_bwd_tile_kernel(MlpBwdArgs a) {
   float* DO = HID + 3 * kWidth * kTS; // [10]: dL/d(X', r', s')
   float4* sRow = reinterpret_cast<float4*>(DO + kDeltaDim * kTS);  // (X, t) per Gaussian
   int* sG = reinterpret_cast<int*>(sRow + kTG);                     // Gaussian index per column
-  for (int i = threadIdx.x; i < mg.total / 4; i += kTT) smem4[i] = __ldg(reinterpret_cast<const float4*>(f.mlp_t) + i);
+  // the weights by cp.async (every 16-byte copy in flight at once), waited for below
+  for (int i = threadIdx.x; i < mg.total / 4; i += kTT) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem4 + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(reinterpret_cast<const float4*>(f.mlp_t) + i)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" "cp.async.wait_all;\n" ::: "memory");
   const int g4 = (threadIdx.x & 15) * 4, o4 = (threadIdx.x >> 4) * 4;
   const long long n = f.n;
   const MlpActs& act = a.act;

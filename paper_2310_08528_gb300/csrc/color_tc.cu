@@ -4,13 +4,16 @@
 //   D1 [128 x 128] = F . [W_C1; W_a1]^T               both hidden layers (K = 64)
 //   D2 [128 x 64]  = H . blockdiag(W_C2, W_a2)^T      3K colour outputs, then the
 //                                                     opacity output (K = 128)
-// F is f_d (float32 from the deformation kernel, rounded to BF16 when staged), H
-// the ReLU'd hidden layers in BF16, both in the UMMA canonical no-swizzle K-major
-// layout.  Each CTA converts the four layers from the scene's float32 weights into
+// F is f_d, which the BF16 deformation kernel leaves as each tile's operand image
+// (BF16, UMMA canonical no-swizzle K-major layout, 16 KB per tile), H the ReLU'd
+// hidden layers in BF16 in the same layout.  The outputs are staged in shared
+// memory and written row by row, so that a warp's stores cover whole rows of C'.  Each CTA converts the four layers from the scene's float32 weights into
 // operand images in its own shared memory once, so a weight update needs no
 // refresh.  Persistent CTAs (two per SM, 256 TMEM columns each); one thread issues
 // each GEMM and commits it to an mbarrier; every wait is bounded (on a timeout the
 // CTA records kStatusTimeout, stops, frees its TMEM and returns).
+#include <type_traits>
+
 #include "tc_util.cuh"
 
 namespace fs4d {
@@ -41,36 +44,6 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
   return q;
 }
 
-// The 32 output columns c0..c0+31 of one Gaussian: SH coefficient o < K3 is
-// C[o] + (acc + b), column K3 is the opacity logit's offset.
-template <int K3>
-__device__ __forceinline__ void write_outputs(const ColorArgs& a, int g, int c0, const float (&v)[32],
-                                              const float* b) {
-  const float* src = a.sh + (size_t)g * K3;
-  float* dst = a.sh_out + (size_t)g * K3;
-  if constexpr (K3 % 4 == 0) {  // rows and column groups 16-byte aligned
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-      const int o = c0 + j;
-      if (o < K3) {
-        float4 s = *reinterpret_cast<const float4*>(src + o);
-        s.x += v[j] + b[j];
-        s.y += v[j + 1] + b[j + 1];
-        s.z += v[j + 2] + b[j + 2];
-        s.w += v[j + 3] + b[j + 3];
-        *reinterpret_cast<float4*>(dst + o) = s;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < K3) dst[c0 + j] = src[c0 + j] + (v[j] + b[j]);
-  }
-#pragma unroll
-  for (int j = 0; j < 32; ++j)
-    if (c0 + j == K3) a.logit_out[g] = a.logits[g] + (v[j] + b[j]);
-}
-
 template <int K3>
 __global__ void __launch_bounds__(kThreads, 2) color_tc_kernel(const ColorArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -83,28 +56,44 @@ __global__ void __launch_bounds__(kThreads, 2) color_tc_kernel(const ColorArgs a
   const float* w = a.weights;
   constexpr int c1w = 0, c1b = c1w + kW * kW, c2w = c1b + kW, c2b = c2w + K3 * kW, a1w = c2b + K3,
                 a1b = a1w + kW * kW, a2w = a1b + kW, a2b = a2w + kW;
-  for (int c = tid; c < 128 * 8; c += kThreads) {  // B1: rows 0..63 W_C1, 64..127 W_a1
-    const int r = c >> 3, k0 = (c & 7) * 8;
-    const float* src = w + (r < kW ? c1w + r * kW : a1w + (r - kW) * kW) + k0;
-    float v[8];
+  // operand images of the four layers: each thread loads all its values first (every
+  // load in flight at once), then converts and stores them; B1 and B2 have 1024
+  // chunks of 8 values each, 4 per thread
+  {
+    float v[4][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = src[j];
-    *reinterpret_cast<uint4*>(smem + kB1 + a_off(r, k0, 64)) = pack8(v);
-  }
-  for (int c = tid; c < 64 * 16; c += kThreads) {  // B2: W_C2 on K 0..63, W_a2 in row K3 on K 64..127
-    const int r = c >> 4, k0 = (c & 15) * 8;
-    float v[8];
+    for (int j = 0; j < 4; ++j) {  // B1: rows 0..63 W_C1, 64..127 W_a1 (K = 64)
+      const int c = tid + kThreads * j, r = c >> 3, k0 = (c & 7) * 8;
+      const float* src = w + (r < kW ? c1w + r * kW : a1w + (r - kW) * kW) + k0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      v[j] = (r < K3 && k0 < kW) ? w[c2w + r * kW + k0 + j] : (r == K3 && k0 >= kW) ? w[a2w + k0 - kW + j] : 0.f;
-    *reinterpret_cast<uint4*>(smem + kB2 + a_off(r, k0, 128)) = pack8(v);
+      for (int k = 0; k < 8; ++k) v[j][k] = __ldg(src + k);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tid + kThreads * j, r = c >> 3, k0 = (c & 7) * 8;
+      *reinterpret_cast<uint4*>(smem + kB1 + a_off(r, k0, 64)) = pack8(v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // B2: W_C2 on K 0..63, W_a2 in row K3 on K 64..127, else 0
+      const int c = tid + kThreads * j, r = c >> 4, k0 = (c & 15) * 8;
+      const bool col = r < K3 && k0 < kW, op = r == K3 && k0 >= kW;
+      const float* src = w + (col ? c2w + r * kW + k0 : a2w + k0 - kW);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[j][k] = (col || op) ? __ldg(src + k) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tid + kThreads * j, r = c >> 4, k0 = (c & 15) * 8;
+      *reinterpret_cast<uint4*>(smem + kB2 + a_off(r, k0, 128)) = pack8(v[j]);
+    }
   }
-  for (int i = tid; i < 128 + 64; i += kThreads) {
+  if (tid < 128 + 64) {
+    const int i = tid;
     float b = 0.f;
-    if (i < kW) b = w[c1b + i];
-    else if (i < 2 * kW) b = w[a1b + i - kW];
-    else if (i - 2 * kW < K3) b = w[c2b + i - 2 * kW];
-    else if (i - 2 * kW == K3) b = w[a2b];
+    if (i < kW) b = __ldg(w + c1b + i);
+    else if (i < 2 * kW) b = __ldg(w + a1b + i - kW);
+    else if (i - 2 * kW < K3) b = __ldg(w + c2b + i - 2 * kW);
+    else if (i - 2 * kW == K3) b = __ldg(w + a2b);
     sBias[i] = b;
   }
   const uint32_t mbar = smem_u32(sMbar);
@@ -126,26 +115,50 @@ __global__ void __launch_bounds__(kThreads, 2) color_tc_kernel(const ColorArgs a
   const int half = warp >> 2;              // which half of the columns
   uint32_t phase = 0;
   const long long tiles = ((long long)a.n + kRows - 1) / kRows;
+  // C' rows of a tile, cooperatively: vector q (kVec floats) of row r is item r * kPerRow + q
+  constexpr int kVec = (K3 % 4 == 0) ? 4 : 1;
+  constexpr int kPerRow = K3 / kVec;
+  constexpr int kItems = (kRows * kPerRow + kThreads - 1) / kThreads;
+  constexpr int kStride = K3 + 1;  // staged row: K3 colour offsets, then the opacity offset
+  float* sOut = reinterpret_cast<float*>(smem + kH);  // reuses H once D2 has read it
+  static_assert(kRows * kStride * 4 <= 128 * 128 * 2, "staged outputs fit in H");
+  // this tile's F image, and the next tile's while this one's GEMMs run (4 x 16 B per thread)
+  uint4 fimg[4];
+  auto load_f = [&](long long t) {
+    const uint4* src = a.fd_tiles + (size_t)t * (kRows * 64 / 8);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fimg[j] = __ldg(src + tid + kThreads * j);
+  };
+  if (blockIdx.x < tiles) load_f(blockIdx.x);
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long base = tile * kRows;
-    // ---- F: 128 rows x 8 chunks of 8 features; 8 threads read one row's 256 bytes
-    for (int c = tid; c < 128 * 8; c += kThreads) {
-      const int r = c >> 3, k0 = (c & 7) * 8;
-      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (base + r < a.n) {
-        const float4* src = reinterpret_cast<const float4*>(a.fd + (size_t)(base + r) * kW + k0);
-        const float4 x = src[0], y = src[1];
-        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-      }
-      *reinterpret_cast<uint4*>(smem + kF + a_off(r, k0, 64)) = pack8(v);
-    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) reinterpret_cast<uint4*>(smem + kF)[tid + kThreads * j] = fimg[j];
     fence_async_smem();
     __syncthreads();
     // ---- D1 (cols 0..127) = F . [W_C1; W_a1]^T -> H = relu(D1 + b) in BF16
     if (tid == 0) {
       tc_fence_after();
       issue_gemm(tmem, 0, s_addr + kF, s_addr + kB1, 64, 128, mbar);
+    }
+    if (tile + gridDim.x < tiles) load_f(tile + gridDim.x);
+    // the canonical colours this thread will write, and its row's opacity logit, loaded
+    // while the GEMMs run
+    using V = typename std::conditional<kVec == 4, float4, float>::type;
+    V cs[kItems];
+    int gi[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int it = tid + kThreads * j, r = it / kPerRow, q = it % kPerRow;
+      const bool ok = it < kRows * kPerRow && base + r < a.n;
+      gi[j] = ok ? (a.perm ? (int)__ldg(a.perm + base + r) : (int)(base + r)) : -1;
+      if (ok) cs[j] = __ldg(reinterpret_cast<const V*>(a.sh + (size_t)gi[j] * K3) + q);
+    }
+    int g_row = -1;
+    float logit = 0.f;
+    if (tid < kRows && base + tid < a.n) {
+      g_row = a.perm ? (int)__ldg(a.perm + base + tid) : (int)(base + tid);
+      logit = __ldg(a.logits + g_row);
     }
     if (!mbar_wait(mbar, phase)) *sFail = 1;
     phase ^= 1;
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 2) color_tc_kernel(const ColorArgs a
     tc_fence_before();
     fence_async_smem();
     __syncthreads();
-    // ---- D2 (cols 128..191) = H . blockdiag(W_C2, W_a2)^T -> C', logit'
+    // ---- D2 (cols 128..191) = H . blockdiag(W_C2, W_a2)^T -> staged offsets
     if (tid == 0) {
       tc_fence_after();
       issue_gemm(tmem, 128, s_addr + kH, s_addr + kB2, 128, 64, mbar);
@@ -171,12 +184,30 @@ __global__ void __launch_bounds__(kThreads, 2) color_tc_kernel(const ColorArgs a
     {
       float v[32];
       tmem_ld32(tmem + lane_base + 128u + (uint32_t)(half * 32), v);
-      const long long i = base + row;
-      if (i < a.n) {
-        const int g = a.perm ? (int)a.perm[i] : (int)i;
-        write_outputs<K3>(a, g, half * 32, v, sBias + 128 + half * 32);
-      }
+      const float* b = sBias + 128 + half * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (half * 32 + j <= K3) sOut[row * kStride + half * 32 + j] = v[j] + b[j];
     }
+    __syncthreads();
+    // ---- C' = C + offset, whole rows per warp; logit' = logit + offset
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      if (gi[j] < 0) continue;
+      const int it = tid + kThreads * j, r = it / kPerRow, q = it % kPerRow;
+      const float* o = sOut + r * kStride + q * kVec;
+      V out = cs[j];
+      if constexpr (kVec == 4) {
+        out.x += o[0];
+        out.y += o[1];
+        out.z += o[2];
+        out.w += o[3];
+      } else {
+        out += o[0];
+      }
+      reinterpret_cast<V*>(a.sh_out + (size_t)gi[j] * K3)[q] = out;
+    }
+    if (g_row >= 0) a.logit_out[g_row] = logit + sOut[tid * kStride + K3];
     tc_fence_before();
     __syncthreads();
     if (*sFail) break;  // uniform: read after the barrier
@@ -204,7 +235,7 @@ cudaError_t launch_k(const ColorArgs& a, cudaStream_t s) {
 
 cudaError_t launch_color_heads_bf16(const ColorArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if ((reinterpret_cast<uintptr_t>(a.fd) & 15u) || (reinterpret_cast<uintptr_t>(a.sh) & 15u) ||
+  if (!a.fd_tiles || (reinterpret_cast<uintptr_t>(a.fd_tiles) & 15u) || (reinterpret_cast<uintptr_t>(a.sh) & 15u) ||
       (reinterpret_cast<uintptr_t>(a.sh_out) & 15u))
     return cudaErrorInvalidValue;
   switch (a.k3) {

@@ -92,8 +92,14 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   float4* sRowX = reinterpret_cast<float4*>(D + kDeltaDim * kGS);
   float4* sRowQ = sRowX + kTileG;
   float4* sRowS = sRowQ + kTileG;
-  for (int i = threadIdx.x; i < a.mg.total / 4; i += kThreads)
-    smem4[i] = __ldg(reinterpret_cast<const float4*>(a.mlp_t) + i);
+  // the weights by cp.async (every 16-byte copy in flight at once), waited for
+  // before the first tile's MLP below
+  for (int i = threadIdx.x; i < a.mg.total / 4; i += kThreads) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem4 + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(reinterpret_cast<const float4*>(a.mlp_t) + i)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   // the weights above are the scene's; the rows below may come from earlier work
   pdl_wait();
   pdl_trigger();
@@ -171,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
         dst[e * kGS] = v;
       }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // the weights (first tile; later a no-op)
     __syncthreads();
 
     // ---- 2. phi_d, in place in X

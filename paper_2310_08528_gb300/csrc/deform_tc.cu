@@ -15,6 +15,8 @@
 //   3. between GEMMs, 8 warps read the accumulator back with tcgen05.ld, add the
 //      bias, apply ReLU, round to BF16 and write the next A tile;
 //   4. the last epilogue adds dX, dr, ds to X, r, s (Eq. 6).
+// For scenes with colour and opacity heads (App. B) each tile's f_d operand image
+// (A3) is also copied out, whole, as the input of the heads' tensor-core kernel.
 // Every wait on the mbarrier is bounded; on a timeout the CTA records
 // kStatusTimeout, stops, frees its TMEM and returns.
 #include "tc_util.cuh"
@@ -93,8 +95,9 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
   float4* sRows = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(sMbar) + 16);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < tg.bytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(a.tc_ops)[i];
+  // the weights by cp.async: every 16-byte copy in flight at once
+  for (int i = tid; i < tg.bytes / 16; i += kThreads) cp_async(sB + 16 * i, a.tc_ops + 16 * i, 1);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int i = tid; i < kBiasFloats; i += kThreads) sBias[i] = a.tc_bias[i];
   const uint32_t mbar = smem_u32(sMbar);
   if (tid == 0) {
@@ -102,6 +105,7 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
     *sFail = 0;
   }
   if (warp == 0) tmem_alloc(smem_u32(sTmem), kTmemCols);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -221,14 +225,6 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
       float v[32];
       tmem_ld32(tmem + lane_base + 64u + (uint32_t)(half * 32), v);
       store_relu32(sX, row, half * 32, 64, v, sBias + 64 + half * 32);
-      if (a.fd_out && base + row < total) {  // f_d for the colour and opacity heads, work order
-        float4* dst = reinterpret_cast<float4*>(a.fd_out + (size_t)(base + row) * 64 + half * 32);
-        const float* b = sBias + 64 + half * 32;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          dst[j] = make_float4(fmaxf(v[4 * j] + b[4 * j], 0.f), fmaxf(v[4 * j + 1] + b[4 * j + 1], 0.f),
-                               fmaxf(v[4 * j + 2] + b[4 * j + 2], 0.f), fmaxf(v[4 * j + 3] + b[4 * j + 3], 0.f));
-      }
     }
     tc_fence_before();
     fence_async_smem();
@@ -238,6 +234,12 @@ __global__ void __launch_bounds__(kThreads, 2) deform_tc_kernel(DeformArgs a) {
     if (tid == 0) {
       tc_fence_after();
       issue_gemm(tmem, 0, x_addr, b_addr + tg.b3_off, 64, 192, mbar);
+    }
+    if (a.fd_tiles) {  // f_d as this tile's BF16 operand image (the colour heads' input), while D3 runs
+      const uint4* src = reinterpret_cast<const uint4*>(sX);
+      uint4* dst = a.fd_tiles + (size_t)tile * (kRows * 64 / 8);
+      for (int i = tid; i < kRows * 64 / 8; i += kThreads) dst[i] = src[i];
+      __syncthreads();  // every thread has read A3 before the epilogue below overwrites it
     }
     if (!mbar_wait(mbar, phase)) *sFail = 1;
     phase ^= 1;

@@ -137,14 +137,17 @@ struct DeformArgs {
   MlpGeomTC tg;
   PlaneGeom pg;
   uint32_t* status;
-  float* fd_out;                // optional [n][64]: f_d (after phi_d) in work order (n_t must be 1)
+  float* fd_out;                // FP32 kernel, optional [n][64]: f_d (after phi_d) in work order (n_t must be 1)
+  uint4* fd_tiles;              // BF16 kernel, optional: f_d of each tile of 128 work-order rows as its BF16
+                                // operand image (UMMA no-swizzle K-major, 16 KB per tile; n_t must be 1)
 };
 
 // Colour and opacity heads (App. B, color.cu): per Gaussian from f_d in work order.
 struct ColorArgs {
   int n;
   const uint32_t* perm;         // work order (NULL: index order)
-  const float* fd;              // [n][64] work order, 16-byte aligned
+  const float* fd;              // SIMT form: [n][64] work order, 16-byte aligned
+  const uint4* fd_tiles;        // tensor-core form: BF16 operand images, 16 KB per tile of 128 rows
   const float* weights;         // the four layers c1 c2 a1 a2 in the source layout (W[out][in] then b)
   int k3;                       // 3 x SH coefficients per channel
   const float* sh;              // [n][K][3] canonical
@@ -156,7 +159,7 @@ struct ColorArgs {
 int color_layer_floats(int k3);
 // float32 SIMT form (the FP32 path)
 cudaError_t launch_color_heads(const ColorArgs& a, cudaStream_t s);
-// BF16 tcgen05 form (the BF16 path): k3 in {3, 12, 27, 48}; fd, sh, sh_out 16-byte aligned
+// BF16 tcgen05 form (the BF16 path): k3 in {3, 12, 27, 48}; fd_tiles, sh, sh_out 16-byte aligned
 cudaError_t launch_color_heads_bf16(const ColorArgs& a, cudaStream_t s);
 
 struct CamParams {
