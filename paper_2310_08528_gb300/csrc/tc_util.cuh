@@ -46,6 +46,25 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// one arrival (release, CTA scope) on an mbarrier initialised with count 1
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// barrier `id` (1..15) of `n` threads (a multiple of 32): one warp group's __syncthreads
+__device__ __forceinline__ void group_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// group_sync that also ORs `pred` over the group: the same answer in every thread
+__device__ __forceinline__ bool group_sync_or(uint32_t id, uint32_t n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   for (uint32_t i = 0; i < kWaitLimit; ++i) {
     uint32_t done;
