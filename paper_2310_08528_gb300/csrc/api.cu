@@ -687,9 +687,11 @@ long long parts_total(const FramePart* parts, int n_parts) {
 // offset, and for a scene with them the colour and opacity heads (App. B) on the
 // f_d the deformation leaves.
 fs4d_status deform_part(fs4d_ctx* c, Work& w, const FramePart& q, fs4d_precision prec, const float* d_t, float t,
-                        cudaStream_t stream, uint32_t* status) {
+                        cudaStream_t stream, uint32_t* status, void* zero = nullptr, size_t zero_bytes = 0) {
   DeformArgs da = deform_args(q.s, d_t, t, 1, P<float>(w.dmeans) + 3 * q.off, P<float>(w.dquats) + 4 * q.off,
                               P<float>(w.dscales) + 3 * q.off);
+  da.zero = static_cast<uint4*>(zero);
+  da.zero_n16 = (long long)(zero_bytes / 16);
   // f_d: float32 rows from the FP32 kernel; BF16 tile images from the tensor-core kernel (a part's
   // images may run up to 16 KB past its 256 bytes per Gaussian, into the next part's share, which
   // is written only after this part's heads have read them; the buffer has 16 KB to spare)
@@ -733,13 +735,16 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
   frame_zero_layout(N, tx * ty, cap, sort_passes(tile_bits), static_cast<unsigned char*>(w.zero.p), &z);
   if (z.bytes > w.zero.bytes) return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory was not reserved");
   mark(e, 0);
-  FS4D_CUDA(c, cudaMemsetAsync(w.zero.p, 0, z.bytes, stream));
   for (int i = 0; i < n_parts; ++i)
     if (parts[i].s->color_heads && w.cap_color < N)
       return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory of the colour heads was not reserved");
+  // the first deformation kernel clears the frame's zeroed state (no memset of its own)
+  const bool fold = deform && n_parts > 0 && parts[0].s->n > 0 && z.bytes % 16 == 0;
+  if (!fold) FS4D_CUDA(c, cudaMemsetAsync(w.zero.p, 0, z.bytes, stream));
   if (deform) {
     for (int i = 0; i < n_parts; ++i) {
-      fs4d_status st = deform_part(c, w, parts[i], prec, d_t, t, stream, e.status);
+      fs4d_status st = deform_part(c, w, parts[i], prec, d_t, t, stream, e.status, i == 0 && fold ? w.zero.p : nullptr,
+                                   i == 0 && fold ? z.bytes : 0);
       if (st != FS4D_OK) return st;
     }
   }

@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(kThreads, 1) deform_fp32_kernel(DeformArgs a) 
   // the weights above are the scene's; the rows below may come from earlier work
   pdl_wait();
   pdl_trigger();
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.zero_n16; i += (long long)gridDim.x * kThreads)
+    a.zero[i] = make_uint4(0u, 0u, 0u, 0u);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g4 = lane * 4, o8 = warp * 8;

@@ -120,6 +120,8 @@ __global__ void __launch_bounds__(kThreads, 1) deform_tc_kernel(DeformArgs a) {
   // from earlier work on the stream
   pdl_wait();
   pdl_trigger();
+  for (long long i = (long long)blockIdx.x * kThreads + tid; i < a.zero_n16; i += (long long)gridDim.x * kThreads)
+    a.zero[i] = make_uint4(0u, 0u, 0u, 0u);
   const uint32_t tmem = *sTmem;
   const PlaneGeom& pg = a.pg;
   const long long total = (long long)a.n * a.n_t;

@@ -138,6 +138,8 @@ struct DeformArgs {
   PlaneGeom pg;
   uint32_t* status;
   float* fd_out;                // FP32 kernel, optional [n][64]: f_d (after phi_d) in work order (n_t must be 1)
+  uint4* zero;                  // optional: zero_n16 16-byte words the kernel sets to 0 (a frame's counters
+  long long zero_n16;           // and look-back tables, cleared here instead of by a separate memset)
   uint4* fd_tiles;              // BF16 kernel, optional: f_d of each tile of 128 work-order rows as its BF16
                                 // operand image (UMMA no-swizzle K-major, 16 KB per tile; n_t must be 1)
 };
