@@ -787,6 +787,7 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
   dsw.hist = z.hist; dsw.lookback = z.dlb; dsw.part_counters = z.counters + 8; dsw.max_parts = z.dparts;
   dsw.prezeroed = true;
   dsw.spin_limit = c->spin_limit;
+  dsw.grid_counter = z.counters + 56;  // (words 0..7 emission, 8..24 this sort, 32..48 the pair sort)
   FS4D_CUDA(c, launch_sort(P<unsigned long long>(w.dkeys), P<uint32_t>(w.dvals), P<unsigned long long>(w.dkeys_alt),
                            P<uint32_t>(w.dvals_alt), nullptr, N, 0, 32, true, dsw, e.status, stream, &dalt,
                            &dsel));

@@ -246,6 +246,8 @@ struct SortWork {
   long long max_parts;          // >= sort_parts(n_bound) lets every partition size be chosen
   bool prezeroed = false;       // tickets, selection words and look-back already zero
   uint32_t spin_limit = kSpinLimit;  // polls of a look-back wait before it gives up
+  uint32_t* grid_counter = nullptr;  // optional, zero (with prezeroed): lets a small sort with result_sel
+                                     // run every pass in one launch, its CTAs meeting at a grid barrier
 };
 
 // ---------------------------------------------------------------- launchers

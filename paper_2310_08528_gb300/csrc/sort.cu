@@ -108,46 +108,19 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp) {
   return base + incl - v;
 }
 
-// VALS = false: keys only (values_* unused); the key carries its payload.
+// One pass over partition `part` (elements [base, base + kThreads * ITEMS) of n):
+// rank the keys stably within the CTA, publish the digit counts, sort locally,
+// resolve the global offsets by decoupled look-back and scatter.  h = the
+// pass's global count of digit tid.  Every thread of the CTA calls it.
 template <int ITEMS, bool VALS>
-__global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
+__device__ __forceinline__ void onesweep_pass(PassSmem<ITEMS>& sm, const PassArgs& a, uint32_t part, long long base,
+                                              long long n, uint32_t h, const unsigned long long* keys_in,
+                                              const uint32_t* values_in, unsigned long long* keys_out,
+                                              uint32_t* values_out) {
   constexpr int kItems = ITEMS;
   constexpr int kPartPairs = kThreads * ITEMS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassSmem<ITEMS>& sm = *reinterpret_cast<PassSmem<ITEMS>*>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id(), warp = tid / 32;
-  pdl_wait();
-  pdl_trigger();
-  if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
-  // independent of the ticket: issued while it is in flight
-  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
-  const uint32_t h = a.hist[tid];
-  const bool in_b = a.sel_in && *a.sel_in;
-  const unsigned long long* keys_in = in_b ? a.keys_out : a.keys_in;
-  const uint32_t* values_in = in_b ? a.values_out : a.values_in;
-  unsigned long long* keys_out = in_b ? const_cast<unsigned long long*>(a.keys_in) : a.keys_out;
-  uint32_t* values_out = in_b ? const_cast<uint32_t*>(a.values_in) : a.values_out;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
-  __syncthreads();
-  const uint32_t part = sm.part;
-  const long long base = (long long)part * kPartPairs;
-  if (base >= n) return;  // uniform across the CTA
-  // A pass whose digit is the same for every key keeps the order: with a
-  // selection word it only records that the data stayed put, else it copies.
-  const bool trivial = __syncthreads_or((long long)h == n);
-  if (a.sel_out && part == 0 && tid == 0) *a.sel_out = (uint32_t)in_b ^ (trivial ? 0u : 1u);
-  if (trivial) {
-    if (a.sel_out) return;
-    const long long m = min((long long)kPartPairs, n - base);
-    for (long long i = tid; i < m; i += kThreads) {
-      keys_out[base + i] = keys_in[base + i];
-      if (VALS) values_out[base + i] = values_in[base + i];
-    }
-    return;
-  }
-
   // Global offset of each digit.
   sm.global_off[tid] = block_excl_scan(h, sm.scan_tmp);
 
@@ -255,6 +228,107 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
       if (VALS) values_out[out] = sm.values[j];
     }
   }
+}
+
+
+// VALS = false: keys only (values_* unused); the key carries its payload.
+template <int ITEMS, bool VALS>
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(PassArgs a) {
+  constexpr int kPartPairs = kThreads * ITEMS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem<ITEMS>& sm = *reinterpret_cast<PassSmem<ITEMS>*>(smem_raw);
+  const int tid = threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (tid == 0) sm.part = atomicAdd(a.part_counter, 1u);
+  // independent of the ticket: issued while it is in flight
+  const long long n = a.n_dev ? min((long long)*a.n_dev, a.n_bound) : a.n_bound;
+  const uint32_t h = a.hist[tid];
+  const bool in_b = a.sel_in && *a.sel_in;
+  const unsigned long long* keys_in = in_b ? a.keys_out : a.keys_in;
+  const uint32_t* values_in = in_b ? a.values_out : a.values_in;
+  unsigned long long* keys_out = in_b ? const_cast<unsigned long long*>(a.keys_in) : a.keys_out;
+  uint32_t* values_out = in_b ? const_cast<uint32_t*>(a.values_in) : a.values_out;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
+  __syncthreads();
+  const uint32_t part = sm.part;
+  const long long base = (long long)part * kPartPairs;
+  if (base >= n) return;  // uniform across the CTA
+  // A pass whose digit is the same for every key keeps the order: with a
+  // selection word it only records that the data stayed put, else it copies.
+  const bool trivial = __syncthreads_or((long long)h == n);
+  if (a.sel_out && part == 0 && tid == 0) *a.sel_out = (uint32_t)in_b ^ (trivial ? 0u : 1u);
+  if (trivial) {
+    if (a.sel_out) return;
+    const long long m = min((long long)kPartPairs, n - base);
+    for (long long i = tid; i < m; i += kThreads) {
+      keys_out[base + i] = keys_in[base + i];
+      if (VALS) values_out[base + i] = values_in[base + i];
+    }
+    return;
+  }
+
+  onesweep_pass<ITEMS, VALS>(sm, a, part, base, n, h, keys_in, values_in, keys_out, values_out);
+}
+
+// Grid-wide barrier of a kernel whose CTAs are all resident: arrival counter
+// (zero before the launch), bounded spin by thread 0 (on giving up it records
+// kStatusTimeout and lets the CTA go on).
+__device__ __forceinline__ void grid_sync(uint32_t* counter, uint32_t target, uint32_t* status, uint32_t spin_limit) {
+  __syncthreads();  // the CTA's stores of this pass are issued
+  if (threadIdx.x == 0) {
+    __threadfence();  // ... and visible device-wide before the arrival
+    atomicAdd(counter, 1u);
+    uint32_t spins = 0;
+    while (ld_relaxed_u32(counter) < target) {
+      if (++spins > spin_limit) {
+        atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Every pass of a sort small enough that all its 1024-key partitions are resident
+// at once (a frame's depth sort: 100k keys, 98 partitions) in one launch: CTA b owns
+// partition b in every pass and a grid barrier separates the passes, so the passes
+// need no further launch and no ticket.  A pass whose digit every key shares moves
+// nothing (the same decision in every CTA: it comes from the global histogram);
+// *a.sel_out records whether the result ended in the alternate buffers.
+__global__ void __launch_bounds__(kThreads) onesweep_fused_kernel(PassArgs a, int passes, int first_bit,
+                                                                  int key_bits, uint32_t* grid_counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem<kItemsSmall>& sm = *reinterpret_cast<PassSmem<kItemsSmall>*>(smem_raw);
+  const int tid = threadIdx.x;
+  pdl_wait();
+  pdl_trigger();  // (fires once every CTA of this grid runs: they are all resident)
+  const long long n = a.n_bound;
+  const uint32_t part = blockIdx.x;
+  const long long base = (long long)part * kPartPairsSmall;
+  uint32_t cur = 0, barriers = 0;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t h = a.hist[p * kRadix + tid];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sm.warp_cnt[w][tid] = 0;
+    if (__syncthreads_or((long long)h == n)) continue;  // trivial pass (uniform)
+    if (barriers > 0) grid_sync(grid_counter, barriers * gridDim.x, a.status, a.spin_limit);  // the last pass is out
+    PassArgs pa = a;
+    pa.shift = first_bit + 8 * p;
+    pa.bits = min(8, key_bits - 8 * p);
+    pa.lookback = a.lookback + (size_t)p * gridDim.x * kRadix;
+    const unsigned long long* kin = cur ? a.keys_out : a.keys_in;
+    const uint32_t* vin = cur ? a.values_out : a.values_in;
+    unsigned long long* kout = cur ? const_cast<unsigned long long*>(a.keys_in) : a.keys_out;
+    uint32_t* vout = cur ? const_cast<uint32_t*>(a.values_in) : a.values_out;
+    onesweep_pass<kItemsSmall, true>(sm, pa, part, base, n, h, kin, vin, kout, vout);
+    cur ^= 1u;
+    ++barriers;
+  }
+  if (part == 0 && tid == 0) *a.sel_out = cur;
 }
 
 // ---------------------------------------------------------------- large sorts
@@ -531,6 +605,37 @@ cudaError_t launch_sort(unsigned long long* keys, uint32_t* values, unsigned lon
   unsigned long long* kout = keys_alt;
   uint32_t* vout = values_alt;
   uint32_t* sel = result_sel ? work.part_counters + kMaxPasses : nullptr;
+  // every pass in one launch when all the partitions fit on the GPU at once
+  if (small && !n_dev && sel && values && work.prezeroed && work.grid_counter) {
+    static std::atomic<int> per_sm[kMaxDevices] = {};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int fit = per_sm[dev].load(std::memory_order_relaxed);
+    if (fit <= 0) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, onesweep_fused_kernel, kThreads,
+                                                         sizeof(PassSmem<kItemsSmall>));
+      if (e != cudaSuccess) return e;
+      per_sm[dev].store(std::max(fit, 1), std::memory_order_relaxed);
+    }
+    // (half of what fits, so that a kernel still running beside it cannot keep a partition out)
+    if (parts * 2 <= (long long)fit * device_sm_count()) {
+      PassArgs pa{};
+      pa.keys_in = keys; pa.values_in = values; pa.keys_out = keys_alt; pa.values_out = values_alt;
+      pa.sel_out = sel;
+      pa.n_bound = n_bound;
+      pa.hist = work.hist;
+      pa.lookback = work.lookback;
+      pa.status = status;
+      pa.spin_limit = work.spin_limit;
+      e = launch_pdl(onesweep_fused_kernel, (unsigned)parts, kThreads, sizeof(PassSmem<kItemsSmall>), s, pa, passes,
+                     first_bit, key_bits, work.grid_counter);
+      if (e != cudaSuccess) return e;
+      *result_sel = sel;
+      return cudaSuccess;
+    }
+  }
   // large sorts without device-side buffer selection: the persistent, prefetching pass
   const bool persist = !small && !sel;
   int persist_grid = 0;
