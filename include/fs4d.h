@@ -283,6 +283,11 @@ FS4D_API fs4d_status fs4d_frame_free(fs4d_ctx* ctx, fs4d_frame* frame);
  * {alpha >= 1/255} reaches, which leaves the image unchanged and their lists shorter). */
 FS4D_API fs4d_status fs4d_frame_pairs(const fs4d_frame* frame, int64_t* pairs);
 FS4D_API fs4d_status fs4d_last_pairs(const fs4d_ctx* ctx, int64_t* pairs);
+/* Number of kernels the last fs4d_render or fs4d_render_async call on the context
+ * launched from the calling thread (memsets and copies not counted; a frame captured
+ * into a graph launches the same kernels on every replay).  FS4D_ERR_INVALID_ARG on
+ * NULL arguments. */
+FS4D_API fs4d_status fs4d_last_launches(const fs4d_ctx* ctx, int64_t* launches);
 /* Number of bands of tile rows the last fs4d_render / fs4d_render_host frame on the
  * context was rendered in (1 unless its pairs exceeded one pair-sort pass). */
 FS4D_API fs4d_status fs4d_last_bands(const fs4d_ctx* ctx, int32_t* bands);

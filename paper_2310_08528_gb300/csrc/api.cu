@@ -22,6 +22,10 @@
 
 #include "fs4d_internal.cuh"
 
+namespace fs4d {
+thread_local unsigned long long g_kernel_launches = 0;
+}  // namespace fs4d
+
 using namespace fs4d;
 
 namespace {
@@ -244,6 +248,7 @@ struct fs4d_ctx {
   int band_scene = -1, band_w = 0, band_h = 0, band_hint = 0;  // bands the last such frame used
   std::vector<std::pair<int, int>> band_rows;  // ... and their tile rows (the next frame reuses them)
   int last_bands = 1;
+  long long last_launches = 0;  // kernels the last fs4d_render / fs4d_render_async call launched
   long long band_pairs = (1ll << 30) - 1;  // most pairs one band may hold (fs4d_set_band_pairs)
   float stage_acc[6] = {};                // stage times summed over a banded frame's passes
   bool stage_acc_valid = false;
@@ -1351,7 +1356,8 @@ fs4d_status fs4d_deform(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, cons
   return run_deform(c, s, prec, a);
 }
 
-fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
+namespace {
+fs4d_status render_impl(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
                         float* d_image, float* d_t_final, int32_t* d_n_contrib, fs4d_frame** saved) {
   if (!c) return FS4D_ERR_INVALID_ARG;
   if (!valid_cam(cam) || !d_image) return fail(c, FS4D_ERR_INVALID_ARG, "render: camera and image are required");
@@ -1378,6 +1384,15 @@ fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, cons
   }
   *saved = f;
   return FS4D_OK;
+}
+}  // namespace
+
+fs4d_status fs4d_render(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* cam, float t,
+                        float* d_image, float* d_t_final, int32_t* d_n_contrib, fs4d_frame** saved) {
+  const unsigned long long before = g_kernel_launches;
+  const fs4d_status st = render_impl(c, id, prec, cam, t, d_image, d_t_final, d_n_contrib, saved);
+  if (c) c->last_launches = (long long)(g_kernel_launches - before);
+  return st;
 }
 
 fs4d_status fs4d_render_composed(fs4d_ctx* c, const fs4d_scene_id* ids, const float* h_shifts, int32_t n_scenes,
@@ -1543,7 +1558,8 @@ fs4d_status fs4d_reserve(fs4d_ctx* c, fs4d_scene_id id, int32_t width, int32_t h
   return FS4D_OK;
 }
 
-fs4d_status fs4d_render_async(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* shape,
+namespace {
+fs4d_status render_async_impl(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* shape,
                               const fs4d_camera* d_cam, const float* d_t, float* d_image) {
   if (!c) return FS4D_ERR_INVALID_ARG;
   if (!valid_cam(shape) || !d_cam || !d_t || !d_image)
@@ -1559,6 +1575,15 @@ fs4d_status fs4d_render_async(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec
   st = frame_front(c, s, prec, *shape, d_cam, d_t, 0.f, cap, true, false, true);
   if (st != FS4D_OK) return st;
   return frame_back(c, *shape, cap, d_image, nullptr, nullptr);
+}
+}  // namespace
+
+fs4d_status fs4d_render_async(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec, const fs4d_camera* shape,
+                              const fs4d_camera* d_cam, const float* d_t, float* d_image) {
+  const unsigned long long before = g_kernel_launches;
+  const fs4d_status st = render_async_impl(c, id, prec, shape, d_cam, d_t, d_image);
+  if (c) c->last_launches = (long long)(g_kernel_launches - before);
+  return st;
 }
 
 fs4d_status fs4d_set_stage_timing(fs4d_ctx* c, int32_t enable) {
@@ -1795,6 +1820,12 @@ fs4d_status fs4d_set_band_pairs(fs4d_ctx* c, int64_t max_pairs) {
 fs4d_status fs4d_last_bands(const fs4d_ctx* c, int32_t* bands) {
   if (!c || !bands) return FS4D_ERR_INVALID_ARG;
   *bands = c->last_bands;
+  return FS4D_OK;
+}
+
+fs4d_status fs4d_last_launches(const fs4d_ctx* c, int64_t* launches) {
+  if (!c || !launches) return FS4D_ERR_INVALID_ARG;
+  *launches = c->last_launches;
   return FS4D_OK;
 }
 

@@ -36,9 +36,14 @@ constexpr uint32_t kStatusCapacity = 2u;  // more tile pairs than buffer capacit
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Kernel launches issued through launch_pdl by the calling thread (the frame
+// kernels all are): the render entry points report a frame's count from it.
+extern thread_local unsigned long long g_kernel_launches;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                               Args... args) {
+  ++g_kernel_launches;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);

@@ -25,7 +25,7 @@ STATUS = {0: "FS4D_OK", 1: "FS4D_ERR_INVALID_ARG", 2: "FS4D_ERR_OOM", 3: "FS4D_E
 EXPORTS = ("fs4d_create", "fs4d_destroy", "fs4d_last_error", "fs4d_set_stream", "fs4d_check_device_status",
            "fs4d_load_scene", "fs4d_unload_scene", "fs4d_update_scene", "fs4d_scene_bytes", "fs4d_deform", "fs4d_render",
            "fs4d_render_host", "fs4d_render_host_batch", "fs4d_reserve", "fs4d_render_async", "fs4d_render_backward", "fs4d_frame_free",
-           "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
+           "fs4d_frame_pairs", "fs4d_last_pairs", "fs4d_last_launches", "fs4d_set_binning", "fs4d_last_binning", "fs4d_set_stage_timing", "fs4d_stage_times", "fs4d_project",
            "fs4d_bin_sort", "fs4d_sort_pairs", "fs4d_sort_pairs_noalloc", "fs4d_sort_pairs_noalloc_status",
            "fs4d_composite", "fs4d_set_wait_limit", "fs4d_last_bands", "fs4d_set_band_pairs",
            "fs4d_train_create", "fs4d_train_step", "fs4d_train_losses", "fs4d_train_steps_done",
@@ -134,6 +134,7 @@ def library(path: str = LIB_PATH):
         "fs4d_frame_free": [vp, vp],
         "fs4d_frame_pairs": [vp, C.POINTER(i64)],
         "fs4d_last_pairs": [vp, C.POINTER(i64)],
+        "fs4d_last_launches": [vp, C.POINTER(i64)],
         "fs4d_last_bands": [vp, C.POINTER(i32)],
         "fs4d_train_create": [vp, i32, C.POINTER(TrainConfig), C.POINTER(vp)],
         "fs4d_train_step": [vp, i32, C.POINTER(Camera), f32, vp, vp],
@@ -454,6 +455,12 @@ class Context:
     def last_pairs(self) -> int:
         k = C.c_int64()
         self.call("fs4d_last_pairs", C.byref(k))
+        return k.value
+
+    def last_launches(self) -> int:
+        """Kernels the last render / render_async call launched."""
+        k = C.c_int64()
+        self.call("fs4d_last_launches", C.byref(k))
         return k.value
 
     def last_bands(self) -> int:
