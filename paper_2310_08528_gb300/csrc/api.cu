@@ -1572,6 +1572,7 @@ fs4d_status render_async_impl(fs4d_ctx* c, fs4d_scene_id id, fs4d_precision prec
     return fail(c, FS4D_ERR_INVALID_ARG, "render_async: call fs4d_reserve for this scene and size first");
   DeviceGuard g(c->device);
   const long long cap = s->reserved_pairs;
+  c->stage_acc_valid = false;  // (a banded frame's sums no longer describe the last frame)
   st = frame_front(c, s, prec, *shape, d_cam, d_t, 0.f, cap, true, false, true);
   if (st != FS4D_OK) return st;
   return frame_back(c, *shape, cap, d_image, nullptr, nullptr);

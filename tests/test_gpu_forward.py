@@ -236,6 +236,27 @@ def test_sort_pairs_matches_stable_numpy(ctx, n, bits):
     assert np.array_equal(tv.cpu().numpy().view(np.uint32), vals[order])
 
 
+@pytest.mark.parametrize("binning", ["auto", "sort"])
+def test_last_launches_counts_the_frame_kernels(ctx, binning):
+    """fs4d_last_launches: deform, project, the depth sort in one launch (its 1024-key
+    partitions all fit at once), then mark, tile scan, extract (bitmap) or emission,
+    tile scan and the pair-sort passes on the tile bits (sort), then composite."""
+    s = sg.make_tiny(41, n=3000)
+    cam = sg.tiny_camera(200, 136)
+    sid = ctx.load_scene(s)
+    try:
+        ctx.set_binning(fs4d.BINNING_SORT if binning == "sort" else fs4d.BINNING_AUTO)
+        ctx.render(sid, cam, 0.5)
+        torch.cuda.synchronize()
+        tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+        passes = (int(np.ceil(np.log2(tiles))) + 7) // 8
+        want = 7 if ctx.last_binning() == fs4d.BINNING_BITMAP else 6 + passes
+        assert ctx.last_launches() == want
+    finally:
+        ctx.set_binning(fs4d.BINNING_AUTO)
+        ctx.unload_scene(sid)
+
+
 @pytest.mark.parametrize("n", [5, 100000, 131072])
 def test_sort_depth_keys_and_constant_digits(ctx, n):
     """Depth-like keys (float32 bits of depths in [2, 4): the top byte is the same

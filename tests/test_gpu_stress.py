@@ -59,8 +59,17 @@ def test_banded_frame_matches_oracle(ctx):
         ctx.set_stage_timing(True)
         ctx.render(sid, cam, 0.4)
         st = ctx.stage_times()
-        ctx.set_stage_timing(False)
         assert all(v > 0 for v in st.values()), st
+        # a frame after the banded one reports its own stage times, not the bands' sums
+        ctx.set_band_pairs(0)
+        shape = fs4d.camera_struct(cam)
+        d_cam = torch.from_numpy(np.frombuffer(bytes(shape), dtype=np.float32).copy()).cuda()
+        d_t = torch.full((1,), 0.4, device="cuda")
+        ctx.reserve(sid, cam.width, cam.height, K + 4096)
+        ctx.render_async(sid, cam, d_cam, d_t, torch.empty((cam.height, cam.width, 3), device="cuda"))
+        st1 = ctx.stage_times()
+        ctx.set_stage_timing(False)
+        assert st1 != st and all(v >= 0 for v in st1.values()), (st, st1)
         with pytest.raises(fs4d.Fs4dError) as e:
             ctx.render_saved(sid, cam, 0.4)
         assert e.value.status == 3
