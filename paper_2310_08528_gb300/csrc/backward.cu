@@ -1060,9 +1060,16 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
   const long long n = wa.n;
   const int O = ly.O, I = ly.I;
   float* __restrict__ partial = wa.partial + ly.part_off;
-  __shared__ __align__(16) float sD[kWStage][64];
-  __shared__ __align__(16) float sX[kWStage][100];
-  __shared__ float sRed[256][20];
+  // two stages of D [kWStage][64] and X [kWStage][96] (the next one loading by
+  // cp.async while this one is multiplied); rows padded to 68 and 100 floats, so that
+  // a warp's transposing stores (one Gaussian per lane) spread over 8 banks, not 1;
+  // after the loop the same memory holds the slices' sums
+  constexpr int kDS = 68, kXS = 100;
+  __shared__ __align__(16) float sBuf[2 * kWStage * kDS + 2 * kWStage * kXS];
+  float (*sD)[kWStage][kDS] = reinterpret_cast<float (*)[kWStage][kDS]>(sBuf);
+  float (*sX)[kWStage][kXS] = reinterpret_cast<float (*)[kWStage][kXS]>(sBuf + 2 * kWStage * kDS);
+  float (*sRed)[20] = reinterpret_cast<float (*)[20]>(sBuf);
+  static_assert(256 * 20 <= 2 * kWStage * kDS + 2 * kWStage * kXS, "slice sums fit in the stage buffers");
   const int E = O * I + O;
   const int IB = I / 4, OB = (O + 3) / 4, NB = OB * IB;
   const int ks = NB >= 256 ? 1 : 256 / NB;  // slices of the staged Gaussians
@@ -1077,16 +1084,43 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
 #pragma unroll
     for (int k = 0; k < 4; ++k) bacc[b][k] = 0.f;
   }
-  for (long long b0 = n0; b0 < n1; b0 += kWStage) {
+  // one stage into buffer `buf`: 4-byte copies (the arrays are transposed on the way)
+  auto stage = [&](int buf, long long b0) {
     const int m = (int)min((long long)kWStage, n1 - b0);
-    __syncthreads();
     for (int t = threadIdx.x; t < kWStage * 64; t += 256) {
       const int o = t / kWStage, j = t % kWStage;
-      sD[j][o] = (j < m && o < O) ? D[(long long)o * n + b0 + j] : 0.f;
+      float* dst = &sD[buf][j][o];
+      if (j < m && o < O) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(D + (long long)o * n + b0 + j)
+                     : "memory");
+      } else {
+        *dst = 0.f;
+      }
     }
     for (int t = threadIdx.x; t < kWStage * I; t += 256) {
       const int i = t / kWStage, j = t % kWStage;
-      sX[j][i] = j < m ? X[(long long)i * n + b0 + j] : 0.f;
+      float* dst = &sX[buf][j][i];
+      if (j < m) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(X + (long long)i * n + b0 + j)
+                     : "memory");
+      } else {
+        *dst = 0.f;
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (n0 < n1) stage(0, n0);
+  int buf = 0;
+  for (long long b0 = n0; b0 < n1; b0 += kWStage, buf ^= 1) {
+    // the next stage into the other buffer (last read by the previous step, before its
+    // closing barrier), then wait for this one
+    if (b0 + kWStage < n1) {
+      stage(buf ^ 1, b0 + kWStage);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
     if (slice < ks) {
@@ -1098,8 +1132,8 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
         float* a = acc[b];
 #pragma unroll 4
         for (int j = slice; j < kWStage; j += ks) {
-          const float4 d4 = *reinterpret_cast<const float4*>(&sD[j][4 * ob]);
-          const float4 x4 = *reinterpret_cast<const float4*>(&sX[j][4 * ib]);
+          const float4 d4 = *reinterpret_cast<const float4*>(&sD[buf][j][4 * ob]);
+          const float4 x4 = *reinterpret_cast<const float4*>(&sX[buf][j][4 * ib]);
           const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
           for (int r = 0; r < 4; ++r)
@@ -1111,6 +1145,7 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
         }
       }
     }
+    __syncthreads();  // this buffer is refilled two steps on
   }
   if (ks > 1) {  // add the slices up: slice 0 of each block collects the others
     __syncthreads();
