@@ -59,8 +59,15 @@ def test_banded_frame_matches_oracle(ctx):
         ctx.set_stage_timing(True)
         ctx.render(sid, cam, 0.4)
         st = ctx.stage_times()
+        ctx.set_stage_timing(False)
         assert all(v > 0 for v in st.values()), st
+        with pytest.raises(fs4d.Fs4dError) as e:
+            ctx.render_saved(sid, cam, 0.4)
+        assert e.value.status == 3
         # a frame after the banded one reports its own stage times, not the bands' sums
+        ctx.set_stage_timing(True)
+        ctx.render(sid, cam, 0.4)
+        st = ctx.stage_times()
         ctx.set_band_pairs(0)
         shape = fs4d.camera_struct(cam)
         d_cam = torch.from_numpy(np.frombuffer(bytes(shape), dtype=np.float32).copy()).cuda()
@@ -70,9 +77,6 @@ def test_banded_frame_matches_oracle(ctx):
         st1 = ctx.stage_times()
         ctx.set_stage_timing(False)
         assert st1 != st and all(v >= 0 for v in st1.values()), (st, st1)
-        with pytest.raises(fs4d.Fs4dError) as e:
-            ctx.render_saved(sid, cam, 0.4)
-        assert e.value.status == 3
         fr = parity.oracle_frame(s, cam, 0.4)
         stt = parity.check_frame(img.cpu().numpy(), fr, T.cpu().numpy(), nc.cpu().numpy(), tol=IMG_TOL,
                                  px_tol=5e-4)
