@@ -10,7 +10,8 @@
 //        D1 = A1 . W_d1^T  (N 64)            f_h  -> hidden
 //        D2 = A2 . W_d2^T  (N 64)            hidden -> f_d
 //        D3 = A3 . [W_x1; W_r1; W_s1]^T (N 192)  three head hidden layers at once
-//        D4 = A4 . blockdiag(W_x2, W_r2, W_s2)^T (N 16, 10 used)
+//        D4 = A4 . blockdiag(W_x2, W_r2, W_s2)^T (N 16, 10 used; one GEMM per head over its
+//             own 64 columns of A4)
 //      one elected thread issues each GEMM and commits it to an mbarrier;
 //   3. between GEMMs, 8 warps read the accumulator back with tcgen05.ld, add the
 //      bias, apply ReLU, round to BF16 and write the next A tile;
@@ -277,17 +278,27 @@ __global__ void __launch_bounds__(kThreads, 1) deform_tc_kernel(DeformArgs a) {
       fence_async_smem();
       group_sync(2, kConsThreads);
 
-      // ---- heads, output layers: D4 (cols 192..207) = A4 . blockdiag(W_x2, W_r2, W_s2)^T
+      // ---- heads, output layers: A4 . blockdiag(W_x2, W_r2, W_s2)^T as three GEMMs over the
+      // heads' own 64 columns of A4 (cols 192, 208, 224): three independent chains of 4 MMAs
+      // instead of one of 12; the block-diagonal zeros made the other heads' terms exact zeros
       if (ct == 0) {
         tc_fence_after();
-        issue_gemm(tmem, 192, x_addr, b_addr + tg.b4_off, 192, 16, mma_bar);
+#pragma unroll
+        for (int h = 0; h < 3; ++h) issue_mmas(tmem, 192 + 16 * h, x_addr, b_addr + tg.b4_off, 192, 64 * h, 64, 16);
+        mma_commit(mma_bar);
       }
       if (!mbar_wait(mma_bar, phase)) *fail = 1;
       phase ^= 1;
       tc_fence_after();
       if (cw < 4) {
-        float v[16];
+        float v[16], vr[16], vs[16];
         tmem_ld16(tmem + lane_base + 192u, v);
+        tmem_ld16(tmem + lane_base + 208u, vr);
+        tmem_ld16(tmem + lane_base + 224u, vs);
+#pragma unroll
+        for (int j = 3; j < 7; ++j) v[j] = vr[j];
+#pragma unroll
+        for (int j = 7; j < 10; ++j) v[j] = vs[j];
         const long long gi = base + row;
         if (gi < total) {
           const float4* sRowX = sRows + 3 * kRows * rs;

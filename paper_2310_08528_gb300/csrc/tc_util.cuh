@@ -142,16 +142,24 @@ __device__ __forceinline__ void store_relu32(uint8_t* tile, int r, int k0, int K
   }
 }
 
+// The MMAs of a GEMM over columns [k0, k0 + kn) of two K-major operands with K
+// columns (k0, kn multiples of 16) into TMEM column `col`; no commit.
+__device__ __forceinline__ void issue_mmas(uint32_t tmem, int col, uint32_t a_addr, uint32_t b_addr, int K, int k0,
+                                           int kn, int N) {
+  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+  const uint32_t id = idesc_bf16(kTcRows, N);
+  for (int kk = 0; kk < kn / 16; ++kk) {
+    const uint32_t off = 256u * (uint32_t)(k0 / 16 + kk);
+    const uint64_t da = smem_desc(a_addr + off, 128u, sbo);
+    const uint64_t db = smem_desc(b_addr + off, 128u, sbo);
+    mma(tmem + (uint32_t)col, da, db, id, kk > 0 ? 1u : 0u);
+  }
+}
+
 // One GEMM of K columns into TMEM column `col`: K/16 MMAs, then a commit.
 __device__ __forceinline__ void issue_gemm(uint32_t tmem, int col, uint32_t a_addr, uint32_t b_addr, int K, int N,
                                            uint32_t mbar) {
-  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-  const uint32_t id = idesc_bf16(kTcRows, N);
-  for (int kk = 0; kk < K / 16; ++kk) {
-    const uint64_t da = smem_desc(a_addr + 256u * kk, 128u, sbo);
-    const uint64_t db = smem_desc(b_addr + 256u * kk, 128u, sbo);
-    mma(tmem + (uint32_t)col, da, db, id, kk > 0 ? 1u : 0u);
-  }
+  issue_mmas(tmem, col, a_addr, b_addr, K, 0, K, N);
   mma_commit(mbar);
 }
 
