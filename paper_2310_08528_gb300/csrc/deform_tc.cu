@@ -1,25 +1,29 @@
 // Gaussian deformation field, BF16 tensor-core path (Sec. 4.2, Eq. 5, Eq. 6).
 //
-// Persistent CTAs of 256 threads, each owning 256 TMEM columns, walk tiles of
-// 128 (timestamp, Gaussian) rows:
-//   1. sampling: 256 threads take (row, level) items; each interpolates the six
-//      BF16 planes of its level bilinearly in FP32, multiplies them (Eq. 5) and
-//      stores its h features as BF16 straight into the A operand tile in shared
-//      memory (UMMA canonical no-swizzle K-major layout);
-//   2. four GEMMs on tcgen05 (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128):
+// One persistent CTA of 512 threads per SM, holding 256 TMEM columns, walks tiles of
+// 128 (timestamp, Gaussian) rows with two warp groups:
+//   1. samplers (warps 0-7): fetch each tile's rows one tile ahead (cp.async), then
+//      take (row, level) items; each interpolates the six BF16 planes of its level
+//      bilinearly in FP32, multiplies them (Eq. 5) and stores its h features as BF16
+//      straight into the A operand tile -- one slot of a two-slot ring in shared
+//      memory (UMMA canonical no-swizzle K-major layout) -- and marks the slot full
+//      on its mbarrier;
+//   2. consumers (warps 8-15) wait for the slot, then run four GEMMs on tcgen05
+//      (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128):
 //        D1 = A1 . W_d1^T  (N 64)            f_h  -> hidden
 //        D2 = A2 . W_d2^T  (N 64)            hidden -> f_d
 //        D3 = A3 . [W_x1; W_r1; W_s1]^T (N 192)  three head hidden layers at once
 //        D4 = A4 . blockdiag(W_x2, W_r2, W_s2)^T (N 16, 10 used; one GEMM per head over its
 //             own 64 columns of A4)
-//      one elected thread issues each GEMM and commits it to an mbarrier;
-//   3. between GEMMs, 8 warps read the accumulator back with tcgen05.ld, add the
-//      bias, apply ReLU, round to BF16 and write the next A tile;
-//   4. the last epilogue adds dX, dr, ds to X, r, s (Eq. 6).
+//      one elected thread issues each GEMM and commits it to an mbarrier; between
+//      GEMMs the consumers read the accumulator back with tcgen05.ld, add the bias,
+//      apply ReLU, round to BF16 and write the next A tile; the last epilogue adds
+//      dX, dr, ds to X, r, s (Eq. 6), and the slot is marked empty for the samplers.
 // For scenes with colour and opacity heads (App. B) each tile's f_d operand image
 // (A3) is also copied out, whole, as the input of the heads' tensor-core kernel.
-// Every wait on the mbarrier is bounded; on a timeout the CTA records
-// kStatusTimeout, stops, frees its TMEM and returns.
+// Every wait on an mbarrier is bounded; on a timeout the group records
+// kStatusTimeout, both groups leave their loops on the same decision (a barrier
+// reduction), the CTA frees its TMEM and returns.
 #include "tc_util.cuh"
 
 namespace fs4d {
