@@ -6,10 +6,13 @@
 //    peers per digit, warp offsets chained through shared memory), publishes its
 //    per-digit counts and resolves its global per-digit offsets by decoupled
 //    look-back on its predecessors, then scatters through shared memory so that
-//    runs of equal digits are written contiguously.
+//    runs of equal digits are written contiguously;
+//  - or, for a sort whose 1024-key partitions are all resident at once (a frame's
+//    depth sort of up to ~150k keys), every pass in one launch: CTA b owns
+//    partition b in every pass and a bounded grid barrier separates the passes.
 // Only the key bits that can differ are sorted.  A frame sorts the N float32
-// depths (32 bits in 4 passes; a pass whose digit is the same for every key exits
-// at once) and, on the key-emission route, the pairs on their tile bits only (the
+// depths (32 bits in 4 passes; a pass whose digit is the same for every key moves
+// nothing) and, on the key-emission route, the pairs on their tile bits only (the
 // pairs are emitted in depth order, so 2500 tiles sort 12 bits in 2 passes).
 #include <algorithm>
 
