@@ -728,31 +728,58 @@ __device__ __forceinline__ void t_fwd(const float* __restrict__ Wt, int ldw, con
   for (int o = 0; o < 4; ++o)
 #pragma unroll
     for (int g = 0; g < 4; ++g) acc[g][o] = b[o4 + o];
+  float2 a2[4][2];  // outputs in pairs: one f32x2 FMA per two (each element the same FP32 FMA)
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    a2[g][0] = make_float2(acc[g][0], acc[g][1]);
+    a2[g][1] = make_float2(acc[g][2], acc[g][3]);
+  }
 #pragma unroll 4
   for (int i = 0; i < IN; ++i) {
     const float4 x = *reinterpret_cast<const float4*>(src + i * kTS + g4);
     const float4 w = *reinterpret_cast<const float4*>(Wt + i * ldw + o4);
-    const float xs[4] = {x.x, x.y, x.z, x.w}, ws[4] = {w.x, w.y, w.z, w.w};
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+    const float2 w01 = make_float2(w.x, w.y), w23 = make_float2(w.z, w.w);
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
+    for (int g = 0; g < 4; ++g) {
+      const float2 xg = make_float2(xs[g], xs[g]);
+      a2[g][0] = __ffma2_rn(w01, xg, a2[g][0]);
+      a2[g][1] = __ffma2_rn(w23, xg, a2[g][1]);
+    }
+  }
 #pragma unroll
-      for (int o = 0; o < 4; ++o) acc[g][o] = fmaf(ws[o], xs[g], acc[g][o]);
+  for (int g = 0; g < 4; ++g) {
+    acc[g][0] = a2[g][0].x; acc[g][1] = a2[g][0].y;
+    acc[g][2] = a2[g][1].x; acc[g][3] = a2[g][1].y;
   }
 }
 
 // acc[g][i] += sum_{o < nout} Wt[(i4 + i) * ldw + o] d[o][g4 + g]  (the transposed layer)
 __device__ __forceinline__ void t_bwd(const float* __restrict__ Wt, int ldw, const float* __restrict__ d, int nout,
                                       int g4, int i4, float (&acc)[4][4]) {
+  float2 a2[4][2];  // inputs in pairs: one f32x2 FMA per two (each element the same FP32 FMA)
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    a2[g][0] = make_float2(acc[g][0], acc[g][1]);
+    a2[g][1] = make_float2(acc[g][2], acc[g][3]);
+  }
 #pragma unroll 4
   for (int o = 0; o < nout; ++o) {
     const float4 x = *reinterpret_cast<const float4*>(d + o * kTS + g4);
-    const float ws[4] = {Wt[(i4 + 0) * ldw + o], Wt[(i4 + 1) * ldw + o], Wt[(i4 + 2) * ldw + o],
-                         Wt[(i4 + 3) * ldw + o]};
+    const float2 w01 = make_float2(Wt[(i4 + 0) * ldw + o], Wt[(i4 + 1) * ldw + o]),
+                 w23 = make_float2(Wt[(i4 + 2) * ldw + o], Wt[(i4 + 3) * ldw + o]);
     const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
+    for (int g = 0; g < 4; ++g) {
+      const float2 xg = make_float2(xs[g], xs[g]);
+      a2[g][0] = __ffma2_rn(w01, xg, a2[g][0]);
+      a2[g][1] = __ffma2_rn(w23, xg, a2[g][1]);
+    }
+  }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) acc[g][i] = fmaf(ws[i], xs[g], acc[g][i]);
+  for (int g = 0; g < 4; ++g) {
+    acc[g][0] = a2[g][0].x; acc[g][1] = a2[g][0].y;
+    acc[g][2] = a2[g][1].x; acc[g][3] = a2[g][1].y;
   }
 }
 
@@ -1134,11 +1161,16 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
         for (int j = slice; j < kWStage; j += ks) {
           const float4 d4 = *reinterpret_cast<const float4*>(&sD[buf][j][4 * ob]);
           const float4 x4 = *reinterpret_cast<const float4*>(&sX[buf][j][4 * ib]);
-          const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+          const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+          const float2 x01 = make_float2(x4.x, x4.y), x23 = make_float2(x4.z, x4.w);
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) a[4 * r + c] = fmaf(dv[r], xv[c], a[4 * r + c]);
+          for (int r = 0; r < 4; ++r) {  // column pairs: one f32x2 FMA per two (the same FP32 FMAs)
+            const float2 dr = make_float2(dv[r], dv[r]);
+            float2 p0 = make_float2(a[4 * r], a[4 * r + 1]), p1 = make_float2(a[4 * r + 2], a[4 * r + 3]);
+            p0 = __ffma2_rn(dr, x01, p0);
+            p1 = __ffma2_rn(dr, x23, p1);
+            a[4 * r] = p0.x; a[4 * r + 1] = p0.y; a[4 * r + 2] = p1.x; a[4 * r + 3] = p1.y;
+          }
           if (ib == 0)
 #pragma unroll
             for (int r = 0; r < 4; ++r) bacc[b][r] += dv[r];

@@ -44,18 +44,34 @@ __device__ __forceinline__ void layer64(const float* __restrict__ Wt, const floa
 #pragma unroll
     for (int g = 0; g < 4; ++g) acc[g][o] = bo;
   }
+  // outputs in pairs: one f32x2 FMA per two outputs (each element the same FP32 FMA)
+  float2 a2[4][4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int o = 0; o < 4; ++o) a2[g][o] = make_float2(acc[g][2 * o], acc[g][2 * o + 1]);
 #pragma unroll 4
   for (int i = 0; i < IN; ++i) {
     const float4 x = *reinterpret_cast<const float4*>(src + i * kGS + g4);
     const float4 w0 = *reinterpret_cast<const float4*>(Wt + i * kWidth + o8);
     const float4 w1 = *reinterpret_cast<const float4*>(Wt + i * kWidth + o8 + 4);
     const float xs[4] = {x.x, x.y, x.z, x.w};
-    const float ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const float2 ws[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                          make_float2(w1.z, w1.w)};
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
+    for (int g = 0; g < 4; ++g) {
+      const float2 xg = make_float2(xs[g], xs[g]);
 #pragma unroll
-      for (int o = 0; o < 8; ++o) acc[g][o] = fmaf(ws[o], xs[g], acc[g][o]);
+      for (int o = 0; o < 4; ++o) a2[g][o] = __ffma2_rn(ws[o], xg, a2[g][o]);
+    }
   }
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      acc[g][2 * o] = a2[g][o].x;
+      acc[g][2 * o + 1] = a2[g][o].y;
+    }
 }
 
 __device__ __forceinline__ void store_relu(float* __restrict__ dst, int g4, int o8, const float (&acc)[4][8]) {
