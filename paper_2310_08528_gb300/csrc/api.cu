@@ -735,7 +735,7 @@ fs4d_status frame_front(const Env& e, const FramePart* parts, int n_parts, fs4d_
   const int tx = tiles_of(shape.width), ty = tiles_of(shape.height);
   const int tile_bits = ceil_log2((long long)tx * ty);
   const int N = (int)parts_total(parts, n_parts);
-  // every buffer the frame needs at zero, in one memset
+  // every buffer the frame needs at zero, in one allocation (cleared below)
   FrameZero& z = w.z;
   frame_zero_layout(N, tx * ty, cap, sort_passes(tile_bits), static_cast<unsigned char*>(w.zero.p), &z);
   if (z.bytes > w.zero.bytes) return fail(c, FS4D_ERR_INVALID_ARG, "frame work memory was not reserved");
