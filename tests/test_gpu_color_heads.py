@@ -136,6 +136,30 @@ def test_composition_with_color_heads_matches_oracle(ctx):
             ctx.unload_scene(sid)
 
 
+def test_composition_with_color_heads_bf16(ctx):
+    """BF16 composition of two scenes with heads and one without; the first has 60
+    Gaussians, so its f_d tile image (16 KB) runs past its share of the f_d buffer
+    into the next scene's, which the next deformation writes only after the first
+    scene's heads have read it.  PSNR against the oracle's composed frame."""
+    scenes = [sg.with_color_heads(sg.make_tiny(26, n=60, mlp_std=0.05), 8, std=0.08),
+              sg.with_color_heads(sg.make_tiny(27, n=4000, mlp_std=0.05), 9, std=0.08),
+              sg.make_tiny(28, n=2000, mlp_std=0.05)]
+    shifts = np.array([[0.0, 0.0, 0.0], [0.3, 0.1, -0.1], [-0.4, 0.2, 0.1]])
+    sids = [ctx.load_scene(x) for x in scenes]
+    cam = sg.tiny_camera(160, 128)
+    try:
+        bf = ctx.render_composed(sids, cam, 0.45, fs4d.BF16, shifts=shifts).cpu().numpy()
+        oracle.set_threads(oracle.default_threads())
+        fr = parity.oracle_frame_composed(scenes, shifts, cam, 0.45)
+        mse = float(np.mean((bf - fr["img"]) ** 2))
+        psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
+        print(f"composed BF16 with colour heads: PSNR {psnr:.1f} dB")
+        assert psnr >= 45.0
+    finally:
+        for sid in sids:
+            ctx.unload_scene(sid)
+
+
 def test_unsupported_calls_fail_loudly(ctx, tmp_path):
     s, cam = _scenes()[0]
     sid = ctx.load_scene(s)
