@@ -106,8 +106,10 @@ typedef struct fs4d_scene_desc {
   int32_t color_heads;         /* 0, or 1: the colour and opacity heads of App. B, applied in
                                   every frame: C' = C + phi_C(f_d) over the [K][3] SH
                                   coefficients, logit' = logit + phi_alpha(f_d) (f_d the output of
-                                  phi_d).  Such scenes render (fs4d_render*, composition) but have
-                                  no backward, trainer or serving (FS4D_ERR_UNIMPLEMENTED), and
+                                  phi_d); in FP32 frames by float32 SIMT arithmetic, in BF16 frames
+                                  as two BF16 tensor-core GEMMs per 128 Gaussians (FP32
+                                  accumulation).  Such scenes render (fs4d_render*, composition) but
+                                  have no backward, trainer or serving (FS4D_ERR_UNIMPLEMENTED), and
                                   fs4d_deform returns only X', r', s'. */
 } fs4d_scene_desc;
 
