@@ -1230,23 +1230,31 @@ __global__ void __launch_bounds__(256) wgrad_partial_kernel(const __grid_constan
   }
 }
 
+// Four threads per weight (adjacent lanes), each summing every fourth chunk in
+// eight running sums (eight loads in flight), then the four combined by two
+// shuffles: a fixed order, so the result is deterministic.
+constexpr int kRedSplit = 4;
 __global__ void wgrad_reduce_kernel(const __grid_constant__ WgradArgs wa) {
   const WgradLayer& ly = wa.l[blockIdx.y];
   const int O = ly.O, I = ly.I;
   const int E = O * I + O;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
+  const int e = blockIdx.x * (blockDim.x / kRedSplit) + (int)threadIdx.x / kRedSplit;
+  const int split = (int)threadIdx.x % kRedSplit;
+  const bool live = e < E;  // (every lane stays for the shuffles)
   const float* partial = wa.partial + ly.part_off;
-  // eight running sums (eight loads in flight), each over a fixed set of chunks and
-  // combined in a fixed order: deterministic
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int c = 0;
-  for (; c + 8 <= wa.chunks; c += 8) {
+  if (live) {
+    int c = split, k = 0;
+    for (; c + 7 * kRedSplit < wa.chunks; c += 8 * kRedSplit) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += partial[(long long)(c + u) * E + e];
+      for (int u = 0; u < 8; ++u) acc[u] += partial[(long long)(c + u * kRedSplit) * E + e];
+    }
+    for (; c < wa.chunks; c += kRedSplit, ++k) acc[k & 7] += partial[(long long)c * E + e];
   }
-  for (; c < wa.chunks; ++c) acc[c & 7] += partial[(long long)c * E + e];
-  const float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (!live || split != 0) return;
   if (e < O * I)
     ly.gW[e] += s;
   else
@@ -1297,7 +1305,7 @@ cudaError_t launch_wgrad(WgradArgs& a, cudaStream_t s) {
   wgrad_partial_kernel<<<dim3(a.chunks, a.n_layers), 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_reduce_kernel<<<dim3((maxE + 255) / 256, a.n_layers), 256, 0, s>>>(a);
+  wgrad_reduce_kernel<<<dim3((maxE + 256 / kRedSplit - 1) / (256 / kRedSplit), a.n_layers), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
