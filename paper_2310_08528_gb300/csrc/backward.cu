@@ -30,7 +30,6 @@ namespace {
 
 constexpr int kBatch = kTile * kTile;
 constexpr float kAlphaMax = 0.99f;
-constexpr float kDilation = 0.3f;
 constexpr float kGuard = 1.3f;
 
 // ------------------------------------------------------------------ compositing
