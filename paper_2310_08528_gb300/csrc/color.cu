@@ -1,103 +1,157 @@
-// Colour and opacity deformation (App. B): two more heads on the deformation
-// feature f_d, each Lin(64 -> 64), ReLU, Lin(64 -> out) like phi_x, phi_r, phi_s:
+// Colour and opacity deformation (App. B), float32 path: two more heads on the
+// deformation feature f_d, each Lin(64 -> 64), ReLU, Lin(64 -> out) like phi_x,
+// phi_r, phi_s:
 //   C' = C + phi_C(f_d)            (every SH coefficient, out = 3K)
 //   logit' = logit + phi_alpha(f_d) (the opacity as stored, out = 1)
-// The deformation kernels leave f_d (float32, after phi_d's second ReLU) in work
-// order; one thread per Gaussian runs both heads in float32 with the weights in
-// shared memory (read as broadcasts) and writes the frame's deformed SH and
-// opacity logits, which the projection then reads in place of the scene's.
-// FMA-bound SIMT work (~11.4k FMA per Gaussian), off the path of scenes without
-// these heads.
+// The FP32 deformation kernel leaves f_d (after phi_d's second ReLU) in work
+// order.  Persistent CTAs of 256 threads take tiles of 128 Gaussians: f_d is
+// transposed into shared memory (feature-major) and each layer is a register-
+// blocked SIMT GEMM -- a thread computes 4 Gaussians x 8 outputs with f32x2 FMAs
+// on output pairs, every output summed from its bias in input order, the same
+// float32 arithmetic per element as one thread per Gaussian -- over weights held
+// transposed in shared memory.  It writes the frame's deformed SH and opacity
+// logits, which the projection then reads in place of the scene's.
 #include "fs4d_internal.cuh"
 
 namespace fs4d {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr int kW = 64;
+constexpr int kTileG = 128;      // Gaussians per tile
+constexpr int kGS = kTileG + 4;  // row stride (floats) of the activation arrays
+constexpr int kOutC = 48;        // colour outputs, padded with zero weights (3K <= 48)
 
-// Shared-memory layout of the four layers (each weight block 16-byte aligned):
-// c1 W [64][64], c1 b [64], c2 W [3K][64], c2 b [3K], a1 W, a1 b, a2 W [64], a2 b.
-struct ColorSmem {
-  int c1w, c1b, c2w, c2b, a1w, a1b, a2w, a2b, total;
-};
-__host__ __device__ inline ColorSmem color_smem(int k3) {
-  ColorSmem m;
-  m.c1w = 0;
-  m.c1b = kW * kW;
-  m.c2w = m.c1b + kW;
-  m.c2b = m.c2w + k3 * kW;
-  m.a1w = (m.c2b + k3 + 3) & ~3;
-  m.a1b = m.a1w + kW * kW;
-  m.a2w = m.a1b + kW;
-  m.a2b = m.a2w + kW;
-  m.total = m.a2b + 1;
-  return m;
-}
+// Shared memory (floats): the weights transposed, Wt[in][out], and the biases of
+// c1 c2 a1 a2, then the activations F [64][kGS] (f_d) and H [64][kGS] (the hidden
+// layer of the head being evaluated).  Every row start is 16-byte aligned.
+constexpr int kC1 = 0;
+constexpr int kC1b = kC1 + kW * kW;
+constexpr int kC2 = kC1b + kW;
+constexpr int kC2b = kC2 + kW * kOutC;
+constexpr int kA1 = kC2b + kOutC;
+constexpr int kA1b = kA1 + kW * kW;
+constexpr int kA2 = kA1b + kW;
+constexpr int kA2b = kA2 + kW;
+constexpr int kF = (kA2b + 1 + 3) & ~3;
+constexpr int kH = kF + kW * kGS;
+constexpr int kTotal = kH + kW * kGS;
 
-// y[o] = relu(b[o] + sum_i W[o][i] x[i]) for a 64 x 64 layer.
-__device__ __forceinline__ void hidden64(const float* __restrict__ w, const float* __restrict__ b,
-                                         const float (&x)[kW], float (&y)[kW]) {
+// acc[g][o] = b[o8 + o] + sum_i Wt[i][o8 + o] src[i][g4 + g], in input order, for
+// the thread's 4 Gaussians (g4..) and 8 outputs (o8..) of a 64-input layer.
+__device__ __forceinline__ void tile_layer(const float* __restrict__ Wt, int ldo, const float* __restrict__ b,
+                                           const float* __restrict__ src, int g4, int o8, float (&acc)[4][8]) {
+  float2 a2[4][4];
 #pragma unroll
-  for (int o = 0; o < kW; ++o) {
-    const float4* row = reinterpret_cast<const float4*>(w + o * kW);
-    float acc = b[o];
+  for (int p = 0; p < 4; ++p) {
+    const float2 bp = make_float2(b[o8 + 2 * p], b[o8 + 2 * p + 1]);
 #pragma unroll
-    for (int i = 0; i < kW / 4; ++i) {
-      const float4 v = row[i];
-      acc = fmaf(v.x, x[4 * i], acc);
-      acc = fmaf(v.y, x[4 * i + 1], acc);
-      acc = fmaf(v.z, x[4 * i + 2], acc);
-      acc = fmaf(v.w, x[4 * i + 3], acc);
+    for (int g = 0; g < 4; ++g) a2[g][p] = bp;
+  }
+#pragma unroll 4
+  for (int i = 0; i < kW; ++i) {
+    const float4 x = *reinterpret_cast<const float4*>(src + i * kGS + g4);
+    const float4 w0 = *reinterpret_cast<const float4*>(Wt + i * ldo + o8);
+    const float4 w1 = *reinterpret_cast<const float4*>(Wt + i * ldo + o8 + 4);
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+    const float2 ws[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                          make_float2(w1.z, w1.w)};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float2 xg = make_float2(xs[g], xs[g]);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a2[g][p] = __ffma2_rn(ws[p], xg, a2[g][p]);
     }
-    y[o] = fmaxf(acc, 0.f);
   }
-}
-
-// bias + sum_i row[i] h[i] for one output of a layer (row: 64 weights, 16-byte aligned).
-__device__ __forceinline__ float out_row(const float* __restrict__ row_w, float bias, const float (&h)[kW]) {
-  const float4* row = reinterpret_cast<const float4*>(row_w);
-  float acc = bias;
 #pragma unroll
-  for (int i = 0; i < kW / 4; ++i) {
-    const float4 v = row[i];
-    acc = fmaf(v.x, h[4 * i], acc);
-    acc = fmaf(v.y, h[4 * i + 1], acc);
-    acc = fmaf(v.z, h[4 * i + 2], acc);
-    acc = fmaf(v.w, h[4 * i + 3], acc);
-  }
-  return acc;
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      acc[g][2 * p] = a2[g][p].x;
+      acc[g][2 * p + 1] = a2[g][p].y;
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) color_heads_kernel(const ColorArgs a) {
+// dst[o8 + o][g4 + g] = relu(acc[g][o])
+__device__ __forceinline__ void store_relu(float* __restrict__ dst, int g4, int o8, const float (&acc)[4][8]) {
+#pragma unroll
+  for (int o = 0; o < 8; ++o)
+    *reinterpret_cast<float4*>(dst + (o8 + o) * kGS + g4) =
+        make_float4(fmaxf(acc[0][o], 0.f), fmaxf(acc[1][o], 0.f), fmaxf(acc[2][o], 0.f), fmaxf(acc[3][o], 0.f));
+}
+
+__global__ void __launch_bounds__(kThreads, 2) color_heads_kernel(const ColorArgs a) {
   extern __shared__ float4 smem4[];
-  float* sw = reinterpret_cast<float*>(smem4);
-  const ColorSmem m = color_smem(a.k3);
-  // the source layout is contiguous (W then b per layer); a1 may move up to 3 floats
-  const int src_a1 = m.c2b + a.k3;
-  for (int i = threadIdx.x; i < src_a1; i += kThreads) sw[i] = a.weights[i];
-  for (int i = threadIdx.x; i < m.total - m.a1w; i += kThreads) sw[m.a1w + i] = a.weights[src_a1 + i];
-  __syncthreads();
-  const int i = blockIdx.x * kThreads + threadIdx.x;
-  if (i >= a.n) return;
-  const int g = a.perm ? (int)a.perm[i] : i;
-  float f[kW];
-  const float4* src = reinterpret_cast<const float4*>(a.fd + (size_t)i * kW);
-#pragma unroll
-  for (int k = 0; k < kW / 4; ++k) {
-    const float4 v = src[k];
-    f[4 * k] = v.x;
-    f[4 * k + 1] = v.y;
-    f[4 * k + 2] = v.z;
-    f[4 * k + 3] = v.w;
+  float* sm = reinterpret_cast<float*>(smem4);
+  const int tid = threadIdx.x;
+  const int k3 = a.k3;
+  // the source layout: W_C1 [64][64], b_C1, W_C2 [3K][64], b_C2, W_a1, b_a1, W_a2 [64], b_a2
+  const float* w = a.weights;
+  const int c1w = 0, c1b = kW * kW, c2w = c1b + kW, c2b = c2w + k3 * kW, a1w = c2b + k3, a1b = a1w + kW * kW,
+            a2w = a1b + kW, a2b = a2w + kW;
+  for (int e = tid; e < kW * kW; e += kThreads) {  // e = o * 64 + i  ->  Wt[i][o]
+    const int o = e / kW, i = e % kW;
+    sm[kC1 + i * kW + o] = w[c1w + e];
+    sm[kA1 + i * kW + o] = w[a1w + e];
   }
-  float h[kW];
-  hidden64(sw + m.c1w, sw + m.c1b, f, h);
-  const float* sh = a.sh + (size_t)g * a.k3;
-  float* sh_out = a.sh_out + (size_t)g * a.k3;
-  for (int o = 0; o < a.k3; ++o) sh_out[o] = sh[o] + out_row(sw + m.c2w + o * kW, sw[m.c2b + o], h);
-  hidden64(sw + m.a1w, sw + m.a1b, f, h);
-  a.logit_out[g] = a.logits[g] + out_row(sw + m.a2w, sw[m.a2b], h);
+  for (int e = tid; e < kOutC * kW; e += kThreads) {
+    const int o = e / kW, i = e % kW;
+    sm[kC2 + i * kOutC + o] = o < k3 ? w[c2w + o * kW + i] : 0.f;
+  }
+  for (int e = tid; e < kW; e += kThreads) {
+    sm[kC1b + e] = w[c1b + e];
+    sm[kA1b + e] = w[a1b + e];
+    sm[kA2 + e] = w[a2w + e];
+  }
+  for (int e = tid; e < kOutC; e += kThreads) sm[kC2b + e] = e < k3 ? w[c2b + e] : 0.f;
+  if (tid == 0) sm[kA2b] = w[a2b];
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g4 = lane * 4, o8 = warp * 8;
+  const long long tiles = ((long long)a.n + kTileG - 1) / kTileG;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long base = tile * kTileG;
+    __syncthreads();  // the weights are in; the previous tile is done with F and H
+    // f_d rows -> F [feature][Gaussian]
+    for (int e = tid; e < kTileG * (kW / 4); e += kThreads) {
+      const int r = e / (kW / 4), k4 = (e % (kW / 4)) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (base + r < a.n) v = __ldg(reinterpret_cast<const float4*>(a.fd + (size_t)(base + r) * kW + k4));
+      sm[kF + (k4 + 0) * kGS + r] = v.x;
+      sm[kF + (k4 + 1) * kGS + r] = v.y;
+      sm[kF + (k4 + 2) * kGS + r] = v.z;
+      sm[kF + (k4 + 3) * kGS + r] = v.w;
+    }
+    __syncthreads();
+    float acc[4][8];
+    // ---- phi_C: hidden layer into H, then the 3K outputs added to the SH
+    tile_layer(sm + kC1, kW, sm + kC1b, sm + kF, g4, o8, acc);
+    store_relu(sm + kH, g4, o8, acc);
+    __syncthreads();
+    if (o8 < k3) {  // warp-uniform: the warps whose outputs hold colour coefficients
+      tile_layer(sm + kC2, kOutC, sm + kC2b, sm + kH, g4, o8, acc);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const long long gi = base + g4 + g;
+        if (gi >= a.n) continue;
+        const size_t gg = a.perm ? (size_t)a.perm[gi] : (size_t)gi;
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          if (o8 + o < k3) a.sh_out[gg * k3 + o8 + o] = a.sh[gg * k3 + o8 + o] + acc[g][o];
+      }
+    }
+    __syncthreads();  // H is rewritten below
+    // ---- phi_alpha: hidden layer into H, then one output per Gaussian
+    tile_layer(sm + kA1, kW, sm + kA1b, sm + kF, g4, o8, acc);
+    store_relu(sm + kH, g4, o8, acc);
+    __syncthreads();
+    if (tid < kTileG && base + tid < a.n) {
+      float s = sm[kA2b];
+#pragma unroll 8
+      for (int o = 0; o < kW; ++o) s = fmaf(sm[kA2 + o], sm[kH + o * kGS + tid], s);
+      const size_t gg = a.perm ? (size_t)a.perm[base + tid] : (size_t)(base + tid);
+      a.logit_out[gg] = a.logits[gg] + s;
+    }
+  }
 }
 
 }  // namespace
@@ -106,15 +160,17 @@ int color_layer_floats(int k3) { return 2 * (kW * kW + kW) + k3 * kW + k3 + kW +
 
 cudaError_t launch_color_heads(const ColorArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (a.k3 < 3 || a.k3 > 48 || (reinterpret_cast<uintptr_t>(a.fd) & 15u)) return cudaErrorInvalidValue;
-  const size_t smem = 4 * (size_t)color_smem(a.k3).total;
+  if (a.k3 < 3 || a.k3 > kOutC || (reinterpret_cast<uintptr_t>(a.fd) & 15u)) return cudaErrorInvalidValue;
+  const size_t smem = 4 * (size_t)kTotal;
   static PerDeviceFlag attr;
   cudaError_t e = once_per_device(attr, [&] {
-    return cudaFuncSetAttribute(color_heads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * color_smem(48).total);
+    return cudaFuncSetAttribute(color_heads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return e;
-  color_heads_kernel<<<(a.n + kThreads - 1) / kThreads, kThreads, smem, s>>>(a);
+  const long long tiles = ((long long)a.n + kTileG - 1) / kTileG;
+  const int sms = device_sm_count();
+  const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
+  color_heads_kernel<<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
